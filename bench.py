@@ -1,0 +1,313 @@
+"""Benchmark: forward + adjoint Mpaths/s of one nested-SGD iteration of
+inverse path tracing on the 61k-triangle procedural room (8 views of
+320x240, 32 residual + 32 derivative samples per pixel, depth 5, NEE + MIS,
+L2 loss, Adam).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = light tables + forward (residual set) + fused residual + adjoint
+(derivative set) + loss/gradient reduction + Adam, with every input resident
+in device memory.  L2 is flushed (a 256 MiB write) between timed steps and
+the flush is outside each step's CUDA-event bracket.  Rank 0 prints one JSON
+line.  Under torchrun each rank optimises its own independent room (weak
+scaling, no collective in the data path).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="room_61k_tri", triangles=61160, segments=48, views=8, width=320,
+                height=240, spp_r=32, spp_d=32, max_depth=5, nee=True, mis=True, loss="l2",
+                init=0.5, target_spp=1024)
+METRIC = "fwd+adjoint Mpaths/s"
+NODE_BYTES, TRI_BYTES = 64, 48
+
+
+def paths_per_step():
+    w = WORKLOAD
+    return (w["spp_r"] + w["spp_d"]) * w["views"] * w["width"] * w["height"]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for s in self.samples for n, v in zip(names, s[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(target_seconds=15.0, seed=1001):
+    """The FP64 oracle (as it stands) on a bounded pixel sample of the same
+    workload: loss + gradient on the sampled pixels of all views."""
+    from oracle import oracle as O
+    from paper_1903_07145_gb300 import scenes
+    w = WORKLOAD
+    sc = scenes.room_60k(seed)
+    osc = O.OracleScene(sc)
+    p = scenes.initial_params(sc, w["init"])
+    rng = np.random.default_rng(0)
+    threads = O.default_threads()
+
+    def run(per_view):
+        pix = [rng.choice(w["width"] * w["height"], per_view, replace=False).astype(np.uint32)
+               for _ in sc.cameras]
+        targets = [np.full((w["width"] * w["height"], 3), 0.5) for _ in sc.cameras]
+        t0 = time.perf_counter()
+        O.loss_grad(osc, p, targets, w["spp_r"], w["spp_d"], w["max_depth"], seed=7, pixels=pix,
+                    threads=threads)
+        return time.perf_counter() - t0
+    per_view = 32
+    dt = run(per_view)
+    per_view = int(min(w["width"] * w["height"], max(32, per_view * target_seconds / max(dt, 1e-3))))
+    dt = run(per_view)
+    n_paths = per_view * len(sc.cameras) * (w["spp_r"] + w["spp_d"])
+    return {"value": n_paths / dt / 1e6, "unit": "Mpaths/s", "cores": threads, "kind": "oracle",
+            "sample": f"{per_view} random pixels per view x {len(sc.cameras)} views, "
+                      f"{w['spp_r']}+{w['spp_d']} paths each ({n_paths} paths, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    base = None
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(target_seconds=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            times.append(r["value"])
+        base = r
+    value = float(np.mean(times))
+    w = WORKLOAD
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": paths_per_step() / (value * 1e6) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": w["workload"], **{k: v for k, v in w.items() if k != "workload"},
+                                           "sample": base["sample"]},
+           "cpu_baseline": {**base, "value": value},
+           "e2e": {"value": value, "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        __graft_entry__.build()
+    from paper_1903_07145_gb300 import scenes
+    from paper_1903_07145_gb300 import _lib as L
+    from paper_1903_07145_gb300.tracer import AdamOptions, TraceOptions, Tracer
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOAD
+    sc = scenes.room_60k(1001 + rank)
+    opts = TraceOptions(spp_r=w["spp_r"], spp_d=w["spp_d"], max_depth=w["max_depth"], nee=True, mis=True)
+    adam = AdamOptions()
+    tr = Tracer(sc, device=local, seed=1903 + rank, flags=L.IPT_FLAG_KERNEL_TIMING)
+    # targets: the ground truth rendered with an independent sample set
+    tr.set_params(sc.gt_params)
+    target = tr.render(opts, view=-1, set_id=L.IPT_SET_TARGET, spp=w["target_spp"])
+    tr.set_targets(target)
+    tr.set_params(scenes.initial_params(sc, w["init"]))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        tr.step(opts, adam, want_loss=False)
+    torch.cuda.synchronize(dev)
+    tr.kernel_times(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            tr.step(opts, adam, want_loss=False)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ktimes = tr.kernel_times(reset=True)
+    loss_end = tr.loss_grad(opts, iteration=10_000)[0]
+
+    # algorithmic traffic of the dominant kernel: node and triangle fetches per
+    # launch, counted by a separate context with counters (same seeds, same paths)
+    ct = Tracer(sc, device=local, seed=1903 + rank, flags=L.IPT_FLAG_COUNTERS)
+    ct.set_targets(target)
+    ct.set_params(scenes.initial_params(sc, w["init"]))
+    ct.counters(reset=True)
+    ct.render(opts, view=-1, set_id=L.IPT_SET_RESIDUAL, spp=w["spp_r"])
+    fwd_cnt = ct.counters(reset=True)
+    g = torch.full((tr.n_pix, 3), 1.0, device=dev)
+    ct.backward(g, opts, set_id=L.IPT_SET_DERIVATIVE)
+    adj_cnt = ct.counters(reset=True)
+    ct.close()
+
+    # end to end through the C ABI with host buffers: targets uploaded from
+    # pinned memory, loss and parameters read back, every step
+    host_target = target.cpu().pin_memory()
+    host_params = np.zeros((sc.n_segments, 10), np.float32)
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        L.ipt_targets_set(tr.ctx, tr.sid, host_target.data_ptr(), 0)
+        tr.step(opts, adam, want_loss=True)
+        L.ipt_params_get(tr.ctx, tr.sid, host_params.ctypes.data)
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    tr.close()
+
+    if rank != 0:
+        return
+    n_paths = paths_per_step() * world
+    value = n_paths / (ms * 1e-3) / 1e6
+    dom = max(("forward", "adjoint"), key=lambda k: ktimes[k][0])
+    cnt = adj_cnt if dom == "adjoint" else fwd_cnt
+    dom_ms = ktimes[dom][0] / max(1, ktimes[dom][1])
+    alg_bytes = cnt["node_visits"] * NODE_BYTES + cnt["tri_tests"] * TRI_BYTES
+    peak, src = measured_peaks()
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    launches = sum(n for _, n in ktimes.values())
+    rays = sum(v for k, v in fwd_cnt.items() if k.endswith("rays")) + \
+        sum(v for k, v in adj_cnt.items() if k.endswith("rays"))
+    out = {
+        "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD["workload"], **{k: v for k, v in WORKLOAD.items() if k != "workload"},
+                   "l2": "256 MiB flush between timed steps (outside the step events)",
+                   "parallelism": f"{world} independent rooms, one per GPU"},
+        "mrays_per_s": rays / (ms * 1e-3) / 1e6,
+        "kernel_ms": {k: round(v[0] / max(1, v[1]), 4) for k, v in ktimes.items() if v[1]},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": src,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "units": {"node_visits": cnt["node_visits"], "tri_tests": cnt["tri_tests"],
+                               "rays": cnt["closest_rays"] + cnt["shadow_rays"]}},
+        "e2e": {"value": paths_per_step() / e2e_s / 1e6, "unit": "Mpaths/s",
+                "h2d_bytes_per_step": int(host_target.numel() * 4),
+                "d2h_bytes_per_step": int(8 + host_params.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "loss_after": loss_end,
+        "wall_s_timed_region": t_wall,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

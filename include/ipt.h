@@ -1,0 +1,250 @@
+/*
+ * ipt.h -- C ABI of the GB300 inverse path tracer.
+ *
+ * Inverse Path Tracing (Azinovic, Li, Kaplanyan, Niessner, CVPR 2019) recovers
+ * per-object materials and emission of a triangle-mesh scene from images with
+ * known camera poses, by nesting a differentiable Monte Carlo path tracer in
+ * stochastic gradient descent (Sec. 3, Fig. 2).  The problem statement gives
+ * the shape of this interface: geometry, segmentation, camera poses and images
+ * go in; the unknowns Theta = {M, L} (Sec. 3.2) are optimised and come out.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an ipt_status; nothing throws across the ABI.
+ *   - Host pointers are read during the call and copied; the caller keeps
+ *     ownership.  Device pointers must stay valid until the work queued on the
+ *     context's stream has finished; the library never frees them.
+ *   - Device work is queued on the context's CUDA stream.  Calls that return
+ *     host data (loss, parameters) synchronise that stream first.
+ *   - Argument errors are reported as IPT_ERR_INVALID_ARG before anything is
+ *     launched.  Errors found on the device (a traversal stack overflow) set a
+ *     status word that the next synchronising call returns as IPT_ERR_CUDA.
+ *   - ipt_last_error_detail gives a one-line description of the last error.
+ *   - A context is bound to one device and one stream and is not thread-safe.
+ *
+ * Parameters (Sec. 4.1, Sec. 4.2): one row of 10 floats per segment (object),
+ *   [kd_r, kd_g, kd_b, ks_r, ks_g, ks_b, roughness, e_r, e_g, e_b],
+ *   row-major S x 10.  f_r = kd/pi + ks * D G2 / (4 |n.wi| |n.wo|), GGX with
+ *   alpha = max(roughness^2, 1e-4), height-correlated Smith G2, no Fresnel.
+ *   Emitted radiance is emission_scale * e * profile, with the profile
+ *   (w . n)_+ of Sec. 4.3 (or a uniform front-face profile).
+ */
+#ifndef IPT_H_
+#define IPT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IPT_OK = 0,
+  IPT_ERR_INVALID_ARG = 1,
+  IPT_ERR_OUT_OF_MEMORY = 2,
+  IPT_ERR_CUDA = 3,
+  IPT_ERR_TIMEOUT = 4,
+  IPT_ERR_NONFINITE = 5,
+  IPT_ERR_NOT_READY = 6
+} ipt_status;
+
+typedef struct ipt_ctx ipt_ctx;
+
+/* ipt_options.flags bits. */
+#define IPT_FLAG_KERNEL_TIMING 1 /* time every launch with CUDA events on the context stream */
+#define IPT_FLAG_COUNTERS 2      /* count rays, BVH node visits and triangle tests */
+
+/* Kernel ids reported by ipt_kernel_times. */
+typedef enum {
+  IPT_KERNEL_PREPARE = 0,
+  IPT_KERNEL_FORWARD = 1,
+  IPT_KERNEL_ADJOINT = 2,
+  IPT_KERNEL_FINALIZE = 3,
+  IPT_KERNEL_ADAM = 4,
+  IPT_KERNEL_TRACE = 5,
+  IPT_KERNEL_PHILOX = 6,
+  IPT_KERNEL_COUNT = 7
+} ipt_kernel_id;
+
+/* device: CUDA device ordinal.  stream: a cudaStream_t (NULL = a stream the
+ * context creates and owns).  seed: Philox key for all sample sets. */
+typedef struct {
+  int32_t device;
+  void* stream;
+  uint64_t seed;
+  int32_t flags; /* IPT_FLAG_* bits */
+} ipt_options;
+
+/* Pinhole camera.  cam_to_world is row-major 3x4; its columns are the
+ * camera's right, up and backward axes and its position (the camera looks
+ * down its -z axis; image row 0 is the top).  Pixel j integrates a box filter
+ * over its own footprint (h_j in Eq. 1). */
+typedef struct {
+  float cam_to_world[12];
+  float fov_y_deg;
+  uint32_t width;
+  uint32_t height;
+} ipt_camera;
+
+/* Per-call tracing options.
+ *   spp_r, spp_d: samples per pixel of the residual image and of the
+ *     derivative estimate; the two use independent sample sets (Sec. 3.3),
+ *     unless gradcheck_same_set is non-zero.
+ *   max_depth: number of scattering events (1 = direct light only, App. A.3).
+ *   loss: 0 = L2, 1 = L1 (Eq. 3).
+ *   nee, mis: light sampling and its MIS with BRDF sampling (App. A.2).
+ *   emission_profile: 0 = (w.n)_+ (Sec. 4.3), 1 = uniform over the front face. */
+typedef struct {
+  uint32_t spp_r;
+  uint32_t spp_d;
+  uint32_t max_depth;
+  int32_t loss;
+  int32_t nee;
+  int32_t mis;
+  int32_t emission_profile;
+  int32_t gradcheck_same_set;
+} ipt_trace_opts;
+
+/* Adam (Sec. 4.5: Adam, learning rate 5e-3) plus the L1 emission regulariser
+ * of Sec. 4.4 with weight l1_emission; after the update kd, ks are clamped
+ * to [0,1], roughness to [0.02,1], emission to >= 0. */
+typedef struct {
+  float lr;
+  float beta1;
+  float beta2;
+  float eps;
+  float l1_emission;
+} ipt_adam_opts;
+
+/* Sample-set ids for ipt_render / ipt_backward. */
+#define IPT_SET_RESIDUAL 0u
+#define IPT_SET_DERIVATIVE 1u
+#define IPT_SET_TARGET 2u
+
+/* Create a context on opt->device.  *out receives the handle.  Fails with
+ * IPT_ERR_CUDA if the device cannot be used. */
+ipt_status ipt_create(ipt_ctx** out, const ipt_options* opt);
+
+/* Release every device buffer the context owns.  NULL is accepted. */
+ipt_status ipt_destroy(ipt_ctx* ctx);
+
+/* Static string for a status code. */
+const char* ipt_status_string(ipt_status s);
+
+/* Copy the last error message (NUL-terminated, truncated to n bytes). */
+ipt_status ipt_last_error_detail(const ipt_ctx* ctx, char* buf, size_t n);
+
+/* Scene geometry (Sec. 4.2): n_vert positions (host, n_vert x 3), optional
+ * per-vertex normals (host, n_vert x 3, NULL = geometric normals; when given
+ * they are interpolated with barycentrics), n_tri index triples (host), a
+ * segment id per triangle (host, each < n_seg).  Builds the BVH (binned SAH)
+ * and the per-segment light-selection tables, uploads everything and returns
+ * the scene's id.  Errors: non-finite coordinates, out-of-range index or
+ * segment id, zero triangles, degenerate (zero-area) triangles. */
+ipt_status ipt_scene_upload(ipt_ctx* ctx, const float* pos, uint32_t n_vert, const float* nrm,
+                            const uint32_t* idx, uint32_t n_tri, const uint32_t* tri_seg,
+                            uint32_t n_seg, float emission_scale, int32_t* scene_id);
+
+/* Camera poses and (optionally) the captured images I_C (Sec. 3.2, 3.4).
+ * cams: host array of n_views cameras.  target_rgb: linear RGB, the views'
+ * W*H*3 float images concatenated in view order; host or device according to
+ * target_on_device; NULL keeps no target.  Copied into the context. */
+ipt_status ipt_views_set(ipt_ctx* ctx, int32_t scene, const ipt_camera* cams, uint32_t n_views,
+                         const float* target_rgb, int32_t target_on_device);
+
+/* Replace the targets only (same layout as ipt_views_set). */
+ipt_status ipt_targets_set(ipt_ctx* ctx, int32_t scene, const float* target_rgb,
+                           int32_t target_on_device);
+
+/* Parameters Theta: host S x 10 floats (layout above).  free_mask: host
+ * S x 10 bytes, non-zero = optimised (NULL = all free).  Resets the Adam
+ * moments and step counter. */
+ipt_status ipt_params_set(ipt_ctx* ctx, int32_t scene, const float* params,
+                          const uint8_t* free_mask);
+
+/* Copy the current parameters to host memory (S x 10 floats). */
+ipt_status ipt_params_get(ipt_ctx* ctx, int32_t scene, float* params_out);
+
+/* Device pointer of the context's S x 10 parameter buffer (valid until the
+ * scene is destroyed). */
+ipt_status ipt_params_device(ipt_ctx* ctx, int32_t scene, float** params_dev);
+
+/* Forward render (Eq. 1-2) of one view (view >= 0) or all views (view = -1,
+ * images concatenated in view order): per-pixel mean over `spp` samples of
+ * sample set `set` at iteration `iteration`, and optionally the per-pixel
+ * mean of squares (for standard errors).  params / sampling_params: device
+ * S x 10 (NULL = the context's parameters; sampling_params NULL = params).
+ * Sampling decisions (lobe choice, light selection, MIS weights) use
+ * sampling_params; BRDF values and emission use params.  rgb_out, msq_out:
+ * device float arrays of pixels x 3 (msq_out may be NULL). */
+ipt_status ipt_render(ipt_ctx* ctx, int32_t scene, int32_t view, const ipt_trace_opts* opts,
+                      uint32_t set, uint32_t spp, uint64_t iteration, const float* params,
+                      const float* sampling_params, float* rgb_out, float* msq_out);
+
+/* Vector-Jacobian product of the rendered images (Eq. 5-6): grad_out (device
+ * S x 10, overwritten) = sum over all pixels of all views and channels of
+ * grad_image * d(mean over spp_d samples of set `set`)/d(params), with pdfs,
+ * MIS weights and light selection held at sampling_params.  grad_image:
+ * device, all views concatenated, pixels x 3. */
+ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t set,
+                        uint64_t iteration, const float* params, const float* sampling_params,
+                        const float* grad_image, float* grad_out);
+
+/* One gradient evaluation of the nested SGD (Sec. 3.2-3.4): render the
+ * residual set with spp_r, compare with the targets (L2 or L1, normalised by
+ * the number of pixel-channels N), and trace the derivative set with spp_d
+ * to accumulate dE/dTheta.  loss_out (host, may be NULL) receives E; grad_out
+ * (device S x 10, may be NULL to keep the gradient in the context). */
+ipt_status ipt_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
+                         uint64_t iteration, double* loss_out, float* grad_out);
+
+/* Adam step on the context's parameters (Sec. 4.5) with grad (device S x 10;
+ * NULL = the gradient left by ipt_loss_grad). */
+ipt_status ipt_adam_step(ipt_ctx* ctx, int32_t scene, const float* grad,
+                         const ipt_adam_opts* adam);
+
+/* ipt_loss_grad followed by ipt_adam_step; the iteration counter lives on
+ * the device and advances by one.  loss_out (host, may be NULL) receives the
+ * loss of this step and makes the call synchronous. */
+ipt_status ipt_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
+                    const ipt_adam_opts* adam, double* loss_out);
+
+/* Closest-hit ray casting (the paper's Embree queries, App. E): n rays,
+ * device arrays orig and dir (n x 3 floats), optional skip triangle per ray
+ * (device int32, -1 = none), t in (0, inf).  Outputs (device, n each):
+ * original triangle id or -1, t, barycentrics u, v with hit point
+ * (1-u-v) p0 + u p1 + v p2.  Any output but tri_out may be NULL. */
+ipt_status ipt_trace_rays(ipt_ctx* ctx, int32_t scene, uint32_t n, const float* orig,
+                          const float* dir, const int32_t* skip, int32_t* tri_out, float* t_out,
+                          float* u_out, float* v_out);
+
+/* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator behind
+ * every random decision: out[4i..4i+3] = philox(ctr[4i..4i+3], key[2i..2i+1]).
+ * All arrays on the device. */
+ipt_status ipt_philox(ipt_ctx* ctx, uint32_t n, const uint32_t* ctr, const uint32_t* key,
+                      uint32_t* out);
+
+/* Wait for the context's stream and return any device-side error. */
+ipt_status ipt_synchronize(ipt_ctx* ctx);
+
+/* Scene statistics: triangles, segments, BVH inner nodes, BVH depth,
+ * views, total pixels.  Any pointer may be NULL. */
+ipt_status ipt_scene_info(ipt_ctx* ctx, int32_t scene, uint32_t* n_tri, uint32_t* n_seg,
+                          uint32_t* n_nodes, uint32_t* bvh_depth, uint32_t* n_views,
+                          uint64_t* n_pixels);
+
+/* Per-kernel device time (requires IPT_FLAG_KERNEL_TIMING): total_ms and
+ * launches are arrays of IPT_KERNEL_COUNT entries (either may be NULL),
+ * accumulated since the last reset.  Synchronises the context's stream. */
+ipt_status ipt_kernel_times(ipt_ctx* ctx, double* total_ms, uint64_t* launches, int32_t reset);
+
+/* Traversal counters (requires IPT_FLAG_COUNTERS): out[0] closest-hit rays,
+ * out[1] shadow rays, out[2] BVH inner-node visits, out[3] triangle tests,
+ * accumulated since the last reset.  Synchronises the context's stream. */
+ipt_status ipt_counters_read(ipt_ctx* ctx, uint64_t* out, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPT_H_ */

@@ -1,0 +1,213 @@
+"""ctypes binding of libipt.so (include/ipt.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and raises
+IptError on a non-zero status.  Device buffers are passed as integer device
+pointers (e.g. ``tensor.data_ptr()``); nothing here computes any part of the
+path.  If the shared library is missing the import of a call fails loudly:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libipt.so")
+
+IPT_OK = 0
+IPT_SET_RESIDUAL, IPT_SET_DERIVATIVE, IPT_SET_TARGET = 0, 1, 2
+
+EXPORTED = [
+    "ipt_create", "ipt_destroy", "ipt_status_string", "ipt_last_error_detail",
+    "ipt_scene_upload", "ipt_views_set", "ipt_targets_set", "ipt_params_set",
+    "ipt_params_get", "ipt_params_device", "ipt_render", "ipt_backward", "ipt_loss_grad",
+    "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_philox", "ipt_synchronize",
+    "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read",
+]
+IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS = 1, 2
+KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox"]
+
+
+class IptError(RuntimeError):
+    def __init__(self, status, detail=""):
+        self.status = status
+        super().__init__(f"ipt status {status}: {detail}")
+
+
+class ipt_options(C.Structure):
+    _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("seed", C.c_uint64),
+                ("flags", C.c_int32)]
+
+
+class ipt_camera(C.Structure):
+    _fields_ = [("cam_to_world", C.c_float * 12), ("fov_y_deg", C.c_float),
+                ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class ipt_trace_opts(C.Structure):
+    _fields_ = [("spp_r", C.c_uint32), ("spp_d", C.c_uint32), ("max_depth", C.c_uint32),
+                ("loss", C.c_int32), ("nee", C.c_int32), ("mis", C.c_int32),
+                ("emission_profile", C.c_int32), ("gradcheck_same_set", C.c_int32)]
+
+
+class ipt_adam_opts(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("l1_emission", C.c_float)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libipt.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: run paper_1903_07145_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            P, U32, I32, U64 = C.c_void_p, C.c_uint32, C.c_int32, C.c_uint64
+            sig = {
+                "ipt_create": [C.POINTER(P), C.POINTER(ipt_options)],
+                "ipt_destroy": [P],
+                "ipt_last_error_detail": [P, C.c_char_p, C.c_size_t],
+                "ipt_scene_upload": [P, P, U32, P, P, U32, P, U32, C.c_float, C.POINTER(I32)],
+                "ipt_views_set": [P, I32, C.POINTER(ipt_camera), U32, P, I32],
+                "ipt_targets_set": [P, I32, P, I32],
+                "ipt_params_set": [P, I32, P, P],
+                "ipt_params_get": [P, I32, P],
+                "ipt_params_device": [P, I32, C.POINTER(P)],
+                "ipt_render": [P, I32, I32, C.POINTER(ipt_trace_opts), U32, U32, U64, P, P, P, P],
+                "ipt_backward": [P, I32, C.POINTER(ipt_trace_opts), U32, U64, P, P, P, P],
+                "ipt_loss_grad": [P, I32, C.POINTER(ipt_trace_opts), U64, C.POINTER(C.c_double), P],
+                "ipt_adam_step": [P, I32, P, C.POINTER(ipt_adam_opts)],
+                "ipt_step": [P, I32, C.POINTER(ipt_trace_opts), C.POINTER(ipt_adam_opts),
+                             C.POINTER(C.c_double)],
+                "ipt_trace_rays": [P, I32, U32, P, P, P, P, P, P, P],
+                "ipt_philox": [P, U32, P, P, P],
+                "ipt_synchronize": [P],
+                "ipt_scene_info": [P, I32, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32),
+                                   C.POINTER(U32), C.POINTER(U32), C.POINTER(U64)],
+                "ipt_kernel_times": [P, C.POINTER(C.c_double), C.POINTER(U64), I32],
+                "ipt_counters_read": [P, C.POINTER(U64), I32],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            L.ipt_status_string.argtypes = [C.c_int]
+            L.ipt_status_string.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != IPT_OK:
+        buf = C.create_string_buffer(512)
+        if ctx:
+            lib().ipt_last_error_detail(ctx, buf, 512)
+        msg = lib().ipt_status_string(status).decode()
+        raise IptError(status, f"{msg}: {buf.value.decode()}")
+
+
+def ipt_create(device=0, stream=0, seed=0, flags=0):
+    o = ipt_options(device, stream or None, seed, flags)
+    h = C.c_void_p()
+    _check(None, lib().ipt_create(C.byref(h), C.byref(o)))
+    return h
+
+
+def ipt_destroy(ctx):
+    _check(None, lib().ipt_destroy(ctx))
+
+
+def ipt_scene_upload(ctx, pos, n_vert, nrm, idx, n_tri, tri_seg, n_seg, emission_scale):
+    sid = C.c_int32()
+    _check(ctx, lib().ipt_scene_upload(ctx, pos, n_vert, nrm, idx, n_tri, tri_seg, n_seg,
+                                       emission_scale, C.byref(sid)))
+    return sid.value
+
+
+def ipt_views_set(ctx, scene, cams, n_views, target, target_on_device):
+    _check(ctx, lib().ipt_views_set(ctx, scene, cams, n_views, target, target_on_device))
+
+
+def ipt_targets_set(ctx, scene, target, target_on_device):
+    _check(ctx, lib().ipt_targets_set(ctx, scene, target, target_on_device))
+
+
+def ipt_params_set(ctx, scene, params, free_mask):
+    _check(ctx, lib().ipt_params_set(ctx, scene, params, free_mask))
+
+
+def ipt_params_get(ctx, scene, out):
+    _check(ctx, lib().ipt_params_get(ctx, scene, out))
+
+
+def ipt_params_device(ctx, scene):
+    p = C.c_void_p()
+    _check(ctx, lib().ipt_params_device(ctx, scene, C.byref(p)))
+    return p.value
+
+
+def ipt_render(ctx, scene, view, opts, set_id, spp, iteration, params, sparams, rgb, msq):
+    _check(ctx, lib().ipt_render(ctx, scene, view, C.byref(opts), set_id, spp, iteration,
+                                 params, sparams, rgb, msq))
+
+
+def ipt_backward(ctx, scene, opts, set_id, iteration, params, sparams, grad_image, grad_out):
+    _check(ctx, lib().ipt_backward(ctx, scene, C.byref(opts), set_id, iteration, params, sparams,
+                                   grad_image, grad_out))
+
+
+def ipt_loss_grad(ctx, scene, opts, iteration, want_loss, grad_out):
+    loss = C.c_double()
+    _check(ctx, lib().ipt_loss_grad(ctx, scene, C.byref(opts), iteration,
+                                    C.byref(loss) if want_loss else None, grad_out))
+    return loss.value if want_loss else None
+
+
+def ipt_adam_step(ctx, scene, grad, adam):
+    _check(ctx, lib().ipt_adam_step(ctx, scene, grad, C.byref(adam)))
+
+
+def ipt_step(ctx, scene, opts, adam, want_loss):
+    loss = C.c_double()
+    _check(ctx, lib().ipt_step(ctx, scene, C.byref(opts), C.byref(adam),
+                               C.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def ipt_trace_rays(ctx, scene, n, orig, dirs, skip, tri, t, u, v):
+    _check(ctx, lib().ipt_trace_rays(ctx, scene, n, orig, dirs, skip, tri, t, u, v))
+
+
+def ipt_philox(ctx, n, ctr, key, out):
+    _check(ctx, lib().ipt_philox(ctx, n, ctr, key, out))
+
+
+def ipt_synchronize(ctx):
+    _check(ctx, lib().ipt_synchronize(ctx))
+
+
+def ipt_scene_info(ctx, scene):
+    a = [C.c_uint32() for _ in range(5)]
+    npx = C.c_uint64()
+    _check(ctx, lib().ipt_scene_info(ctx, scene, *[C.byref(x) for x in a], C.byref(npx)))
+    return dict(n_tri=a[0].value, n_seg=a[1].value, n_nodes=a[2].value, bvh_depth=a[3].value,
+                n_views=a[4].value, n_pixels=npx.value)
+
+
+def ipt_kernel_times(ctx, reset=False):
+    ms = (C.c_double * len(KERNEL_NAMES))()
+    n = (C.c_uint64 * len(KERNEL_NAMES))()
+    _check(ctx, lib().ipt_kernel_times(ctx, ms, n, int(reset)))
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_NAMES)}
+
+
+def ipt_counters_read(ctx, reset=False):
+    out = (C.c_uint64 * 4)()
+    _check(ctx, lib().ipt_counters_read(ctx, out, int(reset)))
+    return dict(closest_rays=out[0], shadow_rays=out[1], node_visits=out[2], tri_tests=out[3])

@@ -1,0 +1,680 @@
+// C ABI of the GB300 inverse path tracer: context, scenes, views, parameters
+// and the calls of one nested-SGD iteration.  See include/ipt.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ipt.h"
+#include "ipt_internal.h"
+
+using ipt::HostScene;
+
+namespace {
+
+struct DeviceScene {
+  uint32_t n_tri = 0, n_seg = 0, n_nodes = 0, depth = 0;
+  float eps = 0.f, emission_scale = 1.f;
+  // geometry
+  float4* nodes = nullptr;
+  float4* tris = nullptr;
+  float4* vnrm = nullptr;
+  uint32_t* seg_tris = nullptr;
+  uint32_t* seg_begin = nullptr;
+  double* tri_cdf = nullptr;
+  double* seg_area = nullptr;
+  uint32_t* orig_to_internal = nullptr;
+  // parameter tables
+  ipt::SegBuffers tab{};
+  bool tab_is_ctx = false;  // tables were built from the context's own parameters
+  // parameters and optimiser state
+  float* params = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  uint8_t* free_mask = nullptr;
+  int* step_dev = nullptr;
+  bool params_set = false;
+  // views and per-pixel buffers
+  std::vector<ipt::ViewHost> views;
+  ipt::ViewHost* views_dev = nullptr;
+  uint64_t n_pix = 0;
+  float* target = nullptr;
+  float* g_img = nullptr;
+  // reductions
+  double* grad_acc = nullptr;
+  float* grad_f = nullptr;
+  double* loss_partials = nullptr;
+  double* loss_dev = nullptr;
+  uint64_t iteration = 0;
+  std::vector<void*> owned;
+};
+
+}  // namespace
+
+struct PendingTiming {
+  int id;
+  cudaEvent_t a, b;
+};
+
+struct ipt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t seed = 0;
+  int flags = 0;
+  ipt::Launcher L;
+  std::vector<DeviceScene*> scenes;
+  std::string last_error;
+  uint32_t* err_dev = nullptr;
+  double* loss_host = nullptr;  // pinned
+  unsigned long long* counters_dev = nullptr;
+  std::vector<PendingTiming> pending;
+  std::vector<cudaEvent_t> spare_events;
+  double kernel_ms[IPT_KERNEL_COUNT] = {0};
+  uint64_t kernel_n[IPT_KERNEL_COUNT] = {0};
+};
+
+namespace {
+
+ipt_status fail(ipt_ctx* c, ipt_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+ipt_status cuda_fail(ipt_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? IPT_ERR_OUT_OF_MEMORY : IPT_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define IPT_CK(expr)                                          \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr);  \
+  } while (0)
+
+template <class T>
+cudaError_t dev_alloc(DeviceScene* s, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+  if (e == cudaSuccess) {
+    s->owned.push_back(q);
+    *p = static_cast<T*>(q);
+  }
+  return e;
+}
+
+void free_scene(DeviceScene* s) {
+  if (!s) return;
+  for (void* p : s->owned) cudaFree(p);
+  delete s;
+}
+
+// Resolves recorded event pairs into per-kernel totals (waits for them).
+void resolve_timings(ipt_ctx* c) {
+  for (const PendingTiming& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->kernel_ms[p.id] += ms;
+      c->kernel_n[p.id] += 1;
+    }
+    c->spare_events.push_back(p.a);
+    c->spare_events.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+cudaEvent_t take_event(ipt_ctx* c) {
+  if (!c->spare_events.empty()) {
+    cudaEvent_t e = c->spare_events.back();
+    c->spare_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch with CUDA events on the context stream when kernel
+// timing is on.
+struct Timed {
+  ipt_ctx* c;
+  int id;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(ipt_ctx* ctx, int kernel) : c(ctx), id(kernel) {
+    if (c->flags & IPT_FLAG_KERNEL_TIMING) {
+      if (c->pending.size() > 8192) resolve_timings(c);
+      a = take_event(c);
+      b = take_event(c);
+      if (a && b) cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Timed() {
+    if (a && b) {
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({id, a, b});
+    }
+  }
+};
+
+ipt::SceneBuffers buffers(const ipt_ctx* ctx, const DeviceScene* s) {
+  ipt::SceneBuffers b;
+  b.counters = ctx->counters_dev;
+  b.nodes = s->nodes;
+  b.tris = s->tris;
+  b.vnrm = s->vnrm;
+  b.seg_tris = s->seg_tris;
+  b.seg_begin = s->seg_begin;
+  b.tri_cdf = s->tri_cdf;
+  b.seg_area = s->seg_area;
+  b.orig_to_internal = s->orig_to_internal;
+  b.n_seg = s->n_seg;
+  b.n_tri = s->n_tri;
+  b.eps = s->eps;
+  b.emission_scale = s->emission_scale;
+  return b;
+}
+
+ipt_status get_scene(ipt_ctx* ctx, int32_t id, DeviceScene** out) {
+  if (!ctx) return IPT_ERR_INVALID_ARG;
+  if (id < 0 || (size_t)id >= ctx->scenes.size() || !ctx->scenes[id])
+    return fail(ctx, IPT_ERR_INVALID_ARG, "unknown scene id " + std::to_string(id));
+  *out = ctx->scenes[id];
+  return IPT_OK;
+}
+
+ipt_status check_opts(ipt_ctx* ctx, const ipt_trace_opts* o, bool adjoint) {
+  if (!o) return fail(ctx, IPT_ERR_INVALID_ARG, "null trace options");
+  const uint32_t maxd = adjoint ? ipt::kMaxAdjointDepth : ipt::kMaxForwardDepth;
+  if (o->max_depth > maxd)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "max_depth " + std::to_string(o->max_depth) + " above limit " +
+                                              std::to_string(maxd));
+  if (o->loss != 0 && o->loss != 1) return fail(ctx, IPT_ERR_INVALID_ARG, "loss must be 0 (L2) or 1 (L1)");
+  if (o->emission_profile != 0 && o->emission_profile != 1)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "emission_profile must be 0 or 1");
+  return IPT_OK;
+}
+
+ipt::TraceParams trace_params(const ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* o, uint32_t set,
+                              uint32_t spp, uint64_t it) {
+  ipt::TraceParams tp;
+  tp.seed = ctx->seed;
+  tp.scene_id = (uint32_t)scene;
+  tp.set = set;
+  tp.iteration = it;
+  tp.spp = spp;
+  tp.max_depth = o->max_depth;
+  tp.nee = o->nee;
+  tp.mis = o->mis;
+  tp.profile = o->emission_profile;
+  return tp;
+}
+
+ipt_status ensure_tables(ipt_ctx* ctx, DeviceScene* s, const float* params, const float* sparams) {
+  const bool is_ctx = (params == s->params) && (sparams == nullptr || sparams == s->params);
+  if (is_ctx && s->tab_is_ctx) return IPT_OK;
+  Timed tm(ctx, IPT_KERNEL_PREPARE);
+  IPT_CK(ipt::launch_prepare(buffers(ctx, s), s->tab, params, sparams ? sparams : params, ctx->stream));
+  s->tab_is_ctx = is_ctx;
+  return IPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ipt_status_string(ipt_status s) {
+  switch (s) {
+    case IPT_OK: return "ok";
+    case IPT_ERR_INVALID_ARG: return "invalid argument";
+    case IPT_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case IPT_ERR_CUDA: return "CUDA error";
+    case IPT_ERR_TIMEOUT: return "timeout";
+    case IPT_ERR_NONFINITE: return "non-finite value";
+    case IPT_ERR_NOT_READY: return "not ready";
+  }
+  return "unknown status";
+}
+
+ipt_status ipt_last_error_detail(const ipt_ctx* ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return IPT_ERR_INVALID_ARG;
+  std::snprintf(buf, n, "%s", ctx->last_error.c_str());
+  return IPT_OK;
+}
+
+ipt_status ipt_create(ipt_ctx** out, const ipt_options* opt) {
+  if (!out || !opt) return IPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  ipt_ctx* ctx = new (std::nothrow) ipt_ctx();
+  if (!ctx) return IPT_ERR_OUT_OF_MEMORY;
+  ctx->device = opt->device;
+  ctx->seed = opt->seed;
+  ctx->flags = opt->flags;
+  cudaError_t e = cudaSetDevice(opt->device);
+  if (e == cudaSuccess && opt->stream) {
+    ctx->stream = static_cast<cudaStream_t>(opt->stream);
+  } else if (e == cudaSuccess) {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    ctx->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = ipt::init_launcher(&ctx->L, opt->device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->err_dev, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->loss_host, sizeof(double));
+  if (e == cudaSuccess && (opt->flags & IPT_FLAG_COUNTERS)) {
+    e = cudaMalloc(&ctx->counters_dev, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->counters_dev, 0, 4 * sizeof(unsigned long long));
+  }
+  if (e != cudaSuccess) {
+    ipt_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? IPT_ERR_OUT_OF_MEMORY : IPT_ERR_CUDA;
+  }
+  *out = ctx;
+  return IPT_OK;
+}
+
+ipt_status ipt_destroy(ipt_ctx* ctx) {
+  if (!ctx) return IPT_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (DeviceScene* s : ctx->scenes) free_scene(s);
+  resolve_timings(ctx);
+  for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
+  if (ctx->counters_dev) cudaFree(ctx->counters_dev);
+  if (ctx->err_dev) cudaFree(ctx->err_dev);
+  if (ctx->loss_host) cudaFreeHost(ctx->loss_host);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return IPT_OK;
+}
+
+ipt_status ipt_scene_upload(ipt_ctx* ctx, const float* pos, uint32_t n_vert, const float* nrm,
+                            const uint32_t* idx, uint32_t n_tri, const uint32_t* tri_seg,
+                            uint32_t n_seg, float emission_scale, int32_t* scene_id) {
+  if (!ctx || !scene_id) return IPT_ERR_INVALID_ARG;
+  if (!(emission_scale > 0.0f) || !std::isfinite(emission_scale))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "emission_scale must be positive and finite");
+  HostScene hs;
+  std::string err;
+  if (!ipt::build_scene(pos, n_vert, nrm, idx, n_tri, tri_seg, n_seg, &hs, &err))
+    return fail(ctx, IPT_ERR_INVALID_ARG, err);
+  IPT_CK(cudaSetDevice(ctx->device));
+  DeviceScene* s = new (std::nothrow) DeviceScene();
+  if (!s) return IPT_ERR_OUT_OF_MEMORY;
+  s->n_tri = hs.n_tri;
+  s->n_seg = hs.n_seg;
+  s->n_nodes = hs.n_nodes;
+  s->depth = hs.depth;
+  s->eps = (float)(1e-5 * hs.diameter);
+  s->emission_scale = emission_scale;
+  const uint32_t S = n_seg;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t n) {
+    if (e == cudaSuccess) e = dev_alloc(s, p, n);
+  };
+  A(&s->nodes, 4 * (size_t)hs.n_nodes);
+  A(&s->tris, 3 * (size_t)n_tri);
+  if (!hs.vnrm.empty()) A(&s->vnrm, 3 * (size_t)n_tri);
+  A(&s->seg_tris, n_tri);
+  A(&s->seg_begin, S + 1);
+  A(&s->tri_cdf, n_tri);
+  A(&s->seg_area, S);
+  A(&s->orig_to_internal, n_tri);
+  A(&s->tab.mat_a, S);
+  A(&s->tab.mat_b, S);
+  A(&s->tab.emis, S);
+  A(&s->tab.samp, S);
+  A(&s->tab.pspec, S);
+  A(&s->tab.cdf, S);
+  A(&s->tab.lum, S);
+  A(&s->tab.W, 1);
+  A(&s->params, 10 * (size_t)S);
+  A(&s->adam_m, 10 * (size_t)S);
+  A(&s->adam_v, 10 * (size_t)S);
+  A(&s->free_mask, 10 * (size_t)S);
+  A(&s->step_dev, 1);
+  A(&s->grad_acc, 10 * (size_t)S);
+  A(&s->grad_f, 10 * (size_t)S);
+  A(&s->loss_partials, (size_t)ipt::loss_partials_capacity(ctx->L));
+  A(&s->loss_dev, 1);
+  auto H = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  H(s->nodes, hs.nodes.data(), hs.nodes.size() * sizeof(float));
+  H(s->tris, hs.tris.data(), hs.tris.size() * sizeof(float));
+  if (s->vnrm) H(s->vnrm, hs.vnrm.data(), hs.vnrm.size() * sizeof(float));
+  H(s->seg_tris, hs.seg_tris.data(), hs.seg_tris.size() * sizeof(uint32_t));
+  H(s->seg_begin, hs.seg_begin.data(), hs.seg_begin.size() * sizeof(uint32_t));
+  H(s->tri_cdf, hs.tri_cdf.data(), hs.tri_cdf.size() * sizeof(double));
+  H(s->seg_area, hs.seg_area.data(), hs.seg_area.size() * sizeof(double));
+  H(s->orig_to_internal, hs.orig_to_internal.data(), hs.orig_to_internal.size() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(s->params, 0, 10 * sizeof(float) * S);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, 10 * sizeof(float) * S);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, 10 * sizeof(float) * S);
+  if (e == cudaSuccess) e = cudaMemset(s->free_mask, 1, 10 * S);
+  if (e == cudaSuccess) e = cudaMemset(s->step_dev, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_scene(s);
+    return cuda_fail(ctx, e, "scene upload");
+  }
+  ctx->scenes.push_back(s);
+  *scene_id = (int32_t)ctx->scenes.size() - 1;
+  return IPT_OK;
+}
+
+ipt_status ipt_views_set(ipt_ctx* ctx, int32_t scene, const ipt_camera* cams, uint32_t n_views,
+                         const float* target_rgb, int32_t target_on_device) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!cams || n_views == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "need at least one view");
+  std::vector<ipt::ViewHost> v(n_views);
+  uint64_t off = 0;
+  for (uint32_t i = 0; i < n_views; ++i) {
+    const ipt_camera& c = cams[i];
+    if (c.width == 0 || c.height == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "view with zero width or height");
+    if (!(c.fov_y_deg > 0.0f && c.fov_y_deg < 180.0f))
+      return fail(ctx, IPT_ERR_INVALID_ARG, "fov_y_deg must be in (0, 180)");
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(c.cam_to_world[k])) return fail(ctx, IPT_ERR_INVALID_ARG, "non-finite camera matrix");
+    std::memcpy(v[i].m, c.cam_to_world, sizeof(v[i].m));
+    const double th = std::tan(0.5 * (double)c.fov_y_deg * 3.14159265358979323846 / 180.0);
+    v[i].ty = (float)th;
+    v[i].tx = (float)(th * (double)c.width / (double)c.height);
+    v[i].w = c.width;
+    v[i].h = c.height;
+    v[i].offset = (uint32_t)off;
+    off += (uint64_t)c.width * c.height;
+    if (off >= (1ull << 32)) return fail(ctx, IPT_ERR_INVALID_ARG, "more than 2^32 pixels");
+  }
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaStreamSynchronize(ctx->stream));
+  if (s->views_dev) cudaFree(s->views_dev), s->views_dev = nullptr;
+  if (s->target) cudaFree(s->target), s->target = nullptr;
+  if (s->g_img) cudaFree(s->g_img), s->g_img = nullptr;
+  IPT_CK(cudaMalloc(&s->views_dev, n_views * sizeof(ipt::ViewHost)));
+  IPT_CK(cudaMemcpy(s->views_dev, v.data(), n_views * sizeof(ipt::ViewHost), cudaMemcpyHostToDevice));
+  IPT_CK(cudaMalloc(&s->g_img, off * 3 * sizeof(float)));
+  s->views = v;
+  s->n_pix = off;
+  if (target_rgb) return ipt_targets_set(ctx, scene, target_rgb, target_on_device);
+  return IPT_OK;
+}
+
+ipt_status ipt_targets_set(ipt_ctx* ctx, int32_t scene, const float* target_rgb, int32_t target_on_device) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!target_rgb || s->n_pix == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "targets need views and data");
+  IPT_CK(cudaSetDevice(ctx->device));
+  if (!s->target) IPT_CK(cudaMalloc(&s->target, s->n_pix * 3 * sizeof(float)));
+  IPT_CK(cudaMemcpyAsync(s->target, target_rgb, s->n_pix * 3 * sizeof(float),
+                         target_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  return IPT_OK;
+}
+
+ipt_status ipt_params_set(ipt_ctx* ctx, int32_t scene, const float* params, const uint8_t* free_mask) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!params) return fail(ctx, IPT_ERR_INVALID_ARG, "null params");
+  const size_t n = 10 * (size_t)s->n_seg;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(params[i])) return fail(ctx, IPT_ERR_NONFINITE, "non-finite parameter " + std::to_string(i));
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaMemcpyAsync(s->params, params, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  IPT_CK(cudaMemsetAsync(s->adam_m, 0, n * sizeof(float), ctx->stream));
+  IPT_CK(cudaMemsetAsync(s->adam_v, 0, n * sizeof(float), ctx->stream));
+  IPT_CK(cudaMemsetAsync(s->step_dev, 0, sizeof(int), ctx->stream));
+  if (free_mask) {
+    IPT_CK(cudaMemcpyAsync(s->free_mask, free_mask, n, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    IPT_CK(cudaMemsetAsync(s->free_mask, 1, n, ctx->stream));
+  }
+  IPT_CK(cudaStreamSynchronize(ctx->stream));  // host buffers may be released on return
+  s->tab_is_ctx = false;
+  s->params_set = true;
+  s->iteration = 0;
+  return IPT_OK;
+}
+
+ipt_status ipt_params_get(ipt_ctx* ctx, int32_t scene, float* params_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!params_out) return fail(ctx, IPT_ERR_INVALID_ARG, "null output");
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaMemcpyAsync(params_out, s->params, 10 * sizeof(float) * s->n_seg, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  return ipt_synchronize(ctx);
+}
+
+ipt_status ipt_params_device(ipt_ctx* ctx, int32_t scene, float** params_dev) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!params_dev) return IPT_ERR_INVALID_ARG;
+  *params_dev = s->params;
+  s->tab_is_ctx = false;  // the caller may write through the pointer
+  return IPT_OK;
+}
+
+ipt_status ipt_render(ipt_ctx* ctx, int32_t scene, int32_t view, const ipt_trace_opts* opts, uint32_t set,
+                      uint32_t spp, uint64_t iteration, const float* params, const float* sampling_params,
+                      float* rgb_out, float* msq_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if ((st = check_opts(ctx, opts, false)) != IPT_OK) return st;
+  if (s->views.empty()) return fail(ctx, IPT_ERR_INVALID_ARG, "no views set");
+  if (view < -1 || view >= (int32_t)s->views.size()) return fail(ctx, IPT_ERR_INVALID_ARG, "view out of range");
+  if (spp == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp must be positive");
+  if (!rgb_out && !msq_out) return fail(ctx, IPT_ERR_INVALID_ARG, "no output");
+  IPT_CK(cudaSetDevice(ctx->device));
+  const float* p = params ? params : s->params;
+  if ((st = ensure_tables(ctx, s, p, sampling_params)) != IPT_OK) return st;
+  const uint32_t begin = view < 0 ? 0u : s->views[view].offset;
+  const uint32_t n = view < 0 ? (uint32_t)s->n_pix : s->views[view].w * s->views[view].h;
+  Timed tm(ctx, IPT_KERNEL_FORWARD);
+  IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
+                             trace_params(ctx, scene, opts, set, spp, iteration), rgb_out, msq_out, nullptr,
+                             nullptr, nullptr, 0.f, 0, ctx->err_dev, ctx->stream));
+  return IPT_OK;
+}
+
+ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t set, uint64_t iteration,
+                        const float* params, const float* sampling_params, const float* grad_image,
+                        float* grad_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if ((st = check_opts(ctx, opts, true)) != IPT_OK) return st;
+  if (s->views.empty()) return fail(ctx, IPT_ERR_INVALID_ARG, "no views set");
+  if (!grad_image || !grad_out) return fail(ctx, IPT_ERR_INVALID_ARG, "null grad_image or grad_out");
+  if (opts->spp_d == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp_d must be positive");
+  IPT_CK(cudaSetDevice(ctx->device));
+  const float* p = params ? params : s->params;
+  if ((st = ensure_tables(ctx, s, p, sampling_params)) != IPT_OK) return st;
+  const uint32_t np = 10u * s->n_seg;
+  IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
+  {
+    Timed tm(ctx, IPT_KERNEL_ADJOINT);
+    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(),
+                               (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
+                               grad_image, s->grad_acc, ctx->err_dev, ctx->stream));
+  }
+  Timed tm(ctx, IPT_KERNEL_FINALIZE);
+  IPT_CK(ipt::launch_finalize(nullptr, 0, nullptr, s->grad_acc, grad_out, np, ctx->stream));
+  return IPT_OK;
+}
+
+static ipt_status loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, const ipt_trace_opts* opts,
+                                  uint64_t iteration, float* grad_out) {
+  ipt_status st;
+  if ((st = check_opts(ctx, opts, true)) != IPT_OK) return st;
+  if (s->views.empty() || !s->target) return fail(ctx, IPT_ERR_INVALID_ARG, "loss needs views and targets");
+  if (opts->spp_r == 0 || opts->spp_d == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp_r and spp_d must be positive");
+  IPT_CK(cudaSetDevice(ctx->device));
+  if ((st = ensure_tables(ctx, s, s->params, nullptr)) != IPT_OK) return st;
+  const uint32_t np = 10u * s->n_seg;
+  const float g_scale = (float)(1.0 / (3.0 * (double)s->n_pix));
+  {
+    Timed tm(ctx, IPT_KERNEL_FORWARD);
+    IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), 0,
+                               (uint32_t)s->n_pix,
+                               trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration), nullptr,
+                               nullptr, s->target, s->g_img, s->loss_partials, g_scale, opts->loss, ctx->err_dev,
+                               ctx->stream));
+  }
+  IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
+  const uint32_t set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
+  {
+    Timed tm(ctx, IPT_KERNEL_ADJOINT);
+    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(),
+                               (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
+                               s->g_img, s->grad_acc, ctx->err_dev, ctx->stream));
+  }
+  Timed tm(ctx, IPT_KERNEL_FINALIZE);
+  IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, s->grad_acc,
+                              grad_out, np, ctx->stream));
+  return IPT_OK;
+}
+
+static ipt_status read_loss(ipt_ctx* ctx, DeviceScene* s, double* loss_out) {
+  IPT_CK(cudaMemcpyAsync(ctx->loss_host, s->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  ipt_status st = ipt_synchronize(ctx);
+  if (st != IPT_OK) return st;
+  *loss_out = *ctx->loss_host / (3.0 * (double)s->n_pix);
+  return IPT_OK;
+}
+
+ipt_status ipt_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint64_t iteration,
+                         double* loss_out, float* grad_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if ((st = loss_grad_async(ctx, scene, s, opts, iteration, grad_out)) != IPT_OK) return st;
+  if (loss_out) return read_loss(ctx, s, loss_out);
+  return IPT_OK;
+}
+
+static ipt::AdamHost adam_host(const ipt_adam_opts* a) {
+  ipt::AdamHost h;
+  h.lr = a->lr;
+  h.beta1 = a->beta1;
+  h.beta2 = a->beta2;
+  h.eps = a->eps;
+  h.l1 = a->l1_emission;
+  return h;
+}
+
+ipt_status ipt_adam_step(ipt_ctx* ctx, int32_t scene, const float* grad, const ipt_adam_opts* adam) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!adam) return fail(ctx, IPT_ERR_INVALID_ARG, "null adam options");
+  if (!(adam->lr >= 0.0f) || !(adam->beta1 >= 0.0f && adam->beta1 < 1.0f) ||
+      !(adam->beta2 >= 0.0f && adam->beta2 < 1.0f) || !(adam->eps > 0.0f) || !(adam->l1_emission >= 0.0f))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "invalid adam options");
+  IPT_CK(cudaSetDevice(ctx->device));
+  Timed tm(ctx, IPT_KERNEL_ADAM);
+  IPT_CK(ipt::launch_adam(buffers(ctx, s), s->tab, s->params, s->adam_m, s->adam_v, s->free_mask, s->grad_acc, grad,
+                          s->step_dev, adam_host(adam), ctx->stream));
+  s->tab_is_ctx = true;  // the Adam kernel rebuilt the tables from the new parameters
+  return IPT_OK;
+}
+
+ipt_status ipt_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, const ipt_adam_opts* adam,
+                    double* loss_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if ((st = loss_grad_async(ctx, scene, s, opts, s->iteration, nullptr)) != IPT_OK) return st;
+  if ((st = ipt_adam_step(ctx, scene, nullptr, adam)) != IPT_OK) return st;
+  s->iteration++;
+  if (loss_out) return read_loss(ctx, s, loss_out);
+  return IPT_OK;
+}
+
+ipt_status ipt_trace_rays(ipt_ctx* ctx, int32_t scene, uint32_t n, const float* orig, const float* dir,
+                          const int32_t* skip, int32_t* tri_out, float* t_out, float* u_out, float* v_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (n && (!orig || !dir || !tri_out)) return fail(ctx, IPT_ERR_INVALID_ARG, "null ray buffers");
+  IPT_CK(cudaSetDevice(ctx->device));
+  Timed tm(ctx, IPT_KERNEL_TRACE);
+  IPT_CK(ipt::launch_trace_rays(buffers(ctx, s), n, orig, dir, skip, tri_out, t_out, u_out, v_out, ctx->err_dev,
+                                ctx->stream));
+  return IPT_OK;
+}
+
+ipt_status ipt_philox(ipt_ctx* ctx, uint32_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  if (!ctx) return IPT_ERR_INVALID_ARG;
+  if (n && (!ctr || !key || !out)) return fail(ctx, IPT_ERR_INVALID_ARG, "null philox buffers");
+  IPT_CK(cudaSetDevice(ctx->device));
+  Timed tm(ctx, IPT_KERNEL_PHILOX);
+  IPT_CK(ipt::launch_philox(n, ctr, key, out, ctx->stream));
+  return IPT_OK;
+}
+
+ipt_status ipt_synchronize(ipt_ctx* ctx) {
+  if (!ctx) return IPT_ERR_INVALID_ARG;
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaStreamSynchronize(ctx->stream));
+  uint32_t err = 0;
+  IPT_CK(cudaMemcpy(&err, ctx->err_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (err) {
+    cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
+    return fail(ctx, IPT_ERR_CUDA, "device error word " + std::to_string(err) + " (traversal stack overflow)");
+  }
+  return IPT_OK;
+}
+
+ipt_status ipt_scene_info(ipt_ctx* ctx, int32_t scene, uint32_t* n_tri, uint32_t* n_seg, uint32_t* n_nodes,
+                          uint32_t* bvh_depth, uint32_t* n_views, uint64_t* n_pixels) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (n_tri) *n_tri = s->n_tri;
+  if (n_seg) *n_seg = s->n_seg;
+  if (n_nodes) *n_nodes = s->n_nodes;
+  if (bvh_depth) *bvh_depth = s->depth;
+  if (n_views) *n_views = (uint32_t)s->views.size();
+  if (n_pixels) *n_pixels = s->n_pix;
+  return IPT_OK;
+}
+
+ipt_status ipt_kernel_times(ipt_ctx* ctx, double* total_ms, uint64_t* launches, int32_t reset) {
+  if (!ctx) return IPT_ERR_INVALID_ARG;
+  if (!(ctx->flags & IPT_FLAG_KERNEL_TIMING))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "context created without IPT_FLAG_KERNEL_TIMING");
+  IPT_CK(cudaSetDevice(ctx->device));
+  resolve_timings(ctx);
+  for (int k = 0; k < IPT_KERNEL_COUNT; ++k) {
+    if (total_ms) total_ms[k] = ctx->kernel_ms[k];
+    if (launches) launches[k] = ctx->kernel_n[k];
+    if (reset) {
+      ctx->kernel_ms[k] = 0.0;
+      ctx->kernel_n[k] = 0;
+    }
+  }
+  return IPT_OK;
+}
+
+ipt_status ipt_counters_read(ipt_ctx* ctx, uint64_t* out, int32_t reset) {
+  if (!ctx || !out) return IPT_ERR_INVALID_ARG;
+  if (!ctx->counters_dev) return fail(ctx, IPT_ERR_INVALID_ARG, "context created without IPT_FLAG_COUNTERS");
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaStreamSynchronize(ctx->stream));
+  unsigned long long v[4];
+  IPT_CK(cudaMemcpy(v, ctx->counters_dev, sizeof(v), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 4; ++k) out[k] = v[k];
+  if (reset) IPT_CK(cudaMemset(ctx->counters_dev, 0, sizeof(v)));
+  return IPT_OK;
+}
+
+}  // extern "C"

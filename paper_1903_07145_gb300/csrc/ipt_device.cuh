@@ -1,0 +1,460 @@
+// Device building blocks of the GB300 inverse path tracer: float3 algebra,
+// Philox4x32-10, the scene layout in HBM, watertight ray casting over a
+// binary BVH, the Lambert + GGX material model and its sampling routines.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ipt {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr int kStackSize = 64;
+constexpr uint32_t kErrStack = 1u;  // traversal stack would overflow
+
+// ---------------------------------------------------------------------------
+// float3 algebra
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 a) { return a * rsqrtf(dot(a, a)); }
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+__device__ __forceinline__ float comp(float3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Bumping the key after
+// each round is the same as bumping it before every round but the first.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// top 24 bits -> [0,1), exactly representable in FP32 and FP64
+__device__ __forceinline__ float to_unit(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+// Counter layout of one path: (pixel id, sample id, (set << 24) | iteration,
+// 4 * vertex + call).  Calls: 0 -> (u_lobe, u_dir1, u_dir2, u_light_segment),
+// 1 -> (u_light_triangle, u_light_a, u_light_b, -), vertex 0 call 2 ->
+// (u_jitter_x, u_jitter_y, -, -).
+struct PathRng {
+  uint4 base;  // w holds nothing; set per draw
+  uint2 key;
+  __device__ __forceinline__ float4 draw(uint32_t vertex, uint32_t call) const {
+    const uint4 o = philox4x32_10(make_uint4(base.x, base.y, base.z, vertex * 4u + call), key);
+    return make_float4(to_unit(o.x), to_unit(o.y), to_unit(o.z), to_unit(o.w));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Scene layout in device memory.
+//   nodes: 4 float4 per inner node of a binary BVH, both children's boxes in
+//     the parent: (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y), (c1 same),
+//     (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z), (child0, child1 as int bits).
+//     child >= 0: inner node index; child < 0: leaf, v = -child - 1,
+//     first triangle = v >> 3, count = (v & 7) + 1.
+//   tris: 3 float4 per triangle in leaf order; p0.w = original triangle id,
+//     p1.w = segment id (both as int bits).
+//   vnrm: 3 float4 per triangle (vertex normals) or nullptr.
+//   Light selection (static): seg_tris lists the triangles of each segment
+//     (internal ids, by increasing original id), seg_begin[s]..seg_begin[s+1];
+//     tri_cdf is the inclusive FP64 area prefix inside each segment.
+// ---------------------------------------------------------------------------
+struct SceneDev {
+  const float4* nodes;
+  const float4* tris;
+  const float4* vnrm;
+  const uint32_t* seg_tris;
+  const uint32_t* seg_begin;
+  const double* tri_cdf;
+  const double* seg_area;
+  uint32_t n_seg;
+  uint32_t n_tri;
+  float eps;  // spawn offset along the oriented geometric normal
+  unsigned long long* counters;  // optional: closest rays, shadow rays, node visits, triangle tests
+};
+
+__device__ __forceinline__ void count_ray(const SceneDev& s, int kind, uint32_t nodes, uint32_t tests) {
+  if (s.counters) {
+    atomicAdd(&s.counters[kind], 1ull);
+    atomicAdd(&s.counters[2], (unsigned long long)nodes);
+    atomicAdd(&s.counters[3], (unsigned long long)tests);
+  }
+}
+
+// Per-segment tables derived from the parameters (rebuilt whenever the
+// parameters change).  Evaluation uses params; sampling uses sampling params.
+struct SegDev {
+  const float4* mat_a;   // kd.rgb, roughness            (params)
+  const float4* mat_b;   // ks.rgb, alpha = max(r^2,1e-4) (params)
+  const float4* emis;    // emission_scale * e.rgb, -    (params)
+  const float4* samp;    // alpha_s, P_spec (float), p_A = lum_s / W (float), -   (sampling)
+  const double* pspec;   // P_spec in FP64 (lobe decision)
+  const double* cdf;     // inclusive FP64 prefix of lum(e_s) A_s
+  const double* W;       // total; 0 disables light sampling
+};
+
+struct ViewDev {
+  float m[12];      // cam_to_world, row-major 3x4
+  float tx, ty;     // tan(fov/2) * aspect, tan(fov/2)
+  uint32_t w, h;
+  uint32_t offset;  // global id of this view's first pixel
+  uint32_t pad[3];
+};
+
+struct Hit {
+  int tri;      // internal (leaf-order) id, -1 = miss
+  float t, u, v;
+};
+
+// ---------------------------------------------------------------------------
+// Watertight ray/triangle test: Woop, Benthin, Wald, "Watertight Ray/Triangle
+// Intersection", JCGT 2(1), 2013.  The edge functions are evaluated without
+// FMA contraction so that a shared edge gives the same value (up to sign) in
+// both triangles; exact zeros are re-evaluated in FP64.
+// ---------------------------------------------------------------------------
+struct RayPre {
+  float3 o, d, inv;
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
+  RayPre r;
+  r.o = o;
+  r.d = d;
+  const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  r.kx = r.kz + 1 == 3 ? 0 : r.kz + 1;
+  r.ky = r.kx + 1 == 3 ? 0 : r.kx + 1;
+  if (comp(d, r.kz) < 0.0f) {
+    const int t = r.kx;
+    r.kx = r.ky;
+    r.ky = t;
+  }
+  const float dz = comp(d, r.kz);
+  r.Sx = comp(d, r.kx) / dz;
+  r.Sy = comp(d, r.ky) / dz;
+  r.Sz = 1.0f / dz;
+  const float tiny = 1e-30f;
+  r.inv = f3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+             1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+             1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+  return r;
+}
+
+// Returns true and (t, u, v) on a hit with 0 < t < tmax.
+__device__ __forceinline__ bool tri_test(const RayPre& r, float3 p0, float3 p1, float3 p2, float tmax,
+                                         float& t_out, float& u_out, float& v_out) {
+  const float3 A = p0 - r.o, B = p1 - r.o, C = p2 - r.o;
+  const float Az0 = comp(A, r.kz), Bz0 = comp(B, r.kz), Cz0 = comp(C, r.kz);
+  const float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Az0));
+  const float Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Az0));
+  const float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bz0));
+  const float By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bz0));
+  const float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Cz0));
+  const float Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Cz0));
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.0f || V == 0.0f || W == 0.0f) {
+    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+    V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  }
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+  const float det = U + V + W;
+  if (det == 0.0f) return false;
+  const float T = U * (r.Sz * Az0) + V * (r.Sz * Bz0) + W * (r.Sz * Cz0);
+  const float inv = 1.0f / det;
+  const float t = T * inv;
+  if (!(t > 0.0f) || !(t < tmax)) return false;
+  t_out = t;
+  u_out = V * inv;
+  v_out = W * inv;
+  return true;
+}
+
+__device__ __forceinline__ void decode_leaf(int child, int& first, int& count) {
+  const int v = -child - 1;
+  first = v >> 3;
+  count = (v & 7) + 1;
+}
+
+// Slab test of both children; returns entry distances (or +inf on a miss).
+__device__ __forceinline__ void box2(const RayPre& r, float3 oinv, float4 n0, float4 n1, float4 n2,
+                                     float tmax, float& t0, float& t1) {
+  const float far_scale = 1.0000005f;  // conservative far bound (a few ulps)
+  const float a_lx = n0.x * r.inv.x - oinv.x, a_hx = n0.y * r.inv.x - oinv.x;
+  const float a_ly = n0.z * r.inv.y - oinv.y, a_hy = n0.w * r.inv.y - oinv.y;
+  const float a_lz = n2.x * r.inv.z - oinv.z, a_hz = n2.y * r.inv.z - oinv.z;
+  const float b_lx = n1.x * r.inv.x - oinv.x, b_hx = n1.y * r.inv.x - oinv.x;
+  const float b_ly = n1.z * r.inv.y - oinv.y, b_hy = n1.w * r.inv.y - oinv.y;
+  const float b_lz = n2.z * r.inv.z - oinv.z, b_hz = n2.w * r.inv.z - oinv.z;
+  const float an = fmaxf(fmaxf(fminf(a_lx, a_hx), fminf(a_ly, a_hy)), fmaxf(fminf(a_lz, a_hz), 0.0f));
+  const float af = fminf(fminf(fmaxf(a_lx, a_hx), fmaxf(a_ly, a_hy)), fminf(fmaxf(a_lz, a_hz), tmax)) * far_scale;
+  const float bn = fmaxf(fmaxf(fminf(b_lx, b_hx), fminf(b_ly, b_hy)), fmaxf(fminf(b_lz, b_hz), 0.0f));
+  const float bf = fminf(fminf(fmaxf(b_lx, b_hx), fmaxf(b_ly, b_hy)), fminf(fmaxf(b_lz, b_hz), tmax)) * far_scale;
+  t0 = an <= af ? an : __int_as_float(0x7f800000);
+  t1 = bn <= bf ? bn : __int_as_float(0x7f800000);
+}
+
+// Closest hit in (0, tmax), skipping one internal triangle id; equal t keeps
+// the smaller original id.  On stack overflow the ray reports a miss and the
+// error word is set.
+__device__ __forceinline__ Hit trace_closest(const SceneDev& s, float3 o, float3 d, float tmax, int skip,
+                                             uint32_t* err) {
+  const RayPre r = ray_pre(o, d);
+  const float3 oinv = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+  Hit h;
+  h.tri = -1;
+  h.t = tmax;
+  h.u = h.v = 0.0f;
+  int best_orig = 0x7fffffff;
+  int stack[kStackSize];
+  int sp = 0;
+  int node = 0;
+  uint32_t n_nodes = 0, n_tests = 0;
+  for (;;) {
+    if (node >= 0) {
+      ++n_nodes;
+      const float4 n0 = __ldg(&s.nodes[4 * node + 0]);
+      const float4 n1 = __ldg(&s.nodes[4 * node + 1]);
+      const float4 n2 = __ldg(&s.nodes[4 * node + 2]);
+      const float4 n3 = __ldg(&s.nodes[4 * node + 3]);
+      float t0, t1;
+      box2(r, oinv, n0, n1, n2, h.t, t0, t1);
+      const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      const bool h0 = t0 != __int_as_float(0x7f800000);
+      const bool h1 = t1 != __int_as_float(0x7f800000);
+      if (h0 && h1) {
+        if (sp >= kStackSize) {
+          atomicOr(err, kErrStack);
+          h.tri = -1;
+          return h;
+        }
+        if (t1 < t0) {
+          stack[sp++] = c0;
+          node = c1;
+        } else {
+          stack[sp++] = c1;
+          node = c0;
+        }
+        continue;
+      }
+      if (h0 || h1) {
+        node = h0 ? c0 : c1;
+        continue;
+      }
+    } else {
+      int first, count;
+      decode_leaf(node, first, count);
+      n_tests += count;
+      for (int i = first; i < first + count; ++i) {
+        if (i == skip) continue;
+        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+        float t, u, v;
+        if (tri_test(r, xyz(q0), xyz(q1), xyz(q2), h.t * 1.0000002f, t, u, v)) {
+          const int orig = __float_as_int(q0.w);
+          if (t < h.t || (t == h.t && orig < best_orig)) {
+            h.tri = i;
+            h.t = t;
+            h.u = u;
+            h.v = v;
+            best_orig = orig;
+          }
+        }
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  count_ray(s, 0, n_nodes, n_tests);
+  return h;
+}
+
+// Any hit in (0, tmax), skipping two internal triangle ids.
+__device__ __forceinline__ bool trace_any(const SceneDev& s, float3 o, float3 d, float tmax, int skip_a,
+                                          int skip_b, uint32_t* err) {
+  const RayPre r = ray_pre(o, d);
+  const float3 oinv = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+  int stack[kStackSize];
+  int sp = 0;
+  int node = 0;
+  uint32_t n_nodes = 0, n_tests = 0;
+  for (;;) {
+    if (node >= 0) {
+      ++n_nodes;
+      const float4 n0 = __ldg(&s.nodes[4 * node + 0]);
+      const float4 n1 = __ldg(&s.nodes[4 * node + 1]);
+      const float4 n2 = __ldg(&s.nodes[4 * node + 2]);
+      const float4 n3 = __ldg(&s.nodes[4 * node + 3]);
+      float t0, t1;
+      box2(r, oinv, n0, n1, n2, tmax, t0, t1);
+      const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      const bool h0 = t0 != __int_as_float(0x7f800000);
+      const bool h1 = t1 != __int_as_float(0x7f800000);
+      if (h0 && h1) {
+        if (sp >= kStackSize) {
+          atomicOr(err, kErrStack);
+          return true;
+        }
+        stack[sp++] = c1;
+        node = c0;
+        continue;
+      }
+      if (h0 || h1) {
+        node = h0 ? c0 : c1;
+        continue;
+      }
+    } else {
+      int first, count;
+      decode_leaf(node, first, count);
+      n_tests += count;
+      for (int i = first; i < first + count; ++i) {
+        if (i == skip_a || i == skip_b) continue;
+        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+        float t, u, v;
+        if (tri_test(r, xyz(q0), xyz(q1), xyz(q2), tmax, t, u, v)) {
+          count_ray(s, 1, n_nodes, n_tests);
+          return true;
+        }
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  count_ray(s, 1, n_nodes, n_tests);
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Material model: f_r = kd/pi + ks * D(h) G2 / (4 ci co), GGX D, height-
+// correlated Smith G2, alpha = max(r^2, 1e-4), no Fresnel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ggx_D(float nh, float a) {
+  if (!(nh > 0.0f)) return 0.0f;
+  const float a2 = a * a;
+  const float q = nh * nh * (a2 - 1.0f) + 1.0f;
+  return a2 / (kPi * q * q);
+}
+__device__ __forceinline__ float ggx_dD_da(float nh, float a) {
+  if (!(nh > 0.0f)) return 0.0f;
+  const float a2 = a * a;
+  const float q = nh * nh * (a2 - 1.0f) + 1.0f;
+  return 2.0f * a / (kPi * q * q) * (1.0f - 2.0f * a2 * nh * nh / q);
+}
+__device__ __forceinline__ float smith_lambda(float c, float a) {
+  const float c2 = c * c;
+  const float t2 = (1.0f - c2) / c2;
+  return 0.5f * (sqrtf(1.0f + a * a * t2) - 1.0f);
+}
+__device__ __forceinline__ float smith_dlambda_da(float c, float a) {
+  const float c2 = c * c;
+  const float t2 = (1.0f - c2) / c2;
+  return 0.5f * a * t2 * rsqrtf(1.0f + a * a * t2);
+}
+
+struct Spec {
+  float s;      // D G2 / (4 ci co)
+  float ds_dr;  // d s / d roughness
+};
+
+// r: roughness (for d alpha / d r), a = max(r^2, 1e-4)
+__device__ __forceinline__ Spec spec_term(float ci, float co, float nh, float r, float a) {
+  const float D = ggx_D(nh, a);
+  const float G2 = 1.0f / (1.0f + smith_lambda(ci, a) + smith_lambda(co, a));
+  const float inv_den = 1.0f / (4.0f * ci * co);
+  Spec sp;
+  sp.s = D * G2 * inv_den;
+  const float dG2 = -G2 * G2 * (smith_dlambda_da(ci, a) + smith_dlambda_da(co, a));
+  const float dsda = (ggx_dD_da(nh, a) * G2 + D * dG2) * inv_den;
+  sp.ds_dr = r * r > 1e-4f ? dsda * 2.0f * r : 0.0f;
+  return sp;
+}
+
+// Orthonormal basis around unit n (Duff et al., JCGT 6(1), 2017).
+__device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
+  const float sign = copysignf(1.0f, n.z);
+  const float a = -1.0f / (sign + n.z);
+  const float b = n.x * n.y * a;
+  b1 = f3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  b2 = f3(b, sign + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float smith_G1(float c, float a) { return 1.0f / (1.0f + smith_lambda(c, a)); }
+
+// Mixture pdf (solid angle) for sampling wo given wi; P = specular probability.
+__device__ __forceinline__ float bsdf_pdf(float P, float a_s, float3 n, float3 wi, float3 wo) {
+  const float ci = dot(n, wi), co = dot(n, wo);
+  if (!(ci > 0.0f) || !(co > 0.0f)) return 0.0f;
+  float ps = 0.0f;
+  if (P > 0.0f) {
+    const float3 h = normalize(wi + wo);
+    ps = smith_G1(ci, a_s) * ggx_D(dot(n, h), a_s) / (4.0f * ci);
+  }
+  return (1.0f - P) * (co * (1.0f / kPi)) + P * ps;
+}
+
+// Lobe by u_lobe < P_spec (FP64 decision); diffuse: cosine-weighted
+// (r = sqrt(u1), phi = 2 pi u2); specular: GGX visible normals (Heitz, JCGT
+// 7(4), 2018) and a mirror reflection of wi.
+__device__ __forceinline__ float3 bsdf_sample(double P, float a_s, float3 n, float3 wi, float u_lobe,
+                                              float u1, float u2) {
+  float3 b1, b2;
+  onb(n, b1, b2);
+  float sphi, cphi;
+  sincospif(2.0f * u2, &sphi, &cphi);
+  const float rr = sqrtf(u1);
+  if ((double)u_lobe < P) {
+    const float3 vl = f3(dot(wi, b1), dot(wi, b2), dot(wi, n));
+    const float3 vh = normalize(f3(a_s * vl.x, a_s * vl.y, vl.z));
+    const float lensq = vh.x * vh.x + vh.y * vh.y;
+    const float3 t1 = lensq > 0.0f ? f3(-vh.y, vh.x, 0.0f) * rsqrtf(lensq) : f3(1.0f, 0.0f, 0.0f);
+    const float3 t2 = cross(vh, t1);
+    const float q1 = rr * cphi;
+    float q2 = rr * sphi;
+    const float s = 0.5f * (1.0f + vh.z);
+    q2 = (1.0f - s) * sqrtf(fmaxf(0.0f, 1.0f - q1 * q1)) + s * q2;
+    const float3 nh = t1 * q1 + t2 * q2 + vh * sqrtf(fmaxf(0.0f, 1.0f - q1 * q1 - q2 * q2));
+    const float3 ne = normalize(f3(a_s * nh.x, a_s * nh.y, fmaxf(0.0f, nh.z)));
+    const float3 hw = b1 * ne.x + b2 * ne.y + n * ne.z;
+    return hw * (2.0f * dot(wi, hw)) - wi;
+  }
+  const float z = sqrtf(fmaxf(0.0f, 1.0f - u1));
+  return b1 * (rr * cphi) + b2 * (rr * sphi) + n * z;
+}
+
+// First index i in [b, e) with x < a[i] (e - 1 if none); a non-decreasing.
+__device__ __forceinline__ int upper_bound_d(const double* a, int b, int e, double x) {
+  int lo = b, hi = e - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (x < __ldg(&a[mid]))
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+}  // namespace ipt

@@ -1,0 +1,125 @@
+// Host-side declarations shared by the C ABI and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace ipt {
+
+// Result of the host scene build: BVH, triangle layout and light tables.
+struct HostScene {
+  uint32_t n_tri = 0, n_seg = 0, n_nodes = 0, depth = 0;
+  std::vector<float> nodes;      // 16 floats per inner node
+  std::vector<float> tris;       // 12 floats per triangle (leaf order)
+  std::vector<float> vnrm;       // 12 floats per triangle, empty if no normals
+  std::vector<uint32_t> orig_to_internal;
+  std::vector<uint32_t> seg_tris;
+  std::vector<uint32_t> seg_begin;
+  std::vector<double> tri_cdf;
+  std::vector<double> seg_area;
+  double diameter = 0.0;
+};
+
+// Validates the input and builds the scene; returns false with a message.
+bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint32_t* idx,
+                 uint32_t n_tri, const uint32_t* tri_seg, uint32_t n_seg, HostScene* out,
+                 std::string* err);
+
+// Device pointers of one scene, passed to the launchers.
+struct SceneBuffers {
+  const float4* nodes;
+  const float4* tris;
+  const float4* vnrm;
+  const uint32_t* seg_tris;
+  const uint32_t* seg_begin;
+  const double* tri_cdf;
+  const double* seg_area;
+  const uint32_t* orig_to_internal;
+  uint32_t n_seg, n_tri;
+  float eps;
+  float emission_scale;
+  unsigned long long* counters;  // nullptr unless counting
+};
+
+// Per-segment parameter tables (device).
+struct SegBuffers {
+  float4* mat_a;
+  float4* mat_b;
+  float4* emis;
+  float4* samp;
+  double* pspec;
+  double* cdf;
+  double* lum;
+  double* W;
+};
+
+struct ViewHost {
+  float m[12];
+  float tx, ty;
+  uint32_t w, h;
+  uint32_t offset;
+  uint32_t pad[3];
+};
+
+struct TraceParams {
+  uint64_t seed;
+  uint32_t scene_id;
+  uint32_t set;
+  uint64_t iteration;
+  uint32_t spp;
+  uint32_t max_depth;
+  int nee, mis, profile;
+};
+
+struct Launcher {
+  int num_sms = 0;
+  int fwd_blocks_per_sm = 0;
+  int adj_blocks_per_sm[4] = {0, 0, 0, 0};
+};
+
+constexpr int kMaxAdjointDepth = 8;
+constexpr int kMaxForwardDepth = 64;
+constexpr int kBlockThreads = 128;
+
+int loss_partials_capacity(const Launcher& L);
+
+cudaError_t launch_prepare(const SceneBuffers& s, const SegBuffers& t, const float* params,
+                           const float* sparams, cudaStream_t st);
+
+cudaError_t launch_forward(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
+                           const ViewHost* views_dev, uint32_t n_views, uint32_t pix_begin,
+                           uint32_t n_pix, const TraceParams& tp, float* img, float* msq,
+                           const float* target, float* g_out, double* loss_partials,
+                           float g_scale, int loss_kind, uint32_t* err, cudaStream_t st);
+
+cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
+                           const ViewHost* views_dev, uint32_t n_views, uint32_t n_pix,
+                           const TraceParams& tp, const float* g_img, double* grad_acc,
+                           uint32_t* err, cudaStream_t st);
+
+cudaError_t launch_finalize(const double* loss_partials, int n_partials, double* loss_dev,
+                            const double* grad_acc, float* grad_out, uint32_t n_params,
+                            cudaStream_t st);
+
+struct AdamHost {
+  float lr, beta1, beta2, eps, l1;
+};
+
+cudaError_t launch_adam(const SceneBuffers& s, const SegBuffers& t, float* params, float* m,
+                        float* v, const uint8_t* free_mask, const double* grad_acc,
+                        const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st);
+
+cudaError_t launch_trace_rays(const SceneBuffers& s, uint32_t n, const float* orig,
+                              const float* dir, const int32_t* skip, int32_t* tri_out,
+                              float* t_out, float* u_out, float* v_out, uint32_t* err,
+                              cudaStream_t st);
+
+cudaError_t launch_philox(uint32_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          cudaStream_t st);
+
+cudaError_t init_launcher(Launcher* L, int device);
+
+}  // namespace ipt

@@ -1,0 +1,730 @@
+// Kernels of one nested-SGD iteration of inverse path tracing:
+//   k_prepare   per-segment tables from the parameters (light selection CDF,
+//               lobe probabilities): the per-iteration form of the emission-
+//               proportional light selection of Appendix E;
+//   k_forward   Monte Carlo pixel estimates (Eq. 1-2) with MIS (App. A.2),
+//               optionally fused with the residual of the loss (Eq. 3);
+//   k_adjoint   derivative paths from an independent sample set (Sec. 3.3),
+//               scattering g . dI/dTheta (Eq. 5-6) into per-block shared
+//               accumulators;
+//   k_finalize  loss and gradient reduction;
+//   k_adam      Adam + L1 emission regulariser + clamps (Sec. 4.4-4.5), then
+//               the tables for the next iteration;
+//   k_trace_rays, k_philox: the ray-casting and random-number primitives.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ipt_device.cuh"
+#include "ipt_internal.h"
+
+namespace ipt {
+
+constexpr double kLumR = 0.2126, kLumG = 0.7152, kLumB = 0.0722;  // Rec. 709 luminance
+
+struct PathParams {
+  uint2 key;
+  uint32_t set_iter;  // (set << 24) | (iteration & 0xFFFFFF)
+  uint32_t spp;
+  uint32_t group;     // lanes per pixel (power of two dividing spp, <= 32)
+  uint32_t max_depth;
+  int nee, mis, profile;
+  float emission_scale;
+};
+
+__host__ __device__ inline uint32_t lanes_per_pixel(uint32_t spp) {
+  uint32_t g = 1;
+  while (g < 32 && (spp % (2 * g)) == 0) g *= 2;
+  return g;
+}
+
+static PathParams make_path_params(const TraceParams& tp, const SceneBuffers& s) {
+  PathParams p;
+  p.key = make_uint2((uint32_t)(tp.seed & 0xFFFFFFFFu), (uint32_t)(tp.seed >> 32) ^ tp.scene_id);
+  p.set_iter = (tp.set << 24) | (uint32_t)(tp.iteration & 0xFFFFFFu);
+  p.spp = tp.spp;
+  p.group = lanes_per_pixel(tp.spp);
+  p.max_depth = tp.max_depth;
+  p.nee = tp.nee;
+  p.mis = tp.mis;
+  p.profile = tp.profile;
+  p.emission_scale = s.emission_scale;
+  return p;
+}
+
+static SceneDev scene_dev(const SceneBuffers& s) {
+  SceneDev d;
+  d.nodes = s.nodes;
+  d.tris = s.tris;
+  d.vnrm = s.vnrm;
+  d.seg_tris = s.seg_tris;
+  d.seg_begin = s.seg_begin;
+  d.tri_cdf = s.tri_cdf;
+  d.seg_area = s.seg_area;
+  d.n_seg = s.n_seg;
+  d.n_tri = s.n_tri;
+  d.eps = s.eps;
+  d.counters = s.counters;
+  return d;
+}
+
+static SegDev seg_dev(const SegBuffers& t) {
+  SegDev d;
+  d.mat_a = t.mat_a;
+  d.mat_b = t.mat_b;
+  d.emis = t.emis;
+  d.samp = t.samp;
+  d.pspec = t.pspec;
+  d.cdf = t.cdf;
+  d.W = t.W;
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Parameter tables.  Decisions that pick an integer (light segment, lobe) are
+// taken in FP64 from FP64 tables evaluated without contraction.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double lum_d(double r, double g, double b) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(kLumR, r), __dmul_rn(kLumG, g)), __dmul_rn(kLumB, b));
+}
+
+__device__ void build_tables(const float* params, const float* sparams, uint32_t S, float es,
+                             const double* seg_area, SegBuffers t) {
+  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+    const float* p = params + 10 * s;
+    const float* q = sparams + 10 * s;
+    const float r = p[6];
+    t.mat_a[s] = make_float4(p[0], p[1], p[2], r);
+    t.mat_b[s] = make_float4(p[3], p[4], p[5], fmaxf(r * r, 1e-4f));
+    t.emis[s] = make_float4(es * p[7], es * p[8], es * p[9], 0.0f);
+    const double ld = lum_d(q[0], q[1], q[2]);
+    const double ls = lum_d(q[3], q[4], q[5]);
+    const double sum = __dadd_rn(ld, ls);
+    t.pspec[s] = sum > 0.0 ? __ddiv_rn(ls, sum) : 0.0;
+    double le = lum_d(q[7], q[8], q[9]);
+    if (!(le > 0.0)) le = 0.0;
+    t.lum[s] = le;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (uint32_t s = 0; s < S; ++s) {
+      acc = __dadd_rn(acc, __dmul_rn(t.lum[s], seg_area[s]));
+      t.cdf[s] = acc;
+    }
+    *t.W = acc;
+  }
+  __syncthreads();
+  const double W = *t.W;
+  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+    const float rs = sparams[10 * s + 6];
+    const double le = t.lum[s];
+    t.samp[s] = make_float4(fmaxf(rs * rs, 1e-4f), (float)t.pspec[s],
+                            (W > 0.0 && le > 0.0) ? (float)(le / W) : 0.0f, 0.0f);
+  }
+}
+
+__global__ void k_prepare(const float* params, const float* sparams, uint32_t S, float es,
+                          const double* seg_area, SegBuffers t) {
+  build_tables(params, sparams, S, es, seg_area, t);
+}
+
+// ---------------------------------------------------------------------------
+// Path construction shared by the forward and adjoint kernels.
+// ---------------------------------------------------------------------------
+struct Vtx {
+  int tri, seg;
+  float3 x, ng, ns, wi;  // normals oriented to the incoming side
+  float cos_e;           // wi . n_g (unflipped): > 0 on the emitting face
+  float prof;            // emission profile toward wi
+};
+
+__device__ __forceinline__ Vtx make_vertex(const SceneDev& s, const Hit& h, float3 d, int profile) {
+  Vtx v;
+  v.tri = h.tri;
+  const float4 q0 = __ldg(&s.tris[3 * h.tri + 0]);
+  const float4 q1 = __ldg(&s.tris[3 * h.tri + 1]);
+  const float4 q2 = __ldg(&s.tris[3 * h.tri + 2]);
+  v.seg = __float_as_int(q1.w);
+  const float w0 = 1.0f - h.u - h.v;
+  const float3 p0 = xyz(q0), p1 = xyz(q1), p2 = xyz(q2);
+  v.x = p0 * w0 + p1 * h.u + p2 * h.v;
+  const float3 ng0 = normalize(cross(p1 - p0, p2 - p0));
+  float3 ns = ng0;
+  if (s.vnrm) {
+    const float3 a = xyz(__ldg(&s.vnrm[3 * h.tri + 0]));
+    const float3 b = xyz(__ldg(&s.vnrm[3 * h.tri + 1]));
+    const float3 c = xyz(__ldg(&s.vnrm[3 * h.tri + 2]));
+    ns = normalize(a * w0 + b * h.u + c * h.v);
+  }
+  v.wi = -d;
+  v.cos_e = dot(v.wi, ng0);
+  v.prof = profile == 0 ? fmaxf(0.0f, v.cos_e) : (v.cos_e > 0.0f ? 1.0f : 0.0f);
+  const float sg = v.cos_e < 0.0f ? -1.0f : 1.0f;
+  v.ng = ng0 * sg;
+  v.ns = ns * sg;
+  return v;
+}
+
+// MIS weight of emission found by BRDF sampling (power heuristic, beta = 2).
+__device__ __forceinline__ float emission_weight(const SegDev& t, const Vtx& v, float dist, bool after_scatter,
+                                                 bool prev_light, float prev_pdf, int mis) {
+  if (!after_scatter || !prev_light) return 1.0f;
+  const float pa = __ldg(&t.samp[v.seg]).z;
+  if (!(pa > 0.0f) || !(v.cos_e > 0.0f)) return 1.0f;
+  if (!mis) return 0.0f;
+  const float pl = pa * dist * dist / v.cos_e;
+  return prev_pdf * prev_pdf / (prev_pdf * prev_pdf + pl * pl);
+}
+
+__device__ __forceinline__ float3 camera_ray(const ViewDev& vw, uint32_t px, uint32_t py, const PathRng& rng,
+                                             float3& org) {
+  const float4 u = rng.draw(0, 2);
+  const float ndc_x = 2.0f * ((float)px + u.x) / (float)vw.w - 1.0f;
+  const float ndc_y = 1.0f - 2.0f * ((float)py + u.y) / (float)vw.h;
+  const float3 dc = f3(ndc_x * vw.tx, ndc_y * vw.ty, -1.0f);
+  const float* M = vw.m;
+  org = f3(M[3], M[7], M[11]);
+  return normalize(f3(M[0] * dc.x + M[1] * dc.y + M[2] * dc.z, M[4] * dc.x + M[5] * dc.y + M[6] * dc.z,
+                      M[8] * dc.x + M[9] * dc.y + M[10] * dc.z));
+}
+
+struct NeeResult {
+  bool valid;
+  int seg;       // emitting segment
+  float3 wl;
+  float k;       // cos_x * profile * (cos_l / r^2) / p_A * w_light
+};
+
+// Light selection proportional to lum(e_s) A_s, then area within the segment,
+// then a uniform point (sqrt parameterisation); visibility by a shadow ray
+// from the offset point, skipping both end triangles.
+__device__ __forceinline__ NeeResult next_event(const SceneDev& s, const SegDev& t, const Vtx& v, float4 ua,
+                                                float4 ub, double W, int profile, int mis, float P,
+                                                float a_s, uint32_t* err) {
+  NeeResult r;
+  r.valid = false;
+  const int sl = upper_bound_d(t.cdf, 0, (int)s.n_seg, (double)ua.w * W);
+  const int b = (int)__ldg(&s.seg_begin[sl]), e = (int)__ldg(&s.seg_begin[sl + 1]);
+  if (e <= b) return r;  // a segment without triangles is never selectable; guard anyway
+  const int j = upper_bound_d(s.tri_cdf, b, e, (double)ub.x * __ldg(&s.seg_area[sl]));
+  const int lt = (int)__ldg(&s.seg_tris[j]);
+  const float3 p0 = xyz(__ldg(&s.tris[3 * lt + 0]));
+  const float3 p1 = xyz(__ldg(&s.tris[3 * lt + 1]));
+  const float3 p2 = xyz(__ldg(&s.tris[3 * lt + 2]));
+  const float su = sqrtf(ub.y);
+  const float b0 = 1.0f - su, b1 = ub.z * su, b2 = 1.0f - b0 - b1;
+  const float3 y = p0 * b0 + p1 * b1 + p2 * b2;
+  const float3 dl = y - v.x;
+  const float r2 = dot(dl, dl);
+  const float3 wl = dl * rsqrtf(r2);
+  const float3 nl = normalize(cross(p1 - p0, p2 - p0));
+  const float cos_l = -dot(wl, nl);
+  const float lprof = profile == 0 ? fmaxf(0.0f, cos_l) : (cos_l > 0.0f ? 1.0f : 0.0f);
+  const float cxg = dot(wl, v.ng), cxs = dot(wl, v.ns);
+  if (!(lprof > 0.0f) || !(cxg > 0.0f) || !(cxs > 0.0f) || !(dot(v.wi, v.ns) > 0.0f)) return r;
+  const float3 so = v.x + v.ng * s.eps;
+  const float3 ds = y - so;
+  const float rs = sqrtf(dot(ds, ds));
+  if (trace_any(s, so, ds * (1.0f / rs), rs * 0.99999f, v.tri, lt, err)) return r;
+  const float pA = __ldg(&t.samp[sl]).z;
+  float wlight = 1.0f;
+  if (mis) {
+    const float pl = pA * r2 / cos_l;
+    const float pb = bsdf_pdf(P, a_s, v.ns, v.wi, wl);
+    wlight = pl * pl / (pl * pl + pb * pb);
+  }
+  r.valid = true;
+  r.seg = sl;
+  r.wl = wl;
+  r.k = cxs * lprof * (cos_l / r2) / pA * wlight;
+  return r;
+}
+
+struct BrdfVal {
+  float3 f;
+  Spec sp;
+};
+
+__device__ __forceinline__ BrdfVal brdf_eval(float4 ma, float4 mb, float3 n, float3 wi, float3 wo) {
+  const float ci = dot(n, wi), co = dot(n, wo);
+  const float3 h = normalize(wi + wo);
+  BrdfVal b;
+  b.sp = spec_term(ci, co, dot(n, h), ma.w, mb.w);
+  b.f = f3(ma.x, ma.y, ma.z) * (1.0f / kPi) + f3(mb.x, mb.y, mb.z) * b.sp.s;
+  return b;
+}
+
+__device__ __forceinline__ const ViewDev& find_view(const ViewDev* views, uint32_t n_views, uint32_t p) {
+  uint32_t v = n_views - 1;
+  while (v > 0 && p < views[v].offset) --v;
+  return views[v];
+}
+
+// Radiance estimate of one camera path.
+__device__ float3 forward_path(const SceneDev& s, const SegDev& t, const ViewDev& vw, uint32_t px, uint32_t py,
+                               uint32_t pid, uint32_t sample, const PathParams& pp, double W,
+                               uint32_t* err) {
+  PathRng rng;
+  rng.base = make_uint4(pid, sample, pp.set_iter, 0);
+  rng.key = pp.key;
+  float3 o;
+  float3 d = camera_ray(vw, px, py, rng, o);
+  float3 beta = f3(1.0f, 1.0f, 1.0f), L = f3(0.0f, 0.0f, 0.0f);
+  const bool light_on = pp.nee && W > 0.0;
+  int skip = -1;
+  float prev_pdf = 0.0f;
+  for (uint32_t k = 0;; ++k) {
+    const Hit h = trace_closest(s, o, d, __int_as_float(0x7f800000), skip, err);
+    if (h.tri < 0) break;
+    const Vtx v = make_vertex(s, h, d, pp.profile);
+    if (v.prof > 0.0f) {
+      const float wb = emission_weight(t, v, h.t, k > 0, light_on, prev_pdf, pp.mis);
+      if (wb > 0.0f) L = L + beta * xyz(__ldg(&t.emis[v.seg])) * (wb * v.prof);
+    }
+    if (k == pp.max_depth) break;
+    const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
+    const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
+    const float4 sa = __ldg(&t.samp[v.seg]);
+    if (light_on) {
+      const NeeResult ne = next_event(s, t, v, ua, ub, W, pp.profile, pp.mis, sa.y, sa.x, err);
+      if (ne.valid) {
+        const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
+        L = L + beta * bv.f * xyz(__ldg(&t.emis[ne.seg])) * ne.k;
+      }
+    }
+    if (!(dot(v.wi, v.ns) > 0.0f)) break;
+    const float3 wo = bsdf_sample(__ldg(&t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
+    const float pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
+    const float co = dot(wo, v.ns);
+    if (!(dot(wo, v.ng) > 0.0f) || !(co > 0.0f) || !(pdf > 0.0f)) break;
+    const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
+    beta = beta * bv.f * (co / pdf);
+    prev_pdf = pdf;
+    o = v.x + v.ng * s.eps;
+    d = wo;
+    skip = h.tri;
+  }
+  return L;
+}
+
+__device__ __forceinline__ void add3(float* acc, int i, float3 v) {
+  atomicAdd(&acc[i], v.x);
+  atomicAdd(&acc[i + 1], v.y);
+  atomicAdd(&acc[i + 2], v.z);
+}
+
+// Derivative of one camera path, contracted with the pixel's upstream
+// gradient gp and scattered into acc (S x 10).  Eq. 5-6 differentiate the
+// product of BSDFs along each light path; here each continuing vertex l keeps
+// T_l (the throughput with its own weight w_l left out) and U_l (the sum of
+// later contributions through T_l), so that d/dTheta_l of the whole path is
+// (dw_l/dTheta) . U_l without dividing by w_l.  Emission and the local NEE term
+// are differentiated on the spot.  Pdfs and MIS weights are held constant.
+template <int MAXD>
+__device__ void adjoint_path(const SceneDev& s, const SegDev& t, const ViewDev& vw, uint32_t px, uint32_t py,
+                             uint32_t pid, uint32_t sample, const PathParams& pp, double W, float3 gp,
+                             float* acc, uint32_t* err) {
+  PathRng rng;
+  rng.base = make_uint4(pid, sample, pp.set_iter, 0);
+  rng.key = pp.key;
+  float3 o;
+  float3 d = camera_ray(vw, px, py, rng, o);
+  float3 beta = f3(1.0f, 1.0f, 1.0f);
+  const bool light_on = pp.nee && W > 0.0;
+  const float es = pp.emission_scale;
+  float3 T[MAXD], U[MAXD];
+  float AD[MAXD], AS[MAXD], AR[MAXD];
+  int SG[MAXD];
+  int nv = 0;
+  int skip = -1;
+  float prev_pdf = 0.0f;
+  for (uint32_t k = 0;; ++k) {
+    const Hit h = trace_closest(s, o, d, __int_as_float(0x7f800000), skip, err);
+    if (h.tri < 0) break;
+    const Vtx v = make_vertex(s, h, d, pp.profile);
+    float3 C = f3(0.0f, 0.0f, 0.0f);
+    if (v.prof > 0.0f) {
+      const float wb = emission_weight(t, v, h.t, k > 0, light_on, prev_pdf, pp.mis);
+      if (wb > 0.0f) {
+        const float f = wb * v.prof;
+        C = xyz(__ldg(&t.emis[v.seg])) * f;
+        add3(acc, 10 * v.seg + 7, gp * beta * (f * es));  // Eq. 5 at the hit
+      }
+    }
+    const bool last = k == pp.max_depth;
+    const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
+    const float4 sa = __ldg(&t.samp[v.seg]);
+    float4 ua = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!last) {
+      ua = rng.draw(k, 0);
+      const float4 ub = rng.draw(k, 1);
+      if (light_on) {
+        const NeeResult ne = next_event(s, t, v, ua, ub, W, pp.profile, pp.mis, sa.y, sa.x, err);
+        if (ne.valid) {
+          const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
+          const float3 Le = xyz(__ldg(&t.emis[ne.seg]));
+          C = C + bv.f * Le * ne.k;
+          add3(acc, 10 * ne.seg + 7, gp * beta * bv.f * (ne.k * es));        // Eq. 5, light end
+          const float3 q = gp * beta * Le * ne.k;                              // Eq. 6, l = this vertex
+          add3(acc, 10 * v.seg + 0, q * (1.0f / kPi));
+          add3(acc, 10 * v.seg + 3, q * bv.sp.s);
+          atomicAdd(&acc[10 * v.seg + 6], dot(q, f3(mb.x, mb.y, mb.z)) * bv.sp.ds_dr);
+        }
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < MAXD; ++l)
+      if (l < nv) U[l] = U[l] + T[l] * C;
+    if (last || !(dot(v.wi, v.ns) > 0.0f)) break;
+    const float3 wo = bsdf_sample(__ldg(&t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
+    const float pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
+    const float co = dot(wo, v.ns);
+    if (!(dot(wo, v.ng) > 0.0f) || !(co > 0.0f) || !(pdf > 0.0f)) break;
+    const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
+    const float kk = co / pdf;
+    const float3 w = bv.f * kk;
+#pragma unroll
+    for (int l = 0; l < MAXD; ++l) {
+      if (l < nv) T[l] = T[l] * w;
+      if (l == nv) {
+        T[l] = beta;
+        U[l] = f3(0.0f, 0.0f, 0.0f);
+        AD[l] = kk * (1.0f / kPi);
+        AS[l] = kk * bv.sp.s;
+        AR[l] = kk * bv.sp.ds_dr;
+        SG[l] = v.seg;
+      }
+    }
+    ++nv;
+    beta = beta * w;
+    prev_pdf = pdf;
+    o = v.x + v.ng * s.eps;
+    d = wo;
+    skip = h.tri;
+  }
+#pragma unroll
+  for (int l = 0; l < MAXD; ++l) {
+    if (l < nv) {
+      const float3 q = gp * U[l];
+      const int sg = SG[l];
+      add3(acc, 10 * sg + 0, q * AD[l]);
+      add3(acc, 10 * sg + 3, q * AS[l]);
+      const float4 mb = __ldg(&t.mat_b[sg]);
+      atomicAdd(&acc[10 * sg + 6], dot(q, f3(mb.x, mb.y, mb.z)) * AR[l]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward kernel: each pixel is handled by `group` lanes of one warp, each
+// lane tracing spp / group samples; the lanes' sums are combined with
+// butterfly shuffles, so the pixel estimate is deterministic.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) k_forward(SceneDev s, SegDev t, const ViewDev* views,
+                                                           uint32_t n_views, uint32_t pix_begin, uint32_t n_pix,
+                                                           PathParams pp, float* img, float* msq,
+                                                           const float* target, float* g_out,
+                                                           double* loss_partials, float g_scale, int loss_kind,
+                                                           uint32_t* err) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t G = pp.group;
+  const uint32_t ppw = 32u / G;
+  const uint32_t sub = lane & (G - 1u);
+  const uint32_t warps_per_block = blockDim.x >> 5;
+  const uint32_t n_tasks = (n_pix + ppw - 1) / ppw;
+  const uint32_t stride = gridDim.x * warps_per_block;
+  const double W = *t.W;
+  const float inv_spp = 1.0f / (float)pp.spp;
+  double loss_acc = 0.0;
+  for (uint32_t task = blockIdx.x * warps_per_block + (threadIdx.x >> 5); task < n_tasks; task += stride) {
+    const uint32_t local = task * ppw + lane / G;
+    const bool active = local < n_pix;
+    float3 a = f3(0.f, 0.f, 0.f), a2 = f3(0.f, 0.f, 0.f);
+    if (active) {
+      const uint32_t pid = pix_begin + local;
+      const ViewDev& vw = find_view(views, n_views, pid);
+      const uint32_t lp = pid - vw.offset;
+      const uint32_t px = lp % vw.w, py = lp / vw.w;
+      for (uint32_t smp = sub; smp < pp.spp; smp += G) {
+        const float3 L = forward_path(s, t, vw, px, py, pid, smp, pp, W, err);
+        a = a + L;
+        a2 = a2 + L * L;
+      }
+    }
+    for (uint32_t off = G >> 1; off >= 1; off >>= 1) {
+      a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
+      a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+      a.z += __shfl_xor_sync(0xffffffffu, a.z, off);
+      a2.x += __shfl_xor_sync(0xffffffffu, a2.x, off);
+      a2.y += __shfl_xor_sync(0xffffffffu, a2.y, off);
+      a2.z += __shfl_xor_sync(0xffffffffu, a2.z, off);
+    }
+    if (active && sub == 0) {
+      const float3 mean = a * inv_spp;
+      if (img) {
+        img[3 * local + 0] = mean.x;
+        img[3 * local + 1] = mean.y;
+        img[3 * local + 2] = mean.z;
+      }
+      if (msq) {
+        msq[3 * local + 0] = a2.x * inv_spp;
+        msq[3 * local + 1] = a2.y * inv_spp;
+        msq[3 * local + 2] = a2.z * inv_spp;
+      }
+      if (target) {
+        const float r[3] = {mean.x - target[3 * local + 0], mean.y - target[3 * local + 1],
+                            mean.z - target[3 * local + 2]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (loss_kind == 0) {
+            g_out[3 * local + c] = 2.0f * r[c] * g_scale;
+            loss_acc += (double)r[c] * (double)r[c];
+          } else {
+            g_out[3 * local + c] = (r[c] > 0.0f ? 1.0f : (r[c] < 0.0f ? -1.0f : 0.0f)) * g_scale;
+            loss_acc += fabs((double)r[c]);
+          }
+        }
+      }
+    }
+  }
+  if (loss_partials) {
+    __shared__ double red[kBlockThreads / 32];
+    for (int off = 16; off >= 1; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+    if (lane == 0) red[threadIdx.x >> 5] = loss_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (uint32_t w = 0; w < warps_per_block; ++w) sum += red[w];
+      loss_partials[blockIdx.x] = sum;
+    }
+  }
+}
+
+template <int MAXD>
+__global__ void __launch_bounds__(kBlockThreads) k_adjoint(SceneDev s, SegDev t, const ViewDev* views,
+                                                           uint32_t n_views, uint32_t n_pix, PathParams pp,
+                                                           const float* g_img, double* grad_acc,
+                                                           uint32_t* err) {
+  extern __shared__ float sgrad[];
+  const uint32_t n_par = 10u * s.n_seg;
+  for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) sgrad[i] = 0.0f;
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t G = pp.group;
+  const uint32_t ppw = 32u / G;
+  const uint32_t sub = lane & (G - 1u);
+  const uint32_t warps_per_block = blockDim.x >> 5;
+  const uint32_t n_tasks = (n_pix + ppw - 1) / ppw;
+  const uint32_t stride = gridDim.x * warps_per_block;
+  const double W = *t.W;
+  const float inv_spp = 1.0f / (float)pp.spp;
+  for (uint32_t task = blockIdx.x * warps_per_block + (threadIdx.x >> 5); task < n_tasks; task += stride) {
+    const uint32_t pid = task * ppw + lane / G;
+    if (pid >= n_pix) continue;
+    const float3 gp = f3(g_img[3 * pid], g_img[3 * pid + 1], g_img[3 * pid + 2]) * inv_spp;
+    if (gp.x == 0.0f && gp.y == 0.0f && gp.z == 0.0f) continue;
+    const ViewDev& vw = find_view(views, n_views, pid);
+    const uint32_t lp = pid - vw.offset;
+    const uint32_t px = lp % vw.w, py = lp / vw.w;
+    for (uint32_t smp = sub; smp < pp.spp; smp += G)
+      adjoint_path<MAXD>(s, t, vw, px, py, pid, smp, pp, W, gp, sgrad, err);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) {
+    const float v = sgrad[i];
+    if (v != 0.0f) atomicAdd(&grad_acc[i], (double)v);
+  }
+}
+
+// One block: fixed-order sums (deterministic for a fixed grid).
+__global__ void k_finalize(const double* loss_partials, int n_partials, double* loss_dev,
+                           const double* grad_acc, float* grad_out, uint32_t n_params) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n_partials; i += blockDim.x) s += loss_partials[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w >= 1; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss_dev) *loss_dev = red[0];
+  if (grad_out)
+    for (uint32_t i = threadIdx.x; i < n_params; i += blockDim.x) grad_out[i] = (float)grad_acc[i];
+}
+
+__global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_mask,
+                       const double* grad_acc, const float* grad_f, int* step_dev, AdamHost a, uint32_t S,
+                       float es, const double* seg_area, SegBuffers t) {
+  const int step = *step_dev + 1;
+  const float bc1 = 1.0f - powf(a.beta1, (float)step);
+  const float bc2 = 1.0f - powf(a.beta2, (float)step);
+  for (uint32_t i = threadIdx.x; i < 10u * S; i += blockDim.x) {
+    if (free_mask && !free_mask[i]) continue;
+    const uint32_t j = i % 10u;
+    float g = grad_f ? grad_f[i] : (float)grad_acc[i];
+    const float th = params[i];
+    if (j >= 7) g += a.l1 * (th > 0.0f ? 1.0f : (th < 0.0f ? -1.0f : 0.0f));
+    const float mi = a.beta1 * m[i] + (1.0f - a.beta1) * g;
+    const float vi = a.beta2 * v[i] + (1.0f - a.beta2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    float nt = th - a.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.eps);
+    if (j < 6)
+      nt = fminf(fmaxf(nt, 0.0f), 1.0f);
+    else if (j == 6)
+      nt = fminf(fmaxf(nt, 0.02f), 1.0f);
+    else
+      nt = fmaxf(nt, 0.0f);
+    params[i] = nt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *step_dev = step;
+  build_tables(params, params, S, es, seg_area, t);
+}
+
+__global__ void k_trace_rays(SceneDev s, const uint32_t* orig_to_internal, uint32_t n, const float* orig,
+                             const float* dir, const int32_t* skip, int32_t* tri_out, float* t_out,
+                             float* u_out, float* v_out, uint32_t* err) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float3 o = f3(orig[3 * i], orig[3 * i + 1], orig[3 * i + 2]);
+  const float3 d = f3(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]);
+  int sk = -1;
+  if (skip && skip[i] >= 0 && (uint32_t)skip[i] < s.n_tri) sk = (int)orig_to_internal[skip[i]];
+  const Hit h = trace_closest(s, o, d, __int_as_float(0x7f800000), sk, err);
+  tri_out[i] = h.tri >= 0 ? __float_as_int(__ldg(&s.tris[3 * h.tri]).w) : -1;
+  if (t_out) t_out[i] = h.t;
+  if (u_out) u_out[i] = h.u;
+  if (v_out) v_out[i] = h.v;
+}
+
+__global__ void k_philox(uint32_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 o = philox4x32_10(c, make_uint2(key[2 * i], key[2 * i + 1]));
+  out[4 * i] = o.x;
+  out[4 * i + 1] = o.y;
+  out[4 * i + 2] = o.z;
+  out[4 * i + 3] = o.w;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <int MAXD>
+static void adjoint_occupancy(int* out) {
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_adjoint<MAXD>, kBlockThreads, 16384);
+}
+
+cudaError_t init_launcher(Launcher* L, int device) {
+  cudaError_t e = cudaDeviceGetAttribute(&L->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->fwd_blocks_per_sm, k_forward, kBlockThreads, 0);
+  if (e != cudaSuccess) return e;
+  adjoint_occupancy<2>(&L->adj_blocks_per_sm[0]);
+  adjoint_occupancy<4>(&L->adj_blocks_per_sm[1]);
+  adjoint_occupancy<6>(&L->adj_blocks_per_sm[2]);
+  adjoint_occupancy<8>(&L->adj_blocks_per_sm[3]);
+  for (int i = 0; i < 4; ++i)
+    if (L->adj_blocks_per_sm[i] < 1) L->adj_blocks_per_sm[i] = 1;
+  if (L->fwd_blocks_per_sm < 1) L->fwd_blocks_per_sm = 1;
+  return cudaGetLastError();
+}
+
+int loss_partials_capacity(const Launcher& L) { return L.num_sms * L.fwd_blocks_per_sm; }
+
+static int grid_for(uint64_t n_tasks_warps, int blocks_cap) {
+  const uint64_t per_block = kBlockThreads / 32;
+  uint64_t g = (n_tasks_warps + per_block - 1) / per_block;
+  if (g > (uint64_t)blocks_cap) g = blocks_cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_prepare(const SceneBuffers& s, const SegBuffers& t, const float* params,
+                           const float* sparams, cudaStream_t st) {
+  k_prepare<<<1, 256, 0, st>>>(params, sparams ? sparams : params, s.n_seg, s.emission_scale, s.seg_area, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
+                           const ViewHost* views_dev, uint32_t n_views, uint32_t pix_begin,
+                           uint32_t n_pix, const TraceParams& tp, float* img, float* msq,
+                           const float* target, float* g_out, double* loss_partials,
+                           float g_scale, int loss_kind, uint32_t* err, cudaStream_t st) {
+  const PathParams pp = make_path_params(tp, s);
+  const uint64_t tasks = (n_pix + (32 / pp.group) - 1) / (32 / pp.group);
+  const int cap = L.num_sms * L.fwd_blocks_per_sm;
+  // with a loss the grid is fixed, so the partial sums reduce in a fixed order
+  const int grid = loss_partials ? cap : grid_for(tasks, cap);
+  k_forward<<<grid, kBlockThreads, 0, st>>>(scene_dev(s), seg_dev(t), reinterpret_cast<const ViewDev*>(views_dev),
+                                             n_views, pix_begin, n_pix, pp, img, msq, target, g_out,
+                                             loss_partials, g_scale, loss_kind, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
+                           const ViewHost* views_dev, uint32_t n_views, uint32_t n_pix,
+                           const TraceParams& tp, const float* g_img, double* grad_acc,
+                           uint32_t* err, cudaStream_t st) {
+  const PathParams pp = make_path_params(tp, s);
+  const uint64_t tasks = (n_pix + (32 / pp.group) - 1) / (32 / pp.group);
+  const size_t shmem = sizeof(float) * 10u * s.n_seg;
+  const ViewDev* vd = reinterpret_cast<const ViewDev*>(views_dev);
+  const int md = tp.max_depth < 1 ? 1 : (int)tp.max_depth;
+#define IPT_LAUNCH_ADJ(D, I)                                                                         \
+  {                                                                                                  \
+    if (shmem > 48 * 1024)                                                                           \
+      cudaFuncSetAttribute(k_adjoint<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);  \
+    const int grid = grid_for(tasks, L.num_sms * L.adj_blocks_per_sm[I]);                            \
+    k_adjoint<D><<<grid, kBlockThreads, shmem, st>>>(scene_dev(s), seg_dev(t), vd, n_views, n_pix, pp, \
+                                                     g_img, grad_acc, err);                          \
+  }
+  if (md <= 2)
+    IPT_LAUNCH_ADJ(2, 0)
+  else if (md <= 4)
+    IPT_LAUNCH_ADJ(4, 1)
+  else if (md <= 6)
+    IPT_LAUNCH_ADJ(6, 2)
+  else
+    IPT_LAUNCH_ADJ(8, 3)
+#undef IPT_LAUNCH_ADJ
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* loss_partials, int n_partials, double* loss_dev,
+                            const double* grad_acc, float* grad_out, uint32_t n_params,
+                            cudaStream_t st) {
+  k_finalize<<<1, 256, 0, st>>>(loss_partials, n_partials, loss_dev, grad_acc, grad_out, n_params);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const SceneBuffers& s, const SegBuffers& t, float* params, float* m,
+                        float* v, const uint8_t* free_mask, const double* grad_acc,
+                        const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st) {
+  k_adam<<<1, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg,
+                            s.emission_scale, s.seg_area, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_rays(const SceneBuffers& s, uint32_t n, const float* orig,
+                              const float* dir, const int32_t* skip, int32_t* tri_out,
+                              float* t_out, float* u_out, float* v_out, uint32_t* err,
+                              cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int block = 128;
+  k_trace_rays<<<(n + block - 1) / block, block, 0, st>>>(scene_dev(s), s.orig_to_internal, n, orig, dir, skip,
+                                                           tri_out, t_out, u_out, v_out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint32_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_philox<<<(n + 255) / 256, 256, 0, st>>>(n, ctr, key, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ipt

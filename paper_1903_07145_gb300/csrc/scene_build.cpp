@@ -1,0 +1,364 @@
+// Host-side scene build: input validation, a binned-SAH binary BVH laid out
+// for the GPU traversal, triangles in leaf order, and the per-segment area
+// tables used for light selection.  Compiled without floating-point
+// contraction so the FP64 area sums are reproducible across hosts.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ipt_internal.h"
+
+namespace ipt {
+namespace {
+
+struct Box {
+  double lo[3], hi[3];
+  void reset() {
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = 1e300;
+      hi[k] = -1e300;
+    }
+  }
+  void grow(const double* p) {
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], p[k]);
+      hi[k] = std::max(hi[k], p[k]);
+    }
+  }
+  void grow(const Box& b) {
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], b.lo[k]);
+      hi[k] = std::max(hi[k], b.hi[k]);
+    }
+  }
+  double area() const {
+    const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    if (dx < 0 || dy < 0 || dz < 0) return 0.0;
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+  }
+};
+
+struct BNode {
+  Box box;
+  int left = -1, right = -1;
+  uint32_t first = 0, count = 0;
+  int depth = 0;
+};
+
+constexpr int kBins = 16;
+constexpr uint32_t kMaxLeaf = 8;
+constexpr int kMedianDepth = 48;
+
+struct Builder {
+  std::vector<Box> pbox;
+  std::vector<double> cen;  // 3 per primitive
+  std::vector<uint32_t> order;
+  std::vector<BNode> nodes;
+
+  int make_node(uint32_t b, uint32_t e, int depth) {
+    BNode n;
+    n.box.reset();
+    for (uint32_t i = b; i < e; ++i) n.box.grow(pbox[order[i]]);
+    n.first = b;
+    n.count = e - b;
+    n.depth = depth;
+    nodes.push_back(n);
+    return (int)nodes.size() - 1;
+  }
+
+  // Returns split position in [b, e] or b when the range should stay a leaf.
+  uint32_t split(uint32_t b, uint32_t e, int depth, bool force) {
+    const uint32_t n = e - b;
+    Box cb;
+    cb.reset();
+    for (uint32_t i = b; i < e; ++i) cb.grow(&cen[3 * order[i]]);
+    int axis = 0;
+    double ext[3];
+    for (int k = 0; k < 3; ++k) ext[k] = cb.hi[k] - cb.lo[k];
+    axis = (ext[0] >= ext[1] && ext[0] >= ext[2]) ? 0 : (ext[1] >= ext[2] ? 1 : 2);
+    auto median = [&](int ax) {
+      const uint32_t mid = b + n / 2;
+      std::nth_element(order.begin() + b, order.begin() + mid, order.begin() + e, [&](uint32_t x, uint32_t y) {
+        const double cx = cen[3 * x + ax], cy = cen[3 * y + ax];
+        return cx < cy || (cx == cy && x < y);
+      });
+      return mid;
+    };
+    if (ext[axis] <= 0.0) {
+      if (n <= kMaxLeaf && !force) return b;
+      return median(axis);
+    }
+    if (depth >= kMedianDepth) {
+      if (n <= 2 && !force) return b;
+      return median(axis);
+    }
+    Box parent;
+    parent.reset();
+    for (uint32_t i = b; i < e; ++i) parent.grow(pbox[order[i]]);
+    const double pa = parent.area();
+    double best = 1e300;
+    int best_axis = -1, best_bin = -1;
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ext[ax] <= 0.0) continue;
+      Box bins[kBins];
+      uint32_t cnt[kBins] = {0};
+      for (int k = 0; k < kBins; ++k) bins[k].reset();
+      const double scale = kBins / ext[ax];
+      for (uint32_t i = b; i < e; ++i) {
+        int k = (int)((cen[3 * order[i] + ax] - cb.lo[ax]) * scale);
+        k = std::min(std::max(k, 0), kBins - 1);
+        cnt[k]++;
+        bins[k].grow(pbox[order[i]]);
+      }
+      double right_area[kBins];
+      uint32_t right_cnt[kBins];
+      Box acc;
+      acc.reset();
+      uint32_t c = 0;
+      for (int k = kBins - 1; k >= 1; --k) {
+        acc.grow(bins[k]);
+        c += cnt[k];
+        right_area[k] = acc.area();
+        right_cnt[k] = c;
+      }
+      acc.reset();
+      c = 0;
+      for (int k = 0; k < kBins - 1; ++k) {
+        acc.grow(bins[k]);
+        c += cnt[k];
+        if (c == 0 || right_cnt[k + 1] == 0) continue;
+        const double cost = 1.0 + (acc.area() * c + right_area[k + 1] * right_cnt[k + 1]) / pa;
+        if (cost < best) {
+          best = cost;
+          best_axis = ax;
+          best_bin = k;
+        }
+      }
+    }
+    if (best_axis < 0) return median(axis);
+    if (!force && n <= kMaxLeaf && best >= (double)n) return b;
+    const double scale = kBins / ext[best_axis];
+    auto it = std::partition(order.begin() + b, order.begin() + e, [&](uint32_t x) {
+      int k = (int)((cen[3 * x + best_axis] - cb.lo[best_axis]) * scale);
+      k = std::min(std::max(k, 0), kBins - 1);
+      return k <= best_bin;
+    });
+    uint32_t mid = (uint32_t)(it - order.begin());
+    if (mid == b || mid == e) mid = median(best_axis);
+    return mid;
+  }
+
+  void build(uint32_t n) {
+    order.resize(n);
+    for (uint32_t i = 0; i < n; ++i) order[i] = i;
+    nodes.reserve(2 * (size_t)n + 2);
+    make_node(0, n, 0);
+    std::vector<int> work = {0};
+    while (!work.empty()) {
+      const int ni = work.back();
+      work.pop_back();
+      const uint32_t b = nodes[ni].first, e = b + nodes[ni].count;
+      const int depth = nodes[ni].depth;
+      const bool force = (ni == 0 && e - b >= 2) || (e - b > kMaxLeaf);
+      const uint32_t mid = (e - b >= 2) ? split(b, e, depth, force) : b;
+      if (mid == b || mid == e) continue;  // leaf
+      const int l = make_node(b, mid, depth + 1);
+      const int r = make_node(mid, e, depth + 1);
+      nodes[ni].left = l;
+      nodes[ni].right = r;
+      work.push_back(r);
+      work.push_back(l);
+    }
+  }
+};
+
+inline float down(double x) { return std::nextafter((float)x, -INFINITY); }
+inline float up(double x) { return std::nextafter((float)x, INFINITY); }
+inline float bits_f(uint32_t v) {
+  float f;
+  std::memcpy(&f, &v, 4);
+  return f;
+}
+
+}  // namespace
+
+bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint32_t* idx,
+                 uint32_t n_tri, const uint32_t* tri_seg, uint32_t n_seg, HostScene* out,
+                 std::string* err) {
+  if (!pos || !idx || !tri_seg || !out) {
+    *err = "null geometry pointer";
+    return false;
+  }
+  if (n_tri == 0 || n_vert == 0 || n_seg == 0) {
+    *err = "scene needs at least one vertex, triangle and segment";
+    return false;
+  }
+  if (n_tri >= (1u << 28)) {
+    *err = "too many triangles (limit 2^28)";
+    return false;
+  }
+  double maxabs = 0.0;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (uint64_t i = 0; i < 3ull * n_vert; ++i) {
+    if (!std::isfinite(pos[i])) {
+      *err = "non-finite vertex coordinate at vertex " + std::to_string(i / 3);
+      return false;
+    }
+    maxabs = std::max(maxabs, std::fabs((double)pos[i]));
+    lo[i % 3] = std::min(lo[i % 3], (double)pos[i]);
+    hi[i % 3] = std::max(hi[i % 3], (double)pos[i]);
+  }
+  if (nrm)
+    for (uint64_t i = 0; i < n_vert; ++i) {
+      const double x = nrm[3 * i], y = nrm[3 * i + 1], z = nrm[3 * i + 2];
+      if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || x * x + y * y + z * z == 0.0) {
+        *err = "invalid vertex normal at vertex " + std::to_string(i);
+        return false;
+      }
+    }
+  HostScene& s = *out;
+  s.n_tri = n_tri;
+  s.n_seg = n_seg;
+  s.diameter = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                         (hi[2] - lo[2]) * (hi[2] - lo[2]));
+  std::vector<double> area(n_tri);
+  Builder B;
+  B.pbox.resize(n_tri);
+  B.cen.resize(3 * (size_t)n_tri);
+  for (uint32_t t = 0; t < n_tri; ++t) {
+    double p[3][3];
+    for (int j = 0; j < 3; ++j) {
+      const uint32_t v = idx[3 * t + j];
+      if (v >= n_vert) {
+        *err = "vertex index out of range in triangle " + std::to_string(t);
+        return false;
+      }
+      for (int k = 0; k < 3; ++k) p[j][k] = pos[3 * v + k];
+    }
+    if (tri_seg[t] >= n_seg) {
+      *err = "segment id out of range in triangle " + std::to_string(t);
+      return false;
+    }
+    const double e1[3] = {p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]};
+    const double e2[3] = {p[2][0] - p[0][0], p[2][1] - p[0][1], p[2][2] - p[0][2]};
+    const double cx = e1[1] * e2[2] - e1[2] * e2[1];
+    const double cy = e1[2] * e2[0] - e1[0] * e2[2];
+    const double cz = e1[0] * e2[1] - e1[1] * e2[0];
+    const double len = std::sqrt(cx * cx + cy * cy + cz * cz);
+    area[t] = 0.5 * len;
+    if (!(area[t] > 0.0)) {
+      *err = "degenerate (zero-area) triangle " + std::to_string(t);
+      return false;
+    }
+    B.pbox[t].reset();
+    for (int j = 0; j < 3; ++j) B.pbox[t].grow(p[j]);
+    for (int k = 0; k < 3; ++k) B.cen[3 * t + k] = (p[0][k] + p[1][k] + p[2][k]) / 3.0;
+  }
+  B.build(n_tri);
+
+  // inner nodes in depth-first order; children boxes stored in the parent
+  const double pad = maxabs * 1e-6 + 1e-30;
+  std::vector<int> gpu_index(B.nodes.size(), -1);
+  std::vector<int> inner;
+  {
+    std::vector<int> st = {0};
+    while (!st.empty()) {
+      const int n = st.back();
+      st.pop_back();
+      if (B.nodes[n].left < 0) continue;
+      gpu_index[n] = (int)inner.size();
+      inner.push_back(n);
+      st.push_back(B.nodes[n].right);
+      st.push_back(B.nodes[n].left);
+    }
+  }
+  auto leaf_code = [&](const BNode& l) {
+    return -(int)((l.first << 3) | (l.count - 1)) - 1;
+  };
+  uint32_t max_depth = 0;
+  for (const BNode& n : B.nodes) max_depth = std::max<uint32_t>(max_depth, (uint32_t)n.depth);
+  s.depth = max_depth;
+  if (inner.empty()) {
+    // single triangle: a root whose second child can never be hit
+    s.n_nodes = 1;
+    s.nodes.assign(16, 0.0f);
+    const Box& b = B.nodes[0].box;
+    float* q = s.nodes.data();
+    q[0] = down(b.lo[0] - pad); q[1] = up(b.hi[0] + pad); q[2] = down(b.lo[1] - pad); q[3] = up(b.hi[1] + pad);
+    q[4] = INFINITY; q[5] = -INFINITY; q[6] = INFINITY; q[7] = -INFINITY;
+    q[8] = down(b.lo[2] - pad); q[9] = up(b.hi[2] + pad); q[10] = INFINITY; q[11] = -INFINITY;
+    const int code = leaf_code(B.nodes[0]);
+    std::memcpy(&q[12], &code, 4);
+    std::memcpy(&q[13], &code, 4);
+  } else {
+    s.n_nodes = (uint32_t)inner.size();
+    s.nodes.assign(16 * (size_t)inner.size(), 0.0f);
+    for (size_t i = 0; i < inner.size(); ++i) {
+      const BNode& n = B.nodes[inner[i]];
+      const BNode& a = B.nodes[n.left];
+      const BNode& c = B.nodes[n.right];
+      float* q = &s.nodes[16 * i];
+      q[0] = down(a.box.lo[0] - pad); q[1] = up(a.box.hi[0] + pad);
+      q[2] = down(a.box.lo[1] - pad); q[3] = up(a.box.hi[1] + pad);
+      q[4] = down(c.box.lo[0] - pad); q[5] = up(c.box.hi[0] + pad);
+      q[6] = down(c.box.lo[1] - pad); q[7] = up(c.box.hi[1] + pad);
+      q[8] = down(a.box.lo[2] - pad); q[9] = up(a.box.hi[2] + pad);
+      q[10] = down(c.box.lo[2] - pad); q[11] = up(c.box.hi[2] + pad);
+      const int ca = a.left < 0 ? leaf_code(a) : gpu_index[n.left];
+      const int cc = c.left < 0 ? leaf_code(c) : gpu_index[n.right];
+      std::memcpy(&q[12], &ca, 4);
+      std::memcpy(&q[13], &cc, 4);
+    }
+  }
+  // triangles in leaf order
+  s.tris.assign(12 * (size_t)n_tri, 0.0f);
+  s.orig_to_internal.assign(n_tri, 0);
+  if (nrm) s.vnrm.assign(12 * (size_t)n_tri, 0.0f);
+  for (uint32_t i = 0; i < n_tri; ++i) {
+    const uint32_t t = B.order[i];
+    s.orig_to_internal[t] = i;
+    float* q = &s.tris[12 * (size_t)i];
+    for (int j = 0; j < 3; ++j) {
+      const uint32_t v = idx[3 * t + j];
+      q[4 * j + 0] = pos[3 * v + 0];
+      q[4 * j + 1] = pos[3 * v + 1];
+      q[4 * j + 2] = pos[3 * v + 2];
+      if (nrm) {
+        float* m = &s.vnrm[12 * (size_t)i + 4 * j];
+        m[0] = nrm[3 * v];
+        m[1] = nrm[3 * v + 1];
+        m[2] = nrm[3 * v + 2];
+      }
+    }
+    q[3] = bits_f(t);
+    q[7] = bits_f(tri_seg[t]);
+  }
+  // per-segment triangle lists (increasing original id) and area CDFs
+  s.seg_begin.assign(n_seg + 1, 0);
+  for (uint32_t t = 0; t < n_tri; ++t) s.seg_begin[tri_seg[t] + 1]++;
+  for (uint32_t k = 0; k < n_seg; ++k) s.seg_begin[k + 1] += s.seg_begin[k];
+  s.seg_tris.assign(n_tri, 0);
+  s.tri_cdf.assign(n_tri, 0.0);
+  s.seg_area.assign(n_seg, 0.0);
+  std::vector<uint32_t> fill(s.seg_begin.begin(), s.seg_begin.end() - 1);
+  std::vector<uint32_t> orig_list(n_tri);
+  for (uint32_t t = 0; t < n_tri; ++t) orig_list[fill[tri_seg[t]]++] = t;
+  for (uint32_t k = 0; k < n_seg; ++k) {
+    double acc = 0.0;
+    for (uint32_t j = s.seg_begin[k]; j < s.seg_begin[k + 1]; ++j) {
+      acc = acc + area[orig_list[j]];
+      s.tri_cdf[j] = acc;
+      s.seg_tris[j] = s.orig_to_internal[orig_list[j]];
+    }
+    s.seg_area[k] = acc;
+  }
+  if (s.depth + 2 > 64) {
+    *err = "BVH deeper than the traversal stack";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace ipt
