@@ -177,6 +177,7 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     w = WORKLOAD
     sc = scenes.room_60k(1001 + rank)
+    sc.cameras = sc.cameras[:w["views"]]
     opts = TraceOptions(spp_r=w["spp_r"], spp_d=w["spp_d"], max_depth=w["max_depth"], nee=True, mis=True)
     adam = AdamOptions()
     tr = Tracer(sc, device=local, seed=1903 + rank, flags=L.IPT_FLAG_KERNEL_TIMING)
@@ -291,7 +292,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--views", type=int, default=None,
+                    help="profiling only: use the first V views (not a benchmark line)")
+    ap.add_argument("--spp", type=int, default=None,
+                    help="profiling only: spp_r = spp_d = S (not a benchmark line)")
     args = ap.parse_args()
+    if args.views:
+        WORKLOAD["views"] = args.views
+        WORKLOAD["workload"] += f"_first{args.views}views"
+    if args.spp:
+        WORKLOAD["spp_r"] = WORKLOAD["spp_d"] = args.spp
+        WORKLOAD["workload"] += f"_spp{args.spp}"
+        WORKLOAD["target_spp"] = min(WORKLOAD["target_spp"], 64)
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -53,6 +53,7 @@ typedef struct ipt_ctx ipt_ctx;
 /* ipt_options.flags bits. */
 #define IPT_FLAG_KERNEL_TIMING 1 /* time every launch with CUDA events on the context stream */
 #define IPT_FLAG_COUNTERS 2      /* count rays, BVH node visits and triangle tests */
+#define IPT_FLAG_OWN_STREAM 4    /* create and own a non-blocking stream, ignoring .stream */
 
 /* Kernel ids reported by ipt_kernel_times. */
 typedef enum {
@@ -66,8 +67,9 @@ typedef enum {
   IPT_KERNEL_COUNT = 7
 } ipt_kernel_id;
 
-/* device: CUDA device ordinal.  stream: a cudaStream_t (NULL = a stream the
- * context creates and owns).  seed: Philox key for all sample sets. */
+/* device: CUDA device ordinal.  stream: the cudaStream_t every call queues
+ * its work on (NULL = the legacy default stream), unless flags has
+ * IPT_FLAG_OWN_STREAM.  seed: Philox key for all sample sets. */
 typedef struct {
   int32_t device;
   void* stream;

@@ -25,7 +25,7 @@ EXPORTED = [
     "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_philox", "ipt_synchronize",
     "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read",
 ]
-IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS = 1, 2
+IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox"]
 
 

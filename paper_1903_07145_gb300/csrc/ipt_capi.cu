@@ -254,11 +254,11 @@ ipt_status ipt_create(ipt_ctx** out, const ipt_options* opt) {
   ctx->seed = opt->seed;
   ctx->flags = opt->flags;
   cudaError_t e = cudaSetDevice(opt->device);
-  if (e == cudaSuccess && opt->stream) {
-    ctx->stream = static_cast<cudaStream_t>(opt->stream);
-  } else if (e == cudaSuccess) {
+  if (e == cudaSuccess && (opt->flags & IPT_FLAG_OWN_STREAM)) {
     e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
     ctx->own_stream = e == cudaSuccess;
+  } else {
+    ctx->stream = static_cast<cudaStream_t>(opt->stream);  // NULL: legacy default stream
   }
   if (e == cudaSuccess) e = ipt::init_launcher(&ctx->L, opt->device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->err_dev, sizeof(uint32_t));

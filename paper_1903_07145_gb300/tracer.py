@@ -72,8 +72,10 @@ class Tracer:
             raise RuntimeError("the inverse path tracer needs a CUDA device")
         self.scene = scene
         self.device = torch.device("cuda", device)
+        # the library queues its work on torch's current stream, so torch ops
+        # and the kernels stay ordered
         stream = torch.cuda.current_stream(self.device).cuda_stream
-        self.ctx = L.ipt_create(device, stream, seed, flags)
+        self.ctx = L.ipt_create(device, stream, seed, flags & ~L.IPT_FLAG_OWN_STREAM)
         pos = np.ascontiguousarray(scene.positions, np.float32)
         nrm = None if scene.normals is None else np.ascontiguousarray(scene.normals, np.float32)
         idx = np.ascontiguousarray(scene.indices, np.uint32)
@@ -132,7 +134,8 @@ class Tracer:
         n = self.n_pix if view < 0 else self.sizes[view][0] * self.sizes[view][1]
         img = torch.empty((n, 3), device=self.device, dtype=torch.float32)
         msq = torch.empty_like(img) if with_msq else None
-        L.ipt_render(self.ctx, self.sid, view, opts.c(), set_id, spp or opts.spp_r, iteration,
+        L.ipt_render(self.ctx, self.sid, view, opts.c(), set_id, opts.spp_r if spp is None else spp,
+                     iteration,
                      _ptr(params), _ptr(sampling_params), _ptr(img), _ptr(msq))
         return (img, msq) if with_msq else img
 
