@@ -200,6 +200,17 @@ ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
 ipt_status ipt_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
                          uint64_t iteration, double* loss_out, float* grad_out);
 
+/* The part of ipt_loss_grad that belongs to pixels [pix_begin, pix_begin +
+ * pix_count) of the concatenated views, for sharding one scene over several
+ * devices (each pixel's residual and derivative samples stay on one shard).
+ * Both the loss and the gradient are normalised by n_total_pixels (the pixel
+ * count of all shards together), so the shards' results add up to the
+ * unsharded ones.  grad_out: device S x 10 (required); loss_out: host, may be
+ * NULL.  Errors: an empty range or one beyond the views. */
+ipt_status ipt_loss_grad_shard(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
+                               uint64_t iteration, uint64_t pix_begin, uint64_t pix_count,
+                               uint64_t n_total_pixels, double* loss_out, float* grad_out);
+
 /* Adam step on the context's parameters (Sec. 4.5) with grad (device S x 10;
  * NULL = the gradient left by ipt_loss_grad). */
 ipt_status ipt_adam_step(ipt_ctx* ctx, int32_t scene, const float* grad,

@@ -23,7 +23,7 @@ EXPORTED = [
     "ipt_scene_upload", "ipt_views_set", "ipt_targets_set", "ipt_params_set",
     "ipt_params_get", "ipt_params_device", "ipt_render", "ipt_backward", "ipt_loss_grad",
     "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_philox", "ipt_synchronize",
-    "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read",
+    "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read", "ipt_loss_grad_shard",
 ]
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox"]
@@ -92,6 +92,8 @@ def lib():
                                    C.POINTER(U32), C.POINTER(U32), C.POINTER(U64)],
                 "ipt_kernel_times": [P, C.POINTER(C.c_double), C.POINTER(U64), I32],
                 "ipt_counters_read": [P, C.POINTER(U64), I32],
+                "ipt_loss_grad_shard": [P, I32, C.POINTER(ipt_trace_opts), U64, U64, U64, U64,
+                                        C.POINTER(C.c_double), P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -211,3 +213,10 @@ def ipt_counters_read(ctx, reset=False):
     out = (C.c_uint64 * 4)()
     _check(ctx, lib().ipt_counters_read(ctx, out, int(reset)))
     return dict(closest_rays=out[0], shadow_rays=out[1], node_visits=out[2], tri_tests=out[3])
+
+
+def ipt_loss_grad_shard(ctx, scene, opts, iteration, pix_begin, pix_count, n_total, grad_out):
+    loss = C.c_double()
+    _check(ctx, lib().ipt_loss_grad_shard(ctx, scene, C.byref(opts), iteration, pix_begin, pix_count,
+                                          n_total, C.byref(loss), grad_out))
+    return loss.value

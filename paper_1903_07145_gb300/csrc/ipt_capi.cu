@@ -502,7 +502,7 @@ ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
   {
     Timed tm(ctx, IPT_KERNEL_ADJOINT);
-    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(),
+    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), 0,
                                (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
                                grad_image, s->grad_acc, ctx->err_dev, ctx->stream));
   }
@@ -511,31 +511,37 @@ ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
   return IPT_OK;
 }
 
+// Forward + residual + adjoint over pixels [begin, begin + count), with the
+// loss normalised by n_total pixels (all shards together).
 static ipt_status loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, const ipt_trace_opts* opts,
-                                  uint64_t iteration, float* grad_out) {
+                                  uint64_t iteration, float* grad_out, uint64_t begin, uint64_t count,
+                                  uint64_t n_total) {
   ipt_status st;
   if ((st = check_opts(ctx, opts, true)) != IPT_OK) return st;
   if (s->views.empty() || !s->target) return fail(ctx, IPT_ERR_INVALID_ARG, "loss needs views and targets");
   if (opts->spp_r == 0 || opts->spp_d == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp_r and spp_d must be positive");
+  if (begin + count > s->n_pix || count == 0 || n_total < count)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "pixel range outside the views");
   IPT_CK(cudaSetDevice(ctx->device));
   if ((st = ensure_tables(ctx, s, s->params, nullptr)) != IPT_OK) return st;
   const uint32_t np = 10u * s->n_seg;
-  const float g_scale = (float)(1.0 / (3.0 * (double)s->n_pix));
+  const float g_scale = (float)(1.0 / (3.0 * (double)n_total));
   {
     Timed tm(ctx, IPT_KERNEL_FORWARD);
-    IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), 0,
-                               (uint32_t)s->n_pix,
+    IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(),
+                               (uint32_t)begin, (uint32_t)count,
                                trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration), nullptr,
-                               nullptr, s->target, s->g_img, s->loss_partials, g_scale, opts->loss, ctx->err_dev,
-                               ctx->stream));
+                               nullptr, s->target + 3 * begin, s->g_img + 3 * begin, s->loss_partials, g_scale,
+                               opts->loss, ctx->err_dev, ctx->stream));
   }
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
   const uint32_t set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
   {
     Timed tm(ctx, IPT_KERNEL_ADJOINT);
     IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(),
-                               (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
-                               s->g_img, s->grad_acc, ctx->err_dev, ctx->stream));
+                               (uint32_t)begin, (uint32_t)count,
+                               trace_params(ctx, scene, opts, set, opts->spp_d, iteration), s->g_img + 3 * begin,
+                               s->grad_acc, ctx->err_dev, ctx->stream));
   }
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, s->grad_acc,
@@ -543,11 +549,11 @@ static ipt_status loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, c
   return IPT_OK;
 }
 
-static ipt_status read_loss(ipt_ctx* ctx, DeviceScene* s, double* loss_out) {
+static ipt_status read_loss(ipt_ctx* ctx, DeviceScene* s, double* loss_out, uint64_t n_total) {
   IPT_CK(cudaMemcpyAsync(ctx->loss_host, s->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   ipt_status st = ipt_synchronize(ctx);
   if (st != IPT_OK) return st;
-  *loss_out = *ctx->loss_host / (3.0 * (double)s->n_pix);
+  *loss_out = *ctx->loss_host / (3.0 * (double)n_total);
   return IPT_OK;
 }
 
@@ -556,8 +562,22 @@ ipt_status ipt_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts
   DeviceScene* s;
   ipt_status st = get_scene(ctx, scene, &s);
   if (st != IPT_OK) return st;
-  if ((st = loss_grad_async(ctx, scene, s, opts, iteration, grad_out)) != IPT_OK) return st;
-  if (loss_out) return read_loss(ctx, s, loss_out);
+  if ((st = loss_grad_async(ctx, scene, s, opts, iteration, grad_out, 0, s->n_pix, s->n_pix)) != IPT_OK) return st;
+  if (loss_out) return read_loss(ctx, s, loss_out, s->n_pix);
+  return IPT_OK;
+}
+
+ipt_status ipt_loss_grad_shard(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint64_t iteration,
+                               uint64_t pix_begin, uint64_t pix_count, uint64_t n_total_pixels,
+                               double* loss_out, float* grad_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!grad_out) return fail(ctx, IPT_ERR_INVALID_ARG, "null grad_out");
+  if ((st = loss_grad_async(ctx, scene, s, opts, iteration, grad_out, pix_begin, pix_count, n_total_pixels)) !=
+      IPT_OK)
+    return st;
+  if (loss_out) return read_loss(ctx, s, loss_out, n_total_pixels);
   return IPT_OK;
 }
 
@@ -592,10 +612,10 @@ ipt_status ipt_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, con
   DeviceScene* s;
   ipt_status st = get_scene(ctx, scene, &s);
   if (st != IPT_OK) return st;
-  if ((st = loss_grad_async(ctx, scene, s, opts, s->iteration, nullptr)) != IPT_OK) return st;
+  if ((st = loss_grad_async(ctx, scene, s, opts, s->iteration, nullptr, 0, s->n_pix, s->n_pix)) != IPT_OK) return st;
   if ((st = ipt_adam_step(ctx, scene, nullptr, adam)) != IPT_OK) return st;
   s->iteration++;
-  if (loss_out) return read_loss(ctx, s, loss_out);
+  if (loss_out) return read_loss(ctx, s, loss_out, s->n_pix);
   return IPT_OK;
 }
 

@@ -96,7 +96,7 @@ cudaError_t launch_forward(const Launcher& L, const SceneBuffers& s, const SegBu
                            float g_scale, int loss_kind, uint32_t* err, cudaStream_t st);
 
 cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
-                           const ViewHost* views_dev, uint32_t n_views, uint32_t n_pix,
+                           const ViewHost* views_dev, uint32_t n_views, uint32_t pix_begin, uint32_t n_pix,
                            const TraceParams& tp, const float* g_img, double* grad_acc,
                            uint32_t* err, cudaStream_t st);
 

@@ -500,10 +500,12 @@ __global__ void __launch_bounds__(kBlockThreads) k_forward(SceneDev s, SegDev t,
   }
 }
 
+// Pixels [pix_begin, pix_begin + n_pix) of the concatenated views; g_img is
+// indexed relative to pix_begin.
 template <int MAXD>
 __global__ void __launch_bounds__(kBlockThreads) k_adjoint(SceneDev s, SegDev t, const ViewDev* views,
-                                                           uint32_t n_views, uint32_t n_pix, PathParams pp,
-                                                           const float* g_img, double* grad_acc,
+                                                           uint32_t n_views, uint32_t pix_begin, uint32_t n_pix,
+                                                           PathParams pp, const float* g_img, double* grad_acc,
                                                            uint32_t* err) {
   extern __shared__ float sgrad[];
   const uint32_t n_par = 10u * s.n_seg;
@@ -519,9 +521,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_adjoint(SceneDev s, SegDev t,
   const double W = *t.W;
   const float inv_spp = 1.0f / (float)pp.spp;
   for (uint32_t task = blockIdx.x * warps_per_block + (threadIdx.x >> 5); task < n_tasks; task += stride) {
-    const uint32_t pid = task * ppw + lane / G;
-    if (pid >= n_pix) continue;
-    const float3 gp = f3(g_img[3 * pid], g_img[3 * pid + 1], g_img[3 * pid + 2]) * inv_spp;
+    const uint32_t local = task * ppw + lane / G;
+    if (local >= n_pix) continue;
+    const uint32_t pid = pix_begin + local;
+    const float3 gp = f3(g_img[3 * local], g_img[3 * local + 1], g_img[3 * local + 2]) * inv_spp;
     if (gp.x == 0.0f && gp.y == 0.0f && gp.z == 0.0f) continue;
     const ViewDev& vw = find_view(views, n_views, pid);
     const uint32_t lp = pid - vw.offset;
@@ -666,7 +669,7 @@ cudaError_t launch_forward(const Launcher& L, const SceneBuffers& s, const SegBu
 }
 
 cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
-                           const ViewHost* views_dev, uint32_t n_views, uint32_t n_pix,
+                           const ViewHost* views_dev, uint32_t n_views, uint32_t pix_begin, uint32_t n_pix,
                            const TraceParams& tp, const float* g_img, double* grad_acc,
                            uint32_t* err, cudaStream_t st) {
   const PathParams pp = make_path_params(tp, s);
@@ -679,7 +682,7 @@ cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBu
     if (shmem > 48 * 1024)                                                                           \
       cudaFuncSetAttribute(k_adjoint<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);  \
     const int grid = grid_for(tasks, L.num_sms * L.adj_blocks_per_sm[I]);                            \
-    k_adjoint<D><<<grid, kBlockThreads, shmem, st>>>(scene_dev(s), seg_dev(t), vd, n_views, n_pix, pp, \
+    k_adjoint<D><<<grid, kBlockThreads, shmem, st>>>(scene_dev(s), seg_dev(t), vd, n_views, pix_begin, n_pix, pp, \
                                                      g_img, grad_acc, err);                          \
   }
   if (md <= 2)

@@ -153,6 +153,13 @@ class Tracer:
         loss = L.ipt_loss_grad(self.ctx, self.sid, opts.c(), iteration, True, _ptr(grad))
         return loss, grad
 
+    def loss_grad_shard(self, opts: TraceOptions, iteration: int, pix_begin: int, pix_count: int,
+                        n_total: int):
+        grad = torch.empty((self.n_seg, 10), device=self.device, dtype=torch.float32)
+        loss = L.ipt_loss_grad_shard(self.ctx, self.sid, opts.c(), iteration, pix_begin, pix_count,
+                                     n_total, _ptr(grad))
+        return loss, grad
+
     def adam_step(self, adam: AdamOptions, grad=None):
         L.ipt_adam_step(self.ctx, self.sid, _ptr(grad), adam.c())
 
