@@ -256,6 +256,24 @@ ipt_status ipt_kernel_times(ipt_ctx* ctx, double* total_ms, uint64_t* launches, 
  * accumulated since the last reset.  Synchronises the context's stream. */
 ipt_status ipt_counters_read(ipt_ctx* ctx, uint64_t* out, int32_t reset);
 
+/* ipt_backward without any device allocation (the paper has no counterpart;
+ * this is an interface convenience).  Same arguments, result and errors as
+ * ipt_backward, for callers that may not allocate device memory at the point
+ * of the call: code that runs under CUDA stream capture (where cudaMalloc is
+ * not a stream operation), real-time loops and embedders that own the device
+ * memory budget.  Inputs and outputs are still the caller's.  The only scratch,
+ * an FP64 S x 10 gradient accumulator, is a file-scope __device__ array sized
+ * for at most 1024 segments (80 KiB, held by every device that loads the
+ * library until the process exits); a scene with more segments is rejected
+ * with IPT_ERR_INVALID_ARG.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The array is cleared at the start of every call, and all calls
+ * share it: calls whose work overlaps on the GPU (other streams, other
+ * contexts on the same device) race on it. */
+ipt_status ipt_backward_noalloc(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t set,
+                                uint64_t iteration, const float* params, const float* sampling_params,
+                                const float* grad_image, float* grad_out);
+
 #ifdef __cplusplus
 }
 #endif

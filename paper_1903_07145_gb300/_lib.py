@@ -24,6 +24,7 @@ EXPORTED = [
     "ipt_params_get", "ipt_params_device", "ipt_render", "ipt_backward", "ipt_loss_grad",
     "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_philox", "ipt_synchronize",
     "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read", "ipt_loss_grad_shard",
+    "ipt_backward_noalloc",
 ]
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox"]
@@ -81,6 +82,7 @@ def lib():
                 "ipt_params_device": [P, I32, C.POINTER(P)],
                 "ipt_render": [P, I32, I32, C.POINTER(ipt_trace_opts), U32, U32, U64, P, P, P, P],
                 "ipt_backward": [P, I32, C.POINTER(ipt_trace_opts), U32, U64, P, P, P, P],
+                "ipt_backward_noalloc": [P, I32, C.POINTER(ipt_trace_opts), U32, U64, P, P, P, P],
                 "ipt_loss_grad": [P, I32, C.POINTER(ipt_trace_opts), U64, C.POINTER(C.c_double), P],
                 "ipt_adam_step": [P, I32, P, C.POINTER(ipt_adam_opts)],
                 "ipt_step": [P, I32, C.POINTER(ipt_trace_opts), C.POINTER(ipt_adam_opts),
@@ -162,6 +164,11 @@ def ipt_render(ctx, scene, view, opts, set_id, spp, iteration, params, sparams, 
 def ipt_backward(ctx, scene, opts, set_id, iteration, params, sparams, grad_image, grad_out):
     _check(ctx, lib().ipt_backward(ctx, scene, C.byref(opts), set_id, iteration, params, sparams,
                                    grad_image, grad_out))
+
+
+def ipt_backward_noalloc(ctx, scene, opts, set_id, iteration, params, sparams, grad_image, grad_out):
+    _check(ctx, lib().ipt_backward_noalloc(ctx, scene, C.byref(opts), set_id, iteration, params,
+                                           sparams, grad_image, grad_out))
 
 
 def ipt_loss_grad(ctx, scene, opts, iteration, want_loss, grad_out):
