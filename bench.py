@@ -188,6 +188,14 @@ def run_ours(args, rank, world, local):
     tr.set_params(scenes.initial_params(sc, w["init"]))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuned = {}
+    if args.integrator == "auto":
+        from paper_1903_07145_gb300 import autotune
+        best, tuned = autotune.tune(tr, lambda: tr.loss_grad(opts, iteration=0))
+        tr.set_params(scenes.initial_params(sc, w["init"]))
+    else:
+        tr.configure(args.integrator)
+    chosen = tr.config()
     for _ in range(args.warmup):
         tr.step(opts, adam, want_loss=False)
     torch.cuda.synchronize(dev)
@@ -220,6 +228,7 @@ def run_ours(args, rank, world, local):
     # algorithmic traffic of the dominant kernel: node and triangle fetches per
     # launch, counted by a separate context with counters (same seeds, same paths)
     ct = Tracer(sc, device=local, seed=1903 + rank, flags=L.IPT_FLAG_COUNTERS)
+    ct.configure(**{**chosen, "integrator": "wavefront" if chosen["integrator"] == 1 else "megakernel"})
     ct.set_targets(target)
     ct.set_params(scenes.initial_params(sc, w["init"]))
     ct.counters(reset=True)
@@ -249,29 +258,47 @@ def run_ours(args, rank, world, local):
         return
     n_paths = paths_per_step() * world
     value = n_paths / (ms * 1e-3) / 1e6
-    dom = max(("forward", "adjoint"), key=lambda k: ktimes[k][0])
-    cnt = adj_cnt if dom == "adjoint" else fwd_cnt
-    dom_ms = ktimes[dom][0] / max(1, ktimes[dom][1])
-    alg_bytes = cnt["node_visits"] * NODE_BYTES + cnt["tri_tests"] * TRI_BYTES
+    # dominant kernel by total device time in the timed region
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_total_ms, dom_launches = ktimes[dom]
+    both = {k: fwd_cnt[k] + adj_cnt[k] for k in fwd_cnt}
+    if dom in ("wf_closest", "wf_shadow"):
+        kind = "closest" if dom == "wf_closest" else "shadow"
+        nodes, tris = both[f"{kind}_node_visits"], both[f"{kind}_tri_tests"]
+        rays = both[f"{kind}_rays"]
+    elif dom in ("forward", "adjoint"):
+        c = fwd_cnt if dom == "forward" else adj_cnt
+        nodes = c["closest_node_visits"] + c["shadow_node_visits"]
+        tris = c["closest_tri_tests"] + c["shadow_tri_tests"]
+        rays = c["closest_rays"] + c["shadow_rays"]
+    else:
+        nodes = tris = rays = 0
+    # counters cover one step's passes; the timed region ran args.steps steps
+    launches_per_step = dom_launches / args.steps
+    alg_bytes_step = nodes * NODE_BYTES + tris * TRI_BYTES
+    alg_bytes_launch = alg_bytes_step / max(launches_per_step, 1)
+    dom_ms = dom_total_ms / max(1, dom_launches)
     peak, src = measured_peaks()
-    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    achieved = alg_bytes_launch / (dom_ms * 1e-3) / 1e9 if alg_bytes_launch else 0.0
     launches = sum(n for _, n in ktimes.values())
-    rays = sum(v for k, v in fwd_cnt.items() if k.endswith("rays")) + \
-        sum(v for k, v in adj_cnt.items() if k.endswith("rays"))
+    rays_step = both["closest_rays"] + both["shadow_rays"]
     out = {
         "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD["workload"], **{k: v for k, v in WORKLOAD.items() if k != "workload"},
                    "l2": "256 MiB flush between timed steps (outside the step events)",
-                   "parallelism": f"{world} independent rooms, one per GPU"},
-        "mrays_per_s": rays / (ms * 1e-3) / 1e6,
-        "kernel_ms": {k: round(v[0] / max(1, v[1]), 4) for k, v in ktimes.items() if v[1]},
+                   "parallelism": f"{world} independent rooms, one per GPU",
+                   "integrator": {**chosen, "integrator": ["megakernel", "wavefront"][chosen["integrator"]]},
+                   "autotune_ms": tuned},
+        "mrays_per_s": rays_step / (ms * 1e-3) / 1e6,
+        "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in ktimes.items() if v[1]},
+        "kernel_launches_per_step": {k: v[1] / args.steps for k, v in ktimes.items() if v[1]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": src,
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "units": {"node_visits": cnt["node_visits"], "tri_tests": cnt["tri_tests"],
-                               "rays": cnt["closest_rays"] + cnt["shadow_rays"]}},
+                     "algorithmic_bytes_per_launch": alg_bytes_launch,
+                     "avg_launch_ms": dom_ms,
+                     "units_per_step": {"node_visits": nodes, "tri_tests": tris, "rays": rays}},
         "e2e": {"value": paths_per_step() / e2e_s / 1e6, "unit": "Mpaths/s",
                 "h2d_bytes_per_step": int(host_target.numel() * 4),
                 "d2h_bytes_per_step": int(8 + host_params.nbytes)},
@@ -292,6 +319,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--integrator", default="auto", choices=["auto", "megakernel", "wavefront"])
     ap.add_argument("--views", type=int, default=None,
                     help="profiling only: use the first V views (not a benchmark line)")
     ap.add_argument("--spp", type=int, default=None,

@@ -64,7 +64,16 @@ typedef enum {
   IPT_KERNEL_ADAM = 4,
   IPT_KERNEL_TRACE = 5,
   IPT_KERNEL_PHILOX = 6,
-  IPT_KERNEL_COUNT = 7
+  /* wavefront integrator stages */
+  IPT_KERNEL_WF_CAMERA = 7,
+  IPT_KERNEL_WF_CLOSEST = 8,
+  IPT_KERNEL_WF_SHADOW = 9,
+  IPT_KERNEL_WF_SHADE = 10,
+  IPT_KERNEL_WF_ADJ_A = 11,
+  IPT_KERNEL_WF_ADJ_CONNECT = 12,
+  IPT_KERNEL_WF_ADJ_B = 13,
+  IPT_KERNEL_WF_REDUCE = 14,
+  IPT_KERNEL_COUNT = 15
 } ipt_kernel_id;
 
 /* device: CUDA device ordinal.  stream: the cudaStream_t every call queues
@@ -76,6 +85,25 @@ typedef struct {
   uint64_t seed;
   int32_t flags; /* IPT_FLAG_* bits */
 } ipt_options;
+
+/* Integrator configuration of a context (picked per workload by the autotuner
+ * in paper_1903_07145_gb300/autotune.py; both integrators trace identical
+ * paths).
+ *   integrator: 0 = megakernel (one thread per path, every stage inline),
+ *     1 = wavefront (chunks of path slots; persistent traversal kernels over
+ *     compacted ray queues).
+ *   wavefront_slots: path slots per wavefront chunk (0 = 1 << 20); rounded
+ *     down to whole pixels.
+ *   trace_steps: node visits per refill round of the persistent traversal
+ *     (0 = 32).
+ *   blocks_per_sm: persistent blocks per SM for the wavefront kernels (0 =
+ *     as many as fit). */
+typedef struct {
+  int32_t integrator;
+  uint32_t wavefront_slots;
+  uint32_t trace_steps;
+  uint32_t blocks_per_sm;
+} ipt_config;
 
 /* Pinhole camera.  cam_to_world is row-major 3x4; its columns are the
  * camera's right, up and backward axes and its position (the camera looks
@@ -126,6 +154,11 @@ typedef struct {
 /* Create a context on opt->device.  *out receives the handle.  Fails with
  * IPT_ERR_CUDA if the device cannot be used. */
 ipt_status ipt_create(ipt_ctx** out, const ipt_options* opt);
+
+/* Set or read the integrator configuration (see ipt_config).  Setting it
+ * may release wavefront buffers; they are re-created on first use. */
+ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg);
+ipt_status ipt_config_get(const ipt_ctx* ctx, ipt_config* cfg);
 
 /* Release every device buffer the context owns.  NULL is accepted. */
 ipt_status ipt_destroy(ipt_ctx* ctx);
@@ -251,9 +284,11 @@ ipt_status ipt_scene_info(ipt_ctx* ctx, int32_t scene, uint32_t* n_tri, uint32_t
  * accumulated since the last reset.  Synchronises the context's stream. */
 ipt_status ipt_kernel_times(ipt_ctx* ctx, double* total_ms, uint64_t* launches, int32_t reset);
 
-/* Traversal counters (requires IPT_FLAG_COUNTERS): out[0] closest-hit rays,
- * out[1] shadow rays, out[2] BVH inner-node visits, out[3] triangle tests,
- * accumulated since the last reset.  Synchronises the context's stream. */
+/* Traversal counters (requires IPT_FLAG_COUNTERS), accumulated since the
+ * last reset: out[0] closest-hit rays, out[1] shadow rays, out[2] BVH
+ * inner-node visits and out[3] triangle tests of closest-hit rays, out[4]
+ * node visits and out[5] triangle tests of shadow rays (out has 6 entries).
+ * Synchronises the context's stream. */
 ipt_status ipt_counters_read(ipt_ctx* ctx, uint64_t* out, int32_t reset);
 
 /* ipt_backward without any device allocation (the paper has no counterpart;

@@ -24,10 +24,12 @@ EXPORTED = [
     "ipt_params_get", "ipt_params_device", "ipt_render", "ipt_backward", "ipt_loss_grad",
     "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_philox", "ipt_synchronize",
     "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read", "ipt_loss_grad_shard",
-    "ipt_backward_noalloc",
+    "ipt_backward_noalloc", "ipt_config_set", "ipt_config_get",
 ]
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
-KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox"]
+KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox",
+                "wf_camera", "wf_closest", "wf_shadow", "wf_shade", "wf_adj_a", "wf_adj_connect",
+                "wf_adj_b", "wf_reduce"]
 
 
 class IptError(RuntimeError):
@@ -44,6 +46,11 @@ class ipt_options(C.Structure):
 class ipt_camera(C.Structure):
     _fields_ = [("cam_to_world", C.c_float * 12), ("fov_y_deg", C.c_float),
                 ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class ipt_config(C.Structure):
+    _fields_ = [("integrator", C.c_int32), ("wavefront_slots", C.c_uint32),
+                ("trace_steps", C.c_uint32), ("blocks_per_sm", C.c_uint32)]
 
 
 class ipt_trace_opts(C.Structure):
@@ -94,6 +101,8 @@ def lib():
                                    C.POINTER(U32), C.POINTER(U32), C.POINTER(U64)],
                 "ipt_kernel_times": [P, C.POINTER(C.c_double), C.POINTER(U64), I32],
                 "ipt_counters_read": [P, C.POINTER(U64), I32],
+                "ipt_config_set": [P, C.POINTER(ipt_config)],
+                "ipt_config_get": [P, C.POINTER(ipt_config)],
                 "ipt_loss_grad_shard": [P, I32, C.POINTER(ipt_trace_opts), U64, U64, U64, U64,
                                         C.POINTER(C.c_double), P],
             }
@@ -217,9 +226,10 @@ def ipt_kernel_times(ctx, reset=False):
 
 
 def ipt_counters_read(ctx, reset=False):
-    out = (C.c_uint64 * 4)()
+    out = (C.c_uint64 * 6)()
     _check(ctx, lib().ipt_counters_read(ctx, out, int(reset)))
-    return dict(closest_rays=out[0], shadow_rays=out[1], node_visits=out[2], tri_tests=out[3])
+    return dict(closest_rays=out[0], shadow_rays=out[1], closest_node_visits=out[2],
+                closest_tri_tests=out[3], shadow_node_visits=out[4], shadow_tri_tests=out[5])
 
 
 def ipt_loss_grad_shard(ctx, scene, opts, iteration, pix_begin, pix_count, n_total, grad_out):
@@ -227,3 +237,15 @@ def ipt_loss_grad_shard(ctx, scene, opts, iteration, pix_begin, pix_count, n_tot
     _check(ctx, lib().ipt_loss_grad_shard(ctx, scene, C.byref(opts), iteration, pix_begin, pix_count,
                                           n_total, C.byref(loss), grad_out))
     return loss.value
+
+
+def ipt_config_set(ctx, integrator=1, wavefront_slots=0, trace_steps=0, blocks_per_sm=0):
+    c = ipt_config(integrator, wavefront_slots, trace_steps, blocks_per_sm)
+    _check(ctx, lib().ipt_config_set(ctx, C.byref(c)))
+
+
+def ipt_config_get(ctx):
+    c = ipt_config()
+    _check(ctx, lib().ipt_config_get(ctx, C.byref(c)))
+    return dict(integrator=c.integrator, wavefront_slots=c.wavefront_slots,
+                trace_steps=c.trace_steps, blocks_per_sm=c.blocks_per_sm)

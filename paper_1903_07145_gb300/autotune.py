@@ -1,0 +1,48 @@
+"""Picks the integrator configuration of a context by measurement.
+
+Candidates: the megakernel, and the wavefront integrator with a few chunk
+sizes and traversal refill granularities.  Each candidate runs one
+loss-and-gradient evaluation of the caller's workload (after one untimed
+run that allocates its buffers); the fastest by CUDA-event time wins and is
+left configured.  Every candidate traces the same paths, so the choice
+changes speed only.
+"""
+from __future__ import annotations
+
+import itertools
+
+import torch
+
+DEFAULT_CANDIDATES = (
+    [dict(integrator="megakernel")]
+    + [dict(integrator="wavefront", wavefront_slots=s, trace_steps=k)
+       for s, k in itertools.product([1 << 19, 1 << 20, 1 << 21], [16, 32, 64])]
+)
+
+
+def _time_once(tracer, run):
+    stream = torch.cuda.current_stream(tracer.device)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    run()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def tune(tracer, run, candidates=DEFAULT_CANDIDATES, repeats=1):
+    """run(): one evaluation of the workload on `tracer` (no host sync
+    needed).  Returns (best config dict, {repr(config): ms})."""
+    results = {}
+    best, best_ms = None, float("inf")
+    for cfg in candidates:
+        tracer.configure(**cfg)
+        run()  # first use allocates the candidate's buffers
+        torch.cuda.synchronize(tracer.device)
+        ms = min(_time_once(tracer, run) for _ in range(repeats))
+        results[repr(cfg)] = ms
+        if ms < best_ms:
+            best, best_ms = cfg, ms
+    tracer.configure(**best)
+    return best, results

@@ -7,7 +7,9 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <algorithm>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ipt.h"
@@ -59,6 +61,7 @@ struct DeviceScene {
 struct PendingTiming {
   int id;
   cudaEvent_t a, b;
+  int launches;
 };
 
 struct ipt_ctx {
@@ -77,6 +80,10 @@ struct ipt_ctx {
   std::vector<cudaEvent_t> spare_events;
   double kernel_ms[IPT_KERNEL_COUNT] = {0};
   uint64_t kernel_n[IPT_KERNEL_COUNT] = {0};
+  ipt_config cfg = {1, 1u << 20, 32, 0};
+  ipt::WfBuffers wf;
+  std::vector<void*> wf_owned;
+  bool wf_adjoint = false;
 };
 
 namespace {
@@ -120,7 +127,7 @@ void resolve_timings(ipt_ctx* c) {
     float ms = 0.f;
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       c->kernel_ms[p.id] += ms;
-      c->kernel_n[p.id] += 1;
+      c->kernel_n[p.id] += (uint64_t)p.launches;
     }
     c->spare_events.push_back(p.a);
     c->spare_events.push_back(p.b);
@@ -144,6 +151,7 @@ cudaEvent_t take_event(ipt_ctx* c) {
 struct Timed {
   ipt_ctx* c;
   int id;
+  int launches = 1;  // kernels launched inside the bracket
   cudaEvent_t a = nullptr, b = nullptr;
   Timed(ipt_ctx* ctx, int kernel) : c(ctx), id(kernel) {
     if (c->flags & IPT_FLAG_KERNEL_TIMING) {
@@ -156,10 +164,35 @@ struct Timed {
   ~Timed() {
     if (a && b) {
       cudaEventRecord(b, c->stream);
-      c->pending.push_back({id, a, b});
+      c->pending.push_back({id, a, b, launches});
     }
   }
 };
+
+// Stage hook for the wavefront launchers: one event pair per launch.
+struct StageTimer {
+  ipt_ctx* c;
+  int id = 0;
+  cudaEvent_t a = nullptr;
+};
+
+void stage_begin(void* user, int id) {
+  StageTimer* t = static_cast<StageTimer*>(user);
+  if (t->c->pending.size() > 8192) resolve_timings(t->c);
+  t->id = id;
+  t->a = take_event(t->c);
+  if (t->a) cudaEventRecord(t->a, t->c->stream);
+}
+
+void stage_end(void* user) {
+  StageTimer* t = static_cast<StageTimer*>(user);
+  if (!t->a) return;
+  cudaEvent_t b = take_event(t->c);
+  if (!b) return;
+  cudaEventRecord(b, t->c->stream);
+  t->c->pending.push_back({t->id, t->a, b, 1});
+  t->a = nullptr;
+}
 
 ipt::SceneBuffers buffers(const ipt_ctx* ctx, const DeviceScene* s) {
   ipt::SceneBuffers b;
@@ -223,6 +256,112 @@ ipt_status ensure_tables(ipt_ctx* ctx, DeviceScene* s, const float* params, cons
   return IPT_OK;
 }
 
+void wf_release(ipt_ctx* c) {
+  for (void* p : c->wf_owned) cudaFree(p);
+  c->wf_owned.clear();
+  c->wf = ipt::WfBuffers();
+  c->wf_adjoint = false;
+}
+
+// Wavefront buffers for `cap` slots (plus the adjoint's carry when asked),
+// allocated on first use and kept by the context.
+ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params) {
+  const uint32_t cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
+  const bool fits = ctx->wf.cap == cap && (!adjoint || (ctx->wf_adjoint && ctx->wf.blk_params >= n_params));
+  if (fits) return IPT_OK;
+  IPT_CK(cudaStreamSynchronize(ctx->stream));
+  const uint32_t keep_params = std::max(n_params, ctx->wf.blk_params);
+  const bool want_adj = adjoint || ctx->wf_adjoint;
+  wf_release(ctx);
+  ipt::WfBuffers& w = ctx->wf;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t n) {
+    if (e != cudaSuccess) return;
+    void* q = nullptr;
+    e = cudaMalloc(&q, n * sizeof(**p));
+    if (e == cudaSuccess) {
+      ctx->wf_owned.push_back(q);
+      *p = static_cast<std::remove_reference_t<decltype(*p)>>(q);
+    }
+  };
+  A(&w.ray_o, cap);
+  A(&w.ray_d, cap);
+  A(&w.hit, cap);
+  A(&w.beta, cap);
+  A(&w.rad, cap);
+  A(&w.q0, cap);
+  A(&w.q1, cap);
+  A(&w.cnt, 8);
+  A(&w.sh_o, cap);
+  A(&w.sh_d, cap);
+  A(&w.sh_meta, cap);
+  A(&w.sh_c, cap);
+  A(&w.sh_vis, cap);
+  if (want_adj) {
+    A(&w.aT, (size_t)ipt::kMaxAdjointDepth * cap);
+    A(&w.aU, (size_t)ipt::kMaxAdjointDepth * cap);
+    A(&w.aR, (size_t)ipt::kMaxAdjointDepth * cap);
+    A(&w.nv, cap);
+    A(&w.sh_ge, cap);
+    A(&w.sh_gm, cap);
+    A(&w.sh_n, cap);
+    A(&w.blk, (size_t)ipt::wf_max_blocks(ctx->L) * keep_params);
+  }
+  if (e != cudaSuccess) {
+    wf_release(ctx);
+    return cuda_fail(ctx, e, "wavefront buffers");
+  }
+  w.cap = cap;
+  w.blk_params = want_adj ? keep_params : 0;
+  ctx->wf_adjoint = want_adj;
+  return IPT_OK;
+}
+
+bool use_wavefront(const ipt_ctx* ctx, uint32_t spp) {
+  const uint32_t cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
+  return ctx->cfg.integrator == 1 && spp <= cap;
+}
+
+// Forward pass through the configured integrator.
+ipt_status run_forward(ipt_ctx* ctx, DeviceScene* s, uint32_t begin, uint32_t n, const ipt::TraceParams& tp,
+                       float* img, float* msq, const float* target, float* g_out, double* partials, float g_scale,
+                       int loss_kind) {
+  if (use_wavefront(ctx, tp.spp)) {
+    ipt_status st = ensure_wf(ctx, false, 10u * s->n_seg);
+    if (st != IPT_OK) return st;
+    StageTimer timer{ctx};
+    const ipt::WfHook hook{stage_begin, stage_end, &timer};
+    IPT_CK(ipt::wf_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n, tp,
+                           ctx->wf, img, msq, target, g_out, partials, g_scale, loss_kind, ctx->err_dev,
+                           ctx->stream, (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr));
+  } else {
+    Timed tm(ctx, IPT_KERNEL_FORWARD);
+    IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
+                               tp, img, msq, target, g_out, partials, g_scale, loss_kind, ctx->err_dev,
+                               ctx->stream));
+  }
+  return IPT_OK;
+}
+
+// Adjoint pass (accumulates into grad_acc, which the caller zeroes).
+ipt_status run_adjoint(ipt_ctx* ctx, DeviceScene* s, uint32_t begin, uint32_t n, const ipt::TraceParams& tp,
+                       const float* g_img, double* grad_acc) {
+  if (use_wavefront(ctx, tp.spp)) {
+    ipt_status st = ensure_wf(ctx, true, 10u * s->n_seg);
+    if (st != IPT_OK) return st;
+    StageTimer timer{ctx};
+    const ipt::WfHook hook{stage_begin, stage_end, &timer};
+    IPT_CK(ipt::wf_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n, tp,
+                           ctx->wf, g_img, grad_acc, ctx->err_dev, ctx->stream,
+                           (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr));
+  } else {
+    Timed tm(ctx, IPT_KERNEL_ADJOINT);
+    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
+                               tp, g_img, grad_acc, ctx->err_dev, ctx->stream));
+  }
+  return IPT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -266,8 +405,8 @@ ipt_status ipt_create(ipt_ctx** out, const ipt_options* opt) {
   if (e == cudaSuccess) e = cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->loss_host, sizeof(double));
   if (e == cudaSuccess && (opt->flags & IPT_FLAG_COUNTERS)) {
-    e = cudaMalloc(&ctx->counters_dev, 4 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(ctx->counters_dev, 0, 4 * sizeof(unsigned long long));
+    e = cudaMalloc(&ctx->counters_dev, 6 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->counters_dev, 0, 6 * sizeof(unsigned long long));
   }
   if (e != cudaSuccess) {
     ipt_destroy(ctx);
@@ -282,6 +421,7 @@ ipt_status ipt_destroy(ipt_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (DeviceScene* s : ctx->scenes) free_scene(s);
+  wf_release(ctx);
   resolve_timings(ctx);
   for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
   if (ctx->counters_dev) cudaFree(ctx->counters_dev);
@@ -479,11 +619,8 @@ ipt_status ipt_render(ipt_ctx* ctx, int32_t scene, int32_t view, const ipt_trace
   if ((st = ensure_tables(ctx, s, p, sampling_params)) != IPT_OK) return st;
   const uint32_t begin = view < 0 ? 0u : s->views[view].offset;
   const uint32_t n = view < 0 ? (uint32_t)s->n_pix : s->views[view].w * s->views[view].h;
-  Timed tm(ctx, IPT_KERNEL_FORWARD);
-  IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
-                             trace_params(ctx, scene, opts, set, spp, iteration), rgb_out, msq_out, nullptr,
-                             nullptr, nullptr, 0.f, 0, ctx->err_dev, ctx->stream));
-  return IPT_OK;
+  return run_forward(ctx, s, begin, n, trace_params(ctx, scene, opts, set, spp, iteration), rgb_out, msq_out,
+                     nullptr, nullptr, nullptr, 0.f, 0);
 }
 
 ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t set, uint64_t iteration,
@@ -501,12 +638,9 @@ ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
   if ((st = ensure_tables(ctx, s, p, sampling_params)) != IPT_OK) return st;
   const uint32_t np = 10u * s->n_seg;
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
-  {
-    Timed tm(ctx, IPT_KERNEL_ADJOINT);
-    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), 0,
-                               (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
-                               grad_image, s->grad_acc, ctx->err_dev, ctx->stream));
-  }
+  st = run_adjoint(ctx, s, 0, (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
+                   grad_image, s->grad_acc);
+  if (st != IPT_OK) return st;
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(nullptr, 0, nullptr, s->grad_acc, grad_out, np, ctx->stream));
   return IPT_OK;
@@ -527,23 +661,16 @@ static ipt_status loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, c
   if ((st = ensure_tables(ctx, s, s->params, nullptr)) != IPT_OK) return st;
   const uint32_t np = 10u * s->n_seg;
   const float g_scale = (float)(1.0 / (3.0 * (double)n_total));
-  {
-    Timed tm(ctx, IPT_KERNEL_FORWARD);
-    IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(),
-                               (uint32_t)begin, (uint32_t)count,
-                               trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration), nullptr,
-                               nullptr, s->target + 3 * begin, s->g_img + 3 * begin, s->loss_partials, g_scale,
-                               opts->loss, ctx->err_dev, ctx->stream));
-  }
+  st = run_forward(ctx, s, (uint32_t)begin, (uint32_t)count,
+                   trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration), nullptr, nullptr,
+                   s->target + 3 * begin, s->g_img + 3 * begin, s->loss_partials, g_scale, opts->loss);
+  if (st != IPT_OK) return st;
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
   const uint32_t set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
-  {
-    Timed tm(ctx, IPT_KERNEL_ADJOINT);
-    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(),
-                               (uint32_t)begin, (uint32_t)count,
-                               trace_params(ctx, scene, opts, set, opts->spp_d, iteration), s->g_img + 3 * begin,
-                               s->grad_acc, ctx->err_dev, ctx->stream));
-  }
+  st = run_adjoint(ctx, s, (uint32_t)begin, (uint32_t)count,
+                   trace_params(ctx, scene, opts, set, opts->spp_d, iteration), s->g_img + 3 * begin,
+                   s->grad_acc);
+  if (st != IPT_OK) return st;
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, s->grad_acc,
                               grad_out, np, ctx->stream));
@@ -669,6 +796,36 @@ ipt_status ipt_scene_info(ipt_ctx* ctx, int32_t scene, uint32_t* n_tri, uint32_t
   return IPT_OK;
 }
 
+ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg) {
+  if (!ctx || !cfg) return IPT_ERR_INVALID_ARG;
+  if (cfg->integrator != 0 && cfg->integrator != 1)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "integrator must be 0 (megakernel) or 1 (wavefront)");
+  if (cfg->wavefront_slots && cfg->wavefront_slots < 1024)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "wavefront_slots must be 0 or at least 1024");
+  if (cfg->trace_steps > 4096) return fail(ctx, IPT_ERR_INVALID_ARG, "trace_steps above 4096");
+  IPT_CK(cudaSetDevice(ctx->device));
+  const uint32_t old_cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
+  const uint32_t new_cap = cfg->wavefront_slots ? cfg->wavefront_slots : (1u << 20);
+  if (old_cap != new_cap || cfg->blocks_per_sm != ctx->cfg.blocks_per_sm) {
+    IPT_CK(cudaStreamSynchronize(ctx->stream));
+    wf_release(ctx);
+  }
+  ctx->cfg = *cfg;
+  ctx->L.wf_steps = cfg->trace_steps ? (int)cfg->trace_steps : 32;
+  if (cfg->blocks_per_sm) {
+    ctx->L.wf_blocks_per_sm = (int)cfg->blocks_per_sm;
+  } else {
+    IPT_CK(ipt::wf_init(&ctx->L));
+  }
+  return IPT_OK;
+}
+
+ipt_status ipt_config_get(const ipt_ctx* ctx, ipt_config* cfg) {
+  if (!ctx || !cfg) return IPT_ERR_INVALID_ARG;
+  *cfg = ctx->cfg;
+  return IPT_OK;
+}
+
 ipt_status ipt_kernel_times(ipt_ctx* ctx, double* total_ms, uint64_t* launches, int32_t reset) {
   if (!ctx) return IPT_ERR_INVALID_ARG;
   if (!(ctx->flags & IPT_FLAG_KERNEL_TIMING))
@@ -691,9 +848,9 @@ ipt_status ipt_counters_read(ipt_ctx* ctx, uint64_t* out, int32_t reset) {
   if (!ctx->counters_dev) return fail(ctx, IPT_ERR_INVALID_ARG, "context created without IPT_FLAG_COUNTERS");
   IPT_CK(cudaSetDevice(ctx->device));
   IPT_CK(cudaStreamSynchronize(ctx->stream));
-  unsigned long long v[4];
+  unsigned long long v[6];
   IPT_CK(cudaMemcpy(v, ctx->counters_dev, sizeof(v), cudaMemcpyDeviceToHost));
-  for (int k = 0; k < 4; ++k) out[k] = v[k];
+  for (int k = 0; k < 6; ++k) out[k] = v[k];
   if (reset) IPT_CK(cudaMemset(ctx->counters_dev, 0, sizeof(v)));
   return IPT_OK;
 }

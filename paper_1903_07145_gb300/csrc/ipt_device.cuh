@@ -89,11 +89,12 @@ struct SceneDev {
   unsigned long long* counters;  // optional: closest rays, shadow rays, node visits, triangle tests
 };
 
+// kind 0: closest-hit ray, 1: shadow ray
 __device__ __forceinline__ void count_ray(const SceneDev& s, int kind, uint32_t nodes, uint32_t tests) {
   if (s.counters) {
     atomicAdd(&s.counters[kind], 1ull);
-    atomicAdd(&s.counters[2], (unsigned long long)nodes);
-    atomicAdd(&s.counters[3], (unsigned long long)tests);
+    atomicAdd(&s.counters[2 + 2 * kind], (unsigned long long)nodes);
+    atomicAdd(&s.counters[3 + 2 * kind], (unsigned long long)tests);
   }
 }
 

@@ -78,6 +78,25 @@ struct Launcher {
   int num_sms = 0;
   int fwd_blocks_per_sm = 0;
   int adj_blocks_per_sm[4] = {0, 0, 0, 0};
+  int wf_blocks_per_sm = 0;
+  int wf_steps = 32;  // node visits per refill round of the persistent traversal
+};
+
+// Wavefront state (device), sized for `cap` path slots per chunk.
+struct WfBuffers {
+  float4 *ray_o = nullptr, *ray_d = nullptr, *hit = nullptr, *beta = nullptr, *rad = nullptr;
+  uint32_t *q0 = nullptr, *q1 = nullptr, *cnt = nullptr;
+  float4 *sh_o = nullptr, *sh_d = nullptr;
+  uint4* sh_meta = nullptr;
+  float4* sh_c = nullptr;
+  uint32_t* sh_vis = nullptr;
+  float4 *aT = nullptr, *aU = nullptr;
+  float2* aR = nullptr;
+  uint32_t* nv = nullptr;
+  float4 *sh_ge = nullptr, *sh_gm = nullptr, *sh_n = nullptr;
+  float* blk = nullptr;
+  uint32_t cap = 0;
+  uint32_t blk_params = 0;  // S x 10 capacity of each block row
 };
 
 constexpr int kMaxAdjointDepth = 8;
@@ -121,5 +140,26 @@ cudaError_t launch_philox(uint32_t n, const uint32_t* ctr, const uint32_t* key, 
                           cudaStream_t st);
 
 cudaError_t init_launcher(Launcher* L, int device);
+
+// Optional per-stage timing hook of the wavefront launchers.
+struct WfHook {
+  void (*begin)(void* user, int kernel_id);
+  void (*end)(void* user);
+  void* user;
+};
+
+cudaError_t wf_init(Launcher* L);
+int wf_max_blocks(const Launcher& L);
+
+cudaError_t wf_forward(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
+                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
+                       const WfBuffers& wb, float* img, float* msq, const float* target, float* g_out,
+                       double* loss_partials, float g_scale, int loss_kind, uint32_t* err, cudaStream_t st,
+                       const WfHook* hook);
+
+cudaError_t wf_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
+                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
+                       const WfBuffers& wb, const float* g_img, double* grad_acc, uint32_t* err,
+                       cudaStream_t st, const WfHook* hook);
 
 }  // namespace ipt

@@ -1,0 +1,831 @@
+// Wavefront integrator: the same paths as the megakernel (same random numbers
+// at the same (vertex, call) slots), traced stage by stage over chunks of
+// path slots so that every traversal launch works on a compacted queue.
+//
+// Per chunk (slots are pixel-major: slot = local_pixel * spp + sample):
+//   wf_camera                   camera rays, path state, queue 0 = all slots
+//   per vertex k = 0..D:
+//     wf_trace<closest>         persistent closest-hit traversal; lanes refill
+//                               from the queue as their rays finish
+//     shading                   emission (MIS), next-event candidate -> shadow
+//                               queue, BRDF sample -> next queue
+//     wf_trace<any>             persistent shadow-ray traversal
+//   wf_reduce                   per-pixel mean / residual / loss partials
+// The adjoint splits shading in two (before and after the shadow rays), keeps
+// each path's per-vertex carry (T_l, U_l, dw/dtheta factors) in SoA global
+// memory, and accumulates g . dI/dtheta in per-block shared memory flushed to
+// block-private global rows (reduced in FP64 at the end of the pass).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ipt_device.cuh"
+#include "ipt_internal.h"
+#include "ipt_path.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ipt {
+
+constexpr uint32_t kDead = 0x80000000u;  // beta.w flag: path finished
+constexpr int kWfThreads = 128;
+
+struct WfDev {
+  float4* ray_o;  // origin, w = skip triangle (int bits)
+  float4* ray_d;  // direction, w = pdf of this direction (0 for camera rays)
+  float4* hit;    // x = triangle (int bits, -1 miss), t, u, v
+  float4* beta;   // throughput, w = vertex index | kDead
+  float4* rad;    // path radiance (forward)
+  uint32_t* q0;
+  uint32_t* q1;
+  uint32_t* cnt;  // [0] |q0|, [1] |q1|, [2] |shadow|, [3] closest fetch, [4] shadow fetch
+  float4* sh_o;   // origin, w = skip triangle a
+  float4* sh_d;   // direction, w = extent
+  uint4* sh_meta; // slot, skip triangle b (light), vertex segment, light segment
+  float4* sh_c;   // forward: contribution
+  uint32_t* sh_vis;
+  // adjoint
+  float4* aT;     // [l * cap + slot]: T_l.xyz, dw/dkd factor
+  float4* aU;     // U_l.xyz, dw/dks factor
+  float2* aR;     // dw/dr factor, segment (int bits)
+  uint32_t* nv;
+  float4* sh_ge;  // g beta f k es (emission gradient of the light segment)
+  float4* sh_gm;  // g beta Le k, w = specular factor
+  float4* sh_n;   // f Le k (the contribution without beta), w = d spec / d r
+  float* blk;     // per-block rows of S x 10 partial gradients
+  uint32_t cap;
+};
+
+__device__ __forceinline__ uint32_t* queue(const WfDev& w, int which) { return which ? w.q1 : w.q0; }
+
+// Warp-aggregated append: one atomic per group of lanes that arrive together.
+__device__ __forceinline__ uint32_t enqueue(uint32_t* counter, bool want) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  const unsigned m = g.ballot(want);
+  if (!m) return 0xffffffffu;
+  const int leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if ((int)g.thread_rank() == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
+  base = g.shfl(base, leader);
+  return want ? base + (uint32_t)__popc(m & ((1u << g.thread_rank()) - 1u)) : 0xffffffffu;
+}
+
+__device__ __forceinline__ void slot_pixel(uint32_t slot, uint32_t spp, uint32_t& lp, uint32_t& smp) {
+  lp = slot / spp;
+  smp = slot - lp * spp;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWfThreads) wf_camera(const ViewDev* views, uint32_t n_views, uint32_t pix0,
+                                                        uint32_t n_slots, PathParams pp, WfDev w) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    w.cnt[0] = n_slots;
+    w.cnt[3] = 0;
+  }
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n_slots; slot += gridDim.x * blockDim.x) {
+    uint32_t lp, smp;
+    slot_pixel(slot, pp.spp, lp, smp);
+    const uint32_t pid = pix0 + lp;
+    const ViewDev& vw = find_view(views, n_views, pid);
+    const uint32_t l = pid - vw.offset;
+    PathRng rng;
+    rng.base = make_uint4(pid, smp, pp.set_iter, 0);
+    rng.key = pp.key;
+    float3 o;
+    const float3 d = camera_ray(vw, l % vw.w, l / vw.w, rng, o);
+    w.ray_o[slot] = make_float4(o.x, o.y, o.z, __int_as_float(-1));
+    w.ray_d[slot] = make_float4(d.x, d.y, d.z, 0.0f);
+    w.beta[slot] = make_float4(1.0f, 1.0f, 1.0f, __uint_as_float(0u));
+    w.rad[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    w.q0[slot] = slot;
+    if (w.nv) w.nv[slot] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent traversal with per-lane refill.  kMode 0: closest hit of queue
+// `cur` into w.hit; 1: shadow rays, adding the forward contribution of the
+// unoccluded ones; 2: shadow rays, visibility flag only (adjoint).
+// ---------------------------------------------------------------------------
+struct Trav {
+  RayPre r;
+  float3 oinv;
+  float tmax;
+  int skip_a, skip_b;
+  int node, sp;
+  int stack[kStackSize];
+  int best, best_orig;
+  float bt, bu, bv;
+  bool occluded;
+  uint32_t n_nodes, n_tests;
+};
+
+__device__ __forceinline__ void trav_init(Trav& T, float3 o, float3 d, float tmax, int skip_a, int skip_b) {
+  T.r = ray_pre(o, d);
+  T.oinv = f3(o.x * T.r.inv.x, o.y * T.r.inv.y, o.z * T.r.inv.z);
+  T.tmax = tmax;
+  T.skip_a = skip_a;
+  T.skip_b = skip_b;
+  T.node = 0;
+  T.sp = 0;
+  T.best = -1;
+  T.best_orig = 0x7fffffff;
+  T.bt = tmax;
+  T.bu = T.bv = 0.0f;
+  T.occluded = false;
+  T.n_nodes = T.n_tests = 0;
+}
+
+// Runs up to `steps` node visits; returns true when the traversal is over.
+template <bool kAny>
+__device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, int steps, uint32_t* err) {
+  for (int it = 0; it < steps; ++it) {
+    if (T.node >= 0) {
+      ++T.n_nodes;
+      const float4 n0 = __ldg(&s.nodes[4 * T.node + 0]);
+      const float4 n1 = __ldg(&s.nodes[4 * T.node + 1]);
+      const float4 n2 = __ldg(&s.nodes[4 * T.node + 2]);
+      const float4 n3 = __ldg(&s.nodes[4 * T.node + 3]);
+      float t0, t1;
+      box2(T.r, T.oinv, n0, n1, n2, kAny ? T.tmax : T.bt, t0, t1);
+      const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      const bool h0 = t0 != __int_as_float(0x7f800000);
+      const bool h1 = t1 != __int_as_float(0x7f800000);
+      if (h0 && h1) {
+        if (T.sp >= kStackSize) {
+          atomicOr(err, kErrStack);
+          T.best = -1;
+          T.occluded = true;
+          return true;
+        }
+        if (!kAny && t1 < t0) {
+          T.stack[T.sp++] = c0;
+          T.node = c1;
+        } else {
+          T.stack[T.sp++] = c1;
+          T.node = c0;
+        }
+        continue;
+      }
+      if (h0 || h1) {
+        T.node = h0 ? c0 : c1;
+        continue;
+      }
+    } else {
+      int first, count;
+      decode_leaf(T.node, first, count);
+      T.n_tests += count;
+      for (int i = first; i < first + count; ++i) {
+        if (i == T.skip_a || i == T.skip_b) continue;
+        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+        float t, u, v;
+        if (kAny) {
+          if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.tmax, t, u, v)) {
+            T.occluded = true;
+            return true;
+          }
+        } else if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.bt * 1.0000002f, t, u, v)) {
+          const int orig = __float_as_int(q0.w);
+          if (t < T.bt || (t == T.bt && orig < T.best_orig)) {
+            T.best = i;
+            T.bt = t;
+            T.bu = u;
+            T.bv = v;
+            T.best_orig = orig;
+          }
+        }
+      }
+    }
+    if (T.sp == 0) return true;
+    T.node = T.stack[--T.sp];
+  }
+  return false;
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int cur, int steps, uint32_t* err) {
+  constexpr bool kAny = kMode != 0;
+  if (!kAny && blockIdx.x == 0 && threadIdx.x == 0) {
+    w.cnt[cur ? 0 : 1] = 0;  // next queue, filled by the shading stage
+    w.cnt[2] = 0;            // shadow queue
+    w.cnt[4] = 0;            // shadow fetch counter
+  }
+  const uint32_t n = kAny ? w.cnt[2] : w.cnt[cur];
+  uint32_t* fetch = kAny ? &w.cnt[4] : &w.cnt[3];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  Trav T;
+  int64_t item = -1;
+  bool exhausted = false;
+  for (;;) {
+    const bool need = item < 0 && !exhausted;
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      uint32_t base = 0;
+      if ((int)lane == leader) base = atomicAdd(fetch, (uint32_t)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const uint32_t i = base + (uint32_t)__popc(m & lt_mask);
+        if (i < n) {
+          item = i;
+          if (kAny) {
+            const float4 o = w.sh_o[i], d = w.sh_d[i];
+            trav_init(T, xyz(o), xyz(d), d.w, __float_as_int(o.w), (int)w.sh_meta[i].y);
+          } else {
+            const uint32_t slot = queue(w, cur)[i];
+            const float4 o = w.ray_o[slot], d = w.ray_d[slot];
+            trav_init(T, xyz(o), xyz(d), __int_as_float(0x7f800000), __float_as_int(o.w), -1);
+          }
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, item < 0)) break;
+    if (item >= 0 && trav_run<kAny>(s, T, steps, err)) {
+      const uint32_t i = (uint32_t)item;
+      count_ray(s, kAny ? 1 : 0, T.n_nodes, T.n_tests);
+      if (kMode == 0) {
+        const uint32_t slot = queue(w, cur)[i];
+        w.hit[slot] = make_float4(__int_as_float(T.best), T.bt, T.bu, T.bv);
+      } else if (kMode == 1) {
+        if (!T.occluded) {
+          const uint32_t slot = w.sh_meta[i].x;
+          const float4 c = w.sh_c[i];
+          float4 r = w.rad[slot];
+          r.x += c.x;
+          r.y += c.y;
+          r.z += c.z;
+          w.rad[slot] = r;
+        }
+      } else {
+        w.sh_vis[i] = T.occluded ? 0u : 1u;
+      }
+      item = -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward shading of queue `cur`.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(SceneDev s, SegDev t, uint32_t pix0, PathParams pp,
+                                                           WfDev w, int cur) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;  // closest fetch counter of the next vertex
+  const uint32_t n = w.cnt[cur];
+  const double W = *t.W;
+  const bool light_on = pp.nee && W > 0.0;
+  uint32_t* qin = queue(w, cur);
+  uint32_t* qout = queue(w, cur ^ 1);
+  uint32_t* nout = &w.cnt[cur ^ 1];
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t slot = qin[q];
+    const float4 hh = w.hit[slot];
+    const int tri = __float_as_int(hh.x);
+    bool cont = false, shadow = false;
+    NeeResult ne;
+    float3 shc = f3(0.f, 0.f, 0.f);
+    float3 beta = f3(0.f, 0.f, 0.f), wo = f3(0.f, 0.f, 0.f), org = f3(0.f, 0.f, 0.f);
+    float pdf = 0.0f;
+    uint32_t k = 0;
+    if (tri >= 0) {
+      const float4 bt = w.beta[slot];
+      k = __float_as_uint(bt.w) & 0xffffu;
+      beta = xyz(bt);
+      const float4 rd = w.ray_d[slot];
+      Hit h;
+      h.tri = tri;
+      h.t = hh.y;
+      h.u = hh.z;
+      h.v = hh.w;
+      const Vtx v = make_vertex(s, h, xyz(rd), pp.profile);
+      if (v.prof > 0.0f) {
+        const float wb = emission_weight(t, v, h.t, k > 0, light_on, rd.w, pp.mis);
+        if (wb > 0.0f) {
+          const float3 L = beta * xyz(__ldg(&t.emis[v.seg])) * (wb * v.prof);
+          float4 r = w.rad[slot];
+          w.rad[slot] = make_float4(r.x + L.x, r.y + L.y, r.z + L.z, 0.0f);
+        }
+      }
+      if (k < pp.max_depth) {
+        uint32_t lp, smp;
+        slot_pixel(slot, pp.spp, lp, smp);
+        PathRng rng;
+        rng.base = make_uint4(pix0 + lp, smp, pp.set_iter, 0);
+        rng.key = pp.key;
+        const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
+        const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
+        const float4 sa = __ldg(&t.samp[v.seg]);
+        if (light_on) {
+          ne = nee_prepare(s, t, v, ua, ub, W, pp.profile, pp.mis, sa.y, sa.x);
+          if (ne.valid) {
+            const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
+            shc = beta * bv.f * xyz(__ldg(&t.emis[ne.seg])) * ne.k;
+            shadow = true;
+          }
+        }
+        if (dot(v.wi, v.ns) > 0.0f) {
+          wo = bsdf_sample(__ldg(&t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
+          pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
+          const float co = dot(wo, v.ns);
+          if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
+            const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
+            beta = beta * bv.f * (co / pdf);
+            org = v.x + v.ng * s.eps;
+            cont = true;
+          }
+        }
+      }
+    }
+    const uint32_t si = enqueue(&w.cnt[2], shadow);
+    if (shadow) {
+      w.sh_o[si] = make_float4(ne.so.x, ne.so.y, ne.so.z, __int_as_float(tri));
+      w.sh_d[si] = make_float4(ne.sd.x, ne.sd.y, ne.sd.z, ne.st);
+      w.sh_meta[si] = make_uint4(slot, (uint32_t)ne.tri, 0u, (uint32_t)ne.seg);
+      w.sh_c[si] = make_float4(shc.x, shc.y, shc.z, 0.0f);
+    }
+    const uint32_t ci = enqueue(nout, cont);
+    if (cont) {
+      qout[ci] = slot;
+      w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
+      w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
+      w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(k + 1));
+    }
+  }
+}
+
+// Per-pixel reduction of a chunk: mean (and mean of squares), or the residual
+// and loss partials.  Outputs are indexed by pixel - out_begin.
+__global__ void __launch_bounds__(kWfThreads) wf_reduce(WfDev w, uint32_t pix0, uint32_t n_pix, uint32_t spp,
+                                                        uint32_t out_begin, float* img, float* msq,
+                                                        const float* target, float* g_out, double* loss_partials,
+                                                        int first_chunk, float g_scale, int loss_kind) {
+  double loss_acc = 0.0;
+  const float inv = 1.0f / (float)spp;
+  for (uint32_t lp = blockIdx.x * blockDim.x + threadIdx.x; lp < n_pix; lp += gridDim.x * blockDim.x) {
+    float3 a = f3(0.f, 0.f, 0.f), a2 = f3(0.f, 0.f, 0.f);
+    for (uint32_t smp = 0; smp < spp; ++smp) {
+      const float3 L = xyz(w.rad[lp * spp + smp]);
+      a = a + L;
+      a2 = a2 + L * L;
+    }
+    const uint32_t o = pix0 + lp - out_begin;
+    const float3 mean = a * inv;
+    if (img) {
+      img[3 * o + 0] = mean.x;
+      img[3 * o + 1] = mean.y;
+      img[3 * o + 2] = mean.z;
+    }
+    if (msq) {
+      msq[3 * o + 0] = a2.x * inv;
+      msq[3 * o + 1] = a2.y * inv;
+      msq[3 * o + 2] = a2.z * inv;
+    }
+    if (target) {
+      const float r[3] = {mean.x - target[3 * o], mean.y - target[3 * o + 1], mean.z - target[3 * o + 2]};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (loss_kind == 0) {
+          g_out[3 * o + c] = 2.0f * r[c] * g_scale;
+          loss_acc += (double)r[c] * (double)r[c];
+        } else {
+          g_out[3 * o + c] = (r[c] > 0.0f ? 1.0f : (r[c] < 0.0f ? -1.0f : 0.0f)) * g_scale;
+          loss_acc += fabs((double)r[c]);
+        }
+      }
+    }
+  }
+  if (loss_partials) {
+    __shared__ double red[kWfThreads / 32];
+    for (int off = 16; off >= 1; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loss_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int i = 0; i < kWfThreads / 32; ++i) sum += red[i];
+      loss_partials[blockIdx.x] = first_chunk ? sum : loss_partials[blockIdx.x] + sum;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint stages.  Shared accumulator helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void acc_zero(float* sacc, uint32_t n) {
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sacc[i] = 0.0f;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void acc_flush(const float* sacc, uint32_t n, float* blk) {
+  __syncthreads();
+  float* row = blk + (size_t)blockIdx.x * n;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = sacc[i];
+    if (v != 0.0f) row[i] += v;
+  }
+}
+
+__device__ __forceinline__ void scatter3(float* acc, int i, float3 v) {
+  atomicAdd(&acc[i], v.x);
+  atomicAdd(&acc[i + 1], v.y);
+  atomicAdd(&acc[i + 2], v.z);
+}
+
+__device__ __forceinline__ float3 pixel_grad(const float* g_img, uint32_t pix0, uint32_t g_begin, uint32_t slot,
+                                             uint32_t spp, float inv_spp) {
+  const uint32_t lp = slot / spp;
+  const uint32_t o = pix0 + lp - g_begin;
+  return f3(g_img[3 * o], g_img[3 * o + 1], g_img[3 * o + 2]) * inv_spp;
+}
+
+// Continuation terms of a finished path: (dw_l / dtheta) . (g * U_l).
+__device__ __forceinline__ void finish_path(const WfDev& w, const SegDev& t, uint32_t slot, float3 gp, float* sacc) {
+  const uint32_t nv = w.nv[slot];
+  for (uint32_t l = 0; l < nv; ++l) {
+    const size_t ix = (size_t)l * w.cap + slot;
+    const float4 T = w.aT[ix], U = w.aU[ix];
+    const float2 R = w.aR[ix];
+    const int sg = __float_as_int(R.y);
+    const float3 q = gp * xyz(U);
+    scatter3(sacc, 10 * sg + 0, q * T.w);
+    scatter3(sacc, 10 * sg + 3, q * U.w);
+    const float4 mb = __ldg(&t.mat_b[sg]);
+    atomicAdd(&sacc[10 * sg + 6], dot(q, f3(mb.x, mb.y, mb.z)) * R.x);
+  }
+}
+
+__device__ __forceinline__ void add_to_carry(const WfDev& w, uint32_t slot, float3 C) {
+  const uint32_t nv = w.nv[slot];
+  for (uint32_t l = 0; l < nv; ++l) {
+    const size_t ix = (size_t)l * w.cap + slot;
+    const float4 T = w.aT[ix];
+    float4 U = w.aU[ix];
+    U.x += T.x * C.x;
+    U.y += T.y * C.y;
+    U.z += T.z * C.z;
+    w.aU[ix] = U;
+  }
+}
+
+// Stage A: emission at the vertex, its contribution to the carry, and the
+// next-event candidate.
+__global__ void __launch_bounds__(kWfThreads) wf_adj_a(SceneDev s, SegDev t, uint32_t pix0, uint32_t g_begin,
+                                                       PathParams pp, WfDev w, int cur, const float* g_img) {
+  extern __shared__ float sacc[];
+  const uint32_t np = 10u * s.n_seg;
+  acc_zero(sacc, np);
+  const uint32_t n = w.cnt[cur];
+  const double W = *t.W;
+  const bool light_on = pp.nee && W > 0.0;
+  const float es = pp.emission_scale;
+  const float inv_spp = 1.0f / (float)pp.spp;
+  uint32_t* qin = queue(w, cur);
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t slot = qin[q];
+    const float4 hh = w.hit[slot];
+    const int tri = __float_as_int(hh.x);
+    const float3 gp = pixel_grad(g_img, pix0, g_begin, slot, pp.spp, inv_spp);
+    const float4 bt = w.beta[slot];
+    const uint32_t k = __float_as_uint(bt.w) & 0xffffu;
+    bool shadow = false;
+    NeeResult ne;
+    float3 ge = f3(0.f, 0.f, 0.f), gm = f3(0.f, 0.f, 0.f), cn = f3(0.f, 0.f, 0.f);
+    float spec = 0.0f, dsdr = 0.0f;
+    int vseg = 0;
+    if (tri < 0) {
+      finish_path(w, t, slot, gp, sacc);
+      w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(k | kDead));
+    } else {
+      const float3 beta = xyz(bt);
+      const float4 rd = w.ray_d[slot];
+      Hit h;
+      h.tri = tri;
+      h.t = hh.y;
+      h.u = hh.z;
+      h.v = hh.w;
+      const Vtx v = make_vertex(s, h, xyz(rd), pp.profile);
+      vseg = v.seg;
+      if (v.prof > 0.0f) {
+        const float wb = emission_weight(t, v, h.t, k > 0, light_on, rd.w, pp.mis);
+        if (wb > 0.0f) {
+          const float f = wb * v.prof;
+          add_to_carry(w, slot, xyz(__ldg(&t.emis[v.seg])) * f);
+          scatter3(sacc, 10 * v.seg + 7, gp * beta * (f * es));
+        }
+      }
+      if (k == pp.max_depth) {
+        finish_path(w, t, slot, gp, sacc);
+        w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(k | kDead));
+      } else if (light_on) {
+        uint32_t lp, smp;
+        slot_pixel(slot, pp.spp, lp, smp);
+        PathRng rng;
+        rng.base = make_uint4(pix0 + lp, smp, pp.set_iter, 0);
+        rng.key = pp.key;
+        const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
+        const float4 sa = __ldg(&t.samp[v.seg]);
+        ne = nee_prepare(s, t, v, ua, ub, W, pp.profile, pp.mis, sa.y, sa.x);
+        if (ne.valid) {
+          const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
+          const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
+          const float3 Le = xyz(__ldg(&t.emis[ne.seg]));
+          ge = gp * beta * bv.f * (ne.k * es);
+          gm = gp * beta * Le * ne.k;
+          cn = bv.f * Le * ne.k;
+          spec = bv.sp.s;
+          dsdr = bv.sp.ds_dr;
+          shadow = true;
+        }
+      }
+    }
+    const uint32_t si = enqueue(&w.cnt[2], shadow);
+    if (shadow) {
+      w.sh_o[si] = make_float4(ne.so.x, ne.so.y, ne.so.z, __int_as_float(tri));
+      w.sh_d[si] = make_float4(ne.sd.x, ne.sd.y, ne.sd.z, ne.st);
+      w.sh_meta[si] = make_uint4(slot, (uint32_t)ne.tri, (uint32_t)vseg, (uint32_t)ne.seg);
+      w.sh_ge[si] = make_float4(ge.x, ge.y, ge.z, 0.0f);
+      w.sh_gm[si] = make_float4(gm.x, gm.y, gm.z, spec);
+      w.sh_n[si] = make_float4(cn.x, cn.y, cn.z, dsdr);
+    }
+  }
+  acc_flush(sacc, np, w.blk);
+}
+
+// Unoccluded next-event terms: light emission (Eq. 5), the vertex material
+// (Eq. 6 at this vertex) and the carry of the earlier vertices.
+__global__ void __launch_bounds__(kWfThreads) wf_adj_connect(SceneDev s, SegDev t, WfDev w) {
+  extern __shared__ float sacc[];
+  const uint32_t np = 10u * s.n_seg;
+  acc_zero(sacc, np);
+  const uint32_t n = w.cnt[2];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (!w.sh_vis[i]) continue;
+    const uint4 m = w.sh_meta[i];
+    const float4 ge = w.sh_ge[i], gm = w.sh_gm[i], cn = w.sh_n[i];
+    scatter3(sacc, 10 * m.w + 7, xyz(ge));
+    const float3 q = xyz(gm);
+    scatter3(sacc, 10 * m.z + 0, q * (1.0f / kPi));
+    scatter3(sacc, 10 * m.z + 3, q * gm.w);
+    const float4 mb = __ldg(&t.mat_b[m.z]);
+    atomicAdd(&sacc[10 * m.z + 6], dot(q, f3(mb.x, mb.y, mb.z)) * cn.w);
+    add_to_carry(w, m.x, xyz(cn));
+  }
+  acc_flush(sacc, np, w.blk);
+}
+
+// Stage B: BRDF sampling; the new vertex joins the carry.
+__global__ void __launch_bounds__(kWfThreads) wf_adj_b(SceneDev s, SegDev t, uint32_t pix0, uint32_t g_begin,
+                                                       PathParams pp, WfDev w, int cur, const float* g_img) {
+  extern __shared__ float sacc[];
+  const uint32_t np = 10u * s.n_seg;
+  acc_zero(sacc, np);
+  if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;
+  const uint32_t n = w.cnt[cur];
+  const float inv_spp = 1.0f / (float)pp.spp;
+  uint32_t* qin = queue(w, cur);
+  uint32_t* qout = queue(w, cur ^ 1);
+  uint32_t* nout = &w.cnt[cur ^ 1];
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t slot = qin[q];
+    const float4 bt = w.beta[slot];
+    const uint32_t kw = __float_as_uint(bt.w);
+    bool cont = false;
+    float3 org = f3(0.f, 0.f, 0.f), wo = f3(0.f, 0.f, 0.f), beta = xyz(bt);
+    float pdf = 0.0f;
+    int tri = -1;
+    const uint32_t k = kw & 0xffffu;
+    if (!(kw & kDead)) {
+      const float4 hh = w.hit[slot];
+      tri = __float_as_int(hh.x);
+      const float4 rd = w.ray_d[slot];
+      Hit h;
+      h.tri = tri;
+      h.t = hh.y;
+      h.u = hh.z;
+      h.v = hh.w;
+      const Vtx v = make_vertex(s, h, xyz(rd), pp.profile);
+      uint32_t lp, smp;
+      slot_pixel(slot, pp.spp, lp, smp);
+      PathRng rng;
+      rng.base = make_uint4(pix0 + lp, smp, pp.set_iter, 0);
+      rng.key = pp.key;
+      const float4 ua = rng.draw(k, 0);
+      const float4 sa = __ldg(&t.samp[v.seg]);
+      if (dot(v.wi, v.ns) > 0.0f) {
+        wo = bsdf_sample(__ldg(&t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
+        pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
+        const float co = dot(wo, v.ns);
+        if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
+          const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
+          const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
+          const float kk = co / pdf;
+          const float3 wgt = bv.f * kk;
+          const uint32_t nv = w.nv[slot];
+          for (uint32_t l = 0; l < nv; ++l) {
+            const size_t ix = (size_t)l * w.cap + slot;
+            float4 T = w.aT[ix];
+            T.x *= wgt.x;
+            T.y *= wgt.y;
+            T.z *= wgt.z;
+            w.aT[ix] = T;
+          }
+          const size_t ix = (size_t)nv * w.cap + slot;
+          w.aT[ix] = make_float4(beta.x, beta.y, beta.z, kk * (1.0f / kPi));
+          w.aU[ix] = make_float4(0.f, 0.f, 0.f, kk * bv.sp.s);
+          w.aR[ix] = make_float2(kk * bv.sp.ds_dr, __int_as_float(v.seg));
+          w.nv[slot] = nv + 1;
+          beta = beta * wgt;
+          org = v.x + v.ng * s.eps;
+          cont = true;
+        }
+      }
+      if (!cont) {
+        finish_path(w, t, slot, pixel_grad(g_img, pix0, g_begin, slot, pp.spp, inv_spp), sacc);
+        w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(k | kDead));
+      }
+    }
+    const uint32_t ci = enqueue(nout, cont);
+    if (cont) {
+      qout[ci] = slot;
+      w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
+      w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
+      w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(k + 1));
+    }
+  }
+  acc_flush(sacc, np, w.blk);
+}
+
+__global__ void wf_blk_reduce(const float* blk, int rows, uint32_t np, double* grad_acc) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += (double)blk[(size_t)r * np + i];
+    grad_acc[i] += s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static WfDev wf_dev(const WfBuffers& b) {
+  WfDev w;
+  w.ray_o = b.ray_o;
+  w.ray_d = b.ray_d;
+  w.hit = b.hit;
+  w.beta = b.beta;
+  w.rad = b.rad;
+  w.q0 = b.q0;
+  w.q1 = b.q1;
+  w.cnt = b.cnt;
+  w.sh_o = b.sh_o;
+  w.sh_d = b.sh_d;
+  w.sh_meta = b.sh_meta;
+  w.sh_c = b.sh_c;
+  w.sh_vis = b.sh_vis;
+  w.aT = b.aT;
+  w.aU = b.aU;
+  w.aR = b.aR;
+  w.nv = b.nv;
+  w.sh_ge = b.sh_ge;
+  w.sh_gm = b.sh_gm;
+  w.sh_n = b.sh_n;
+  w.blk = b.blk;
+  w.cap = b.cap;
+  return w;
+}
+
+static int wf_grid(const Launcher& L) { return L.num_sms * L.wf_blocks_per_sm; }
+
+// Brackets a stage launch for the caller's timing hook (kernel ids of ipt.h).
+struct StageMark {
+  const WfHook* hook;
+  StageMark(const WfHook* h, int id) : hook(h) {
+    if (hook && hook->begin) hook->begin(hook->user, id);
+  }
+  ~StageMark() {
+    if (hook && hook->end) hook->end(hook->user);
+  }
+};
+#define IPT_STAGE(id) StageMark stage_mark_(hook, id)
+
+int wf_max_blocks(const Launcher& L) { return wf_grid(L); }
+
+cudaError_t wf_forward(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
+                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
+                       const WfBuffers& wb, float* img, float* msq, const float* target, float* g_out,
+                       double* loss_partials, float g_scale, int loss_kind, uint32_t* err, cudaStream_t st,
+                       const WfHook* hook) {
+  const PathParams pp = make_path_params(tp, s);
+  const SceneDev sd = scene_dev(s);
+  const SegDev tt = seg_dev(t);
+  const ViewDev* vd = reinterpret_cast<const ViewDev*>(views_dev);
+  const WfDev w = wf_dev(wb);
+  const uint32_t pix_per_chunk = wb.cap / tp.spp;
+  if (pix_per_chunk == 0) return cudaErrorInvalidValue;
+  const int grid = wf_grid(L);
+  const int red_grid = loss_partials_capacity(L);  // every partial is written
+  int first = 1;
+  for (uint32_t c0 = 0; c0 < n_pix; c0 += pix_per_chunk) {
+    const uint32_t cp = n_pix - c0 < pix_per_chunk ? n_pix - c0 : pix_per_chunk;
+    const uint32_t pix0 = pix_begin + c0;
+    const uint32_t slots = cp * tp.spp;
+    {
+      IPT_STAGE(7);
+      wf_camera<<<grid, kWfThreads, 0, st>>>(vd, n_views, pix0, slots, pp, w);
+    }
+    int cur = 0;
+    for (uint32_t k = 0; k <= tp.max_depth; ++k) {
+      {
+        IPT_STAGE(8);
+        wf_trace<0><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+      }
+      {
+        IPT_STAGE(10);
+        wf_shade_fwd<<<grid, kWfThreads, 0, st>>>(sd, tt, pix0, pp, w, cur);
+      }
+      if (k < tp.max_depth && tp.nee) {
+        IPT_STAGE(9);
+        wf_trace<1><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+      }
+      cur ^= 1;
+    }
+    {
+      IPT_STAGE(14);
+      wf_reduce<<<red_grid, kWfThreads, 0, st>>>(w, pix0, cp, tp.spp, pix_begin, img, msq, target, g_out,
+                                                 loss_partials, first, g_scale, loss_kind);
+    }
+    first = 0;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t wf_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
+                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
+                       const WfBuffers& wb, const float* g_img, double* grad_acc, uint32_t* err,
+                       cudaStream_t st, const WfHook* hook) {
+  const PathParams pp = make_path_params(tp, s);
+  const SceneDev sd = scene_dev(s);
+  const SegDev tt = seg_dev(t);
+  const ViewDev* vd = reinterpret_cast<const ViewDev*>(views_dev);
+  const WfDev w = wf_dev(wb);
+  const uint32_t pix_per_chunk = wb.cap / tp.spp;
+  if (pix_per_chunk == 0 || !wb.aT) return cudaErrorInvalidValue;
+  const int grid = wf_grid(L);
+  const uint32_t np = 10u * s.n_seg;
+  const size_t shmem = np * sizeof(float);
+  if (shmem > 48 * 1024) {
+    cudaFuncSetAttribute(wf_adj_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    cudaFuncSetAttribute(wf_adj_connect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    cudaFuncSetAttribute(wf_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+  }
+  cudaError_t e = cudaMemsetAsync(wb.blk, 0, (size_t)grid * np * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  for (uint32_t c0 = 0; c0 < n_pix; c0 += pix_per_chunk) {
+    const uint32_t cp = n_pix - c0 < pix_per_chunk ? n_pix - c0 : pix_per_chunk;
+    const uint32_t pix0 = pix_begin + c0;
+    const uint32_t slots = cp * tp.spp;
+    {
+      IPT_STAGE(7);
+      wf_camera<<<grid, kWfThreads, 0, st>>>(vd, n_views, pix0, slots, pp, w);
+    }
+    int cur = 0;
+    for (uint32_t k = 0; k <= tp.max_depth; ++k) {
+      {
+        IPT_STAGE(8);
+        wf_trace<0><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+      }
+      {
+        IPT_STAGE(11);
+        wf_adj_a<<<grid, kWfThreads, shmem, st>>>(sd, tt, pix0, pix_begin, pp, w, cur, g_img);
+      }
+      if (k < tp.max_depth) {
+        if (tp.nee) {
+          {
+            IPT_STAGE(9);
+            wf_trace<2><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+          }
+          IPT_STAGE(12);
+          wf_adj_connect<<<grid, kWfThreads, shmem, st>>>(sd, tt, w);
+        }
+        IPT_STAGE(13);
+        wf_adj_b<<<grid, kWfThreads, shmem, st>>>(sd, tt, pix0, pix_begin, pp, w, cur, g_img);
+      }
+      cur ^= 1;
+    }
+  }
+  IPT_STAGE(14);
+  wf_blk_reduce<<<(np + 127) / 128, 128, 0, st>>>(wb.blk, grid, np, grad_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t wf_init(Launcher* L) {
+  int b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wf_trace<0>, kWfThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->wf_blocks_per_sm = b < 1 ? 1 : b;
+  return cudaSuccess;
+}
+
+}  // namespace ipt

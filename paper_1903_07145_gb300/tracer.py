@@ -192,6 +192,13 @@ class Tracer:
     def info(self):
         return L.ipt_scene_info(self.ctx, self.sid)
 
+    def configure(self, integrator="wavefront", wavefront_slots=0, trace_steps=0, blocks_per_sm=0):
+        L.ipt_config_set(self.ctx, 1 if integrator == "wavefront" else 0, wavefront_slots,
+                         trace_steps, blocks_per_sm)
+
+    def config(self):
+        return L.ipt_config_get(self.ctx)
+
     def kernel_times(self, reset=False):
         return L.ipt_kernel_times(self.ctx, reset)
 

@@ -46,6 +46,15 @@ def built():
     return True
 
 
+INTEGRATORS = ["megakernel", "wavefront"]
+
+
+def tracer(sc, seed, integrator="wavefront", **kw):
+    tr = Tracer(sc, seed=seed, **kw)
+    tr.configure(integrator)
+    return tr
+
+
 def perturbed(scene, seed=3, emission=0.15):
     """Parameters away from the initial guess: random materials, some
     emission on every segment (so light sampling covers many segments)."""
@@ -104,8 +113,8 @@ def test_ray_hits_match_oracle(built, which):
 
 # ---------------------------------------------------------------------------
 def render_both(sc, params, spp, D, seed_gpu, seed_ora, view=0, set_id=2, nee=True, mis=True, profile=0,
-                sparams=None):
-    tr = Tracer(sc, seed=seed_gpu)
+                sparams=None, integrator="wavefront"):
+    tr = tracer(sc, seed_gpu, integrator)
     tr.set_params(params)
     opts = TraceOptions(spp_r=spp, max_depth=D, nee=nee, mis=mis,
                         emission_profile="cosine" if profile == 0 else "uniform")
@@ -119,24 +128,29 @@ def render_both(sc, params, spp, D, seed_gpu, seed_ora, view=0, set_id=2, nee=Tr
     return img.cpu().numpy().astype(np.float64), msq.cpu().numpy().astype(np.float64), om, omsq
 
 
+@pytest.mark.parametrize("integrator", INTEGRATORS)
 @pytest.mark.parametrize("nee,mis,profile,D", [(True, True, 0, 3), (False, False, 0, 3),
                                                (True, False, 1, 2), (True, True, 0, 0),
                                                (True, True, 1, 6)])
-def test_image_same_key(built, nee, mis, profile, D):
+def test_image_same_key(built, nee, mis, profile, D, integrator):
     sc = scenes.cornell_box(1000, 64, 64)
     p = perturbed(sc)
-    g, _, o, _ = render_both(sc, p, 32, D, SEED, SEED, nee=nee, mis=mis, profile=profile)
+    g, _, o, _ = render_both(sc, p, 32, D, SEED, SEED, nee=nee, mis=mis, profile=profile,
+                             integrator=integrator)
     assert rel(g, o) <= 1e-3, rel(g, o)
 
 
-def test_image_same_key_ragged_spp_and_views(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_image_same_key_ragged_spp_and_views(built, integrator):
     """spp = 12 (3 samples per lane over 4 lanes), several views of
-    different sizes, with the whole-image (view = -1) render."""
+    different sizes, with the whole-image (view = -1) render; the wavefront
+    runs with chunks of 1024 slots, so chunks end inside views."""
     sc = scenes.indoor_room(11, n_cuboids=8, cuboid_sub=3, room_sub=4, n_lights=2, n_views=3,
                             width=37, height=23)
     sc.cameras[1] = scenes.Camera(sc.cameras[1].cam_to_world, 50.0, 19, 31)
     p = perturbed(sc)
     tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator, wavefront_slots=1024)
     tr.set_params(p)
     opts = TraceOptions(spp_r=12, max_depth=4)
     img = tr.render(opts, view=-1, set_id=2, spp=12).cpu().numpy()
@@ -185,8 +199,9 @@ def test_image_with_vertex_normals(built):
 
 
 # ---------------------------------------------------------------------------
-def backward_both(sc, p, spp, D, set_id=1, nee=True, mis=True, profile=0, pixels_mask=None, seed=SEED):
-    tr = Tracer(sc, seed=seed)
+def backward_both(sc, p, spp, D, set_id=1, nee=True, mis=True, profile=0, pixels_mask=None, seed=SEED,
+                  integrator="wavefront"):
+    tr = tracer(sc, seed, integrator)
     tr.set_params(p)
     rng = np.random.default_rng(9)
     w = rng.normal(size=(tr.n_pix, 3)).astype(np.float32)
@@ -211,17 +226,19 @@ def backward_both(sc, p, spp, D, set_id=1, nee=True, mis=True, profile=0, pixels
     return g, ref
 
 
+@pytest.mark.parametrize("integrator", INTEGRATORS)
 @pytest.mark.parametrize("nee,mis,profile,D", [(True, True, 0, 3), (False, False, 0, 3),
                                                (True, False, 1, 2), (True, True, 0, 6), (True, True, 0, 1)])
-def test_gradient_matches_oracle_cornell(built, nee, mis, profile, D):
+def test_gradient_matches_oracle_cornell(built, nee, mis, profile, D, integrator):
     sc = scenes.cornell_box(1000, 64, 64)
     p = perturbed(sc)
-    g, ref = backward_both(sc, p, 16, D, nee=nee, mis=mis, profile=profile)
+    g, ref = backward_both(sc, p, 16, D, nee=nee, mis=mis, profile=profile, integrator=integrator)
     assert cosine(g, ref) >= 0.999, cosine(g, ref)
     assert rel(g, ref) <= 1e-2, rel(g, ref)
 
 
-def test_gradient_matches_oracle_large_room_crop(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_gradient_matches_oracle_large_room_crop(built, integrator):
     """~516k triangles, 150 segments: a 64x48 crop of view 0 (the other
     pixels get a zero upstream gradient and are skipped)."""
     sc = scenes.room_500k()
@@ -231,17 +248,18 @@ def test_gradient_matches_oracle_large_room_crop(built):
     mask = np.zeros(sum(c.width * c.height for c in sc.cameras), bool)
     for y in range(200, 248):
         mask[y * W + 300: y * W + 364] = True
-    g, ref = backward_both(sc, p, 16, 6, pixels_mask=mask)
+    g, ref = backward_both(sc, p, 16, 6, pixels_mask=mask, integrator=integrator)
     assert cosine(g, ref) >= 0.999, cosine(g, ref)
     assert rel(g, ref) <= 1e-2, rel(g, ref)
 
 
-def test_gradient_central_differences(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_gradient_central_differences(built, integrator):
     """<w, I(p+h e_k) - I(p-h e_k)>/2h against J^T w on 20 random parameters,
     same sample set on both sides and sampling frozen at p (h = 1e-3)."""
     sc = scenes.cornell_box(1000, 32, 32)
     p = perturbed(sc)
-    tr = Tracer(sc, seed=SEED)
+    tr = tracer(sc, SEED, integrator)
     tr.set_params(p)
     opts = TraceOptions(spp_r=16, spp_d=16, max_depth=3, gradcheck_same_set=True)
     rng = np.random.default_rng(4)
@@ -277,12 +295,13 @@ def test_autograd_function(built):
 
 
 # ---------------------------------------------------------------------------
-def test_loss_grad_and_adam_match_oracle(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_loss_grad_and_adam_match_oracle(built, integrator):
     sc = scenes.cornell_box(1000, 32, 32)
     gt = sc.gt_params
     osc = O.OracleScene(sc)
     target, _ = osc.render(gt, spp=64, max_depth=3, set_id=2, seed=77)
-    tr = Tracer(sc, seed=SEED)
+    tr = tracer(sc, SEED, integrator)
     p0 = scenes.initial_params(sc, 0.5)
     tr.set_params(p0)
     tr.set_targets(torch.from_numpy(target.astype(np.float32)).cuda())
@@ -301,13 +320,14 @@ def test_loss_grad_and_adam_match_oracle(built):
     assert np.max(np.abs(newp - ref)) < 1e-6
 
 
-def test_full_size_room_sampled_pixels(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_full_size_room_sampled_pixels(built, integrator):
     """The 61k-triangle room at its benchmark size (8 views of 320x240, 32
     spp, depth 5): 24 pixels sampled across the views, recomputed one by one
     by the oracle with the same key."""
     sc = scenes.room_60k()
     p = perturbed(sc, emission=0.02)
-    tr = Tracer(sc, seed=SEED)
+    tr = tracer(sc, SEED, integrator)
     tr.set_params(p)
     opts = TraceOptions(spp_r=32, max_depth=5)
     img = tr.render(opts, view=-1, set_id=0, spp=32).cpu().numpy()
@@ -324,11 +344,12 @@ def test_full_size_room_sampled_pixels(built):
     assert rel(got, ref) <= 1e-3, rel(got, ref)
 
 
-def test_full_size_large_room_sampled_pixels(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_full_size_large_room_sampled_pixels(built, integrator):
     """~516k triangles, 16 views of 640x480, 16 spp, depth 6: 16 sampled pixels."""
     sc = scenes.room_500k()
     p = perturbed(sc, emission=0.02)
-    tr = Tracer(sc, seed=SEED)
+    tr = tracer(sc, SEED, integrator)
     tr.set_params(p)
     opts = TraceOptions(spp_r=16, max_depth=6)
     img = tr.render(opts, view=-1, set_id=0, spp=16).cpu().numpy()
@@ -396,7 +417,8 @@ def test_invalid_arguments_rejected(built):
     tr.synchronize()
 
 
-def test_loss_grad_shards_add_up(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_loss_grad_shards_add_up(built, integrator):
     """ipt_loss_grad_shard over 3 pixel ranges sums to ipt_loss_grad (the
     random numbers are keyed by global pixel id, so each pixel's samples are
     the same whichever shard traces them)."""
@@ -404,7 +426,7 @@ def test_loss_grad_shards_add_up(built):
     sc = scenes.cornell_box(1000, 32, 32)
     osc = O.OracleScene(sc)
     target, _ = osc.render(sc.gt_params, spp=16, max_depth=3, set_id=2, seed=5)
-    tr = Tracer(sc, seed=SEED)
+    tr = tracer(sc, SEED, integrator)
     tr.set_params(scenes.initial_params(sc, 0.5))
     tr.set_targets(torch.from_numpy(target.astype(np.float32)).cuda())
     opts = TraceOptions(spp_r=8, spp_d=8, max_depth=3)
@@ -420,3 +442,25 @@ def test_loss_grad_shards_add_up(built):
     assert rel(tot_g.cpu().numpy(), grad.cpu().numpy()) <= 1e-5
     with pytest.raises(_lib.IptError):
         tr.loss_grad_shard(opts, 3, n - 1, 2, n)
+
+
+@pytest.mark.parametrize("spp,slots", [(32, 1 << 20), (12, 4096), (1, 1024)])
+def test_wavefront_equals_megakernel(built, spp, slots):
+    """Both integrators draw the same numbers at the same slots: images agree
+    to float rounding, gradients to the order of the float sums."""
+    sc = scenes.indoor_room(13, n_cuboids=10, cuboid_sub=3, room_sub=4, n_lights=3, n_views=2,
+                            width=40, height=30)
+    p = perturbed(sc, emission=0.05)
+    out = {}
+    for integ in INTEGRATORS:
+        tr = Tracer(sc, seed=SEED)
+        tr.configure(integ, wavefront_slots=slots)
+        tr.set_params(p)
+        opts = TraceOptions(spp_r=spp, spp_d=spp, max_depth=5)
+        img = tr.render(opts, set_id=0, spp=spp).cpu().numpy()
+        w = torch.from_numpy(np.random.default_rng(1).normal(size=(tr.n_pix, 3)).astype(np.float32)).cuda()
+        g = tr.backward(w, opts, set_id=1).cpu().numpy()
+        out[integ] = (img, g)
+        tr.close()
+    assert rel(out["wavefront"][0], out["megakernel"][0]) <= 1e-5
+    assert rel(out["wavefront"][1], out["megakernel"][1]) <= 1e-4
