@@ -228,7 +228,7 @@ def run_ours(args, rank, world, local):
     # algorithmic traffic of the dominant kernel: node and triangle fetches per
     # launch, counted by a separate context with counters (same seeds, same paths)
     ct = Tracer(sc, device=local, seed=1903 + rank, flags=L.IPT_FLAG_COUNTERS)
-    ct.configure(**{**chosen, "integrator": "wavefront" if chosen["integrator"] == 1 else "megakernel"})
+    ct.configure(**chosen)
     ct.set_targets(target)
     ct.set_params(scenes.initial_params(sc, w["init"]))
     ct.counters(reset=True)

@@ -87,8 +87,8 @@ typedef struct {
 } ipt_options;
 
 /* Integrator configuration of a context (picked per workload by the autotuner
- * in paper_1903_07145_gb300/autotune.py; both integrators trace identical
- * paths).
+ * in paper_1903_07145_gb300/autotune.py; every configuration traces
+ * identical paths).
  *   integrator: 0 = megakernel (one thread per path, every stage inline),
  *     1 = wavefront (chunks of path slots; persistent traversal kernels over
  *     compacted ray queues).
@@ -97,12 +97,15 @@ typedef struct {
  *   trace_steps: node visits per refill round of the persistent traversal
  *     (0 = 32).
  *   blocks_per_sm: persistent blocks per SM for the wavefront kernels (0 =
- *     as many as fit). */
+ *     as many as fit).
+ *   bvh_width: BVH used by the wavefront traversal: 2 = binary nodes with
+ *     float boxes, 4 = 4-wide nodes with 8-bit child boxes (0 = 4). */
 typedef struct {
   int32_t integrator;
   uint32_t wavefront_slots;
   uint32_t trace_steps;
   uint32_t blocks_per_sm;
+  uint32_t bvh_width;
 } ipt_config;
 
 /* Pinhole camera.  cam_to_world is row-major 3x4; its columns are the

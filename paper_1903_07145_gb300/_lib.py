@@ -50,7 +50,8 @@ class ipt_camera(C.Structure):
 
 class ipt_config(C.Structure):
     _fields_ = [("integrator", C.c_int32), ("wavefront_slots", C.c_uint32),
-                ("trace_steps", C.c_uint32), ("blocks_per_sm", C.c_uint32)]
+                ("trace_steps", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("bvh_width", C.c_uint32)]
 
 
 class ipt_trace_opts(C.Structure):
@@ -239,8 +240,8 @@ def ipt_loss_grad_shard(ctx, scene, opts, iteration, pix_begin, pix_count, n_tot
     return loss.value
 
 
-def ipt_config_set(ctx, integrator=1, wavefront_slots=0, trace_steps=0, blocks_per_sm=0):
-    c = ipt_config(integrator, wavefront_slots, trace_steps, blocks_per_sm)
+def ipt_config_set(ctx, integrator=1, wavefront_slots=0, trace_steps=0, blocks_per_sm=0, bvh_width=0):
+    c = ipt_config(integrator, wavefront_slots, trace_steps, blocks_per_sm, bvh_width)
     _check(ctx, lib().ipt_config_set(ctx, C.byref(c)))
 
 
@@ -248,4 +249,4 @@ def ipt_config_get(ctx):
     c = ipt_config()
     _check(ctx, lib().ipt_config_get(ctx, C.byref(c)))
     return dict(integrator=c.integrator, wavefront_slots=c.wavefront_slots,
-                trace_steps=c.trace_steps, blocks_per_sm=c.blocks_per_sm)
+                trace_steps=c.trace_steps, blocks_per_sm=c.blocks_per_sm, bvh_width=c.bvh_width)

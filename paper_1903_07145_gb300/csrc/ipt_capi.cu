@@ -24,6 +24,7 @@ struct DeviceScene {
   float eps = 0.f, emission_scale = 1.f;
   // geometry
   float4* nodes = nullptr;
+  uint4* nodes4 = nullptr;
   float4* tris = nullptr;
   float4* vnrm = nullptr;
   uint32_t* seg_tris = nullptr;
@@ -80,7 +81,7 @@ struct ipt_ctx {
   std::vector<cudaEvent_t> spare_events;
   double kernel_ms[IPT_KERNEL_COUNT] = {0};
   uint64_t kernel_n[IPT_KERNEL_COUNT] = {0};
-  ipt_config cfg = {1, 1u << 20, 32, 0};
+  ipt_config cfg = {1, 1u << 20, 32, 0, 4};
   ipt::WfBuffers wf;
   std::vector<void*> wf_owned;
   bool wf_adjoint = false;
@@ -197,7 +198,9 @@ void stage_end(void* user) {
 ipt::SceneBuffers buffers(const ipt_ctx* ctx, const DeviceScene* s) {
   ipt::SceneBuffers b;
   b.counters = ctx->counters_dev;
+  b.wide = ctx->cfg.bvh_width != 2 ? 1 : 0;
   b.nodes = s->nodes;
+  b.nodes4 = s->nodes4;
   b.tris = s->tris;
   b.vnrm = s->vnrm;
   b.seg_tris = s->seg_tris;
@@ -457,6 +460,7 @@ ipt_status ipt_scene_upload(ipt_ctx* ctx, const float* pos, uint32_t n_vert, con
     if (e == cudaSuccess) e = dev_alloc(s, p, n);
   };
   A(&s->nodes, 4 * (size_t)hs.n_nodes);
+  A(&s->nodes4, 4 * (size_t)hs.n_nodes4);
   A(&s->tris, 3 * (size_t)n_tri);
   if (!hs.vnrm.empty()) A(&s->vnrm, 3 * (size_t)n_tri);
   A(&s->seg_tris, n_tri);
@@ -485,6 +489,7 @@ ipt_status ipt_scene_upload(ipt_ctx* ctx, const float* pos, uint32_t n_vert, con
     if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
   };
   H(s->nodes, hs.nodes.data(), hs.nodes.size() * sizeof(float));
+  H(s->nodes4, hs.nodes4.data(), hs.nodes4.size() * sizeof(uint32_t));
   H(s->tris, hs.tris.data(), hs.tris.size() * sizeof(float));
   if (s->vnrm) H(s->vnrm, hs.vnrm.data(), hs.vnrm.size() * sizeof(float));
   H(s->seg_tris, hs.seg_tris.data(), hs.seg_tris.size() * sizeof(uint32_t));
@@ -803,6 +808,8 @@ ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg) {
   if (cfg->wavefront_slots && cfg->wavefront_slots < 1024)
     return fail(ctx, IPT_ERR_INVALID_ARG, "wavefront_slots must be 0 or at least 1024");
   if (cfg->trace_steps > 4096) return fail(ctx, IPT_ERR_INVALID_ARG, "trace_steps above 4096");
+  if (cfg->bvh_width != 0 && cfg->bvh_width != 2 && cfg->bvh_width != 4)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "bvh_width must be 0, 2 or 4");
   IPT_CK(cudaSetDevice(ctx->device));
   const uint32_t old_cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
   const uint32_t new_cap = cfg->wavefront_slots ? cfg->wavefront_slots : (1u << 20);

@@ -77,6 +77,7 @@ struct PathRng {
 // ---------------------------------------------------------------------------
 struct SceneDev {
   const float4* nodes;
+  const uint4* nodes4;  // 4-wide quantized nodes (4 x uint4 each), or nullptr
   const float4* tris;
   const float4* vnrm;
   const uint32_t* seg_tris;
@@ -87,6 +88,7 @@ struct SceneDev {
   uint32_t n_tri;
   float eps;  // spawn offset along the oriented geometric normal
   unsigned long long* counters;  // optional: closest rays, shadow rays, node visits, triangle tests
+  int wide;   // traverse the 4-wide quantized BVH
 };
 
 // kind 0: closest-hit ray, 1: shadow ray
@@ -215,11 +217,72 @@ __device__ __forceinline__ void box2(const RayPre& r, float3 oinv, float4 n0, fl
   t1 = bn <= bf ? bn : __int_as_float(0x7f800000);
 }
 
+// ---------------------------------------------------------------------------
+// 4-wide node with 8-bit child boxes (see the scene builder): entry distances
+// of its children (or +inf), and their links.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float q_byte(uint32_t w, int i) {
+  // byte i of w as a float, via the 2^23 mantissa trick (exact)
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)i)) - 8388608.0f;
+}
+
+__device__ __forceinline__ uint32_t node4_children(const SceneDev& s, int node, const RayPre& r, float tmax,
+                                                   float tn[4], int ref[4]) {
+  const uint4 a = __ldg(&s.nodes4[4 * node + 0]);
+  const uint4 c = __ldg(&s.nodes4[4 * node + 1]);
+  const uint4 qa = __ldg(&s.nodes4[4 * node + 2]);
+  const uint4 qb = __ldg(&s.nodes4[4 * node + 3]);
+  const float sx = __uint_as_float((a.w & 0xffu) << 23);
+  const float sy = __uint_as_float(((a.w >> 8) & 0xffu) << 23);
+  const float sz = __uint_as_float(((a.w >> 16) & 0xffu) << 23);
+  const int n = (int)(a.w >> 24);
+  const float ax = sx * r.inv.x, bx = (__uint_as_float(a.x) - r.o.x) * r.inv.x;
+  const float ay = sy * r.inv.y, by = (__uint_as_float(a.y) - r.o.y) * r.inv.y;
+  const float az = sz * r.inv.z, bz = (__uint_as_float(a.z) - r.o.z) * r.inv.z;
+  ref[0] = (int)c.x;
+  ref[1] = (int)c.y;
+  ref[2] = (int)c.z;
+  ref[3] = (int)c.w;
+  uint32_t mask = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float tlx = fmaf(q_byte(qa.x, i), ax, bx), thx = fmaf(q_byte(qa.y, i), ax, bx);
+    const float tly = fmaf(q_byte(qa.z, i), ay, by), thy = fmaf(q_byte(qa.w, i), ay, by);
+    const float tlz = fmaf(q_byte(qb.x, i), az, bz), thz = fmaf(q_byte(qb.y, i), az, bz);
+    const float tnear = fmaxf(fmaxf(fminf(tlx, thx), fminf(tly, thy)), fmaxf(fminf(tlz, thz), 0.0f));
+    const float tfar =
+        fminf(fminf(fmaxf(tlx, thx), fmaxf(tly, thy)), fminf(fmaxf(tlz, thz), tmax)) * 1.0000005f;
+    const bool hit = i < n && tnear <= tfar;
+    tn[i] = hit ? tnear : __int_as_float(0x7f800000);
+    mask |= hit ? (1u << i) : 0u;
+  }
+  return mask;
+}
+
+// Sorts four (distance, link) pairs by distance (misses carry +inf).
+__device__ __forceinline__ void sort4(float t[4], int r[4]) {
+#define IPT_CSWAP(i, j)                 \
+  if (t[j] < t[i]) {                    \
+    const float tt = t[i];              \
+    t[i] = t[j];                        \
+    t[j] = tt;                          \
+    const int rr = r[i];                \
+    r[i] = r[j];                        \
+    r[j] = rr;                          \
+  }
+  IPT_CSWAP(0, 1)
+  IPT_CSWAP(2, 3)
+  IPT_CSWAP(0, 2)
+  IPT_CSWAP(1, 3)
+  IPT_CSWAP(1, 2)
+#undef IPT_CSWAP
+}
+
 // Closest hit in (0, tmax), skipping one internal triangle id; equal t keeps
 // the smaller original id.  On stack overflow the ray reports a miss and the
 // error word is set.
-__device__ __forceinline__ Hit trace_closest(const SceneDev& s, float3 o, float3 d, float tmax, int skip,
-                                             uint32_t* err) {
+__device__ __forceinline__ Hit trace_closest2(const SceneDev& s, float3 o, float3 d, float tmax, int skip,
+                                              uint32_t* err) {
   const RayPre r = ray_pre(o, d);
   const float3 oinv = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
   Hit h;
@@ -292,8 +355,8 @@ __device__ __forceinline__ Hit trace_closest(const SceneDev& s, float3 o, float3
 }
 
 // Any hit in (0, tmax), skipping two internal triangle ids.
-__device__ __forceinline__ bool trace_any(const SceneDev& s, float3 o, float3 d, float tmax, int skip_a,
-                                          int skip_b, uint32_t* err) {
+__device__ __forceinline__ bool trace_any2(const SceneDev& s, float3 o, float3 d, float tmax, int skip_a,
+                                           int skip_b, uint32_t* err) {
   const RayPre r = ray_pre(o, d);
   const float3 oinv = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
   int stack[kStackSize];
@@ -346,6 +409,147 @@ __device__ __forceinline__ bool trace_any(const SceneDev& s, float3 o, float3 d,
   }
   count_ray(s, 1, n_nodes, n_tests);
   return false;
+}
+
+// The same two queries over the 4-wide quantized BVH.
+__device__ __forceinline__ Hit trace_closest4(const SceneDev& s, float3 o, float3 d, float tmax, int skip,
+                                              uint32_t* err) {
+  const RayPre r = ray_pre(o, d);
+  Hit h;
+  h.tri = -1;
+  h.t = tmax;
+  h.u = h.v = 0.0f;
+  int best_orig = 0x7fffffff;
+  int stack[kStackSize];
+  float stack_t[kStackSize];
+  int sp = 0;
+  int node = 0;
+  uint32_t n_nodes = 0, n_tests = 0;
+  for (;;) {
+    if (node >= 0) {
+      ++n_nodes;
+      float tn[4];
+      int ref[4];
+      const uint32_t mask = node4_children(s, node, r, h.t, tn, ref);
+      const int k = __popc(mask);
+      if (k > 0) {
+        if (sp + k - 1 > kStackSize) {
+          atomicOr(err, kErrStack);
+          h.tri = -1;
+          return h;
+        }
+        sort4(tn, ref);
+#pragma unroll
+        for (int i = 3; i >= 1; --i)
+          if (i < k) {
+            stack[sp] = ref[i];
+            stack_t[sp] = tn[i];
+            ++sp;
+          }
+        node = ref[0];
+        continue;
+      }
+    } else {
+      int first, count;
+      decode_leaf(node, first, count);
+      n_tests += count;
+      for (int i = first; i < first + count; ++i) {
+        if (i == skip) continue;
+        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+        float t, u, v;
+        if (tri_test(r, xyz(q0), xyz(q1), xyz(q2), h.t * 1.0000002f, t, u, v)) {
+          const int orig = __float_as_int(q0.w);
+          if (t < h.t || (t == h.t && orig < best_orig)) {
+            h.tri = i;
+            h.t = t;
+            h.u = u;
+            h.v = v;
+            best_orig = orig;
+          }
+        }
+      }
+    }
+    bool done = false;
+    for (;;) {
+      if (sp == 0) {
+        done = true;
+        break;
+      }
+      --sp;
+      if (stack_t[sp] <= h.t * 1.0000005f) break;
+    }
+    if (done) break;
+    node = stack[sp];
+  }
+  count_ray(s, 0, n_nodes, n_tests);
+  return h;
+}
+
+__device__ __forceinline__ bool trace_any4(const SceneDev& s, float3 o, float3 d, float tmax, int skip_a,
+                                           int skip_b, uint32_t* err) {
+  const RayPre r = ray_pre(o, d);
+  int stack[kStackSize];
+  int sp = 0;
+  int node = 0;
+  uint32_t n_nodes = 0, n_tests = 0;
+  for (;;) {
+    if (node >= 0) {
+      ++n_nodes;
+      float tn[4];
+      int ref[4];
+      const uint32_t mask = node4_children(s, node, r, tmax, tn, ref);
+      const int k = __popc(mask);
+      if (k > 0) {
+        if (sp + k - 1 > kStackSize) {
+          atomicOr(err, kErrStack);
+          return true;
+        }
+        const int first = __ffs(mask) - 1;
+        int next = ref[0];
+#pragma unroll
+        for (int i = 3; i >= 0; --i) {
+          if (!(mask & (1u << i))) continue;
+          if (i == first)
+            next = ref[i];
+          else
+            stack[sp++] = ref[i];
+        }
+        node = next;
+        continue;
+      }
+    } else {
+      int first, count;
+      decode_leaf(node, first, count);
+      n_tests += count;
+      for (int i = first; i < first + count; ++i) {
+        if (i == skip_a || i == skip_b) continue;
+        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+        float t, u, v;
+        if (tri_test(r, xyz(q0), xyz(q1), xyz(q2), tmax, t, u, v)) {
+          count_ray(s, 1, n_nodes, n_tests);
+          return true;
+        }
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  count_ray(s, 1, n_nodes, n_tests);
+  return false;
+}
+
+__device__ __forceinline__ Hit trace_closest(const SceneDev& s, float3 o, float3 d, float tmax, int skip,
+                                             uint32_t* err) {
+  return s.wide ? trace_closest4(s, o, d, tmax, skip, err) : trace_closest2(s, o, d, tmax, skip, err);
+}
+
+__device__ __forceinline__ bool trace_any(const SceneDev& s, float3 o, float3 d, float tmax, int skip_a,
+                                          int skip_b, uint32_t* err) {
+  return s.wide ? trace_any4(s, o, d, tmax, skip_a, skip_b, err) : trace_any2(s, o, d, tmax, skip_a, skip_b, err);
 }
 
 // ---------------------------------------------------------------------------

@@ -13,6 +13,8 @@ namespace ipt {
 struct HostScene {
   uint32_t n_tri = 0, n_seg = 0, n_nodes = 0, depth = 0;
   std::vector<float> nodes;      // 16 floats per inner node
+  std::vector<uint32_t> nodes4;  // 16 words per 4-wide quantized node
+  uint32_t n_nodes4 = 0;
   std::vector<float> tris;       // 12 floats per triangle (leaf order)
   std::vector<float> vnrm;       // 12 floats per triangle, empty if no normals
   std::vector<uint32_t> orig_to_internal;
@@ -31,6 +33,7 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
 // Device pointers of one scene, passed to the launchers.
 struct SceneBuffers {
   const float4* nodes;
+  const uint4* nodes4;
   const float4* tris;
   const float4* vnrm;
   const uint32_t* seg_tris;
@@ -42,6 +45,7 @@ struct SceneBuffers {
   float eps;
   float emission_scale;
   unsigned long long* counters;  // nullptr unless counting
+  int wide;                      // traverse the 4-wide quantized BVH
 };
 
 // Per-segment parameter tables (device).

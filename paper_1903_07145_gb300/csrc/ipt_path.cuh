@@ -47,6 +47,7 @@ inline PathParams make_path_params(const TraceParams& tp, const SceneBuffers& s)
 inline SceneDev scene_dev(const SceneBuffers& s) {
   SceneDev d;
   d.nodes = s.nodes;
+  d.nodes4 = s.nodes4;
   d.tris = s.tris;
   d.vnrm = s.vnrm;
   d.seg_tris = s.seg_tris;
@@ -57,6 +58,7 @@ inline SceneDev scene_dev(const SceneBuffers& s) {
   d.n_tri = s.n_tri;
   d.eps = s.eps;
   d.counters = s.counters;
+  d.wide = s.wide;
   return d;
 }
 

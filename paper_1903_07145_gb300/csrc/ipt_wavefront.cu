@@ -114,6 +114,7 @@ struct Trav {
   int skip_a, skip_b;
   int node, sp;
   int stack[kStackSize];
+  float stack_t[kStackSize];  // entry distance of each pushed child (4-wide)
   int best, best_orig;
   float bt, bu, bv;
   bool occluded;
@@ -204,7 +205,91 @@ __device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, int steps, 
   return false;
 }
 
-template <int kMode>
+// Same contract over 4-wide quantized nodes: the hit children are visited
+// nearest first (any-hit: in slot order), and popped entries farther than
+// the current hit are skipped.
+template <bool kAny>
+__device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps, uint32_t* err) {
+  for (int it = 0; it < steps; ++it) {
+    if (T.node >= 0) {
+      ++T.n_nodes;
+      float tn[4];
+      int ref[4];
+      const uint32_t mask = node4_children(s, T.node, T.r, kAny ? T.tmax : T.bt, tn, ref);
+      const int k = __popc(mask);
+      if (k > 0) {
+        if (T.sp + k - 1 > kStackSize) {
+          atomicOr(err, kErrStack);
+          T.best = -1;
+          T.occluded = true;
+          return true;
+        }
+        if (!kAny) {
+          // nearest first: misses sort to the back (+inf)
+          sort4(tn, ref);
+#pragma unroll
+          for (int i = 3; i >= 1; --i)
+            if (i < k) {
+              T.stack[T.sp] = ref[i];
+              T.stack_t[T.sp] = tn[i];
+              ++T.sp;
+            }
+          T.node = ref[0];
+        } else {
+          // slot order: descend into the lowest hit slot, push the others
+          const int first = __ffs(mask) - 1;
+          int next = ref[0];
+#pragma unroll
+          for (int i = 3; i >= 0; --i) {
+            if (!(mask & (1u << i))) continue;
+            if (i == first)
+              next = ref[i];
+            else
+              T.stack[T.sp++] = ref[i];
+          }
+          T.node = next;
+        }
+        continue;
+      }
+    } else {
+      int first, count;
+      decode_leaf(T.node, first, count);
+      T.n_tests += count;
+      for (int i = first; i < first + count; ++i) {
+        if (i == T.skip_a || i == T.skip_b) continue;
+        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+        float t, u, v;
+        if (kAny) {
+          if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.tmax, t, u, v)) {
+            T.occluded = true;
+            return true;
+          }
+        } else if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.bt * 1.0000002f, t, u, v)) {
+          const int orig = __float_as_int(q0.w);
+          if (t < T.bt || (t == T.bt && orig < T.best_orig)) {
+            T.best = i;
+            T.bt = t;
+            T.bu = u;
+            T.bv = v;
+            T.best_orig = orig;
+          }
+        }
+      }
+    }
+    // pop, skipping entries that start beyond the current closest hit
+    for (;;) {
+      if (T.sp == 0) return true;
+      --T.sp;
+      if (kAny || T.stack_t[T.sp] <= T.bt * 1.0000005f) break;
+    }
+    T.node = T.stack[T.sp];
+  }
+  return false;
+}
+
+template <int kMode, bool kWide>
 __global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int cur, int steps, uint32_t* err) {
   constexpr bool kAny = kMode != 0;
   if (!kAny && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -245,7 +330,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int 
       }
     }
     if (__all_sync(0xffffffffu, item < 0)) break;
-    if (item >= 0 && trav_run<kAny>(s, T, steps, err)) {
+    if (item >= 0 && (kWide ? trav_run4<kAny>(s, T, steps, err) : trav_run<kAny>(s, T, steps, err))) {
       const uint32_t i = (uint32_t)item;
       count_ray(s, kAny ? 1 : 0, T.n_nodes, T.n_tests);
       if (kMode == 0) {
@@ -739,7 +824,8 @@ cudaError_t wf_forward(const Launcher& L, const SceneBuffers& s, const SegBuffer
     for (uint32_t k = 0; k <= tp.max_depth; ++k) {
       {
         IPT_STAGE(8);
-        wf_trace<0><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        if (s.wide) wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        else wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
       }
       {
         IPT_STAGE(10);
@@ -747,7 +833,8 @@ cudaError_t wf_forward(const Launcher& L, const SceneBuffers& s, const SegBuffer
       }
       if (k < tp.max_depth && tp.nee) {
         IPT_STAGE(9);
-        wf_trace<1><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        if (s.wide) wf_trace<1, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        else wf_trace<1, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
       }
       cur ^= 1;
     }
@@ -794,7 +881,8 @@ cudaError_t wf_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffer
     for (uint32_t k = 0; k <= tp.max_depth; ++k) {
       {
         IPT_STAGE(8);
-        wf_trace<0><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        if (s.wide) wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        else wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
       }
       {
         IPT_STAGE(11);
@@ -804,7 +892,8 @@ cudaError_t wf_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffer
         if (tp.nee) {
           {
             IPT_STAGE(9);
-            wf_trace<2><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+            if (s.wide) wf_trace<2, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+            else wf_trace<2, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
           }
           IPT_STAGE(12);
           wf_adj_connect<<<grid, kWfThreads, shmem, st>>>(sd, tt, w);
@@ -822,7 +911,7 @@ cudaError_t wf_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffer
 
 cudaError_t wf_init(Launcher* L) {
   int b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wf_trace<0>, kWfThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wf_trace<0, true>, kWfThreads, 0);
   if (e != cudaSuccess) return e;
   L->wf_blocks_per_sm = b < 1 ? 1 : b;
   return cudaSuccess;

@@ -174,6 +174,55 @@ struct Builder {
   }
 };
 
+// 4-wide node with 8-bit child boxes (64 bytes, 16 words):
+//   w0..w2: origin p (float bits); w3: exponents ex | ey << 8 | ez << 16 |
+//   child count << 24; w4..w7: child links (inner node index, or a leaf code
+//   as in the binary layout); w8: lo.x of children 0..3 (one byte each),
+//   w9: hi.x, w10: lo.y, w11: hi.y, w12: lo.z, w13: hi.z; w14, w15 unused.
+// A child box is p + q * 2^(e - 127) per axis, rounded outward so that it
+// contains the child's (padded) box in float arithmetic.
+struct Quantizer {
+  float p;
+  int e;  // biased exponent of the scale
+  float scale() const {
+    uint32_t bits = (uint32_t)e << 23;
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return f;
+  }
+};
+
+Quantizer make_axis(double lo, double hi) {
+  Quantizer q;
+  q.p = std::nextafter((float)lo, -INFINITY);
+  const double ext = std::max(hi - (double)q.p, 1e-30);
+  int e2 = (int)std::ceil(std::log2(ext / 255.0));
+  // the largest code (255) must reach past hi
+  for (;;) {
+    const double s = std::ldexp(1.0, e2);
+    if ((double)q.p + 255.0 * s >= hi) break;
+    ++e2;
+  }
+  q.e = std::min(std::max(e2 + 127, 1), 254);
+  return q;
+}
+
+uint32_t q_lo(const Quantizer& a, double lo) {
+  const float s = a.scale();
+  int q = (int)std::floor((lo - (double)a.p) / (double)s);
+  q = std::min(std::max(q, 0), 255);
+  while (q > 0 && (double)(a.p + (float)q * s) > lo) --q;
+  return (uint32_t)q;
+}
+
+uint32_t q_hi(const Quantizer& a, double hi) {
+  const float s = a.scale();
+  int q = (int)std::ceil((hi - (double)a.p) / (double)s);
+  q = std::min(std::max(q, 0), 255);
+  while (q < 255 && (double)(a.p + (float)q * s) < hi) ++q;
+  return (uint32_t)q;
+}
+
 inline float down(double x) { return std::nextafter((float)x, -INFINITY); }
 inline float up(double x) { return std::nextafter((float)x, INFINITY); }
 inline float bits_f(uint32_t v) {
@@ -311,6 +360,84 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
       std::memcpy(&q[12], &ca, 4);
       std::memcpy(&q[13], &cc, 4);
     }
+  }
+  // 4-wide quantized nodes: open the largest-area inner child until four
+  // children, depth first (a node precedes its subtree)
+  {
+    std::vector<uint32_t>& out = s.nodes4;
+    out.clear();
+    struct Item {
+      int bnode;
+      uint32_t slot;
+    };
+    std::vector<Item> work;
+    auto alloc = [&]() {
+      out.resize(out.size() + 16, 0u);
+      return (uint32_t)(out.size() / 16 - 1);
+    };
+    work.push_back({0, alloc()});
+    while (!work.empty()) {
+      const Item it = work.back();
+      work.pop_back();
+      std::vector<int> ch;
+      const BNode& root = B.nodes[it.bnode];
+      if (root.left < 0) {
+        ch.push_back(it.bnode);  // a leaf as the only child (single-leaf scene)
+      } else {
+        ch = {root.left, root.right};
+        while (ch.size() < 4) {
+          int best = -1;
+          double best_area = -1.0;
+          for (size_t i = 0; i < ch.size(); ++i) {
+            const BNode& c = B.nodes[ch[i]];
+            if (c.left >= 0 && c.box.area() > best_area) {
+              best_area = c.box.area();
+              best = (int)i;
+            }
+          }
+          if (best < 0) break;
+          const BNode& c = B.nodes[ch[best]];
+          const int l = c.left, r = c.right;
+          ch[best] = l;
+          ch.push_back(r);
+        }
+      }
+      Box u;
+      u.reset();
+      std::vector<Box> cb(ch.size());
+      for (size_t i = 0; i < ch.size(); ++i) {
+        cb[i] = B.nodes[ch[i]].box;
+        for (int k = 0; k < 3; ++k) {
+          cb[i].lo[k] -= pad;
+          cb[i].hi[k] += pad;
+        }
+        u.grow(cb[i]);
+      }
+      Quantizer qa[3];
+      for (int k = 0; k < 3; ++k) qa[k] = make_axis(u.lo[k], u.hi[k]);
+      uint32_t w[16] = {0};
+      for (int k = 0; k < 3; ++k) std::memcpy(&w[k], &qa[k].p, 4);
+      w[3] = (uint32_t)qa[0].e | ((uint32_t)qa[1].e << 8) | ((uint32_t)qa[2].e << 16) |
+             ((uint32_t)ch.size() << 24);
+      for (size_t i = 0; i < ch.size(); ++i) {
+        const BNode& c = B.nodes[ch[i]];
+        int ref;
+        if (c.left < 0) {
+          ref = leaf_code(c);
+        } else {
+          const uint32_t slot = alloc();
+          ref = (int)slot;
+          work.push_back({ch[i], slot});
+        }
+        std::memcpy(&w[4 + i], &ref, 4);
+        for (int k = 0; k < 3; ++k) {
+          w[8 + 2 * k] |= q_lo(qa[k], cb[i].lo[k]) << (8 * i);
+          w[9 + 2 * k] |= q_hi(qa[k], cb[i].hi[k]) << (8 * i);
+        }
+      }
+      std::memcpy(&out[16 * (size_t)it.slot], w, sizeof(w));
+    }
+    s.n_nodes4 = (uint32_t)(out.size() / 16);
   }
   // triangles in leaf order
   s.tris.assign(12 * (size_t)n_tri, 0.0f);

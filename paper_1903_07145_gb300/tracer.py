@@ -192,9 +192,12 @@ class Tracer:
     def info(self):
         return L.ipt_scene_info(self.ctx, self.sid)
 
-    def configure(self, integrator="wavefront", wavefront_slots=0, trace_steps=0, blocks_per_sm=0):
+    def configure(self, integrator="wavefront", wavefront_slots=0, trace_steps=0, blocks_per_sm=0,
+                  bvh_width=0):
+        if isinstance(integrator, int):
+            integrator = "wavefront" if integrator == 1 else "megakernel"
         L.ipt_config_set(self.ctx, 1 if integrator == "wavefront" else 0, wavefront_slots,
-                         trace_steps, blocks_per_sm)
+                         trace_steps, blocks_per_sm, bvh_width)
 
     def config(self):
         return L.ipt_config_get(self.ctx)

@@ -82,16 +82,21 @@ def test_philox_bit_exact(built):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("which", ["cornell", "room_small", "room_61k"])
-def test_ray_hits_match_oracle(built, which):
+@pytest.mark.parametrize("bvh_width", [2, 4])
+@pytest.mark.parametrize("which", ["cornell", "room_small", "room_61k", "room_516k"])
+def test_ray_hits_match_oracle(built, which, bvh_width):
     if which == "cornell":
         sc = scenes.cornell_box(1000)
     elif which == "room_small":
         sc = scenes.indoor_room(7, n_cuboids=6, cuboid_sub=3, room_sub=4, n_lights=2, n_views=1,
                                 width=16, height=12)
-    else:
+    elif which == "room_61k":
         sc = scenes.room_60k()
+    else:
+        sc = scenes.room_500k()
+        sc.cameras = sc.cameras[:1]
     tr = Tracer(sc, seed=1)
+    tr.configure("wavefront", bvh_width=bvh_width)
     o, d = scenes.random_rays(sc, 100000, seed=5)
     tri, t, u, v = [x.cpu().numpy() for x in tr.trace_rays(torch.from_numpy(o), torch.from_numpy(d))]
     osc = O.OracleScene(sc)
@@ -291,7 +296,8 @@ def test_autograd_function(built):
     w = torch.randn_like(img)
     (img * w).sum().backward()
     direct = tr.backward(w, opts, set_id=0, params=p.detach(), sampling_params=p.detach())
-    assert torch.allclose(p.grad, direct, rtol=1e-5, atol=1e-6)
+    # same paths; only the order of the float gradient sums differs
+    assert float(torch.linalg.norm(p.grad - direct) / torch.linalg.norm(direct)) <= 1e-5
 
 
 # ---------------------------------------------------------------------------
@@ -444,8 +450,8 @@ def test_loss_grad_shards_add_up(built, integrator):
         tr.loss_grad_shard(opts, 3, n - 1, 2, n)
 
 
-@pytest.mark.parametrize("spp,slots", [(32, 1 << 20), (12, 4096), (1, 1024)])
-def test_wavefront_equals_megakernel(built, spp, slots):
+@pytest.mark.parametrize("spp,slots,bvh_width", [(32, 1 << 20, 4), (12, 4096, 4), (1, 1024, 4), (8, 4096, 2)])
+def test_wavefront_equals_megakernel(built, spp, slots, bvh_width):
     """Both integrators draw the same numbers at the same slots: images agree
     to float rounding, gradients to the order of the float sums."""
     sc = scenes.indoor_room(13, n_cuboids=10, cuboid_sub=3, room_sub=4, n_lights=3, n_views=2,
@@ -454,7 +460,7 @@ def test_wavefront_equals_megakernel(built, spp, slots):
     out = {}
     for integ in INTEGRATORS:
         tr = Tracer(sc, seed=SEED)
-        tr.configure(integ, wavefront_slots=slots)
+        tr.configure(integ, wavefront_slots=slots, bvh_width=bvh_width)
         tr.set_params(p)
         opts = TraceOptions(spp_r=spp, spp_d=spp, max_depth=5)
         img = tr.render(opts, set_id=0, spp=spp).cpu().numpy()
@@ -464,3 +470,19 @@ def test_wavefront_equals_megakernel(built, spp, slots):
         tr.close()
     assert rel(out["wavefront"][0], out["megakernel"][0]) <= 1e-5
     assert rel(out["wavefront"][1], out["megakernel"][1]) <= 1e-4
+
+
+def test_bvh_widths_give_the_same_images(built):
+    """The binary and the 4-wide BVH find the same closest hits (up to exact
+    ties), so images agree to float rounding."""
+    sc = scenes.room_60k()
+    sc.cameras = sc.cameras[:2]
+    p = perturbed(sc, emission=0.02)
+    imgs = []
+    for width in (2, 4):
+        tr = Tracer(sc, seed=SEED)
+        tr.configure("wavefront", bvh_width=width)
+        tr.set_params(p)
+        imgs.append(tr.render(TraceOptions(max_depth=5), set_id=0, spp=8).cpu().numpy())
+        tr.close()
+    assert rel(imgs[1], imgs[0]) <= 1e-4
