@@ -73,7 +73,8 @@ typedef enum {
   IPT_KERNEL_WF_ADJ_CONNECT = 12,
   IPT_KERNEL_WF_ADJ_B = 13,
   IPT_KERNEL_WF_REDUCE = 14,
-  IPT_KERNEL_COUNT = 15
+  IPT_KERNEL_BATCH_STEP = 15, /* one replay of a batch's iteration graph */
+  IPT_KERNEL_COUNT = 16
 } ipt_kernel_id;
 
 /* device: CUDA device ordinal.  stream: the cudaStream_t every call queues
@@ -293,6 +294,33 @@ ipt_status ipt_kernel_times(ipt_ctx* ctx, double* total_ms, uint64_t* launches, 
  * node visits and out[5] triangle tests of shadow rays (out has 6 entries).
  * Synchronises the context's stream. */
 ipt_status ipt_counters_read(ipt_ctx* ctx, uint64_t* out, int32_t reset);
+
+/* Batches: several scenes optimised together (independent problems; each
+ * keeps its own parameters, Adam state and loss).  Every stage of an
+ * iteration is one launch over the concatenated pixels of all member
+ * scenes, and ipt_batch_step replays the whole iteration as one CUDA graph
+ * (captured on first use and again whenever the options or the context
+ * configuration change).  A scene gives the same paths in a batch as alone.
+ *
+ * ipt_batch_create: scenes (host array of n scene ids, each with views,
+ * targets and parameters set) -> *batch_id.  Copies each member's current
+ * parameters and free mask; Adam state and the iteration counter start at 0.
+ * Errors: unknown or repeated scene, missing views or targets, n == 0 or
+ * more than 4096 members. */
+ipt_status ipt_batch_create(ipt_ctx* ctx, const int32_t* scenes, uint32_t n, int32_t* batch_id);
+
+/* One nested-SGD iteration of every member (residual set, derivative set,
+ * per-member loss and Adam step).  losses_out: host array of n (may be NULL;
+ * then the call does not wait for the GPU). */
+ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opts,
+                          const ipt_adam_opts* adam, double* losses_out);
+
+/* Current parameters of member `member` (0-based position in the batch):
+ * host S x 10 floats. */
+ipt_status ipt_batch_params_get(ipt_ctx* ctx, int32_t batch, uint32_t member, float* params_out);
+
+/* Release a batch (its member scenes stay). */
+ipt_status ipt_batch_destroy(ipt_ctx* ctx, int32_t batch);
 
 /* ipt_backward without any device allocation (the paper has no counterpart;
  * this is an interface convenience).  Same arguments, result and errors as

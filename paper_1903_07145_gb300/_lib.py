@@ -25,11 +25,12 @@ EXPORTED = [
     "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_philox", "ipt_synchronize",
     "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read", "ipt_loss_grad_shard",
     "ipt_backward_noalloc", "ipt_config_set", "ipt_config_get",
+    "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy",
 ]
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox",
                 "wf_camera", "wf_closest", "wf_shadow", "wf_shade", "wf_adj_a", "wf_adj_connect",
-                "wf_adj_b", "wf_reduce"]
+                "wf_adj_b", "wf_reduce", "batch_step"]
 
 
 class IptError(RuntimeError):
@@ -102,6 +103,10 @@ def lib():
                                    C.POINTER(U32), C.POINTER(U32), C.POINTER(U64)],
                 "ipt_kernel_times": [P, C.POINTER(C.c_double), C.POINTER(U64), I32],
                 "ipt_counters_read": [P, C.POINTER(U64), I32],
+                "ipt_batch_create": [P, P, U32, C.POINTER(I32)],
+                "ipt_batch_step": [P, I32, C.POINTER(ipt_trace_opts), C.POINTER(ipt_adam_opts), P],
+                "ipt_batch_params_get": [P, I32, U32, P],
+                "ipt_batch_destroy": [P, I32],
                 "ipt_config_set": [P, C.POINTER(ipt_config)],
                 "ipt_config_get": [P, C.POINTER(ipt_config)],
                 "ipt_loss_grad_shard": [P, I32, C.POINTER(ipt_trace_opts), U64, U64, U64, U64,
@@ -250,3 +255,22 @@ def ipt_config_get(ctx):
     _check(ctx, lib().ipt_config_get(ctx, C.byref(c)))
     return dict(integrator=c.integrator, wavefront_slots=c.wavefront_slots,
                 trace_steps=c.trace_steps, blocks_per_sm=c.blocks_per_sm, bvh_width=c.bvh_width)
+
+
+def ipt_batch_create(ctx, scene_ids):
+    arr = (C.c_int32 * len(scene_ids))(*scene_ids)
+    bid = C.c_int32()
+    _check(ctx, lib().ipt_batch_create(ctx, arr, len(scene_ids), C.byref(bid)))
+    return bid.value
+
+
+def ipt_batch_step(ctx, batch, opts, adam, losses_out):
+    _check(ctx, lib().ipt_batch_step(ctx, batch, C.byref(opts), C.byref(adam), losses_out))
+
+
+def ipt_batch_params_get(ctx, batch, member, out):
+    _check(ctx, lib().ipt_batch_params_get(ctx, batch, member, out))
+
+
+def ipt_batch_destroy(ctx, batch):
+    _check(ctx, lib().ipt_batch_destroy(ctx, batch))

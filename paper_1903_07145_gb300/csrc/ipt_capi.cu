@@ -14,6 +14,8 @@
 
 #include "../../include/ipt.h"
 #include "ipt_internal.h"
+#include "ipt_path.cuh"
+#include "ipt_wavefront.h"
 
 using ipt::HostScene;
 
@@ -59,6 +61,31 @@ struct DeviceScene {
 
 }  // namespace
 
+struct Batch {
+  std::vector<int32_t> members;
+  uint32_t n_seg_total = 0;
+  uint64_t n_pix_total = 0;
+  std::vector<ipt::WfScene> tab_host;
+  ipt::WfScene* tab_dev = nullptr;
+  std::vector<ipt::BatchMember> mem_host;
+  ipt::BatchMember* mem_dev = nullptr;
+  float* params = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  uint8_t* free_mask = nullptr;
+  double* grad_acc = nullptr;
+  uint32_t* iter_dev = nullptr;
+  double* loss_rows = nullptr;
+  double* losses_dev = nullptr;
+  double* losses_host = nullptr;  // pinned
+  std::vector<void*> owned;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ipt_trace_opts g_opts{};
+  ipt_adam_opts g_adam{};
+  ipt_config g_cfg{};
+};
+
 struct PendingTiming {
   int id;
   cudaEvent_t a, b;
@@ -85,6 +112,9 @@ struct ipt_ctx {
   ipt::WfBuffers wf;
   std::vector<void*> wf_owned;
   bool wf_adjoint = false;
+  ipt::WfScene* wf_tab = nullptr;  // one-entry scene table of single-scene launches
+  std::vector<Batch*> batches;
+  cudaStream_t cap_stream = nullptr;  // stream the batch graphs are captured on
 };
 
 namespace {
@@ -325,19 +355,56 @@ bool use_wavefront(const ipt_ctx* ctx, uint32_t spp) {
   return ctx->cfg.integrator == 1 && spp <= cap;
 }
 
-// Forward pass through the configured integrator.
-ipt_status run_forward(ipt_ctx* ctx, DeviceScene* s, uint32_t begin, uint32_t n, const ipt::TraceParams& tp,
-                       float* img, float* msq, const float* target, float* g_out, double* partials, float g_scale,
-                       int loss_kind) {
+// Scene-table entry of one scene for a launch over its pixels
+// [pix_base, pix_base + n) (launch pixels 0..n-1).
+ipt::WfScene wf_entry(const ipt_ctx* ctx, int32_t scene_id, const DeviceScene* s, uint32_t pix_base, uint32_t n) {
+  ipt::WfScene e{};
+  e.s = ipt::scene_dev(buffers(ctx, s));
+  e.t = ipt::seg_dev(s->tab);
+  e.views = reinterpret_cast<const ipt::ViewDev*>(s->views_dev);
+  e.n_views = (uint32_t)s->views.size();
+  e.pix_begin = 0;
+  e.n_pix = n;
+  e.pix_base = pix_base;
+  e.seg_offset = 0;
+  e.n_seg = s->n_seg;
+  e.key = make_uint2((uint32_t)(ctx->seed & 0xFFFFFFFFu), (uint32_t)(ctx->seed >> 32) ^ (uint32_t)scene_id);
+  e.es = s->emission_scale;
+  return e;
+}
+
+ipt_status upload_entry(ipt_ctx* ctx, const ipt::WfScene& e) {
+  if (!ctx->wf_tab) IPT_CK(cudaMalloc(&ctx->wf_tab, sizeof(ipt::WfScene)));
+  IPT_CK(cudaMemcpyAsync(ctx->wf_tab, &e, sizeof(e), cudaMemcpyHostToDevice, ctx->stream));
+  return IPT_OK;
+}
+
+// Forward pass through the configured integrator.  Launch pixel i is scene
+// pixel begin + i; img/msq are indexed by launch pixel, target and g_out by
+// scene pixel.
+ipt_status run_forward(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t begin, uint32_t n,
+                       const ipt::TraceParams& tp, float* img, float* msq, const float* target, float* g_out,
+                       double* partials, float g_scale, int loss_kind) {
   if (use_wavefront(ctx, tp.spp)) {
     ipt_status st = ensure_wf(ctx, false, 10u * s->n_seg);
     if (st != IPT_OK) return st;
+    ipt::WfScene e = wf_entry(ctx, scene_id, s, begin, n);
+    e.g_scale = g_scale;
+    e.target = target;
+    e.g_img = g_out;
+    e.img = img;
+    e.msq = msq;
+    if ((st = upload_entry(ctx, e)) != IPT_OK) return st;
     StageTimer timer{ctx};
     const ipt::WfHook hook{stage_begin, stage_end, &timer};
-    IPT_CK(ipt::wf_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n, tp,
-                           ctx->wf, img, msq, target, g_out, partials, g_scale, loss_kind, ctx->err_dev,
-                           ctx->stream, (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr));
+    IPT_CK(ipt::wf_forward(ctx->L, ctx->wf_tab, std::vector<ipt::WfScene>{e}, tp, loss_kind, nullptr, ctx->wf,
+                           partials, ctx->err_dev, ctx->stream,
+                           (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr));
   } else {
+    if (target) {
+      target += 3 * (size_t)begin;
+      g_out += 3 * (size_t)begin;
+    }
     Timed tm(ctx, IPT_KERNEL_FORWARD);
     IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
                                tp, img, msq, target, g_out, partials, g_scale, loss_kind, ctx->err_dev,
@@ -346,21 +413,24 @@ ipt_status run_forward(ipt_ctx* ctx, DeviceScene* s, uint32_t begin, uint32_t n,
   return IPT_OK;
 }
 
-// Adjoint pass (accumulates into grad_acc, which the caller zeroes).
-ipt_status run_adjoint(ipt_ctx* ctx, DeviceScene* s, uint32_t begin, uint32_t n, const ipt::TraceParams& tp,
-                       const float* g_img, double* grad_acc) {
+// Adjoint pass over scene pixels [begin, begin + n) (accumulates into
+// grad_acc, which the caller zeroes).  g_img is indexed by scene pixel.
+ipt_status run_adjoint(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t begin, uint32_t n,
+                       const ipt::TraceParams& tp, const float* g_img, double* grad_acc) {
   if (use_wavefront(ctx, tp.spp)) {
     ipt_status st = ensure_wf(ctx, true, 10u * s->n_seg);
     if (st != IPT_OK) return st;
+    ipt::WfScene e = wf_entry(ctx, scene_id, s, begin, n);
+    e.g_img = const_cast<float*>(g_img);
+    if ((st = upload_entry(ctx, e)) != IPT_OK) return st;
     StageTimer timer{ctx};
     const ipt::WfHook hook{stage_begin, stage_end, &timer};
-    IPT_CK(ipt::wf_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n, tp,
-                           ctx->wf, g_img, grad_acc, ctx->err_dev, ctx->stream,
-                           (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr));
+    IPT_CK(ipt::wf_adjoint(ctx->L, ctx->wf_tab, std::vector<ipt::WfScene>{e}, tp, nullptr, ctx->wf, grad_acc,
+                           ctx->err_dev, ctx->stream, (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr));
   } else {
     Timed tm(ctx, IPT_KERNEL_ADJOINT);
     IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
-                               tp, g_img, grad_acc, ctx->err_dev, ctx->stream));
+                               tp, g_img + 3 * (size_t)begin, grad_acc, ctx->err_dev, ctx->stream));
   }
   return IPT_OK;
 }
@@ -423,8 +493,18 @@ ipt_status ipt_destroy(ipt_ctx* ctx) {
   if (!ctx) return IPT_OK;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (Batch* b : ctx->batches)
+    if (b) {
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      for (void* p : b->owned) cudaFree(p);
+      if (b->losses_host) cudaFreeHost(b->losses_host);
+      delete b;
+    }
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DeviceScene* s : ctx->scenes) free_scene(s);
   wf_release(ctx);
+  if (ctx->wf_tab) cudaFree(ctx->wf_tab);
   resolve_timings(ctx);
   for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
   if (ctx->counters_dev) cudaFree(ctx->counters_dev);
@@ -624,7 +704,7 @@ ipt_status ipt_render(ipt_ctx* ctx, int32_t scene, int32_t view, const ipt_trace
   if ((st = ensure_tables(ctx, s, p, sampling_params)) != IPT_OK) return st;
   const uint32_t begin = view < 0 ? 0u : s->views[view].offset;
   const uint32_t n = view < 0 ? (uint32_t)s->n_pix : s->views[view].w * s->views[view].h;
-  return run_forward(ctx, s, begin, n, trace_params(ctx, scene, opts, set, spp, iteration), rgb_out, msq_out,
+  return run_forward(ctx, scene, s, begin, n, trace_params(ctx, scene, opts, set, spp, iteration), rgb_out, msq_out,
                      nullptr, nullptr, nullptr, 0.f, 0);
 }
 
@@ -643,8 +723,8 @@ ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
   if ((st = ensure_tables(ctx, s, p, sampling_params)) != IPT_OK) return st;
   const uint32_t np = 10u * s->n_seg;
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
-  st = run_adjoint(ctx, s, 0, (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
-                   grad_image, s->grad_acc);
+  st = run_adjoint(ctx, scene, s, 0, (uint32_t)s->n_pix,
+                   trace_params(ctx, scene, opts, set, opts->spp_d, iteration), grad_image, s->grad_acc);
   if (st != IPT_OK) return st;
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(nullptr, 0, nullptr, s->grad_acc, grad_out, np, ctx->stream));
@@ -666,15 +746,14 @@ static ipt_status loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, c
   if ((st = ensure_tables(ctx, s, s->params, nullptr)) != IPT_OK) return st;
   const uint32_t np = 10u * s->n_seg;
   const float g_scale = (float)(1.0 / (3.0 * (double)n_total));
-  st = run_forward(ctx, s, (uint32_t)begin, (uint32_t)count,
+  st = run_forward(ctx, scene, s, (uint32_t)begin, (uint32_t)count,
                    trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration), nullptr, nullptr,
-                   s->target + 3 * begin, s->g_img + 3 * begin, s->loss_partials, g_scale, opts->loss);
+                   s->target, s->g_img, s->loss_partials, g_scale, opts->loss);
   if (st != IPT_OK) return st;
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
   const uint32_t set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
-  st = run_adjoint(ctx, s, (uint32_t)begin, (uint32_t)count,
-                   trace_params(ctx, scene, opts, set, opts->spp_d, iteration), s->g_img + 3 * begin,
-                   s->grad_acc);
+  st = run_adjoint(ctx, scene, s, (uint32_t)begin, (uint32_t)count,
+                   trace_params(ctx, scene, opts, set, opts->spp_d, iteration), s->g_img, s->grad_acc);
   if (st != IPT_OK) return st;
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, s->grad_acc,
@@ -830,6 +909,236 @@ ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg) {
 ipt_status ipt_config_get(const ipt_ctx* ctx, ipt_config* cfg) {
   if (!ctx || !cfg) return IPT_ERR_INVALID_ARG;
   *cfg = ctx->cfg;
+  return IPT_OK;
+}
+
+static ipt_status get_batch(ipt_ctx* ctx, int32_t id, Batch** out) {
+  if (!ctx) return IPT_ERR_INVALID_ARG;
+  if (id < 0 || (size_t)id >= ctx->batches.size() || !ctx->batches[id])
+    return fail(ctx, IPT_ERR_INVALID_ARG, "unknown batch id " + std::to_string(id));
+  *out = ctx->batches[id];
+  return IPT_OK;
+}
+
+// Scene table of a batch for the context's current configuration.
+static void batch_table(ipt_ctx* ctx, Batch* b) {
+  b->tab_host.clear();
+  uint32_t pix = 0, seg = 0;
+  for (int32_t id : b->members) {
+    DeviceScene* s = ctx->scenes[id];
+    ipt::WfScene e = wf_entry(ctx, id, s, 0, (uint32_t)s->n_pix);
+    e.pix_begin = pix;
+    e.seg_offset = seg;
+    e.g_scale = (float)(1.0 / (3.0 * (double)s->n_pix));
+    e.target = s->target;
+    e.g_img = s->g_img;
+    b->tab_host.push_back(e);
+    pix += (uint32_t)s->n_pix;
+    seg += s->n_seg;
+  }
+}
+
+ipt_status ipt_batch_create(ipt_ctx* ctx, const int32_t* scenes, uint32_t n, int32_t* batch_id) {
+  if (!ctx || !scenes || !batch_id) return IPT_ERR_INVALID_ARG;
+  if (n == 0 || n > 4096) return fail(ctx, IPT_ERR_INVALID_ARG, "a batch needs 1 to 4096 scenes");
+  std::vector<int32_t> ids(scenes, scenes + n);
+  {
+    std::vector<int32_t> sorted = ids;
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(ctx, IPT_ERR_INVALID_ARG, "a scene appears twice in the batch");
+  }
+  uint64_t pix = 0;
+  uint32_t segs = 0;
+  for (int32_t id : ids) {
+    DeviceScene* s;
+    ipt_status st = get_scene(ctx, id, &s);
+    if (st != IPT_OK) return st;
+    if (s->views.empty() || !s->target)
+      return fail(ctx, IPT_ERR_INVALID_ARG, "batch member " + std::to_string(id) + " has no views or targets");
+    pix += s->n_pix;
+    segs += s->n_seg;
+  }
+  if (pix >= (1ull << 32)) return fail(ctx, IPT_ERR_INVALID_ARG, "batch above 2^32 pixels");
+  IPT_CK(cudaSetDevice(ctx->device));
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return IPT_ERR_OUT_OF_MEMORY;
+  b->members = ids;
+  b->n_seg_total = segs;
+  b->n_pix_total = pix;
+  const size_t np = 10 * (size_t)segs;
+  const int rows = ipt::loss_partials_capacity(ctx->L);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t count) {
+    if (e != cudaSuccess) return;
+    void* q = nullptr;
+    e = cudaMalloc(&q, count * sizeof(**p));
+    if (e == cudaSuccess) {
+      b->owned.push_back(q);
+      *p = static_cast<std::remove_reference_t<decltype(*p)>>(q);
+    }
+  };
+  A(&b->tab_dev, n);
+  A(&b->mem_dev, n);
+  A(&b->params, np);
+  A(&b->adam_m, np);
+  A(&b->adam_v, np);
+  A(&b->free_mask, np);
+  A(&b->grad_acc, np);
+  A(&b->iter_dev, 1);
+  A(&b->loss_rows, (size_t)rows * n);
+  A(&b->losses_dev, n);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->losses_host, n * sizeof(double));
+  uint32_t off = 0;
+  for (int32_t id : ids) {
+    DeviceScene* s = ctx->scenes[id];
+    const size_t k = 10 * (size_t)s->n_seg;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->params + 10 * (size_t)off, s->params, k * sizeof(float), cudaMemcpyDeviceToDevice,
+                          ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->free_mask + 10 * (size_t)off, s->free_mask, k, cudaMemcpyDeviceToDevice, ctx->stream);
+    ipt::BatchMember m;
+    m.tab = s->tab;
+    m.seg_area = s->seg_area;
+    m.seg_offset = off;
+    m.n_seg = s->n_seg;
+    m.es = s->emission_scale;
+    m.inv_n = (float)(1.0 / (3.0 * (double)s->n_pix));
+    b->mem_host.push_back(m);
+    s->tab_is_ctx = false;  // the batch owns the member's tables from now on
+    off += s->n_seg;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->adam_m, 0, np * sizeof(float), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->adam_v, 0, np * sizeof(float), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->iter_dev, 0, sizeof(uint32_t), ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->mem_dev, b->mem_host.data(), n * sizeof(ipt::BatchMember), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess) e = ipt::launch_prepare_batch(b->mem_dev, n, b->params, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    for (void* p : b->owned) cudaFree(p);
+    if (b->losses_host) cudaFreeHost(b->losses_host);
+    delete b;
+    return cuda_fail(ctx, e, "batch create");
+  }
+  ctx->batches.push_back(b);
+  *batch_id = (int32_t)ctx->batches.size() - 1;
+  return IPT_OK;
+}
+
+static bool same_opts(const ipt_trace_opts& a, const ipt_trace_opts& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+static bool same_adam(const ipt_adam_opts& a, const ipt_adam_opts& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+static bool same_cfg(const ipt_config& a, const ipt_config& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+
+// The iteration of a batch, queued on stream `st` (captured into the graph).
+static ipt_status batch_enqueue(ipt_ctx* ctx, Batch* b, const ipt_trace_opts* opts, const ipt_adam_opts* adam,
+                                cudaStream_t st) {
+  const uint32_t n = (uint32_t)b->members.size();
+  const size_t np = 10 * (size_t)b->n_seg_total;
+  ipt::TraceParams tp{};
+  tp.seed = ctx->seed;
+  tp.set = IPT_SET_RESIDUAL;
+  tp.iteration = 0;
+  tp.spp = opts->spp_r;
+  tp.max_depth = opts->max_depth;
+  tp.nee = opts->nee;
+  tp.mis = opts->mis;
+  tp.profile = opts->emission_profile;
+  IPT_CK(ipt::wf_forward(ctx->L, b->tab_dev, b->tab_host, tp, opts->loss, b->iter_dev, ctx->wf, b->loss_rows,
+                         ctx->err_dev, st, nullptr));
+  IPT_CK(cudaMemsetAsync(b->grad_acc, 0, np * sizeof(double), st));
+  tp.set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
+  tp.spp = opts->spp_d;
+  IPT_CK(ipt::wf_adjoint(ctx->L, b->tab_dev, b->tab_host, tp, b->iter_dev, ctx->wf, b->grad_acc, ctx->err_dev, st,
+                         nullptr));
+  IPT_CK(ipt::launch_batch_losses(b->loss_rows, ipt::loss_partials_capacity(ctx->L), b->mem_dev, n, b->losses_dev,
+                                  st));
+  IPT_CK(ipt::launch_adam_batch(b->mem_dev, n, b->params, b->adam_m, b->adam_v, b->free_mask, b->grad_acc,
+                                b->iter_dev, adam_host(adam), st));
+  IPT_CK(ipt::launch_tick(b->iter_dev, st));
+  return IPT_OK;
+}
+
+ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opts, const ipt_adam_opts* adam,
+                          double* losses_out) {
+  Batch* b;
+  ipt_status st = get_batch(ctx, batch, &b);
+  if (st != IPT_OK) return st;
+  if ((st = check_opts(ctx, opts, true)) != IPT_OK) return st;
+  if (!adam) return fail(ctx, IPT_ERR_INVALID_ARG, "null adam options");
+  if (opts->spp_r == 0 || opts->spp_d == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp_r and spp_d must be positive");
+  const uint32_t cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
+  if (std::max(opts->spp_r, opts->spp_d) > cap)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "spp above the wavefront chunk size");
+  IPT_CK(cudaSetDevice(ctx->device));
+  if (!b->exec || !same_opts(*opts, b->g_opts) || !same_adam(*adam, b->g_adam) || !same_cfg(ctx->cfg, b->g_cfg)) {
+    // everything the graph touches is allocated before the capture
+    batch_table(ctx, b);
+    uint32_t max_seg = 0;
+    for (const ipt::WfChunk& c : ipt::wf_plan(b->tab_host, cap, opts->spp_d, ipt::wf_max_segments()))
+      max_seg = std::max(max_seg, c.seg_n);
+    if ((st = ensure_wf(ctx, true, 10u * max_seg)) != IPT_OK) return st;
+    IPT_CK(cudaMemcpyAsync(b->tab_dev, b->tab_host.data(), b->tab_host.size() * sizeof(ipt::WfScene),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    IPT_CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->cap_stream) IPT_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    if (b->exec) cudaGraphExecDestroy(b->exec), b->exec = nullptr;
+    if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
+    IPT_CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    st = batch_enqueue(ctx, b, opts, adam, ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (st != IPT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    IPT_CK(ce);
+    b->graph = g;
+    IPT_CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->g_opts = *opts;
+    b->g_adam = *adam;
+    b->g_cfg = ctx->cfg;
+  }
+  {
+    Timed tm(ctx, IPT_KERNEL_BATCH_STEP);
+    IPT_CK(cudaGraphLaunch(b->exec, ctx->stream));
+  }
+  if (losses_out) {
+    const size_t n = b->members.size();
+    IPT_CK(cudaMemcpyAsync(b->losses_host, b->losses_dev, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((st = ipt_synchronize(ctx)) != IPT_OK) return st;
+    std::memcpy(losses_out, b->losses_host, n * sizeof(double));
+  }
+  return IPT_OK;
+}
+
+ipt_status ipt_batch_params_get(ipt_ctx* ctx, int32_t batch, uint32_t member, float* params_out) {
+  Batch* b;
+  ipt_status st = get_batch(ctx, batch, &b);
+  if (st != IPT_OK) return st;
+  if (member >= b->members.size() || !params_out) return fail(ctx, IPT_ERR_INVALID_ARG, "bad member or output");
+  const ipt::BatchMember& m = b->mem_host[member];
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaMemcpyAsync(params_out, b->params + 10 * (size_t)m.seg_offset, 10 * sizeof(float) * m.n_seg,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+  return ipt_synchronize(ctx);
+}
+
+ipt_status ipt_batch_destroy(ipt_ctx* ctx, int32_t batch) {
+  Batch* b;
+  ipt_status st = get_batch(ctx, batch, &b);
+  if (st != IPT_OK) return st;
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaStreamSynchronize(ctx->stream));
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void* p : b->owned) cudaFree(p);
+  if (b->losses_host) cudaFreeHost(b->losses_host);
+  for (int32_t id : b->members) ctx->scenes[id]->tab_is_ctx = false;
+  delete b;
+  ctx->batches[batch] = nullptr;
   return IPT_OK;
 }
 

@@ -135,6 +135,29 @@ cudaError_t launch_adam(const SceneBuffers& s, const SegBuffers& t, float* param
                         float* v, const uint8_t* free_mask, const double* grad_acc,
                         const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st);
 
+// One member scene of a batch: where its parameters sit in the batch's
+// concatenated vector, and its parameter tables.
+struct BatchMember {
+  SegBuffers tab;
+  const double* seg_area;
+  uint32_t seg_offset, n_seg;
+  float es;
+  float inv_n;  // 1 / (3 N) of its loss
+};
+
+// Adam over the whole batch (block b updates member b, then rebuilds its
+// tables); step t = *iter_dev + 1.
+cudaError_t launch_adam_batch(const BatchMember* members, uint32_t n_members, float* params, float* m, float* v,
+                              const uint8_t* free_mask, const double* grad_acc, const uint32_t* iter_dev,
+                              const AdamHost& a, cudaStream_t st);
+// Tables of every member from the batch parameters.
+cudaError_t launch_prepare_batch(const BatchMember* members, uint32_t n_members, const float* params,
+                                 cudaStream_t st);
+// loss[b] = sum over rows of rows[r * n + b], scaled by the member's 1 / (3 N).
+cudaError_t launch_batch_losses(const double* rows, int n_rows, const BatchMember* members, uint32_t n,
+                                double* loss, cudaStream_t st);
+cudaError_t launch_tick(uint32_t* counter, cudaStream_t st);
+
 cudaError_t launch_trace_rays(const SceneBuffers& s, uint32_t n, const float* orig,
                               const float* dir, const int32_t* skip, int32_t* tri_out,
                               float* t_out, float* u_out, float* v_out, uint32_t* err,
@@ -154,16 +177,5 @@ struct WfHook {
 
 cudaError_t wf_init(Launcher* L);
 int wf_max_blocks(const Launcher& L);
-
-cudaError_t wf_forward(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
-                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
-                       const WfBuffers& wb, float* img, float* msq, const float* target, float* g_out,
-                       double* loss_partials, float g_scale, int loss_kind, uint32_t* err, cudaStream_t st,
-                       const WfHook* hook);
-
-cudaError_t wf_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
-                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
-                       const WfBuffers& wb, const float* g_img, double* grad_acc, uint32_t* err,
-                       cudaStream_t st, const WfHook* hook);
 
 }  // namespace ipt

@@ -321,13 +321,14 @@ __global__ void k_finalize(const double* loss_partials, int n_partials, double* 
     for (uint32_t i = threadIdx.x; i < n_params; i += blockDim.x) grad_out[i] = (float)grad_acc[i];
 }
 
-__global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_mask,
-                       const double* grad_acc, const float* grad_f, int* step_dev, AdamHost a, uint32_t S,
-                       float es, const double* seg_area, SegBuffers t) {
-  const int step = *step_dev + 1;
+// Adam on the concatenated parameters of a batch, one block per member,
+// followed by that member's tables for the next iteration.
+__device__ __forceinline__ void adam_range(float* params, float* m, float* v, const uint8_t* free_mask,
+                                           const double* grad_acc, const float* grad_f, uint32_t begin,
+                                           uint32_t end, const AdamHost& a, int step) {
   const float bc1 = 1.0f - powf(a.beta1, (float)step);
   const float bc2 = 1.0f - powf(a.beta2, (float)step);
-  for (uint32_t i = threadIdx.x; i < 10u * S; i += blockDim.x) {
+  for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
     if (free_mask && !free_mask[i]) continue;
     const uint32_t j = i % 10u;
     float g = grad_f ? grad_f[i] : (float)grad_acc[i];
@@ -346,10 +347,53 @@ __global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_ma
       nt = fmaxf(nt, 0.0f);
     params[i] = nt;
   }
+}
+
+__global__ void k_adam_batch(const BatchMember* members, float* params, float* m, float* v,
+                             const uint8_t* free_mask, const double* grad_acc, const uint32_t* iter_dev,
+                             AdamHost a) {
+  const BatchMember mb = members[blockIdx.x];
+  const int step = (int)*iter_dev + 1;
+  adam_range(params, m, v, free_mask, grad_acc, nullptr, 10u * mb.seg_offset, 10u * (mb.seg_offset + mb.n_seg), a,
+             step);
+  __syncthreads();
+  const float* p = params + 10u * mb.seg_offset;
+  build_tables(p, p, mb.n_seg, mb.es, mb.seg_area, mb.tab);
+}
+
+__global__ void k_prepare_batch(const BatchMember* members, const float* params) {
+  const BatchMember mb = members[blockIdx.x];
+  const float* p = params + 10u * mb.seg_offset;
+  build_tables(p, p, mb.n_seg, mb.es, mb.seg_area, mb.tab);
+}
+
+__global__ void k_batch_losses(const double* rows, int n_rows, const BatchMember* members, uint32_t n,
+                               double* loss) {
+  __shared__ double red[256];
+  const uint32_t b = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n_rows; r += blockDim.x) s += rows[(size_t)r * n + b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w >= 1; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[b] = red[0] * (double)members[b].inv_n;
+}
+
+__global__ void k_tick(uint32_t* counter) { *counter += 1u; }
+
+__global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_mask,
+                       const double* grad_acc, const float* grad_f, int* step_dev, AdamHost a, uint32_t S,
+                       float es, const double* seg_area, SegBuffers t) {
+  const int step = *step_dev + 1;
+  adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, a, step);
   __syncthreads();
   if (threadIdx.x == 0) *step_dev = step;
   build_tables(params, params, S, es, seg_area, t);
 }
+
 
 __global__ void k_trace_rays(SceneDev s, const uint32_t* orig_to_internal, uint32_t n, const float* orig,
                              const float* dir, const int32_t* skip, int32_t* tri_out, float* t_out,
@@ -476,6 +520,30 @@ cudaError_t launch_adam(const SceneBuffers& s, const SegBuffers& t, float* param
                         const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st) {
   k_adam<<<1, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg,
                             s.emission_scale, s.seg_area, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_batch(const BatchMember* members, uint32_t n_members, float* params, float* m, float* v,
+                              const uint8_t* free_mask, const double* grad_acc, const uint32_t* iter_dev,
+                              const AdamHost& a, cudaStream_t st) {
+  k_adam_batch<<<n_members, 256, 0, st>>>(members, params, m, v, free_mask, grad_acc, iter_dev, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_batch(const BatchMember* members, uint32_t n_members, const float* params,
+                                 cudaStream_t st) {
+  k_prepare_batch<<<n_members, 256, 0, st>>>(members, params);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_losses(const double* rows, int n_rows, const BatchMember* members, uint32_t n,
+                                double* loss, cudaStream_t st) {
+  k_batch_losses<<<n, 256, 0, st>>>(rows, n_rows, members, n, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tick(uint32_t* counter, cudaStream_t st) {
+  k_tick<<<1, 1, 0, st>>>(counter);
   return cudaGetLastError();
 }
 

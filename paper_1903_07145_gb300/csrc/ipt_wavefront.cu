@@ -1,6 +1,9 @@
-// Wavefront integrator: the same paths as the megakernel (same random numbers
-// at the same (vertex, call) slots), traced stage by stage over chunks of
-// path slots so that every traversal launch works on a compacted queue.
+// Wavefront integrator over a table of scenes: the same paths as the
+// megakernel (same random numbers at the same (vertex, call) slots), traced
+// stage by stage over chunks of path slots so that every traversal launch
+// works on a compacted queue.  A launch covers the concatenated pixels of
+// one or more scenes (a batch); every slot carries its scene index, and a
+// scene's paths are identical whether it is traced alone or in a batch.
 //
 // Per chunk (slots are pixel-major: slot = local_pixel * spp + sample):
 //   wf_camera                   camera rays, path state, queue 0 = all slots
@@ -10,31 +13,40 @@
 //     shading                   emission (MIS), next-event candidate -> shadow
 //                               queue, BRDF sample -> next queue
 //     wf_trace<any>             persistent shadow-ray traversal
-//   wf_reduce                   per-pixel mean / residual / loss partials
+//   wf_reduce                   per-pixel mean / residual / per-scene loss
 // The adjoint splits shading in two (before and after the shadow rays), keeps
 // each path's per-vertex carry (T_l, U_l, dw/dtheta factors) in SoA global
-// memory, and accumulates g . dI/dtheta in per-block shared memory flushed to
-// block-private global rows (reduced in FP64 at the end of the pass).
+// memory, and accumulates g . dI/dtheta in per-block shared memory over the
+// chunk's segment range, flushed to block-private rows and reduced in FP64.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "ipt_device.cuh"
 #include "ipt_internal.h"
 #include "ipt_path.cuh"
+#include "ipt_wavefront.h"
 
 namespace cg = cooperative_groups;
 
 namespace ipt {
 
-constexpr uint32_t kDead = 0x80000000u;  // beta.w flag: path finished
+constexpr uint32_t kDead = 0x80000000u;  // beta.w: path finished
+constexpr uint32_t kSceneShift = 8;      // beta.w: vertex index in bits 0-7, scene in bits 8-23
 constexpr int kWfThreads = 128;
+
+__device__ __forceinline__ uint32_t pack_state(uint32_t k, uint32_t scene) { return k | (scene << kSceneShift); }
+__device__ __forceinline__ uint32_t state_k(uint32_t w) { return w & 0xffu; }
+__device__ __forceinline__ uint32_t state_scene(uint32_t w) { return (w >> kSceneShift) & 0xffffu; }
 
 struct WfDev {
   float4* ray_o;  // origin, w = skip triangle (int bits)
   float4* ray_d;  // direction, w = pdf of this direction (0 for camera rays)
   float4* hit;    // x = triangle (int bits, -1 miss), t, u, v
-  float4* beta;   // throughput, w = vertex index | kDead
+  float4* beta;   // throughput, w = vertex index | scene << 8 | kDead
   float4* rad;    // path radiance (forward)
   uint32_t* q0;
   uint32_t* q1;
@@ -52,9 +64,26 @@ struct WfDev {
   float4* sh_ge;  // g beta f k es (emission gradient of the light segment)
   float4* sh_gm;  // g beta Le k, w = specular factor
   float4* sh_n;   // f Le k (the contribution without beta), w = d spec / d r
-  float* blk;     // per-block rows of S x 10 partial gradients
+  float* blk;     // per-block rows of the chunk's partial gradients
   uint32_t cap;
 };
+
+// Per-launch constants.
+struct WfParams {
+  uint32_t set;
+  uint32_t iter;
+  const uint32_t* iter_dev;  // iteration counter on the device (overrides iter)
+  uint32_t spp;
+  uint32_t max_depth;
+  int nee, mis, profile, loss_kind;
+  uint32_t n_scenes;
+  uint32_t seg_lo, seg_n;    // segment range of the chunk's gradient accumulators
+};
+
+__device__ __forceinline__ uint32_t set_iter(const WfParams& p) {
+  const uint32_t it = p.iter_dev ? *p.iter_dev : p.iter;
+  return (p.set << 24) | (it & 0xffffffu);
+}
 
 __device__ __forceinline__ uint32_t* queue(const WfDev& w, int which) { return which ? w.q1 : w.q0; }
 
@@ -70,32 +99,51 @@ __device__ __forceinline__ uint32_t enqueue(uint32_t* counter, bool want) {
   return want ? base + (uint32_t)__popc(m & ((1u << g.thread_rank()) - 1u)) : 0xffffffffu;
 }
 
-__device__ __forceinline__ void slot_pixel(uint32_t slot, uint32_t spp, uint32_t& lp, uint32_t& smp) {
-  lp = slot / spp;
+// Scene pixel id and sample of a slot of the chunk starting at launch pixel p0.
+__device__ __forceinline__ void slot_pixel(const WfScene& e, uint32_t p0, uint32_t slot, uint32_t spp,
+                                           uint32_t& pid, uint32_t& smp) {
+  const uint32_t lp = slot / spp;
   smp = slot - lp * spp;
+  pid = p0 + lp - e.pix_begin + e.pix_base;
+}
+
+__device__ __forceinline__ PathRng path_rng(const WfScene& e, uint32_t pid, uint32_t smp, uint32_t si) {
+  PathRng rng;
+  rng.base = make_uint4(pid, smp, si, 0);
+  rng.key = e.key;
+  return rng;
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWfThreads) wf_camera(const ViewDev* views, uint32_t n_views, uint32_t pix0,
-                                                        uint32_t n_slots, PathParams pp, WfDev w) {
+__global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfParams lp, uint32_t p0,
+                                                        uint32_t n_slots, WfDev w) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     w.cnt[0] = n_slots;
     w.cnt[3] = 0;
   }
+  const uint32_t si = set_iter(lp);
   for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n_slots; slot += gridDim.x * blockDim.x) {
-    uint32_t lp, smp;
-    slot_pixel(slot, pp.spp, lp, smp);
-    const uint32_t pid = pix0 + lp;
-    const ViewDev& vw = find_view(views, n_views, pid);
+    const uint32_t P = p0 + slot / lp.spp;
+    // scene of launch pixel P: the last entry with pix_begin <= P
+    uint32_t lo = 0, hi = lp.n_scenes - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (tab[mid].pix_begin <= P)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const WfScene& e = tab[lo];
+    uint32_t pid, smp;
+    slot_pixel(e, p0, slot, lp.spp, pid, smp);
+    const ViewDev& vw = find_view(e.views, e.n_views, pid);
     const uint32_t l = pid - vw.offset;
-    PathRng rng;
-    rng.base = make_uint4(pid, smp, pp.set_iter, 0);
-    rng.key = pp.key;
+    const PathRng rng = path_rng(e, pid, smp, si);
     float3 o;
     const float3 d = camera_ray(vw, l % vw.w, l / vw.w, rng, o);
     w.ray_o[slot] = make_float4(o.x, o.y, o.z, __int_as_float(-1));
     w.ray_d[slot] = make_float4(d.x, d.y, d.z, 0.0f);
-    w.beta[slot] = make_float4(1.0f, 1.0f, 1.0f, __uint_as_float(0u));
+    w.beta[slot] = make_float4(1.0f, 1.0f, 1.0f, __uint_as_float(pack_state(0, lo)));
     w.rad[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     w.q0[slot] = slot;
     if (w.nv) w.nv[slot] = 0;
@@ -137,9 +185,39 @@ __device__ __forceinline__ void trav_init(Trav& T, float3 o, float3 d, float tma
   T.n_nodes = T.n_tests = 0;
 }
 
-// Runs up to `steps` node visits; returns true when the traversal is over.
 template <bool kAny>
-__device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, int steps, uint32_t* err) {
+__device__ __forceinline__ bool leaf_tests(const SceneDev& s, Trav& T) {
+  int first, count;
+  decode_leaf(T.node, first, count);
+  T.n_tests += count;
+  for (int i = first; i < first + count; ++i) {
+    if (i == T.skip_a || i == T.skip_b) continue;
+    const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+    const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+    const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+    float t, u, v;
+    if (kAny) {
+      if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.tmax, t, u, v)) {
+        T.occluded = true;
+        return true;
+      }
+    } else if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.bt * 1.0000002f, t, u, v)) {
+      const int orig = __float_as_int(q0.w);
+      if (t < T.bt || (t == T.bt && orig < T.best_orig)) {
+        T.best = i;
+        T.bt = t;
+        T.bu = u;
+        T.bv = v;
+        T.best_orig = orig;
+      }
+    }
+  }
+  return false;
+}
+
+// Binary nodes: runs up to `steps` node visits; true when the traversal is over.
+template <bool kAny>
+__device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, int steps, uint32_t* err) {
   for (int it = 0; it < steps; ++it) {
     if (T.node >= 0) {
       ++T.n_nodes;
@@ -172,32 +250,8 @@ __device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, int steps, 
         T.node = h0 ? c0 : c1;
         continue;
       }
-    } else {
-      int first, count;
-      decode_leaf(T.node, first, count);
-      T.n_tests += count;
-      for (int i = first; i < first + count; ++i) {
-        if (i == T.skip_a || i == T.skip_b) continue;
-        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
-        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
-        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
-        float t, u, v;
-        if (kAny) {
-          if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.tmax, t, u, v)) {
-            T.occluded = true;
-            return true;
-          }
-        } else if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.bt * 1.0000002f, t, u, v)) {
-          const int orig = __float_as_int(q0.w);
-          if (t < T.bt || (t == T.bt && orig < T.best_orig)) {
-            T.best = i;
-            T.bt = t;
-            T.bu = u;
-            T.bv = v;
-            T.best_orig = orig;
-          }
-        }
-      }
+    } else if (leaf_tests<kAny>(s, T)) {
+      return true;
     }
     if (T.sp == 0) return true;
     T.node = T.stack[--T.sp];
@@ -205,9 +259,8 @@ __device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, int steps, 
   return false;
 }
 
-// Same contract over 4-wide quantized nodes: the hit children are visited
-// nearest first (any-hit: in slot order), and popped entries farther than
-// the current hit are skipped.
+// 4-wide quantized nodes: hit children nearest first (any-hit: slot order);
+// popped entries farther than the current hit are skipped.
 template <bool kAny>
 __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps, uint32_t* err) {
   for (int it = 0; it < steps; ++it) {
@@ -225,7 +278,6 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps,
           return true;
         }
         if (!kAny) {
-          // nearest first: misses sort to the back (+inf)
           sort4(tn, ref);
 #pragma unroll
           for (int i = 3; i >= 1; --i)
@@ -236,7 +288,6 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps,
             }
           T.node = ref[0];
         } else {
-          // slot order: descend into the lowest hit slot, push the others
           const int first = __ffs(mask) - 1;
           int next = ref[0];
 #pragma unroll
@@ -251,34 +302,9 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps,
         }
         continue;
       }
-    } else {
-      int first, count;
-      decode_leaf(T.node, first, count);
-      T.n_tests += count;
-      for (int i = first; i < first + count; ++i) {
-        if (i == T.skip_a || i == T.skip_b) continue;
-        const float4 q0 = __ldg(&s.tris[3 * i + 0]);
-        const float4 q1 = __ldg(&s.tris[3 * i + 1]);
-        const float4 q2 = __ldg(&s.tris[3 * i + 2]);
-        float t, u, v;
-        if (kAny) {
-          if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.tmax, t, u, v)) {
-            T.occluded = true;
-            return true;
-          }
-        } else if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.bt * 1.0000002f, t, u, v)) {
-          const int orig = __float_as_int(q0.w);
-          if (t < T.bt || (t == T.bt && orig < T.best_orig)) {
-            T.best = i;
-            T.bt = t;
-            T.bu = u;
-            T.bv = v;
-            T.best_orig = orig;
-          }
-        }
-      }
+    } else if (leaf_tests<kAny>(s, T)) {
+      return true;
     }
-    // pop, skipping entries that start beyond the current closest hit
     for (;;) {
       if (T.sp == 0) return true;
       --T.sp;
@@ -290,7 +316,8 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps,
 }
 
 template <int kMode, bool kWide>
-__global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int cur, int steps, uint32_t* err) {
+__global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev w, int cur, int steps,
+                                                       uint32_t* err) {
   constexpr bool kAny = kMode != 0;
   if (!kAny && blockIdx.x == 0 && threadIdx.x == 0) {
     w.cnt[cur ? 0 : 1] = 0;  // next queue, filled by the shading stage
@@ -302,6 +329,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
   Trav T;
+  SceneDev sd = tab[0].s;
   int64_t item = -1;
   bool exhausted = false;
   for (;;) {
@@ -316,11 +344,12 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int 
         const uint32_t i = base + (uint32_t)__popc(m & lt_mask);
         if (i < n) {
           item = i;
+          const uint32_t slot = kAny ? w.sh_meta[i].x : queue(w, cur)[i];
+          sd = tab[state_scene(__float_as_uint(w.beta[slot].w))].s;
           if (kAny) {
             const float4 o = w.sh_o[i], d = w.sh_d[i];
             trav_init(T, xyz(o), xyz(d), d.w, __float_as_int(o.w), (int)w.sh_meta[i].y);
           } else {
-            const uint32_t slot = queue(w, cur)[i];
             const float4 o = w.ray_o[slot], d = w.ray_d[slot];
             trav_init(T, xyz(o), xyz(d), __int_as_float(0x7f800000), __float_as_int(o.w), -1);
           }
@@ -330,9 +359,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int 
       }
     }
     if (__all_sync(0xffffffffu, item < 0)) break;
-    if (item >= 0 && (kWide ? trav_run4<kAny>(s, T, steps, err) : trav_run<kAny>(s, T, steps, err))) {
+    if (item >= 0 && (kWide ? trav_run4<kAny>(sd, T, steps, err) : trav_run2<kAny>(sd, T, steps, err))) {
       const uint32_t i = (uint32_t)item;
-      count_ray(s, kAny ? 1 : 0, T.n_nodes, T.n_tests);
+      count_ray(sd, kAny ? 1 : 0, T.n_nodes, T.n_tests);
       if (kMode == 0) {
         const uint32_t slot = queue(w, cur)[i];
         w.hit[slot] = make_float4(__int_as_float(T.best), T.bt, T.bu, T.bv);
@@ -357,12 +386,11 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(SceneDev s, WfDev w, int 
 // ---------------------------------------------------------------------------
 // Forward shading of queue `cur`.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(SceneDev s, SegDev t, uint32_t pix0, PathParams pp,
+__global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(const WfScene* tab, WfParams lp, uint32_t p0,
                                                            WfDev w, int cur) {
   if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;  // closest fetch counter of the next vertex
   const uint32_t n = w.cnt[cur];
-  const double W = *t.W;
-  const bool light_on = pp.nee && W > 0.0;
+  const uint32_t si = set_iter(lp);
   uint32_t* qin = queue(w, cur);
   uint32_t* qout = queue(w, cur ^ 1);
   uint32_t* nout = &w.cnt[cur ^ 1];
@@ -370,134 +398,137 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(SceneDev s, SegDev t,
     const uint32_t slot = qin[q];
     const float4 hh = w.hit[slot];
     const int tri = __float_as_int(hh.x);
+    const float4 bt = w.beta[slot];
+    const uint32_t st = __float_as_uint(bt.w);
+    const uint32_t k = state_k(st), b = state_scene(st);
     bool cont = false, shadow = false;
     NeeResult ne;
     float3 shc = f3(0.f, 0.f, 0.f);
-    float3 beta = f3(0.f, 0.f, 0.f), wo = f3(0.f, 0.f, 0.f), org = f3(0.f, 0.f, 0.f);
+    float3 beta = xyz(bt), wo = f3(0.f, 0.f, 0.f), org = f3(0.f, 0.f, 0.f);
     float pdf = 0.0f;
-    uint32_t k = 0;
     if (tri >= 0) {
-      const float4 bt = w.beta[slot];
-      k = __float_as_uint(bt.w) & 0xffffu;
-      beta = xyz(bt);
+      const WfScene& e = tab[b];
+      const double W = *e.t.W;
+      const bool light_on = lp.nee && W > 0.0;
       const float4 rd = w.ray_d[slot];
       Hit h;
       h.tri = tri;
       h.t = hh.y;
       h.u = hh.z;
       h.v = hh.w;
-      const Vtx v = make_vertex(s, h, xyz(rd), pp.profile);
+      const Vtx v = make_vertex(e.s, h, xyz(rd), lp.profile);
       if (v.prof > 0.0f) {
-        const float wb = emission_weight(t, v, h.t, k > 0, light_on, rd.w, pp.mis);
+        const float wb = emission_weight(e.t, v, h.t, k > 0, light_on, rd.w, lp.mis);
         if (wb > 0.0f) {
-          const float3 L = beta * xyz(__ldg(&t.emis[v.seg])) * (wb * v.prof);
-          float4 r = w.rad[slot];
+          const float3 L = beta * xyz(__ldg(&e.t.emis[v.seg])) * (wb * v.prof);
+          const float4 r = w.rad[slot];
           w.rad[slot] = make_float4(r.x + L.x, r.y + L.y, r.z + L.z, 0.0f);
         }
       }
-      if (k < pp.max_depth) {
-        uint32_t lp, smp;
-        slot_pixel(slot, pp.spp, lp, smp);
-        PathRng rng;
-        rng.base = make_uint4(pix0 + lp, smp, pp.set_iter, 0);
-        rng.key = pp.key;
+      if (k < lp.max_depth) {
+        uint32_t pid, smp;
+        slot_pixel(e, p0, slot, lp.spp, pid, smp);
+        const PathRng rng = path_rng(e, pid, smp, si);
         const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
-        const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
-        const float4 sa = __ldg(&t.samp[v.seg]);
+        const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
+        const float4 sa = __ldg(&e.t.samp[v.seg]);
         if (light_on) {
-          ne = nee_prepare(s, t, v, ua, ub, W, pp.profile, pp.mis, sa.y, sa.x);
+          ne = nee_prepare(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis, sa.y, sa.x);
           if (ne.valid) {
             const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
-            shc = beta * bv.f * xyz(__ldg(&t.emis[ne.seg])) * ne.k;
+            shc = beta * bv.f * xyz(__ldg(&e.t.emis[ne.seg])) * ne.k;
             shadow = true;
           }
         }
         if (dot(v.wi, v.ns) > 0.0f) {
-          wo = bsdf_sample(__ldg(&t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
+          wo = bsdf_sample(__ldg(&e.t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
           pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
           const float co = dot(wo, v.ns);
           if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
             const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
             beta = beta * bv.f * (co / pdf);
-            org = v.x + v.ng * s.eps;
+            org = v.x + v.ng * e.s.eps;
             cont = true;
           }
         }
       }
     }
-    const uint32_t si = enqueue(&w.cnt[2], shadow);
+    const uint32_t sq = enqueue(&w.cnt[2], shadow);
     if (shadow) {
-      w.sh_o[si] = make_float4(ne.so.x, ne.so.y, ne.so.z, __int_as_float(tri));
-      w.sh_d[si] = make_float4(ne.sd.x, ne.sd.y, ne.sd.z, ne.st);
-      w.sh_meta[si] = make_uint4(slot, (uint32_t)ne.tri, 0u, (uint32_t)ne.seg);
-      w.sh_c[si] = make_float4(shc.x, shc.y, shc.z, 0.0f);
+      w.sh_o[sq] = make_float4(ne.so.x, ne.so.y, ne.so.z, __int_as_float(tri));
+      w.sh_d[sq] = make_float4(ne.sd.x, ne.sd.y, ne.sd.z, ne.st);
+      w.sh_meta[sq] = make_uint4(slot, (uint32_t)ne.tri, 0u, (uint32_t)ne.seg);
+      w.sh_c[sq] = make_float4(shc.x, shc.y, shc.z, 0.0f);
     }
     const uint32_t ci = enqueue(nout, cont);
     if (cont) {
       qout[ci] = slot;
       w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
       w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
-      w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(k + 1));
+      w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
     }
   }
 }
 
-// Per-pixel reduction of a chunk: mean (and mean of squares), or the residual
-// and loss partials.  Outputs are indexed by pixel - out_begin.
-__global__ void __launch_bounds__(kWfThreads) wf_reduce(WfDev w, uint32_t pix0, uint32_t n_pix, uint32_t spp,
-                                                        uint32_t out_begin, float* img, float* msq,
-                                                        const float* target, float* g_out, double* loss_partials,
-                                                        int first_chunk, float g_scale, int loss_kind) {
-  double loss_acc = 0.0;
-  const float inv = 1.0f / (float)spp;
-  for (uint32_t lp = blockIdx.x * blockDim.x + threadIdx.x; lp < n_pix; lp += gridDim.x * blockDim.x) {
+// Per-pixel reduction of a chunk: mean (and mean of squares) into the
+// scene's optional outputs, or the residual of its target and the scene's
+// loss, accumulated per block (rows[block * n_scenes + scene]).
+__global__ void __launch_bounds__(kWfThreads) wf_reduce(const WfScene* tab, WfParams lp, uint32_t p0,
+                                                        uint32_t n_pix, WfDev w, double* rows, int first_chunk) {
+  extern __shared__ double sloss[];
+  for (uint32_t i = threadIdx.x; i < lp.n_scenes; i += blockDim.x) sloss[i] = 0.0;
+  __syncthreads();
+  const float inv = 1.0f / (float)lp.spp;
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n_pix; l += gridDim.x * blockDim.x) {
     float3 a = f3(0.f, 0.f, 0.f), a2 = f3(0.f, 0.f, 0.f);
-    for (uint32_t smp = 0; smp < spp; ++smp) {
-      const float3 L = xyz(w.rad[lp * spp + smp]);
+    for (uint32_t smp = 0; smp < lp.spp; ++smp) {
+      const float3 L = xyz(w.rad[l * lp.spp + smp]);
       a = a + L;
       a2 = a2 + L * L;
     }
-    const uint32_t o = pix0 + lp - out_begin;
+    const uint32_t b = state_scene(__float_as_uint(w.beta[l * lp.spp].w));
+    const WfScene& e = tab[b];
+    const uint32_t pid = p0 + l - e.pix_begin + e.pix_base;
+    const uint32_t o = pid - e.pix_base;
     const float3 mean = a * inv;
-    if (img) {
-      img[3 * o + 0] = mean.x;
-      img[3 * o + 1] = mean.y;
-      img[3 * o + 2] = mean.z;
+    if (e.img) {
+      e.img[3 * o + 0] = mean.x;
+      e.img[3 * o + 1] = mean.y;
+      e.img[3 * o + 2] = mean.z;
     }
-    if (msq) {
-      msq[3 * o + 0] = a2.x * inv;
-      msq[3 * o + 1] = a2.y * inv;
-      msq[3 * o + 2] = a2.z * inv;
+    if (e.msq) {
+      e.msq[3 * o + 0] = a2.x * inv;
+      e.msq[3 * o + 1] = a2.y * inv;
+      e.msq[3 * o + 2] = a2.z * inv;
     }
-    if (target) {
-      const float r[3] = {mean.x - target[3 * o], mean.y - target[3 * o + 1], mean.z - target[3 * o + 2]};
+    if (e.target) {
+      const float r[3] = {mean.x - e.target[3 * pid], mean.y - e.target[3 * pid + 1],
+                          mean.z - e.target[3 * pid + 2]};
+      double acc = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if (loss_kind == 0) {
-          g_out[3 * o + c] = 2.0f * r[c] * g_scale;
-          loss_acc += (double)r[c] * (double)r[c];
+        if (lp.loss_kind == 0) {
+          e.g_img[3 * pid + c] = 2.0f * r[c] * e.g_scale;
+          acc += (double)r[c] * (double)r[c];
         } else {
-          g_out[3 * o + c] = (r[c] > 0.0f ? 1.0f : (r[c] < 0.0f ? -1.0f : 0.0f)) * g_scale;
-          loss_acc += fabs((double)r[c]);
+          e.g_img[3 * pid + c] = (r[c] > 0.0f ? 1.0f : (r[c] < 0.0f ? -1.0f : 0.0f)) * e.g_scale;
+          acc += fabs((double)r[c]);
         }
       }
+      atomicAdd(&sloss[b], acc);
     }
   }
-  if (loss_partials) {
-    __shared__ double red[kWfThreads / 32];
-    for (int off = 16; off >= 1; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loss_acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sum = 0.0;
-      for (int i = 0; i < kWfThreads / 32; ++i) sum += red[i];
-      loss_partials[blockIdx.x] = first_chunk ? sum : loss_partials[blockIdx.x] + sum;
+  __syncthreads();
+  if (rows)
+    for (uint32_t i = threadIdx.x; i < lp.n_scenes; i += blockDim.x) {
+      double* r = &rows[(size_t)blockIdx.x * lp.n_scenes + i];
+      *r = first_chunk ? sloss[i] : *r + sloss[i];
     }
-  }
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint stages.  Shared accumulator helpers.
+// Adjoint stages.  Shared accumulators cover segments [seg_lo, seg_lo + seg_n)
+// of the launch's concatenated segment space.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void acc_zero(float* sacc, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sacc[i] = 0.0f;
@@ -519,15 +550,18 @@ __device__ __forceinline__ void scatter3(float* acc, int i, float3 v) {
   atomicAdd(&acc[i + 2], v.z);
 }
 
-__device__ __forceinline__ float3 pixel_grad(const float* g_img, uint32_t pix0, uint32_t g_begin, uint32_t slot,
-                                             uint32_t spp, float inv_spp) {
-  const uint32_t lp = slot / spp;
-  const uint32_t o = pix0 + lp - g_begin;
-  return f3(g_img[3 * o], g_img[3 * o + 1], g_img[3 * o + 2]) * inv_spp;
+// Accumulator index of parameter j of segment `seg` of scene entry e.
+__device__ __forceinline__ int acc_ix(const WfScene& e, const WfParams& lp, int seg, int j) {
+  return 10 * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
+}
+
+__device__ __forceinline__ float3 pixel_grad(const WfScene& e, uint32_t pid, float inv_spp) {
+  return f3(e.g_img[3 * pid], e.g_img[3 * pid + 1], e.g_img[3 * pid + 2]) * inv_spp;
 }
 
 // Continuation terms of a finished path: (dw_l / dtheta) . (g * U_l).
-__device__ __forceinline__ void finish_path(const WfDev& w, const SegDev& t, uint32_t slot, float3 gp, float* sacc) {
+__device__ __forceinline__ void finish_path(const WfDev& w, const WfScene& e, const WfParams& lp, uint32_t slot,
+                                            float3 gp, float* sacc) {
   const uint32_t nv = w.nv[slot];
   for (uint32_t l = 0; l < nv; ++l) {
     const size_t ix = (size_t)l * w.cap + slot;
@@ -535,10 +569,10 @@ __device__ __forceinline__ void finish_path(const WfDev& w, const SegDev& t, uin
     const float2 R = w.aR[ix];
     const int sg = __float_as_int(R.y);
     const float3 q = gp * xyz(U);
-    scatter3(sacc, 10 * sg + 0, q * T.w);
-    scatter3(sacc, 10 * sg + 3, q * U.w);
-    const float4 mb = __ldg(&t.mat_b[sg]);
-    atomicAdd(&sacc[10 * sg + 6], dot(q, f3(mb.x, mb.y, mb.z)) * R.x);
+    scatter3(sacc, acc_ix(e, lp, sg, 0), q * T.w);
+    scatter3(sacc, acc_ix(e, lp, sg, 3), q * U.w);
+    const float4 mb = __ldg(&e.t.mat_b[sg]);
+    atomicAdd(&sacc[acc_ix(e, lp, sg, 6)], dot(q, f3(mb.x, mb.y, mb.z)) * R.x);
   }
 }
 
@@ -557,33 +591,37 @@ __device__ __forceinline__ void add_to_carry(const WfDev& w, uint32_t slot, floa
 
 // Stage A: emission at the vertex, its contribution to the carry, and the
 // next-event candidate.
-__global__ void __launch_bounds__(kWfThreads) wf_adj_a(SceneDev s, SegDev t, uint32_t pix0, uint32_t g_begin,
-                                                       PathParams pp, WfDev w, int cur, const float* g_img) {
+__global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
+                                                       int cur) {
   extern __shared__ float sacc[];
-  const uint32_t np = 10u * s.n_seg;
+  const uint32_t np = 10u * lp.seg_n;
   acc_zero(sacc, np);
   const uint32_t n = w.cnt[cur];
-  const double W = *t.W;
-  const bool light_on = pp.nee && W > 0.0;
-  const float es = pp.emission_scale;
-  const float inv_spp = 1.0f / (float)pp.spp;
+  const uint32_t si = set_iter(lp);
+  const float inv_spp = 1.0f / (float)lp.spp;
   uint32_t* qin = queue(w, cur);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const uint32_t slot = qin[q];
     const float4 hh = w.hit[slot];
     const int tri = __float_as_int(hh.x);
-    const float3 gp = pixel_grad(g_img, pix0, g_begin, slot, pp.spp, inv_spp);
     const float4 bt = w.beta[slot];
-    const uint32_t k = __float_as_uint(bt.w) & 0xffffu;
+    const uint32_t st = __float_as_uint(bt.w);
+    const uint32_t k = state_k(st), b = state_scene(st);
+    const WfScene& e = tab[b];
+    uint32_t pid, smp;
+    slot_pixel(e, p0, slot, lp.spp, pid, smp);
+    const float3 gp = pixel_grad(e, pid, inv_spp);
     bool shadow = false;
     NeeResult ne;
     float3 ge = f3(0.f, 0.f, 0.f), gm = f3(0.f, 0.f, 0.f), cn = f3(0.f, 0.f, 0.f);
     float spec = 0.0f, dsdr = 0.0f;
     int vseg = 0;
     if (tri < 0) {
-      finish_path(w, t, slot, gp, sacc);
-      w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(k | kDead));
+      finish_path(w, e, lp, slot, gp, sacc);
+      w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
     } else {
+      const double W = *e.t.W;
+      const bool light_on = lp.nee && W > 0.0;
       const float3 beta = xyz(bt);
       const float4 rd = w.ray_d[slot];
       Hit h;
@@ -591,33 +629,29 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(SceneDev s, SegDev t, uin
       h.t = hh.y;
       h.u = hh.z;
       h.v = hh.w;
-      const Vtx v = make_vertex(s, h, xyz(rd), pp.profile);
+      const Vtx v = make_vertex(e.s, h, xyz(rd), lp.profile);
       vseg = v.seg;
       if (v.prof > 0.0f) {
-        const float wb = emission_weight(t, v, h.t, k > 0, light_on, rd.w, pp.mis);
+        const float wb = emission_weight(e.t, v, h.t, k > 0, light_on, rd.w, lp.mis);
         if (wb > 0.0f) {
           const float f = wb * v.prof;
-          add_to_carry(w, slot, xyz(__ldg(&t.emis[v.seg])) * f);
-          scatter3(sacc, 10 * v.seg + 7, gp * beta * (f * es));
+          add_to_carry(w, slot, xyz(__ldg(&e.t.emis[v.seg])) * f);
+          scatter3(sacc, acc_ix(e, lp, v.seg, 7), gp * beta * (f * e.es));
         }
       }
-      if (k == pp.max_depth) {
-        finish_path(w, t, slot, gp, sacc);
-        w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(k | kDead));
+      if (k == lp.max_depth) {
+        finish_path(w, e, lp, slot, gp, sacc);
+        w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       } else if (light_on) {
-        uint32_t lp, smp;
-        slot_pixel(slot, pp.spp, lp, smp);
-        PathRng rng;
-        rng.base = make_uint4(pix0 + lp, smp, pp.set_iter, 0);
-        rng.key = pp.key;
+        const PathRng rng = path_rng(e, pid, smp, si);
         const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
-        const float4 sa = __ldg(&t.samp[v.seg]);
-        ne = nee_prepare(s, t, v, ua, ub, W, pp.profile, pp.mis, sa.y, sa.x);
+        const float4 sa = __ldg(&e.t.samp[v.seg]);
+        ne = nee_prepare(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis, sa.y, sa.x);
         if (ne.valid) {
-          const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
+          const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
           const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
-          const float3 Le = xyz(__ldg(&t.emis[ne.seg]));
-          ge = gp * beta * bv.f * (ne.k * es);
+          const float3 Le = xyz(__ldg(&e.t.emis[ne.seg]));
+          ge = gp * beta * bv.f * (ne.k * e.es);
           gm = gp * beta * Le * ne.k;
           cn = bv.f * Le * ne.k;
           spec = bv.sp.s;
@@ -626,14 +660,14 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(SceneDev s, SegDev t, uin
         }
       }
     }
-    const uint32_t si = enqueue(&w.cnt[2], shadow);
+    const uint32_t sq = enqueue(&w.cnt[2], shadow);
     if (shadow) {
-      w.sh_o[si] = make_float4(ne.so.x, ne.so.y, ne.so.z, __int_as_float(tri));
-      w.sh_d[si] = make_float4(ne.sd.x, ne.sd.y, ne.sd.z, ne.st);
-      w.sh_meta[si] = make_uint4(slot, (uint32_t)ne.tri, (uint32_t)vseg, (uint32_t)ne.seg);
-      w.sh_ge[si] = make_float4(ge.x, ge.y, ge.z, 0.0f);
-      w.sh_gm[si] = make_float4(gm.x, gm.y, gm.z, spec);
-      w.sh_n[si] = make_float4(cn.x, cn.y, cn.z, dsdr);
+      w.sh_o[sq] = make_float4(ne.so.x, ne.so.y, ne.so.z, __int_as_float(tri));
+      w.sh_d[sq] = make_float4(ne.sd.x, ne.sd.y, ne.sd.z, ne.st);
+      w.sh_meta[sq] = make_uint4(slot, (uint32_t)ne.tri, (uint32_t)vseg, (uint32_t)ne.seg);
+      w.sh_ge[sq] = make_float4(ge.x, ge.y, ge.z, 0.0f);
+      w.sh_gm[sq] = make_float4(gm.x, gm.y, gm.z, spec);
+      w.sh_n[sq] = make_float4(cn.x, cn.y, cn.z, dsdr);
     }
   }
   acc_flush(sacc, np, w.blk);
@@ -641,48 +675,51 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(SceneDev s, SegDev t, uin
 
 // Unoccluded next-event terms: light emission (Eq. 5), the vertex material
 // (Eq. 6 at this vertex) and the carry of the earlier vertices.
-__global__ void __launch_bounds__(kWfThreads) wf_adj_connect(SceneDev s, SegDev t, WfDev w) {
+__global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab, WfParams lp, WfDev w) {
   extern __shared__ float sacc[];
-  const uint32_t np = 10u * s.n_seg;
+  const uint32_t np = 10u * lp.seg_n;
   acc_zero(sacc, np);
   const uint32_t n = w.cnt[2];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (!w.sh_vis[i]) continue;
     const uint4 m = w.sh_meta[i];
+    const WfScene& e = tab[state_scene(__float_as_uint(w.beta[m.x].w))];
     const float4 ge = w.sh_ge[i], gm = w.sh_gm[i], cn = w.sh_n[i];
-    scatter3(sacc, 10 * m.w + 7, xyz(ge));
+    scatter3(sacc, acc_ix(e, lp, (int)m.w, 7), xyz(ge));
     const float3 q = xyz(gm);
-    scatter3(sacc, 10 * m.z + 0, q * (1.0f / kPi));
-    scatter3(sacc, 10 * m.z + 3, q * gm.w);
-    const float4 mb = __ldg(&t.mat_b[m.z]);
-    atomicAdd(&sacc[10 * m.z + 6], dot(q, f3(mb.x, mb.y, mb.z)) * cn.w);
+    scatter3(sacc, acc_ix(e, lp, (int)m.z, 0), q * (1.0f / kPi));
+    scatter3(sacc, acc_ix(e, lp, (int)m.z, 3), q * gm.w);
+    const float4 mb = __ldg(&e.t.mat_b[m.z]);
+    atomicAdd(&sacc[acc_ix(e, lp, (int)m.z, 6)], dot(q, f3(mb.x, mb.y, mb.z)) * cn.w);
     add_to_carry(w, m.x, xyz(cn));
   }
   acc_flush(sacc, np, w.blk);
 }
 
 // Stage B: BRDF sampling; the new vertex joins the carry.
-__global__ void __launch_bounds__(kWfThreads) wf_adj_b(SceneDev s, SegDev t, uint32_t pix0, uint32_t g_begin,
-                                                       PathParams pp, WfDev w, int cur, const float* g_img) {
+__global__ void __launch_bounds__(kWfThreads) wf_adj_b(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
+                                                       int cur) {
   extern __shared__ float sacc[];
-  const uint32_t np = 10u * s.n_seg;
+  const uint32_t np = 10u * lp.seg_n;
   acc_zero(sacc, np);
   if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;
   const uint32_t n = w.cnt[cur];
-  const float inv_spp = 1.0f / (float)pp.spp;
+  const uint32_t si = set_iter(lp);
+  const float inv_spp = 1.0f / (float)lp.spp;
   uint32_t* qin = queue(w, cur);
   uint32_t* qout = queue(w, cur ^ 1);
   uint32_t* nout = &w.cnt[cur ^ 1];
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const uint32_t slot = qin[q];
     const float4 bt = w.beta[slot];
-    const uint32_t kw = __float_as_uint(bt.w);
+    const uint32_t st = __float_as_uint(bt.w);
     bool cont = false;
     float3 org = f3(0.f, 0.f, 0.f), wo = f3(0.f, 0.f, 0.f), beta = xyz(bt);
     float pdf = 0.0f;
     int tri = -1;
-    const uint32_t k = kw & 0xffffu;
-    if (!(kw & kDead)) {
+    const uint32_t k = state_k(st), b = state_scene(st);
+    if (!(st & kDead)) {
+      const WfScene& e = tab[b];
       const float4 hh = w.hit[slot];
       tri = __float_as_int(hh.x);
       const float4 rd = w.ray_d[slot];
@@ -691,20 +728,18 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_b(SceneDev s, SegDev t, uin
       h.t = hh.y;
       h.u = hh.z;
       h.v = hh.w;
-      const Vtx v = make_vertex(s, h, xyz(rd), pp.profile);
-      uint32_t lp, smp;
-      slot_pixel(slot, pp.spp, lp, smp);
-      PathRng rng;
-      rng.base = make_uint4(pix0 + lp, smp, pp.set_iter, 0);
-      rng.key = pp.key;
+      const Vtx v = make_vertex(e.s, h, xyz(rd), lp.profile);
+      uint32_t pid, smp;
+      slot_pixel(e, p0, slot, lp.spp, pid, smp);
+      const PathRng rng = path_rng(e, pid, smp, si);
       const float4 ua = rng.draw(k, 0);
-      const float4 sa = __ldg(&t.samp[v.seg]);
+      const float4 sa = __ldg(&e.t.samp[v.seg]);
       if (dot(v.wi, v.ns) > 0.0f) {
-        wo = bsdf_sample(__ldg(&t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
+        wo = bsdf_sample(__ldg(&e.t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
         pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
         const float co = dot(wo, v.ns);
         if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
-          const float4 ma = __ldg(&t.mat_a[v.seg]), mb = __ldg(&t.mat_b[v.seg]);
+          const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
           const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
           const float kk = co / pdf;
           const float3 wgt = bv.f * kk;
@@ -723,13 +758,13 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_b(SceneDev s, SegDev t, uin
           w.aR[ix] = make_float2(kk * bv.sp.ds_dr, __int_as_float(v.seg));
           w.nv[slot] = nv + 1;
           beta = beta * wgt;
-          org = v.x + v.ng * s.eps;
+          org = v.x + v.ng * e.s.eps;
           cont = true;
         }
       }
       if (!cont) {
-        finish_path(w, t, slot, pixel_grad(g_img, pix0, g_begin, slot, pp.spp, inv_spp), sacc);
-        w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(k | kDead));
+        finish_path(w, e, lp, slot, pixel_grad(e, pid, inv_spp), sacc);
+        w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       }
     }
     const uint32_t ci = enqueue(nout, cont);
@@ -737,12 +772,13 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_b(SceneDev s, SegDev t, uin
       qout[ci] = slot;
       w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
       w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
-      w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(k + 1));
+      w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
     }
   }
   acc_flush(sacc, np, w.blk);
 }
 
+// grad_acc[i] += sum over block rows (FP64), for the chunk's parameters.
 __global__ void wf_blk_reduce(const float* blk, int rows, uint32_t np, double* grad_acc) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -783,6 +819,8 @@ static WfDev wf_dev(const WfBuffers& b) {
 
 static int wf_grid(const Launcher& L) { return L.num_sms * L.wf_blocks_per_sm; }
 
+int wf_max_blocks(const Launcher& L) { return wf_grid(L); }
+
 // Brackets a stage launch for the caller's timing hook (kernel ids of ipt.h).
 struct StageMark {
   const WfHook* hook;
@@ -795,117 +833,180 @@ struct StageMark {
 };
 #define IPT_STAGE(id) StageMark stage_mark_(hook, id)
 
-int wf_max_blocks(const Launcher& L) { return wf_grid(L); }
+static WfParams wf_params(const TraceParams& tp, int loss_kind, uint32_t n_scenes, const uint32_t* iter_dev) {
+  WfParams p;
+  p.set = tp.set;
+  p.iter = (uint32_t)(tp.iteration & 0xffffffu);
+  p.iter_dev = iter_dev;
+  p.spp = tp.spp;
+  p.max_depth = tp.max_depth;
+  p.nee = tp.nee;
+  p.mis = tp.mis;
+  p.profile = tp.profile;
+  p.loss_kind = loss_kind;
+  p.n_scenes = n_scenes;
+  p.seg_lo = 0;
+  p.seg_n = 0;
+  return p;
+}
 
-cudaError_t wf_forward(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
-                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
-                       const WfBuffers& wb, float* img, float* msq, const float* target, float* g_out,
-                       double* loss_partials, float g_scale, int loss_kind, uint32_t* err, cudaStream_t st,
-                       const WfHook* hook) {
-  const PathParams pp = make_path_params(tp, s);
-  const SceneDev sd = scene_dev(s);
-  const SegDev tt = seg_dev(t);
-  const ViewDev* vd = reinterpret_cast<const ViewDev*>(views_dev);
+static uint32_t total_pixels(const std::vector<WfScene>& tab) {
+  return tab.empty() ? 0u : tab.back().pix_begin + tab.back().n_pix;
+}
+
+static bool all_wide(const std::vector<WfScene>& tab) {
+  for (const WfScene& e : tab)
+    if (!e.s.wide || !e.s.nodes4) return false;
+  return true;
+}
+
+// Chunks of at most cap / spp pixels; an adjoint chunk also ends before a
+// scene whose segments would take its accumulator range past max_seg.
+std::vector<WfChunk> wf_plan(const std::vector<WfScene>& tab, uint32_t cap, uint32_t spp, uint32_t max_seg) {
+  std::vector<WfChunk> out;
+  const uint32_t per_chunk = cap / spp;
+  const uint32_t total = total_pixels(tab);
+  uint32_t p = 0;
+  size_t b = 0;
+  while (p < total) {
+    while (b + 1 < tab.size() && tab[b].pix_begin + tab[b].n_pix <= p) ++b;
+    WfChunk c;
+    c.p0 = p;
+    c.seg_lo = tab[b].seg_offset;
+    uint32_t end = std::min(total, p + per_chunk);
+    size_t bb = b;
+    while (bb + 1 < tab.size() && tab[bb + 1].pix_begin < end) {
+      const WfScene& nx = tab[bb + 1];
+      if (nx.seg_offset + nx.n_seg - c.seg_lo > max_seg) {
+        end = nx.pix_begin;
+        break;
+      }
+      ++bb;
+    }
+    c.n_pix = end - p;
+    c.seg_n = tab[bb].seg_offset + tab[bb].n_seg - c.seg_lo;
+    out.push_back(c);
+    p = end;
+  }
+  return out;
+}
+
+cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
+                       const TraceParams& tp, int loss_kind, const uint32_t* iter_dev, const WfBuffers& wb,
+                       double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook) {
+  const uint32_t ns = (uint32_t)tab.size();
+  const WfParams lp = wf_params(tp, loss_kind, ns, iter_dev);
   const WfDev w = wf_dev(wb);
-  const uint32_t pix_per_chunk = wb.cap / tp.spp;
-  if (pix_per_chunk == 0) return cudaErrorInvalidValue;
+  if (wb.cap < tp.spp || ns == 0) return cudaErrorInvalidValue;
+  const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
-  const int red_grid = loss_partials_capacity(L);  // every partial is written
+  const int red_grid = loss_partials_capacity(L);
+  const size_t red_smem = sizeof(double) * ns;
+  const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, 0xffffffffu);
   int first = 1;
-  for (uint32_t c0 = 0; c0 < n_pix; c0 += pix_per_chunk) {
-    const uint32_t cp = n_pix - c0 < pix_per_chunk ? n_pix - c0 : pix_per_chunk;
-    const uint32_t pix0 = pix_begin + c0;
-    const uint32_t slots = cp * tp.spp;
+  for (const WfChunk& c : chunks) {
+    const uint32_t slots = c.n_pix * tp.spp;
     {
       IPT_STAGE(7);
-      wf_camera<<<grid, kWfThreads, 0, st>>>(vd, n_views, pix0, slots, pp, w);
+      wf_camera<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
     }
     int cur = 0;
     for (uint32_t k = 0; k <= tp.max_depth; ++k) {
       {
         IPT_STAGE(8);
-        if (s.wide) wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
-        else wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        if (wide)
+          wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+        else
+          wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
       }
       {
         IPT_STAGE(10);
-        wf_shade_fwd<<<grid, kWfThreads, 0, st>>>(sd, tt, pix0, pp, w, cur);
+        wf_shade_fwd<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       if (k < tp.max_depth && tp.nee) {
         IPT_STAGE(9);
-        if (s.wide) wf_trace<1, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
-        else wf_trace<1, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        if (wide)
+          wf_trace<1, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+        else
+          wf_trace<1, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
       }
       cur ^= 1;
     }
     {
       IPT_STAGE(14);
-      wf_reduce<<<red_grid, kWfThreads, 0, st>>>(w, pix0, cp, tp.spp, pix_begin, img, msq, target, g_out,
-                                                 loss_partials, first, g_scale, loss_kind);
+      wf_reduce<<<red_grid, kWfThreads, red_smem, st>>>(tab_dev, lp, c.p0, c.n_pix, w, loss_rows, first);
     }
     first = 0;
   }
   return cudaGetLastError();
 }
 
-cudaError_t wf_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t, const ViewHost* views_dev,
-                       uint32_t n_views, uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp,
-                       const WfBuffers& wb, const float* g_img, double* grad_acc, uint32_t* err,
-                       cudaStream_t st, const WfHook* hook) {
-  const PathParams pp = make_path_params(tp, s);
-  const SceneDev sd = scene_dev(s);
-  const SegDev tt = seg_dev(t);
-  const ViewDev* vd = reinterpret_cast<const ViewDev*>(views_dev);
+uint32_t wf_max_segments() { return (200u * 1024u) / (10u * sizeof(float)); }
+
+cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
+                       const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb, double* grad_acc,
+                       uint32_t* err, cudaStream_t st, const WfHook* hook) {
+  const uint32_t ns = (uint32_t)tab.size();
+  WfParams lp = wf_params(tp, 0, ns, iter_dev);
   const WfDev w = wf_dev(wb);
-  const uint32_t pix_per_chunk = wb.cap / tp.spp;
-  if (pix_per_chunk == 0 || !wb.aT) return cudaErrorInvalidValue;
+  if (wb.cap < tp.spp || !wb.aT || ns == 0) return cudaErrorInvalidValue;
+  const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
-  const uint32_t np = 10u * s.n_seg;
-  const size_t shmem = np * sizeof(float);
+  const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, wf_max_segments());
+  uint32_t max_np = 0;
+  for (const WfChunk& c : chunks) max_np = std::max(max_np, 10u * c.seg_n);
+  if (max_np > wb.blk_params) return cudaErrorInvalidValue;
+  const size_t shmem = max_np * sizeof(float);
   if (shmem > 48 * 1024) {
     cudaFuncSetAttribute(wf_adj_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     cudaFuncSetAttribute(wf_adj_connect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     cudaFuncSetAttribute(wf_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   }
-  cudaError_t e = cudaMemsetAsync(wb.blk, 0, (size_t)grid * np * sizeof(float), st);
-  if (e != cudaSuccess) return e;
-  for (uint32_t c0 = 0; c0 < n_pix; c0 += pix_per_chunk) {
-    const uint32_t cp = n_pix - c0 < pix_per_chunk ? n_pix - c0 : pix_per_chunk;
-    const uint32_t pix0 = pix_begin + c0;
-    const uint32_t slots = cp * tp.spp;
+  for (const WfChunk& c : chunks) {
+    lp.seg_lo = c.seg_lo;
+    lp.seg_n = c.seg_n;
+    const uint32_t np = 10u * c.seg_n;
+    const size_t sm = np * sizeof(float);
+    cudaError_t e = cudaMemsetAsync(wb.blk, 0, (size_t)grid * np * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const uint32_t slots = c.n_pix * tp.spp;
     {
       IPT_STAGE(7);
-      wf_camera<<<grid, kWfThreads, 0, st>>>(vd, n_views, pix0, slots, pp, w);
+      wf_camera<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
     }
     int cur = 0;
     for (uint32_t k = 0; k <= tp.max_depth; ++k) {
       {
         IPT_STAGE(8);
-        if (s.wide) wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
-        else wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+        if (wide)
+          wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+        else
+          wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
       }
       {
         IPT_STAGE(11);
-        wf_adj_a<<<grid, kWfThreads, shmem, st>>>(sd, tt, pix0, pix_begin, pp, w, cur, g_img);
+        wf_adj_a<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       if (k < tp.max_depth) {
         if (tp.nee) {
           {
             IPT_STAGE(9);
-            if (s.wide) wf_trace<2, true><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
-            else wf_trace<2, false><<<grid, kWfThreads, 0, st>>>(sd, w, cur, L.wf_steps, err);
+            if (wide)
+              wf_trace<2, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+            else
+              wf_trace<2, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
           }
           IPT_STAGE(12);
-          wf_adj_connect<<<grid, kWfThreads, shmem, st>>>(sd, tt, w);
+          wf_adj_connect<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, w);
         }
         IPT_STAGE(13);
-        wf_adj_b<<<grid, kWfThreads, shmem, st>>>(sd, tt, pix0, pix_begin, pp, w, cur, g_img);
+        wf_adj_b<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       cur ^= 1;
     }
+    IPT_STAGE(14);
+    wf_blk_reduce<<<(np + 127) / 128, 128, 0, st>>>(wb.blk, grid, np, grad_acc + 10u * c.seg_lo);
   }
-  IPT_STAGE(14);
-  wf_blk_reduce<<<(np + 127) / 128, 128, 0, st>>>(wb.blk, grid, np, grad_acc);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,50 @@
+// Scene table of the wavefront integrator (shared by the launchers and the
+// C ABI).  A launch traces the concatenated pixels of the table's scenes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ipt_device.cuh"
+#include "ipt_internal.h"
+
+namespace ipt {
+
+struct WfScene {
+  SceneDev s;                // geometry
+  SegDev t;                  // parameter tables
+  const ViewDev* views;
+  uint32_t n_views;
+  uint32_t pix_begin;        // first launch pixel of this scene
+  uint32_t n_pix;            // pixels of this scene in the launch
+  uint32_t pix_base;         // scene pixel id of its first launch pixel
+  uint32_t seg_offset;       // first segment of this scene in the launch's segment space
+  uint32_t n_seg;
+  uint2 key;                 // Philox key: (seed_lo, seed_hi ^ scene id)
+  float es;                  // emission scale
+  float g_scale;             // 1 / (3 N) of this scene's loss
+  const float* target;       // indexed by scene pixel id (residual mode), or nullptr
+  float* g_img;              // dE/dI, indexed by scene pixel id
+  float* img;                // optional outputs, indexed by scene pixel id - pix_base
+  float* msq;
+};
+
+struct WfChunk {
+  uint32_t p0, n_pix;        // launch pixels of the chunk
+  uint32_t seg_lo, seg_n;    // segment range its gradient accumulators cover
+};
+
+std::vector<WfChunk> wf_plan(const std::vector<WfScene>& tab, uint32_t cap, uint32_t spp, uint32_t max_seg);
+uint32_t wf_max_segments();
+
+cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
+                       const TraceParams& tp, int loss_kind, const uint32_t* iter_dev, const WfBuffers& wb,
+                       double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook);
+
+cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
+                       const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb, double* grad_acc,
+                       uint32_t* err, cudaStream_t st, const WfHook* hook);
+
+}  // namespace ipt
