@@ -1,0 +1,118 @@
+"""Pins for the radiance-cache oracle: spherical-harmonic orthonormality by
+quadrature, exactness and partition of unity of the hash-grid encoding,
+and finite differences of every gradient."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cache_oracle as K
+
+
+def test_resolutions_follow_the_geometric_rule():
+    r = K.resolutions()
+    assert r[0] == 16 and r[-1] == 2048 and len(r) == 16
+    assert all(b > a for a, b in zip(r, r[1:]))
+
+
+def test_sh_is_orthonormal():
+    # Gauss-Legendre in cos(theta) x uniform in phi, exact for these degrees
+    gx, gw = np.polynomial.legendre.leggauss(24)
+    nphi = 48
+    phi = (np.arange(nphi) + 0.5) * 2 * math.pi / nphi
+    ct, ph = np.meshgrid(gx, phi, indexing="ij")
+    st = np.sqrt(1 - ct * ct)
+    d = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    w = (gw[:, None] * np.full((1, nphi), 2 * math.pi / nphi)).reshape(-1)
+    Y = K.sh4(d)
+    G = (Y * w[:, None]).T @ Y
+    assert np.allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_hash_encoding_corners_and_partition_of_unity():
+    rng = np.random.default_rng(0)
+    table = rng.normal(size=(K.LEVELS, 1 << K.LOG2_T, K.FEATURES))
+    res = K.resolutions()
+    # at a grid vertex of level l the level's feature is the table entry
+    for l in [0, 5, 15]:
+        n = res[l]
+        ijk = np.array([[3, 7, 1], [n, 0, n // 2]])
+        x = ijk / n
+        h, idx, wts = K.hash_encode(x, table)
+        ci = K.corner_index(ijk, n)
+        assert np.allclose(h[:, 2 * l:2 * l + 2], table[l, ci], atol=1e-12)
+    # trilinear weights sum to one; a constant table gives a constant encoding
+    x = rng.random((200, 3))
+    _, _, wts = K.hash_encode(x, table)
+    assert np.allclose(wts.sum(-1), 1.0)
+    h1, _, _ = K.hash_encode(x, np.ones_like(table))
+    assert np.allclose(h1, 1.0)
+    # dense levels index every vertex once; hashed levels stay in range
+    assert (res[0] + 1) ** 3 <= 1 << K.LOG2_T
+    big = K.corner_index(np.array([[2048, 2047, 5]]), 2048)
+    assert 0 <= big[0] < 1 << K.LOG2_T
+
+
+def test_spatial_hash_matches_its_definition():
+    ijk = np.array([[123, 456, 789]])
+    n = 2048
+    T = 1 << K.LOG2_T
+    expect = ((123 * 1) ^ ((456 * 2654435761) & 0xFFFFFFFF) ^ ((789 * 805459861) & 0xFFFFFFFF)) % T
+    assert K.corner_index(ijk, n)[0] == expect
+
+
+def fd_check(f, x, g, h=1e-6, n=12, seed=0):
+    rng = np.random.default_rng(seed)
+    flat = x.reshape(-1)
+    for k in rng.choice(flat.size, n, replace=False):
+        old = flat[k]
+        flat[k] = old + h
+        fp = f()
+        flat[k] = old - h
+        fm = f()
+        flat[k] = old
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g.reshape(-1)[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, g.reshape(-1)[k])
+
+
+def test_mlp_and_loss_gradients_by_finite_differences():
+    rng = np.random.default_rng(1)
+    W = K.init_weights(3)
+    x = rng.normal(size=(20, K.IN_DIM))
+    t = rng.uniform(0, 2, (20, 3))
+
+    def loss_of():
+        y, _ = K.mlp_forward(x, W)
+        return K.rel_l2(y, t)[0]
+
+    def loss_fixed_denominator():
+        # the relative L2 holds its denominator constant: evaluate with the
+        # denominator of the unperturbed prediction
+        y, _ = K.mlp_forward(x, W)
+        r = y[:, :3] - t
+        return float(np.sum(r * r / den)) / r.size
+
+    y0, acts = K.mlp_forward(x, W)
+    den = y0[:, :3] ** 2 + 0.01
+    _, d = K.rel_l2(y0, t)
+    gw, gx = K.mlp_backward(d, acts, W)
+    for i in range(len(W)):
+        fd_check(loss_fixed_denominator, W[i], gw[i], seed=i)
+    fd_check(loss_fixed_denominator, x, gx, seed=9)
+    assert np.isfinite(loss_of())
+
+
+def test_hash_backward_by_finite_differences():
+    rng = np.random.default_rng(2)
+    table = rng.normal(size=(K.LEVELS, 1 << 10, K.FEATURES))
+    # small table: every level hashed or dense over 2^10 entries
+    x = rng.random((30, 3))
+    w = rng.normal(size=(30, K.LEVELS * K.FEATURES))
+
+    def enc_dot():
+        h, _, _ = K.hash_encode(x, table)
+        return float((h * w).sum())
+
+    h, idx, wts = K.hash_encode(x, table)
+    g = K.hash_backward(w, idx, wts, table.shape)
+    fd_check(enc_dot, table, g, n=20)
