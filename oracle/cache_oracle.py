@@ -166,3 +166,47 @@ def rel_l2(y, target, eps=0.01):
     d = np.zeros_like(y)
     d[:, :3] = 2.0 * r / denom / n
     return loss, d
+
+
+def unit_coords(x, lo, hi):
+    """World positions to the grid's unit cube (the scene's bounding box),
+    clamped to [0, 1]."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    return np.clip((np.asarray(x, np.float64) - lo) / (hi - lo), 0.0, 1.0)
+
+
+def cache_eval(x01, wi, ns, p7, weights, table):
+    """Cache prediction Lc (N, 3) and its Jacobian (N, 3, 7) with respect to
+    the 7 material parameters in the input."""
+    inp, _ = encode(x01, wi, ns, p7, table)
+    y, acts = mlp_forward(inp, weights)
+    J = np.zeros((inp.shape[0], 3, 7))
+    for c in range(3):
+        d = np.zeros((inp.shape[0], OUT_DIM))
+        d[:, c] = 1.0
+        _, dx = mlp_backward(d, acts, weights)
+        J[:, c, :] = dx[:, 64:71]
+    return y[:, :3], J
+
+
+def cached_values(term, params, weights, table, lo, hi):
+    """Cache value and Jacobian per path row of oracle terminals (zeros on
+    rows without a terminal vertex)."""
+    rows = term["seg"].shape[0]
+    cval = np.zeros((rows, 3))
+    cjac = np.zeros((rows, 3, 7))
+    m = term["seg"] >= 0
+    if m.any():
+        p7 = np.asarray(params, np.float64)[term["seg"][m], :7]
+        y, J = cache_eval(unit_coords(term["x"][m], lo, hi), term["wi"][m], term["ns"][m], p7,
+                          weights, table)
+        cval[m] = y
+        cjac[m] = J
+    return cval, cjac
+
+
+def cached_image(term, spp, cval):
+    """Pixel means of prefix + beta_b * Lc over each pixel's spp rows."""
+    v = term["prefix"] + term["beta"] * cval
+    return v.reshape(-1, spp, 3).mean(1)

@@ -725,6 +725,59 @@ void path_value_and_grad(const Ctx& C, const std::vector<PathVertex>& path, cons
   }
 }
 
+// Throughput beta_b (per channel) of the first b vertices' BSDF factors,
+// f_r * cos / pdf, evaluated at the parameters.
+void path_beta(const Ctx& C, const std::vector<PathVertex>& path, size_t b, double beta[3]) {
+  beta[0] = beta[1] = beta[2] = 1.0;
+  for (size_t i = 0; i < b; ++i) {
+    const PathVertex& pv = path[i];
+    const BrdfEval be = brdf_eval(mat_of(C.params + 10 * pv.seg), pv.ns, pv.wi, pv.wo);
+    for (int c = 0; c < 3; ++c) beta[c] *= be.f[c] * pv.cont_k;
+  }
+}
+
+// The cached estimator ends a path at vertex b: it keeps the emission found
+// at b, drops next-event estimation and continuation there, and adds
+// beta_b * Lc, where Lc is the cache's reflected radiance at b.  This is the
+// path with its tail cut (the prefix).
+std::vector<PathVertex> cut_at(const std::vector<PathVertex>& path, size_t b) {
+  std::vector<PathVertex> head(path.begin(), path.begin() + (long)(b + 1));
+  head[b].nee = false;
+  head[b].cont = false;
+  return head;
+}
+
+// Value and g-weighted gradient of the cache term beta_b * Lc of one path.
+// Lc depends on the material parameters (kd, ks, r) of the terminal segment
+// through the 3 x 7 Jacobian J; beta_b on the earlier vertices by Eq. 6.
+void cache_term(const Ctx& C, const std::vector<PathVertex>& path, size_t b, const double Lc[3],
+                const double J[21], const double* g, double L[3], double* grad) {
+  std::vector<BrdfEval> be(b);
+  std::vector<Mat> mats(b);
+  for (size_t i = 0; i < b; ++i) {
+    mats[i] = mat_of(C.params + 10 * path[i].seg);
+    be[i] = brdf_eval(mats[i], path[i].ns, path[i].wi, path[i].wo);
+  }
+  const int sb = path[b].seg;
+  for (int c = 0; c < 3; ++c) {
+    double prod = 1.0;
+    for (size_t i = 0; i < b; ++i) prod *= be[i].f[c] * path[i].cont_k;
+    L[c] += Lc[c] * prod;
+    if (!grad) continue;
+    for (int j = 0; j < 7; ++j) grad[10 * sb + j] += g[c] * prod * J[7 * c + j];
+    for (size_t l = 0; l < b; ++l) {
+      double others = 1.0;
+      for (size_t i = 0; i < b; ++i)
+        if (i != l) others *= be[i].f[c] * path[i].cont_k;
+      const double base = g[c] * Lc[c] * others * path[l].cont_k;
+      const int sl = path[l].seg;
+      grad[10 * sl + c] += base / kPi;
+      grad[10 * sl + 3 + c] += base * be[l].spec;
+      grad[10 * sl + 6] += base * mats[l].ks[c] * be[l].dspec_dr;
+    }
+  }
+}
+
 Ctx make_ctx(const Scene* s, const double* params, const double* sparams, const ora_opts* o) {
   Ctx C;
   C.s = s;
@@ -976,6 +1029,107 @@ int ora_count_rays(void* sp, const ora_camera* cam, const double* params, const 
   }
   *n_vertices = nv;
   *n_nee = nn;
+  return 0;
+}
+
+
+// Cached estimator, per path (pixel i, sample k -> row i * spp + k): the
+// prefix value (the path cut at vertex b_term, keeping the emission found
+// there), and, where the path reaches vertex b_term < max_depth, the
+// throughput beta_b, position, direction towards the previous vertex,
+// oriented shading normal and segment of that vertex (seg = -1 otherwise:
+// the prefix is then the whole path).
+int ora_cache_terminals(void* sp, const ora_camera* cam, const double* params, const double* sparams,
+                        const ora_opts* o, uint32_t b_term, const uint32_t* pixels, uint32_t npix,
+                        double* prefix, double* beta, double* x, double* wi, double* ns, int32_t* seg,
+                        int32_t nthreads) {
+  const Scene* s = static_cast<Scene*>(sp);
+  const Ctx C = make_ctx(s, params, sparams, o);
+  parallel_for(npix, nthreads, [&](int, uint32_t i) {
+    const uint32_t pid = pixels ? pixels[i] : i;
+    for (uint32_t smp = 0; smp < o->spp; ++smp) {
+      const size_t r = (size_t)i * o->spp + smp;
+      const std::vector<PathVertex> path = trace_path(C, *cam, pid % cam->width, pid / cam->width, smp);
+      const bool term = b_term < o->max_depth && path.size() > b_term;
+      double L[3];
+      path_value_and_grad(C, term ? cut_at(path, b_term) : path, nullptr, L, nullptr);
+      double bb[3] = {0.0, 0.0, 0.0};
+      if (term) path_beta(C, path, b_term, bb);
+      const PathVertex* v = term ? &path[b_term] : nullptr;
+      for (int c = 0; c < 3; ++c) {
+        prefix[3 * r + c] = L[c];
+        beta[3 * r + c] = bb[c];
+        x[3 * r + c] = v ? comp(v->x, c) : 0.0;
+        wi[3 * r + c] = v ? comp(v->wi, c) : 0.0;
+        ns[3 * r + c] = v ? comp(v->ns, c) : 0.0;
+      }
+      seg[r] = v ? v->seg : -1;
+    }
+  });
+  return 0;
+}
+
+// Vector-Jacobian product of the cached estimator: as ora_gradient, with
+// every path cut at b_term and its cache term beta_b * Lc added.  cval
+// (rows x 3) and cjac (rows x 3 x 7, d Lc_c / d (kd, ks, r)) are given per
+// path row (i * spp + k); rows without a terminal vertex are ignored.
+int ora_cache_gradient(void* sp, const ora_camera* cam, const double* params, const double* sparams,
+                       const ora_opts* o, uint32_t b_term, const uint32_t* pixels, uint32_t npix, const double* g,
+                       const double* cval, const double* cjac, double* grad, int32_t nthreads) {
+  const Scene* s = static_cast<Scene*>(sp);
+  const Ctx C = make_ctx(s, params, sparams, o);
+  const int nt = std::max(1, nthreads);
+  std::vector<std::vector<double>> part(nt, std::vector<double>(10 * (size_t)s->ns, 0.0));
+  parallel_for(npix, nt, [&](int tid, uint32_t i) {
+    const uint32_t pid = pixels ? pixels[i] : i;
+    const double gs[3] = {g[3 * i] / o->spp, g[3 * i + 1] / o->spp, g[3 * i + 2] / o->spp};
+    for (uint32_t smp = 0; smp < o->spp; ++smp) {
+      const size_t r = (size_t)i * o->spp + smp;
+      const std::vector<PathVertex> path = trace_path(C, *cam, pid % cam->width, pid / cam->width, smp);
+      const bool term = b_term < o->max_depth && path.size() > b_term;
+      double L[3];
+      path_value_and_grad(C, term ? cut_at(path, b_term) : path, gs, L, part[tid].data());
+      if (term) cache_term(C, path, b_term, cval + 3 * r, cjac + 21 * r, gs, L, part[tid].data());
+    }
+  });
+  for (int t = 0; t < nt; ++t)
+    for (size_t k = 0; k < part[t].size(); ++k) grad[k] += part[t][k];
+  return 0;
+}
+
+// Training records of the cache: full-length paths (normally set 3); where a
+// path reaches vertex b_term < max_depth, its position, direction, oriented
+// shading normal, segment and the target: the reflected radiance the path
+// estimates there, i.e. everything it gathers from vertex b_term on except
+// the emission found at b_term, divided by beta_b (the sub-path from b_term
+// with unit throughput).  seg = -1 where the path ends earlier.
+int ora_cache_records(void* sp, const ora_camera* cam, const double* params, const double* sparams,
+                      const ora_opts* o, uint32_t b_term, const uint32_t* pixels, uint32_t npix, double* x,
+                      double* wi, double* ns, int32_t* seg, double* target, int32_t nthreads) {
+  const Scene* s = static_cast<Scene*>(sp);
+  const Ctx C = make_ctx(s, params, sparams, o);
+  parallel_for(npix, nthreads, [&](int, uint32_t i) {
+    const uint32_t pid = pixels ? pixels[i] : i;
+    for (uint32_t smp = 0; smp < o->spp; ++smp) {
+      const size_t r = (size_t)i * o->spp + smp;
+      const std::vector<PathVertex> path = trace_path(C, *cam, pid % cam->width, pid / cam->width, smp);
+      const bool term = b_term < o->max_depth && path.size() > b_term;
+      double L[3] = {0.0, 0.0, 0.0};
+      if (term) {
+        std::vector<PathVertex> tail(path.begin() + (long)b_term, path.end());
+        tail[0].prof = 0.0;
+        path_value_and_grad(C, tail, nullptr, L, nullptr);
+      }
+      const PathVertex* v = term ? &path[b_term] : nullptr;
+      for (int c = 0; c < 3; ++c) {
+        x[3 * r + c] = v ? comp(v->x, c) : 0.0;
+        wi[3 * r + c] = v ? comp(v->wi, c) : 0.0;
+        ns[3 * r + c] = v ? comp(v->ns, c) : 0.0;
+        target[3 * r + c] = L[c];
+      }
+      seg[r] = v ? v->seg : -1;
+    }
+  });
   return 0;
 }
 

@@ -90,6 +90,13 @@ def lib():
                                        C.c_uint32, P, P, C.c_int32]
             L.ora_count_rays.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts), P,
                                          C.c_uint32, P, P]
+            L.ora_cache_terminals.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts),
+                                              C.c_uint32, P, C.c_uint32, P, P, P, P, P, P,
+                                              C.c_int32]
+            L.ora_cache_gradient.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts),
+                                             C.c_uint32, P, C.c_uint32, P, P, P, P, C.c_int32]
+            L.ora_cache_records.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts),
+                                            C.c_uint32, P, C.c_uint32, P, P, P, P, P, C.c_int32]
             _lib = L
     return _lib
 
@@ -221,6 +228,60 @@ class OracleScene:
         lib().ora_count_rays(self.h, C.byref(cam), _p(p), None, C.byref(o), _p(px), n,
                              _p(nv), _p(nn))
         return int(nv[0]), int(nn[0])
+
+    def _npix(self, view, pixels):
+        cam = self.cams[view]
+        px = None if pixels is None else np.ascontiguousarray(pixels, np.uint32)
+        return cam, px, (cam.width * cam.height if px is None else px.shape[0])
+
+    def cache_terminals(self, params, b_term, view=0, pixels=None, sparams=None, threads=None, **kw):
+        """Per path row (pixel i, sample k -> i * spp + k) of the cached
+        estimator: prefix value, beta_b, x, wi, ns and segment (-1: no
+        terminal vertex)."""
+        cam, px, n = self._npix(view, pixels)
+        o = self.opts(view=view, **kw)
+        rows = n * o.spp
+        p = np.ascontiguousarray(params, np.float64)
+        sp = None if sparams is None else np.ascontiguousarray(sparams, np.float64)
+        out = {k: np.zeros((rows, 3)) for k in ("prefix", "beta", "x", "wi", "ns")}
+        seg = np.zeros(rows, np.int32)
+        lib().ora_cache_terminals(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), int(b_term), _p(px), n,
+                                  _p(out["prefix"]), _p(out["beta"]), _p(out["x"]), _p(out["wi"]),
+                                  _p(out["ns"]), _p(seg), threads or default_threads())
+        out["seg"] = seg
+        return out
+
+    def cache_gradient(self, params, g, b_term, cval, cjac, view=0, pixels=None, sparams=None,
+                       threads=None, **kw):
+        """J^T g of the cached estimator given per-row cache values (rows, 3)
+        and Jacobians (rows, 3, 7) with respect to (kd, ks, r)."""
+        cam, px, n = self._npix(view, pixels)
+        o = self.opts(view=view, **kw)
+        p = np.ascontiguousarray(params, np.float64)
+        sp = None if sparams is None else np.ascontiguousarray(sparams, np.float64)
+        gg = np.ascontiguousarray(g, np.float64).reshape(n, 3)
+        cv = np.ascontiguousarray(cval, np.float64).reshape(n * o.spp, 3)
+        cj = np.ascontiguousarray(cjac, np.float64).reshape(n * o.spp, 21)
+        out = np.zeros((self.n_seg, 10))
+        lib().ora_cache_gradient(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), int(b_term), _p(px), n,
+                                 _p(gg), _p(cv), _p(cj), _p(out), threads or default_threads())
+        return out
+
+    def cache_records(self, params, b_term, view=0, pixels=None, sparams=None, threads=None, **kw):
+        """Training records of full-length paths: x, wi, ns, segment (-1: the
+        path ends before b_term) and the reflected-radiance target at b_term."""
+        cam, px, n = self._npix(view, pixels)
+        o = self.opts(view=view, **kw)
+        rows = n * o.spp
+        p = np.ascontiguousarray(params, np.float64)
+        sp = None if sparams is None else np.ascontiguousarray(sparams, np.float64)
+        out = {k: np.zeros((rows, 3)) for k in ("x", "wi", "ns", "target")}
+        seg = np.zeros(rows, np.int32)
+        lib().ora_cache_records(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), int(b_term), _p(px), n,
+                                _p(out["x"]), _p(out["wi"]), _p(out["ns"]), _p(seg), _p(out["target"]),
+                                threads or default_threads())
+        out["seg"] = seg
+        return out
 
     def light_sample(self, sparams, u):
         u = np.ascontiguousarray(u, np.float64).reshape(-1, 4)

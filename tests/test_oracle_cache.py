@@ -7,6 +7,8 @@ import numpy as np
 import pytest
 
 from oracle import cache_oracle as K
+from oracle import oracle as O
+from paper_1903_07145_gb300 import scenes
 
 
 def test_resolutions_follow_the_geometric_rule():
@@ -116,3 +118,77 @@ def test_hash_backward_by_finite_differences():
     h, idx, wts = K.hash_encode(x, table)
     g = K.hash_backward(w, idx, wts, table.shape)
     fd_check(enc_dot, table, g, n=20)
+
+
+# ----------------------------------------------------------------------------
+# Paths cut at the cache vertex
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("b_term", [1, 2])
+def test_cut_paths_decompose_the_plain_estimate(b_term):
+    """Per sample, the plain estimate equals prefix + beta_b * (reflected
+    radiance gathered from b on): the cut keeps the emission found at b and
+    the training target holds everything after it."""
+    sc = scenes.cornell_box(1000, 8, 8)
+    osc = O.OracleScene(sc)
+    p = sc.gt_params.astype(np.float64)
+    kw = dict(spp=6, max_depth=4, seed=5, set_id=0, iteration=3)
+    term = osc.cache_terminals(p, b_term, **kw)
+    rec = osc.cache_records(p, b_term, **kw)
+    plain, _ = osc.render(p, **kw)
+    assert np.array_equal(term["seg"], rec["seg"])
+    assert np.array_equal(term["x"], rec["x"]) and np.array_equal(term["ns"], rec["ns"])
+    m = term["seg"] >= 0
+    assert m.mean() > 0.5
+    assert np.all(term["beta"][m] > 0) and np.all(term["beta"][~m] == 0)
+    assert np.all(rec["target"] >= 0)
+    assert np.allclose(np.einsum("ij,ij->i", term["wi"][m], term["ns"][m]) > -1e-12, True)
+    comp = K.cached_image(term, 6, rec["target"])
+    assert np.allclose(comp, plain, rtol=1e-12, atol=1e-14)
+    # with the cut past the last vertex nothing is cached
+    none = osc.cache_terminals(p, 4, **kw)
+    assert np.all(none["seg"] == -1)
+    assert np.allclose(none["prefix"].reshape(-1, 6, 3).mean(1), plain, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("b_term", [1, 2])
+def test_cached_gradient_matches_central_differences(b_term):
+    """With sampling frozen and a closed-form cache Lc = A theta_7 + c, the
+    vector-Jacobian product of the cut estimator matches central differences
+    in every parameter kind (earlier vertices' BSDF factors by Eq. 6, the
+    terminal segment through the cache)."""
+    sc = scenes.cornell_box(1000, 8, 8)
+    osc = O.OracleScene(sc)
+    rng = np.random.default_rng(3)
+    p = sc.gt_params.astype(np.float64).copy()
+    p[:, 3:6] = rng.uniform(0.05, 0.3, (sc.n_segments, 3))
+    A = rng.normal(size=(3, 7))
+    c0 = rng.uniform(0.5, 1.0, 3)
+    w = rng.normal(size=(64, 3))
+    kw = dict(spp=4, max_depth=3, seed=9, set_id=1)
+
+    def image(q):
+        term = osc.cache_terminals(q, b_term, sparams=p, **kw)
+        m = term["seg"] >= 0
+        cval = np.zeros_like(term["prefix"])
+        cval[m] = q[term["seg"][m], :7] @ A.T + c0
+        return K.cached_image(term, 4, cval), term, cval
+
+    _, term, cval = image(p)
+    cjac = np.zeros((cval.shape[0], 3, 7))
+    cjac[term["seg"] >= 0] = A
+    grad = osc.cache_gradient(p, w, b_term, cval, cjac, sparams=p, **kw)
+    h = 1e-5
+    ks = rng.choice(sc.n_segments * 10, 24, replace=False)
+    for k in ks:
+        pp = p.copy().reshape(-1)
+        pm = p.copy().reshape(-1)
+        pp[k] += h
+        pm[k] -= h
+        ip = image(pp.reshape(p.shape))[0]
+        im = image(pm.reshape(p.shape))[0]
+        fd = float((w * (ip - im)).sum() / (2 * h))
+        g = grad.reshape(-1)[k]
+        assert abs(fd - g) <= 1e-6 * max(abs(g), 1e-3 * np.abs(grad).max()), (k, fd, g)
+    # the terminal segments' material rows move through the cache Jacobian
+    assert np.abs(grad[:, :7]).sum() > 0
