@@ -74,7 +74,13 @@ typedef enum {
   IPT_KERNEL_WF_ADJ_B = 13,
   IPT_KERNEL_WF_REDUCE = 14,
   IPT_KERNEL_BATCH_STEP = 15, /* one replay of a batch's iteration graph */
-  IPT_KERNEL_COUNT = 16
+  /* radiance cache */
+  IPT_KERNEL_CACHE_INFER = 16,   /* queries of the forward pass */
+  IPT_KERNEL_CACHE_VJP = 17,     /* queries of the adjoint pass, with input gradients */
+  IPT_KERNEL_CACHE_RECORDS = 18, /* training-record targets */
+  IPT_KERNEL_CACHE_GRAD = 19,    /* training forward + backward */
+  IPT_KERNEL_CACHE_ADAM = 20,    /* optimizer step on weights and hash table */
+  IPT_KERNEL_COUNT = 21
 } ipt_kernel_id;
 
 /* device: CUDA device ordinal.  stream: the cudaStream_t every call queues
@@ -154,6 +160,7 @@ typedef struct {
 #define IPT_SET_RESIDUAL 0u
 #define IPT_SET_DERIVATIVE 1u
 #define IPT_SET_TARGET 2u
+#define IPT_SET_CACHE 3u
 
 /* Create a context on opt->device.  *out receives the handle.  Fails with
  * IPT_ERR_CUDA if the device cannot be used. */
@@ -335,10 +342,142 @@ ipt_status ipt_batch_destroy(ipt_ctx* ctx, int32_t batch);
  * address up (cudaGetSymbolAddress); make that first call before any stream
  * capture.  The array is cleared at the start of every call, and all calls
  * share it: calls whose work overlaps on the GPU (other streams, other
- * contexts on the same device) race on it. */
+ * contexts on the same device) race on it.  It always runs the plain
+ * estimator on the megakernel integrator (a scene's radiance cache is not
+ * used). */
 ipt_status ipt_backward_noalloc(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t set,
                                 uint64_t iteration, const float* params, const float* sampling_params,
                                 const float* grad_image, float* grad_out);
+
+/* ---------------------------------------------------------------------------
+ * Learned radiance cache (the paper has none: its estimator traces every path
+ * to max_depth, Sec. 3.1; this is an optional acceleration of that
+ * estimator).  Paths end at vertex b_term (0 = the camera ray's hit): the
+ * emission found there is kept, and instead of next-event estimation and
+ * continuation the cache's prediction of the reflected radiance at that
+ * vertex, times the path throughput, is added.  The prediction is a small
+ * network: a multiresolution hash-grid encoding of the position (Mueller et
+ * al., SIGGRAPH 2022: 16 levels x 2 features, 2^19 entries per level,
+ * resolutions 16..2048 over the scene's bounding box), spherical harmonics of
+ * degrees 0..3 of the direction towards the previous vertex and of the
+ * oriented shading normal, and the terminal segment's kd, ks and roughness
+ * (input of 80 values, the last 9 zero), then 80 -> 64 -> 64 -> 64 -> 64 ->
+ * 16 with ReLU, no biases, the first 3 outputs being RGB.  It runs on BF16
+ * tensor cores with FP32 accumulation.
+ *
+ * Gradients: the adjoint pass chains the cache's derivative with respect to
+ * the terminal segment's kd, ks and roughness into that segment's gradient,
+ * and the prediction into the earlier vertices' Eq. 6 terms.  What the
+ * reflected radiance owes to other segments' parameters is not seen: the
+ * cached gradient is biased, and ipt_cache_bias measures by how much.
+ *
+ * Training (self-supervised, in ipt_step or ipt_cache_train): train_spp
+ * full-length paths per pixel from a fourth independent sample set
+ * (IPT_SET_CACHE) record, at vertex b_term, the inputs and the reflected
+ * radiance they gather after it (next-event estimation at b_term and every
+ * later contribution, with unit throughput at b_term).  The records are
+ * split into train_steps minibatches, each one step of Adam on the relative
+ * L2 loss mean((y - t)^2 / (y^2 + 0.01)) (the denominator held constant)
+ * over the weights and the hash table.
+ *
+ * A cache belongs to one scene and serves that scene's ipt_render,
+ * ipt_backward, ipt_loss_grad(_shard) and ipt_step calls while active; the
+ * megakernel integrator and batches do not use it (the cached passes always
+ * run on the wavefront integrator).
+ * ------------------------------------------------------------------------- */
+
+/* Number of FP32 network weights: W1 (80 x 64), W2..W4 (64 x 64), W5
+ * (64 x 16), each row-major with the input index first, concatenated. */
+#define IPT_CACHE_WEIGHTS 18432u
+/* Hash-table size in floats: [16 levels][2^19 entries][2 features]. */
+#define IPT_CACHE_TABLE_FLOATS (16u * 524288u * 2u)
+
+typedef struct {
+  int32_t enabled;          /* 1: the scene's passes use the cached estimator */
+  uint32_t b_term;          /* vertex where paths end in the cache; >= 1, and
+                               < max_depth to have any effect */
+  uint32_t train_spp;       /* training paths per pixel; 0: max(1, spp_r / 16) */
+  uint32_t train_steps;     /* Adam steps per training pass (1..64) */
+  uint32_t record_capacity; /* records kept per training pass (others dropped) */
+  float lr, beta1, beta2, eps; /* Adam on weights and table */
+  float bias_threshold;     /* ipt_cache_bias turns the cache off above this
+                               relative bias (0: never) */
+  uint64_t init_seed;       /* weights: uniform +-sqrt(6 / fan_in); table:
+                               uniform +-1e-4 */
+} ipt_cache_opts;
+
+typedef struct {
+  int32_t active;           /* the cached estimator is in use */
+  int32_t fell_back;        /* turned off by ipt_cache_bias */
+  uint32_t records;         /* training paths that reached b_term in the last
+                               pass (may exceed record_capacity) */
+  uint32_t pad;
+  uint64_t train_steps;     /* Adam steps taken */
+  double last_loss;         /* mean relative L2 over the last pass's records */
+  double image_bias;        /* last ipt_cache_bias results, -1: not measured */
+  double grad_bias;
+  float lo[3], hi[3];       /* box mapped to the grid's unit cube */
+  int32_t res[16];          /* grid resolution of each level */
+} ipt_cache_stats;
+
+/* Create (or reconfigure) the scene's cache.  The first call allocates and
+ * initialises the network from init_seed; later calls change the options and
+ * keep the weights.  enabled = 0 turns the cached estimator off (the state is
+ * kept).  Errors: b_term == 0, train_steps outside 1..64, record_capacity 0,
+ * non-positive lr or eps, beta outside [0, 1). */
+ipt_status ipt_cache_configure(ipt_ctx* ctx, int32_t scene, const ipt_cache_opts* opts);
+
+/* Replace the weights (host, IPT_CACHE_WEIGHTS floats) and/or the hash table
+ * (host, IPT_CACHE_TABLE_FLOATS floats); NULL keeps that part.  Adam state is
+ * cleared.  Requires a configured cache. */
+ipt_status ipt_cache_weights_set(ipt_ctx* ctx, int32_t scene, const float* weights, const float* table);
+
+/* Copy the weights and/or the hash table to host arrays (NULL skips). */
+ipt_status ipt_cache_weights_get(ipt_ctx* ctx, int32_t scene, float* weights, float* table);
+
+/* Evaluate the network on n rows given directly (all device arrays):
+ * x01 (n x 3, positions in the unit cube, clamped to [0, 1]), dir and nrm
+ * (n x 3, unit vectors), params7 (n x 7: kd rgb, ks rgb, roughness).
+ * rgb_out (n x 3) receives the prediction.  With upstream (n x 3, nullable)
+ * and dparams_out (n x 7, nullable) both given, dparams_out receives
+ * upstream . d(prediction) / d(params7) per row. */
+ipt_status ipt_cache_eval(ipt_ctx* ctx, int32_t scene, uint32_t n, const float* x01, const float* dir,
+                          const float* nrm, const float* params7, const float* upstream, float* rgb_out,
+                          float* dparams_out);
+
+/* Relative-L2 loss of n rows against target (n x 3, device) and its
+ * gradient, without a step: *loss_out (host, nullable) receives the mean over
+ * rows and channels; grad_weights (device, IPT_CACHE_WEIGHTS, nullable) and
+ * grad_table (device, IPT_CACHE_TABLE_FLOATS, nullable) receive the
+ * gradients of that mean. */
+ipt_status ipt_cache_grad(ipt_ctx* ctx, int32_t scene, uint32_t n, const float* x01, const float* dir,
+                          const float* nrm, const float* params7, const float* target, double* loss_out,
+                          float* grad_weights, float* grad_table);
+
+/* One training pass for `iteration`: record the training paths (set
+ * IPT_SET_CACHE, opts->max_depth, nee, mis, profile; spp from the cache
+ * options) and take train_steps Adam steps.  ipt_step calls this after the
+ * gradient passes while the cache is active. */
+ipt_status ipt_cache_train(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint64_t iteration);
+
+/* Records of the last training pass: *n_out receives how many are kept
+ * (<= record_capacity); records (host, nullable, capacity >= *n_out x 16
+ * floats) receives per record [path id = scene pixel * train_spp + sample,
+ * segment, x (3, world), direction (3), normal (3), target (3), 0, 0, 0].
+ * Record order is not deterministic. */
+ipt_status ipt_cache_records(ipt_ctx* ctx, int32_t scene, uint32_t* n_out, float* records);
+
+ipt_status ipt_cache_status(ipt_ctx* ctx, int32_t scene, ipt_cache_stats* out);
+
+/* Bias of the cached estimator against the plain one, both with sample set 0
+ * of `iteration` at `spp` samples per pixel (common random numbers up to the
+ * cache vertex): image_bias = ||I_cache - I_plain|| / ||I_plain|| over all
+ * views; grad_bias the same for the loss gradients (opts->spp_d derivative
+ * samples; needs targets; -1 without).  When bias_threshold > 0 and either
+ * exceeds it, the cache is turned off (stats.fell_back = 1).  Outputs are
+ * host pointers (nullable). */
+ipt_status ipt_cache_bias(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t spp,
+                          uint64_t iteration, double* image_bias, double* grad_bias);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,14 @@ learned component; this follows the cache's specification in plain numpy:
 * loss: relative L2, mean over records and channels of
   (y - t)^2 / (sg(y)^2 + 0.01), sg = stop-gradient.
 
+The network's operands are specified as BF16 (tensor-core inputs with FP32
+accumulation).  Where that precision decides a discrete branch -- a ReLU
+mask, a unit's activation at zero -- the oracle takes the decision the same
+way: with storage="bf16" the input and each hidden activation are rounded
+to BF16 (round to nearest, ties to even) where the network stores them,
+while every sum and product stays FP64.  The default (storage=None) is the
+plain FP64 network.
+
 Parity status: pinned (SH orthonormality by quadrature, exact corner values
 and partition of unity of the hash encoding, finite differences of every
 gradient, see tests/test_oracle_cache.py).
@@ -35,6 +43,14 @@ import numpy as np
 LEVELS, FEATURES, LOG2_T, N_MIN, N_MAX = 16, 2, 19, 16, 2048
 IN_DIM, HIDDEN, OUT_DIM, N_HIDDEN = 80, 64, 16, 4
 PRIMES = (1, 2654435761, 805459861)
+
+
+def bf16(a):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even); the
+    result is returned as float64."""
+    b = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32)).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def resolutions(levels=LEVELS, n_min=N_MIN, n_max=N_MAX):
@@ -133,13 +149,16 @@ def init_weights(seed=0):
     return [rng.uniform(-1, 1, (dims[i], dims[i + 1])) * math.sqrt(6.0 / dims[i]) for i in range(len(dims) - 1)]
 
 
-def mlp_forward(inp, weights):
-    acts = [np.asarray(inp, np.float64)]
+def mlp_forward(inp, weights, storage=None):
+    """Forward pass; storage="bf16" rounds the input and the hidden
+    activations to BF16 where the network stores them."""
+    rnd = bf16 if storage == "bf16" else (lambda a: a)
+    acts = [rnd(np.asarray(inp, np.float64))]
     z = acts[0]
     for i, W in enumerate(weights):
         z = z @ W
         if i < len(weights) - 1:
-            z = np.maximum(z, 0.0)
+            z = rnd(np.maximum(z, 0.0))
         acts.append(z)
     return z, acts
 
@@ -176,11 +195,11 @@ def unit_coords(x, lo, hi):
     return np.clip((np.asarray(x, np.float64) - lo) / (hi - lo), 0.0, 1.0)
 
 
-def cache_eval(x01, wi, ns, p7, weights, table):
+def cache_eval(x01, wi, ns, p7, weights, table, storage=None):
     """Cache prediction Lc (N, 3) and its Jacobian (N, 3, 7) with respect to
     the 7 material parameters in the input."""
     inp, _ = encode(x01, wi, ns, p7, table)
-    y, acts = mlp_forward(inp, weights)
+    y, acts = mlp_forward(inp, weights, storage)
     J = np.zeros((inp.shape[0], 3, 7))
     for c in range(3):
         d = np.zeros((inp.shape[0], OUT_DIM))
@@ -190,7 +209,7 @@ def cache_eval(x01, wi, ns, p7, weights, table):
     return y[:, :3], J
 
 
-def cached_values(term, params, weights, table, lo, hi):
+def cached_values(term, params, weights, table, lo, hi, storage=None):
     """Cache value and Jacobian per path row of oracle terminals (zeros on
     rows without a terminal vertex)."""
     rows = term["seg"].shape[0]
@@ -200,7 +219,7 @@ def cached_values(term, params, weights, table, lo, hi):
     if m.any():
         p7 = np.asarray(params, np.float64)[term["seg"][m], :7]
         y, J = cache_eval(unit_coords(term["x"][m], lo, hi), term["wi"][m], term["ns"][m], p7,
-                          weights, table)
+                          weights, table, storage)
         cval[m] = y
         cjac[m] = J
     return cval, cjac

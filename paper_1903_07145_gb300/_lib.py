@@ -16,7 +16,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libipt.so")
 
 IPT_OK = 0
-IPT_SET_RESIDUAL, IPT_SET_DERIVATIVE, IPT_SET_TARGET = 0, 1, 2
+IPT_SET_RESIDUAL, IPT_SET_DERIVATIVE, IPT_SET_TARGET, IPT_SET_CACHE = 0, 1, 2, 3
+IPT_CACHE_WEIGHTS = 18432
+IPT_CACHE_TABLE_FLOATS = 16 * 524288 * 2
 
 EXPORTED = [
     "ipt_create", "ipt_destroy", "ipt_status_string", "ipt_last_error_detail",
@@ -26,11 +28,14 @@ EXPORTED = [
     "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read", "ipt_loss_grad_shard",
     "ipt_backward_noalloc", "ipt_config_set", "ipt_config_get",
     "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy",
+    "ipt_cache_configure", "ipt_cache_weights_set", "ipt_cache_weights_get", "ipt_cache_eval",
+    "ipt_cache_grad", "ipt_cache_train", "ipt_cache_records", "ipt_cache_status", "ipt_cache_bias",
 ]
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox",
                 "wf_camera", "wf_closest", "wf_shadow", "wf_shade", "wf_adj_a", "wf_adj_connect",
-                "wf_adj_b", "wf_reduce", "batch_step"]
+                "wf_adj_b", "wf_reduce", "batch_step", "cache_infer", "cache_vjp", "cache_records",
+                "cache_grad", "cache_adam"]
 
 
 class IptError(RuntimeError):
@@ -64,6 +69,20 @@ class ipt_trace_opts(C.Structure):
 class ipt_adam_opts(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("l1_emission", C.c_float)]
+
+
+class ipt_cache_opts(C.Structure):
+    _fields_ = [("enabled", C.c_int32), ("b_term", C.c_uint32), ("train_spp", C.c_uint32),
+                ("train_steps", C.c_uint32), ("record_capacity", C.c_uint32), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("bias_threshold", C.c_float), ("init_seed", C.c_uint64)]
+
+
+class ipt_cache_stats(C.Structure):
+    _fields_ = [("active", C.c_int32), ("fell_back", C.c_int32), ("records", C.c_uint32),
+                ("pad", C.c_uint32), ("train_steps", C.c_uint64), ("last_loss", C.c_double),
+                ("image_bias", C.c_double), ("grad_bias", C.c_double), ("lo", C.c_float * 3),
+                ("hi", C.c_float * 3), ("res", C.c_int32 * 16)]
 
 
 _lib = None
@@ -111,6 +130,16 @@ def lib():
                 "ipt_config_get": [P, C.POINTER(ipt_config)],
                 "ipt_loss_grad_shard": [P, I32, C.POINTER(ipt_trace_opts), U64, U64, U64, U64,
                                         C.POINTER(C.c_double), P],
+                "ipt_cache_configure": [P, I32, C.POINTER(ipt_cache_opts)],
+                "ipt_cache_weights_set": [P, I32, P, P],
+                "ipt_cache_weights_get": [P, I32, P, P],
+                "ipt_cache_eval": [P, I32, U32, P, P, P, P, P, P, P],
+                "ipt_cache_grad": [P, I32, U32, P, P, P, P, P, C.POINTER(C.c_double), P, P],
+                "ipt_cache_train": [P, I32, C.POINTER(ipt_trace_opts), U64],
+                "ipt_cache_records": [P, I32, C.POINTER(U32), P],
+                "ipt_cache_status": [P, I32, C.POINTER(ipt_cache_stats)],
+                "ipt_cache_bias": [P, I32, C.POINTER(ipt_trace_opts), U32, U64, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -274,3 +303,53 @@ def ipt_batch_params_get(ctx, batch, member, out):
 
 def ipt_batch_destroy(ctx, batch):
     _check(ctx, lib().ipt_batch_destroy(ctx, batch))
+
+
+def ipt_cache_configure(ctx, scene, opts):
+    _check(ctx, lib().ipt_cache_configure(ctx, scene, C.byref(opts)))
+
+
+def ipt_cache_weights_set(ctx, scene, weights, table):
+    _check(ctx, lib().ipt_cache_weights_set(ctx, scene, weights, table))
+
+
+def ipt_cache_weights_get(ctx, scene, weights, table):
+    _check(ctx, lib().ipt_cache_weights_get(ctx, scene, weights, table))
+
+
+def ipt_cache_eval(ctx, scene, n, x01, dirs, nrm, params7, upstream, rgb_out, dparams_out):
+    _check(ctx, lib().ipt_cache_eval(ctx, scene, n, x01, dirs, nrm, params7, upstream, rgb_out,
+                                     dparams_out))
+
+
+def ipt_cache_grad(ctx, scene, n, x01, dirs, nrm, params7, target, grad_weights, grad_table):
+    loss = C.c_double()
+    _check(ctx, lib().ipt_cache_grad(ctx, scene, n, x01, dirs, nrm, params7, target, C.byref(loss),
+                                     grad_weights, grad_table))
+    return loss.value
+
+
+def ipt_cache_train(ctx, scene, opts, iteration):
+    _check(ctx, lib().ipt_cache_train(ctx, scene, C.byref(opts), iteration))
+
+
+def ipt_cache_records(ctx, scene, out):
+    n = C.c_uint32()
+    _check(ctx, lib().ipt_cache_records(ctx, scene, C.byref(n), out))
+    return n.value
+
+
+def ipt_cache_status(ctx, scene):
+    st = ipt_cache_stats()
+    _check(ctx, lib().ipt_cache_status(ctx, scene, C.byref(st)))
+    return dict(active=bool(st.active), fell_back=bool(st.fell_back), records=st.records,
+                train_steps=st.train_steps, last_loss=st.last_loss, image_bias=st.image_bias,
+                grad_bias=st.grad_bias, lo=list(st.lo), hi=list(st.hi), res=list(st.res))
+
+
+def ipt_cache_bias(ctx, scene, opts, spp, iteration):
+    ib = C.c_double()
+    gb = C.c_double()
+    _check(ctx, lib().ipt_cache_bias(ctx, scene, C.byref(opts), spp, iteration, C.byref(ib),
+                                     C.byref(gb)))
+    return ib.value, gb.value

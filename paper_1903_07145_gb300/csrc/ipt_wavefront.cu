@@ -78,7 +78,12 @@ struct WfParams {
   int nee, mis, profile, loss_kind;
   uint32_t n_scenes;
   uint32_t seg_lo, seg_n;    // segment range of the chunk's gradient accumulators
+  uint32_t cache_k;          // vertex where the radiance cache ends paths (kNoCache: off)
+  int cache_record;          // training pass: record at cache_k, gather only from there on
+  CacheBuffers cb;
 };
+
+constexpr uint32_t kNoCache = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t set_iter(const WfParams& p) {
   const uint32_t it = p.iter_dev ? *p.iter_dev : p.iter;
@@ -120,6 +125,10 @@ __global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfPa
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     w.cnt[0] = n_slots;
     w.cnt[3] = 0;
+    if (lp.cache_k != kNoCache) {
+      lp.cb.counts[0] = 0;
+      lp.cb.counts[2] = min(lp.cb.counts[1], lp.cb.r_cap);
+    }
   }
   const uint32_t si = set_iter(lp);
   for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n_slots; slot += gridDim.x * blockDim.x) {
@@ -401,11 +410,13 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(const WfScene* tab, W
     const float4 bt = w.beta[slot];
     const uint32_t st = __float_as_uint(bt.w);
     const uint32_t k = state_k(st), b = state_scene(st);
-    bool cont = false, shadow = false;
+    bool cont = false, shadow = false, query = false, record = false;
+    uint32_t path_id = 0;
     NeeResult ne;
     float3 shc = f3(0.f, 0.f, 0.f);
     float3 beta = xyz(bt), wo = f3(0.f, 0.f, 0.f), org = f3(0.f, 0.f, 0.f);
     float pdf = 0.0f;
+    Vtx v;
     if (tri >= 0) {
       const WfScene& e = tab[b];
       const double W = *e.t.W;
@@ -416,8 +427,10 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(const WfScene* tab, W
       h.t = hh.y;
       h.u = hh.z;
       h.v = hh.w;
-      const Vtx v = make_vertex(e.s, h, xyz(rd), lp.profile);
-      if (v.prof > 0.0f) {
+      v = make_vertex(e.s, h, xyz(rd), lp.profile);
+      // a training pass gathers only what the path finds after the cache vertex
+      const bool gather = !lp.cache_record || k > lp.cache_k;
+      if (v.prof > 0.0f && gather) {
         const float wb = emission_weight(e.t, v, h.t, k > 0, light_on, rd.w, lp.mis);
         if (wb > 0.0f) {
           const float3 L = beta * xyz(__ldg(&e.t.emis[v.seg])) * (wb * v.prof);
@@ -425,14 +438,21 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(const WfScene* tab, W
           w.rad[slot] = make_float4(r.x + L.x, r.y + L.y, r.z + L.z, 0.0f);
         }
       }
-      if (k < lp.max_depth) {
+      if (k < lp.max_depth && k == lp.cache_k && !lp.cache_record) {
+        query = true;  // the cache supplies the reflected radiance from here
+      } else if (k < lp.max_depth) {
+        if (k == lp.cache_k) {
+          record = true;  // training record; the target is gathered with unit throughput
+          beta = f3(1.0f, 1.0f, 1.0f);
+        }
         uint32_t pid, smp;
         slot_pixel(e, p0, slot, lp.spp, pid, smp);
+        path_id = pid * lp.spp + smp;
         const PathRng rng = path_rng(e, pid, smp, si);
         const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
         const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
         const float4 sa = __ldg(&e.t.samp[v.seg]);
-        if (light_on) {
+        if (light_on && (!lp.cache_record || k >= lp.cache_k)) {
           ne = nee_prepare(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis, sa.y, sa.x);
           if (ne.valid) {
             const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
@@ -451,6 +471,21 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(const WfScene* tab, W
             cont = true;
           }
         }
+      }
+    }
+    if (lp.cache_k != kNoCache) {
+      const uint32_t qi = enqueue(&lp.cb.counts[0], query);
+      if (query) {
+        lp.cb.q.x[qi] = make_float4(v.x.x, v.x.y, v.x.z, __int_as_float(v.seg));
+        lp.cb.q.d[qi] = make_float4(v.wi.x, v.wi.y, v.wi.z, __uint_as_float(slot));
+        lp.cb.q.n[qi] = make_float4(v.ns.x, v.ns.y, v.ns.z, 0.0f);
+        lp.cb.q.u[qi] = make_float4(beta.x, beta.y, beta.z, 0.0f);
+      }
+      const uint32_t ri = enqueue(&lp.cb.counts[1], record);
+      if (record && ri < lp.cb.r_cap) {
+        lp.cb.r.x[ri] = make_float4(v.x.x, v.x.y, v.x.z, __int_as_float(v.seg));
+        lp.cb.r.d[ri] = make_float4(v.wi.x, v.wi.y, v.wi.z, __uint_as_float(slot));
+        lp.cb.r.n[ri] = make_float4(v.ns.x, v.ns.y, v.ns.z, __uint_as_float(path_id));
       }
     }
     const uint32_t sq = enqueue(&w.cnt[2], shadow);
@@ -611,11 +646,13 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfPar
     uint32_t pid, smp;
     slot_pixel(e, p0, slot, lp.spp, pid, smp);
     const float3 gp = pixel_grad(e, pid, inv_spp);
-    bool shadow = false;
+    bool shadow = false, query = false;
     NeeResult ne;
     float3 ge = f3(0.f, 0.f, 0.f), gm = f3(0.f, 0.f, 0.f), cn = f3(0.f, 0.f, 0.f);
     float spec = 0.0f, dsdr = 0.0f;
     int vseg = 0;
+    float4 cq = make_float4(0.f, 0.f, 0.f, 0.f);
+    Vtx cv;
     if (tri < 0) {
       finish_path(w, e, lp, slot, gp, sacc);
       w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
@@ -642,6 +679,12 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfPar
       if (k == lp.max_depth) {
         finish_path(w, e, lp, slot, gp, sacc);
         w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
+      } else if (k == lp.cache_k) {
+        // the cache's prediction and its parameter derivative close the path
+        query = true;
+        const float3 u = gp * beta;
+        cq = make_float4(u.x, u.y, u.z, 0.0f);
+        cv = v;
       } else if (light_on) {
         const PathRng rng = path_rng(e, pid, smp, si);
         const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
@@ -658,6 +701,15 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfPar
           dsdr = bv.sp.ds_dr;
           shadow = true;
         }
+      }
+    }
+    if (lp.cache_k != kNoCache) {
+      const uint32_t qi = enqueue(&lp.cb.counts[0], query);
+      if (query) {
+        lp.cb.q.x[qi] = make_float4(cv.x.x, cv.x.y, cv.x.z, __int_as_float(cv.seg));
+        lp.cb.q.d[qi] = make_float4(cv.wi.x, cv.wi.y, cv.wi.z, __uint_as_float(slot));
+        lp.cb.q.n[qi] = make_float4(cv.ns.x, cv.ns.y, cv.ns.z, 0.0f);
+        lp.cb.q.u[qi] = cq;
       }
     }
     const uint32_t sq = enqueue(&w.cnt[2], shadow);
@@ -778,6 +830,33 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_b(const WfScene* tab, WfPar
   acc_flush(sacc, np, w.blk);
 }
 
+// Paths closed by the cache: its prediction joins the earlier vertices'
+// carry (Eq. 6 through their BSDF factors), its parameter derivative goes to
+// the terminal segment's kd, ks and roughness, and the path finishes.
+__global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w) {
+  extern __shared__ float sacc[];
+  const uint32_t np = 10u * lp.seg_n;
+  acc_zero(sacc, np);
+  const uint32_t n = lp.cb.counts[0];
+  const float inv_spp = 1.0f / (float)lp.spp;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t slot = __float_as_uint(lp.cb.q.d[q].w);
+    const int seg = __float_as_int(lp.cb.q.x[q].w);
+    const uint32_t st = __float_as_uint(w.beta[slot].w);
+    const WfScene& e = tab[state_scene(st)];
+    add_to_carry(w, slot, xyz(lp.cb.qc[q]));
+    const float* dp = lp.cb.qdp + 8 * (size_t)q;
+    const int base = acc_ix(e, lp, seg, 0);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) atomicAdd(&sacc[base + j], dp[j]);
+    uint32_t pid, smp;
+    slot_pixel(e, p0, slot, lp.spp, pid, smp);
+    finish_path(w, e, lp, slot, pixel_grad(e, pid, inv_spp), sacc);
+    w.beta[slot].w = __uint_as_float(st | kDead);
+  }
+  acc_flush(sacc, np, w.blk);
+}
+
 // grad_acc[i] += sum over block rows (FP64), for the chunk's parameters.
 __global__ void wf_blk_reduce(const float* blk, int rows, uint32_t np, double* grad_acc) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
@@ -847,7 +926,17 @@ static WfParams wf_params(const TraceParams& tp, int loss_kind, uint32_t n_scene
   p.n_scenes = n_scenes;
   p.seg_lo = 0;
   p.seg_n = 0;
+  p.cache_k = kNoCache;
+  p.cache_record = 0;
+  p.cb = CacheBuffers{};
   return p;
+}
+
+static void wf_cache_params(WfParams& p, const CachePass* cache, uint32_t max_depth) {
+  if (!cache || cache->b_term >= max_depth) return;
+  p.cache_k = cache->b_term;
+  p.cache_record = cache->record;
+  p.cb = cache->buf;
 }
 
 static uint32_t total_pixels(const std::vector<WfScene>& tab) {
@@ -893,11 +982,17 @@ std::vector<WfChunk> wf_plan(const std::vector<WfScene>& tab, uint32_t cap, uint
 
 cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, int loss_kind, const uint32_t* iter_dev, const WfBuffers& wb,
-                       double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook) {
+                       double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook,
+                       const CachePass* cache) {
   const uint32_t ns = (uint32_t)tab.size();
-  const WfParams lp = wf_params(tp, loss_kind, ns, iter_dev);
+  WfParams lp = wf_params(tp, loss_kind, ns, iter_dev);
+  wf_cache_params(lp, cache, tp.max_depth);
+  const bool query = lp.cache_k != kNoCache && !lp.cache_record;
+  const bool record = lp.cache_k != kNoCache && lp.cache_record;
+  const uint32_t last_k = query ? lp.cache_k : tp.max_depth;
   const WfDev w = wf_dev(wb);
   if (wb.cap < tp.spp || ns == 0) return cudaErrorInvalidValue;
+  if (lp.cache_k != kNoCache && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
   const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
   const int red_grid = loss_partials_capacity(L);
@@ -911,7 +1006,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
       wf_camera<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
     }
     int cur = 0;
-    for (uint32_t k = 0; k <= tp.max_depth; ++k) {
+    for (uint32_t k = 0; k <= last_k; ++k) {
       {
         IPT_STAGE(8);
         if (wide)
@@ -923,7 +1018,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
         IPT_STAGE(10);
         wf_shade_fwd<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, w, cur);
       }
-      if (k < tp.max_depth && tp.nee) {
+      if (k < last_k && k < tp.max_depth && tp.nee && !(record && k < lp.cache_k)) {
         IPT_STAGE(9);
         if (wide)
           wf_trace<1, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
@@ -932,7 +1027,19 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
       }
       cur ^= 1;
     }
-    {
+    if (query) {
+      IPT_STAGE(16);
+      CacheOut o{};
+      o.rad = wb.rad;
+      cudaError_t e = cache_infer(cache->net, lp.cb.q, tab[0].t.mat_a, tab[0].t.mat_b, lp.cb.counts, wb.cap, o,
+                                  false, L.num_sms, st);
+      if (e != cudaSuccess) return e;
+    }
+    if (record) {
+      IPT_STAGE(18);
+      cudaError_t e = cache_targets(lp.cb, wb.rad, st);
+      if (e != cudaSuccess) return e;
+    } else {
       IPT_STAGE(14);
       wf_reduce<<<red_grid, kWfThreads, red_smem, st>>>(tab_dev, lp, c.p0, c.n_pix, w, loss_rows, first);
     }
@@ -945,11 +1052,16 @@ uint32_t wf_max_segments() { return (200u * 1024u) / (10u * sizeof(float)); }
 
 cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb, double* grad_acc,
-                       uint32_t* err, cudaStream_t st, const WfHook* hook) {
+                       uint32_t* err, cudaStream_t st, const WfHook* hook, const CachePass* cache) {
   const uint32_t ns = (uint32_t)tab.size();
   WfParams lp = wf_params(tp, 0, ns, iter_dev);
+  if (cache && cache->record) return cudaErrorInvalidValue;
+  wf_cache_params(lp, cache, tp.max_depth);
+  const bool query = lp.cache_k != kNoCache;
+  const uint32_t last_k = query ? lp.cache_k : tp.max_depth;
   const WfDev w = wf_dev(wb);
   if (wb.cap < tp.spp || !wb.aT || ns == 0) return cudaErrorInvalidValue;
+  if (query && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
   const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
   const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, wf_max_segments());
@@ -961,6 +1073,7 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
     cudaFuncSetAttribute(wf_adj_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     cudaFuncSetAttribute(wf_adj_connect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     cudaFuncSetAttribute(wf_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    cudaFuncSetAttribute(wf_adj_cache, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   }
   for (const WfChunk& c : chunks) {
     lp.seg_lo = c.seg_lo;
@@ -975,7 +1088,7 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
       wf_camera<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
     }
     int cur = 0;
-    for (uint32_t k = 0; k <= tp.max_depth; ++k) {
+    for (uint32_t k = 0; k <= last_k; ++k) {
       {
         IPT_STAGE(8);
         if (wide)
@@ -987,7 +1100,7 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
         IPT_STAGE(11);
         wf_adj_a<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
-      if (k < tp.max_depth) {
+      if (k < last_k) {
         if (tp.nee) {
           {
             IPT_STAGE(9);
@@ -1003,6 +1116,19 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
         wf_adj_b<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       cur ^= 1;
+    }
+    if (query) {
+      {
+        IPT_STAGE(17);
+        CacheOut o{};
+        o.c = lp.cb.qc;
+        o.dp = lp.cb.qdp;
+        e = cache_infer(cache->net, lp.cb.q, tab[0].t.mat_a, tab[0].t.mat_b, lp.cb.counts, wb.cap, o, true,
+                        L.num_sms, st);
+        if (e != cudaSuccess) return e;
+      }
+      IPT_STAGE(13);
+      wf_adj_cache<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w);
     }
     IPT_STAGE(14);
     wf_blk_reduce<<<(np + 127) / 128, 128, 0, st>>>(wb.blk, grid, np, grad_acc + 10u * c.seg_lo);

@@ -7,6 +7,7 @@
 
 #include <vector>
 
+#include "ipt_cache.h"
 #include "ipt_device.cuh"
 #include "ipt_internal.h"
 
@@ -31,6 +32,16 @@ struct WfScene {
   float* msq;
 };
 
+// Radiance cache in a pass: query mode ends paths at vertex b_term and adds
+// the cache's prediction; record mode (training) traces full paths and
+// records, at b_term, the inputs and the reflected radiance gathered after it.
+struct CachePass {
+  CacheNet net;
+  CacheBuffers buf;
+  uint32_t b_term;
+  int record;
+};
+
 struct WfChunk {
   uint32_t p0, n_pix;        // launch pixels of the chunk
   uint32_t seg_lo, seg_n;    // segment range its gradient accumulators cover
@@ -41,10 +52,11 @@ uint32_t wf_max_segments();
 
 cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, int loss_kind, const uint32_t* iter_dev, const WfBuffers& wb,
-                       double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook);
+                       double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook,
+                       const CachePass* cache = nullptr);
 
 cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb, double* grad_acc,
-                       uint32_t* err, cudaStream_t st, const WfHook* hook);
+                       uint32_t* err, cudaStream_t st, const WfHook* hook, const CachePass* cache = nullptr);
 
 }  // namespace ipt

@@ -46,6 +46,27 @@ class AdamOptions:
         return L.ipt_adam_opts(self.lr, self.beta1, self.beta2, self.eps, self.l1_emission)
 
 
+@dataclass
+class CacheOptions:
+    """Radiance-cache options (see ipt_cache_opts in include/ipt.h)."""
+    enabled: bool = True
+    b_term: int = 1
+    train_spp: int = 0
+    train_steps: int = 4
+    record_capacity: int = 1 << 21
+    lr: float = 1e-2
+    beta1: float = 0.9
+    beta2: float = 0.99
+    eps: float = 1e-15
+    bias_threshold: float = 0.0
+    init_seed: int = 1
+
+    def c(self) -> L.ipt_cache_opts:
+        return L.ipt_cache_opts(int(self.enabled), self.b_term, self.train_spp, self.train_steps,
+                                self.record_capacity, self.lr, self.beta1, self.beta2, self.eps,
+                                self.bias_threshold, self.init_seed)
+
+
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -204,6 +225,64 @@ class Tracer:
 
     def kernel_times(self, reset=False):
         return L.ipt_kernel_times(self.ctx, reset)
+
+    # --- radiance cache ---------------------------------------------------
+    def configure_cache(self, opts: CacheOptions):
+        L.ipt_cache_configure(self.ctx, self.sid, opts.c())
+
+    def cache_weights(self, table: bool = False):
+        w = np.zeros(L.IPT_CACHE_WEIGHTS, np.float32)
+        t = np.zeros(L.IPT_CACHE_TABLE_FLOATS, np.float32) if table else None
+        L.ipt_cache_weights_get(self.ctx, self.sid, _np_ptr(w), _np_ptr(t))
+        return (w, t) if table else w
+
+    def set_cache_weights(self, weights=None, table=None):
+        w = None if weights is None else np.ascontiguousarray(weights, np.float32).reshape(-1)
+        t = None if table is None else np.ascontiguousarray(table, np.float32).reshape(-1)
+        if w is not None and w.size != L.IPT_CACHE_WEIGHTS:
+            raise ValueError("weights must hold IPT_CACHE_WEIGHTS floats")
+        if t is not None and t.size != L.IPT_CACHE_TABLE_FLOATS:
+            raise ValueError("table must hold IPT_CACHE_TABLE_FLOATS floats")
+        L.ipt_cache_weights_set(self.ctx, self.sid, _np_ptr(w), _np_ptr(t))
+
+    def cache_eval(self, x01, dirs, nrm, params7, upstream=None):
+        """Prediction (n, 3) and, with upstream, d(upstream . prediction) / d params7 (n, 7)."""
+        dev = self.device
+        f = lambda a, k: torch.as_tensor(a, dtype=torch.float32, device=dev).reshape(-1, k).contiguous()
+        x, d, nn, p7 = f(x01, 3), f(dirs, 3), f(nrm, 3), f(params7, 7)
+        n = x.shape[0]
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        up = None if upstream is None else f(upstream, 3)
+        dp = None if upstream is None else torch.empty((n, 7), dtype=torch.float32, device=dev)
+        L.ipt_cache_eval(self.ctx, self.sid, n, _ptr(x), _ptr(d), _ptr(nn), _ptr(p7), _ptr(up),
+                         _ptr(rgb), _ptr(dp))
+        self.synchronize()
+        return rgb if dp is None else (rgb, dp)
+
+    def cache_grad(self, x01, dirs, nrm, params7, target, table=True):
+        """Relative-L2 loss of the rows and its gradients (weights, table)."""
+        dev = self.device
+        f = lambda a, k: torch.as_tensor(a, dtype=torch.float32, device=dev).reshape(-1, k).contiguous()
+        x, d, nn, p7, tg = f(x01, 3), f(dirs, 3), f(nrm, 3), f(params7, 7), f(target, 3)
+        gw = torch.empty(L.IPT_CACHE_WEIGHTS, dtype=torch.float32, device=dev)
+        gt = torch.empty(L.IPT_CACHE_TABLE_FLOATS, dtype=torch.float32, device=dev) if table else None
+        loss = L.ipt_cache_grad(self.ctx, self.sid, x.shape[0], _ptr(x), _ptr(d), _ptr(nn), _ptr(p7),
+                                _ptr(tg), _ptr(gw), _ptr(gt))
+        return loss, gw, gt
+
+    def cache_train(self, opts: TraceOptions, iteration: int = 0):
+        L.ipt_cache_train(self.ctx, self.sid, opts.c(), iteration)
+
+    def cache_records(self, capacity: int):
+        out = np.zeros((capacity, 16), np.float32)
+        n = L.ipt_cache_records(self.ctx, self.sid, _np_ptr(out))
+        return out[:n]
+
+    def cache_status(self):
+        return L.ipt_cache_status(self.ctx, self.sid)
+
+    def cache_bias(self, opts: TraceOptions, spp: int, iteration: int = 0):
+        return L.ipt_cache_bias(self.ctx, self.sid, opts.c(), spp, iteration)
 
     def counters(self, reset=False):
         return L.ipt_counters_read(self.ctx, reset)

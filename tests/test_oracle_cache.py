@@ -192,3 +192,33 @@ def test_cached_gradient_matches_central_differences(b_term):
         assert abs(fd - g) <= 1e-6 * max(abs(g), 1e-3 * np.abs(grad).max()), (k, fd, g)
     # the terminal segments' material rows move through the cache Jacobian
     assert np.abs(grad[:, :7]).sum() > 0
+
+
+def test_bf16_rounding_ties_to_even_and_matches_torch():
+    one = 1.0
+    assert K.bf16(one) == 1.0 and K.bf16(3.0) == 3.0
+    assert K.bf16(1 + 2 ** -8) == 1.0                      # halfway, even neighbour below
+    assert K.bf16(1 + 3 * 2 ** -8) == 1 + 2 ** -6          # halfway, even neighbour above
+    assert K.bf16(1 + 2 ** -8 + 2 ** -20) == 1 + 2 ** -7   # above halfway
+    assert K.bf16(-(1 + 3 * 2 ** -8)) == -(1 + 2 ** -6)
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(0).normal(size=10000).astype(np.float32) * 10.0 ** np.random.default_rng(1).integers(-6, 6, 10000)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(K.bf16(x), ref)
+
+
+def test_bf16_storage_changes_only_rounding():
+    """With BF16 storage the network is the FP64 one evaluated on rounded
+    operands: close to it, every stored activation is a BF16 value, and an
+    input that is already BF16 reaches the first layer unchanged."""
+    rng = np.random.default_rng(4)
+    W = [K.bf16(w) for w in K.init_weights(5)]
+    x = rng.normal(size=(50, K.IN_DIM))
+    y64, _ = K.mlp_forward(x, W)
+    y16, acts = K.mlp_forward(x, W, storage="bf16")
+    assert np.linalg.norm(y16 - y64) <= 2e-2 * np.linalg.norm(y64)
+    assert all(np.array_equal(a, K.bf16(a)) for a in acts[:-1])
+    xe = K.bf16(x)
+    _, acts_e = K.mlp_forward(xe, W, storage="bf16")
+    assert np.array_equal(acts_e[0], xe)
+    assert np.array_equal(acts_e[1], K.bf16(np.maximum(xe @ W[0], 0.0)))
