@@ -12,6 +12,11 @@ the flush is outside each step's CUDA-event bracket.  Rank 0 prints one JSON
 line.  Under torchrun each rank optimises its own independent room (weak
 scaling, no collective in the data path).
 
+``--cache B`` runs the same step with the learned radiance cache: paths end
+at vertex B (1 or 2) in the cache, which is trained online on 1 in 16
+full-length paths (a training pass per step, counted in the step's time;
+the metric still counts residual plus derivative paths).
+
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the reference arm of this comparison).
 """
@@ -171,7 +176,7 @@ def run_ours(args, rank, world, local):
         __graft_entry__.build()
     from paper_1903_07145_gb300 import scenes
     from paper_1903_07145_gb300 import _lib as L
-    from paper_1903_07145_gb300.tracer import AdamOptions, TraceOptions, Tracer
+    from paper_1903_07145_gb300.tracer import AdamOptions, CacheOptions, TraceOptions, Tracer
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -186,12 +191,16 @@ def run_ours(args, rank, world, local):
     target = tr.render(opts, view=-1, set_id=L.IPT_SET_TARGET, spp=w["target_spp"])
     tr.set_targets(target)
     tr.set_params(scenes.initial_params(sc, w["init"]))
+    if args.cache:
+        tr.configure_cache(CacheOptions(enabled=True, b_term=args.cache, train_spp=max(1, w["spp_r"] // 16),
+                                        train_steps=4))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     tuned = {}
     if args.integrator == "auto":
         from paper_1903_07145_gb300 import autotune
-        best, tuned = autotune.tune(tr, lambda: tr.loss_grad(opts, iteration=0))
+        best, tuned = autotune.tune(tr, lambda: tr.loss_grad(opts, iteration=0),
+                                    wavefront_only=bool(args.cache))
         tr.set_params(scenes.initial_params(sc, w["init"]))
     else:
         tr.configure(args.integrator)
@@ -224,6 +233,11 @@ def run_ours(args, rank, world, local):
         ms = float(t.item())
     ktimes = tr.kernel_times(reset=True)
     loss_end = tr.loss_grad(opts, iteration=10_000)[0]
+    # achievable gather bandwidth over a buffer the size of the scene's nodes
+    # and triangles (the traversal kernels' L2-resident working set)
+    info = tr.info()
+    footprint = max(1 << 16, info["n_nodes"] * NODE_BYTES + info["n_tri"] * TRI_BYTES)
+    l2_gather_gbs = L.ipt_probe_gather(local, footprint)
 
     # algorithmic traffic of the dominant kernel: node and triangle fetches per
     # launch, counted by a separate context with counters (same seeds, same paths)
@@ -231,11 +245,16 @@ def run_ours(args, rank, world, local):
     ct.configure(**chosen)
     ct.set_targets(target)
     ct.set_params(scenes.initial_params(sc, w["init"]))
+    if args.cache:  # the same cut paths as the timed context
+        ct.configure_cache(CacheOptions(enabled=True, b_term=args.cache, train_spp=max(1, w["spp_r"] // 16),
+                                        train_steps=4))
     ct.counters(reset=True)
     ct.render(opts, view=-1, set_id=L.IPT_SET_RESIDUAL, spp=w["spp_r"])
     fwd_cnt = ct.counters(reset=True)
     g = torch.full((tr.n_pix, 3), 1.0, device=dev)
     ct.backward(g, opts, set_id=L.IPT_SET_DERIVATIVE)
+    if args.cache:  # the step's training pass traces too
+        ct.cache_train(opts, iteration=0)
     adj_cnt = ct.counters(reset=True)
     ct.close()
 
@@ -299,6 +318,11 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes_per_launch": alg_bytes_launch,
                      "avg_launch_ms": dom_ms,
                      "units_per_step": {"node_visits": nodes, "tri_tests": tris, "rays": rays}},
+        "roofline_l2": {"bound": "l2_gather", "kernel": dom, "achieved": achieved, "peak": l2_gather_gbs,
+                        "unit": "GB/s", "frac": achieved / l2_gather_gbs if l2_gather_gbs else None,
+                        "probe_bytes": footprint,
+                        "peak_source": "ipt_probe_gather: random 64-byte line gathers over a buffer of the "
+                                       "scene's node + triangle bytes, measured in this run"},
         "e2e": {"value": paths_per_step() / e2e_s / 1e6, "unit": "Mpaths/s",
                 "h2d_bytes_per_step": int(host_target.numel() * 4),
                 "d2h_bytes_per_step": int(8 + host_params.nbytes)},
@@ -312,6 +336,113 @@ def run_ours(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def run_batch64(args):
+    """Aggregate fwd+adjoint Mpaths/s of one batch iteration over the 64
+    uneven rooms (one launch per stage over all rooms, replayed as a CUDA
+    graph)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1903_07145_gb300 import scenes
+    from paper_1903_07145_gb300.batch import SceneSet
+    from paper_1903_07145_gb300.tracer import AdamOptions, TraceOptions
+    t0 = time.perf_counter()
+    rooms = [scenes.batch_room(k, args.res_div) for k in range(64)]
+    gen_s = time.perf_counter() - t0
+    opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.batch_spp, max_depth=args.batch_depth)
+    ss = SceneSet(rooms, seed=1903)
+    ss.configure(integrator="wavefront", wavefront_slots=1 << 21, bvh_width=4)
+    for i, sc in enumerate(rooms):
+        ss.set_params(i, sc.gt_params)
+        ss.set_targets(i, ss.render(i, opts, spp=16))
+        ss.set_params(i, scenes.initial_params(sc, 0.5))
+    ss.make_batch()
+    adam = AdamOptions()
+    dev = ss.device
+    for _ in range(args.warmup):
+        ss.batch_step(opts, adam, want_losses=False)
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ss.batch_step(opts, adam, want_losses=False)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    pix = sum(c.width * c.height for sc in rooms for c in sc.cameras)
+    paths = 2 * args.batch_spp * pix
+    out = {"metric": METRIC, "value": paths / (ms * 1e-3) / 1e6, "unit": "Mpaths/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batch64_rooms_div{args.res_div}", "rooms": 64,
+                      "triangles": int(sum(sc.indices.shape[0] for sc in rooms)),
+                      "segments": int(sum(sc.n_segments for sc in rooms)), "pixels": int(pix),
+                      "spp_r": args.batch_spp, "spp_d": args.batch_spp, "max_depth": args.batch_depth,
+                      "l2": "256 MiB flush between timed steps (outside the step events)",
+                      "generation_s": gen_s},
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def run_time_to_error(args):
+    """Wall time to 1% parameter error.  Without --cache: the 64 rooms
+    (resolution / res_div) optimised together in the batch graph, against
+    the same rooms optimised one after another by the plain single-scene
+    step.  With --cache B: the 61k-triangle room (resolution / res_div) with
+    the cache and its bias monitor (fallback to the plain tracer above 2%),
+    against the plain tracer."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1903_07145_gb300 import convergence, scenes
+    from paper_1903_07145_gb300.tracer import AdamOptions, CacheOptions, TraceOptions
+    adam = AdamOptions(lr=args.lr)
+    res = {}
+    if args.cache:
+        sc = scenes.room_60k(1001)
+        for c in sc.cameras:
+            c.width //= args.res_div
+            c.height //= args.res_div
+        opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.batch_spp, max_depth=5)
+        for arm in ["plain", "cached"]:
+            tr, mask = convergence.prepare_single(sc, opts, target_spp=1024, seed=7)
+            tr.configure("wavefront")
+            if arm == "cached":
+                tr.configure_cache(CacheOptions(enabled=True, b_term=args.cache,
+                                                train_spp=max(1, args.batch_spp // 16), train_steps=4,
+                                                bias_threshold=0.02))
+            first, hist = convergence.time_to_error_single(
+                tr, mask, opts, adam, threshold=0.01, max_iters=args.max_iters, check_every=50,
+                monitor_every=args.monitor_every if arm == "cached" else 0, monitor_spp=args.monitor_spp)
+            res[arm] = {"first": first, "history": [(h[0], round(h[1], 3), round(h[2], 5), h[3]) for h in hist]}
+            tr.close()
+        workload = f"room_61k_tri_div{args.res_div}_cache_b{args.cache}"
+    else:
+        rooms = [scenes.batch_room(k, args.res_div) for k in range(64)]
+        opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.batch_spp, max_depth=args.batch_depth)
+        ss, masks = convergence.prepare(rooms, opts, target_spp=256, init=0.0, seed=7)
+        ss.configure(integrator="wavefront", wavefront_slots=1 << 21, bvh_width=4)
+        first, hist = convergence.time_to_error(ss, masks, opts, adam, threshold=0.01,
+                                                max_iters=args.max_iters, check_every=50)
+        res["batched"] = {"first": first, "history_last": hist[-1][:2]}
+        seq = []
+        for i, sc in enumerate(rooms):
+            tr, m = convergence.prepare_single(sc, opts, target_spp=256, seed=7)
+            tr.configure("wavefront", wavefront_slots=1 << 21, bvh_width=4)
+            f, _ = convergence.time_to_error_single(tr, m, opts, adam, threshold=0.01, max_iters=args.max_iters,
+                                                    check_every=50)
+            seq.append(f)
+            tr.close()
+        res["sequential_plain"] = {"first": seq}
+        workload = f"batch64_rooms_div{args.res_div}"
+    print(json.dumps({"metric": "time to 1% parameter error", "unit": "s", "workload": workload,
+                      "lr": args.lr, "spp": args.batch_spp, "results": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,6 +451,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--integrator", default="auto", choices=["auto", "megakernel", "wavefront"])
+    ap.add_argument("--cache", type=int, default=0, choices=[0, 1, 2],
+                    help="end paths at this vertex in the learned radiance cache (0: plain tracer)")
+    ap.add_argument("--workload", default="room61k", choices=["room61k", "batch64"],
+                    help="batch64: aggregate throughput of the 64 uneven rooms (a separate line)")
+    ap.add_argument("--time-to-error", action="store_true",
+                    help="wall time to 1%% parameter error (batched vs sequential, or cached vs plain)")
+    ap.add_argument("--res-div", type=int, default=1, help="resolution divisor of the extra workloads")
+    ap.add_argument("--batch-spp", type=int, default=8)
+    ap.add_argument("--batch-depth", type=int, default=3)
+    ap.add_argument("--lr", type=float, default=5e-3)
+    ap.add_argument("--max-iters", type=int, default=6000)
+    ap.add_argument("--monitor-every", type=int, default=250)
+    ap.add_argument("--monitor-spp", type=int, default=1024)
     ap.add_argument("--views", type=int, default=None,
                     help="profiling only: use the first V views (not a benchmark line)")
     ap.add_argument("--spp", type=int, default=None,
@@ -332,7 +476,17 @@ def main():
         WORKLOAD["spp_r"] = WORKLOAD["spp_d"] = args.spp
         WORKLOAD["workload"] += f"_spp{args.spp}"
         WORKLOAD["target_spp"] = min(WORKLOAD["target_spp"], 64)
+    if args.cache:
+        WORKLOAD["workload"] += f"_cache_b{args.cache}"
+        WORKLOAD["cache"] = dict(b_term=args.cache, train_spp=max(1, WORKLOAD["spp_r"] // 16), train_steps=4,
+                                 lr=1e-2)
     rank, world, local = dist_env()
+    if args.impl == "ours" and args.time_to_error:
+        run_time_to_error(args)
+        return
+    if args.impl == "ours" and args.workload == "batch64":
+        run_batch64(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

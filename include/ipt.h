@@ -469,15 +469,26 @@ ipt_status ipt_cache_records(ipt_ctx* ctx, int32_t scene, uint32_t* n_out, float
 
 ipt_status ipt_cache_status(ipt_ctx* ctx, int32_t scene, ipt_cache_stats* out);
 
-/* Bias of the cached estimator against the plain one, both with sample set 0
- * of `iteration` at `spp` samples per pixel (common random numbers up to the
- * cache vertex): image_bias = ||I_cache - I_plain|| / ||I_plain|| over all
- * views; grad_bias the same for the loss gradients (opts->spp_d derivative
- * samples; needs targets; -1 without).  When bias_threshold > 0 and either
+/* Bias of the cached estimator against the plain one, both with the sample
+ * sets of `iteration` at `spp` samples per pixel (common random numbers up to
+ * the cache vertex): image_bias = ||I_cache - I_plain|| / ||I_plain|| over all
+ * views (set 0); grad_bias the same for the loss gradients (residual and
+ * derivative sets at spp samples each; needs targets; -1 without).  opts
+ * gives max_depth, loss, nee, mis and profile.  When bias_threshold > 0 and either
  * exceeds it, the cache is turned off (stats.fell_back = 1).  Outputs are
  * host pointers (nullable). */
 ipt_status ipt_cache_bias(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t spp,
                           uint64_t iteration, double* image_bias, double* grad_bias);
+
+/* Measurement support (not part of the method).  Achievable bandwidth, in
+ * GB/s (1e9 bytes), of random 64-byte line gathers over a device buffer of
+ * `bytes` bytes on `device`: four independent gathers in flight per thread,
+ * 8 blocks of 256 threads per SM, best of three timed runs after a warm-up.
+ * This is the access pattern of BVH traversal, and with the size of a
+ * scene's node and triangle arrays the denominator of its roofline.  The
+ * buffer is allocated and freed inside the call.  Errors: bytes < 64 KiB or
+ * above 2^32 lines, out of memory, CUDA failures. */
+ipt_status ipt_probe_gather(int32_t device, uint64_t bytes, double* gbs_out);
 
 #ifdef __cplusplus
 }

@@ -30,6 +30,7 @@ EXPORTED = [
     "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy",
     "ipt_cache_configure", "ipt_cache_weights_set", "ipt_cache_weights_get", "ipt_cache_eval",
     "ipt_cache_grad", "ipt_cache_train", "ipt_cache_records", "ipt_cache_status", "ipt_cache_bias",
+    "ipt_probe_gather",
 ]
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox",
@@ -140,6 +141,7 @@ def lib():
                 "ipt_cache_status": [P, I32, C.POINTER(ipt_cache_stats)],
                 "ipt_cache_bias": [P, I32, C.POINTER(ipt_trace_opts), U32, U64, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)],
+                "ipt_probe_gather": [I32, U64, C.POINTER(C.c_double)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -353,3 +355,9 @@ def ipt_cache_bias(ctx, scene, opts, spp, iteration):
     _check(ctx, lib().ipt_cache_bias(ctx, scene, C.byref(opts), spp, iteration, C.byref(ib),
                                      C.byref(gb)))
     return ib.value, gb.value
+
+
+def ipt_probe_gather(device, nbytes):
+    gbs = C.c_double()
+    _check(None, lib().ipt_probe_gather(device, nbytes, C.byref(gbs)))
+    return gbs.value

@@ -31,9 +31,12 @@ def _time_once(tracer, run):
     return a.elapsed_time(b)
 
 
-def tune(tracer, run, candidates=DEFAULT_CANDIDATES, repeats=1):
+def tune(tracer, run, candidates=DEFAULT_CANDIDATES, repeats=1, wavefront_only=False):
     """run(): one evaluation of the workload on `tracer` (no host sync
-    needed).  Returns (best config dict, {repr(config): ms})."""
+    needed).  Returns (best config dict, {repr(config): ms}).  wavefront_only
+    skips megakernel candidates (the cached passes always run wavefront)."""
+    if wavefront_only:
+        candidates = [c for c in candidates if c.get("integrator", "wavefront") != "megakernel"]
     results = {}
     best, best_ms = None, float("inf")
     for cfg in candidates:

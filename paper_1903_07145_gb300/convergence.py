@@ -6,7 +6,10 @@ the diffuse albedo and emission of every segment (the quantities the paper
 evaluates, Table 1); specular albedo and roughness are held at their true
 values through the free mask, because without a Fresnel term a rough GGX
 lobe can stand in for a Lambertian one and a few views cannot tell them
-apart.  Iterations run as batch-graph replays; the error is read every
+apart.  The error covers segments that a pixel centre sees, except the
+diffuse albedo of emitting segments: an emitter's appearance is almost all
+emission (Sec. 4 notes the same emission/albedo trade-off for objects in
+few pixels), so its albedo is left free but not scored.  Iterations run as batch-graph replays; the error is read every
 `check_every` iterations (the reads are outside the timed iterations).
 """
 from __future__ import annotations
@@ -28,6 +31,15 @@ def diffuse_and_emission_mask(scene) -> np.ndarray:
     return m
 
 
+def scored_mask(scene, free, visible) -> np.ndarray:
+    """Parameters the error scores: free ones of visible segments, without
+    the diffuse albedo of emitting segments."""
+    m = free.copy()
+    m[~visible] = False
+    m[np.asarray(scene.light_segments, int), 0:3] = False
+    return m
+
+
 def prepare(scenes, opts: TraceOptions, target_spp: int = 1024, init: float = 0.0, seed: int = 0,
             configure=None):
     """Context with every scene uploaded, targets rendered from the ground
@@ -46,9 +58,7 @@ def prepare(scenes, opts: TraceOptions, target_spp: int = 1024, init: float = 0.
         tr = Tracer(sc)
         vis = metrics.visible_segments(tr, sc)
         tr.close()
-        m = free.copy()
-        m[~vis] = False
-        masks.append(m)
+        masks.append(scored_mask(sc, free, vis))
     return ss, masks
 
 
@@ -76,4 +86,51 @@ def time_to_error(ss: SceneSet, masks, opts: TraceOptions, adam: AdamOptions, th
         for i, e in enumerate(errs):
             if first[i] is None and e <= threshold:
                 first[i] = (it, elapsed)
+    return first, history
+
+
+def prepare_single(scene, opts: TraceOptions, target_spp: int = 1024, init: float = 0.0, seed: int = 0,
+                   device: int = 0):
+    """One-scene counterpart of prepare(): a Tracer with targets rendered from
+    the ground truth (sample set 2) and the unknowns reset to `init`."""
+    tr = Tracer(scene, device=device, seed=seed)
+    tr.set_params(scene.gt_params)
+    tr.set_targets(tr.render(opts, view=-1, set_id=2, spp=target_spp))
+    free = diffuse_and_emission_mask(scene)
+    p0 = scene.gt_params.copy()
+    p0[free] = init
+    tr.set_params(p0, free_mask=free.astype(np.uint8))
+    return tr, scored_mask(scene, free, metrics.visible_segments(tr, scene))
+
+
+def time_to_error_single(tr: Tracer, mask, opts: TraceOptions, adam: AdamOptions, threshold: float = 0.01,
+                         max_iters: int = 20000, check_every: int = 50, monitor_every: int = 0,
+                         monitor_spp: int = 64):
+    """ipt_step on one scene until its parameter error falls to the
+    threshold.  With the radiance cache active, every `monitor_every`
+    iterations ipt_cache_bias compares the cached and plain estimators (set 0
+    at monitor_spp, the step's spp_d) and turns the cache off once the bias
+    exceeds the cache's threshold; the monitor's time counts.  Returns
+    ((iterations, seconds) or None, history of (iteration, seconds, error,
+    cache active))."""
+    history = []
+    elapsed = 0.0
+    it = 0
+    first = None
+    cached = monitor_every > 0
+    while it < max_iters and first is None:
+        torch.cuda.synchronize(tr.device)
+        t0 = time.perf_counter()
+        for _ in range(check_every):
+            tr.step(opts, adam, want_loss=False)
+            it += 1
+            if cached and it % monitor_every == 0:
+                tr.cache_bias(opts, monitor_spp, iteration=1_000_000 + it)
+                cached = tr.cache_status()["active"]
+        torch.cuda.synchronize(tr.device)
+        elapsed += time.perf_counter() - t0
+        err = metrics.param_error(tr.get_params(), tr.scene.gt_params, mask)
+        history.append((it, elapsed, err, cached))
+        if err <= threshold:
+            first = (it, elapsed)
     return first, history

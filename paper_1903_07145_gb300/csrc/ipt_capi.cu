@@ -1771,12 +1771,15 @@ ipt_status ipt_cache_bias(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opt
     return fail(ctx, IPT_ERR_OUT_OF_MEMORY, "bias buffers");
   }
   const bool was = c->active;
-  const bool with_grad = s->target != nullptr && opts->spp_d > 0 && opts->spp_r > 0;
+  const bool with_grad = s->target != nullptr;
+  ipt_trace_opts go = *opts;  // gradients at the monitor's sample count too
+  go.spp_r = spp;
+  go.spp_d = spp;
   for (int k = 0; k < 2 && st == IPT_OK; ++k) {
     c->active = k == 1;
     st = ipt_render(ctx, scene, -1, opts, IPT_SET_RESIDUAL, spp, iteration, nullptr, nullptr, img + k * npx, nullptr);
     if (st == IPT_OK && with_grad)
-      st = loss_grad_async(ctx, scene, s, opts, iteration, grad + k * np, 0, s->n_pix, s->n_pix);
+      st = loss_grad_async(ctx, scene, s, &go, iteration, grad + k * np, 0, s->n_pix, s->n_pix);
   }
   c->active = was;
   std::vector<float> hi(2 * npx), hg(2 * np);

@@ -302,6 +302,31 @@ def room_500k(seed: int = 1002, n_views: int = 16, width: int = 640, height: int
                        name="room_516k_tri")
 
 
+def batch_room(k: int, res_div: int = 1) -> Scene:
+    """Room k of the 64-scene batch (seed 5000 + k): triangles log-uniform in
+    [5k, 500k], segments uniform in [10, 200], lights in [1, 8], views in
+    [1, 8] at one of 160x120, 320x240, 640x480 (each divided by res_div).
+    Segments = 4 room + lights + cuboids, so the cuboid count follows; the
+    floor grows with it (3 m^2 per cuboid, at least 8 x 6 m, so that
+    placement by rejection stays quick), and the cuboid and room-face
+    subdivisions are set to land near the drawn triangle count."""
+    rng = np.random.default_rng(5000 + k)
+    tris = float(np.exp(rng.uniform(np.log(5e3), np.log(5e5))))
+    n_seg = int(rng.integers(10, 201))
+    n_lights = int(rng.integers(1, 9))
+    n_views = int(rng.integers(1, 9))
+    w, h = [(160, 120), (320, 240), (640, 480)][int(rng.integers(0, 3))]
+    n_cub = max(1, n_seg - 4 - n_lights)
+    area = max(48.0, 3.0 * n_cub)
+    X, Z = math.sqrt(area * 4.0 / 3.0), math.sqrt(area * 3.0 / 4.0)
+    room_sub = int(np.clip(round(math.sqrt(tris * 0.05 / 12.0)), 2, 64))
+    rest = max(tris - 12 * room_sub ** 2 - 2 * n_lights, 12.0 * n_cub)
+    cub_sub = max(1, int(round(math.sqrt(rest / (12.0 * n_cub)))))
+    return indoor_room(5000 + k, room=(X, 3.0, Z), n_cuboids=n_cub, cuboid_sub=cub_sub, room_sub=room_sub,
+                       n_lights=n_lights, n_views=n_views, width=max(8, w // res_div),
+                       height=max(6, h // res_div), name=f"batch_room_{k}")
+
+
 def furnace_box(size=1.0, nsub=1, rho=0.5, emission=0.25, width=8, height=8) -> Scene:
     """Closed box (all six faces inward, one segment), Lambertian albedo rho,
     no specular, uniform emission on every face; camera inside."""
