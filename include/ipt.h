@@ -102,7 +102,7 @@ typedef struct {
  *   wavefront_slots: path slots per wavefront chunk (0 = 1 << 20); rounded
  *     down to whole pixels.
  *   trace_steps: node visits per refill round of the persistent traversal
- *     (0 = 32).
+ *     (0 = 16).
  *   blocks_per_sm: persistent blocks per SM for the wavefront kernels (0 =
  *     as many as fit).
  *   bvh_width: BVH used by the wavefront traversal: 2 = binary nodes with

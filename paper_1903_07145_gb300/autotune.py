@@ -16,7 +16,7 @@ import torch
 DEFAULT_CANDIDATES = (
     [dict(integrator="megakernel")]
     + [dict(integrator="wavefront", wavefront_slots=s, trace_steps=k, bvh_width=b)
-       for b, s, k in itertools.product([2, 4], [1 << 20, 1 << 21], [16, 32])]
+       for b, s, k in itertools.product([2, 4], [1 << 20, 1 << 21], [8, 16])]
 )
 
 

@@ -1074,12 +1074,9 @@ ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg) {
     wf_release(ctx);
   }
   ctx->cfg = *cfg;
-  ctx->L.wf_steps = cfg->trace_steps ? (int)cfg->trace_steps : 32;
-  if (cfg->blocks_per_sm) {
-    ctx->L.wf_blocks_per_sm = (int)cfg->blocks_per_sm;
-  } else {
-    IPT_CK(ipt::wf_init(&ctx->L));
-  }
+  ctx->L.wf_steps = cfg->trace_steps ? (int)cfg->trace_steps : 16;
+  ctx->L.wf_fixed_blocks = (int)cfg->blocks_per_sm;
+  IPT_CK(ipt::wf_init(&ctx->L));
   return IPT_OK;
 }
 

@@ -221,24 +221,71 @@ __device__ __forceinline__ void box2(const RayPre& r, float3 oinv, float4 n0, fl
 // 4-wide node with 8-bit child boxes (see the scene builder): entry distances
 // of its children (or +inf), and their links.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float q_byte(uint32_t w, int i) {
-  // byte i of w as a float, via the 2^23 mantissa trick (exact)
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)i)) - 8388608.0f;
+
+// Three-input minimum / maximum (one instruction on sm_100 and later; NaN
+// operands are ignored as by fminf / fmaxf).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
 }
 
+// One 64-byte node as two 256-bit read-only loads (the node array is 64-byte
+// aligned: cudaMalloc base, 64-byte records).
+__device__ __forceinline__ void load_node4(const uint4* p, uint4& a, uint4& c, uint4& qa, uint4& qb) {
+  asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w)
+      : "l"(p));
+  asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(qa.x), "=r"(qa.y), "=r"(qa.z), "=r"(qa.w), "=r"(qb.x), "=r"(qb.y), "=r"(qb.z), "=r"(qb.w)
+      : "l"(p + 2));
+}
+
+// Byte i of w as the float 1 + byte * 2^-15 (the byte placed in mantissa
+// bits 8-15 of 1.0; exact).
+__device__ __forceinline__ float q_unit(uint32_t w, int i) {
+  return __uint_as_float(__byte_perm(w, 0x3F800000u, 0x7604u | ((uint32_t)i << 4)));
+}
+
+// Slab test of the (up to) four children.
+//  * Near / far planes: the plane distance t(q) = (origin + q * scale - o) / d
+//    is monotonic in the byte q, so for each axis the near plane is the lower
+//    byte when d >= 0 and the upper byte when d < 0: one select per axis and
+//    node instead of a min/max per child and axis.
+//  * One instruction per plane after the byte extraction: with
+//    u = 1 + q * 2^-15 (q_unit), t(q) = u * A + B where A = 2^15 * scale / d and
+//    B = (origin - o) / d - A, evaluated as one fma.  Rounding B, and the
+//    margins below, add absolute errors of at most 2^-24 |A| each to a plane
+//    distance of that axis (beyond the relative rounding the far-plane factor
+//    1.0000005 covers).  Each axis's near planes therefore use B - 2^-22 |A|
+//    and its far planes B + 2^-22 |A| (a widening of 2^-7 of a code on each
+//    side, a few times the error bound): a child box is never missed because
+//    of it.
 __device__ __forceinline__ uint32_t node4_children(const SceneDev& s, int node, const RayPre& r, float tmax,
                                                    float tn[4], int ref[4]) {
-  const uint4 a = __ldg(&s.nodes4[4 * node + 0]);
-  const uint4 c = __ldg(&s.nodes4[4 * node + 1]);
-  const uint4 qa = __ldg(&s.nodes4[4 * node + 2]);
-  const uint4 qb = __ldg(&s.nodes4[4 * node + 3]);
-  const float sx = __uint_as_float((a.w & 0xffu) << 23);
-  const float sy = __uint_as_float(((a.w >> 8) & 0xffu) << 23);
-  const float sz = __uint_as_float(((a.w >> 16) & 0xffu) << 23);
+  uint4 a, c, qa, qb;
+  load_node4(&s.nodes4[4 * node], a, c, qa, qb);
+  // 2^15 * scale: the stored biased exponent plus 15 (the builder keeps the
+  // exponent at most 239)
+  const float sx = __uint_as_float(((a.w & 0xffu) + 15u) << 23);
+  const float sy = __uint_as_float((((a.w >> 8) & 0xffu) + 15u) << 23);
+  const float sz = __uint_as_float((((a.w >> 16) & 0xffu) + 15u) << 23);
   const int n = (int)(a.w >> 24);
-  const float ax = sx * r.inv.x, bx = (__uint_as_float(a.x) - r.o.x) * r.inv.x;
-  const float ay = sy * r.inv.y, by = (__uint_as_float(a.y) - r.o.y) * r.inv.y;
-  const float az = sz * r.inv.z, bz = (__uint_as_float(a.z) - r.o.z) * r.inv.z;
+  const float Ax = sx * r.inv.x, Bx = fmaf(__uint_as_float(a.x) - r.o.x, r.inv.x, -Ax);
+  const float Ay = sy * r.inv.y, By = fmaf(__uint_as_float(a.y) - r.o.y, r.inv.y, -Ay);
+  const float Az = sz * r.inv.z, Bz = fmaf(__uint_as_float(a.z) - r.o.z, r.inv.z, -Az);
+  const float Bnx = fmaf(fabsf(Ax), -0x1p-22f, Bx), Bfx = fmaf(fabsf(Ax), 0x1p-22f, Bx);
+  const float Bny = fmaf(fabsf(Ay), -0x1p-22f, By), Bfy = fmaf(fabsf(Ay), 0x1p-22f, By);
+  const float Bnz = fmaf(fabsf(Az), -0x1p-22f, Bz), Bfz = fmaf(fabsf(Az), 0x1p-22f, Bz);
+  const bool nx = r.inv.x < 0.0f, ny = r.inv.y < 0.0f, nz = r.inv.z < 0.0f;
+  const uint32_t nwx = nx ? qa.y : qa.x, fwx = nx ? qa.x : qa.y;
+  const uint32_t nwy = ny ? qa.w : qa.z, fwy = ny ? qa.z : qa.w;
+  const uint32_t nwz = nz ? qb.y : qb.x, fwz = nz ? qb.x : qb.y;
   ref[0] = (int)c.x;
   ref[1] = (int)c.y;
   ref[2] = (int)c.z;
@@ -246,12 +293,11 @@ __device__ __forceinline__ uint32_t node4_children(const SceneDev& s, int node, 
   uint32_t mask = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const float tlx = fmaf(q_byte(qa.x, i), ax, bx), thx = fmaf(q_byte(qa.y, i), ax, bx);
-    const float tly = fmaf(q_byte(qa.z, i), ay, by), thy = fmaf(q_byte(qa.w, i), ay, by);
-    const float tlz = fmaf(q_byte(qb.x, i), az, bz), thz = fmaf(q_byte(qb.y, i), az, bz);
-    const float tnear = fmaxf(fmaxf(fminf(tlx, thx), fminf(tly, thy)), fmaxf(fminf(tlz, thz), 0.0f));
-    const float tfar =
-        fminf(fminf(fmaxf(tlx, thx), fmaxf(tly, thy)), fminf(fmaxf(tlz, thz), tmax)) * 1.0000005f;
+    const float tnx = fmaf(q_unit(nwx, i), Ax, Bnx), tfx = fmaf(q_unit(fwx, i), Ax, Bfx);
+    const float tny = fmaf(q_unit(nwy, i), Ay, Bny), tfy = fmaf(q_unit(fwy, i), Ay, Bfy);
+    const float tnz = fmaf(q_unit(nwz, i), Az, Bnz), tfz = fmaf(q_unit(fwz, i), Az, Bfz);
+    const float tnear = max3f(tnx, tny, fmaxf(tnz, 0.0f));
+    const float tfar = min3f(tfx, tfy, fminf(tfz, tmax)) * 1.0000005f;
     const bool hit = i < n && tnear <= tfar;
     tn[i] = hit ? tnear : __int_as_float(0x7f800000);
     mask |= hit ? (1u << i) : 0u;

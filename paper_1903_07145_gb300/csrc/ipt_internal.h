@@ -82,8 +82,10 @@ struct Launcher {
   int num_sms = 0;
   int fwd_blocks_per_sm = 0;
   int adj_blocks_per_sm[4] = {0, 0, 0, 0};
-  int wf_blocks_per_sm = 0;
-  int wf_steps = 32;  // node visits per refill round of the persistent traversal
+  int wf_blocks_per_sm = 0;  // traversal kernels
+  int wf_fixed_blocks = 0;   // configured blocks per SM for every wavefront kernel (0: by occupancy)
+  int wf_max_rows = 0;       // gradient rows any adjoint stage may use (blocks of its widest grid)
+  int wf_steps = 16;  // node visits per refill round of the persistent traversal
 };
 
 // Wavefront state (device), sized for `cap` path slots per chunk.

@@ -164,19 +164,38 @@ __global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfPa
 // `cur` into w.hit; 1: shadow rays, adding the forward contribution of the
 // unoccluded ones; 2: shadow rays, visibility flag only (adjoint).
 // ---------------------------------------------------------------------------
+// Traversal stack: the top kShortStack entries of each lane live in shared
+// memory (entry e of thread t at [e * kWfThreads + t], so a warp's accesses
+// fall in distinct banks whatever its lanes' depths); deeper entries spill to
+// a per-lane local array.  An entry is (node link, entry distance bits).
+constexpr int kShortStack = 12;
+
 struct Trav {
   RayPre r;
   float3 oinv;
   float tmax;
   int skip_a, skip_b;
   int node, sp;
-  int stack[kStackSize];
-  float stack_t[kStackSize];  // entry distance of each pushed child (4-wide)
+  uint2 deep[kStackSize - kShortStack];
   int best, best_orig;
   float bt, bu, bv;
   bool occluded;
   uint32_t n_nodes, n_tests;
 };
+
+__device__ __forceinline__ void st_push(uint2* sh, Trav& T, int ref, float t) {
+  const uint2 e = make_uint2((uint32_t)ref, __float_as_uint(t));
+  if (T.sp < kShortStack)
+    sh[T.sp * kWfThreads] = e;
+  else
+    T.deep[T.sp - kShortStack] = e;
+  ++T.sp;
+}
+
+__device__ __forceinline__ uint2 st_pop(const uint2* sh, Trav& T) {
+  --T.sp;
+  return T.sp < kShortStack ? sh[T.sp * kWfThreads] : T.deep[T.sp - kShortStack];
+}
 
 __device__ __forceinline__ void trav_init(Trav& T, float3 o, float3 d, float tmax, int skip_a, int skip_b) {
   T.r = ray_pre(o, d);
@@ -195,9 +214,9 @@ __device__ __forceinline__ void trav_init(Trav& T, float3 o, float3 d, float tma
 }
 
 template <bool kAny>
-__device__ __forceinline__ bool leaf_tests(const SceneDev& s, Trav& T) {
+__device__ __forceinline__ bool leaf_tests(const SceneDev& s, Trav& T, int leaf) {
   int first, count;
-  decode_leaf(T.node, first, count);
+  decode_leaf(leaf, first, count);
   T.n_tests += count;
   for (int i = first; i < first + count; ++i) {
     if (i == T.skip_a || i == T.skip_b) continue;
@@ -226,7 +245,7 @@ __device__ __forceinline__ bool leaf_tests(const SceneDev& s, Trav& T) {
 
 // Binary nodes: runs up to `steps` node visits; true when the traversal is over.
 template <bool kAny>
-__device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, int steps, uint32_t* err) {
+__device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, uint2* sh, int steps, uint32_t* err) {
   for (int it = 0; it < steps; ++it) {
     if (T.node >= 0) {
       ++T.n_nodes;
@@ -247,10 +266,10 @@ __device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, int steps,
           return true;
         }
         if (!kAny && t1 < t0) {
-          T.stack[T.sp++] = c0;
+          st_push(sh, T, c0, 0.0f);
           T.node = c1;
         } else {
-          T.stack[T.sp++] = c1;
+          st_push(sh, T, c1, 0.0f);
           T.node = c0;
         }
         continue;
@@ -259,11 +278,11 @@ __device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, int steps,
         T.node = h0 ? c0 : c1;
         continue;
       }
-    } else if (leaf_tests<kAny>(s, T)) {
+    } else if (leaf_tests<kAny>(s, T, T.node)) {
       return true;
     }
     if (T.sp == 0) return true;
-    T.node = T.stack[--T.sp];
+    T.node = (int)st_pop(sh, T).x;
   }
   return false;
 }
@@ -271,7 +290,7 @@ __device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, int steps,
 // 4-wide quantized nodes: hit children nearest first (any-hit: slot order);
 // popped entries farther than the current hit are skipped.
 template <bool kAny>
-__device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps, uint32_t* err) {
+__device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh, int steps, uint32_t* err) {
   for (int it = 0; it < steps; ++it) {
     if (T.node >= 0) {
       ++T.n_nodes;
@@ -290,11 +309,7 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps,
           sort4(tn, ref);
 #pragma unroll
           for (int i = 3; i >= 1; --i)
-            if (i < k) {
-              T.stack[T.sp] = ref[i];
-              T.stack_t[T.sp] = tn[i];
-              ++T.sp;
-            }
+            if (i < k) st_push(sh, T, ref[i], tn[i]);
           T.node = ref[0];
         } else {
           const int first = __ffs(mask) - 1;
@@ -305,25 +320,28 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, int steps,
             if (i == first)
               next = ref[i];
             else
-              T.stack[T.sp++] = ref[i];
+              st_push(sh, T, ref[i], 0.0f);
           }
           T.node = next;
         }
         continue;
       }
-    } else if (leaf_tests<kAny>(s, T)) {
+    } else if (leaf_tests<kAny>(s, T, T.node)) {
       return true;
     }
+    uint2 e;
     for (;;) {
       if (T.sp == 0) return true;
-      --T.sp;
-      if (kAny || T.stack_t[T.sp] <= T.bt * 1.0000005f) break;
+      e = st_pop(sh, T);
+      if (kAny || __uint_as_float(e.y) <= T.bt * 1.0000005f) break;
     }
-    T.node = T.stack[T.sp];
+    T.node = (int)e.x;
   }
   return false;
 }
 
+// Lanes run rounds of `steps` node visits; between rounds the warp fetches
+// new rays for the lanes whose ray has finished (one atomic per warp).
 template <int kMode, bool kWide>
 __global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev w, int cur, int steps,
                                                        uint32_t* err) {
@@ -337,6 +355,8 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev
   uint32_t* fetch = kAny ? &w.cnt[4] : &w.cnt[3];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  __shared__ uint2 s_stack[kShortStack * kWfThreads];
+  uint2* sh = s_stack + threadIdx.x;
   Trav T;
   SceneDev sd = tab[0].s;
   int64_t item = -1;
@@ -368,7 +388,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev
       }
     }
     if (__all_sync(0xffffffffu, item < 0)) break;
-    if (item >= 0 && (kWide ? trav_run4<kAny>(sd, T, steps, err) : trav_run2<kAny>(sd, T, steps, err))) {
+    const bool done =
+        item >= 0 && (kWide ? trav_run4<kAny>(sd, T, sh, steps, err) : trav_run2<kAny>(sd, T, sh, steps, err));
+    if (done) {
       const uint32_t i = (uint32_t)item;
       count_ray(sd, kAny ? 1 : 0, T.n_nodes, T.n_tests);
       if (kMode == 0) {
@@ -898,7 +920,18 @@ static WfDev wf_dev(const WfBuffers& b) {
 
 static int wf_grid(const Launcher& L) { return L.num_sms * L.wf_blocks_per_sm; }
 
-int wf_max_blocks(const Launcher& L) { return wf_grid(L); }
+// One full wave of a grid-stride kernel: every SM holds as many blocks as fit
+// (or the configured count), so each SM gets the same share of the work and
+// there is no partial second wave.
+template <typename K>
+static int one_wave(const Launcher& L, K kernel, size_t smem) {
+  if (L.wf_fixed_blocks > 0) return L.num_sms * L.wf_fixed_blocks;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kWfThreads, smem) != cudaSuccess || b < 1) b = 1;
+  return L.num_sms * b;
+}
+
+int wf_max_blocks(const Launcher& L) { return std::max(wf_grid(L), L.wf_max_rows); }
 
 // Brackets a stage launch for the caller's timing hook (kernel ids of ipt.h).
 struct StageMark {
@@ -995,6 +1028,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
   if (lp.cache_k != kNoCache && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
   const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
+  const int grid_cam = one_wave(L, wf_camera, 0), grid_sh = one_wave(L, wf_shade_fwd, 0);
   const int red_grid = loss_partials_capacity(L);
   const size_t red_smem = sizeof(double) * ns;
   const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, 0xffffffffu);
@@ -1003,7 +1037,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
     const uint32_t slots = c.n_pix * tp.spp;
     {
       IPT_STAGE(7);
-      wf_camera<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
+      wf_camera<<<grid_cam, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
     }
     int cur = 0;
     for (uint32_t k = 0; k <= last_k; ++k) {
@@ -1016,7 +1050,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
       }
       {
         IPT_STAGE(10);
-        wf_shade_fwd<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, w, cur);
+        wf_shade_fwd<<<grid_sh, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       if (k < last_k && k < tp.max_depth && tp.nee && !(record && k < lp.cache_k)) {
         IPT_STAGE(9);
@@ -1064,6 +1098,7 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
   if (query && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
   const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
+  const int grid_cam = one_wave(L, wf_camera, 0);
   const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, wf_max_segments());
   uint32_t max_np = 0;
   for (const WfChunk& c : chunks) max_np = std::max(max_np, 10u * c.seg_n);
@@ -1080,12 +1115,18 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
     lp.seg_n = c.seg_n;
     const uint32_t np = 10u * c.seg_n;
     const size_t sm = np * sizeof(float);
-    cudaError_t e = cudaMemsetAsync(wb.blk, 0, (size_t)grid * np * sizeof(float), st);
+    // each adjoint stage runs one wave at its own occupancy for this
+    // accumulator size; block b of every stage adds into gradient row b
+    const int g_a = one_wave(L, wf_adj_a, sm), g_c = one_wave(L, wf_adj_connect, sm);
+    const int g_b = one_wave(L, wf_adj_b, sm), g_q = one_wave(L, wf_adj_cache, sm);
+    const int rows = std::max(std::max(g_a, g_c), std::max(g_b, g_q));
+    if (rows > wf_max_blocks(L)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(wb.blk, 0, (size_t)rows * np * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const uint32_t slots = c.n_pix * tp.spp;
     {
       IPT_STAGE(7);
-      wf_camera<<<grid, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
+      wf_camera<<<grid_cam, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
     }
     int cur = 0;
     for (uint32_t k = 0; k <= last_k; ++k) {
@@ -1098,7 +1139,7 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
       }
       {
         IPT_STAGE(11);
-        wf_adj_a<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
+        wf_adj_a<<<g_a, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       if (k < last_k) {
         if (tp.nee) {
@@ -1110,10 +1151,10 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
               wf_trace<2, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
           }
           IPT_STAGE(12);
-          wf_adj_connect<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, w);
+          wf_adj_connect<<<g_c, kWfThreads, sm, st>>>(tab_dev, lp, w);
         }
         IPT_STAGE(13);
-        wf_adj_b<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
+        wf_adj_b<<<g_b, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       cur ^= 1;
     }
@@ -1128,10 +1169,10 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
         if (e != cudaSuccess) return e;
       }
       IPT_STAGE(13);
-      wf_adj_cache<<<grid, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w);
+      wf_adj_cache<<<g_q, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w);
     }
     IPT_STAGE(14);
-    wf_blk_reduce<<<(np + 127) / 128, 128, 0, st>>>(wb.blk, grid, np, grad_acc + 10u * c.seg_lo);
+    wf_blk_reduce<<<(np + 127) / 128, 128, 0, st>>>(wb.blk, rows, np, grad_acc + 10u * c.seg_lo);
   }
   return cudaGetLastError();
 }
@@ -1141,6 +1182,15 @@ cudaError_t wf_init(Launcher* L) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wf_trace<0, true>, kWfThreads, 0);
   if (e != cudaSuccess) return e;
   L->wf_blocks_per_sm = b < 1 ? 1 : b;
+  if (L->wf_fixed_blocks > 0) L->wf_blocks_per_sm = L->wf_fixed_blocks;
+  // gradient rows: the widest one-wave grid of an adjoint stage (accumulators
+  // in dynamic shared memory only lower the occupancy)
+  int rows = 0;
+  rows = std::max(rows, one_wave(*L, wf_adj_a, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_connect, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_b, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_cache, 0));
+  L->wf_max_rows = rows;
   return cudaSuccess;
 }
 

@@ -203,7 +203,9 @@ Quantizer make_axis(double lo, double hi) {
     if ((double)q.p + 255.0 * s >= hi) break;
     ++e2;
   }
-  q.e = std::min(std::max(e2 + 127, 1), 254);
+  // coordinates are at most 1e30 in magnitude, so e2 + 127 stays far below
+  // 239, the largest exponent traversal accepts (it adds 15 to it)
+  q.e = std::min(std::max(e2 + 127, 1), 239);
   return q;
 }
 
@@ -256,6 +258,11 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
       return false;
     }
     maxabs = std::max(maxabs, std::fabs((double)pos[i]));
+    if (maxabs > 1e30) {
+      // keeps every 4-wide node's scale exponent small enough for traversal
+      *err = "vertex coordinate beyond 1e30 at vertex " + std::to_string(i / 3);
+      return false;
+    }
     lo[i % 3] = std::min(lo[i % 3], (double)pos[i]);
     hi[i % 3] = std::max(hi[i % 3], (double)pos[i]);
   }
