@@ -960,17 +960,21 @@ int ora_light_sample(void* sp, const double* sparams, uint32_t n, const double* 
 
 // Render pixels of one view: mean and mean of squares per channel over the
 // opts->spp samples.  pixels: linear ids py*W+px (NULL = all, in order).
+// sample_base: per listed pixel, the sample counter of its first sample
+// (NULL = 0); a pixel drawn into a stochastic pixel batch (Sec. 4.5) uses
+// samples b*spp .. b*spp+spp-1 for batch entry b.
 int ora_render(void* sp, const ora_camera* cam, const double* params, const double* sparams,
-               const ora_opts* o, const uint32_t* pixels, uint32_t npix, double* mean, double* msq,
-               int32_t nthreads) {
+               const ora_opts* o, const uint32_t* pixels, const uint32_t* sample_base, uint32_t npix,
+               double* mean, double* msq, int32_t nthreads) {
   const Scene* s = static_cast<Scene*>(sp);
   const Ctx C = make_ctx(s, params, sparams, o);
   parallel_for(npix, nthreads, [&](int, uint32_t i) {
     const uint32_t pid = pixels ? pixels[i] : i;
     const uint32_t px = pid % cam->width, py = pid / cam->width;
+    const uint32_t s0 = sample_base ? sample_base[i] : 0u;
     double acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
     for (uint32_t smp = 0; smp < o->spp; ++smp) {
-      const std::vector<PathVertex> path = trace_path(C, *cam, px, py, smp);
+      const std::vector<PathVertex> path = trace_path(C, *cam, px, py, s0 + smp);
       double L[3];
       path_value_and_grad(C, path, nullptr, L, nullptr);
       for (int c = 0; c < 3; ++c) {
@@ -988,10 +992,10 @@ int ora_render(void* sp, const ora_camera* cam, const double* params, const doub
 
 // Vector-Jacobian product: grad[S*10] += sum_pixels sum_c g[pixel,c] *
 // d(mean over opts->spp samples of I_c)/d(params), with pdfs, MIS weights and
-// light selection held at sparams.
+// light selection held at sparams.  sample_base as in ora_render.
 int ora_gradient(void* sp, const ora_camera* cam, const double* params, const double* sparams,
-                 const ora_opts* o, const uint32_t* pixels, uint32_t npix, const double* g,
-                 double* grad, int32_t nthreads) {
+                 const ora_opts* o, const uint32_t* pixels, const uint32_t* sample_base, uint32_t npix,
+                 const double* g, double* grad, int32_t nthreads) {
   const Scene* s = static_cast<Scene*>(sp);
   const Ctx C = make_ctx(s, params, sparams, o);
   const int nt = std::max(1, nthreads);
@@ -1000,8 +1004,9 @@ int ora_gradient(void* sp, const ora_camera* cam, const double* params, const do
     const uint32_t pid = pixels ? pixels[i] : i;
     const uint32_t px = pid % cam->width, py = pid / cam->width;
     const double gs[3] = {g[3 * i] / o->spp, g[3 * i + 1] / o->spp, g[3 * i + 2] / o->spp};
+    const uint32_t s0 = sample_base ? sample_base[i] : 0u;
     for (uint32_t smp = 0; smp < o->spp; ++smp) {
-      const std::vector<PathVertex> path = trace_path(C, *cam, px, py, smp);
+      const std::vector<PathVertex> path = trace_path(C, *cam, px, py, s0 + smp);
       double L[3];
       path_value_and_grad(C, path, gs, L, part[tid].data());
     }

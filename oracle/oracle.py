@@ -28,7 +28,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ipt_oracle.cpp")
 LIB = os.path.join(HERE, "libipt_oracle.so")
 
-SET_RESIDUAL, SET_DERIVATIVE, SET_TARGET, SET_CACHE = 0, 1, 2, 3
+SET_RESIDUAL, SET_DERIVATIVE, SET_TARGET, SET_CACHE, SET_PICK = 0, 1, 2, 3, 4
 
 _lock = threading.Lock()
 _lib = None
@@ -84,9 +84,9 @@ def lib():
             L.ora_bsdf_pdf.argtypes = [P, P, P, P]
             L.ora_light_sample.argtypes = [P, P, C.c_uint32, P, P, P, P]
             L.ora_light_sample.restype = C.c_int
-            L.ora_render.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts), P,
+            L.ora_render.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts), P, P,
                                      C.c_uint32, P, P, C.c_int32]
-            L.ora_gradient.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts), P,
+            L.ora_gradient.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts), P, P,
                                        C.c_uint32, P, P, C.c_int32]
             L.ora_count_rays.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts), P,
                                          C.c_uint32, P, P]
@@ -189,31 +189,34 @@ class OracleScene:
         o.pixel_offset = int(self.offsets[view])
         return o
 
-    def render(self, params, view=0, pixels=None, sparams=None, threads=None, **kw):
-        """Mean and mean-of-squares images (npix, 3) for one view."""
+    def render(self, params, view=0, pixels=None, sparams=None, threads=None, sample_base=None, **kw):
+        """Mean and mean-of-squares images (npix, 3) for one view.
+        sample_base: per listed pixel, the counter of its first sample."""
         cam = self.cams[view]
         p = np.ascontiguousarray(params, np.float64)
         sp = None if sparams is None else np.ascontiguousarray(sparams, np.float64)
         px = None if pixels is None else np.ascontiguousarray(pixels, np.uint32)
         n = cam.width * cam.height if px is None else px.shape[0]
+        sb = None if sample_base is None else np.ascontiguousarray(sample_base, np.uint32).reshape(n)
         mean = np.zeros((n, 3))
         msq = np.zeros((n, 3))
         o = self.opts(view=view, **kw)
-        lib().ora_render(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), _p(px), n,
+        lib().ora_render(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), _p(px), _p(sb), n,
                          _p(mean), _p(msq), threads or default_threads())
         return mean, msq
 
-    def gradient(self, params, g, view=0, pixels=None, sparams=None, threads=None, **kw):
+    def gradient(self, params, g, view=0, pixels=None, sparams=None, threads=None, sample_base=None, **kw):
         """J^T g for one view: g is (npix, 3); returns (S, 10)."""
         cam = self.cams[view]
         p = np.ascontiguousarray(params, np.float64)
         sp = None if sparams is None else np.ascontiguousarray(sparams, np.float64)
         px = None if pixels is None else np.ascontiguousarray(pixels, np.uint32)
         n = cam.width * cam.height if px is None else px.shape[0]
+        sb = None if sample_base is None else np.ascontiguousarray(sample_base, np.uint32).reshape(n)
         gg = np.ascontiguousarray(g, np.float64).reshape(n, 3)
         out = np.zeros((self.n_seg, 10))
         o = self.opts(view=view, **kw)
-        lib().ora_gradient(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), _p(px), n,
+        lib().ora_gradient(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), _p(px), _p(sb), n,
                            _p(gg), _p(out), threads or default_threads())
         return out
 
@@ -389,3 +392,57 @@ def loss_grad(osc: OracleScene, params, targets, spp_r, spp_d, max_depth, iterat
                              set_id=SET_RESIDUAL if same_set else SET_DERIVATIVE,
                              iteration=iteration, seed=seed, threads=threads)
     return total, grad
+
+
+# ---------------------------------------------------------------------------
+# Stochastic pixel batches (Sec. 4.5: B pixels drawn uniformly from all pixels
+# of all images per step)
+# ---------------------------------------------------------------------------
+
+def pick_pixels(n_pixels, batch, iteration, seed=0, scene_id=0):
+    """Global pixel ids (over all views, view-major) of the B batch entries of
+    one iteration, drawn uniformly with replacement.  Entry b takes the first
+    word x of Philox4x32-10 at key (seed_lo, seed_hi ^ scene_id) and counter
+    (b, 0, (4 << 24) | iteration, 0); its pixel is floor(x * n / 2^32), an
+    integer map both sides evaluate exactly."""
+    key = [seed & 0xFFFFFFFF, ((seed >> 32) & 0xFFFFFFFF) ^ scene_id]
+    out = np.zeros(batch, np.uint32)
+    for b in range(batch):
+        x = int(philox4x32_10([b, 0, (SET_PICK << 24) | (iteration & 0xFFFFFF), 0], key)[0])
+        out[b] = (x * int(n_pixels)) >> 32
+    return out
+
+
+def loss_grad_batch(osc: OracleScene, params, targets, batch, spp_r, spp_d, max_depth, iteration=0,
+                    seed=0, loss="l2", nee=True, mis=True, profile=0, same_set=False, scene_id=0,
+                    sparams=None, threads=None):
+    """One nested-SGD gradient evaluation on a stochastic pixel batch: the B
+    entries of pick_pixels; entry b renders spp_r samples of set 0 from sample
+    counter b*spp_r and differentiates spp_d samples of set 1 from b*spp_d; the
+    loss is normalised by the 3B entry-channels, so its expectation over the
+    draw is the full-image loss.  Returns (loss, grad, picked ids)."""
+    offs = np.asarray(osc.offsets, np.int64)
+    n_pix = int(sum(c.width * c.height for c in osc.cams))
+    ids = pick_pixels(n_pix, batch, iteration, seed, scene_id)
+    views = np.searchsorted(offs, ids.astype(np.int64), side="right") - 1
+    n_total = 3 * batch
+    grad = np.zeros((osc.n_seg, 10))
+    total = 0.0
+    for v in range(len(osc.cams)):
+        ent = np.nonzero(views == v)[0].astype(np.uint32)
+        if ent.size == 0:
+            continue
+        px = (ids[ent].astype(np.int64) - offs[v]).astype(np.uint32)
+        img, _ = osc.render(params, view=v, pixels=px, sparams=sparams, sample_base=ent * np.uint32(spp_r),
+                            spp=spp_r,
+                            max_depth=max_depth, nee=nee, mis=mis, profile=profile,
+                            set_id=SET_RESIDUAL, iteration=iteration, seed=seed, scene_id=scene_id,
+                            threads=threads)
+        g, l_v = residual(img, np.asarray(targets[v]).reshape(-1, 3)[px], n_total, loss)
+        total += l_v
+        grad += osc.gradient(params, g, view=v, pixels=px, sparams=sparams, spp=spp_d,
+                             sample_base=ent * np.uint32(spp_r if same_set else spp_d),
+                             max_depth=max_depth, nee=nee, mis=mis, profile=profile,
+                             set_id=SET_RESIDUAL if same_set else SET_DERIVATIVE,
+                             iteration=iteration, seed=seed, scene_id=scene_id, threads=threads)
+    return total, grad, ids
