@@ -427,24 +427,46 @@ def run_time_to_error(args):
         workload = f"room_61k_tri_div{args.res_div}_cache_b{args.cache}"
     else:
         rooms = [scenes.batch_room(k, args.res_div) for k in range(64)]
-        opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.batch_spp, max_depth=args.batch_depth)
-        ss, masks = convergence.prepare(rooms, opts, target_spp=256, init=0.0, seed=7)
+        opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.spp_d or args.batch_spp,
+                            max_depth=args.batch_depth, pixel_batch=args.pixel_batch)
+        tgt = TraceOptions(max_depth=args.batch_depth)
+        ss, masks = convergence.prepare(rooms, tgt, target_spp=256, init=0.0, seed=7)
         ss.configure(integrator="wavefront", wavefront_slots=1 << 21, bvh_width=4)
         first, hist = convergence.time_to_error(ss, masks, opts, adam, threshold=0.01,
-                                                max_iters=args.max_iters, check_every=50)
+                                                max_iters=args.max_iters, check_every=args.check_every)
         res["batched"] = {"first": first, "history_last": hist[-1][:2]}
+        ss.close()
         seq = []
-        for i, sc in enumerate(rooms):
-            tr, m = convergence.prepare_single(sc, opts, target_spp=256, seed=7)
+        for i, sc in enumerate(rooms[:args.seq_rooms]):
+            tr, m = convergence.prepare_single(sc, tgt, target_spp=256, seed=7)
             tr.configure("wavefront", wavefront_slots=1 << 21, bvh_width=4)
             f, _ = convergence.time_to_error_single(tr, m, opts, adam, threshold=0.01, max_iters=args.max_iters,
-                                                    check_every=50)
+                                                    check_every=args.check_every)
             seq.append(f)
             tr.close()
         res["sequential_plain"] = {"first": seq}
-        workload = f"batch64_rooms_div{args.res_div}"
+
+        def summary(fs):
+            t = np.array([f[1] for f in fs if f is not None])
+            return {"reached": int(t.size), "of": len(fs),
+                    "p50_s": float(np.percentile(t, 50)) if t.size else None,
+                    "p99_s": float(np.percentile(t, 99)) if t.size else None}
+        k = len(seq)
+        res["summary"] = {
+            "batched": summary(first), "sequential_plain": summary(seq),
+            # the same first k rooms: batch wall time until all k crossed vs the
+            # sum of their one-after-another times
+            "rooms_compared": k,
+            "batched_wall_s_first_k": (max(f[1] for f in first[:k]) if all(f is not None for f in first[:k])
+                                       else None),
+            "sequential_sum_s_first_k": (sum(f[1] for f in seq) if all(f is not None for f in seq) else None)}
+        s = res["summary"]
+        if s["batched_wall_s_first_k"] and s["sequential_sum_s_first_k"]:
+            s["speedup_first_k"] = s["sequential_sum_s_first_k"] / s["batched_wall_s_first_k"]
+        workload = f"batch64_rooms_div{args.res_div}" + (f"_pixbatch{args.pixel_batch}" if args.pixel_batch else "")
     print(json.dumps({"metric": "time to 1% parameter error", "unit": "s", "workload": workload,
-                      "lr": args.lr, "spp": args.batch_spp, "results": res}), flush=True)
+                      "lr": args.lr, "spp": args.batch_spp, "spp_d": args.spp_d or args.batch_spp,
+                      "pixel_batch": args.pixel_batch, "results": res}), flush=True)
 
 
 def main():
@@ -465,6 +487,12 @@ def main():
     ap.add_argument("--batch-spp", type=int, default=8)
     ap.add_argument("--batch-depth", type=int, default=3)
     ap.add_argument("--lr", type=float, default=5e-3)
+    ap.add_argument("--pixel-batch", type=int, default=0,
+                    help="time-to-error: B pixels drawn per iteration (Sec. 4.5; 0 = whole images)")
+    ap.add_argument("--spp-d", type=int, default=0, help="time-to-error: derivative samples (0 = --batch-spp)")
+    ap.add_argument("--seq-rooms", type=int, default=64,
+                    help="time-to-error: rooms optimised one after another for the plain arm")
+    ap.add_argument("--check-every", type=int, default=50, help="time-to-error: iterations between error reads")
     ap.add_argument("--max-iters", type=int, default=6000)
     ap.add_argument("--monitor-every", type=int, default=250)
     ap.add_argument("--monitor-spp", type=int, default=1024)

@@ -133,7 +133,17 @@ typedef struct {
  *   max_depth: number of scattering events (1 = direct light only, App. A.3).
  *   loss: 0 = L2, 1 = L1 (Eq. 3).
  *   nee, mis: light sampling and its MIS with BRDF sampling (App. A.2).
- *   emission_profile: 0 = (w.n)_+ (Sec. 4.3), 1 = uniform over the front face. */
+ *   emission_profile: 0 = (w.n)_+ (Sec. 4.3), 1 = uniform over the front face.
+ *   pixel_batch: 0 = every pixel of every view.  B > 0 = a stochastic batch
+ *     of B pixels drawn per iteration uniformly, with replacement, from all
+ *     pixels of all views (Sec. 4.5 uses B = 8); see ipt_pick_pixels for the
+ *     draw.  Batch entry b traces its pixel with the sample counters
+ *     b*spp .. b*spp+spp-1 of each set, and the loss and its gradient are
+ *     normalised by the 3B entry-channels, so the batch loss is an unbiased
+ *     estimate of the full-image loss.  Accepted by ipt_loss_grad, ipt_step
+ *     and ipt_batch_step (every other call requires 0); such passes always
+ *     run on the wavefront integrator; not with the radiance cache.
+ *     B * max(spp_r, spp_d) must stay below 2^32. */
 typedef struct {
   uint32_t spp_r;
   uint32_t spp_d;
@@ -143,6 +153,7 @@ typedef struct {
   int32_t mis;
   int32_t emission_profile;
   int32_t gradcheck_same_set;
+  uint32_t pixel_batch;
 } ipt_trace_opts;
 
 /* Adam (Sec. 4.5: Adam, learning rate 5e-3) plus the L1 emission regulariser
@@ -161,6 +172,7 @@ typedef struct {
 #define IPT_SET_DERIVATIVE 1u
 #define IPT_SET_TARGET 2u
 #define IPT_SET_CACHE 3u
+#define IPT_SET_PICK 4u /* the pixel-batch draw (ipt_pick_pixels) */
 
 /* Create a context on opt->device.  *out receives the handle.  Fails with
  * IPT_ERR_CUDA if the device cannot be used. */
@@ -274,6 +286,16 @@ ipt_status ipt_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
 ipt_status ipt_trace_rays(ipt_ctx* ctx, int32_t scene, uint32_t n, const float* orig,
                           const float* dir, const int32_t* skip, int32_t* tri_out, float* t_out,
                           float* u_out, float* v_out);
+
+/* The pixel batch of one iteration (Sec. 4.5: each optimisation step draws
+ * its B pixels uniformly over every pixel of every view): ids_out[b] (device, `batch`
+ * entries) receives the global pixel id (views concatenated in order, row
+ * major within a view) of entry b, floor(x * N / 2^32), where N is the
+ * scene's pixel count and x the first word of Philox4x32-10 at the scene's
+ * key (seed_lo, seed_hi ^ scene) and counter
+ * (b, 0, (IPT_SET_PICK << 24) | (iteration & 0xFFFFFF), 0).  This is the draw
+ * ipt_loss_grad and ipt_step make when opts->pixel_batch = batch. */
+ipt_status ipt_pick_pixels(ipt_ctx* ctx, int32_t scene, uint32_t batch, uint64_t iteration, uint32_t* ids_out);
 
 /* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator behind
  * every random decision: out[4i..4i+3] = philox(ctr[4i..4i+3], key[2i..2i+1]).

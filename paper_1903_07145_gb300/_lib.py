@@ -24,7 +24,7 @@ EXPORTED = [
     "ipt_create", "ipt_destroy", "ipt_status_string", "ipt_last_error_detail",
     "ipt_scene_upload", "ipt_views_set", "ipt_targets_set", "ipt_params_set",
     "ipt_params_get", "ipt_params_device", "ipt_render", "ipt_backward", "ipt_loss_grad",
-    "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_philox", "ipt_synchronize",
+    "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_pick_pixels", "ipt_philox", "ipt_synchronize",
     "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read", "ipt_loss_grad_shard",
     "ipt_backward_noalloc", "ipt_config_set", "ipt_config_get",
     "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy",
@@ -64,7 +64,8 @@ class ipt_config(C.Structure):
 class ipt_trace_opts(C.Structure):
     _fields_ = [("spp_r", C.c_uint32), ("spp_d", C.c_uint32), ("max_depth", C.c_uint32),
                 ("loss", C.c_int32), ("nee", C.c_int32), ("mis", C.c_int32),
-                ("emission_profile", C.c_int32), ("gradcheck_same_set", C.c_int32)]
+                ("emission_profile", C.c_int32), ("gradcheck_same_set", C.c_int32),
+                ("pixel_batch", C.c_uint32)]
 
 
 class ipt_adam_opts(C.Structure):
@@ -118,6 +119,7 @@ def lib():
                              C.POINTER(C.c_double)],
                 "ipt_trace_rays": [P, I32, U32, P, P, P, P, P, P, P],
                 "ipt_philox": [P, U32, P, P, P],
+                "ipt_pick_pixels": [P, I32, U32, U64, P],
                 "ipt_synchronize": [P],
                 "ipt_scene_info": [P, I32, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32),
                                    C.POINTER(U32), C.POINTER(U32), C.POINTER(U64)],
@@ -237,6 +239,10 @@ def ipt_step(ctx, scene, opts, adam, want_loss):
 
 def ipt_trace_rays(ctx, scene, n, orig, dirs, skip, tri, t, u, v):
     _check(ctx, lib().ipt_trace_rays(ctx, scene, n, orig, dirs, skip, tri, t, u, v))
+
+
+def ipt_pick_pixels(ctx, scene, batch, iteration, out):
+    _check(ctx, lib().ipt_pick_pixels(ctx, scene, batch, iteration, out))
 
 
 def ipt_philox(ctx, n, ctr, key, out):

@@ -92,6 +92,10 @@ struct DeviceScene {
   uint64_t n_pix = 0;
   float* target = nullptr;
   float* g_img = nullptr;
+  // stochastic pixel batch: drawn pixel ids and upstream gradient per entry
+  uint32_t* pick = nullptr;
+  float* g_pick = nullptr;
+  uint32_t pick_cap = 0;
   // reductions
   double* grad_acc = nullptr;
   float* grad_f = nullptr;
@@ -194,6 +198,8 @@ void free_scene(DeviceScene* s) {
   if (!s) return;
   free_cache(s->cache);
   for (void* p : s->owned) cudaFree(p);
+  cudaFree(s->pick);
+  cudaFree(s->g_pick);
   delete s;
 }
 
@@ -298,8 +304,11 @@ ipt_status get_scene(ipt_ctx* ctx, int32_t id, DeviceScene** out) {
   return IPT_OK;
 }
 
-ipt_status check_opts(ipt_ctx* ctx, const ipt_trace_opts* o, bool adjoint) {
+ipt_status check_opts(ipt_ctx* ctx, const ipt_trace_opts* o, bool adjoint, bool batch_ok = false) {
   if (!o) return fail(ctx, IPT_ERR_INVALID_ARG, "null trace options");
+  if (o->pixel_batch && !batch_ok) return fail(ctx, IPT_ERR_INVALID_ARG, "pixel_batch must be 0 for this call");
+  if ((uint64_t)o->pixel_batch * std::max(o->spp_r, o->spp_d) >= (1ull << 32))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "pixel_batch * spp must stay below 2^32");
   const uint32_t maxd = adjoint ? ipt::kMaxAdjointDepth : ipt::kMaxForwardDepth;
   if (o->max_depth > maxd)
     return fail(ctx, IPT_ERR_INVALID_ARG, "max_depth " + std::to_string(o->max_depth) + " above limit " +
@@ -323,6 +332,21 @@ ipt::TraceParams trace_params(const ipt_ctx* ctx, int32_t scene, const ipt_trace
   tp.mis = o->mis;
   tp.profile = o->emission_profile;
   return tp;
+}
+
+// Device buffers of a pixel batch of `batch` entries (grown, never shrunk).
+ipt_status ensure_pick(ipt_ctx* ctx, DeviceScene* s, uint32_t batch) {
+  if (s->pick_cap >= batch) return IPT_OK;
+  IPT_CK(cudaStreamSynchronize(ctx->stream));
+  cudaFree(s->pick);
+  cudaFree(s->g_pick);
+  s->pick = nullptr;
+  s->g_pick = nullptr;
+  s->pick_cap = 0;
+  IPT_CK(cudaMalloc(&s->pick, batch * sizeof(uint32_t)));
+  IPT_CK(cudaMalloc(&s->g_pick, 3 * (size_t)batch * sizeof(float)));
+  s->pick_cap = batch;
+  return IPT_OK;
 }
 
 ipt_status ensure_tables(ipt_ctx* ctx, DeviceScene* s, const float* params, const float* sparams) {
@@ -429,18 +453,34 @@ ipt_status upload_entry(ipt_ctx* ctx, const ipt::WfScene& e) {
   return IPT_OK;
 }
 
+// Pixel batch of one iteration into out[0..B-1] (device).
+ipt_status draw_picks(ipt_ctx* ctx, int32_t scene_id, const DeviceScene* s, uint32_t B, uint64_t iteration,
+                      uint32_t* out) {
+  if (s->n_pix >= (1ull << 32)) return fail(ctx, IPT_ERR_INVALID_ARG, "pixel batches need fewer than 2^32 pixels");
+  ipt::WfScene e = wf_entry(ctx, scene_id, s, 0, B);
+  e.pick = out;
+  e.n_all = (uint32_t)s->n_pix;
+  ipt_status st = upload_entry(ctx, e);
+  if (st != IPT_OK) return st;
+  IPT_CK(ipt::wf_pick(ctx->wf_tab, std::vector<ipt::WfScene>{e}, nullptr, (uint32_t)iteration, ctx->stream));
+  return IPT_OK;
+}
+
 // Forward pass through the configured integrator.  Launch pixel i is scene
 // pixel begin + i; img/msq are indexed by launch pixel, target and g_out by
 // scene pixel.
 ipt_status run_forward(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t begin, uint32_t n,
                        const ipt::TraceParams& tp, float* img, float* msq, const float* target, float* g_out,
-                       double* partials, float g_scale, int loss_kind, const ipt::CachePass* cache = nullptr) {
-  if (cache && !use_wavefront_cap(ctx, tp.spp))
-    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes need spp <= wavefront_slots");
-  if (cache || use_wavefront(ctx, tp.spp)) {
+                       double* partials, float g_scale, int loss_kind, const ipt::CachePass* cache = nullptr,
+                       uint32_t* pick = nullptr) {
+  if ((cache || pick) && !use_wavefront_cap(ctx, tp.spp))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes and pixel batches need spp <= wavefront_slots");
+  if (cache || pick || use_wavefront(ctx, tp.spp)) {
     ipt_status st = ensure_wf(ctx, false, 10u * s->n_seg);
     if (st != IPT_OK) return st;
     ipt::WfScene e = wf_entry(ctx, scene_id, s, begin, n);
+    e.pick = pick;  // batch entries 0..n-1 (begin is 0)
+    e.n_all = (uint32_t)s->n_pix;
     e.g_scale = g_scale;
     e.target = target;
     e.g_img = g_out;
@@ -469,13 +509,15 @@ ipt_status run_forward(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t 
 // grad_acc, which the caller zeroes).  g_img is indexed by scene pixel.
 ipt_status run_adjoint(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t begin, uint32_t n,
                        const ipt::TraceParams& tp, const float* g_img, double* grad_acc,
-                       const ipt::CachePass* cache = nullptr) {
-  if (cache && !use_wavefront_cap(ctx, tp.spp))
-    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes need spp <= wavefront_slots");
-  if (cache || use_wavefront(ctx, tp.spp)) {
+                       const ipt::CachePass* cache = nullptr, uint32_t* pick = nullptr) {
+  if ((cache || pick) && !use_wavefront_cap(ctx, tp.spp))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes and pixel batches need spp <= wavefront_slots");
+  if (cache || pick || use_wavefront(ctx, tp.spp)) {
     ipt_status st = ensure_wf(ctx, true, 10u * s->n_seg);
     if (st != IPT_OK) return st;
     ipt::WfScene e = wf_entry(ctx, scene_id, s, begin, n);
+    e.pick = pick;
+    e.n_all = (uint32_t)s->n_pix;
     e.g_img = const_cast<float*>(g_img);
     if ((st = upload_entry(ctx, e)) != IPT_OK) return st;
     StageTimer timer{ctx};
@@ -910,26 +952,35 @@ static ipt_status loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, c
                                   uint64_t iteration, float* grad_out, uint64_t begin, uint64_t count,
                                   uint64_t n_total) {
   ipt_status st;
-  if ((st = check_opts(ctx, opts, true)) != IPT_OK) return st;
+  const bool whole = begin == 0 && count == s->n_pix && n_total == s->n_pix;
+  if ((st = check_opts(ctx, opts, true, whole)) != IPT_OK) return st;
   if (s->views.empty() || !s->target) return fail(ctx, IPT_ERR_INVALID_ARG, "loss needs views and targets");
   if (opts->spp_r == 0 || opts->spp_d == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp_r and spp_d must be positive");
   if (begin + count > s->n_pix || count == 0 || n_total < count)
     return fail(ctx, IPT_ERR_INVALID_ARG, "pixel range outside the views");
+  const uint32_t B = opts->pixel_batch;
+  if (B && cache_on(s)) return fail(ctx, IPT_ERR_INVALID_ARG, "pixel batches do not run with the radiance cache");
   IPT_CK(cudaSetDevice(ctx->device));
   if ((st = ensure_tables(ctx, s, s->params, nullptr)) != IPT_OK) return st;
   const uint32_t np = 10u * s->n_seg;
-  const float g_scale = (float)(1.0 / (3.0 * (double)n_total));
+  // a pixel batch traces entries 0..B-1 of the drawn pixels
+  if (B && ((st = ensure_pick(ctx, s, B)) != IPT_OK || (st = draw_picks(ctx, scene, s, B, iteration, s->pick)) != IPT_OK))
+    return st;
+  const uint32_t lb = B ? 0u : (uint32_t)begin, ln = B ? B : (uint32_t)count;
+  float* g_buf = B ? s->g_pick : s->g_img;
+  uint32_t* pick = B ? s->pick : nullptr;
+  const float g_scale = (float)(1.0 / (3.0 * (double)(B ? B : n_total)));
   ipt::CachePass cp;
   if (cache_on(s) && (st = cache_pass(ctx, s, false, &cp)) != IPT_OK) return st;
   const ipt::CachePass* cpp = cache_on(s) ? &cp : nullptr;
-  st = run_forward(ctx, scene, s, (uint32_t)begin, (uint32_t)count,
-                   trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration), nullptr, nullptr,
-                   s->target, s->g_img, s->loss_partials, g_scale, opts->loss, cpp);
+  st = run_forward(ctx, scene, s, lb, ln, trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration),
+                   nullptr, nullptr, s->target, g_buf, s->loss_partials, g_scale, opts->loss, cpp, pick);
   if (st != IPT_OK) return st;
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
   const uint32_t set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
-  st = run_adjoint(ctx, scene, s, (uint32_t)begin, (uint32_t)count,
-                   trace_params(ctx, scene, opts, set, opts->spp_d, iteration), s->g_img, s->grad_acc, cpp);
+  ipt::TraceParams tpd = trace_params(ctx, scene, opts, set, opts->spp_d, iteration);
+  if (opts->gradcheck_same_set) tpd.sample_stride = opts->spp_r;
+  st = run_adjoint(ctx, scene, s, lb, ln, tpd, g_buf, s->grad_acc, cpp, pick);
   if (st != IPT_OK) return st;
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, s->grad_acc,
@@ -951,7 +1002,7 @@ ipt_status ipt_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts
   ipt_status st = get_scene(ctx, scene, &s);
   if (st != IPT_OK) return st;
   if ((st = loss_grad_async(ctx, scene, s, opts, iteration, grad_out, 0, s->n_pix, s->n_pix)) != IPT_OK) return st;
-  if (loss_out) return read_loss(ctx, s, loss_out, s->n_pix);
+  if (loss_out) return read_loss(ctx, s, loss_out, opts->pixel_batch ? opts->pixel_batch : s->n_pix);
   return IPT_OK;
 }
 
@@ -1004,7 +1055,7 @@ ipt_status ipt_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, con
   if (cache_on(s) && (st = cache_train_pass(ctx, scene, s, opts, s->iteration)) != IPT_OK) return st;
   if ((st = ipt_adam_step(ctx, scene, nullptr, adam)) != IPT_OK) return st;
   s->iteration++;
-  if (loss_out) return read_loss(ctx, s, loss_out, s->n_pix);
+  if (loss_out) return read_loss(ctx, s, loss_out, opts->pixel_batch ? opts->pixel_batch : s->n_pix);
   return IPT_OK;
 }
 
@@ -1019,6 +1070,17 @@ ipt_status ipt_trace_rays(ipt_ctx* ctx, int32_t scene, uint32_t n, const float* 
   IPT_CK(ipt::launch_trace_rays(buffers(ctx, s), n, orig, dir, skip, tri_out, t_out, u_out, v_out, ctx->err_dev,
                                 ctx->stream));
   return IPT_OK;
+}
+
+ipt_status ipt_pick_pixels(ipt_ctx* ctx, int32_t scene, uint32_t batch, uint64_t iteration, uint32_t* ids_out) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (batch == 0) return IPT_OK;
+  if (!ids_out) return fail(ctx, IPT_ERR_INVALID_ARG, "null ids_out");
+  if (s->views.empty()) return fail(ctx, IPT_ERR_INVALID_ARG, "pixel batches need views");
+  IPT_CK(cudaSetDevice(ctx->device));
+  return draw_picks(ctx, scene, s, batch, iteration, ids_out);
 }
 
 ipt_status ipt_philox(ipt_ctx* ctx, uint32_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
@@ -1095,19 +1157,27 @@ static ipt_status get_batch(ipt_ctx* ctx, int32_t id, Batch** out) {
 }
 
 // Scene table of a batch for the context's current configuration.
-static void batch_table(ipt_ctx* ctx, Batch* b) {
+// Scene table of a batch: every member's pixels, or B batch entries per
+// member when the step uses pixel batches (batch > 0; the members' pick
+// buffers must hold B entries).  Also sets each member's loss normalisation.
+static void batch_table(ipt_ctx* ctx, Batch* b, uint32_t batch) {
   b->tab_host.clear();
   uint32_t pix = 0, seg = 0;
-  for (int32_t id : b->members) {
+  for (size_t k = 0; k < b->members.size(); ++k) {
+    const int32_t id = b->members[k];
     DeviceScene* s = ctx->scenes[id];
-    ipt::WfScene e = wf_entry(ctx, id, s, 0, (uint32_t)s->n_pix);
+    const uint32_t n = batch ? batch : (uint32_t)s->n_pix;
+    ipt::WfScene e = wf_entry(ctx, id, s, 0, n);
     e.pix_begin = pix;
     e.seg_offset = seg;
-    e.g_scale = (float)(1.0 / (3.0 * (double)s->n_pix));
+    e.g_scale = (float)(1.0 / (3.0 * (double)n));
     e.target = s->target;
-    e.g_img = s->g_img;
+    e.g_img = batch ? s->g_pick : s->g_img;
+    e.pick = batch ? s->pick : nullptr;
+    e.n_all = (uint32_t)s->n_pix;
     b->tab_host.push_back(e);
-    pix += (uint32_t)s->n_pix;
+    b->mem_host[k].inv_n = e.g_scale;
+    pix += n;
     seg += s->n_seg;
   }
 }
@@ -1220,11 +1290,13 @@ static ipt_status batch_enqueue(ipt_ctx* ctx, Batch* b, const ipt_trace_opts* op
   tp.nee = opts->nee;
   tp.mis = opts->mis;
   tp.profile = opts->emission_profile;
+  if (opts->pixel_batch) IPT_CK(ipt::wf_pick(b->tab_dev, b->tab_host, b->iter_dev, 0u, st));
   IPT_CK(ipt::wf_forward(ctx->L, b->tab_dev, b->tab_host, tp, opts->loss, b->iter_dev, ctx->wf, b->loss_rows,
                          ctx->err_dev, st, nullptr));
   IPT_CK(cudaMemsetAsync(b->grad_acc, 0, np * sizeof(double), st));
   tp.set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
   tp.spp = opts->spp_d;
+  if (opts->gradcheck_same_set) tp.sample_stride = opts->spp_r;
   IPT_CK(ipt::wf_adjoint(ctx->L, b->tab_dev, b->tab_host, tp, b->iter_dev, ctx->wf, b->grad_acc, ctx->err_dev, st,
                          nullptr));
   IPT_CK(ipt::launch_batch_losses(b->loss_rows, ipt::loss_partials_capacity(ctx->L), b->mem_dev, n, b->losses_dev,
@@ -1240,7 +1312,7 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
   Batch* b;
   ipt_status st = get_batch(ctx, batch, &b);
   if (st != IPT_OK) return st;
-  if ((st = check_opts(ctx, opts, true)) != IPT_OK) return st;
+  if ((st = check_opts(ctx, opts, true, true)) != IPT_OK) return st;
   if (!adam) return fail(ctx, IPT_ERR_INVALID_ARG, "null adam options");
   if (opts->spp_r == 0 || opts->spp_d == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp_r and spp_d must be positive");
   const uint32_t cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
@@ -1249,7 +1321,12 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
   IPT_CK(cudaSetDevice(ctx->device));
   if (!b->exec || !same_opts(*opts, b->g_opts) || !same_adam(*adam, b->g_adam) || !same_cfg(ctx->cfg, b->g_cfg)) {
     // everything the graph touches is allocated before the capture
-    batch_table(ctx, b);
+    if (opts->pixel_batch)
+      for (int32_t id : b->members)
+        if ((st = ensure_pick(ctx, ctx->scenes[id], opts->pixel_batch)) != IPT_OK) return st;
+    batch_table(ctx, b, opts->pixel_batch);
+    IPT_CK(cudaMemcpyAsync(b->mem_dev, b->mem_host.data(), b->mem_host.size() * sizeof(ipt::BatchMember),
+                           cudaMemcpyHostToDevice, ctx->stream));
     uint32_t max_seg = 0;
     for (const ipt::WfChunk& c : ipt::wf_plan(b->tab_host, cap, opts->spp_d, ipt::wf_max_segments()))
       max_seg = std::max(max_seg, c.seg_n);

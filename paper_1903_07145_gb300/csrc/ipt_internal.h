@@ -76,6 +76,10 @@ struct TraceParams {
   uint32_t spp;
   uint32_t max_depth;
   int nee, mis, profile;
+  // pixel batches: entry b's samples start at counter b * sample_stride
+  // (0 = spp; the derivative pass of a same-set gradient check uses the
+  // residual's spp so that its samples are the residual's first ones)
+  uint32_t sample_stride = 0;
 };
 
 struct Launcher {

@@ -74,6 +74,7 @@ struct WfParams {
   uint32_t iter;
   const uint32_t* iter_dev;  // iteration counter on the device (overrides iter)
   uint32_t spp;
+  uint32_t stride;           // sample counter stride of pixel-batch entries
   uint32_t max_depth;
   int nee, mis, profile, loss_kind;
   uint32_t n_scenes;
@@ -104,12 +105,19 @@ __device__ __forceinline__ uint32_t enqueue(uint32_t* counter, bool want) {
   return want ? base + (uint32_t)__popc(m & ((1u << g.thread_rank()) - 1u)) : 0xffffffffu;
 }
 
-// Scene pixel id and sample of a slot of the chunk starting at launch pixel p0.
+// Scene pixel id, sample counter and entry (the index of its upstream
+// gradient and image outputs) of a slot of the chunk starting at launch
+// pixel p0.
 __device__ __forceinline__ void slot_pixel(const WfScene& e, uint32_t p0, uint32_t slot, uint32_t spp,
-                                           uint32_t& pid, uint32_t& smp) {
+                                           uint32_t stride, uint32_t& pid, uint32_t& smp, uint32_t& entry) {
   const uint32_t lp = slot / spp;
   smp = slot - lp * spp;
-  pid = p0 + lp - e.pix_begin + e.pix_base;
+  entry = p0 + lp - e.pix_begin + e.pix_base;
+  pid = entry;
+  if (e.pick) {
+    pid = e.pick[entry];
+    smp += entry * stride;
+  }
 }
 
 __device__ __forceinline__ PathRng path_rng(const WfScene& e, uint32_t pid, uint32_t smp, uint32_t si) {
@@ -143,8 +151,8 @@ __global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfPa
         hi = mid - 1;
     }
     const WfScene& e = tab[lo];
-    uint32_t pid, smp;
-    slot_pixel(e, p0, slot, lp.spp, pid, smp);
+    uint32_t pid, smp, ent;
+    slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
     const ViewDev& vw = find_view(e.views, e.n_views, pid);
     const uint32_t l = pid - vw.offset;
     const PathRng rng = path_rng(e, pid, smp, si);
@@ -467,8 +475,8 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(const WfScene* tab, W
           record = true;  // training record; the target is gathered with unit throughput
           beta = f3(1.0f, 1.0f, 1.0f);
         }
-        uint32_t pid, smp;
-        slot_pixel(e, p0, slot, lp.spp, pid, smp);
+        uint32_t pid, smp, ent;
+        slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
         path_id = pid * lp.spp + smp;
         const PathRng rng = path_rng(e, pid, smp, si);
         const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
@@ -545,8 +553,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_reduce(const WfScene* tab, WfPa
     }
     const uint32_t b = state_scene(__float_as_uint(w.beta[l * lp.spp].w));
     const WfScene& e = tab[b];
-    const uint32_t pid = p0 + l - e.pix_begin + e.pix_base;
-    const uint32_t o = pid - e.pix_base;
+    const uint32_t ent = p0 + l - e.pix_begin + e.pix_base;
+    const uint32_t pid = e.pick ? e.pick[ent] : ent;
+    const uint32_t o = ent - e.pix_base;
     const float3 mean = a * inv;
     if (e.img) {
       e.img[3 * o + 0] = mean.x;
@@ -565,10 +574,10 @@ __global__ void __launch_bounds__(kWfThreads) wf_reduce(const WfScene* tab, WfPa
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (lp.loss_kind == 0) {
-          e.g_img[3 * pid + c] = 2.0f * r[c] * e.g_scale;
+          e.g_img[3 * ent + c] = 2.0f * r[c] * e.g_scale;
           acc += (double)r[c] * (double)r[c];
         } else {
-          e.g_img[3 * pid + c] = (r[c] > 0.0f ? 1.0f : (r[c] < 0.0f ? -1.0f : 0.0f)) * e.g_scale;
+          e.g_img[3 * ent + c] = (r[c] > 0.0f ? 1.0f : (r[c] < 0.0f ? -1.0f : 0.0f)) * e.g_scale;
           acc += fabs((double)r[c]);
         }
       }
@@ -612,8 +621,8 @@ __device__ __forceinline__ int acc_ix(const WfScene& e, const WfParams& lp, int 
   return 10 * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
 }
 
-__device__ __forceinline__ float3 pixel_grad(const WfScene& e, uint32_t pid, float inv_spp) {
-  return f3(e.g_img[3 * pid], e.g_img[3 * pid + 1], e.g_img[3 * pid + 2]) * inv_spp;
+__device__ __forceinline__ float3 pixel_grad(const WfScene& e, uint32_t entry, float inv_spp) {
+  return f3(e.g_img[3 * entry], e.g_img[3 * entry + 1], e.g_img[3 * entry + 2]) * inv_spp;
 }
 
 // Continuation terms of a finished path: (dw_l / dtheta) . (g * U_l).
@@ -665,9 +674,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfPar
     const uint32_t st = __float_as_uint(bt.w);
     const uint32_t k = state_k(st), b = state_scene(st);
     const WfScene& e = tab[b];
-    uint32_t pid, smp;
-    slot_pixel(e, p0, slot, lp.spp, pid, smp);
-    const float3 gp = pixel_grad(e, pid, inv_spp);
+    uint32_t pid, smp, ent;
+    slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
+    const float3 gp = pixel_grad(e, ent, inv_spp);
     bool shadow = false, query = false;
     NeeResult ne;
     float3 ge = f3(0.f, 0.f, 0.f), gm = f3(0.f, 0.f, 0.f), cn = f3(0.f, 0.f, 0.f);
@@ -803,8 +812,8 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_b(const WfScene* tab, WfPar
       h.u = hh.z;
       h.v = hh.w;
       const Vtx v = make_vertex(e.s, h, xyz(rd), lp.profile);
-      uint32_t pid, smp;
-      slot_pixel(e, p0, slot, lp.spp, pid, smp);
+      uint32_t pid, smp, ent;
+      slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
       const PathRng rng = path_rng(e, pid, smp, si);
       const float4 ua = rng.draw(k, 0);
       const float4 sa = __ldg(&e.t.samp[v.seg]);
@@ -837,7 +846,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_b(const WfScene* tab, WfPar
         }
       }
       if (!cont) {
-        finish_path(w, e, lp, slot, pixel_grad(e, pid, inv_spp), sacc);
+        finish_path(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
         w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       }
     }
@@ -871,20 +880,59 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
     const int base = acc_ix(e, lp, seg, 0);
 #pragma unroll
     for (int j = 0; j < 7; ++j) atomicAdd(&sacc[base + j], dp[j]);
-    uint32_t pid, smp;
-    slot_pixel(e, p0, slot, lp.spp, pid, smp);
-    finish_path(w, e, lp, slot, pixel_grad(e, pid, inv_spp), sacc);
+    uint32_t pid, smp, ent;
+    slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
+    finish_path(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
     w.beta[slot].w = __uint_as_float(st | kDead);
   }
   acc_flush(sacc, np, w.blk);
 }
 
 // grad_acc[i] += sum over block rows (FP64), for the chunk's parameters.
-__global__ void wf_blk_reduce(const float* blk, int rows, uint32_t np, double* grad_acc) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int r = 0; r < rows; ++r) s += (double)blk[(size_t)r * np + i];
-    grad_acc[i] += s;
+// Block b covers parameters 32b .. 32b+31: warp w sums rows w, w+32, ...
+// (lane l reads parameter 32b+l, so a warp reads 128 contiguous bytes per
+// row), then warp 0 adds the 32 warp sums in a fixed order: the result does
+// not depend on scheduling.
+constexpr int kReduceWarps = 32;
+__global__ void __launch_bounds__(32 * kReduceWarps) wf_blk_reduce(const float* blk, int rows, uint32_t np,
+                                                                    double* grad_acc) {
+  __shared__ double part[kReduceWarps][33];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t i = blockIdx.x * 32u + lane;
+  double s = 0.0;
+  if (i < np)
+    for (int r = (int)warp; r < rows; r += kReduceWarps) s += (double)blk[(size_t)r * np + i];
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && i < np) {
+    double t = 0.0;
+    for (int k = 0; k < kReduceWarps; ++k) t += part[k][lane];
+    grad_acc[i] += t;
+  }
+}
+
+// Pixel batches (Sec. 4.5): entry b of a scene with N pixels is
+// floor(x * N / 2^32), x the first word of Philox4x32-10 at the scene's key
+// and counter (b, 0, (4 << 24) | iteration, 0).  Launch pixels of scenes
+// without a batch are skipped.
+constexpr uint32_t kSetPick = 4u;
+__global__ void __launch_bounds__(kWfThreads) wf_pick_k(const WfScene* tab, uint32_t n_scenes, uint32_t n_launch,
+                                                        const uint32_t* iter_dev, uint32_t iter) {
+  const uint32_t it = iter_dev ? *iter_dev : iter;
+  for (uint32_t P = blockIdx.x * blockDim.x + threadIdx.x; P < n_launch; P += gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (tab[mid].pix_begin <= P)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const WfScene& e = tab[lo];
+    if (!e.pick) continue;
+    const uint32_t b = P - e.pix_begin;
+    const uint4 x = philox4x32_10(make_uint4(b, 0u, (kSetPick << 24) | (it & 0xffffffu), 0u), e.key);
+    e.pick[b] = (uint32_t)(((uint64_t)x.x * (uint64_t)e.n_all) >> 32);
   }
 }
 
@@ -951,6 +999,7 @@ static WfParams wf_params(const TraceParams& tp, int loss_kind, uint32_t n_scene
   p.iter = (uint32_t)(tp.iteration & 0xffffffu);
   p.iter_dev = iter_dev;
   p.spp = tp.spp;
+  p.stride = tp.sample_stride ? tp.sample_stride : tp.spp;
   p.max_depth = tp.max_depth;
   p.nee = tp.nee;
   p.mis = tp.mis;
@@ -1172,8 +1221,18 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
       wf_adj_cache<<<g_q, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w);
     }
     IPT_STAGE(14);
-    wf_blk_reduce<<<(np + 127) / 128, 128, 0, st>>>(wb.blk, rows, np, grad_acc + 10u * c.seg_lo);
+    wf_blk_reduce<<<(np + 31) / 32, 32 * kReduceWarps, 0, st>>>(wb.blk, rows, np, grad_acc + 10u * c.seg_lo);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t wf_pick(const WfScene* tab_dev, const std::vector<WfScene>& tab, const uint32_t* iter_dev,
+                    uint32_t iter, cudaStream_t st) {
+  if (tab.empty()) return cudaSuccess;
+  const WfScene& last = tab.back();
+  const uint32_t n_launch = last.pix_begin + last.n_pix;
+  const uint32_t blocks = std::min<uint32_t>((n_launch + kWfThreads - 1) / kWfThreads, 4096u);
+  wf_pick_k<<<std::max(blocks, 1u), kWfThreads, 0, st>>>(tab_dev, (uint32_t)tab.size(), n_launch, iter_dev, iter);
   return cudaGetLastError();
 }
 

@@ -27,9 +27,15 @@ struct WfScene {
   float es;                  // emission scale
   float g_scale;             // 1 / (3 N) of this scene's loss
   const float* target;       // indexed by scene pixel id (residual mode), or nullptr
-  float* g_img;              // dE/dI, indexed by scene pixel id
-  float* img;                // optional outputs, indexed by scene pixel id - pix_base
+  float* g_img;              // dE/dI, indexed by entry
+  float* img;                // optional outputs, indexed by entry - pix_base
   float* msq;
+  // Stochastic pixel batch (Sec. 4.5), or nullptr: the scene's launch pixels
+  // are then batch entries 0..n_pix-1 (pix_base 0); entry b traces scene
+  // pixel pick[b] with sample counters b*spp .. b*spp+spp-1.  Without a batch
+  // the entry of a launch pixel is its scene pixel id.
+  uint32_t* pick;
+  uint32_t n_all;            // pixels of the scene the batch draws from
 };
 
 // Radiance cache in a pass: query mode ends paths at vertex b_term and adds
@@ -54,6 +60,11 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
                        const TraceParams& tp, int loss_kind, const uint32_t* iter_dev, const WfBuffers& wb,
                        double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook,
                        const CachePass* cache = nullptr);
+
+// Draws the pixel batch of every table entry that has one, for the iteration
+// *iter_dev (or iter when iter_dev is null).
+cudaError_t wf_pick(const WfScene* tab_dev, const std::vector<WfScene>& tab, const uint32_t* iter_dev,
+                    uint32_t iter, cudaStream_t st);
 
 cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb, double* grad_acc,

@@ -26,12 +26,13 @@ class TraceOptions:
     mis: bool = True
     emission_profile: str = "cosine"
     gradcheck_same_set: bool = False
+    pixel_batch: int = 0  # 0: every pixel; B: B pixels drawn per iteration (Sec. 4.5)
 
     def c(self) -> L.ipt_trace_opts:
         return L.ipt_trace_opts(self.spp_r, self.spp_d, self.max_depth,
                                 0 if self.loss == "l2" else 1, int(self.nee), int(self.mis),
                                 0 if self.emission_profile == "cosine" else 1,
-                                int(self.gradcheck_same_set))
+                                int(self.gradcheck_same_set), int(self.pixel_batch))
 
 
 @dataclass
@@ -199,6 +200,12 @@ class Tracer:
         L.ipt_trace_rays(self.ctx, self.sid, n, _ptr(o), _ptr(d), _ptr(sk), _ptr(tri), _ptr(t),
                          _ptr(u), _ptr(v))
         return tri, t, u, v
+
+    def pick_pixels(self, batch: int, iteration: int):
+        """Global pixel ids of the pixel batch of `iteration` (int32 tensor)."""
+        out = torch.empty(max(batch, 1), dtype=torch.int32, device=self.device)
+        L.ipt_pick_pixels(self.ctx, self.sid, batch, iteration, _ptr(out))
+        return out[:batch]
 
     def philox(self, ctr, key):
         c = ctr.to(self.device, torch.int32).contiguous()
