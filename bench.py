@@ -23,6 +23,7 @@ sample of the same workload (the reference arm of this comparison).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -36,11 +37,28 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="room_61k_tri", triangles=61160, segments=48, views=8, width=320,
-                height=240, spp_r=32, spp_d=32, max_depth=5, nee=True, mis=True, loss="l2",
-                init=0.5, target_spp=1024)
+WORKLOADS = {
+    # the benchmark line: the 61k-triangle room with 8 views
+    "room61k": dict(workload="room_61k_tri", triangles=61160, segments=48, views=8, width=320,
+                    height=240, spp_r=32, spp_d=32, max_depth=5, nee=True, mis=True, loss="l2",
+                    init=0.5, target_spp=1024),
+    # differentiation at scale: the 516k-triangle room with 16 views (targets at 256 spp to keep
+    # the run within minutes)
+    "room516k": dict(workload="room_516k_tri", triangles=515728, segments=150, views=16, width=640,
+                     height=480, spp_r=16, spp_d=16, max_depth=6, nee=True, mis=True, loss="l2",
+                     init=0.5, target_spp=256),
+}
+WORKLOAD = dict(WORKLOADS["room61k"])
 METRIC = "fwd+adjoint Mpaths/s"
 NODE_BYTES, TRI_BYTES = 64, 48
+
+
+def make_scene(seed_offset=0):
+    """The workload's scene (seed of the generator + seed_offset)."""
+    from paper_1903_07145_gb300 import scenes
+    if WORKLOAD["workload"].startswith("room_516k"):
+        return scenes.room_500k(1002 + seed_offset)
+    return scenes.room_60k(1001 + seed_offset)
 
 
 def paths_per_step():
@@ -113,13 +131,52 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(target_seconds=15.0, seed=1001):
+# DRAM traffic of the dominant kernel comes from a committed ncu capture (the
+# benchmark cannot read hardware counters itself).  It is reported only while
+# the capture matches: same kernel, workload and wavefront configuration, and
+# the traversal sources unchanged since (their SHA-256 is recorded with it).
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wf_closest_room61k_traffic.txt")
+KERNEL_SOURCES = ["paper_1903_07145_gb300/csrc/ipt_wavefront.cu", "paper_1903_07145_gb300/csrc/ipt_wavefront.h",
+                  "paper_1903_07145_gb300/csrc/ipt_device.cuh"]
+
+
+def kernel_sources_sha256():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, workload, cfg):
+    """DRAM bytes (read + write) per launch, or None."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            lines = fh.read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for line in lines:
+        if ":" in line and not line.lstrip().startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    want = {"kernel": kernel, "workload": workload, "wavefront_slots": str(cfg.get("wavefront_slots")),
+            "bvh_width": str(cfg.get("bvh_width")), "kernel_sources_sha256": kernel_sources_sha256()}
+    if any(kv.get(k) != v for k, v in want.items()):
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(target_seconds=15.0):
     """The FP64 oracle (as it stands) on a bounded pixel sample of the same
     workload: loss + gradient on the sampled pixels of all views."""
     from oracle import oracle as O
     from paper_1903_07145_gb300 import scenes
     w = WORKLOAD
-    sc = scenes.room_60k(seed)
+    sc = make_scene()
     osc = O.OracleScene(sc)
     p = scenes.initial_params(sc, w["init"])
     rng = np.random.default_rng(0)
@@ -181,7 +238,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = WORKLOAD
-    sc = scenes.room_60k(1001 + rank)
+    sc = make_scene(rank)
     sc.cameras = sc.cameras[:w["views"]]
     opts = TraceOptions(spp_r=w["spp_r"], spp_d=w["spp_d"], max_depth=w["max_depth"], nee=True, mis=True)
     adam = AdamOptions()
@@ -318,7 +375,8 @@ def run_ours(args, rank, world, local):
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in ktimes.items() if v[1]},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in ktimes.items() if v[1]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": src,
+                     "frac": achieved / peak, "traffic": recorded_traffic(dom, w["workload"], chosen),
+                     "peak_source": src,
                      "algorithmic_bytes_per_launch": alg_bytes_launch,
                      "avg_launch_ms": dom_ms,
                      "units_per_step": {"node_visits": nodes, "tri_tests": tris, "rays": rays}},
@@ -479,7 +537,7 @@ def main():
     ap.add_argument("--integrator", default="auto", choices=["auto", "megakernel", "wavefront"])
     ap.add_argument("--cache", type=int, default=0, choices=[0, 1, 2],
                     help="end paths at this vertex in the learned radiance cache (0: plain tracer)")
-    ap.add_argument("--workload", default="room61k", choices=["room61k", "batch64"],
+    ap.add_argument("--workload", default="room61k", choices=["room61k", "room516k", "batch64"],
                     help="batch64: aggregate throughput of the 64 uneven rooms (a separate line)")
     ap.add_argument("--time-to-error", action="store_true",
                     help="wall time to 1%% parameter error (batched vs sequential, or cached vs plain)")
@@ -501,6 +559,9 @@ def main():
     ap.add_argument("--spp", type=int, default=None,
                     help="profiling only: spp_r = spp_d = S (not a benchmark line)")
     args = ap.parse_args()
+    if args.workload in WORKLOADS:
+        WORKLOAD.clear()
+        WORKLOAD.update(WORKLOADS[args.workload])
     if args.views:
         WORKLOAD["views"] = args.views
         WORKLOAD["workload"] += f"_first{args.views}views"
