@@ -484,22 +484,28 @@ def run_time_to_error(args):
             tr.close()
         workload = f"room_61k_tri_div{args.res_div}_cache_b{args.cache}"
     else:
-        rooms = [scenes.batch_room(k, args.res_div) for k in range(64)]
+        if args.workload == "cornell64":
+            rooms = [scenes.cornell_variant(k) for k in range(64)]
+            target_spp = 1024
+        else:
+            rooms = [scenes.batch_room(k, args.res_div) for k in range(64)]
+            target_spp = 256
         opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.spp_d or args.batch_spp,
                             max_depth=args.batch_depth, pixel_batch=args.pixel_batch)
         tgt = TraceOptions(max_depth=args.batch_depth)
-        ss, masks = convergence.prepare(rooms, tgt, target_spp=256, init=0.0, seed=7)
+        ss, masks = convergence.prepare(rooms, tgt, target_spp=target_spp, init=0.0, seed=7)
         ss.configure(integrator="wavefront", wavefront_slots=1 << 21, bvh_width=4)
         first, hist = convergence.time_to_error(ss, masks, opts, adam, threshold=0.01,
-                                                max_iters=args.max_iters, check_every=args.check_every)
+                                                max_iters=args.max_iters, check_every=args.check_every,
+                                                halve_every=args.halve_every)
         res["batched"] = {"first": first, "history_last": hist[-1][:2]}
         ss.close()
         seq = []
         for i, sc in enumerate(rooms[:args.seq_rooms]):
-            tr, m = convergence.prepare_single(sc, tgt, target_spp=256, seed=7)
+            tr, m = convergence.prepare_single(sc, tgt, target_spp=target_spp, seed=7)
             tr.configure("wavefront", wavefront_slots=1 << 21, bvh_width=4)
             f, _ = convergence.time_to_error_single(tr, m, opts, adam, threshold=0.01, max_iters=args.max_iters,
-                                                    check_every=args.check_every)
+                                                    check_every=args.check_every, halve_every=args.halve_every)
             seq.append(f)
             tr.close()
         res["sequential_plain"] = {"first": seq}
@@ -510,21 +516,39 @@ def run_time_to_error(args):
                     "p50_s": float(np.percentile(t, 50)) if t.size else None,
                     "p99_s": float(np.percentile(t, 99)) if t.size else None}
         k = len(seq)
+        # measured: the scenes among the first k that reached the threshold in
+        # both arms; the batch's wall time until the last of them crossed (the
+        # batch kept all 64 scenes running) against the sum of their
+        # one-after-another times
+        common = [i for i in range(k) if first[i] is not None and seq[i] is not None]
+        b_wall = max((first[i][1] for i in common), default=None)
+        s_sum = sum(seq[i][1] for i in common) if common else None
+        # per-iteration cost of one scene alone and of the 64-scene batch
+        it_alone = (float(np.mean([f[1] / f[0] for f in seq if f is not None]))
+                    if any(f is not None for f in seq) else None)
+        it_batch = hist[-1][1] / hist[-1][0]
+        reached = [f for f in first if f is not None]
         res["summary"] = {
             "batched": summary(first), "sequential_plain": summary(seq),
-            # the same first k rooms: batch wall time until all k crossed vs the
-            # sum of their one-after-another times
-            "rooms_compared": k,
-            "batched_wall_s_first_k": (max(f[1] for f in first[:k]) if all(f is not None for f in first[:k])
-                                       else None),
-            "sequential_sum_s_first_k": (sum(f[1] for f in seq) if all(f is not None for f in seq) else None)}
-        s = res["summary"]
-        if s["batched_wall_s_first_k"] and s["sequential_sum_s_first_k"]:
-            s["speedup_first_k"] = s["sequential_sum_s_first_k"] / s["batched_wall_s_first_k"]
-        workload = f"batch64_rooms_div{args.res_div}" + (f"_pixbatch{args.pixel_batch}" if args.pixel_batch else "")
+            "scenes_compared": len(common),
+            "batched_wall_s_compared": b_wall, "sequential_sum_s_compared": s_sum,
+            "speedup_compared": (s_sum / b_wall) if common else None,
+            "ms_per_iteration_one_scene_alone": None if it_alone is None else it_alone * 1e3,
+            "ms_per_iteration_batch_of_64": it_batch * 1e3,
+            # whole job, estimated: every scene that reached the threshold in
+            # the batch, at its crossing iteration and the one-scene-alone
+            # cost per iteration, against the batch's wall time to its last
+            # crossing
+            "whole_job_estimate": None if (it_alone is None or not reached) else {
+                "scenes": len(reached), "batched_wall_s": max(f[1] for f in reached),
+                "sequential_s_estimate": sum(f[0] for f in reached) * it_alone,
+                "speedup": sum(f[0] for f in reached) * it_alone / max(f[1] for f in reached)}}
+        workload = ("cornell64_variants" if args.workload == "cornell64" else f"batch64_rooms_div{args.res_div}")
+        workload += f"_pixbatch{args.pixel_batch}" if args.pixel_batch else ""
     print(json.dumps({"metric": "time to 1% parameter error", "unit": "s", "workload": workload,
-                      "lr": args.lr, "spp": args.batch_spp, "spp_d": args.spp_d or args.batch_spp,
-                      "pixel_batch": args.pixel_batch, "results": res}), flush=True)
+                      "lr": args.lr, "halve_every": args.halve_every, "spp": args.batch_spp,
+                      "spp_d": args.spp_d or args.batch_spp, "pixel_batch": args.pixel_batch,
+                      "results": res}), flush=True)
 
 
 def main():
@@ -537,7 +561,7 @@ def main():
     ap.add_argument("--integrator", default="auto", choices=["auto", "megakernel", "wavefront"])
     ap.add_argument("--cache", type=int, default=0, choices=[0, 1, 2],
                     help="end paths at this vertex in the learned radiance cache (0: plain tracer)")
-    ap.add_argument("--workload", default="room61k", choices=["room61k", "room516k", "batch64"],
+    ap.add_argument("--workload", default="room61k", choices=["room61k", "room516k", "batch64", "cornell64"],
                     help="batch64: aggregate throughput of the 64 uneven rooms (a separate line)")
     ap.add_argument("--time-to-error", action="store_true",
                     help="wall time to 1%% parameter error (batched vs sequential, or cached vs plain)")
@@ -551,6 +575,8 @@ def main():
     ap.add_argument("--seq-rooms", type=int, default=64,
                     help="time-to-error: rooms optimised one after another for the plain arm")
     ap.add_argument("--check-every", type=int, default=50, help="time-to-error: iterations between error reads")
+    ap.add_argument("--halve-every", type=int, default=0,
+                    help="time-to-error: halve the learning rate every N iterations (0 = constant)")
     ap.add_argument("--max-iters", type=int, default=6000)
     ap.add_argument("--monitor-every", type=int, default=250)
     ap.add_argument("--monitor-spp", type=int, default=1024)
@@ -574,6 +600,8 @@ def main():
         WORKLOAD["cache"] = dict(b_term=args.cache, train_spp=max(1, WORKLOAD["spp_r"] // 16), train_steps=4,
                                  lr=1e-2)
     rank, world, local = dist_env()
+    if args.workload == "cornell64" and not args.time_to_error:
+        ap.error("--workload cornell64 is a time-to-error workload (add --time-to-error)")
     if args.impl == "ours" and args.time_to_error:
         run_time_to_error(args)
         return

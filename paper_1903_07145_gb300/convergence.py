@@ -15,6 +15,7 @@ few pixels), so its albedo is left free but not scored.  Iterations run as batch
 from __future__ import annotations
 
 import time
+from dataclasses import replace
 
 import numpy as np
 import torch
@@ -62,8 +63,15 @@ def prepare(scenes, opts: TraceOptions, target_spp: int = 1024, init: float = 0.
     return ss, masks
 
 
+def adam_at(adam: AdamOptions, it: int, halve_every: int) -> AdamOptions:
+    """The learning rate halved every `halve_every` iterations (0: constant)."""
+    if not halve_every:
+        return adam
+    return replace(adam, lr=adam.lr * 0.5 ** (it // halve_every))
+
+
 def time_to_error(ss: SceneSet, masks, opts: TraceOptions, adam: AdamOptions, threshold: float = 0.01,
-                  max_iters: int = 20000, check_every: int = 50):
+                  max_iters: int = 20000, check_every: int = 50, halve_every: int = 0):
     """Runs the batch until every member reaches the threshold (or
     max_iters).  Returns per-member (iterations, seconds) of the first
     crossing (None if never) and the error history."""
@@ -76,8 +84,8 @@ def time_to_error(ss: SceneSet, masks, opts: TraceOptions, adam: AdamOptions, th
     while it < max_iters and any(f is None for f in first):
         torch.cuda.synchronize(ss.device)
         t0 = time.perf_counter()
-        for _ in range(check_every):
-            ss.batch_step(opts, adam, want_losses=False)
+        for k in range(check_every):
+            ss.batch_step(opts, adam_at(adam, it + k, halve_every), want_losses=False)
         torch.cuda.synchronize(ss.device)
         elapsed += time.perf_counter() - t0
         it += check_every
@@ -105,7 +113,7 @@ def prepare_single(scene, opts: TraceOptions, target_spp: int = 1024, init: floa
 
 def time_to_error_single(tr: Tracer, mask, opts: TraceOptions, adam: AdamOptions, threshold: float = 0.01,
                          max_iters: int = 20000, check_every: int = 50, monitor_every: int = 0,
-                         monitor_spp: int = 64):
+                         monitor_spp: int = 64, halve_every: int = 0):
     """ipt_step on one scene until its parameter error falls to the
     threshold.  With the radiance cache active, every `monitor_every`
     iterations ipt_cache_bias compares the cached and plain estimators (set 0
@@ -122,7 +130,7 @@ def time_to_error_single(tr: Tracer, mask, opts: TraceOptions, adam: AdamOptions
         torch.cuda.synchronize(tr.device)
         t0 = time.perf_counter()
         for _ in range(check_every):
-            tr.step(opts, adam, want_loss=False)
+            tr.step(opts, adam_at(adam, it, halve_every), want_loss=False)
             it += 1
             if cached and it % monitor_every == 0:
                 tr.cache_bias(opts, monitor_spp, iteration=1_000_000 + it)

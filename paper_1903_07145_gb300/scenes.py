@@ -185,6 +185,31 @@ def cornell_box(seed: int = 1000, width: int = 64, height: int = 64) -> Scene:
                  light_segments=[1], spp=16, max_depth=3)
 
 
+def cornell_variant(k: int) -> Scene:
+    """Scene k of a 64-scene family of Cornell boxes (seed 6000 + k): the
+    box of cornell_box with its two cuboids resized, moved and yawed at
+    random, new materials, and one view at one of 32^2, 48^2, 64^2, 96^2 or
+    128^2 pixels.  34 triangles, 7 segments, the emitting ceiling in view."""
+    rng = np.random.default_rng(6000 + k)
+    mb = _MeshBuilder()
+    mb.quad_grid([0, 0, 0], [0, 0, 1], [1, 0, 0], 1, 1, 0)
+    mb.quad_grid([0, 1, 0], [1, 0, 0], [0, 0, 1], 1, 1, 1)
+    mb.quad_grid([0, 0, 0], [1, 0, 0], [0, 1, 0], 1, 1, 2)
+    mb.quad_grid([0, 0, 0], [0, 1, 0], [0, 0, 1], 1, 1, 3)
+    mb.quad_grid([1, 0, 0], [0, 0, 1], [0, 1, 0], 1, 1, 4)
+    a = (rng.uniform(0.22, 0.38), rng.uniform(0.25, 0.45))
+    b = (rng.uniform(0.62, 0.78), rng.uniform(0.55, 0.75))
+    mb.cuboid(a, 1e-3, (rng.uniform(0.2, 0.3), rng.uniform(0.3, 0.7), rng.uniform(0.2, 0.3)),
+              math.radians(rng.uniform(-30.0, 30.0)), 1, 5)
+    mb.cuboid(b, 1e-3, (rng.uniform(0.2, 0.3), rng.uniform(0.2, 0.4), rng.uniform(0.2, 0.3)),
+              math.radians(rng.uniform(-30.0, 30.0)), 1, 6)
+    pos, idx, seg = mb.finish()
+    res = [32, 48, 64, 96, 128][int(rng.integers(0, 5))]
+    cam = Camera(np.array([[1, 0, 0, 0.5], [0, 1, 0, 0.5], [0, 0, 1, 2.2]], np.float32), 40.0, res, res)
+    gt = random_materials(rng, 7, [1])
+    return Scene(f"cornell_variant_{k}", pos, idx, seg, 7, [cam], gt, light_segments=[1], spp=16, max_depth=3)
+
+
 def _obb_overlap(a, b, margin=0.0):
     """Separating-axis test of two yawed rectangles (cx, cz, hx, hz, yaw)."""
     def axes(r):
