@@ -142,3 +142,69 @@ def time_to_error_single(tr: Tracer, mask, opts: TraceOptions, adam: AdamOptions
         if err <= threshold:
             first = (it, elapsed)
     return first, history
+
+
+
+def _fine_free_mask(sc) -> np.ndarray:
+    """Per-triangle phases: the diffuse albedo of every non-light triangle and
+    the emission of the light triangles are free (App. E keeps the lights
+    fixed but lets their emission change)."""
+    lights = np.zeros(sc.n_segments, bool)
+    lights[np.asarray(sc.light_segments, int)] = True
+    free = np.zeros((sc.n_segments, 10), bool)
+    free[~lights, 0:3] = True
+    free[lights, 7:10] = True
+    return free
+
+
+def coarse_to_fine(scene, opts: TraceOptions, adam: AdamOptions, iters=(300, 300, 300), split_fraction=0.25,
+                   target_spp: int = 256, seed: int = 0, device: int = 0):
+    """The paper's coarse-to-fine schedule (App. E, App. B) on one scene:
+    (1) one albedo and one emission per object, from zero; (2) every
+    triangle its own segment, started from (1), lights fixed except their
+    emission; (3) the triangles whose covered pixels have the highest mean
+    squared error (the top `split_fraction` of those seen) split in four,
+    children started from their parent.  The captured images are rendered
+    from the per-triangle truth (the scene's texture when it has one).
+    Returns per phase (scene, recovered parameters, image relative L2 error
+    against the captured images)."""
+    from .scenes import per_triangle, subdivide
+    truth = per_triangle(scene)
+    tr = Tracer(truth, device=device, seed=seed)
+    tr.set_params(truth.gt_params)
+    tgt = tr.render(opts, view=-1, set_id=2, spp=target_spp)
+    tr.close()
+
+    def optimise(sc, p0, free, n):
+        t = Tracer(sc, device=device, seed=seed)
+        t.set_targets(tgt)
+        t.set_params(p0, free_mask=free.astype(np.uint8))
+        for _ in range(n):
+            t.step(opts, adam, want_loss=False)
+        img = t.render(opts, view=-1, set_id=0, spp=target_spp)
+        return t, img, float(torch.linalg.norm(img - tgt) / torch.linalg.norm(tgt))
+
+    phases = []
+    free = diffuse_and_emission_mask(scene)
+    p0 = scene.gt_params.copy()
+    p0[free] = 0.0
+    t, _, err = optimise(scene, p0, free, iters[0])
+    p1 = t.get_params()
+    t.close()
+    phases.append((scene, p1, err))
+    fine = per_triangle(scene, p1)
+    t, img, err = optimise(fine, fine.start_params, _fine_free_mask(fine), iters[1])
+    p2 = t.get_params()
+    e = metrics.triangle_pixel_errors(t, fine, img, tgt)
+    t.close()
+    phases.append((fine, p2, err))
+    lights = np.zeros(fine.n_segments, bool)
+    lights[np.asarray(fine.light_segments, int)] = True
+    seen = np.isfinite(e) & ~lights
+    k = max(1, int(split_fraction * seen.sum()))
+    thr = np.sort(e[seen])[::-1][k - 1]
+    fine3 = subdivide(fine, seen & (e >= thr), p2)
+    t, _, err = optimise(fine3, fine3.start_params, _fine_free_mask(fine3), iters[2])
+    phases.append((fine3, t.get_params(), err))
+    t.close()
+    return phases

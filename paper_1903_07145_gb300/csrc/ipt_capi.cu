@@ -407,7 +407,10 @@ ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params) {
     A(&w.sh_ge, cap);
     A(&w.sh_gm, cap);
     A(&w.sh_n, cap);
-    A(&w.blk, (size_t)ipt::wf_max_blocks(ctx->L) * keep_params);
+    // block-private rows for chunks whose accumulators fit in shared memory;
+    // a wider chunk accumulates in one row in global memory
+    const size_t shared_params = std::min<size_t>(keep_params, 10u * ipt::wf_max_segments());
+    A(&w.blk, std::max((size_t)ipt::wf_max_blocks(ctx->L) * shared_params, (size_t)keep_params));
   }
   if (e != cudaSuccess) {
     wf_release(ctx);
@@ -528,7 +531,7 @@ ipt_status run_adjoint(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t 
   } else {
     Timed tm(ctx, IPT_KERNEL_ADJOINT);
     IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
-                               tp, g_img + 3 * (size_t)begin, grad_acc, ctx->err_dev, ctx->stream));
+                               tp, g_img + 3 * (size_t)begin, grad_acc, s->grad_f, ctx->err_dev, ctx->stream));
   }
   return IPT_OK;
 }
@@ -1486,7 +1489,7 @@ extern "C" ipt_status ipt_backward_noalloc(ipt_ctx* ctx, int32_t scene, const ip
   IPT_CK(cudaMemsetAsync(acc, 0, np * sizeof(double), ctx->stream));
   IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), 0,
                              (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
-                             grad_image, acc, ctx->err_dev, ctx->stream));
+                             grad_image, acc, nullptr, ctx->err_dev, ctx->stream));
   IPT_CK(ipt::launch_finalize(nullptr, 0, nullptr, acc, grad_out, np, ctx->stream));
   return IPT_OK;
 }

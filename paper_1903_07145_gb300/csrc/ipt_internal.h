@@ -124,10 +124,16 @@ cudaError_t launch_forward(const Launcher& L, const SceneBuffers& s, const SegBu
                            const float* target, float* g_out, double* loss_partials,
                            float g_scale, int loss_kind, uint32_t* err, cudaStream_t st);
 
+// gacc_scratch: 10 * n_seg floats, used (and required) when the scene has
+// more than wf_max_segments() segments; may be null otherwise.
 cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
                            const ViewHost* views_dev, uint32_t n_views, uint32_t pix_begin, uint32_t n_pix,
                            const TraceParams& tp, const float* g_img, double* grad_acc,
-                           uint32_t* err, cudaStream_t st);
+                           float* gacc_scratch, uint32_t* err, cudaStream_t st);
+
+// Segments whose gradient accumulators fit a block's shared memory; chunks
+// (or scenes) with more accumulate in global memory.
+uint32_t wf_max_segments();
 
 cudaError_t launch_finalize(const double* loss_partials, int n_partials, double* loss_dev,
                             const double* grad_acc, float* grad_out, uint32_t n_params,

@@ -271,10 +271,14 @@ template <int MAXD>
 __global__ void __launch_bounds__(kBlockThreads) k_adjoint(SceneDev s, SegDev t, const ViewDev* views,
                                                            uint32_t n_views, uint32_t pix_begin, uint32_t n_pix,
                                                            PathParams pp, const float* g_img, double* grad_acc,
-                                                           uint32_t* err) {
-  extern __shared__ float sgrad[];
+                                                           float* gacc, uint32_t* err) {
+  // per-block accumulators in shared memory, or (scenes with too many
+  // segments for it) one zeroed accumulator in global memory
+  extern __shared__ float sgrad_sh[];
+  float* sgrad = gacc ? gacc : sgrad_sh;
   const uint32_t n_par = 10u * s.n_seg;
-  for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) sgrad[i] = 0.0f;
+  if (!gacc)
+    for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) sgrad[i] = 0.0f;
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t G = pp.group;
@@ -298,10 +302,16 @@ __global__ void __launch_bounds__(kBlockThreads) k_adjoint(SceneDev s, SegDev t,
       adjoint_path<MAXD>(s, t, vw, px, py, pid, smp, pp, W, gp, sgrad, err);
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) {
-    const float v = sgrad[i];
-    if (v != 0.0f) atomicAdd(&grad_acc[i], (double)v);
-  }
+  if (!gacc)
+    for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) {
+      const float v = sgrad[i];
+      if (v != 0.0f) atomicAdd(&grad_acc[i], (double)v);
+    }
+}
+
+__global__ void k_add_to_double(const float* src, uint32_t n, double* dst) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] += (double)src[i];
 }
 
 // One block: fixed-order sums (deterministic for a fixed grid).
@@ -482,10 +492,18 @@ cudaError_t launch_forward(const Launcher& L, const SceneBuffers& s, const SegBu
 cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
                            const ViewHost* views_dev, uint32_t n_views, uint32_t pix_begin, uint32_t n_pix,
                            const TraceParams& tp, const float* g_img, double* grad_acc,
-                           uint32_t* err, cudaStream_t st) {
+                           float* gacc_scratch, uint32_t* err, cudaStream_t st) {
   const PathParams pp = make_path_params(tp, s);
   const uint64_t tasks = (n_pix + (32 / pp.group) - 1) / (32 / pp.group);
-  const size_t shmem = sizeof(float) * 10u * s.n_seg;
+  // above wf_max_segments() segments the accumulators move to global memory
+  const bool global = s.n_seg > wf_max_segments();
+  if (global && !gacc_scratch) return cudaErrorInvalidValue;
+  float* gacc = global ? gacc_scratch : nullptr;
+  const size_t shmem = global ? 0 : sizeof(float) * 10u * s.n_seg;
+  if (global) {
+    cudaError_t e = cudaMemsetAsync(gacc, 0, sizeof(float) * 10u * s.n_seg, st);
+    if (e != cudaSuccess) return e;
+  }
   const ViewDev* vd = reinterpret_cast<const ViewDev*>(views_dev);
   const int md = tp.max_depth < 1 ? 1 : (int)tp.max_depth;
 #define IPT_LAUNCH_ADJ(D, I)                                                                         \
@@ -494,7 +512,7 @@ cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBu
       cudaFuncSetAttribute(k_adjoint<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);  \
     const int grid = grid_for(tasks, L.num_sms * L.adj_blocks_per_sm[I]);                            \
     k_adjoint<D><<<grid, kBlockThreads, shmem, st>>>(scene_dev(s), seg_dev(t), vd, n_views, pix_begin, n_pix, pp, \
-                                                     g_img, grad_acc, err);                          \
+                                                     g_img, grad_acc, gacc, err);                    \
   }
   if (md <= 2)
     IPT_LAUNCH_ADJ(2, 0)
@@ -505,6 +523,7 @@ cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBu
   else
     IPT_LAUNCH_ADJ(8, 3)
 #undef IPT_LAUNCH_ADJ
+  if (global) k_add_to_double<<<(10u * s.n_seg + 255) / 256, 256, 0, st>>>(gacc, 10u * s.n_seg, grad_acc);
   return cudaGetLastError();
 }
 

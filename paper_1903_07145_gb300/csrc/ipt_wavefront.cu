@@ -79,6 +79,7 @@ struct WfParams {
   int nee, mis, profile, loss_kind;
   uint32_t n_scenes;
   uint32_t seg_lo, seg_n;    // segment range of the chunk's gradient accumulators
+  float* gacc;               // accumulators in global memory (chunks too wide for shared memory), or nullptr
   uint32_t cache_k;          // vertex where the radiance cache ends paths (kNoCache: off)
   int cache_record;          // training pass: record at cache_k, gather only from there on
   CacheBuffers cb;
@@ -659,9 +660,10 @@ __device__ __forceinline__ void add_to_carry(const WfDev& w, uint32_t slot, floa
 // next-event candidate.
 __global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
                                                        int cur) {
-  extern __shared__ float sacc[];
+  extern __shared__ float sacc_sh[];
+  float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = 10u * lp.seg_n;
-  acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, np);
   const uint32_t n = w.cnt[cur];
   const uint32_t si = set_iter(lp);
   const float inv_spp = 1.0f / (float)lp.spp;
@@ -753,15 +755,16 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfPar
       w.sh_n[sq] = make_float4(cn.x, cn.y, cn.z, dsdr);
     }
   }
-  acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush(sacc, np, w.blk);
 }
 
 // Unoccluded next-event terms: light emission (Eq. 5), the vertex material
 // (Eq. 6 at this vertex) and the carry of the earlier vertices.
 __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab, WfParams lp, WfDev w) {
-  extern __shared__ float sacc[];
+  extern __shared__ float sacc_sh[];
+  float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = 10u * lp.seg_n;
-  acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, np);
   const uint32_t n = w.cnt[2];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (!w.sh_vis[i]) continue;
@@ -776,15 +779,16 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
     atomicAdd(&sacc[acc_ix(e, lp, (int)m.z, 6)], dot(q, f3(mb.x, mb.y, mb.z)) * cn.w);
     add_to_carry(w, m.x, xyz(cn));
   }
-  acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush(sacc, np, w.blk);
 }
 
 // Stage B: BRDF sampling; the new vertex joins the carry.
 __global__ void __launch_bounds__(kWfThreads) wf_adj_b(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
                                                        int cur) {
-  extern __shared__ float sacc[];
+  extern __shared__ float sacc_sh[];
+  float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = 10u * lp.seg_n;
-  acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, np);
   if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;
   const uint32_t n = w.cnt[cur];
   const uint32_t si = set_iter(lp);
@@ -858,16 +862,17 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_b(const WfScene* tab, WfPar
       w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
     }
   }
-  acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush(sacc, np, w.blk);
 }
 
 // Paths closed by the cache: its prediction joins the earlier vertices'
 // carry (Eq. 6 through their BSDF factors), its parameter derivative goes to
 // the terminal segment's kd, ks and roughness, and the path finishes.
 __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w) {
-  extern __shared__ float sacc[];
+  extern __shared__ float sacc_sh[];
+  float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = 10u * lp.seg_n;
-  acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, np);
   const uint32_t n = lp.cb.counts[0];
   const float inv_spp = 1.0f / (float)lp.spp;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -885,7 +890,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
     finish_path(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
     w.beta[slot].w = __uint_as_float(st | kDead);
   }
-  acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush(sacc, np, w.blk);
 }
 
 // grad_acc[i] += sum over block rows (FP64), for the chunk's parameters.
@@ -1008,6 +1013,7 @@ static WfParams wf_params(const TraceParams& tp, int loss_kind, uint32_t n_scene
   p.n_scenes = n_scenes;
   p.seg_lo = 0;
   p.seg_n = 0;
+  p.gacc = nullptr;
   p.cache_k = kNoCache;
   p.cache_record = 0;
   p.cb = CacheBuffers{};
@@ -1149,10 +1155,15 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
   const int grid = wf_grid(L);
   const int grid_cam = one_wave(L, wf_camera, 0);
   const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, wf_max_segments());
-  uint32_t max_np = 0;
-  for (const WfChunk& c : chunks) max_np = std::max(max_np, 10u * c.seg_n);
+  // chunks of more than wf_max_segments() segments (one scene with that many)
+  // accumulate with atomics in global memory instead of shared memory
+  uint32_t max_np = 0, max_np_shared = 0;
+  for (const WfChunk& c : chunks) {
+    max_np = std::max(max_np, 10u * c.seg_n);
+    if (c.seg_n <= wf_max_segments()) max_np_shared = std::max(max_np_shared, 10u * c.seg_n);
+  }
   if (max_np > wb.blk_params) return cudaErrorInvalidValue;
-  const size_t shmem = max_np * sizeof(float);
+  const size_t shmem = max_np_shared * sizeof(float);
   if (shmem > 48 * 1024) {
     cudaFuncSetAttribute(wf_adj_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     cudaFuncSetAttribute(wf_adj_connect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
@@ -1163,12 +1174,15 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
     lp.seg_lo = c.seg_lo;
     lp.seg_n = c.seg_n;
     const uint32_t np = 10u * c.seg_n;
-    const size_t sm = np * sizeof(float);
+    const bool global = c.seg_n > wf_max_segments();
+    lp.gacc = global ? wb.blk : nullptr;
+    const size_t sm = global ? 0 : np * sizeof(float);
     // each adjoint stage runs one wave at its own occupancy for this
     // accumulator size; block b of every stage adds into gradient row b
+    // (all blocks into row 0 in global mode)
     const int g_a = one_wave(L, wf_adj_a, sm), g_c = one_wave(L, wf_adj_connect, sm);
     const int g_b = one_wave(L, wf_adj_b, sm), g_q = one_wave(L, wf_adj_cache, sm);
-    const int rows = std::max(std::max(g_a, g_c), std::max(g_b, g_q));
+    const int rows = global ? 1 : std::max(std::max(g_a, g_c), std::max(g_b, g_q));
     if (rows > wf_max_blocks(L)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(wb.blk, 0, (size_t)rows * np * sizeof(float), st);
     if (e != cudaSuccess) return e;

@@ -49,3 +49,25 @@ def identifiable_mask(gt: np.ndarray, visible: np.ndarray, roughness_min_lum: fl
 def param_error(params: np.ndarray, gt: np.ndarray, mask: np.ndarray) -> float:
     d = (np.asarray(params, np.float64) - np.asarray(gt, np.float64))[mask]
     return float(np.linalg.norm(d) / np.linalg.norm(np.asarray(gt, np.float64)[mask]))
+
+
+def triangle_pixel_errors(tracer, scene, image, target) -> np.ndarray:
+    """Per triangle (original ids): the mean over the pixels whose centre ray
+    hits it of the squared RGB residual |I - T|^2 (App. B subdivides the
+    triangles where this average is high); NaN where no pixel centre lands."""
+    img = np.asarray(image.cpu() if hasattr(image, "cpu") else image, np.float64).reshape(-1, 3)
+    tgt = np.asarray(target.cpu() if hasattr(target, "cpu") else target, np.float64).reshape(-1, 3)
+    sums = np.zeros(scene.n_tri)
+    cnt = np.zeros(scene.n_tri)
+    off = 0
+    for cam in scene.cameras:
+        n = cam.width * cam.height
+        o, d = pixel_center_rays(cam)
+        tri = tracer.trace_rays(torch.from_numpy(o), torch.from_numpy(d))[0].cpu().numpy()
+        r = ((img[off:off + n] - tgt[off:off + n]) ** 2).sum(axis=1)
+        hit = tri >= 0
+        np.add.at(sums, tri[hit], r[hit])
+        np.add.at(cnt, tri[hit], 1.0)
+        off += n
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return sums / cnt

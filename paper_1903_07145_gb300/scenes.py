@@ -210,6 +210,109 @@ def cornell_variant(k: int) -> Scene:
     return Scene(f"cornell_variant_{k}", pos, idx, seg, 7, [cam], gt, light_segments=[1], spp=16, max_depth=3)
 
 
+def cornell_textured(seed: int = 1000, sub: int = 16, width: int = 64, height: int = 64) -> Scene:
+    """The Cornell box with its five walls split into sub x sub quads and a
+    4 x 4 checker of two diffuse albedos on the floor and the back wall (a
+    texture that per-segment parameters cannot represent); the segments are
+    the objects, as in cornell_box.  gt_params holds the per-segment values
+    (the checker's mean on the floor and back wall) and tri_albedo the
+    per-triangle diffuse albedo the images are rendered with (see
+    per_triangle)."""
+    rng = np.random.default_rng(seed)
+    mb = _MeshBuilder()
+    mb.quad_grid([0, 0, 0], [0, 0, 1], [1, 0, 0], sub, sub, 0)
+    mb.quad_grid([0, 1, 0], [1, 0, 0], [0, 0, 1], sub, sub, 1)
+    mb.quad_grid([0, 0, 0], [1, 0, 0], [0, 1, 0], sub, sub, 2)
+    mb.quad_grid([0, 0, 0], [0, 1, 0], [0, 0, 1], sub, sub, 3)
+    mb.quad_grid([1, 0, 0], [0, 0, 1], [0, 1, 0], sub, sub, 4)
+    mb.cuboid((0.32, 0.36), 1e-3, (0.28, 0.6, 0.28), math.radians(15.0), 1, 5)
+    mb.cuboid((0.70, 0.64), 1e-3, (0.30, 0.3, 0.30), 0.0, 1, 6)
+    pos, idx, seg = mb.finish()
+    cam = Camera(np.array([[1, 0, 0, 0.5], [0, 1, 0, 0.5], [0, 0, 1, 2.2]], np.float32), 40.0, width, height)
+    gt = random_materials(rng, 7, [1])
+    gt[:, 3:6] = 0.0   # diffuse only: the texture is an albedo texture
+    tri_kd = gt[seg, 0:3].astype(np.float64).copy()
+    c = pos[idx].mean(axis=1)
+    dark, light = rng.uniform(0.1, 0.3, 3), rng.uniform(0.6, 0.9, 3)
+    for s_id, (a, b) in ((0, (0, 2)), (2, (0, 1))):
+        on = seg == s_id
+        check = ((np.floor(c[:, a] * 4) + np.floor(c[:, b] * 4)) % 2 == 1)
+        tri_kd[on & check] = light
+        tri_kd[on & ~check] = dark
+        gt[s_id, 0:3] = tri_kd[on].mean(axis=0)
+    sc = Scene("cornell_textured", pos, idx, seg, 7, [cam], gt, light_segments=[1], spp=16, max_depth=3)
+    sc.tri_albedo = tri_kd.astype(np.float32)
+    return sc
+
+
+def per_triangle(scene: Scene, params: np.ndarray | None = None) -> Scene:
+    """The same geometry with every triangle its own segment (the paper's
+    refinement from per-object to per-triangle material parameters, App. E).
+    Triangle t starts from the parameters of its old segment (params, or
+    the ground truth); the new ground truth takes a per-triangle albedo when
+    the scene carries one (tri_albedo).  Light segments map to their
+    triangles."""
+    T = scene.n_tri
+    seg = np.asarray(scene.tri_segment, np.int64)
+    gt = np.asarray(scene.gt_params, np.float32)[seg].copy()
+    if getattr(scene, "tri_albedo", None) is not None:
+        gt[:, 0:3] = scene.tri_albedo
+    lights = [int(t) for t in np.nonzero(np.isin(seg, np.asarray(scene.light_segments, np.int64)))[0]]
+    out = Scene(scene.name + "_per_triangle", scene.positions, scene.indices, np.arange(T, dtype=np.uint32), T,
+                scene.cameras, gt, normals=scene.normals, emission_scale=scene.emission_scale,
+                light_segments=lights, spp=scene.spp, max_depth=scene.max_depth)
+    out.start_params = (np.asarray(params, np.float32)[seg].copy() if params is not None
+                        else np.asarray(scene.gt_params, np.float32)[seg].copy())
+    if getattr(scene, "tri_albedo", None) is not None:
+        out.tri_albedo = scene.tri_albedo
+    return out
+
+
+def subdivide(scene: Scene, split: np.ndarray, params: np.ndarray | None = None) -> Scene:
+    """Splits the triangles with split[t] into four at their edge midpoints
+    (adaptive subdivision, App. B); every triangle stays its own segment and
+    the four children inherit their parent's parameters (params, else
+    start_params, else the ground truth) and ground truth.  A split
+    triangle's midpoints lie on its neighbours' edges, so the surface is
+    unchanged."""
+    P = np.asarray(scene.positions, np.float64)
+    I = np.asarray(scene.indices, np.int64)
+    split = np.asarray(split, bool)
+    base = params if params is not None else getattr(scene, "start_params", scene.gt_params)
+    base = np.asarray(base, np.float32)
+    gt = np.asarray(scene.gt_params, np.float32)
+    new_pos = [P]
+    mid_id = {}
+
+    def mid(a, b):
+        k = (min(a, b), max(a, b))
+        if k not in mid_id:
+            mid_id[k] = len(P) + len(mid_id)
+            new_pos.append(((P[a] + P[b]) * 0.5)[None])
+        return mid_id[k]
+
+    tris, owner = [], []
+    for t, (a, b, c) in enumerate(I):
+        if not split[t]:
+            tris.append((a, b, c))
+            owner.append(t)
+            continue
+        ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+        for tri in ((a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)):
+            tris.append(tri)
+            owner.append(t)
+    owner = np.asarray(owner, np.int64)
+    lights = set(int(x) for x in scene.light_segments)
+    out = Scene(scene.name + "_sub", np.concatenate(new_pos).astype(np.float32),
+                np.asarray(tris, np.uint32), np.arange(len(tris), dtype=np.uint32), len(tris), scene.cameras,
+                gt[owner].copy(), emission_scale=scene.emission_scale,
+                light_segments=[i for i, o in enumerate(owner) if int(o) in lights], spp=scene.spp,
+                max_depth=scene.max_depth)
+    out.start_params = base[owner].copy()
+    out.parent = owner
+    return out
+
+
 def _obb_overlap(a, b, margin=0.0):
     """Separating-axis test of two yawed rectangles (cx, cz, hx, hz, yaw)."""
     def axes(r):

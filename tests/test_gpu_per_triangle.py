@@ -1,0 +1,112 @@
+"""Per-triangle parameters (App. E: after the per-object phase every triangle
+gets its own material parameters; App. B: triangles whose pixels keep a high
+error are subdivided).  A scene with more segments than fit a block's shared
+accumulators takes the global-memory accumulation path in both integrators;
+its gradient must match the FP64 oracle.  The coarse-to-fine schedule must
+lower the image error phase by phase on a textured scene."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_1903_07145_gb300 import convergence, scenes  # noqa: E402
+from paper_1903_07145_gb300.tracer import AdamOptions, TraceOptions, Tracer  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+SEED = 77
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    return True
+
+
+@pytest.mark.parametrize("integrator", ["wavefront", "megakernel"])
+def test_per_triangle_gradient_matches_oracle(built, integrator):
+    sc = scenes.per_triangle(scenes.cornell_textured(1000, 32, 32, 24))
+    assert sc.n_segments > 5120  # more than the shared accumulators hold
+    rng = np.random.default_rng(3)
+    p = sc.gt_params.astype(np.float64).copy()
+    p[:, 0:3] = rng.uniform(0.2, 0.8, (sc.n_segments, 3))
+    targets = [rng.uniform(0.0, 0.8, (32 * 24, 3))]
+    osc = O.OracleScene(sc)
+    lo, go = O.loss_grad(osc, p, targets, 8, 8, 3, iteration=2, seed=SEED)
+    tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator)
+    tr.set_params(p.astype(np.float32))
+    tr.set_targets(torch.from_numpy(targets[0].astype(np.float32)).cuda())
+    lg, gg = tr.loss_grad(TraceOptions(spp_r=8, spp_d=8, max_depth=3), iteration=2)
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert abs(lg - lo) <= 1e-3 * abs(lo)
+    cos = float((gg * go).sum() / (np.linalg.norm(gg) * np.linalg.norm(go)))
+    rel = float(np.linalg.norm(gg - go) / np.linalg.norm(go))
+    assert cos >= 0.999 and rel <= 1e-2, (cos, rel)
+    assert np.count_nonzero(go[:, 0:3]) > 1000  # many triangles get a gradient
+    tr.close()
+
+
+def jittered_rays(cam, n, seed):
+    """Camera rays through uniformly random points of the image (no ray sits
+    on the regular grid of the walls' quad edges)."""
+    rng = np.random.default_rng(seed)
+    W, H = cam.width, cam.height
+    th = np.tan(0.5 * np.radians(cam.fov_y_deg))
+    px, py = rng.uniform(0, W, n), rng.uniform(0, H, n)
+    dc = np.stack([(2 * px / W - 1) * th * W / H, (1 - 2 * py / H) * th, -np.ones(n)], -1)
+    M = np.asarray(cam.cam_to_world, np.float64)
+    d = dc @ M[:, :3].T
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = np.broadcast_to(M[:, 3], d.shape)
+    return torch.from_numpy(o.astype(np.float32).copy()), torch.from_numpy(d.astype(np.float32))
+
+
+def test_subdivision_keeps_the_surface(built):
+    """Split triangles cover the same surface: a ray hits a child of the
+    triangle it hit before the split, at the same distance."""
+    base = scenes.per_triangle(scenes.cornell_textured(1000, 8, 24, 24))
+    split = np.zeros(base.n_tri, bool)
+    split[::3] = True
+    sub = scenes.subdivide(base, split)
+    o, d = jittered_rays(base.cameras[0], 20000, 1)
+    a, b = Tracer(base), Tracer(sub)
+    ta, da = [x.cpu().numpy() for x in a.trace_rays(o, d)[:2]]
+    tb, db = [x.cpu().numpy() for x in b.trace_rays(o, d)[:2]]
+    hit = ta >= 0
+    assert np.array_equal(hit, tb >= 0)
+    assert np.mean(sub.parent[tb[hit]] == ta[hit]) >= 0.999
+    assert np.allclose(da[hit], db[hit], rtol=1e-5)
+    a.close()
+    b.close()
+
+
+def test_coarse_to_fine_lowers_the_image_error(built):
+    """Per-object parameters cannot show the checker on the floor and back
+    wall; per-triangle ones can: the image error drops and the albedo seen
+    through the pixels of those two walls moves towards the texture."""
+    from paper_1903_07145_gb300 import metrics
+    sc = scenes.cornell_textured(1000, 8, 64, 64)
+    opts = TraceOptions(spp_r=16, spp_d=16, max_depth=3)
+    phases = convergence.coarse_to_fine(sc, opts, AdamOptions(lr=2e-2), iters=(400, 600, 300), target_spp=256,
+                                        seed=5)
+    errs = [e for _, _, e in phases]
+    assert errs[1] < 0.7 * errs[0], errs
+    assert errs[2] <= 1.05 * errs[1], errs
+    # the diffuse albedo of the triangle under each pixel centre
+    o, d = metrics.pixel_center_rays(sc.cameras[0])
+    t = Tracer(sc)
+    tri = t.trace_rays(torch.from_numpy(o), torch.from_numpy(d))[0].cpu().numpy()
+    t.close()
+    seg = np.asarray(sc.tri_segment)
+    on = (tri >= 0)
+    on[on] = np.isin(seg[tri[on]], [0, 2])
+    truth = sc.tri_albedo[tri[on]]
+    per_object = phases[0][1][seg[tri[on]], 0:3]
+    per_triangle = phases[1][1][tri[on], 0:3]
+    e_obj = np.linalg.norm(per_object - truth) / np.linalg.norm(truth)
+    e_tri = np.linalg.norm(per_triangle - truth) / np.linalg.norm(truth)
+    assert e_tri < 0.6 * e_obj, (e_obj, e_tri)
