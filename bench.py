@@ -134,17 +134,23 @@ def measured_peaks():
 # DRAM traffic of the dominant kernel comes from a committed ncu capture (the
 # benchmark cannot read hardware counters itself).  It is reported only while
 # the capture matches: same kernel, workload and wavefront configuration, and
-# the traversal sources unchanged since (their SHA-256 is recorded with it).
+# the traversal kernel's sources unchanged since (their SHA-256 is recorded
+# with it): the device header, the wavefront header, and the traversal
+# section of the wavefront source.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wf_closest_room61k_traffic.txt")
-KERNEL_SOURCES = ["paper_1903_07145_gb300/csrc/ipt_wavefront.cu", "paper_1903_07145_gb300/csrc/ipt_wavefront.h",
-                  "paper_1903_07145_gb300/csrc/ipt_device.cuh"]
+CSRC = os.path.join(ROOT, "paper_1903_07145_gb300", "csrc")
+TRAVERSAL_SECTION = ("// Persistent traversal with per-lane refill", "// Forward shading of queue")
 
 
 def kernel_sources_sha256():
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
+    for f in ("ipt_device.cuh", "ipt_wavefront.h"):
+        with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(CSRC, "ipt_wavefront.cu")) as fh:
+        text = fh.read()
+    a, b = text.index(TRAVERSAL_SECTION[0]), text.index(TRAVERSAL_SECTION[1])
+    h.update(text[a:b].encode())
     return h.hexdigest()
 
 
