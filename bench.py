@@ -338,6 +338,17 @@ def run_ours(args, rank, world, local):
         L.ipt_params_get(tr.ctx, tr.sid, host_params.ctypes.data)
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    cache_bias = None
+    if args.cache:
+        # bias of the cached estimator against the plain one (image and loss
+        # gradient, both at 4096 spp), after further training outside the
+        # timed region
+        extra = 300
+        for it in range(extra):
+            tr.cache_train(opts, iteration=100_000 + it)
+        ib, gb = tr.cache_bias(opts, 4096, iteration=200_000)
+        cache_bias = {"training_passes": args.warmup + args.steps + e2e_steps + extra, "spp": 4096,
+                      "image_rel": ib, "grad_rel": gb}
     tr.close()
 
     if rank != 0:
@@ -399,6 +410,8 @@ def run_ours(args, rank, world, local):
         "loss_after": loss_end,
         "wall_s_timed_region": t_wall,
     }
+    if cache_bias is not None:
+        out["cache_bias"] = cache_bias
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

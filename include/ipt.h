@@ -502,6 +502,24 @@ ipt_status ipt_cache_status(ipt_ctx* ctx, int32_t scene, ipt_cache_stats* out);
 ipt_status ipt_cache_bias(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t spp,
                           uint64_t iteration, double* image_bias, double* grad_bias);
 
+/* Checkpoint of a scene's optimisation (to resume a run of the nested SGD of
+ * Sec. 3 later or elsewhere): its parameters, free mask, Adam moments and
+ * step count, its iteration counter and, when it has a radiance cache, the
+ * cache's weights, hash table, their Adam moments and step count and its
+ * on/off state.  Host memory, the library's own layout: a 64-byte header
+ * ("IPTCKPT1", version, segment count, counters, flags) followed by the
+ * arrays.  Save: with buf == NULL, *n receives the size in bytes; with a
+ * buffer, *n must hold at least that size and receives the bytes written.
+ * Load: the checkpoint must come from a scene with the same number of
+ * segments, and a checkpoint with cache state needs a configured cache
+ * (ipt_cache_configure) on the target scene; the cache's options are not part
+ * of the checkpoint.  Batches (ipt_batch_*) keep their own state and are not
+ * covered.  Errors: IPT_ERR_INVALID_ARG for a short buffer, a wrong magic,
+ * version or size, or a segment-count or cache mismatch, before any state
+ * changes. */
+ipt_status ipt_checkpoint_save(ipt_ctx* ctx, int32_t scene, void* buf, size_t* n);
+ipt_status ipt_checkpoint_load(ipt_ctx* ctx, int32_t scene, const void* buf, size_t n);
+
 /* Measurement support (not part of the method).  Achievable bandwidth, in
  * GB/s (1e9 bytes), of random 64-byte line gathers over a device buffer of
  * `bytes` bytes on `device`: four independent gathers in flight per thread,

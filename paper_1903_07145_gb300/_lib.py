@@ -30,7 +30,7 @@ EXPORTED = [
     "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy",
     "ipt_cache_configure", "ipt_cache_weights_set", "ipt_cache_weights_get", "ipt_cache_eval",
     "ipt_cache_grad", "ipt_cache_train", "ipt_cache_records", "ipt_cache_status", "ipt_cache_bias",
-    "ipt_probe_gather",
+    "ipt_probe_gather", "ipt_checkpoint_save", "ipt_checkpoint_load",
 ]
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox",
@@ -120,6 +120,8 @@ def lib():
                 "ipt_trace_rays": [P, I32, U32, P, P, P, P, P, P, P],
                 "ipt_philox": [P, U32, P, P, P],
                 "ipt_pick_pixels": [P, I32, U32, U64, P],
+                "ipt_checkpoint_save": [P, I32, P, C.POINTER(C.c_size_t)],
+                "ipt_checkpoint_load": [P, I32, P, C.c_size_t],
                 "ipt_synchronize": [P],
                 "ipt_scene_info": [P, I32, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32),
                                    C.POINTER(U32), C.POINTER(U32), C.POINTER(U64)],
@@ -239,6 +241,19 @@ def ipt_step(ctx, scene, opts, adam, want_loss):
 
 def ipt_trace_rays(ctx, scene, n, orig, dirs, skip, tri, t, u, v):
     _check(ctx, lib().ipt_trace_rays(ctx, scene, n, orig, dirs, skip, tri, t, u, v))
+
+
+def ipt_checkpoint_save(ctx, scene) -> bytes:
+    n = C.c_size_t(0)
+    _check(ctx, lib().ipt_checkpoint_save(ctx, scene, None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, lib().ipt_checkpoint_save(ctx, scene, buf, C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def ipt_checkpoint_load(ctx, scene, data: bytes):
+    buf = C.create_string_buffer(data, len(data))
+    _check(ctx, lib().ipt_checkpoint_load(ctx, scene, buf, len(data)))
 
 
 def ipt_pick_pixels(ctx, scene, batch, iteration, out):

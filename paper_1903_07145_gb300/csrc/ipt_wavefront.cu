@@ -426,7 +426,10 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev
 // ---------------------------------------------------------------------------
 // Forward shading of queue `cur`.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWfThreads) wf_shade_fwd(const WfScene* tab, WfParams lp, uint32_t p0,
+// The shading and adjoint stages ask for 8 resident blocks of 128 threads per
+// SM (at most 64 registers, a few bytes spilled): they wait on scattered
+// path-state loads, and the extra warps hide more of that latency.
+__global__ void __launch_bounds__(kWfThreads, 8) wf_shade_fwd(const WfScene* tab, WfParams lp, uint32_t p0,
                                                            WfDev w, int cur) {
   if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;  // closest fetch counter of the next vertex
   const uint32_t n = w.cnt[cur];
@@ -658,7 +661,7 @@ __device__ __forceinline__ void add_to_carry(const WfDev& w, uint32_t slot, floa
 
 // Stage A: emission at the vertex, its contribution to the carry, and the
 // next-event candidate.
-__global__ void __launch_bounds__(kWfThreads) wf_adj_a(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
+__global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
                                                        int cur) {
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
@@ -783,7 +786,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
 }
 
 // Stage B: BRDF sampling; the new vertex joins the carry.
-__global__ void __launch_bounds__(kWfThreads) wf_adj_b(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
+__global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
                                                        int cur) {
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;

@@ -201,6 +201,14 @@ class Tracer:
                          _ptr(u), _ptr(v))
         return tri, t, u, v
 
+    def checkpoint(self) -> bytes:
+        """The scene's optimisation state (parameters, Adam state, iteration,
+        radiance cache) as bytes."""
+        return L.ipt_checkpoint_save(self.ctx, self.sid)
+
+    def restore(self, data: bytes):
+        L.ipt_checkpoint_load(self.ctx, self.sid, data)
+
     def pick_pixels(self, batch: int, iteration: int):
         """Global pixel ids of the pixel batch of `iteration` (int32 tensor)."""
         out = torch.empty(max(batch, 1), dtype=torch.int32, device=self.device)
