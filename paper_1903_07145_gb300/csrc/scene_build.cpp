@@ -3,6 +3,7 @@
 // tables used for light selection.  Compiled without floating-point
 // contraction so the FP64 area sums are reproducible across hosts.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -47,7 +48,8 @@ struct BNode {
   int depth = 0;
 };
 
-constexpr int kBins = 16;
+constexpr int kBins = 32;
+constexpr double kCtrav = 1.0;  // SAH: cost of a node step relative to a triangle test
 constexpr uint32_t kMaxLeaf = 8;
 constexpr int kMedianDepth = 48;
 
@@ -129,7 +131,7 @@ struct Builder {
         acc.grow(bins[k]);
         c += cnt[k];
         if (c == 0 || right_cnt[k + 1] == 0) continue;
-        const double cost = 1.0 + (acc.area() * c + right_area[k + 1] * right_cnt[k + 1]) / pa;
+        const double cost = kCtrav + (acc.area() * c + right_area[k + 1] * right_cnt[k + 1]) / pa;
         if (cost < best) {
           best = cost;
           best_axis = ax;
@@ -368,9 +370,57 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
       std::memcpy(&q[13], &cc, 4);
     }
   }
-  // 4-wide quantized nodes: open the largest-area inner child until four
-  // children, depth first (a node precedes its subtree)
+  // 4-wide quantized nodes: the binary tree's subtrees are spread over at
+  // most four child slots per node so as to minimise the surface-area cost
+  // (dynamic programming over "subtree of n in k slots", k = 1..4)
   {
+    const size_t NB = B.nodes.size();
+    const double kCn = 1.0, kCt = 0.4;   // 4-wide node visit vs triangle test (relative cost)
+    std::vector<double> f(NB * 5, 0.0);  // f[n*5+k]: cost of n's subtree in <= k slots
+    std::vector<int8_t> sp(NB * 5, 0);   // split of k slots: i to the left child (0: use k-1)
+    std::vector<int8_t> gi(NB, 1);       // best left share when n is a 4-wide node
+    // children after parents in B.nodes: a reverse sweep sees children first
+    for (size_t t = NB; t-- > 0;) {
+      const BNode& n = B.nodes[t];
+      const double A = n.box.area();
+      if (n.left < 0) {
+        for (int k = 1; k <= 4; ++k) f[t * 5 + k] = kCt * A * n.count;
+        continue;
+      }
+      const size_t L = (size_t)n.left, R = (size_t)n.right;
+      double best = 1e300;
+      for (int i = 1; i <= 3; ++i) {
+        const double c = f[L * 5 + i] + f[R * 5 + 4 - i];
+        if (c < best) {
+          best = c;
+          gi[t] = (int8_t)i;
+        }
+      }
+      f[t * 5 + 1] = kCn * A + best;  // n as one 4-wide node
+      for (int k = 2; k <= 4; ++k) {
+        double b2 = f[t * 5 + k - 1];
+        int8_t choice = 0;
+        for (int i = 1; i <= k - 1; ++i) {
+          const double c = f[L * 5 + i] + f[R * 5 + k - i];
+          if (c < b2) {
+            b2 = c;
+            choice = (int8_t)i;
+          }
+        }
+        f[t * 5 + k] = b2;
+        sp[t * 5 + k] = choice;
+      }
+    }
+    std::function<void(int, int, std::vector<int>&)> collect = [&](int n, int k, std::vector<int>& out) {
+      while (k > 1 && B.nodes[n].left >= 0 && sp[(size_t)n * 5 + k] == 0) --k;
+      if (k == 1 || B.nodes[n].left < 0) {
+        out.push_back(n);
+        return;
+      }
+      const int i = sp[(size_t)n * 5 + k];
+      collect(B.nodes[n].left, i, out);
+      collect(B.nodes[n].right, k - i, out);
+    };
     std::vector<uint32_t>& out = s.nodes4;
     out.clear();
     struct Item {
@@ -389,25 +439,11 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
       std::vector<int> ch;
       const BNode& root = B.nodes[it.bnode];
       if (root.left < 0) {
-        ch.push_back(it.bnode);  // a leaf as the only child (single-leaf scene)
+        ch.push_back(it.bnode);
       } else {
-        ch = {root.left, root.right};
-        while (ch.size() < 4) {
-          int best = -1;
-          double best_area = -1.0;
-          for (size_t i = 0; i < ch.size(); ++i) {
-            const BNode& c = B.nodes[ch[i]];
-            if (c.left >= 0 && c.box.area() > best_area) {
-              best_area = c.box.area();
-              best = (int)i;
-            }
-          }
-          if (best < 0) break;
-          const BNode& c = B.nodes[ch[best]];
-          const int l = c.left, r = c.right;
-          ch[best] = l;
-          ch.push_back(r);
-        }
+        const int i = gi[(size_t)it.bnode];
+        collect(root.left, i, ch);
+        collect(root.right, 4 - i, ch);
       }
       Box u;
       u.reset();
