@@ -519,15 +519,21 @@ def run_time_to_error(args):
                                                 halve_every=args.halve_every)
         res["batched"] = {"first": first, "history_last": hist[-1][:2]}
         ss.close()
-        seq = []
+        # the plain arm: each scene alone with its fastest integrator
+        # configuration (autotuned on its own workload, outside the timing)
+        from paper_1903_07145_gb300 import autotune
+        seq, seq_cfg = [], []
         for i, sc in enumerate(rooms[:args.seq_rooms]):
             tr, m = convergence.prepare_single(sc, tgt, target_spp=target_spp, seed=7)
-            tr.configure("wavefront", wavefront_slots=1 << 21, bvh_width=4)
+            p0 = tr.get_params()
+            best, _ = autotune.tune(tr, lambda: tr.loss_grad(opts, iteration=0), repeats=3)
+            tr.set_params(p0, free_mask=convergence.diffuse_and_emission_mask(sc).astype(np.uint8))
+            seq_cfg.append(best.get("integrator"))
             f, _ = convergence.time_to_error_single(tr, m, opts, adam, threshold=0.01, max_iters=args.max_iters,
                                                     check_every=args.check_every, halve_every=args.halve_every)
             seq.append(f)
             tr.close()
-        res["sequential_plain"] = {"first": seq}
+        res["sequential_plain"] = {"first": seq, "integrators": seq_cfg}
 
         def summary(fs):
             t = np.array([f[1] for f in fs if f is not None])

@@ -141,8 +141,8 @@ typedef struct {
  *     b*spp .. b*spp+spp-1 of each set, and the loss and its gradient are
  *     normalised by the 3B entry-channels, so the batch loss is an unbiased
  *     estimate of the full-image loss.  Accepted by ipt_loss_grad, ipt_step
- *     and ipt_batch_step (every other call requires 0); such passes always
- *     run on the wavefront integrator; not with the radiance cache.
+ *     and ipt_batch_step (every other call requires 0), on either integrator
+ *     (batches of scenes: wavefront); not with the radiance cache.
  *     B * max(spp_r, spp_d) must stay below 2^32. */
 typedef struct {
   uint32_t spp_r;

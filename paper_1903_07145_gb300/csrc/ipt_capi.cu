@@ -476,9 +476,9 @@ ipt_status run_forward(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t 
                        const ipt::TraceParams& tp, float* img, float* msq, const float* target, float* g_out,
                        double* partials, float g_scale, int loss_kind, const ipt::CachePass* cache = nullptr,
                        uint32_t* pick = nullptr) {
-  if ((cache || pick) && !use_wavefront_cap(ctx, tp.spp))
-    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes and pixel batches need spp <= wavefront_slots");
-  if (cache || pick || use_wavefront(ctx, tp.spp)) {
+  if (cache && !use_wavefront_cap(ctx, tp.spp))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes need spp <= wavefront_slots");
+  if (cache || use_wavefront(ctx, tp.spp)) {
     ipt_status st = ensure_wf(ctx, false, 10u * s->n_seg);
     if (st != IPT_OK) return st;
     ipt::WfScene e = wf_entry(ctx, scene_id, s, begin, n);
@@ -496,13 +496,17 @@ ipt_status run_forward(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t 
                            partials, ctx->err_dev, ctx->stream,
                            (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr, cache));
   } else {
-    if (target) {
+    // a pixel batch (begin 0) keeps the whole target: the kernel reads the
+    // drawn pixel's value
+    if (target && !pick) {
       target += 3 * (size_t)begin;
       g_out += 3 * (size_t)begin;
     }
+    ipt::TraceParams tpk = tp;
+    tpk.pick = pick;
     Timed tm(ctx, IPT_KERNEL_FORWARD);
     IPT_CK(ipt::launch_forward(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
-                               tp, img, msq, target, g_out, partials, g_scale, loss_kind, ctx->err_dev,
+                               tpk, img, msq, target, g_out, partials, g_scale, loss_kind, ctx->err_dev,
                                ctx->stream));
   }
   return IPT_OK;
@@ -513,9 +517,9 @@ ipt_status run_forward(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t 
 ipt_status run_adjoint(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t begin, uint32_t n,
                        const ipt::TraceParams& tp, const float* g_img, double* grad_acc,
                        const ipt::CachePass* cache = nullptr, uint32_t* pick = nullptr) {
-  if ((cache || pick) && !use_wavefront_cap(ctx, tp.spp))
-    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes and pixel batches need spp <= wavefront_slots");
-  if (cache || pick || use_wavefront(ctx, tp.spp)) {
+  if (cache && !use_wavefront_cap(ctx, tp.spp))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes need spp <= wavefront_slots");
+  if (cache || use_wavefront(ctx, tp.spp)) {
     ipt_status st = ensure_wf(ctx, true, 10u * s->n_seg);
     if (st != IPT_OK) return st;
     ipt::WfScene e = wf_entry(ctx, scene_id, s, begin, n);
@@ -529,9 +533,12 @@ ipt_status run_adjoint(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t 
                            ctx->err_dev, ctx->stream, (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr,
                            cache));
   } else {
+    ipt::TraceParams tpk = tp;
+    tpk.pick = pick;
     Timed tm(ctx, IPT_KERNEL_ADJOINT);
     IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), begin, n,
-                               tp, g_img + 3 * (size_t)begin, grad_acc, s->grad_f, ctx->err_dev, ctx->stream));
+                               tpk, pick ? g_img : g_img + 3 * (size_t)begin, grad_acc, s->grad_f, ctx->err_dev,
+                               ctx->stream));
   }
   return IPT_OK;
 }

@@ -80,6 +80,8 @@ struct TraceParams {
   // (0 = spp; the derivative pass of a same-set gradient check uses the
   // residual's spp so that its samples are the residual's first ones)
   uint32_t sample_stride = 0;
+  // megakernel: the pixel batch's drawn pixels (entries 0..n-1), or nullptr
+  const uint32_t* pick = nullptr;
 };
 
 struct Launcher {

@@ -205,13 +205,18 @@ __global__ void __launch_bounds__(kBlockThreads) k_forward(SceneDev s, SegDev t,
     const uint32_t local = task * ppw + lane / G;
     const bool active = local < n_pix;
     float3 a = f3(0.f, 0.f, 0.f), a2 = f3(0.f, 0.f, 0.f);
+    uint32_t pid = pix_begin + local;
     if (active) {
-      const uint32_t pid = pix_begin + local;
+      uint32_t s0 = 0;
+      if (pp.pick) {
+        pid = pp.pick[local];
+        s0 = local * pp.stride;
+      }
       const ViewDev& vw = find_view(views, n_views, pid);
       const uint32_t lp = pid - vw.offset;
       const uint32_t px = lp % vw.w, py = lp / vw.w;
       for (uint32_t smp = sub; smp < pp.spp; smp += G) {
-        const float3 L = forward_path(s, t, vw, px, py, pid, smp, pp, W, err);
+        const float3 L = forward_path(s, t, vw, px, py, pid, s0 + smp, pp, W, err);
         a = a + L;
         a2 = a2 + L * L;
       }
@@ -237,8 +242,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_forward(SceneDev s, SegDev t,
         msq[3 * local + 2] = a2.z * inv_spp;
       }
       if (target) {
-        const float r[3] = {mean.x - target[3 * local + 0], mean.y - target[3 * local + 1],
-                            mean.z - target[3 * local + 2]};
+        // a pixel batch reads the target of the drawn pixel (the caller passes
+        // the whole target image); otherwise target is indexed like the outputs
+        const uint32_t ti = pp.pick ? pid : local;
+        const float r[3] = {mean.x - target[3 * ti + 0], mean.y - target[3 * ti + 1],
+                            mean.z - target[3 * ti + 2]};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if (loss_kind == 0) {
@@ -292,14 +300,15 @@ __global__ void __launch_bounds__(kBlockThreads) k_adjoint(SceneDev s, SegDev t,
   for (uint32_t task = blockIdx.x * warps_per_block + (threadIdx.x >> 5); task < n_tasks; task += stride) {
     const uint32_t local = task * ppw + lane / G;
     if (local >= n_pix) continue;
-    const uint32_t pid = pix_begin + local;
+    const uint32_t pid = pp.pick ? pp.pick[local] : pix_begin + local;
+    const uint32_t s0 = pp.pick ? local * pp.stride : 0u;
     const float3 gp = f3(g_img[3 * local], g_img[3 * local + 1], g_img[3 * local + 2]) * inv_spp;
     if (gp.x == 0.0f && gp.y == 0.0f && gp.z == 0.0f) continue;
     const ViewDev& vw = find_view(views, n_views, pid);
     const uint32_t lp = pid - vw.offset;
     const uint32_t px = lp % vw.w, py = lp / vw.w;
     for (uint32_t smp = sub; smp < pp.spp; smp += G)
-      adjoint_path<MAXD>(s, t, vw, px, py, pid, smp, pp, W, gp, sgrad, err);
+      adjoint_path<MAXD>(s, t, vw, px, py, pid, s0 + smp, pp, W, gp, sgrad, err);
   }
   __syncthreads();
   if (!gacc)

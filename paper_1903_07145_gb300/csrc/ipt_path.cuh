@@ -22,6 +22,11 @@ struct PathParams {
   uint32_t max_depth;
   int nee, mis, profile;
   float emission_scale;
+  // pixel batch: launch pixel i is entry i, tracing scene pixel pick[i] with
+  // sample counters i * stride + s (nullptr: launch pixel i is pixel
+  // pix_begin + i with counters s)
+  const uint32_t* pick;
+  uint32_t stride;
 };
 
 __host__ __device__ inline uint32_t lanes_per_pixel(uint32_t spp) {
@@ -41,6 +46,8 @@ inline PathParams make_path_params(const TraceParams& tp, const SceneBuffers& s)
   p.mis = tp.mis;
   p.profile = tp.profile;
   p.emission_scale = s.emission_scale;
+  p.pick = tp.pick;
+  p.stride = tp.sample_stride ? tp.sample_stride : tp.spp;
   return p;
 }
 

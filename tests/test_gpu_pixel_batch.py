@@ -49,9 +49,10 @@ def test_pick_matches_oracle(built):
     tr.close()
 
 
+@pytest.mark.parametrize("integrator", ["wavefront", "megakernel"])
 @pytest.mark.parametrize("loss,same_set,batch", [("l2", False, 600), ("l1", False, 600), ("l2", True, 600),
                                                  ("l2", False, 300)])
-def test_batch_loss_and_gradient_match_oracle(built, loss, same_set, batch):
+def test_batch_loss_and_gradient_match_oracle(built, loss, same_set, batch, integrator):
     """batch 300 over 2 x 12 x 10 = 240 pixels draws most pixels more than once:
     each entry keeps its own samples and upstream gradient."""
     w, h = (12, 10) if batch == 300 else (32, 24)
@@ -68,6 +69,7 @@ def test_batch_loss_and_gradient_match_oracle(built, loss, same_set, batch):
     if batch == 300:
         assert len(np.unique(ids)) < batch
     tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator)
     tr.set_params(p.astype(np.float32))
     tr.set_targets(torch.from_numpy(np.concatenate(targets).astype(np.float32)).cuda())
     opts = TraceOptions(spp_r=spp_r, spp_d=spp_d, max_depth=D, loss=loss, gradcheck_same_set=same_set,
