@@ -514,9 +514,11 @@ def run_time_to_error(args):
         tgt = TraceOptions(max_depth=args.batch_depth)
         ss, masks = convergence.prepare(rooms, tgt, target_spp=target_spp, init=0.0, seed=7)
         ss.configure(integrator="wavefront", wavefront_slots=1 << 21, bvh_width=4)
+        # a scene leaves the batch when it reaches the threshold, as one optimised
+        # alone stops at its own crossing
         first, hist = convergence.time_to_error(ss, masks, opts, adam, threshold=0.01,
                                                 max_iters=args.max_iters, check_every=args.check_every,
-                                                halve_every=args.halve_every)
+                                                halve_every=args.halve_every, retire=not args.no_retire)
         res["batched"] = {"first": first, "history_last": hist[-1][:2]}
         ss.close()
         # the plain arm: each scene alone with its fastest integrator
@@ -571,9 +573,32 @@ def run_time_to_error(args):
         workload = ("cornell64_variants" if args.workload == "cornell64" else f"batch64_rooms_div{args.res_div}")
         workload += f"_pixbatch{args.pixel_batch}" if args.pixel_batch else ""
     print(json.dumps({"metric": "time to 1% parameter error", "unit": "s", "workload": workload,
-                      "lr": args.lr, "halve_every": args.halve_every, "spp": args.batch_spp,
+                      "lr": args.lr, "halve_every": args.halve_every, "retire": not args.no_retire,
+                      "spp": args.batch_spp,
                       "spp_d": args.spp_d or args.batch_spp, "pixel_batch": args.pixel_batch,
                       "results": res}), flush=True)
+
+
+def run_sweep(args):
+    """Convergence curves of the optimiser ablations on a 64 x 64 Cornell box:
+    per setting (iteration, seconds, parameter error, image L1 loss) at equal
+    optimisation time, and the final errors."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1903_07145_gb300 import ablation, scenes
+    from paper_1903_07145_gb300.tracer import AdamOptions
+    kinds = list(ablation.SWEEPS) if args.sweep == "all" else [args.sweep]
+    for kind in kinds:
+        sc = scenes.cornell_box(1000, 64, 64)
+        curves = ablation.sweep(kind, sc, AdamOptions(lr=args.lr), args.sweep_seconds)
+        final = {k: {"iterations": v[-1][0], "seconds": round(v[-1][1], 3), "param_error": round(v[-1][2], 5),
+                     "image_l1": v[-1][3],
+                     "best_param_error": round(min(c[2] for c in v), 5)} for k, v in curves.items()}
+        print(json.dumps({"metric": "convergence at equal time", "sweep": kind,
+                          "workload": "cornell_64x64_pixel_batches_l1", "seconds_per_setting": args.sweep_seconds,
+                          "lr": args.lr, "final": final,
+                          "curves": {k: [(c[0], round(c[1], 4), round(c[2], 5), c[3]) for c in v]
+                                     for k, v in curves.items()}}), flush=True)
 
 
 def main():
@@ -600,9 +625,14 @@ def main():
     ap.add_argument("--seq-rooms", type=int, default=64,
                     help="time-to-error: rooms optimised one after another for the plain arm")
     ap.add_argument("--check-every", type=int, default=50, help="time-to-error: iterations between error reads")
+    ap.add_argument("--no-retire", action="store_true",
+                    help="time-to-error: keep stepping batch members that reached the threshold")
     ap.add_argument("--halve-every", type=int, default=0,
                     help="time-to-error: halve the learning rate every N iterations (0 = constant)")
     ap.add_argument("--max-iters", type=int, default=6000)
+    ap.add_argument("--sweep", default=None, choices=["paths", "split", "batch", "mis", "bounces", "all"],
+                    help="optimiser ablation curves (paths per pixel, sample split, batch size, MIS, bounces)")
+    ap.add_argument("--sweep-seconds", type=float, default=8.0, help="optimisation time per sweep setting")
     ap.add_argument("--monitor-every", type=int, default=250)
     ap.add_argument("--monitor-spp", type=int, default=1024)
     ap.add_argument("--views", type=int, default=None,
@@ -629,6 +659,9 @@ def main():
         ap.error("--workload cornell64 is a time-to-error workload (add --time-to-error)")
     if args.impl == "ours" and args.time_to_error:
         run_time_to_error(args)
+        return
+    if args.impl == "ours" and args.sweep:
+        run_sweep(args)
         return
     if args.impl == "ours" and args.workload == "batch64":
         run_batch64(args)

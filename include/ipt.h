@@ -348,6 +348,16 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
  * host S x 10 floats. */
 ipt_status ipt_batch_params_get(ipt_ctx* ctx, int32_t batch, uint32_t member, float* params_out);
 
+/* Which members take part in the batch's next steps (active[k] != 0 for
+ * member k; host array of one byte per member; all members start active).
+ * An inactive member traces nothing and keeps its parameters and Adam
+ * moments as they are; its loss reads 0.  This lets a serving loop retire
+ * scenes that have finished (or hold some back) without rebuilding the
+ * batch; Adam's bias correction counts the batch's iterations, so a member
+ * made active again continues with the batch's step count.  The next step
+ * recaptures the graph when the set changed. */
+ipt_status ipt_batch_set_active(ipt_ctx* ctx, int32_t batch, const uint8_t* active);
+
 /* Release a batch (its member scenes stay). */
 ipt_status ipt_batch_destroy(ipt_ctx* ctx, int32_t batch);
 

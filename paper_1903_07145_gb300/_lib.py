@@ -27,7 +27,7 @@ EXPORTED = [
     "ipt_adam_step", "ipt_step", "ipt_trace_rays", "ipt_pick_pixels", "ipt_philox", "ipt_synchronize",
     "ipt_scene_info", "ipt_kernel_times", "ipt_counters_read", "ipt_loss_grad_shard",
     "ipt_backward_noalloc", "ipt_config_set", "ipt_config_get",
-    "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy",
+    "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy", "ipt_batch_set_active",
     "ipt_cache_configure", "ipt_cache_weights_set", "ipt_cache_weights_get", "ipt_cache_eval",
     "ipt_cache_grad", "ipt_cache_train", "ipt_cache_records", "ipt_cache_status", "ipt_cache_bias",
     "ipt_probe_gather", "ipt_checkpoint_save", "ipt_checkpoint_load",
@@ -127,6 +127,7 @@ def lib():
                                    C.POINTER(U32), C.POINTER(U32), C.POINTER(U64)],
                 "ipt_kernel_times": [P, C.POINTER(C.c_double), C.POINTER(U64), I32],
                 "ipt_counters_read": [P, C.POINTER(U64), I32],
+                "ipt_batch_set_active": [P, I32, P],
                 "ipt_batch_create": [P, P, U32, C.POINTER(I32)],
                 "ipt_batch_step": [P, I32, C.POINTER(ipt_trace_opts), C.POINTER(ipt_adam_opts), P],
                 "ipt_batch_params_get": [P, I32, U32, P],
@@ -322,6 +323,12 @@ def ipt_batch_step(ctx, batch, opts, adam, losses_out):
 
 def ipt_batch_params_get(ctx, batch, member, out):
     _check(ctx, lib().ipt_batch_params_get(ctx, batch, member, out))
+
+
+def ipt_batch_set_active(ctx, batch, active):
+    flags = [1 if int(x) else 0 for x in active]
+    buf = (C.c_uint8 * len(flags))(*flags)
+    _check(ctx, lib().ipt_batch_set_active(ctx, batch, C.cast(buf, C.c_void_p)))
 
 
 def ipt_batch_destroy(ctx, batch):

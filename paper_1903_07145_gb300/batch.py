@@ -91,6 +91,11 @@ class SceneSet:
         self.batch = L.ipt_batch_create(self.ctx, self.sids)
         return self.batch
 
+    def set_active(self, active):
+        """Members that take part in the next batch steps (inactive ones keep
+        their parameters and Adam state)."""
+        L.ipt_batch_set_active(self.ctx, self.batch, np.asarray(active, np.uint8))
+
     def batch_step(self, opts: TraceOptions, adam: AdamOptions, want_losses=True):
         out = np.zeros(len(self.sids), np.float64) if want_losses else None
         L.ipt_batch_step(self.ctx, self.batch, opts.c(), adam.c(),

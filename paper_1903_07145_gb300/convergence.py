@@ -71,9 +71,11 @@ def adam_at(adam: AdamOptions, it: int, halve_every: int) -> AdamOptions:
 
 
 def time_to_error(ss: SceneSet, masks, opts: TraceOptions, adam: AdamOptions, threshold: float = 0.01,
-                  max_iters: int = 20000, check_every: int = 50, halve_every: int = 0):
+                  max_iters: int = 20000, check_every: int = 50, halve_every: int = 0, retire: bool = False):
     """Runs the batch until every member reaches the threshold (or
-    max_iters).  Returns per-member (iterations, seconds) of the first
+    max_iters).  With retire, a member that has crossed stops taking part
+    (ipt_batch_set_active), as a scene optimised alone stops at its own
+    crossing.  Returns per-member (iterations, seconds) of the first
     crossing (None if never) and the error history."""
     n = len(ss.scenes)
     ss.make_batch()
@@ -94,6 +96,8 @@ def time_to_error(ss: SceneSet, masks, opts: TraceOptions, adam: AdamOptions, th
         for i, e in enumerate(errs):
             if first[i] is None and e <= threshold:
                 first[i] = (it, elapsed)
+        if retire:
+            ss.set_active([f is None for f in first])
     return first, history
 
 

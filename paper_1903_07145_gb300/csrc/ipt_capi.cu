@@ -117,6 +117,7 @@ struct Batch {
   ipt::WfScene* tab_dev = nullptr;
   std::vector<ipt::BatchMember> mem_host;
   ipt::BatchMember* mem_dev = nullptr;
+  std::vector<uint8_t> active;  // members that take part in the steps
   float* params = nullptr;
   float* adam_m = nullptr;
   float* adam_v = nullptr;
@@ -1176,6 +1177,10 @@ static void batch_table(ipt_ctx* ctx, Batch* b, uint32_t batch) {
   for (size_t k = 0; k < b->members.size(); ++k) {
     const int32_t id = b->members[k];
     DeviceScene* s = ctx->scenes[id];
+    b->mem_host[k].active = b->active[k];
+    b->mem_host[k].slot = (uint32_t)b->tab_host.size();
+    b->mem_host[k].grad_offset = seg;
+    if (!b->active[k]) continue;  // no pixels in the launch; its segment range stays unused
     const uint32_t n = batch ? batch : (uint32_t)s->n_pix;
     ipt::WfScene e = wf_entry(ctx, id, s, 0, n);
     e.pix_begin = pix;
@@ -1218,6 +1223,7 @@ ipt_status ipt_batch_create(ipt_ctx* ctx, const int32_t* scenes, uint32_t n, int
   Batch* b = new (std::nothrow) Batch();
   if (!b) return IPT_ERR_OUT_OF_MEMORY;
   b->members = ids;
+  b->active.assign(ids.size(), 1);
   b->n_seg_total = segs;
   b->n_pix_total = pix;
   const size_t np = 10 * (size_t)segs;
@@ -1259,6 +1265,9 @@ ipt_status ipt_batch_create(ipt_ctx* ctx, const int32_t* scenes, uint32_t n, int
     m.n_seg = s->n_seg;
     m.es = s->emission_scale;
     m.inv_n = (float)(1.0 / (3.0 * (double)s->n_pix));
+    m.active = 1;
+    m.slot = (uint32_t)b->mem_host.size();
+    m.grad_offset = off;
     b->mem_host.push_back(m);
     s->tab_is_ctx = false;  // the batch owns the member's tables from now on
     off += s->n_seg;
@@ -1309,8 +1318,8 @@ static ipt_status batch_enqueue(ipt_ctx* ctx, Batch* b, const ipt_trace_opts* op
   if (opts->gradcheck_same_set) tp.sample_stride = opts->spp_r;
   IPT_CK(ipt::wf_adjoint(ctx->L, b->tab_dev, b->tab_host, tp, b->iter_dev, ctx->wf, b->grad_acc, ctx->err_dev, st,
                          nullptr));
-  IPT_CK(ipt::launch_batch_losses(b->loss_rows, ipt::loss_partials_capacity(ctx->L), b->mem_dev, n, b->losses_dev,
-                                  st));
+  IPT_CK(ipt::launch_batch_losses(b->loss_rows, ipt::loss_partials_capacity(ctx->L), b->mem_dev, n,
+                                  (uint32_t)b->tab_host.size(), b->losses_dev, st));
   IPT_CK(ipt::launch_adam_batch(b->mem_dev, n, b->params, b->adam_m, b->adam_v, b->free_mask, b->grad_acc,
                                 b->iter_dev, adam_host(adam), st));
   IPT_CK(ipt::launch_tick(b->iter_dev, st));
@@ -1329,6 +1338,11 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
   if (std::max(opts->spp_r, opts->spp_d) > cap)
     return fail(ctx, IPT_ERR_INVALID_ARG, "spp above the wavefront chunk size");
   IPT_CK(cudaSetDevice(ctx->device));
+  if (std::find(b->active.begin(), b->active.end(), (uint8_t)1) == b->active.end()) {
+    // no member takes part: nothing to trace or update
+    if (losses_out) std::fill(losses_out, losses_out + b->members.size(), 0.0);
+    return IPT_OK;
+  }
   if (!b->exec || !same_opts(*opts, b->g_opts) || !same_adam(*adam, b->g_adam) || !same_cfg(ctx->cfg, b->g_cfg)) {
     // everything the graph touches is allocated before the capture
     if (opts->pixel_batch)
@@ -1371,6 +1385,27 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
     IPT_CK(cudaMemcpyAsync(b->losses_host, b->losses_dev, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if ((st = ipt_synchronize(ctx)) != IPT_OK) return st;
     std::memcpy(losses_out, b->losses_host, n * sizeof(double));
+  }
+  return IPT_OK;
+}
+
+ipt_status ipt_batch_set_active(ipt_ctx* ctx, int32_t batch, const uint8_t* active) {
+  Batch* b;
+  ipt_status st = get_batch(ctx, batch, &b);
+  if (st != IPT_OK) return st;
+  if (!active) return fail(ctx, IPT_ERR_INVALID_ARG, "null active flags");
+  bool changed = false;
+  for (size_t k = 0; k < b->members.size(); ++k) {
+    const uint8_t a = active[k] ? 1 : 0;
+    changed |= a != b->active[k];
+    b->active[k] = a;
+  }
+  if (changed && b->exec) {  // the next step recaptures with the new launch table
+    IPT_CK(cudaSetDevice(ctx->device));
+    IPT_CK(cudaStreamSynchronize(ctx->stream));
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
   }
   return IPT_OK;
 }

@@ -156,7 +156,10 @@ struct BatchMember {
   const double* seg_area;
   uint32_t seg_offset, n_seg;
   float es;
-  float inv_n;  // 1 / (3 N) of its loss
+  float inv_n;      // 1 / (3 N) of its loss
+  uint32_t active;  // 0: takes no part in the batch's steps (parameters and Adam state frozen)
+  uint32_t slot;         // its entry in the launch table when active
+  uint32_t grad_offset;  // its first segment in the step's gradient accumulators (active members, packed)
 };
 
 // Adam over the whole batch (block b updates member b, then rebuilds its
@@ -167,9 +170,10 @@ cudaError_t launch_adam_batch(const BatchMember* members, uint32_t n_members, fl
 // Tables of every member from the batch parameters.
 cudaError_t launch_prepare_batch(const BatchMember* members, uint32_t n_members, const float* params,
                                  cudaStream_t st);
-// loss[b] = sum over rows of rows[r * n + b], scaled by the member's 1 / (3 N).
+// loss[b] = sum over rows of rows[r * n_tab + slot_b], scaled by the member's
+// 1 / (3 N); 0 for members that are not active.
 cudaError_t launch_batch_losses(const double* rows, int n_rows, const BatchMember* members, uint32_t n,
-                                double* loss, cudaStream_t st);
+                                uint32_t n_tab, double* loss, cudaStream_t st);
 cudaError_t launch_tick(uint32_t* counter, cudaStream_t st);
 
 cudaError_t launch_trace_rays(const SceneBuffers& s, uint32_t n, const float* orig,

@@ -344,13 +344,13 @@ __global__ void k_finalize(const double* loss_partials, int n_partials, double* 
 // followed by that member's tables for the next iteration.
 __device__ __forceinline__ void adam_range(float* params, float* m, float* v, const uint8_t* free_mask,
                                            const double* grad_acc, const float* grad_f, uint32_t begin,
-                                           uint32_t end, const AdamHost& a, int step) {
+                                           uint32_t end, uint32_t g_begin, const AdamHost& a, int step) {
   const float bc1 = 1.0f - powf(a.beta1, (float)step);
   const float bc2 = 1.0f - powf(a.beta2, (float)step);
   for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
     if (free_mask && !free_mask[i]) continue;
     const uint32_t j = i % 10u;
-    float g = grad_f ? grad_f[i] : (float)grad_acc[i];
+    float g = grad_f ? grad_f[i] : (float)grad_acc[g_begin + (i - begin)];
     const float th = params[i];
     if (j >= 7) g += a.l1 * (th > 0.0f ? 1.0f : (th < 0.0f ? -1.0f : 0.0f));
     const float mi = a.beta1 * m[i] + (1.0f - a.beta1) * g;
@@ -372,9 +372,10 @@ __global__ void k_adam_batch(const BatchMember* members, float* params, float* m
                              const uint8_t* free_mask, const double* grad_acc, const uint32_t* iter_dev,
                              AdamHost a) {
   const BatchMember mb = members[blockIdx.x];
+  if (!mb.active) return;
   const int step = (int)*iter_dev + 1;
-  adam_range(params, m, v, free_mask, grad_acc, nullptr, 10u * mb.seg_offset, 10u * (mb.seg_offset + mb.n_seg), a,
-             step);
+  adam_range(params, m, v, free_mask, grad_acc, nullptr, 10u * mb.seg_offset, 10u * (mb.seg_offset + mb.n_seg),
+             10u * mb.grad_offset, a, step);
   __syncthreads();
   const float* p = params + 10u * mb.seg_offset;
   build_tables(p, p, mb.n_seg, mb.es, mb.seg_area, mb.tab);
@@ -386,12 +387,19 @@ __global__ void k_prepare_batch(const BatchMember* members, const float* params)
   build_tables(p, p, mb.n_seg, mb.es, mb.seg_area, mb.tab);
 }
 
-__global__ void k_batch_losses(const double* rows, int n_rows, const BatchMember* members, uint32_t n,
+// Loss of each member from the per-block rows of the launch table (n_tab
+// entries: the active members).
+__global__ void k_batch_losses(const double* rows, int n_rows, const BatchMember* members, uint32_t n_tab,
                                double* loss) {
   __shared__ double red[256];
   const uint32_t b = blockIdx.x;
+  if (!members[b].active) {  // traced nothing this step
+    if (threadIdx.x == 0) loss[b] = 0.0;
+    return;
+  }
+  const uint32_t slot = members[b].slot;
   double s = 0.0;
-  for (int r = threadIdx.x; r < n_rows; r += blockDim.x) s += rows[(size_t)r * n + b];
+  for (int r = threadIdx.x; r < n_rows; r += blockDim.x) s += rows[(size_t)r * n_tab + slot];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w >= 1; w >>= 1) {
@@ -407,7 +415,7 @@ __global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_ma
                        const double* grad_acc, const float* grad_f, int* step_dev, AdamHost a, uint32_t S,
                        float es, const double* seg_area, SegBuffers t) {
   const int step = *step_dev + 1;
-  adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, a, step);
+  adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, 0u, a, step);
   __syncthreads();
   if (threadIdx.x == 0) *step_dev = step;
   build_tables(params, params, S, es, seg_area, t);
@@ -565,8 +573,8 @@ cudaError_t launch_prepare_batch(const BatchMember* members, uint32_t n_members,
 }
 
 cudaError_t launch_batch_losses(const double* rows, int n_rows, const BatchMember* members, uint32_t n,
-                                double* loss, cudaStream_t st) {
-  k_batch_losses<<<n, 256, 0, st>>>(rows, n_rows, members, n, loss);
+                                uint32_t n_tab, double* loss, cudaStream_t st) {
+  k_batch_losses<<<n, 256, 0, st>>>(rows, n_rows, members, n_tab, loss);
   return cudaGetLastError();
 }
 

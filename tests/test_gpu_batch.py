@@ -107,3 +107,34 @@ def test_cornell_box_reaches_one_percent_parameter_error(built):
     print("cornell error history:", [(h[0], round(h[1], 2), round(h[2][0], 4)) for h in hist])
     assert first[0] is not None, hist[-1]
     ss.close()
+
+
+def test_inactive_member_is_frozen(built):
+    """A member made inactive traces nothing and keeps its parameters; the
+    others step exactly as they do in the full batch."""
+    opts = TraceOptions(spp_r=8, spp_d=8, max_depth=4)
+    adam = AdamOptions()
+    ss = prepared()
+    init = [ss.params(i) for i in range(3)]
+    ss.make_batch()
+    full = [ss.batch_step(opts, adam) for _ in range(2)]
+    full_params = [ss.batch_params(i) for i in range(3)]
+    for i in range(3):
+        ss.set_params(i, init[i])
+    ss.make_batch()
+    ss.set_active([1, 0, 1])
+    part = [ss.batch_step(opts, adam) for _ in range(2)]
+    assert np.array_equal(ss.batch_params(1), init[1])
+    assert part[0][1] == 0.0 and part[1][1] == 0.0
+    for i in (0, 2):
+        assert abs(part[0][i] - full[0][i]) <= 1e-6 * abs(full[0][i])
+        d = np.abs(ss.batch_params(i) - full_params[i])
+        assert np.mean(d < 1e-5) >= 0.95 and d.max() <= 6 * adam.lr
+    ss.set_active([0, 0, 0])  # nothing to do: a no-op step
+    before = [ss.batch_params(i) for i in range(3)]
+    assert np.all(ss.batch_step(opts, adam) == 0.0)
+    assert all(np.array_equal(ss.batch_params(i), before[i]) for i in range(3))
+    ss.set_active([1, 1, 1])
+    assert np.all(np.isfinite(ss.batch_step(opts, adam)))
+    ss.synchronize()
+    ss.close()
