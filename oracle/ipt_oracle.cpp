@@ -432,6 +432,280 @@ inline V3 bsdf_sample(const Mat& ms, V3 n, V3 wi, double u_lobe, double u1, doub
 }
 
 // ---------------------------------------------------------------------------
+// Disney material model (Sec. 4.1: a base colour and ten further scalars, all
+// in [0, 1]).  Restated from Burley, "Physically-Based Shading at Disney",
+// SIGGRAPH 2012 course notes, with the base colour taken as linear RGB.
+// Per segment 16 values: base colour (0-2), subsurface (3), metallic (4),
+// specular (5), specular tint (6), roughness (7), anisotropic (8), sheen (9),
+// sheen tint (10), clearcoat (11), clearcoat gloss (12), emission (13-15).
+//
+// With l = wo, v = wi, h their half vector, S(c) = (1 - c)^5, rho the
+// roughness, mu metallic, sigma subsurface, C_t = base / lum(base) (white
+// for a black base):
+//   diffuse   (1 - mu) base / pi [(1 - sigma) fD + sigma fSS],
+//             fD  = (1 + (FD90 - 1) S(n.l)) (1 + (FD90 - 1) S(n.v)), FD90 = 1/2 + 2 rho (l.h)^2,
+//             fSS = 5/4 [FSS (1 / (n.l + n.v) - 1/2) + 1/2],
+//             FSS = (1 + (F90 - 1) S(n.l)) (1 + (F90 - 1) S(n.v)), F90 = rho (l.h)^2;
+//   sheen     (1 - mu) sheen S(l.h) (1 + sheen_tint (C_t - 1));
+//   specular  D_s F_s G_s: anisotropic GGX (GTR, gamma = 2),
+//             a_x = max(1e-3, rho^2 / k), a_y = max(1e-3, rho^2 k), k = sqrt(1 - 0.9 aniso),
+//             F_s = C0 + (1 - C0) S(l.h),
+//             C0 = (1 - mu) 0.08 specular (1 + spec_tint (C_t - 1)) + mu base,
+//             G_s = g(l) g(v), g(w) = 1 / (n.w + sqrt((w.X a_x)^2 + (w.Y a_y)^2 + (n.w)^2))
+//             (separable Smith masking with the 1 / (4 n.l n.v) folded in);
+//   clearcoat clearcoat / 4 D_c F_c G_c: GTR with gamma = 1 and a_c = 0.1 - 0.099 gloss,
+//             D_c = (a_c^2 - 1) / (pi ln(a_c^2) (1 + (a_c^2 - 1) (n.h)^2)),
+//             F_c = 0.04 + 0.96 S(l.h), G_c = g_c(l) g_c(v) with width 0.25.
+// X, Y: tangent frame (the hit triangle's first edge made orthogonal to the
+// shading normal, then n x X).  Derivatives with respect to the 13 material
+// values are exact first derivatives by forward-mode dual numbers.
+// ---------------------------------------------------------------------------
+constexpr int kDisneyMat = 13;
+constexpr int kDisneyStride = 16;
+
+struct Dual {
+  double v;
+  double d[kDisneyMat];
+};
+inline Dual dconst(double x) {
+  Dual r;
+  r.v = x;
+  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = 0.0;
+  return r;
+}
+inline Dual dvar(double x, int i) {
+  Dual r = dconst(x);
+  r.d[i] = 1.0;
+  return r;
+}
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r;
+  r.v = a.v + b.v;
+  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r;
+  r.v = a.v - b.v;
+  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r;
+  r.v = a.v * b.v;
+  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r;
+  r.v = a.v / b.v;
+  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);
+  return r;
+}
+inline Dual operator+(const Dual& a, double b) { return a + dconst(b); }
+inline Dual operator+(double a, const Dual& b) { return dconst(a) + b; }
+inline Dual operator-(const Dual& a, double b) { return a - dconst(b); }
+inline Dual operator-(double a, const Dual& b) { return dconst(a) - b; }
+inline Dual operator*(const Dual& a, double b) { return a * dconst(b); }
+inline Dual operator*(double a, const Dual& b) { return dconst(a) * b; }
+inline Dual operator/(const Dual& a, double b) { return a / dconst(b); }
+inline Dual operator/(double a, const Dual& b) { return dconst(a) / b; }
+inline Dual sqrt(const Dual& a) {
+  Dual r;
+  r.v = std::sqrt(a.v);
+  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+  return r;
+}
+inline Dual log(const Dual& a) {
+  Dual r;
+  r.v = std::log(a.v);
+  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] / a.v;
+  return r;
+}
+inline double sqrt(double a) { return std::sqrt(a); }
+inline double log(double a) { return std::log(a); }
+inline double value(double x) { return x; }
+inline double value(const Dual& x) { return x.v; }
+// max(a, c) for a constant c (zero derivative where the constant wins)
+inline double floor_at(double a, double c) { return a > c ? a : c; }
+inline Dual floor_at(const Dual& a, double c) { return a.v > c ? a : dconst(c); }
+
+inline double schlick_w(double c) {
+  const double m = std::min(1.0, std::max(0.0, 1.0 - c));
+  return m * m * m * m * m;
+}
+
+// Tangent frame at shading normal n from a triangle edge e1.
+inline void tangent_frame(V3 e1, V3 n, V3& X, V3& Y) {
+  V3 t = e1 - n * dot(n, e1);
+  double len = length(t);
+  if (!(len > 1e-12 * length(e1))) {
+    V3 b2;
+    onb(n, t, b2);
+    len = 1.0;
+  }
+  X = t * (1.0 / len);
+  Y = cross(n, X);
+}
+
+// Anisotropic widths (a_x, a_y) from roughness and anisotropy.
+template <class T>
+inline void disney_widths(const T& rho, const T& ani, T& ax, T& ay) {
+  const T k = sqrt(1.0 - 0.9 * ani);
+  ax = floor_at(rho * rho / k, 1e-3);
+  ay = floor_at(rho * rho * k, 1e-3);
+}
+
+inline double clearcoat_width(double gloss) { return 0.1 - 0.099 * gloss; }
+
+// GTR, gamma = 1 (the clearcoat lobe's normal distribution).
+template <class T>
+inline T gtr1(double ch, const T& a) {
+  const T a2 = a * a;
+  return (a2 - 1.0) / (kPi * log(a2) * (1.0 + (a2 - 1.0) * (ch * ch)));
+}
+
+// f_r per channel for the 13 material values m (double, or Dual for the
+// derivatives); zero unless both directions are above the shading hemisphere.
+template <class T>
+void disney_f(const T* m, V3 n, V3 X, V3 Y, V3 wi, V3 wo, T f[3]) {
+  const double cl = dot(n, wo), cv = dot(n, wi);
+  if (!(cl > 0.0) || !(cv > 0.0)) {
+    for (int c = 0; c < 3; ++c) f[c] = m[0] * 0.0;
+    return;
+  }
+  const V3 h = normalize(wi + wo);
+  const double ch = dot(n, h), cd = dot(wo, h);
+  const double Sl = schlick_w(cl), Sv = schlick_w(cv), Sd = schlick_w(cd);
+  const T& sub = m[3];
+  const T& met = m[4];
+  const T& spc = m[5];
+  const T& spt = m[6];
+  const T& rho = m[7];
+  const T& shn = m[9];
+  const T& sht = m[10];
+  const T& cc = m[11];
+  const T lb = m[0] * kLumR + m[1] * kLumG + m[2] * kLumB;
+  T tint[3];
+  for (int c = 0; c < 3; ++c) tint[c] = value(lb) > 0.0 ? m[c] / lb : m[c] * 0.0 + 1.0;
+  // diffuse with the subsurface blend
+  const T fd90 = 0.5 + (2.0 * cd * cd) * rho;
+  const T fd = (1.0 + (fd90 - 1.0) * Sl) * (1.0 + (fd90 - 1.0) * Sv);
+  const T f90 = (cd * cd) * rho;
+  const T fss0 = (1.0 + (f90 - 1.0) * Sl) * (1.0 + (f90 - 1.0) * Sv);
+  const T fss = 1.25 * (fss0 * (1.0 / (cl + cv) - 0.5) + 0.5);
+  const T diff = (1.0 - met) * ((1.0 - sub) * fd + sub * fss) * (1.0 / kPi);
+  // anisotropic GGX
+  T ax, ay;
+  disney_widths(rho, m[8], ax, ay);
+  const double hx = dot(h, X), hy = dot(h, Y);
+  const T q = (hx * hx) / (ax * ax) + (hy * hy) / (ay * ay) + ch * ch;
+  const T Ds = 1.0 / (kPi * ax * ay * q * q);
+  const double lx = dot(wo, X), ly = dot(wo, Y), vx = dot(wi, X), vy = dot(wi, Y);
+  const T gl = 1.0 / (cl + sqrt((lx * lx) * (ax * ax) + (ly * ly) * (ay * ay) + cl * cl));
+  const T gv = 1.0 / (cv + sqrt((vx * vx) * (ax * ax) + (vy * vy) * (ay * ay) + cv * cv));
+  const T spec_geo = Ds * gl * gv;
+  // clearcoat
+  const T ac = 0.1 - 0.099 * m[12];
+  const double gcl = 1.0 / (cl + std::sqrt(0.0625 + cl * cl - 0.0625 * cl * cl));
+  const double gcv = 1.0 / (cv + std::sqrt(0.0625 + cv * cv - 0.0625 * cv * cv));
+  const T coat = 0.25 * cc * gtr1(ch, ac) * ((0.04 + 0.96 * Sd) * gcl * gcv);
+  for (int c = 0; c < 3; ++c) {
+    const T C0 = (1.0 - met) * 0.08 * spc * (1.0 + spt * (tint[c] - 1.0)) + met * m[c];
+    const T Fs = C0 + (1.0 - C0) * Sd;
+    const T sheen = (1.0 - met) * shn * Sd * (1.0 + sht * (tint[c] - 1.0));
+    f[c] = m[c] * diff + sheen + Fs * spec_geo + coat;
+  }
+}
+
+// Lobe probabilities (diffuse, specular, clearcoat) from the sampling
+// parameters: weights (1 - mu) lum(base), (1 - mu) 0.08 specular + mu lum(base)
+// and clearcoat / 4, normalised (all diffuse when they sum to zero).
+inline void disney_lobes(const double* m, double p[3]) {
+  const double lb = kLumR * m[0] + kLumG * m[1] + kLumB * m[2];
+  const double wd = (1.0 - m[4]) * lb;
+  const double ws = (1.0 - m[4]) * 0.08 * m[5] + m[4] * lb;
+  const double wc = 0.25 * m[11];
+  const double sum = wd + ws + wc;
+  if (!(sum > 0.0)) {
+    p[0] = 1.0;
+    p[1] = p[2] = 0.0;
+    return;
+  }
+  p[0] = wd / sum;
+  p[1] = ws / sum;
+  p[2] = wc / sum;
+}
+
+// Solid-angle pdf of the Disney sampler: cosine-weighted diffuse, visible
+// anisotropic GGX normals (Heitz 2018, stretched by a_x, a_y in the tangent
+// frame) and GTR1 normals for the clearcoat, mixed by the lobe probabilities.
+inline double disney_pdf(const double* ms, V3 n, V3 X, V3 Y, V3 wi, V3 wo) {
+  const double cv = dot(n, wi), cl = dot(n, wo);
+  if (!(cv > 0.0) || !(cl > 0.0)) return 0.0;
+  double p[3];
+  disney_lobes(ms, p);
+  const V3 h = normalize(wi + wo);
+  const double ch = dot(n, h);
+  double pdf = p[0] * cl / kPi;
+  if (p[1] > 0.0) {
+    double ax, ay;
+    disney_widths(ms[7], ms[8], ax, ay);
+    const double hx = dot(h, X), hy = dot(h, Y);
+    const double q = (hx * hx) / (ax * ax) + (hy * hy) / (ay * ay) + ch * ch;
+    const double D = 1.0 / (kPi * ax * ay * q * q);
+    const double vx = dot(wi, X), vy = dot(wi, Y);
+    const double lam = 0.5 * (std::sqrt(1.0 + (vx * vx * ax * ax + vy * vy * ay * ay) / (cv * cv)) - 1.0);
+    pdf += p[1] * D / (1.0 + lam) / (4.0 * cv);
+  }
+  if (p[2] > 0.0) {
+    const double wh = dot(wo, h);
+    if (wh > 0.0) pdf += p[2] * gtr1(ch, clearcoat_width(ms[12])) * ch / (4.0 * wh);
+  }
+  return pdf;
+}
+
+// Sample wo from wi: lobe by u_lobe against the cumulative lobe
+// probabilities, then (u1, u2) as in the lobe's sampler.
+inline V3 disney_sample(const double* ms, V3 n, V3 X, V3 Y, V3 wi, double u_lobe, double u1, double u2) {
+  double p[3];
+  disney_lobes(ms, p);
+  const double rr = std::sqrt(u1);
+  const double phi = 2.0 * kPi * u2;
+  if (u_lobe < p[0]) {
+    V3 b1, b2;
+    onb(n, b1, b2);
+    return b1 * (rr * std::cos(phi)) + b2 * (rr * std::sin(phi)) + n * std::sqrt(std::max(0.0, 1.0 - u1));
+  }
+  V3 hw;
+  if (u_lobe < p[0] + p[1]) {
+    double ax, ay;
+    disney_widths(ms[7], ms[8], ax, ay);
+    const V3 vl = {dot(wi, X), dot(wi, Y), dot(wi, n)};
+    const V3 vh = normalize(V3{ax * vl.x, ay * vl.y, vl.z});
+    const double lensq = vh.x * vh.x + vh.y * vh.y;
+    const V3 t1 = lensq > 0.0 ? V3{-vh.y, vh.x, 0.0} * (1.0 / std::sqrt(lensq)) : V3{1.0, 0.0, 0.0};
+    const V3 t2 = cross(vh, t1);
+    const double q1 = rr * std::cos(phi);
+    double q2 = rr * std::sin(phi);
+    const double s = 0.5 * (1.0 + vh.z);
+    q2 = (1.0 - s) * std::sqrt(1.0 - q1 * q1) + s * q2;
+    const V3 nh = t1 * q1 + t2 * q2 + vh * std::sqrt(std::max(0.0, 1.0 - q1 * q1 - q2 * q2));
+    const V3 ne = normalize(V3{ax * nh.x, ay * nh.y, std::max(0.0, nh.z)});
+    hw = X * ne.x + Y * ne.y + n * ne.z;
+  } else {
+    // GTR1: cos^2 theta_h = (1 - a^(2 (1 - u1))) / (1 - a^2)
+    const double a2 = clearcoat_width(ms[12]) * clearcoat_width(ms[12]);
+    const double c2 = (1.0 - std::pow(a2, 1.0 - u1)) / (1.0 - a2);
+    const double ct = std::sqrt(std::max(0.0, c2)), st = std::sqrt(std::max(0.0, 1.0 - c2));
+    V3 b1, b2;
+    onb(n, b1, b2);
+    hw = b1 * (st * std::cos(phi)) + b2 * (st * std::sin(phi)) + n * ct;
+  }
+  return hw * (2.0 * dot(wi, hw)) - wi;
+}
+
+// ---------------------------------------------------------------------------
 // Light selection proportional to current emission (Appendix E keeps these
 // probabilities per object in a Fenwick tree; here the object distribution is
 // rebuilt per call).  Object s is chosen with probability
@@ -444,13 +718,15 @@ struct LightDist {
   double W = 0.0;
 };
 
-LightDist light_dist(const Scene& s, const double* sparams) {
+// Emission of segment k sits at offset stride - 3 of its parameter block
+// (10 values per segment for Lambert + GGX, 16 for the Disney model).
+LightDist light_dist(const Scene& s, const double* sparams, int stride = 10) {
   LightDist L;
   L.cdf.resize(s.ns);
   L.lum.resize(s.ns);
   double acc = 0.0;
   for (uint32_t k = 0; k < s.ns; ++k) {
-    const double* e = sparams + 10 * k + 7;
+    const double* e = sparams + (size_t)stride * k + (stride - 3);
     double l = kLumR * e[0] + kLumG * e[1] + kLumB * e[2];
     if (!(l > 0.0)) l = 0.0;
     L.lum[k] = l;
@@ -513,6 +789,7 @@ typedef struct {
   uint64_t seed;
   double emission_scale;
   uint32_t pixel_offset;  // global id of pixel 0 of this view (= sum of earlier views' W*H)
+  uint32_t model;         // 0: Lambert + GGX (10 values per segment), 1: Disney (16)
 } ora_opts;
 
 }  // extern "C"
@@ -522,6 +799,7 @@ namespace {
 struct PathVertex {
   int tri, seg;
   V3 x, ns, ng;    // normals oriented to the incoming side
+  V3 tx, ty;       // tangent frame (Disney model)
   V3 wi;           // towards the previous vertex
   double prof;     // emission profile toward wi (0 on the back face)
   double w_bsdf;   // MIS weight of emission found at this vertex
@@ -543,7 +821,19 @@ struct Ctx {
   const ora_opts* o;
   LightDist L;
   double eps;  // spawn offset along the oriented geometric normal
+  int disney;  // material model: Disney (16 values per segment) or Lambert + GGX (10)
+  int stride;
 };
+
+// Sampling pdf and direction at a path vertex, for the context's model.
+inline double vertex_pdf(const Ctx& C, const PathVertex& v, V3 wo) {
+  if (C.disney) return disney_pdf(C.sparams + kDisneyStride * v.seg, v.ns, v.tx, v.ty, v.wi, wo);
+  return bsdf_pdf(mat_of(C.sparams + 10 * v.seg), v.ns, v.wi, wo);
+}
+inline V3 vertex_sample(const Ctx& C, const PathVertex& v, double ul, double u1, double u2) {
+  if (C.disney) return disney_sample(C.sparams + kDisneyStride * v.seg, v.ns, v.tx, v.ty, v.wi, ul, u1, u2);
+  return bsdf_sample(mat_of(C.sparams + 10 * v.seg), v.ns, v.wi, ul, u1, u2);
+}
 
 // One camera path for pixel (px, py), sample index `sample`, following the
 // dimension map: vertex k, call 0 -> (u_lobe, u_dir1, u_dir2, u_light_seg),
@@ -604,6 +894,7 @@ std::vector<PathVertex> trace_path(const Ctx& C, const ora_camera& cam, uint32_t
     const double sg = cos_e < 0.0 ? -1.0 : 1.0;
     v.ng = ng0 * sg;
     v.ns = ns * sg;
+    if (C.disney) tangent_frame(s.p1[t] - s.p0[t], v.ns, v.tx, v.ty);
     v.nee = false;
     v.cont = false;
     if (k == o.max_depth) {
@@ -613,7 +904,6 @@ std::vector<PathVertex> trace_path(const Ctx& C, const ora_camera& cam, uint32_t
     double ua[4], ub[4];
     rng.draw(k, 0, ua);
     rng.draw(k, 1, ub);
-    const Mat ms = mat_of(C.sparams + 10 * v.seg);
     if (light_on) {
       const LightSample ls = light_sample(s, C.L, ua[3], ub[0], ub[1], ub[2]);
       const V3 dl = ls.y - v.x;
@@ -631,7 +921,7 @@ std::vector<PathVertex> trace_path(const Ctx& C, const ora_camera& cam, uint32_t
         double wlight = 1.0;
         if (o.mis) {
           const double pl = ls.pA * r2 / cos_l;
-          const double pb = bsdf_pdf(ms, v.ns, v.wi, wl);
+          const double pb = vertex_pdf(C, v, wl);
           wlight = pl * pl / (pl * pl + pb * pb);
         }
         v.nee = true;
@@ -645,8 +935,8 @@ std::vector<PathVertex> trace_path(const Ctx& C, const ora_camera& cam, uint32_t
       path.push_back(v);
       break;
     }
-    const V3 wo = bsdf_sample(ms, v.ns, v.wi, ua[0], ua[1], ua[2]);
-    const double pdf = bsdf_pdf(ms, v.ns, v.wi, wo);
+    const V3 wo = vertex_sample(C, v, ua[0], ua[1], ua[2]);
+    const double pdf = vertex_pdf(C, v, wo);
     if (!(dot(wo, v.ng) > 0.0) || !(dot(wo, v.ns) > 0.0) || !(pdf > 0.0)) {
       path.push_back(v);
       break;
@@ -673,8 +963,15 @@ struct BsdfFactor {
 // Radiance and (optionally) g-weighted parameter gradient of one path, by
 // enumerating its light paths (one per emission event) and applying Eq. 2,
 // Eq. 5 and Eq. 6 to each.
+void disney_value_and_grad(const Ctx& C, const std::vector<PathVertex>& path, const double* g,
+                           double L[3], double* grad);
+
 void path_value_and_grad(const Ctx& C, const std::vector<PathVertex>& path, const double* g,
                          double L[3], double* grad) {
+  if (C.disney) {
+    disney_value_and_grad(C, path, g, L, grad);
+    return;
+  }
   const double es = C.o->emission_scale;
   L[0] = L[1] = L[2] = 0.0;
   std::vector<BsdfFactor> fs;
@@ -778,13 +1075,69 @@ void cache_term(const Ctx& C, const std::vector<PathVertex>& path, size_t b, con
   }
 }
 
+// The same enumeration of light paths for the Disney model: each BSDF factor
+// is f_r * k with f_r from disney_f, and Eq. 6 takes its 3 x 13 Jacobian
+// times the product of the other factors.
+void disney_value_and_grad(const Ctx& C, const std::vector<PathVertex>& path, const double* g,
+                           double L[3], double* grad) {
+  const double es = C.o->emission_scale;
+  const int S = kDisneyStride;
+  L[0] = L[1] = L[2] = 0.0;
+  std::vector<BsdfFactor> fs;
+  auto light_path = [&](const std::vector<BsdfFactor>& f, int e_seg, double ek) {
+    const size_t n = f.size();
+    std::vector<double> fv(3 * n);
+    std::vector<Dual> fd(grad ? 3 * n : 0);
+    for (size_t i = 0; i < n; ++i) {
+      const PathVertex& pv = path[f[i].vtx];
+      const double* p = C.params + (size_t)S * pv.seg;
+      disney_f(p, pv.ns, pv.tx, pv.ty, pv.wi, f[i].wo, &fv[3 * i]);
+      if (grad) {
+        Dual md[kDisneyMat];
+        for (int j = 0; j < kDisneyMat; ++j) md[j] = dvar(p[j], j);
+        disney_f(md, pv.ns, pv.tx, pv.ty, pv.wi, f[i].wo, &fd[3 * i]);
+      }
+    }
+    const double* e = C.params + (size_t)S * e_seg + kDisneyMat;
+    for (int c = 0; c < 3; ++c) {
+      double prod = 1.0;
+      for (size_t i = 0; i < n; ++i) prod *= fv[3 * i + c] * f[i].k;
+      const double Le = es * e[c] * ek;
+      L[c] += Le * prod;
+      if (!grad) continue;
+      grad[(size_t)S * e_seg + kDisneyMat + c] += g[c] * es * ek * prod;  // Eq. 5
+      for (size_t l = 0; l < n; ++l) {                                       // Eq. 6
+        double others = 1.0;
+        for (size_t i = 0; i < n; ++i)
+          if (i != l) others *= fv[3 * i + c] * f[i].k;
+        const double base = g[c] * Le * others * f[l].k;
+        double* gs = grad + (size_t)S * path[f[l].vtx].seg;
+        for (int j = 0; j < kDisneyMat; ++j) gs[j] += base * fd[3 * l + c].d[j];
+      }
+    }
+  };
+  for (size_t m = 0; m < path.size(); ++m) {
+    const PathVertex& v = path[m];
+    if (v.prof > 0.0 && v.w_bsdf > 0.0) light_path(fs, v.seg, v.prof * v.w_bsdf);
+    if (v.nee) {
+      fs.push_back({(int)m, v.wl, v.nee_k});
+      light_path(fs, v.l_seg, 1.0);
+      fs.pop_back();
+    }
+    if (!v.cont) break;
+    fs.push_back({(int)m, v.wo, v.cont_k});
+  }
+}
+
 Ctx make_ctx(const Scene* s, const double* params, const double* sparams, const ora_opts* o) {
   Ctx C;
   C.s = s;
   C.params = params;
   C.sparams = sparams ? sparams : params;
   C.o = o;
-  C.L = light_dist(*s, C.sparams);
+  C.disney = o->model == 1 ? 1 : 0;
+  C.stride = C.disney ? kDisneyStride : 10;
+  C.L = light_dist(*s, C.sparams, C.stride);
   C.eps = 1e-5 * s->diameter;
   return C;
 }
@@ -941,6 +1294,48 @@ double ora_bsdf_pdf(const double* p, const double* n, const double* wi, const do
   return bsdf_pdf(mat_of(p), {n[0], n[1], n[2]}, {wi[0], wi[1], wi[2]}, {wo[0], wo[1], wo[2]});
 }
 
+// Disney model at one configuration: f_r per channel and (J nullable) its
+// Jacobian J[13 c + j] = d f_c / d m_j.  X: a vector in the tangent plane
+// direction (made orthogonal to n here).
+int ora_disney_brdf(const double* m, const double* n, const double* x, const double* wi, const double* wo,
+                    double* f3, double* J) {
+  const V3 nn = {n[0], n[1], n[2]};
+  V3 X, Y;
+  tangent_frame({x[0], x[1], x[2]}, nn, X, Y);
+  const V3 vi = {wi[0], wi[1], wi[2]}, vo = {wo[0], wo[1], wo[2]};
+  disney_f(m, nn, X, Y, vi, vo, f3);
+  if (J) {
+    Dual md[kDisneyMat], fd[3];
+    for (int j = 0; j < kDisneyMat; ++j) md[j] = dvar(m[j], j);
+    disney_f(md, nn, X, Y, vi, vo, fd);
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < kDisneyMat; ++j) J[kDisneyMat * c + j] = fd[c].d[j];
+  }
+  return (dot(nn, vi) > 0.0 && dot(nn, vo) > 0.0) ? 1 : 0;
+}
+
+double ora_disney_pdf(const double* m, const double* n, const double* x, const double* wi, const double* wo) {
+  const V3 nn = {n[0], n[1], n[2]};
+  V3 X, Y;
+  tangent_frame({x[0], x[1], x[2]}, nn, X, Y);
+  return disney_pdf(m, nn, X, Y, {wi[0], wi[1], wi[2]}, {wo[0], wo[1], wo[2]});
+}
+
+int ora_disney_sample(const double* m, const double* n, const double* x, const double* wi, double u_lobe,
+                      double u1, double u2, double* wo, double* pdf) {
+  const V3 nn = {n[0], n[1], n[2]}, w = {wi[0], wi[1], wi[2]};
+  V3 X, Y;
+  tangent_frame({x[0], x[1], x[2]}, nn, X, Y);
+  const V3 o = disney_sample(m, nn, X, Y, w, u_lobe, u1, u2);
+  wo[0] = o.x;
+  wo[1] = o.y;
+  wo[2] = o.z;
+  *pdf = disney_pdf(m, nn, X, Y, w, o);
+  return 0;
+}
+
+void ora_disney_lobes(const double* m, double* p3) { disney_lobes(m, p3); }
+
 // Light selection for an array of uniforms (4 per sample): triangle, point, p_A.
 int ora_light_sample(void* sp, const double* sparams, uint32_t n, const double* u, int32_t* tri,
                      double* y, double* pA) {
@@ -990,7 +1385,7 @@ int ora_render(void* sp, const ora_camera* cam, const double* params, const doub
   return 0;
 }
 
-// Vector-Jacobian product: grad[S*10] += sum_pixels sum_c g[pixel,c] *
+// Vector-Jacobian product: grad[S * stride] += sum_pixels sum_c g[pixel,c] *
 // d(mean over opts->spp samples of I_c)/d(params), with pdfs, MIS weights and
 // light selection held at sparams.  sample_base as in ora_render.
 int ora_gradient(void* sp, const ora_camera* cam, const double* params, const double* sparams,
@@ -999,7 +1394,7 @@ int ora_gradient(void* sp, const ora_camera* cam, const double* params, const do
   const Scene* s = static_cast<Scene*>(sp);
   const Ctx C = make_ctx(s, params, sparams, o);
   const int nt = std::max(1, nthreads);
-  std::vector<std::vector<double>> part(nt, std::vector<double>(10 * (size_t)s->ns, 0.0));
+  std::vector<std::vector<double>> part(nt, std::vector<double>((size_t)C.stride * s->ns, 0.0));
   parallel_for(npix, nt, [&](int tid, uint32_t i) {
     const uint32_t pid = pixels ? pixels[i] : i;
     const uint32_t px = pid % cam->width, py = pid / cam->width;

@@ -53,7 +53,11 @@ class Opts(C.Structure):
     _fields_ = [("spp", C.c_uint32), ("max_depth", C.c_uint32), ("nee", C.c_int32),
                 ("mis", C.c_int32), ("profile", C.c_int32), ("set", C.c_uint32),
                 ("iteration", C.c_uint32), ("scene_id", C.c_uint32), ("seed", C.c_uint64),
-                ("emission_scale", C.c_double), ("pixel_offset", C.c_uint32)]
+                ("emission_scale", C.c_double), ("pixel_offset", C.c_uint32), ("model", C.c_uint32)]
+
+
+MODEL_LAMBERT_GGX, MODEL_DISNEY = 0, 1
+STRIDE = {MODEL_LAMBERT_GGX: 10, MODEL_DISNEY: 16}
 
 
 def lib():
@@ -82,6 +86,12 @@ def lib():
             L.ora_bsdf_sample.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P, dp]
             L.ora_bsdf_pdf.restype = C.c_double
             L.ora_bsdf_pdf.argtypes = [P, P, P, P]
+            L.ora_disney_brdf.argtypes = [P, P, P, P, P, P, P]
+            L.ora_disney_brdf.restype = C.c_int
+            L.ora_disney_pdf.argtypes = [P, P, P, P, P]
+            L.ora_disney_pdf.restype = C.c_double
+            L.ora_disney_sample.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, P, dp]
+            L.ora_disney_lobes.argtypes = [P, P]
             L.ora_light_sample.argtypes = [P, P, C.c_uint32, P, P, P, P]
             L.ora_light_sample.restype = C.c_int
             L.ora_render.argtypes = [P, C.POINTER(Camera), P, P, C.POINTER(Opts), P, P,
@@ -174,8 +184,9 @@ class OracleScene:
         return tri, t, u, v
 
     def opts(self, view=0, spp=16, max_depth=3, nee=True, mis=True, profile=0, set_id=0,
-             iteration=0, seed=0, scene_id=0):
+             iteration=0, seed=0, scene_id=0, model=MODEL_LAMBERT_GGX):
         o = Opts()
+        o.model = model
         o.spp = spp
         o.max_depth = max_depth
         o.nee = int(nee)
@@ -206,7 +217,8 @@ class OracleScene:
         return mean, msq
 
     def gradient(self, params, g, view=0, pixels=None, sparams=None, threads=None, sample_base=None, **kw):
-        """J^T g for one view: g is (npix, 3); returns (S, 10)."""
+        """J^T g for one view: g is (npix, 3); returns (S, 10), or (S, 16) for
+        the Disney model."""
         cam = self.cams[view]
         p = np.ascontiguousarray(params, np.float64)
         sp = None if sparams is None else np.ascontiguousarray(sparams, np.float64)
@@ -214,8 +226,8 @@ class OracleScene:
         n = cam.width * cam.height if px is None else px.shape[0]
         sb = None if sample_base is None else np.ascontiguousarray(sample_base, np.uint32).reshape(n)
         gg = np.ascontiguousarray(g, np.float64).reshape(n, 3)
-        out = np.zeros((self.n_seg, 10))
         o = self.opts(view=view, **kw)
+        out = np.zeros((self.n_seg, STRIDE[o.model]))
         lib().ora_gradient(self.h, C.byref(cam), _p(p), _p(sp), C.byref(o), _p(px), _p(sb), n,
                            _p(gg), _p(out), threads or default_threads())
         return out
@@ -332,6 +344,45 @@ def bsdf_pdf(params10, n, wi, wo):
                               _p(np.asarray(wi, np.float64)), _p(np.asarray(wo, np.float64)))
 
 
+def _vec3s(*vs):
+    """float64 copies kept alive by the caller for the duration of a call."""
+    return [np.ascontiguousarray(v, np.float64).reshape(3) for v in vs]
+
+
+def disney_brdf(m13, n, x, wi, wo, jacobian=False):
+    """Disney model (Sec. 4.1) at one configuration: f_r (3,), and with
+    jacobian the (3, 13) derivatives with respect to the material values."""
+    m = np.ascontiguousarray(m13, np.float64)
+    n, x, wi, wo = _vec3s(n, x, wi, wo)
+    f = np.zeros(3)
+    J = np.zeros((3, 13)) if jacobian else None
+    ok = lib().ora_disney_brdf(_p(m), _p(n), _p(x), _p(wi), _p(wo), _p(f), _p(J))
+    return (f, J, bool(ok)) if jacobian else (f, bool(ok))
+
+
+def disney_pdf(m13, n, x, wi, wo):
+    m = np.ascontiguousarray(m13, np.float64)
+    n, x, wi, wo = _vec3s(n, x, wi, wo)
+    return lib().ora_disney_pdf(_p(m), _p(n), _p(x), _p(wi), _p(wo))
+
+
+def disney_sample(m13, n, x, wi, u_lobe, u1, u2):
+    m = np.ascontiguousarray(m13, np.float64)
+    n, x, wi = _vec3s(n, x, wi)
+    wo = np.zeros(3)
+    pdf = C.c_double()
+    lib().ora_disney_sample(_p(m), _p(n), _p(x), _p(wi), float(u_lobe), float(u1), float(u2), _p(wo),
+                            C.byref(pdf))
+    return wo, pdf.value
+
+
+def disney_lobes(m13):
+    m = np.ascontiguousarray(m13, np.float64)
+    p = np.zeros(3)
+    lib().ora_disney_lobes(_p(m), _p(p))
+    return p
+
+
 # ---------------------------------------------------------------------------
 # Loss, residual and optimiser (plain numpy, float64)
 # ---------------------------------------------------------------------------
@@ -370,27 +421,52 @@ def adam_update(theta, grad, m, v, t, free=None, lr=5e-3, beta1=0.9, beta2=0.999
     return theta, m, v
 
 
+def adam_update_disney(theta, grad, m, v, t, free=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                       l1_emission=1e-3):
+    """adam_update for the Disney model's (S, 16) parameters: the 13
+    material values clamped to [0, 1] (roughness to [0.02, 1]), emission
+    (13-15) >= 0 with the L1 regulariser."""
+    theta = np.array(theta, np.float64)
+    g = np.array(grad, np.float64)
+    g[:, 13:16] += l1_emission * np.sign(theta[:, 13:16])
+    m = np.array(m, np.float64)
+    v = np.array(v, np.float64)
+    fm = np.ones_like(theta, bool) if free is None else np.asarray(free, bool)
+    m_new = beta1 * m + (1 - beta1) * g
+    v_new = beta2 * v + (1 - beta2) * g * g
+    mh = m_new / (1 - beta1 ** t)
+    vh = v_new / (1 - beta2 ** t)
+    th_new = theta - lr * mh / (np.sqrt(vh) + eps)
+    th_new[:, 0:13] = np.clip(th_new[:, 0:13], 0.0, 1.0)
+    th_new[:, 7] = np.clip(th_new[:, 7], 0.02, 1.0)
+    th_new[:, 13:16] = np.maximum(th_new[:, 13:16], 0.0)
+    theta = np.where(fm, th_new, theta)
+    m = np.where(fm, m_new, m)
+    v = np.where(fm, v_new, v)
+    return theta, m, v
+
+
 def loss_grad(osc: OracleScene, params, targets, spp_r, spp_d, max_depth, iteration=0, seed=0,
               loss="l2", nee=True, mis=True, profile=0, same_set=False, pixels=None,
-              threads=None):
+              threads=None, model=MODEL_LAMBERT_GGX):
     """One nested-SGD gradient evaluation over all views (or a pixel subset per
     view): render set 0, residual against targets, J^T g with set 1."""
     n_total = sum(c.width * c.height * 3 for c in osc.cams) if pixels is None else \
         sum(len(p) * 3 for p in pixels)
-    grad = np.zeros((osc.n_seg, 10))
+    grad = np.zeros((osc.n_seg, STRIDE[model]))
     total = 0.0
     for v in range(len(osc.cams)):
         px = None if pixels is None else pixels[v]
         img, _ = osc.render(params, view=v, pixels=px, spp=spp_r, max_depth=max_depth,
                             nee=nee, mis=mis, profile=profile, set_id=SET_RESIDUAL,
-                            iteration=iteration, seed=seed, threads=threads)
+                            iteration=iteration, seed=seed, threads=threads, model=model)
         tgt = targets[v] if px is None else targets[v][px]
         g, l_v = residual(img, tgt.reshape(-1, 3), n_total, loss)
         total += l_v
         grad += osc.gradient(params, g, view=v, pixels=px, spp=spp_d, max_depth=max_depth,
                              nee=nee, mis=mis, profile=profile,
                              set_id=SET_RESIDUAL if same_set else SET_DERIVATIVE,
-                             iteration=iteration, seed=seed, threads=threads)
+                             iteration=iteration, seed=seed, threads=threads, model=model)
     return total, grad
 
 

@@ -489,6 +489,25 @@ def config_scene(index: int) -> Scene:
     raise ValueError(f"no scene for workload {index}")
 
 
+DISNEY_VALUES = 16  # base rgb, subsurface, metallic, specular, spec tint, roughness, aniso,
+                   # sheen, sheen tint, clearcoat, clearcoat gloss, emission rgb
+
+
+def disney_materials(scene: Scene, seed: int) -> np.ndarray:
+    """Random Disney parameter blocks (Sec. 4.1) for a scene: base colour
+    U[0.1, 0.9]^3, every other material value U[0, 1] except roughness
+    U[0.15, 0.9] (the model's GGX is near-singular towards 0), and the scene's
+    own emission on its light segments (stored / emission scale)."""
+    rng = np.random.default_rng(seed)
+    S = scene.n_segments
+    p = np.zeros((S, DISNEY_VALUES), np.float64)
+    p[:, 0:3] = rng.uniform(0.1, 0.9, (S, 3))
+    p[:, 3:13] = rng.uniform(0.0, 1.0, (S, 10))
+    p[:, 7] = rng.uniform(0.15, 0.9, S)
+    p[:, 13:16] = np.asarray(scene.gt_params, np.float64)[:, 7:10]
+    return p.astype(np.float32)
+
+
 def initial_params(scene: Scene, value: float = 0.5) -> np.ndarray:
     p = np.full((scene.n_segments, PARAMS_PER_SEGMENT), value, np.float32)
     return p
