@@ -579,6 +579,66 @@ def run_time_to_error(args):
                       "results": res}), flush=True)
 
 
+def run_disney(args):
+    """fwd+adjoint Mpaths/s of the Disney material model (Sec. 4.1, megakernel)
+    on the benchmark room with random Disney materials: one step = loss,
+    gradient and Adam over all views; per-kernel device times from the
+    library's own events (a second, identical timing pass)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1903_07145_gb300 import _lib as L
+    from paper_1903_07145_gb300 import scenes
+    from paper_1903_07145_gb300.tracer import AdamOptions, TraceOptions, Tracer
+    w = WORKLOAD
+    sc = make_scene()
+    sc.cameras = sc.cameras[: w["views"]]
+    truth = scenes.disney_materials(sc, 77)
+    opts = TraceOptions(spp_r=w["spp_r"], spp_d=w["spp_d"], max_depth=w["max_depth"])
+    adam = AdamOptions()
+    res = {}
+    for timing in (False, True):
+        tr = Tracer(sc, seed=1903, flags=L.IPT_FLAG_KERNEL_TIMING if timing else 0)
+        tr.disney_set_params(truth)
+        tr.set_targets(tr.disney_render(TraceOptions(max_depth=w["max_depth"]), set_id=L.IPT_SET_TARGET, spp=16))
+        p0 = truth.copy()
+        p0[:, 0:13] = 0.5
+        tr.disney_set_params(p0)
+        for _ in range(args.warmup):
+            tr.disney_step(opts, adam, want_loss=False)
+        dev = tr.device
+        torch.cuda.synchronize(dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        tr.kernel_times(reset=True)
+        with ClockSampler(0) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                tr.disney_step(opts, adam, want_loss=False)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        if timing:
+            kt = tr.kernel_times()
+            res["kernel_ms_per_step"] = {k: round(v[0] / args.steps, 3) for k, v in kt.items() if v[1]}
+        else:
+            res["ms"], res["clocks"] = ms, clk.summary()
+        tr.close()
+    paths = paths_per_step()
+    out = {"metric": METRIC + " (Disney material model)", "value": paths / (res["ms"] * 1e-3) / 1e6,
+           "unit": "Mpaths/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w["workload"] + "_disney", "views": w["views"], "width": w["width"],
+                      "height": w["height"], "spp_r": w["spp_r"], "spp_d": w["spp_d"],
+                      "max_depth": w["max_depth"], "integrator": "megakernel",
+                      "l2": "256 MiB flush between timed steps (outside the step events)"},
+           "kernel_ms_per_step": res["kernel_ms_per_step"], "clocks": res["clocks"]}
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(args):
     """Convergence curves of the optimiser ablations on a 64 x 64 Cornell box:
     per setting (iteration, seconds, parameter error, image L1 loss) at equal
@@ -591,9 +651,18 @@ def run_sweep(args):
     for kind in kinds:
         sc = scenes.cornell_box(1000, 64, 64)
         curves = ablation.sweep(kind, sc, AdamOptions(lr=args.lr), args.sweep_seconds)
-        final = {k: {"iterations": v[-1][0], "seconds": round(v[-1][1], 3), "param_error": round(v[-1][2], 5),
-                     "image_l1": v[-1][3],
-                     "best_param_error": round(min(c[2] for c in v), 5)} for k, v in curves.items()}
+        def first_below(v, thr):
+            return next((round(c[1], 3) for c in v if c[2] <= thr), None)
+
+        def tail(v, i):  # mean over the last quarter of the checkpoints
+            t = v[-max(1, len(v) // 4):]
+            return float(np.mean([c[i] for c in t]))
+        final = {k: {"iterations": v[-1][0], "seconds": round(v[-1][1], 3),
+                     "param_error_last_quarter_mean": round(tail(v, 2), 5),
+                     "image_l1_last_quarter_mean": round(tail(v, 3), 5),
+                     "best_param_error": round(min(c[2] for c in v), 5),
+                     "seconds_to_5pct": first_below(v, 0.05), "seconds_to_2pct": first_below(v, 0.02)}
+                 for k, v in curves.items()}
         print(json.dumps({"metric": "convergence at equal time", "sweep": kind,
                           "workload": "cornell_64x64_pixel_batches_l1", "seconds_per_setting": args.sweep_seconds,
                           "lr": args.lr, "final": final,
@@ -633,6 +702,8 @@ def main():
     ap.add_argument("--sweep", default=None, choices=["paths", "split", "batch", "mis", "bounces", "all"],
                     help="optimiser ablation curves (paths per pixel, sample split, batch size, MIS, bounces)")
     ap.add_argument("--sweep-seconds", type=float, default=8.0, help="optimisation time per sweep setting")
+    ap.add_argument("--material", default="lambert_ggx", choices=["lambert_ggx", "disney"],
+                    help="disney: time the Disney material model's step (megakernel) on the workload")
     ap.add_argument("--monitor-every", type=int, default=250)
     ap.add_argument("--monitor-spp", type=int, default=1024)
     ap.add_argument("--views", type=int, default=None,
@@ -662,6 +733,9 @@ def main():
         return
     if args.impl == "ours" and args.sweep:
         run_sweep(args)
+        return
+    if args.impl == "ours" and args.material == "disney":
+        run_disney(args)
         return
     if args.impl == "ours" and args.workload == "batch64":
         run_batch64(args)

@@ -530,6 +530,46 @@ ipt_status ipt_cache_bias(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opt
 ipt_status ipt_checkpoint_save(ipt_ctx* ctx, int32_t scene, void* buf, size_t* n);
 ipt_status ipt_checkpoint_load(ipt_ctx* ctx, int32_t scene, const void* buf, size_t n);
 
+/* Disney material model (Sec. 4.1: a base colour and ten further values,
+ * all in [0, 1]; Burley 2012 with linear base colour), on the megakernel
+ * integrator whatever ipt_config_set selects.  Its parameter block per
+ * segment is 16 floats: base colour r, g, b (0-2), subsurface (3), metallic
+ * (4), specular (5), specular tint (6), roughness (7), anisotropic (8), sheen
+ * (9), sheen tint (10), clearcoat (11), clearcoat gloss (12), emission r, g, b
+ * (13-15).  Anisotropy is measured in the tangent frame whose first axis is
+ * the hit triangle's first edge (vertex 1 - vertex 0) made orthogonal to the
+ * shading normal.  Paths, light selection, sample sets, the random-number
+ * slots, pixel batches and the losses are those of the Lambert + GGX calls;
+ * the sampler mixes cosine-weighted diffuse, visible anisotropic GGX normals
+ * and GTR1 clearcoat normals with lobe weights (1 - metallic) lum(base),
+ * (1 - metallic) 0.08 specular + metallic lum(base) and clearcoat / 4.
+ * These blocks live beside the scene's 10-value parameters (which the other
+ * calls keep using); batches, checkpoints and the radiance cache do not
+ * include them.  Errors: as the corresponding Lambert + GGX call; calls other
+ * than ipt_disney_params_set fail until the blocks are set. */
+#define IPT_DISNEY_VALUES 16u
+
+/* Host S x 16 parameters and (NULL = all free) S x 16 free mask; resets the
+ * Adam moments, step counter and iteration. */
+ipt_status ipt_disney_params_set(ipt_ctx* ctx, int32_t scene, const float* params, const uint8_t* free_mask);
+ipt_status ipt_disney_params_get(ipt_ctx* ctx, int32_t scene, float* params_out);
+
+/* As ipt_render; sampling_params (device S x 16, nullable) replaces the
+ * parameters the sampler and light selection use. */
+ipt_status ipt_disney_render(ipt_ctx* ctx, int32_t scene, int32_t view, const ipt_trace_opts* opts, uint32_t set,
+                             uint32_t spp, uint64_t iteration, const float* sampling_params, float* rgb_out,
+                             float* msq_out);
+
+/* As ipt_loss_grad; grad_out: device S x 16 floats, nullable. */
+ipt_status ipt_disney_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint64_t iteration,
+                                double* loss_out, float* grad_out);
+
+/* As ipt_step: loss and gradient at the scene's Disney iteration counter,
+ * then Adam with the material values clamped to [0, 1] (roughness to
+ * [0.02, 1]) and emission kept >= 0 under the L1 term. */
+ipt_status ipt_disney_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, const ipt_adam_opts* adam,
+                           double* loss_out);
+
 /* Measurement support (not part of the method).  Achievable bandwidth, in
  * GB/s (1e9 bytes), of random 64-byte line gathers over a device buffer of
  * `bytes` bytes on `device`: four independent gathers in flight per thread,

@@ -31,7 +31,10 @@ EXPORTED = [
     "ipt_cache_configure", "ipt_cache_weights_set", "ipt_cache_weights_get", "ipt_cache_eval",
     "ipt_cache_grad", "ipt_cache_train", "ipt_cache_records", "ipt_cache_status", "ipt_cache_bias",
     "ipt_probe_gather", "ipt_checkpoint_save", "ipt_checkpoint_load",
+    "ipt_disney_params_set", "ipt_disney_params_get", "ipt_disney_render", "ipt_disney_loss_grad",
+    "ipt_disney_step",
 ]
+IPT_DISNEY_VALUES = 16
 IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox",
                 "wf_camera", "wf_closest", "wf_shadow", "wf_shade", "wf_adj_a", "wf_adj_connect",
@@ -147,6 +150,12 @@ def lib():
                 "ipt_cache_bias": [P, I32, C.POINTER(ipt_trace_opts), U32, U64, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)],
                 "ipt_probe_gather": [I32, U64, C.POINTER(C.c_double)],
+                "ipt_disney_params_set": [P, I32, P, P],
+                "ipt_disney_params_get": [P, I32, P],
+                "ipt_disney_render": [P, I32, I32, C.POINTER(ipt_trace_opts), U32, U32, U64, P, P, P],
+                "ipt_disney_loss_grad": [P, I32, C.POINTER(ipt_trace_opts), U64, C.POINTER(C.c_double), P],
+                "ipt_disney_step": [P, I32, C.POINTER(ipt_trace_opts), C.POINTER(ipt_adam_opts),
+                                    C.POINTER(C.c_double)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -237,6 +246,32 @@ def ipt_step(ctx, scene, opts, adam, want_loss):
     loss = C.c_double()
     _check(ctx, lib().ipt_step(ctx, scene, C.byref(opts), C.byref(adam),
                                C.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def ipt_disney_params_set(ctx, scene, params, free_mask):
+    _check(ctx, lib().ipt_disney_params_set(ctx, scene, params, free_mask))
+
+
+def ipt_disney_params_get(ctx, scene, out):
+    _check(ctx, lib().ipt_disney_params_get(ctx, scene, out))
+
+
+def ipt_disney_render(ctx, scene, view, opts, set_id, spp, iteration, sparams, rgb, msq):
+    _check(ctx, lib().ipt_disney_render(ctx, scene, view, C.byref(opts), set_id, spp, iteration, sparams, rgb, msq))
+
+
+def ipt_disney_loss_grad(ctx, scene, opts, iteration, want_loss, grad_out):
+    loss = C.c_double()
+    _check(ctx, lib().ipt_disney_loss_grad(ctx, scene, C.byref(opts), iteration,
+                                           C.byref(loss) if want_loss else None, grad_out))
+    return loss.value if want_loss else None
+
+
+def ipt_disney_step(ctx, scene, opts, adam, want_loss):
+    loss = C.c_double()
+    _check(ctx, lib().ipt_disney_step(ctx, scene, C.byref(opts), C.byref(adam),
+                                      C.byref(loss) if want_loss else None))
     return loss.value if want_loss else None
 
 

@@ -43,9 +43,12 @@ SWEEPS = {
 TARGET_DEPTH = {"bounces": 10}
 
 
-def _eval_loss(ev: Tracer, params, opts: TraceOptions, iteration: int) -> float:
+def _eval_loss(ev: Tracer, target, params, opts: TraceOptions, iteration: int) -> float:
+    """Image L1 loss (1/N) sum |I - I_C| over all pixel-channels, I rendered
+    with residual sample set 0 at a fixed iteration."""
     ev.set_params(params)
-    return float(ev.loss_grad(opts, iteration=iteration)[0])
+    img = ev.render(opts, view=-1, set_id=0, spp=opts.spp_r, iteration=iteration)
+    return float(torch.mean(torch.abs(img - target)))
 
 
 def curve(scene, opts: TraceOptions, adam: AdamOptions, seconds: float, target_depth: int, points: int = 24,
@@ -58,12 +61,13 @@ def curve(scene, opts: TraceOptions, adam: AdamOptions, seconds: float, target_d
     ss.configure(integrator="wavefront")
     ev = Tracer(scene, seed=seed + 1)
     ev.set_params(scene.gt_params)
-    ev.set_targets(ev.render(tgt, view=-1, set_id=2, spp=target_spp))
+    target = ev.render(tgt, view=-1, set_id=2, spp=target_spp)
     eval_opts = TraceOptions(spp_r=eval_spp, spp_d=1, max_depth=target_depth, loss="l1")
     eval_it = 1 << 24  # the same sample set for every setting and checkpoint
     ss.make_batch()
     p = ss.batch_params(0)
-    out = [(0, 0.0, metrics.param_error(p, scene.gt_params, masks[0]), _eval_loss(ev, p, eval_opts, eval_it))]
+    out = [(0, 0.0, metrics.param_error(p, scene.gt_params, masks[0]),
+            _eval_loss(ev, target, p, eval_opts, eval_it))]
     # step cost from a short run (not part of the curve), then a fresh batch
     # from the same start (the scene's own parameters are still the start)
     probe = 20
@@ -86,7 +90,7 @@ def curve(scene, opts: TraceOptions, adam: AdamOptions, seconds: float, target_d
         it += chunk
         p = ss.batch_params(0)
         out.append((it, elapsed, metrics.param_error(p, scene.gt_params, masks[0]),
-                    _eval_loss(ev, p, eval_opts, eval_it)))
+                    _eval_loss(ev, target, p, eval_opts, eval_it)))
     ev.close()
     ss.close()
     return out

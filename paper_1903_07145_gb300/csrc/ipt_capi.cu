@@ -63,6 +63,30 @@ void free_cache(CacheState* c) {
   delete c;
 }
 
+// Disney material model of one scene (Sec. 4.1): its own 16-value
+// parameter blocks, optimiser state and tables, next to the scene's
+// Lambert + GGX parameters.
+struct DisneyState {
+  float* params = nullptr;   // S x 16
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  uint8_t* free_mask = nullptr;
+  int* step_dev = nullptr;
+  double* grad_acc = nullptr;
+  float* gacc = nullptr;     // global accumulators when shared memory is too small
+  ipt::SegBuffers tab{};     // emission, light selection (mat_a, mat_b, pspec unused)
+  ipt::DisneyBuffers dt{};
+  bool tab_is_ctx = false;
+  uint64_t iteration = 0;
+  std::vector<void*> owned;
+};
+
+void free_disney(DisneyState* d) {
+  if (!d) return;
+  for (void* p : d->owned) cudaFree(p);
+  delete d;
+}
+
 struct DeviceScene {
   uint32_t n_tri = 0, n_seg = 0, n_nodes = 0, depth = 0;
   float eps = 0.f, emission_scale = 1.f;
@@ -104,6 +128,7 @@ struct DeviceScene {
   uint64_t iteration = 0;
   float bb_lo[3] = {0.f, 0.f, 0.f}, bb_hi[3] = {1.f, 1.f, 1.f};  // vertex bounding box
   CacheState* cache = nullptr;
+  DisneyState* disney = nullptr;
   std::vector<void*> owned;
 };
 
@@ -198,6 +223,7 @@ cudaError_t dev_alloc(DeviceScene* s, T** p, size_t count) {
 void free_scene(DeviceScene* s) {
   if (!s) return;
   free_cache(s->cache);
+  free_disney(s->disney);
   for (void* p : s->owned) cudaFree(p);
   cudaFree(s->pick);
   cudaFree(s->g_pick);
@@ -2077,6 +2103,214 @@ ipt_status ipt_checkpoint_load(ipt_ctx* ctx, int32_t scene, const void* buf, siz
   s->iteration = h.iteration;
   s->tab_is_ctx = false;  // tables are rebuilt from the loaded parameters
   s->params_set = true;
+  return IPT_OK;
+}
+
+}  // extern "C"
+
+// --- Disney material model (megakernel integrator) -------------------------
+
+namespace {
+
+constexpr uint32_t kDisneyValues = 16;
+
+ipt_status disney_state(ipt_ctx* ctx, DeviceScene* s, DisneyState** out) {
+  if (s->disney) {
+    *out = s->disney;
+    return IPT_OK;
+  }
+  DisneyState* d = new (std::nothrow) DisneyState();
+  if (!d) return IPT_ERR_OUT_OF_MEMORY;
+  const size_t S = s->n_seg, np = kDisneyValues * S;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t count) {
+    if (e != cudaSuccess) return;
+    void* q = nullptr;
+    e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(**p));
+    if (e == cudaSuccess) {
+      d->owned.push_back(q);
+      *p = static_cast<std::remove_reference_t<decltype(*p)>>(q);
+    }
+  };
+  A(&d->params, np);
+  A(&d->adam_m, np);
+  A(&d->adam_v, np);
+  A(&d->free_mask, np);
+  A(&d->step_dev, 1);
+  A(&d->grad_acc, np);
+  if (S > ipt::disney_max_shared_segments()) A(&d->gacc, np);
+  A(&d->tab.emis, S);
+  A(&d->tab.samp, S);
+  A(&d->tab.cdf, S);
+  A(&d->tab.lum, S);
+  A(&d->tab.W, 1);
+  A(&d->dt.mat, 4 * S);
+  A(&d->dt.lobe, S);
+  A(&d->dt.samp, 2 * S);
+  if (e != cudaSuccess) {
+    free_disney(d);
+    return cuda_fail(ctx, e, "Disney state");
+  }
+  s->disney = d;
+  *out = d;
+  return IPT_OK;
+}
+
+ipt_status get_disney(ipt_ctx* ctx, int32_t scene, DeviceScene** s, DisneyState** d) {
+  ipt_status st = get_scene(ctx, scene, s);
+  if (st != IPT_OK) return st;
+  if (!(*s)->disney) return fail(ctx, IPT_ERR_INVALID_ARG, "no Disney parameters set (ipt_disney_params_set)");
+  *d = (*s)->disney;
+  return IPT_OK;
+}
+
+ipt_status disney_tables(ipt_ctx* ctx, DeviceScene* s, DisneyState* d, const float* sparams) {
+  if (!sparams && d->tab_is_ctx) return IPT_OK;
+  Timed tm(ctx, IPT_KERNEL_PREPARE);
+  IPT_CK(ipt::launch_disney_tables(buffers(ctx, s), d->tab, d->dt, d->params, sparams, ctx->stream));
+  d->tab_is_ctx = sparams == nullptr;
+  return IPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ipt_status ipt_disney_params_set(ipt_ctx* ctx, int32_t scene, const float* params, const uint8_t* free_mask) {
+  DeviceScene* s;
+  ipt_status st = get_scene(ctx, scene, &s);
+  if (st != IPT_OK) return st;
+  if (!params) return fail(ctx, IPT_ERR_INVALID_ARG, "null params");
+  const size_t n = kDisneyValues * (size_t)s->n_seg;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(params[i])) return fail(ctx, IPT_ERR_NONFINITE, "non-finite parameter " + std::to_string(i));
+  IPT_CK(cudaSetDevice(ctx->device));
+  DisneyState* d;
+  if ((st = disney_state(ctx, s, &d)) != IPT_OK) return st;
+  IPT_CK(cudaMemcpyAsync(d->params, params, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  IPT_CK(cudaMemsetAsync(d->adam_m, 0, n * sizeof(float), ctx->stream));
+  IPT_CK(cudaMemsetAsync(d->adam_v, 0, n * sizeof(float), ctx->stream));
+  IPT_CK(cudaMemsetAsync(d->step_dev, 0, sizeof(int), ctx->stream));
+  if (free_mask) {
+    IPT_CK(cudaMemcpyAsync(d->free_mask, free_mask, n, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    IPT_CK(cudaMemsetAsync(d->free_mask, 1, n, ctx->stream));
+  }
+  IPT_CK(cudaStreamSynchronize(ctx->stream));  // host buffers may be released on return
+  d->tab_is_ctx = false;
+  d->iteration = 0;
+  return IPT_OK;
+}
+
+ipt_status ipt_disney_params_get(ipt_ctx* ctx, int32_t scene, float* params_out) {
+  DeviceScene* s;
+  DisneyState* d;
+  ipt_status st = get_disney(ctx, scene, &s, &d);
+  if (st != IPT_OK) return st;
+  if (!params_out) return fail(ctx, IPT_ERR_INVALID_ARG, "null output");
+  IPT_CK(cudaSetDevice(ctx->device));
+  IPT_CK(cudaMemcpyAsync(params_out, d->params, kDisneyValues * sizeof(float) * s->n_seg, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  return ipt_synchronize(ctx);
+}
+
+ipt_status ipt_disney_render(ipt_ctx* ctx, int32_t scene, int32_t view, const ipt_trace_opts* opts, uint32_t set,
+                             uint32_t spp, uint64_t iteration, const float* sampling_params, float* rgb_out,
+                             float* msq_out) {
+  DeviceScene* s;
+  DisneyState* d;
+  ipt_status st = get_disney(ctx, scene, &s, &d);
+  if (st != IPT_OK) return st;
+  if ((st = check_opts(ctx, opts, false)) != IPT_OK) return st;
+  if (s->views.empty()) return fail(ctx, IPT_ERR_INVALID_ARG, "no views set");
+  if (view < -1 || view >= (int32_t)s->views.size()) return fail(ctx, IPT_ERR_INVALID_ARG, "view out of range");
+  if (spp == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp must be positive");
+  if (!rgb_out && !msq_out) return fail(ctx, IPT_ERR_INVALID_ARG, "no output");
+  IPT_CK(cudaSetDevice(ctx->device));
+  if ((st = disney_tables(ctx, s, d, sampling_params)) != IPT_OK) return st;
+  const uint32_t begin = view < 0 ? 0u : s->views[view].offset;
+  const uint32_t n = view < 0 ? (uint32_t)s->n_pix : s->views[view].w * s->views[view].h;
+  Timed tm(ctx, IPT_KERNEL_FORWARD);
+  IPT_CK(ipt::launch_disney_forward(ctx->L, buffers(ctx, s), d->tab, d->dt, s->views_dev,
+                                    (uint32_t)s->views.size(), begin, n,
+                                    trace_params(ctx, scene, opts, set, spp, iteration), rgb_out, msq_out, nullptr,
+                                    nullptr, nullptr, 0.f, 0, ctx->err_dev, ctx->stream));
+  return IPT_OK;
+}
+
+// Forward + residual + adjoint of the Disney parameters, all pixels or a
+// stochastic pixel batch; grad_out (device, S x 16) nullable.
+static ipt_status disney_loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, DisneyState* d,
+                                         const ipt_trace_opts* opts, uint64_t iteration, float* grad_out) {
+  ipt_status st;
+  if ((st = check_opts(ctx, opts, true, true)) != IPT_OK) return st;
+  if (s->views.empty() || !s->target) return fail(ctx, IPT_ERR_INVALID_ARG, "loss needs views and targets");
+  if (opts->spp_r == 0 || opts->spp_d == 0) return fail(ctx, IPT_ERR_INVALID_ARG, "spp_r and spp_d must be positive");
+  IPT_CK(cudaSetDevice(ctx->device));
+  if ((st = disney_tables(ctx, s, d, nullptr)) != IPT_OK) return st;
+  const uint32_t B = opts->pixel_batch;
+  if (B && ((st = ensure_pick(ctx, s, B)) != IPT_OK || (st = draw_picks(ctx, scene, s, B, iteration, s->pick)) != IPT_OK))
+    return st;
+  const uint32_t n = B ? B : (uint32_t)s->n_pix;
+  float* g_buf = B ? s->g_pick : s->g_img;
+  const uint32_t* pick = B ? s->pick : nullptr;
+  const float g_scale = (float)(1.0 / (3.0 * (double)n));
+  const ipt::SceneBuffers sb = buffers(ctx, s);
+  ipt::TraceParams tpr = trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration);
+  tpr.pick = pick;
+  {
+    Timed tm(ctx, IPT_KERNEL_FORWARD);
+    IPT_CK(ipt::launch_disney_forward(ctx->L, sb, d->tab, d->dt, s->views_dev, (uint32_t)s->views.size(), 0, n, tpr,
+                                      nullptr, nullptr, s->target, g_buf, s->loss_partials, g_scale, opts->loss,
+                                      ctx->err_dev, ctx->stream));
+  }
+  const uint32_t np = kDisneyValues * s->n_seg;
+  IPT_CK(cudaMemsetAsync(d->grad_acc, 0, np * sizeof(double), ctx->stream));
+  const uint32_t set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
+  ipt::TraceParams tpd = trace_params(ctx, scene, opts, set, opts->spp_d, iteration);
+  if (opts->gradcheck_same_set) tpd.sample_stride = opts->spp_r;
+  tpd.pick = pick;
+  {
+    Timed tm(ctx, IPT_KERNEL_ADJOINT);
+    IPT_CK(ipt::launch_disney_adjoint(ctx->L, sb, d->tab, d->dt, s->views_dev, (uint32_t)s->views.size(), 0, n, tpd,
+                                      g_buf, d->grad_acc, d->gacc, ctx->err_dev, ctx->stream));
+  }
+  Timed tm(ctx, IPT_KERNEL_FINALIZE);
+  IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, d->grad_acc,
+                              grad_out, np, ctx->stream));
+  return IPT_OK;
+}
+
+ipt_status ipt_disney_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint64_t iteration,
+                                double* loss_out, float* grad_out) {
+  DeviceScene* s;
+  DisneyState* d;
+  ipt_status st = get_disney(ctx, scene, &s, &d);
+  if (st != IPT_OK) return st;
+  if ((st = disney_loss_grad_async(ctx, scene, s, d, opts, iteration, grad_out)) != IPT_OK) return st;
+  if (loss_out) return read_loss(ctx, s, loss_out, opts->pixel_batch ? opts->pixel_batch : s->n_pix);
+  return IPT_OK;
+}
+
+ipt_status ipt_disney_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, const ipt_adam_opts* adam,
+                           double* loss_out) {
+  DeviceScene* s;
+  DisneyState* d;
+  ipt_status st = get_disney(ctx, scene, &s, &d);
+  if (st != IPT_OK) return st;
+  if (!adam) return fail(ctx, IPT_ERR_INVALID_ARG, "null adam options");
+  if (!(adam->lr >= 0.0f) || !(adam->beta1 >= 0.0f && adam->beta1 < 1.0f) ||
+      !(adam->beta2 >= 0.0f && adam->beta2 < 1.0f) || !(adam->eps > 0.0f) || !(adam->l1_emission >= 0.0f))
+    return fail(ctx, IPT_ERR_INVALID_ARG, "invalid adam options");
+  if ((st = disney_loss_grad_async(ctx, scene, s, d, opts, d->iteration, nullptr)) != IPT_OK) return st;
+  {
+    Timed tm(ctx, IPT_KERNEL_ADAM);
+    IPT_CK(ipt::launch_disney_adam(buffers(ctx, s), d->tab, d->dt, d->params, d->adam_m, d->adam_v, d->free_mask,
+                                   d->grad_acc, nullptr, d->step_dev, adam_host(adam), ctx->stream));
+  }
+  d->tab_is_ctx = true;  // the Adam kernel rebuilt the tables from the new parameters
+  d->iteration++;
+  if (loss_out) return read_loss(ctx, s, loss_out, opts->pixel_batch ? opts->pixel_batch : s->n_pix);
   return IPT_OK;
 }
 

@@ -196,4 +196,33 @@ struct WfHook {
 cudaError_t wf_init(Launcher* L);
 int wf_max_blocks(const Launcher& L);
 
+// Disney material model (megakernel integrator): per-segment tables built
+// from the 16-value parameter blocks, next to the shared light-selection
+// tables in SegBuffers (emis, samp.z = p_A, cdf, lum, W).
+struct DisneyBuffers {
+  float4* mat;    // 4 per segment: the 13 material values, then zeros
+  double2* lobe;  // cumulative lobe probabilities (P_d, P_d + P_s), FP64
+  float4* samp;   // 2 per segment: (a_x, a_y, a_c, 0), (P_d, P_s, P_c, 0)
+};
+
+cudaError_t launch_disney_tables(const SceneBuffers& s, const SegBuffers& t, const DisneyBuffers& d,
+                                 const float* params, const float* sparams, cudaStream_t st);
+cudaError_t launch_disney_forward(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
+                                  const DisneyBuffers& d, const ViewHost* views_dev, uint32_t n_views,
+                                  uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp, float* img, float* msq,
+                                  const float* target, float* g_out, double* loss_partials, float g_scale,
+                                  int loss_kind, uint32_t* err, cudaStream_t st);
+// Accumulates into grad_acc (16 per segment); scenes whose accumulators do
+// not fit a block's shared memory use gacc_scratch (16 S floats).
+cudaError_t launch_disney_adjoint(const Launcher& L, const SceneBuffers& s, const SegBuffers& t,
+                                  const DisneyBuffers& d, const ViewHost* views_dev, uint32_t n_views,
+                                  uint32_t pix_begin, uint32_t n_pix, const TraceParams& tp, const float* g_img,
+                                  double* grad_acc, float* gacc_scratch, uint32_t* err, cudaStream_t st);
+// Adam with the Disney clamps (material values in [0, 1], roughness in
+// [0.02, 1], emission >= 0 with the L1 term), then the tables.
+cudaError_t launch_disney_adam(const SceneBuffers& s, const SegBuffers& t, const DisneyBuffers& d, float* params,
+                               float* m, float* v, const uint8_t* free_mask, const double* grad_acc,
+                               const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st);
+uint32_t disney_max_shared_segments();
+
 }  // namespace ipt

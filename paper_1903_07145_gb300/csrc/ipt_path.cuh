@@ -200,9 +200,12 @@ struct NeeResult {
 // Light selection proportional to lum(e_s) A_s, then area within the segment,
 // then a uniform point (sqrt parameterisation).  Returns the candidate with
 // its shadow ray (from the offset point, skipping both end triangles); the
-// candidate counts only if that ray is unoccluded.
-__device__ __forceinline__ NeeResult nee_prepare(const SceneDev& s, const SegDev& t, const Vtx& v, float4 ua,
-                                                 float4 ub, double W, int profile, int mis, float P, float a_s) {
+// candidate counts only if that ray is unoccluded.  bsdf_pdf_to(wl) is the
+// material sampler's solid-angle pdf towards wl (for the MIS weight).
+template <class PdfTo>
+__device__ __forceinline__ NeeResult nee_prepare_with(const SceneDev& s, const SegDev& t, const Vtx& v, float4 ua,
+                                                      float4 ub, double W, int profile, int mis,
+                                                      const PdfTo& bsdf_pdf_to) {
   NeeResult r;
   r.valid = false;
   const int sl = upper_bound_d(t.cdf, 0, (int)s.n_seg, (double)ua.w * W);
@@ -233,7 +236,7 @@ __device__ __forceinline__ NeeResult nee_prepare(const SceneDev& s, const SegDev
   float wlight = 1.0f;
   if (mis) {
     const float pl = pA * r2 / cos_l;
-    const float pb = bsdf_pdf(P, a_s, v.ns, v.wi, wl);
+    const float pb = bsdf_pdf_to(wl);
     wlight = pl * pl / (pl * pl + pb * pb);
   }
   r.valid = true;
@@ -242,6 +245,13 @@ __device__ __forceinline__ NeeResult nee_prepare(const SceneDev& s, const SegDev
   r.wl = wl;
   r.k = cxs * lprof * (cos_l / r2) / pA * wlight;
   return r;
+}
+
+// Lambert + GGX: the mixture sampler of bsdf_sample.
+__device__ __forceinline__ NeeResult nee_prepare(const SceneDev& s, const SegDev& t, const Vtx& v, float4 ua,
+                                                 float4 ub, double W, int profile, int mis, float P, float a_s) {
+  return nee_prepare_with(s, t, v, ua, ub, W, profile, mis,
+                          [&](float3 wl) { return bsdf_pdf(P, a_s, v.ns, v.wi, wl); });
 }
 
 // Next-event estimation with the visibility test done in place.

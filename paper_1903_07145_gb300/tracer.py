@@ -182,6 +182,37 @@ class Tracer:
                                      n_total, _ptr(grad))
         return loss, grad
 
+    # -- Disney material model (Sec. 4.1; megakernel integrator) -------------
+    def disney_set_params(self, params, free_mask=None):
+        """(S, 16) blocks: base colour, subsurface, metallic, specular,
+        specular tint, roughness, anisotropic, sheen, sheen tint, clearcoat,
+        clearcoat gloss, emission."""
+        p = np.ascontiguousarray(np.asarray(params, np.float32).reshape(self.n_seg, 16))
+        fm = None if free_mask is None else np.ascontiguousarray(np.asarray(free_mask, np.uint8))
+        L.ipt_disney_params_set(self.ctx, self.sid, _np_ptr(p), _np_ptr(fm))
+
+    def disney_params(self) -> np.ndarray:
+        out = np.zeros((self.n_seg, 16), np.float32)
+        L.ipt_disney_params_get(self.ctx, self.sid, _np_ptr(out))
+        return out
+
+    def disney_render(self, opts: TraceOptions, view: int = -1, set_id: int = L.IPT_SET_TARGET,
+                      spp: int | None = None, iteration: int = 0, sampling_params=None, with_msq: bool = False):
+        n = self.n_pix if view < 0 else self.sizes[view][0] * self.sizes[view][1]
+        img = torch.empty((n, 3), device=self.device, dtype=torch.float32)
+        msq = torch.empty_like(img) if with_msq else None
+        L.ipt_disney_render(self.ctx, self.sid, view, opts.c(), set_id, opts.spp_r if spp is None else spp,
+                            iteration, _ptr(sampling_params), _ptr(img), _ptr(msq))
+        return (img, msq) if with_msq else img
+
+    def disney_loss_grad(self, opts: TraceOptions, iteration: int = 0):
+        grad = torch.empty((self.n_seg, 16), device=self.device, dtype=torch.float32)
+        loss = L.ipt_disney_loss_grad(self.ctx, self.sid, opts.c(), iteration, True, _ptr(grad))
+        return loss, grad
+
+    def disney_step(self, opts: TraceOptions, adam: AdamOptions, want_loss: bool = True):
+        return L.ipt_disney_step(self.ctx, self.sid, opts.c(), adam.c(), want_loss)
+
     def adam_step(self, adam: AdamOptions, grad=None):
         L.ipt_adam_step(self.ctx, self.sid, _ptr(grad), adam.c())
 
