@@ -612,7 +612,8 @@ def run_disney(args):
         stream = torch.cuda.current_stream(dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        tr.kernel_times(reset=True)
+        if timing:
+            tr.kernel_times(reset=True)
         with ClockSampler(0) as clk:
             for i in range(args.steps):
                 flush.zero_()

@@ -13,7 +13,9 @@
 // Each warp runs 16 rows through the network with mma.sync m16n8k16 (BF16
 // operands, FP32 accumulation).  The encoded input tile is staged in shared
 // memory; a layer's FP32 accumulator fragments are exactly the next layer's
-// A fragments once packed to BF16, so hidden activations stay in registers.
+// A fragments once packed to BF16, so hidden activations stay in registers,
+// and the inference VJP needs only their ReLU masks (one register per layer).
+// Inference blocks of 16 warps share one weight image (two blocks per SM).
 // The backward pass loads the transposed weights with ldmatrix.trans from the
 // same out-major image.  Training keeps the block's 64 rows of activations
 // and pre-activation gradients in shared memory, so each warp then forms
@@ -52,9 +54,7 @@ constexpr int kSmDz = kSmH + 4 * kTileRows * kHs * 2;
 constexpr int kSmDy = kSmDz + 4 * kTileRows * kHs * 2;
 constexpr int kSmDw = kSmDy + kTileRows * kYs * 2;
 constexpr int kSmEnd = kSmDw + (int)kCacheWeights * 4;
-constexpr int kSmemInfer = kSmH;   // weights, input tile, row metadata
-constexpr int kSmemVjp = kSmDz;    // + hidden activations
-constexpr int kSmemTrain = kSmEnd; // + pre-activation gradients, dY, dW
+constexpr int kSmemTrain = kSmEnd;  // weights, tiles, activations, pre-activation gradients, dY, dW
 static_assert(kSmX % 16 == 0 && kSmMeta % 16 == 0 && kSmH % 16 == 0 && kSmDz % 16 == 0 && kSmDy % 16 == 0 &&
                   kSmDw % 16 == 0,
               "shared regions must be 16-byte aligned");
@@ -304,6 +304,86 @@ __device__ __forceinline__ void relu_grad(const float (&dh)[8][4], const uint32_
   }
 }
 
+// ReLU masks of a hidden layer in one register per lane: bit 4j + k is the
+// fragment element k of n-tile j (k = 0, 1: row g; k = 2, 3: row g + 8) and
+// is set where the BF16 activation is positive.  The input VJP needs only
+// these masks, so inference keeps no activation tile in shared memory.
+__device__ __forceinline__ uint32_t relu_pack_mask(const float (&c)[8][4], uint32_t (&a)[4][4]) {
+  uint32_t mask = 0u;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t lo = pack2(fmaxf(c[j][0], 0.0f), fmaxf(c[j][1], 0.0f));
+    const uint32_t hi = pack2(fmaxf(c[j][2], 0.0f), fmaxf(c[j][3], 0.0f));
+    a[j >> 1][(j & 1) * 2 + 0] = lo;
+    a[j >> 1][(j & 1) * 2 + 1] = hi;
+    mask |= ((lo & 0x7FFFu) ? 1u : 0u) << (4 * j);
+    mask |= ((lo & 0x7FFF0000u) ? 1u : 0u) << (4 * j + 1);
+    mask |= ((hi & 0x7FFFu) ? 1u : 0u) << (4 * j + 2);
+    mask |= ((hi & 0x7FFF0000u) ? 1u : 0u) << (4 * j + 3);
+  }
+  return mask;
+}
+
+__device__ __forceinline__ void relu_grad_mask(const float (&dh)[8][4], uint32_t mask, uint32_t (&a)[4][4]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t m = mask >> (4 * j);
+    a[j >> 1][(j & 1) * 2 + 0] = pack2((m & 1u) ? dh[j][0] : 0.0f, (m & 2u) ? dh[j][1] : 0.0f);
+    a[j >> 1][(j & 1) * 2 + 1] = pack2((m & 4u) ? dh[j][2] : 0.0f, (m & 8u) ? dh[j][3] : 0.0f);
+  }
+}
+
+// Forward pass keeping the hidden layers' ReLU masks (mask[i]: layer i + 1).
+__device__ __forceinline__ void net_forward_mask(const uint32_t* Wt, const uint32_t* X, float (&y)[2][4],
+                                                 uint32_t (&mask)[4], int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  float c[8][4];
+  uint32_t h[4][4];
+  {
+    uint32_t a[5][4];
+#pragma unroll
+    for (int kk = 0; kk < 5; ++kk) {
+      a[kk][0] = X[g * kXw + 8 * kk + t];
+      a[kk][1] = X[(g + 8) * kXw + 8 * kk + t];
+      a[kk][2] = X[g * kXw + 8 * kk + 4 + t];
+      a[kk][3] = X[(g + 8) * kXw + 8 * kk + 4 + t];
+    }
+    layer_fwd<5, 8, kXw>(Wt + kWt1 / 2, a, c, g, t);
+  }
+  mask[0] = relu_pack_mask(c, h);
+  layer_fwd<4, 8, kHw>(Wt + kWt2 / 2, h, c, g, t);
+  mask[1] = relu_pack_mask(c, h);
+  layer_fwd<4, 8, kHw>(Wt + kWt3 / 2, h, c, g, t);
+  mask[2] = relu_pack_mask(c, h);
+  layer_fwd<4, 8, kHw>(Wt + kWt4 / 2, h, c, g, t);
+  mask[3] = relu_pack_mask(c, h);
+  layer_fwd<4, 2, kHw>(Wt + kWt5 / 2, h, y, g, t);
+}
+
+// Input VJP from the masks: gradient fragments of n-tile pairs [JP0, JP1)
+// of the 80 inputs.
+template <int JP0, int JP1>
+__device__ __forceinline__ void net_backward_mask(const __nv_bfloat16* Wtb, const uint32_t (&mask)[4],
+                                                  const float (&dy)[2][4], float (&dx)[2 * (JP1 - JP0)][4],
+                                                  int lane) {
+  uint32_t ay[1][4];
+  ay[0][0] = pack2(dy[0][0], dy[0][1]);
+  ay[0][1] = pack2(dy[0][2], dy[0][3]);
+  ay[0][2] = pack2(dy[1][0], dy[1][1]);
+  ay[0][3] = pack2(dy[1][2], dy[1][3]);
+  float dh[8][4];
+  uint32_t a[4][4];
+  layer_bwd<1, 0, 4, kHs>(Wtb + kWt5, ay, dh, lane);
+  relu_grad_mask(dh, mask[3], a);
+  layer_bwd<4, 0, 4, kHs>(Wtb + kWt4, a, dh, lane);
+  relu_grad_mask(dh, mask[2], a);
+  layer_bwd<4, 0, 4, kHs>(Wtb + kWt3, a, dh, lane);
+  relu_grad_mask(dh, mask[1], a);
+  layer_bwd<4, 0, 4, kHs>(Wtb + kWt2, a, dh, lane);
+  relu_grad_mask(dh, mask[0], a);
+  layer_bwd<4, JP0, JP1, kXs>(Wtb + kWt1, a, dx, lane);
+}
+
 // Backward pass of the warp's rows from dL/dy down to the inputs: returns the
 // input-gradient fragments of n-tile pairs [JP0, JP1) of the 80 inputs.
 // Pre-activation gradients (and dY) are stored when kStore.
@@ -345,11 +425,20 @@ __device__ __forceinline__ void load_weights(const CacheNet& net, unsigned char*
   }
 }
 
-// Inference (and input VJP) over warp tiles of 16 rows.
-template <bool kVjp>
-__global__ void __launch_bounds__(kThreads) cache_infer_k(CacheNet net, CacheRows rows, const float4* mat_a,
-                                                          const float4* mat_b, const uint32_t* count_dev,
-                                                          uint32_t n_max, CacheOut o) {
+// Inference (and input VJP) over warp tiles of 16 rows; W warps share one
+// shared-memory weight image.  The VJP keeps the hidden layers' ReLU masks in
+// registers, so a block holds only the weights and its warps' input tiles.
+constexpr int kInferWarps = 16;
+template <int W>
+constexpr int infer_smem() {
+  return kSmX + W * 16 * kXs * 2 + W * 16 * 16;
+}
+static_assert(kSmX % 16 == 0 && (kSmX + kInferWarps * 16 * kXs * 2) % 16 == 0, "infer tiles must be aligned");
+
+template <bool kVjp, int W>
+__global__ void __launch_bounds__(W * 32, 2) cache_infer_k(CacheNet net, CacheRows rows, const float4* mat_a,
+                                                           const float4* mat_b, const uint32_t* count_dev,
+                                                           uint32_t n_max, CacheOut o) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int res[kCacheLevels];
   load_weights(net, sm, res);
@@ -360,16 +449,15 @@ __global__ void __launch_bounds__(kThreads) cache_infer_k(CacheNet net, CacheRow
   const uint32_t* Wt = reinterpret_cast<const uint32_t*>(sm + kSmWt);
   const __nv_bfloat16* Wtb = reinterpret_cast<const __nv_bfloat16*>(sm + kSmWt);
   uint32_t* X = reinterpret_cast<uint32_t*>(sm + kSmX) + warp * 16 * kXw;
-  float4* meta = reinterpret_cast<float4*>(sm + kSmMeta) + warp * 16;
-  uint32_t* H = reinterpret_cast<uint32_t*>(sm + kSmH) + warp * 16 * kHw;
-  const int hstride = kTileRows * kHw;
+  float4* meta = reinterpret_cast<float4*>(sm + kSmX + W * 16 * kXs * 2) + warp * 16;
   const uint32_t n_tiles = (n + 15u) / 16u;
-  for (uint32_t tile = blockIdx.x * 4u + (uint32_t)warp; tile < n_tiles; tile += gridDim.x * 4u) {
+  for (uint32_t tile = blockIdx.x * (uint32_t)W + (uint32_t)warp; tile < n_tiles; tile += gridDim.x * (uint32_t)W) {
     const uint32_t r0 = tile * 16u;
     __syncwarp();
     encode_rows(net, res, rows, mat_a, mat_b, r0, n, X, meta, lane);
     float y[2][4];
-    net_forward<kVjp>(Wt, X, H, hstride, y, lane);
+    uint32_t mask[4];
+    net_forward_mask(Wt, X, y, mask, lane);
     // rows g and g + 8: lane t = 0 holds outputs 0, 1 and takes 2 from lane t = 1
     const float y2a = __shfl_down_sync(0xffffffffu, y[0][0], 1);
     const float y2b = __shfl_down_sync(0xffffffffu, y[0][2], 1);
@@ -412,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) cache_infer_k(CacheNet net, CacheRow
         }
       }
       float dx[2][4];
-      net_backward<false, 4, 5>(Wtb, H, hstride, nullptr, nullptr, dy, dx, lane);
+      net_backward_mask<4, 5>(Wtb, mask, dy, dx, lane);
       // n-tile 8 = inputs 64..71: kd rgb, ks rgb, roughness, pad
       if (o.dp) {
         if (ra < n) *reinterpret_cast<float2*>(&o.dp[8 * (size_t)ra + 2 * t]) = make_float2(dx[0][0], dx[0][1]);
@@ -672,22 +760,32 @@ void cache_grid(int res[kCacheLevels], uint32_t* dense) {
   }
 }
 
+template <bool kVjp>
+static cudaError_t launch_infer(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,
+                                const uint32_t* count_dev, uint32_t n, const CacheOut& out, int num_sms,
+                                cudaStream_t st) {
+  constexpr int W = kInferWarps, smem = infer_smem<W>();
+  cudaError_t e = cudaFuncSetAttribute(cache_infer_k<kVjp, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  static int per_sm = 0;  // resident blocks per SM at this shared-memory size (the same on every GB300)
+  if (per_sm == 0) {
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cache_infer_k<kVjp, W>, W * 32, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = b < 1 ? 1 : b;
+  }
+  const uint32_t tiles = (n + 16u * W - 1u) / (16u * W);
+  const int grid = (int)std::max<uint32_t>(1u, std::min<uint32_t>(tiles, (uint32_t)(num_sms * per_sm)));
+  cache_infer_k<kVjp, W><<<grid, W * 32, smem, st>>>(net, rows, mat_a, mat_b, count_dev, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t cache_infer(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,
                         const uint32_t* count_dev, uint32_t n, const CacheOut& out, bool vjp, int num_sms,
                         cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const int smem = vjp ? kSmemVjp : kSmemInfer;
-  const int per_sm = vjp ? 2 : 4;
-  const uint32_t tiles = (n + 63u) / 64u;
-  const int grid = (int)std::min<uint32_t>(tiles, (uint32_t)(num_sms * per_sm));
-  if (vjp) {
-    cudaFuncSetAttribute(cache_infer_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cache_infer_k<true><<<grid, kThreads, smem, st>>>(net, rows, mat_a, mat_b, count_dev, n, out);
-  } else {
-    cudaFuncSetAttribute(cache_infer_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cache_infer_k<false><<<grid, kThreads, smem, st>>>(net, rows, mat_a, mat_b, count_dev, n, out);
-  }
-  return cudaGetLastError();
+  return vjp ? launch_infer<true>(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st)
+             : launch_infer<false>(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st);
 }
 
 cudaError_t cache_grad(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,
