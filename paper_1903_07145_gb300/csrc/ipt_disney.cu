@@ -117,19 +117,11 @@ __device__ __forceinline__ float3 disney_eval(const float (&m)[kDisneyMat], floa
 // acc[j] += sum_c q_c d f_c(wi, wo) / d m_j for the 13 material values.
 __device__ __forceinline__ void disney_grad(const float (&m)[kDisneyMat], float3 n, float3 X, float3 Y, float3 wi,
                                             float3 wo, float3 q, float* acc) {
-  Dual13 md[kDisneyMat];
+  float g[kDisneyMat];
+  if (!disney_vjp(m, n, X, Y, wi, wo, q, g)) return;
 #pragma unroll
-  for (int j = 0; j < kDisneyMat; ++j) {
-    md[j] = dc(m[j]);
-    md[j].d[j] = 1.0f;
-  }
-  Dual13 f[3];
-  disney_f(md, n, X, Y, wi, wo, f);
-#pragma unroll
-  for (int j = 0; j < kDisneyMat; ++j) {
-    const float g = q.x * f[0].d[j] + q.y * f[1].d[j] + q.z * f[2].d[j];
-    if (g != 0.0f) atomicAdd(&acc[j], g);
-  }
+  for (int j = 0; j < kDisneyMat; ++j)
+    if (g[j] != 0.0f) atomicAdd(&acc[j], g[j]);
 }
 
 __device__ __forceinline__ void add3d(float* acc, int i, float3 v) {

@@ -24,7 +24,8 @@
 //
 // The derivatives the adjoint needs (the 3 x 13 Jacobian of f_r with respect
 // to the material values, contracted with an RGB weight) come from
-// forward-mode dual numbers: the same templated evaluation run on Dual13.
+// forward-mode dual numbers (DualN: a value and N tangents) where the
+// chain rule is long, and hand-derived partials where it is short.
 #pragma once
 
 #include "ipt_device.cuh"
@@ -36,109 +37,156 @@ constexpr int kDisneyMat = 13;     // material values per segment
 constexpr int kDisneyStride = 16;  // material + emission
 constexpr float kLumRf = (float)kLumR, kLumGf = (float)kLumG, kLumBf = (float)kLumB;
 
-struct Dual13 {
+// Forward-mode dual number: a value and N tangents.
+template <int N>
+struct DualN {
   float v;
-  float d[kDisneyMat];
+  float d[N];
 };
-__device__ __forceinline__ Dual13 dc(float x) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> dconst(float x) {
+  DualN<N> r;
   r.v = x;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = 0.0f;
+  for (int i = 0; i < N; ++i) r.d[i] = 0.0f;
   return r;
 }
-__device__ __forceinline__ Dual13 operator+(const Dual13& a, const Dual13& b) {
-  Dual13 r;
+// the value x with tangent e_i
+template <int N>
+__device__ __forceinline__ DualN<N> dvar(float x, int i) {
+  DualN<N> r = dconst<N>(x);
+  r.d[i] = 1.0f;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator+(const DualN<N>& a, const DualN<N>& b) {
+  DualN<N> r;
   r.v = a.v + b.v;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] + b.d[i];
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
   return r;
 }
-__device__ __forceinline__ Dual13 operator-(const Dual13& a, const Dual13& b) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> operator-(const DualN<N>& a, const DualN<N>& b) {
+  DualN<N> r;
   r.v = a.v - b.v;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] - b.d[i];
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
   return r;
 }
-__device__ __forceinline__ Dual13 operator*(const Dual13& a, const Dual13& b) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> operator*(const DualN<N>& a, const DualN<N>& b) {
+  DualN<N> r;
   r.v = a.v * b.v;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
   return r;
 }
-__device__ __forceinline__ Dual13 operator*(const Dual13& a, float b) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> operator*(const DualN<N>& a, float b) {
+  DualN<N> r;
   r.v = a.v * b;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] * b;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
   return r;
 }
-__device__ __forceinline__ Dual13 operator*(float b, const Dual13& a) { return a * b; }
-__device__ __forceinline__ Dual13 operator+(const Dual13& a, float b) {
-  Dual13 r = a;
+template <int N>
+__device__ __forceinline__ DualN<N> operator*(float b, const DualN<N>& a) {
+  return a * b;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator+(const DualN<N>& a, float b) {
+  DualN<N> r = a;
   r.v += b;
   return r;
 }
-__device__ __forceinline__ Dual13 operator+(float b, const Dual13& a) { return a + b; }
-__device__ __forceinline__ Dual13 operator-(const Dual13& a, float b) {
-  Dual13 r = a;
+template <int N>
+__device__ __forceinline__ DualN<N> operator+(float b, const DualN<N>& a) {
+  return a + b;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator-(const DualN<N>& a, float b) {
+  DualN<N> r = a;
   r.v -= b;
   return r;
 }
-__device__ __forceinline__ Dual13 operator-(float b, const Dual13& a) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> operator-(float b, const DualN<N>& a) {
+  DualN<N> r;
   r.v = b - a.v;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = -a.d[i];
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
   return r;
 }
-// 1 / a
-__device__ __forceinline__ Dual13 rcp(const Dual13& a) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> rcp(const DualN<N>& a) {
+  DualN<N> r;
   r.v = 1.0f / a.v;
   const float k = -r.v * r.v;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] * k;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * k;
   return r;
 }
-__device__ __forceinline__ Dual13 operator/(const Dual13& a, const Dual13& b) { return a * rcp(b); }
-__device__ __forceinline__ Dual13 operator/(float a, const Dual13& b) { return rcp(b) * a; }
-__device__ __forceinline__ Dual13 operator/(const Dual13& a, float b) { return a * (1.0f / b); }
-__device__ __forceinline__ Dual13 dsqrt(const Dual13& a) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> operator/(const DualN<N>& a, const DualN<N>& b) {
+  return a * rcp(b);
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator/(float a, const DualN<N>& b) {
+  return rcp(b) * a;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator/(const DualN<N>& a, float b) {
+  return a * (1.0f / b);
+}
+template <int N>
+__device__ __forceinline__ DualN<N> dsqrt(const DualN<N>& a) {
+  DualN<N> r;
   r.v = sqrtf(a.v);
   const float k = 0.5f / r.v;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] * k;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * k;
   return r;
 }
-__device__ __forceinline__ Dual13 dlog(const Dual13& a) {
-  Dual13 r;
+template <int N>
+__device__ __forceinline__ DualN<N> dlog(const DualN<N>& a) {
+  DualN<N> r;
   r.v = logf(a.v);
   const float k = 1.0f / a.v;
 #pragma unroll
-  for (int i = 0; i < kDisneyMat; ++i) r.d[i] = a.d[i] * k;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * k;
   return r;
 }
 __device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ float dlog(float a) { return logf(a); }
 __device__ __forceinline__ float val(float a) { return a; }
-__device__ __forceinline__ float val(const Dual13& a) { return a.v; }
+template <int N>
+__device__ __forceinline__ float val(const DualN<N>& a) {
+  return a.v;
+}
 // max(a, c) with a constant c (zero derivative where c wins)
 __device__ __forceinline__ float floor_at(float a, float c) { return a > c ? a : c; }
-__device__ __forceinline__ Dual13 floor_at(const Dual13& a, float c) { return a.v > c ? a : dc(c); }
+template <int N>
+__device__ __forceinline__ DualN<N> floor_at(const DualN<N>& a, float c) {
+  return a.v > c ? a : dconst<N>(c);
+}
 template <class T>
-__device__ __forceinline__ T zero_like();
+struct Zero {
+  __device__ static T get();
+};
 template <>
-__device__ __forceinline__ float zero_like<float>() {
-  return 0.0f;
+struct Zero<float> {
+  __device__ static float get() { return 0.0f; }
+};
+template <int N>
+struct Zero<DualN<N>> {
+  __device__ static DualN<N> get() { return dconst<N>(0.0f); }
+};
+template <class T>
+__device__ __forceinline__ T zero_like() {
+  return Zero<T>::get();
 }
-template <>
-__device__ __forceinline__ Dual13 zero_like<Dual13>() {
-  return dc(0.0f);
-}
+using Dual13 = DualN<kDisneyMat>;
 
 __device__ __forceinline__ float schlick_w(float c) {
   const float m = fminf(1.0f, fmaxf(0.0f, 1.0f - c));
@@ -174,19 +222,53 @@ __device__ __forceinline__ T gtr1(float ch, const T& a) {
   return (a2 - 1.0f) / (kPi * dlog(a2) * (1.0f + (a2 - 1.0f) * (ch * ch)));
 }
 
-// f_r per channel for the 13 material values m (float, or Dual13 for the
+// Geometry of one evaluation: cosines with the shading normal, tangent-frame
+// components and Schlick weights.
+struct DisneyGeo {
+  float cl, cv, ch, cd;  // n.wo, n.wi, n.h, wo.h
+  float hx, hy, lx, ly, vx, vy;
+  float Sl, Sv, Sd;
+};
+
+__device__ __forceinline__ bool disney_geo(float3 n, float3 X, float3 Y, float3 wi, float3 wo, DisneyGeo& g) {
+  g.cl = dot(n, wo);
+  g.cv = dot(n, wi);
+  if (!(g.cl > 0.0f) || !(g.cv > 0.0f)) return false;
+  const float3 h = normalize(wi + wo);
+  g.ch = dot(n, h);
+  g.cd = dot(wo, h);
+  g.hx = dot(h, X), g.hy = dot(h, Y);
+  g.lx = dot(wo, X), g.ly = dot(wo, Y), g.vx = dot(wi, X), g.vy = dot(wi, Y);
+  g.Sl = schlick_w(g.cl), g.Sv = schlick_w(g.cv), g.Sd = schlick_w(g.cd);
+  return true;
+}
+
+// D_s g(l) g(v) of the anisotropic GGX lobe at widths (ax, ay).
+template <class T>
+__device__ __forceinline__ T ggx_geo(const T& ax, const T& ay, const DisneyGeo& g) {
+  const T q = (g.hx * g.hx) / (ax * ax) + (g.hy * g.hy) / (ay * ay) + g.ch * g.ch;
+  const T Ds = 1.0f / (kPi * ax * ay * q * q);
+  const T gl = 1.0f / (g.cl + dsqrt((g.lx * g.lx) * (ax * ax) + (g.ly * g.ly) * (ay * ay) + g.cl * g.cl));
+  const T gv = 1.0f / (g.cv + dsqrt((g.vx * g.vx) * (ax * ax) + (g.vy * g.vy) * (ay * ay) + g.cv * g.cv));
+  return Ds * gl * gv;
+}
+
+// Separable Smith masking of the clearcoat (width 0.25), both directions.
+__device__ __forceinline__ float coat_masking(const DisneyGeo& g) {
+  return 1.0f / ((g.cl + sqrtf(0.0625f + 0.9375f * g.cl * g.cl)) * (g.cv + sqrtf(0.0625f + 0.9375f * g.cv * g.cv)));
+}
+
+// f_r per channel for the 13 material values m (float, or DualN for the
 // derivatives); zero unless both directions lie above the shading hemisphere.
 template <class T>
 __device__ __forceinline__ void disney_f(const T (&m)[kDisneyMat], float3 n, float3 X, float3 Y, float3 wi,
                                          float3 wo, T (&f)[3]) {
-  const float cl = dot(n, wo), cv = dot(n, wi);
-  if (!(cl > 0.0f) || !(cv > 0.0f)) {
+  DisneyGeo G;
+  if (!disney_geo(n, X, Y, wi, wo, G)) {
     f[0] = f[1] = f[2] = zero_like<T>();
     return;
   }
-  const float3 h = normalize(wi + wo);
-  const float ch = dot(n, h), cd = dot(wo, h);
-  const float Sl = schlick_w(cl), Sv = schlick_w(cv), Sd = schlick_w(cd);
+  const float cl = G.cl, cv = G.cv, ch = G.ch, cd = G.cd, Sl = G.Sl, Sv = G.Sv, Sd = G.Sd;
   const T lb = m[0] * kLumRf + m[1] * kLumGf + m[2] * kLumBf;
   T tint[3];
 #pragma unroll
@@ -201,18 +283,10 @@ __device__ __forceinline__ void disney_f(const T (&m)[kDisneyMat], float3 n, flo
   // anisotropic GGX with separable masking
   T ax, ay;
   disney_widths(m[7], m[8], ax, ay);
-  const float hx = dot(h, X), hy = dot(h, Y);
-  const T q = (hx * hx) / (ax * ax) + (hy * hy) / (ay * ay) + ch * ch;
-  const T Ds = 1.0f / (kPi * ax * ay * q * q);
-  const float lx = dot(wo, X), ly = dot(wo, Y), vx = dot(wi, X), vy = dot(wi, Y);
-  const T gl = 1.0f / (cl + dsqrt((lx * lx) * (ax * ax) + (ly * ly) * (ay * ay) + cl * cl));
-  const T gv = 1.0f / (cv + dsqrt((vx * vx) * (ax * ax) + (vy * vy) * (ay * ay) + cv * cv));
-  const T spec_geo = Ds * gl * gv;
+  const T spec_geo = ggx_geo(ax, ay, G);
   // clearcoat
   const T ac = 0.1f - 0.099f * m[12];
-  const float gcl = 1.0f / (cl + sqrtf(0.0625f + 0.9375f * cl * cl));
-  const float gcv = 1.0f / (cv + sqrtf(0.0625f + 0.9375f * cv * cv));
-  const T coat = 0.25f * m[11] * gtr1(ch, ac) * ((0.04f + 0.96f * Sd) * gcl * gcv);
+  const T coat = 0.25f * m[11] * gtr1(ch, ac) * ((0.04f + 0.96f * Sd) * coat_masking(G));
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const T C0 = (1.0f - m[4]) * 0.08f * m[5] * (1.0f + m[6] * (tint[c] - 1.0f)) + m[4] * m[c];
@@ -220,6 +294,77 @@ __device__ __forceinline__ void disney_f(const T (&m)[kDisneyMat], float3 n, flo
     const T sheen = (1.0f - m[4]) * m[9] * Sd * (1.0f + m[10] * (tint[c] - 1.0f));
     f[c] = m[c] * diff + sheen + Fs * spec_geo + coat;
   }
+}
+
+// Contracted derivative g_j = sum_c q_c d f_c / d m_j of the 13 material
+// values, by the chain rule written out per parameter; the GGX term's two
+// widths and the clearcoat's GTR1 width go through 2- and 1-tangent dual
+// numbers.  With lum(base) = 0 the tint is the constant white (no base-colour
+// derivative through it), as in the evaluation.  Returns false (g untouched)
+// unless both directions lie above the shading hemisphere.
+__device__ __forceinline__ bool disney_vjp(const float (&m)[kDisneyMat], float3 n, float3 X, float3 Y, float3 wi,
+                                          float3 wo, float3 q3, float (&g)[kDisneyMat]) {
+  DisneyGeo G;
+  if (!disney_geo(n, X, Y, wi, wo, G)) return false;
+  const float q[3] = {q3.x, q3.y, q3.z};
+  const float lw[3] = {kLumRf, kLumGf, kLumBf};
+  const float sub = m[3], met = m[4], spc = m[5], spt = m[6], rho = m[7], shn = m[9], sht = m[10], cc = m[11];
+  const float lb = m[0] * kLumRf + m[1] * kLumGf + m[2] * kLumBf;
+  const bool tinted = lb > 0.0f;
+  float tint[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) tint[c] = tinted ? m[c] / lb : 1.0f;
+  // diffuse and subsurface, with their roughness derivatives
+  const float cd2 = G.cd * G.cd;
+  const float A = 0.5f + 2.0f * cd2 * rho - 1.0f, B = cd2 * rho - 1.0f;
+  const float fd = (1.0f + A * G.Sl) * (1.0f + A * G.Sv);
+  const float dfd = 2.0f * cd2 * (G.Sl * (1.0f + A * G.Sv) + G.Sv * (1.0f + A * G.Sl));
+  const float fss0 = (1.0f + B * G.Sl) * (1.0f + B * G.Sv);
+  const float k_ss = 1.25f * (1.0f / (G.cl + G.cv) - 0.5f);
+  const float fss = k_ss * fss0 + 0.625f;
+  const float dfss = k_ss * cd2 * (G.Sl * (1.0f + B * G.Sv) + G.Sv * (1.0f + B * G.Sl));
+  const float mixd = (1.0f - sub) * fd + sub * fss;
+  const float diff = (1.0f - met) * mixd * (1.0f / kPi);
+  // specular geometry and its derivatives in (roughness, anisotropic)
+  DualN<2> ax, ay;
+  disney_widths(dvar<2>(rho, 0), dvar<2>(m[8], 1), ax, ay);
+  const DualN<2> S = ggx_geo(ax, ay, G);
+  // clearcoat and its derivative in the gloss
+  const DualN<1> Dc = gtr1(G.ch, 0.1f - 0.099f * dvar<1>(m[12], 0));
+  const float cF = (0.04f + 0.96f * G.Sd) * coat_masking(G);
+  const float oSd = 1.0f - G.Sd;
+  float Qb = 0.0f, Qs = 0.0f, QF = 0.0f, Qt = 0.0f, Qsh = 0.0f, Qspt = 0.0f, Qmet = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float tc = 1.0f + spt * (tint[c] - 1.0f);
+    const float sc = 1.0f + sht * (tint[c] - 1.0f);
+    const float C0 = (1.0f - met) * 0.08f * spc * tc + met * m[c];
+    const float Fs = C0 * oSd + G.Sd;
+    Qb += q[c] * m[c];
+    Qs += q[c];
+    QF += q[c] * Fs;
+    Qt += q[c] * tint[c];
+    Qsh += q[c] * sc;
+    Qspt += q[c] * tc;
+    Qmet += q[c] * (-m[c] * mixd * (1.0f / kPi) - shn * G.Sd * sc + oSd * S.v * (m[c] - 0.08f * spc * tc));
+  }
+  // base colour: its own diffuse and metallic Fresnel terms, and the tint of
+  // sheen and specular through d tint_c / d base_k = (delta_ck - tint_c w_k) / lb
+  const float K = (1.0f - met) * (shn * G.Sd * sht + oSd * S.v * 0.08f * spc * spt);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    g[k] = q[k] * (diff + oSd * S.v * met) + (tinted ? K * (q[k] - lw[k] * Qt) / lb : 0.0f);
+  g[3] = Qb * (1.0f - met) * (fss - fd) * (1.0f / kPi);
+  g[4] = Qmet;
+  g[5] = oSd * S.v * (1.0f - met) * 0.08f * Qspt;
+  g[6] = oSd * S.v * (1.0f - met) * 0.08f * spc * (Qt - Qs);
+  g[7] = Qb * (1.0f - met) * ((1.0f - sub) * dfd + sub * dfss) * (1.0f / kPi) + QF * S.d[0];
+  g[8] = QF * S.d[1];
+  g[9] = (1.0f - met) * G.Sd * Qsh;
+  g[10] = (1.0f - met) * shn * G.Sd * (Qt - Qs);
+  g[11] = Qs * 0.25f * Dc.v * cF;
+  g[12] = Qs * 0.25f * cc * cF * Dc.d[0];
+  return true;
 }
 
 // Per-segment sampling data (built from the sampling parameters):
