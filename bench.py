@@ -245,6 +245,8 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     w = WORKLOAD
     sc = make_scene(rank)
+    if args.per_triangle:
+        sc = scenes.per_triangle(sc)
     sc.cameras = sc.cameras[:w["views"]]
     opts = TraceOptions(spp_r=w["spp_r"], spp_d=w["spp_d"], max_depth=w["max_depth"], nee=True, mis=True)
     adam = AdamOptions()
@@ -703,6 +705,8 @@ def main():
     ap.add_argument("--sweep", default=None, choices=["paths", "split", "batch", "mis", "bounces", "all"],
                     help="optimiser ablation curves (paths per pixel, sample split, batch size, MIS, bounces)")
     ap.add_argument("--sweep-seconds", type=float, default=8.0, help="optimisation time per sweep setting")
+    ap.add_argument("--per-triangle", action="store_true",
+                    help="every triangle its own segment (App. E refinement): gradient scatter over T segments")
     ap.add_argument("--material", default="lambert_ggx", choices=["lambert_ggx", "disney"],
                     help="disney: time the Disney material model's step (megakernel) on the workload")
     ap.add_argument("--monitor-every", type=int, default=250)
@@ -722,6 +726,9 @@ def main():
         WORKLOAD["spp_r"] = WORKLOAD["spp_d"] = args.spp
         WORKLOAD["workload"] += f"_spp{args.spp}"
         WORKLOAD["target_spp"] = min(WORKLOAD["target_spp"], 64)
+    if args.per_triangle:
+        WORKLOAD["workload"] += "_per_triangle"
+        WORKLOAD["segments"] = WORKLOAD["triangles"]
     if args.cache:
         WORKLOAD["workload"] += f"_cache_b{args.cache}"
         WORKLOAD["cache"] = dict(b_term=args.cache, train_spp=max(1, WORKLOAD["spp_r"] // 16), train_steps=4,

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "ipt_device.cuh"
 #include "ipt_internal.h"
 #include "ipt_path.cuh"
@@ -344,10 +346,11 @@ __global__ void k_finalize(const double* loss_partials, int n_partials, double* 
 // followed by that member's tables for the next iteration.
 __device__ __forceinline__ void adam_range(float* params, float* m, float* v, const uint8_t* free_mask,
                                            const double* grad_acc, const float* grad_f, uint32_t begin,
-                                           uint32_t end, uint32_t g_begin, const AdamHost& a, int step) {
+                                           uint32_t end, uint32_t g_begin, const AdamHost& a, int step,
+                                           uint32_t lane0, uint32_t lanes) {
   const float bc1 = 1.0f - powf(a.beta1, (float)step);
   const float bc2 = 1.0f - powf(a.beta2, (float)step);
-  for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+  for (uint32_t i = begin + lane0; i < end; i += lanes) {
     if (free_mask && !free_mask[i]) continue;
     const uint32_t j = i % 10u;
     float g = grad_f ? grad_f[i] : (float)grad_acc[g_begin + (i - begin)];
@@ -375,7 +378,7 @@ __global__ void k_adam_batch(const BatchMember* members, float* params, float* m
   if (!mb.active) return;
   const int step = (int)*iter_dev + 1;
   adam_range(params, m, v, free_mask, grad_acc, nullptr, 10u * mb.seg_offset, 10u * (mb.seg_offset + mb.n_seg),
-             10u * mb.grad_offset, a, step);
+             10u * mb.grad_offset, a, step, threadIdx.x, blockDim.x);
   __syncthreads();
   const float* p = params + 10u * mb.seg_offset;
   build_tables(p, p, mb.n_seg, mb.es, mb.seg_area, mb.tab);
@@ -415,10 +418,108 @@ __global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_ma
                        const double* grad_acc, const float* grad_f, int* step_dev, AdamHost a, uint32_t S,
                        float es, const double* seg_area, SegBuffers t) {
   const int step = *step_dev + 1;
-  adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, 0u, a, step);
+  adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, 0u, a, step, threadIdx.x, blockDim.x);
   __syncthreads();
   if (threadIdx.x == 0) *step_dev = step;
   build_tables(params, params, S, es, seg_area, t);
+}
+
+// Scenes with many segments (per-triangle parameters): Adam over a grid, the
+// per-segment tables over a grid, and the light CDF by one block that keeps
+// the sequential FP64 summation order of build_tables.  The terms of
+// non-emitting segments are exact zeros, so the running sum changes only at
+// emitters: those are added in order by one thread, and every other entry
+// takes the running value of the last emitter before it.
+constexpr uint32_t kWideSegments = 4096;
+
+__global__ void k_adam_wide(float* params, float* m, float* v, const uint8_t* free_mask, const double* grad_acc,
+                            const float* grad_f, const int* step_dev, AdamHost a, uint32_t S) {
+  const int step = *step_dev + 1;
+  adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, 0u, a, step,
+             blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void k_tables_seg(const float* params, const float* sparams, uint32_t S, float es, SegBuffers t) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    const float* p = params + 10 * s;
+    const float* q = sparams + 10 * s;
+    const float r = p[6];
+    t.mat_a[s] = make_float4(p[0], p[1], p[2], r);
+    t.mat_b[s] = make_float4(p[3], p[4], p[5], fmaxf(r * r, 1e-4f));
+    t.emis[s] = make_float4(es * p[7], es * p[8], es * p[9], 0.0f);
+    const double ld = lum_d(q[0], q[1], q[2]);
+    const double ls = lum_d(q[3], q[4], q[5]);
+    const double sum = __dadd_rn(ld, ls);
+    t.pspec[s] = sum > 0.0 ? __ddiv_rn(ls, sum) : 0.0;
+    double le = lum_d(q[7], q[8], q[9]);
+    if (!(le > 0.0)) le = 0.0;
+    t.lum[s] = le;
+  }
+}
+
+// One block of 1024 threads; bumps *step_dev when given (after Adam).
+__global__ void __launch_bounds__(1024) k_tables_cdf(uint32_t S, const double* seg_area, SegBuffers t,
+                                                     int* step_dev) {
+  __shared__ double term[1024];
+  __shared__ unsigned nz[32];
+  __shared__ double warp_end[32];
+  __shared__ double carry, start;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+  if (tid == 0) carry = 0.0;
+  for (uint32_t base = 0; base < S; base += 1024u) {
+    const uint32_t i = base + tid;
+    if (tid == 0) start = carry;
+    const double a = i < S ? __dmul_rn(t.lum[i], seg_area[i]) : 0.0;
+    term[tid] = a;
+    const unsigned m = __ballot_sync(0xffffffffu, a != 0.0);
+    if (lane == 0) nz[wid] = m;
+    __syncthreads();
+    if (tid == 0) {
+      double acc = carry;
+      for (int w = 0; w < 32; ++w) {
+        for (unsigned b = nz[w]; b; b &= b - 1u) {
+          const int j = w * 32 + __ffs(b) - 1;
+          acc = __dadd_rn(acc, term[j]);
+          term[j] = acc;
+        }
+        warp_end[w] = acc;
+      }
+      carry = acc;
+    }
+    __syncthreads();
+    // running value after the last emitter at or before this entry
+    const unsigned upto = nz[wid] & (0xffffffffu >> (31u - lane));
+    double c;
+    if (upto)
+      c = term[wid * 32 + 31 - __clz(upto)];
+    else
+      c = wid > 0 ? warp_end[wid - 1] : start;
+    if (i < S) t.cdf[i] = c;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *t.W = carry;
+    if (step_dev) *step_dev += 1;
+  }
+}
+
+__global__ void k_tables_samp(const float* sparams, uint32_t S, SegBuffers t) {
+  const double W = *t.W;
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    const float rs = sparams[10 * s + 6];
+    const double le = t.lum[s];
+    t.samp[s] = make_float4(fmaxf(rs * rs, 1e-4f), (float)t.pspec[s],
+                            (W > 0.0 && le > 0.0) ? (float)(le / W) : 0.0f, 0.0f);
+  }
+}
+
+static cudaError_t launch_tables_wide(const SceneBuffers& s, const SegBuffers& t, const float* params,
+                                      const float* sparams, int* step_dev, cudaStream_t st) {
+  const int grid = (int)std::min<uint32_t>((s.n_seg + 255u) / 256u, 1024u);
+  k_tables_seg<<<grid, 256, 0, st>>>(params, sparams, s.n_seg, s.emission_scale, t);
+  k_tables_cdf<<<1, 1024, 0, st>>>(s.n_seg, s.seg_area, t, step_dev);
+  k_tables_samp<<<grid, 256, 0, st>>>(sparams, s.n_seg, t);
+  return cudaGetLastError();
 }
 
 
@@ -486,6 +587,7 @@ static int grid_for(uint64_t n_tasks_warps, int blocks_cap) {
 
 cudaError_t launch_prepare(const SceneBuffers& s, const SegBuffers& t, const float* params,
                            const float* sparams, cudaStream_t st) {
+  if (s.n_seg > kWideSegments) return launch_tables_wide(s, t, params, sparams ? sparams : params, nullptr, st);
   k_prepare<<<1, 256, 0, st>>>(params, sparams ? sparams : params, s.n_seg, s.emission_scale, s.seg_area, t);
   return cudaGetLastError();
 }
@@ -554,6 +656,11 @@ cudaError_t launch_finalize(const double* loss_partials, int n_partials, double*
 cudaError_t launch_adam(const SceneBuffers& s, const SegBuffers& t, float* params, float* m,
                         float* v, const uint8_t* free_mask, const double* grad_acc,
                         const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st) {
+  if (s.n_seg > kWideSegments) {
+    const int grid = (int)std::min<uint32_t>((10u * s.n_seg + 255u) / 256u, 2048u);
+    k_adam_wide<<<grid, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg);
+    return launch_tables_wide(s, t, params, params, step_dev, st);
+  }
   k_adam<<<1, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg,
                             s.emission_scale, s.seg_area, t);
   return cudaGetLastError();

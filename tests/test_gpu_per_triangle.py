@@ -110,3 +110,34 @@ def test_coarse_to_fine_lowers_the_image_error(built):
     e_obj = np.linalg.norm(per_object - truth) / np.linalg.norm(truth)
     e_tri = np.linalg.norm(per_triangle - truth) / np.linalg.norm(truth)
     assert e_tri < 0.6 * e_obj, (e_obj, e_tri)
+
+
+@pytest.mark.parametrize("integrator", ["wavefront", "megakernel"])
+def test_wide_scene_adam_and_tables_match_oracle(built, integrator):
+    """Above 4096 segments Adam runs over a grid and the light CDF is built by
+    the emitter-only sequential sum: the step equals the oracle's Adam, and
+    the image rendered with the new tables (light selection included, many
+    emitting triangles of different strength) equals the oracle's."""
+    sc = scenes.per_triangle(scenes.cornell_textured(1000, 32, 32, 24))
+    assert sc.n_segments > 4096
+    rng = np.random.default_rng(9)
+    p0 = sc.gt_params.astype(np.float64).copy()
+    p0[:, 0:3] = rng.uniform(0.2, 0.8, (sc.n_segments, 3))
+    emit = rng.random(sc.n_segments) < 0.05  # scattered emitters with their own strengths
+    p0[emit, 7:10] = rng.uniform(0.0, 0.02, (int(emit.sum()), 3))
+    g = rng.normal(scale=0.01, size=p0.shape)
+    tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator)
+    tr.set_params(p0.astype(np.float32))
+    tr.adam_step(AdamOptions(), torch.from_numpy(g.astype(np.float32)).cuda())
+    newp = tr.get_params()
+    ref, _, _ = O.adam_update(p0.astype(np.float32).astype(np.float64), g.astype(np.float32).astype(np.float64),
+                              np.zeros_like(g), np.zeros_like(g), 1)
+    assert np.max(np.abs(newp - ref)) < 1e-6
+    opts = TraceOptions(max_depth=3)
+    img = tr.render(opts, view=0, set_id=0, spp=16, iteration=3).cpu().numpy()
+    osc = O.OracleScene(sc)
+    oref, _ = osc.render(newp.astype(np.float64), spp=16, max_depth=3, set_id=0, iteration=3, seed=SEED)
+    r = float(np.linalg.norm(img - oref) / np.linalg.norm(oref))
+    assert r <= 1e-3, r
+    tr.close()
