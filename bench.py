@@ -582,8 +582,9 @@ def run_time_to_error(args):
 
 
 def run_disney(args):
-    """fwd+adjoint Mpaths/s of the Disney material model (Sec. 4.1, megakernel)
-    on the benchmark room with random Disney materials: one step = loss,
+    """fwd+adjoint Mpaths/s of the Disney material model (Sec. 4.1; wavefront,
+    or the megakernel with --integrator megakernel) on the benchmark room with
+    random Disney materials: one step = loss,
     gradient and Adam over all views; per-kernel device times from the
     library's own events (a second, identical timing pass)."""
     import torch
@@ -599,8 +600,13 @@ def run_disney(args):
     opts = TraceOptions(spp_r=w["spp_r"], spp_d=w["spp_d"], max_depth=w["max_depth"])
     adam = AdamOptions()
     res = {}
+    integ = "megakernel" if args.integrator == "megakernel" else "wavefront"
     for timing in (False, True):
         tr = Tracer(sc, seed=1903, flags=L.IPT_FLAG_KERNEL_TIMING if timing else 0)
+        if integ == "wavefront":  # the configuration the autotuner picks for this room
+            tr.configure("wavefront", wavefront_slots=1 << 21, trace_steps=8, bvh_width=4)
+        else:
+            tr.configure("megakernel")
         tr.disney_set_params(truth)
         tr.set_targets(tr.disney_render(TraceOptions(max_depth=w["max_depth"]), set_id=L.IPT_SET_TARGET, spp=16))
         p0 = truth.copy()
@@ -636,7 +642,7 @@ def run_disney(args):
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w["workload"] + "_disney", "views": w["views"], "width": w["width"],
                       "height": w["height"], "spp_r": w["spp_r"], "spp_d": w["spp_d"],
-                      "max_depth": w["max_depth"], "integrator": "megakernel",
+                      "max_depth": w["max_depth"], "integrator": integ,
                       "l2": "256 MiB flush between timed steps (outside the step events)"},
            "kernel_ms_per_step": res["kernel_ms_per_step"], "clocks": res["clocks"]}
     print(json.dumps(out), flush=True)

@@ -531,8 +531,8 @@ ipt_status ipt_checkpoint_save(ipt_ctx* ctx, int32_t scene, void* buf, size_t* n
 ipt_status ipt_checkpoint_load(ipt_ctx* ctx, int32_t scene, const void* buf, size_t n);
 
 /* Disney material model (Sec. 4.1: a base colour and ten further values,
- * all in [0, 1]; Burley 2012 with linear base colour), on the megakernel
- * integrator whatever ipt_config_set selects.  Its parameter block per
+ * all in [0, 1]; Burley 2012 with linear base colour), on the integrator
+ * ipt_config_set selects (both build the same paths).  Its parameter block per
  * segment is 16 floats: base colour r, g, b (0-2), subsurface (3), metallic
  * (4), specular (5), specular tint (6), roughness (7), anisotropic (8), sheen
  * (9), sheen tint (10), clearcoat (11), clearcoat gloss (12), emission r, g, b

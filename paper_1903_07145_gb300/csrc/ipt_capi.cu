@@ -186,6 +186,7 @@ struct ipt_ctx {
   ipt::WfBuffers wf;
   std::vector<void*> wf_owned;
   bool wf_adjoint = false;
+  bool wf_disney = false;          // the adjoint buffers include the Disney model's records
   ipt::WfScene* wf_tab = nullptr;  // one-entry scene table of single-scene launches
   std::vector<Batch*> batches;
   cudaStream_t cap_stream = nullptr;  // stream the batch graphs are captured on
@@ -390,17 +391,20 @@ void wf_release(ipt_ctx* c) {
   c->wf_owned.clear();
   c->wf = ipt::WfBuffers();
   c->wf_adjoint = false;
+  c->wf_disney = false;
 }
 
 // Wavefront buffers for `cap` slots (plus the adjoint's carry when asked),
 // allocated on first use and kept by the context.
-ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params) {
+ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney = false) {
   const uint32_t cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
-  const bool fits = ctx->wf.cap == cap && (!adjoint || (ctx->wf_adjoint && ctx->wf.blk_params >= n_params));
+  const bool fits = ctx->wf.cap == cap && (!adjoint || (ctx->wf_adjoint && ctx->wf.blk_params >= n_params)) &&
+                    (!disney || ctx->wf_disney);
   if (fits) return IPT_OK;
   IPT_CK(cudaStreamSynchronize(ctx->stream));
   const uint32_t keep_params = std::max(n_params, ctx->wf.blk_params);
   const bool want_adj = adjoint || ctx->wf_adjoint;
+  const bool want_disney = want_adj && (disney || ctx->wf_disney);
   wf_release(ctx);
   ipt::WfBuffers& w = ctx->wf;
   cudaError_t e = cudaSuccess;
@@ -434,6 +438,11 @@ ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params) {
     A(&w.sh_ge, cap);
     A(&w.sh_gm, cap);
     A(&w.sh_n, cap);
+    if (want_disney) {
+      A(&w.aWi, (size_t)ipt::kMaxAdjointDepth * cap);
+      A(&w.aWo, (size_t)ipt::kMaxAdjointDepth * cap);
+      A(&w.sh_dv, 4 * (size_t)cap);
+    }
     // block-private rows for chunks whose accumulators fit in shared memory;
     // a wider chunk accumulates in one row in global memory
     const size_t shared_params = std::min<size_t>(keep_params, 10u * ipt::wf_max_segments());
@@ -446,6 +455,7 @@ ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params) {
   w.cap = cap;
   w.blk_params = want_adj ? keep_params : 0;
   ctx->wf_adjoint = want_adj;
+  ctx->wf_disney = want_disney;
   return IPT_OK;
 }
 
@@ -2164,6 +2174,16 @@ ipt_status get_disney(ipt_ctx* ctx, int32_t scene, DeviceScene** s, DisneyState*
   return IPT_OK;
 }
 
+// Scene-table entry of a Disney-model launch over scene pixels [begin, begin + n).
+ipt::WfScene disney_entry(const ipt_ctx* ctx, int32_t scene, const DeviceScene* s, const DisneyState* d,
+                          uint32_t begin, uint32_t n) {
+  ipt::WfScene e = wf_entry(ctx, scene, s, begin, n);
+  e.t = ipt::seg_dev(d->tab);
+  e.dis = ipt::DisneyDev{d->dt.mat, d->dt.lobe, d->dt.samp};
+  e.n_all = (uint32_t)s->n_pix;
+  return e;
+}
+
 ipt_status disney_tables(ipt_ctx* ctx, DeviceScene* s, DisneyState* d, const float* sparams) {
   if (!sparams && d->tab_is_ctx) return IPT_OK;
   Timed tm(ctx, IPT_KERNEL_PREPARE);
@@ -2230,11 +2250,24 @@ ipt_status ipt_disney_render(ipt_ctx* ctx, int32_t scene, int32_t view, const ip
   if ((st = disney_tables(ctx, s, d, sampling_params)) != IPT_OK) return st;
   const uint32_t begin = view < 0 ? 0u : s->views[view].offset;
   const uint32_t n = view < 0 ? (uint32_t)s->n_pix : s->views[view].w * s->views[view].h;
+  const ipt::TraceParams tp = trace_params(ctx, scene, opts, set, spp, iteration);
+  if (use_wavefront(ctx, spp)) {
+    if ((st = ensure_wf(ctx, false, kDisneyValues * s->n_seg)) != IPT_OK) return st;
+    ipt::WfScene e = disney_entry(ctx, scene, s, d, begin, n);
+    e.img = rgb_out;
+    e.msq = msq_out;
+    if ((st = upload_entry(ctx, e)) != IPT_OK) return st;
+    StageTimer timer{ctx};
+    const ipt::WfHook hook{stage_begin, stage_end, &timer};
+    IPT_CK(ipt::wf_forward(ctx->L, ctx->wf_tab, std::vector<ipt::WfScene>{e}, tp, 0, nullptr, ctx->wf, nullptr,
+                           ctx->err_dev, ctx->stream, (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr,
+                           nullptr, true));
+    return IPT_OK;
+  }
   Timed tm(ctx, IPT_KERNEL_FORWARD);
   IPT_CK(ipt::launch_disney_forward(ctx->L, buffers(ctx, s), d->tab, d->dt, s->views_dev,
-                                    (uint32_t)s->views.size(), begin, n,
-                                    trace_params(ctx, scene, opts, set, spp, iteration), rgb_out, msq_out, nullptr,
-                                    nullptr, nullptr, 0.f, 0, ctx->err_dev, ctx->stream));
+                                    (uint32_t)s->views.size(), begin, n, tp, rgb_out, msq_out, nullptr, nullptr,
+                                    nullptr, 0.f, 0, ctx->err_dev, ctx->stream));
   return IPT_OK;
 }
 
@@ -2256,30 +2289,49 @@ static ipt_status disney_loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScen
   const uint32_t* pick = B ? s->pick : nullptr;
   const float g_scale = (float)(1.0 / (3.0 * (double)n));
   const ipt::SceneBuffers sb = buffers(ctx, s);
-  ipt::TraceParams tpr = trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration);
-  tpr.pick = pick;
-  {
-    Timed tm(ctx, IPT_KERNEL_FORWARD);
-    IPT_CK(ipt::launch_disney_forward(ctx->L, sb, d->tab, d->dt, s->views_dev, (uint32_t)s->views.size(), 0, n, tpr,
-                                      nullptr, nullptr, s->target, g_buf, s->loss_partials, g_scale, opts->loss,
-                                      ctx->err_dev, ctx->stream));
-  }
   const uint32_t np = kDisneyValues * s->n_seg;
-  IPT_CK(cudaMemsetAsync(d->grad_acc, 0, np * sizeof(double), ctx->stream));
+  ipt::TraceParams tpr = trace_params(ctx, scene, opts, IPT_SET_RESIDUAL, opts->spp_r, iteration);
   const uint32_t set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
   ipt::TraceParams tpd = trace_params(ctx, scene, opts, set, opts->spp_d, iteration);
   if (opts->gradcheck_same_set) tpd.sample_stride = opts->spp_r;
-  tpd.pick = pick;
-  {
-    Timed tm(ctx, IPT_KERNEL_ADJOINT);
-    IPT_CK(ipt::launch_disney_adjoint(ctx->L, sb, d->tab, d->dt, s->views_dev, (uint32_t)s->views.size(), 0, n, tpd,
-                                      g_buf, d->grad_acc, d->gacc, ctx->err_dev, ctx->stream));
+  if (use_wavefront(ctx, std::max(opts->spp_r, opts->spp_d))) {
+    StageTimer timer{ctx};
+    const ipt::WfHook hook{stage_begin, stage_end, &timer};
+    const ipt::WfHook* hp = (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr;
+    if ((st = ensure_wf(ctx, true, np, true)) != IPT_OK) return st;
+    ipt::WfScene e = disney_entry(ctx, scene, s, d, 0u, n);
+    e.pick = const_cast<uint32_t*>(pick);
+    e.g_scale = g_scale;
+    e.target = s->target;
+    e.g_img = g_buf;
+    if ((st = upload_entry(ctx, e)) != IPT_OK) return st;
+    IPT_CK(ipt::wf_forward(ctx->L, ctx->wf_tab, std::vector<ipt::WfScene>{e}, tpr, opts->loss, nullptr, ctx->wf,
+                           s->loss_partials, ctx->err_dev, ctx->stream, hp, nullptr, true));
+    IPT_CK(cudaMemsetAsync(d->grad_acc, 0, np * sizeof(double), ctx->stream));
+    IPT_CK(ipt::wf_adjoint(ctx->L, ctx->wf_tab, std::vector<ipt::WfScene>{e}, tpd, nullptr, ctx->wf, d->grad_acc,
+                           ctx->err_dev, ctx->stream, hp, nullptr, true));
+  } else {
+    tpr.pick = pick;
+    tpd.pick = pick;
+    {
+      Timed tm(ctx, IPT_KERNEL_FORWARD);
+      IPT_CK(ipt::launch_disney_forward(ctx->L, sb, d->tab, d->dt, s->views_dev, (uint32_t)s->views.size(), 0, n,
+                                        tpr, nullptr, nullptr, s->target, g_buf, s->loss_partials, g_scale,
+                                        opts->loss, ctx->err_dev, ctx->stream));
+    }
+    IPT_CK(cudaMemsetAsync(d->grad_acc, 0, np * sizeof(double), ctx->stream));
+    {
+      Timed tm(ctx, IPT_KERNEL_ADJOINT);
+      IPT_CK(ipt::launch_disney_adjoint(ctx->L, sb, d->tab, d->dt, s->views_dev, (uint32_t)s->views.size(), 0, n,
+                                        tpd, g_buf, d->grad_acc, d->gacc, ctx->err_dev, ctx->stream));
+    }
   }
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, d->grad_acc,
                               grad_out, np, ctx->stream));
   return IPT_OK;
 }
+
 
 ipt_status ipt_disney_loss_grad(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint64_t iteration,
                                 double* loss_out, float* grad_out) {

@@ -112,6 +112,14 @@ struct SegDev {
   const double* W;       // total; 0 disables light sampling
 };
 
+// Disney material model tables (see ipt_disney.cuh); null pointers when a
+// scene traces with Lambert + GGX.
+struct DisneyDev {
+  const float4* mat;    // 4 per segment: the 13 material values, then zeros
+  const double2* lobe;  // cumulative lobe probabilities (P_d, P_d + P_s), FP64
+  const float4* samp;   // 2 per segment: (a_x, a_y, a_c, 0), (P_d, P_s, P_c, 0)
+};
+
 struct ViewDev {
   float m[12];      // cam_to_world, row-major 3x4
   float tx, ty;     // tan(fov/2) * aspect, tan(fov/2)

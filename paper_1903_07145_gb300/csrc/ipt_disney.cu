@@ -100,20 +100,6 @@ __global__ void k_disney_adam(float* params, float* m, float* v, const uint8_t* 
   disney_tables_body(params, params, S, es, seg_area, t, d);
 }
 
-// Tangent frame of the hit triangle at the oriented shading normal.
-__device__ __forceinline__ void hit_frame(const SceneDev& s, int tri, float3 ns, float3& X, float3& Y) {
-  const float3 p0 = xyz(__ldg(&s.tris[3 * tri + 0]));
-  const float3 p1 = xyz(__ldg(&s.tris[3 * tri + 1]));
-  tangent_frame(p1 - p0, ns, X, Y);
-}
-
-__device__ __forceinline__ float3 disney_eval(const float (&m)[kDisneyMat], float3 n, float3 X, float3 Y, float3 wi,
-                                              float3 wo) {
-  float f[3];
-  disney_f(m, n, X, Y, wi, wo, f);
-  return f3(f[0], f[1], f[2]);
-}
-
 // acc[j] += sum_c q_c d f_c(wi, wo) / d m_j for the 13 material values.
 __device__ __forceinline__ void disney_grad(const float (&m)[kDisneyMat], float3 n, float3 X, float3 Y, float3 wi,
                                             float3 wo, float3 q, float* acc) {

@@ -370,11 +370,6 @@ __device__ __forceinline__ bool disney_vjp(const float (&m)[kDisneyMat], float3 
 // Per-segment sampling data (built from the sampling parameters):
 //   lobe: FP64 cumulative lobe probabilities (P_d, P_d + P_s) for the lobe
 //         decision; samp: (a_x, a_y, a_c, -) and (P_d, P_s, P_c, -) in FP32.
-struct DisneyDev {
-  const float4* mat;    // 4 per segment: material values 0-12, then 0
-  const double2* lobe;
-  const float4* samp;   // 2 per segment
-};
 
 __device__ __forceinline__ void load_disney(const DisneyDev& D, int seg, float (&m)[kDisneyMat]) {
   const float4 a = __ldg(&D.mat[4 * seg]), b = __ldg(&D.mat[4 * seg + 1]);
@@ -447,6 +442,20 @@ __device__ __forceinline__ float3 disney_sample(const DisneyDev& D, int seg, flo
     hw = b1 * (st * cphi) + b2 * (st * sphi) + n * ct;
   }
   return hw * (2.0f * dot(wi, hw)) - wi;
+}
+
+// Tangent frame of the hit triangle at the oriented shading normal.
+__device__ __forceinline__ void hit_frame(const SceneDev& s, int tri, float3 ns, float3& X, float3& Y) {
+  const float3 p0 = xyz(__ldg(&s.tris[3 * tri + 0]));
+  const float3 p1 = xyz(__ldg(&s.tris[3 * tri + 1]));
+  tangent_frame(p1 - p0, ns, X, Y);
+}
+
+__device__ __forceinline__ float3 disney_eval(const float (&m)[kDisneyMat], float3 n, float3 X, float3 Y, float3 wi,
+                                              float3 wo) {
+  float f[3];
+  disney_f(m, n, X, Y, wi, wo, f);
+  return f3(f[0], f[1], f[2]);
 }
 
 }  // namespace ipt

@@ -106,6 +106,9 @@ struct WfBuffers {
   float2* aR = nullptr;
   uint32_t* nv = nullptr;
   float4 *sh_ge = nullptr, *sh_gm = nullptr, *sh_n = nullptr;
+  // Disney model adjoint: per-vertex directions and hit, and the shadow
+  // records' material derivatives (4 float4 = 13 values per record)
+  float4 *aWi = nullptr, *aWo = nullptr, *sh_dv = nullptr;
   float* blk = nullptr;
   uint32_t cap = 0;
   uint32_t blk_params = 0;  // S x 10 capacity of each block row

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "ipt_device.cuh"
+#include "ipt_disney.cuh"
 #include "ipt_internal.h"
 #include "ipt_path.cuh"
 #include "ipt_wavefront.h"
@@ -64,6 +65,11 @@ struct WfDev {
   float4* sh_ge;  // g beta f k es (emission gradient of the light segment)
   float4* sh_gm;  // g beta Le k, w = specular factor
   float4* sh_n;   // f Le k (the contribution without beta), w = d spec / d r
+  // Disney model: aT.w = cos/pdf, aR = (u, segment); aWi = (wi, triangle),
+  // aWo = (wo, v); sh_dv = the vertex material derivative of a shadow record
+  float4* aWi;
+  float4* aWo;
+  float4* sh_dv;
   float* blk;     // per-block rows of the chunk's partial gradients
   uint32_t cap;
 };
@@ -429,6 +435,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev
 // The shading and adjoint stages ask for 8 resident blocks of 128 threads per
 // SM (at most 64 registers, a few bytes spilled): they wait on scattered
 // path-state loads, and the extra warps hide more of that latency.
+// kD: the Disney material model (sampler, BRDF and NEE pdf) in place of
+// Lambert + GGX; the rest of the stage is shared.
+template <bool kD>
 __global__ void __launch_bounds__(kWfThreads, 8) wf_shade_fwd(const WfScene* tab, WfParams lp, uint32_t p0,
                                                            WfDev w, int cur) {
   if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;  // closest fetch counter of the next vertex
@@ -484,25 +493,50 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_shade_fwd(const WfScene* tab
         path_id = pid * lp.spp + smp;
         const PathRng rng = path_rng(e, pid, smp, si);
         const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
-        const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
-        const float4 sa = __ldg(&e.t.samp[v.seg]);
-        if (light_on && (!lp.cache_record || k >= lp.cache_k)) {
-          ne = nee_prepare(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis, sa.y, sa.x);
-          if (ne.valid) {
-            const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
-            shc = beta * bv.f * xyz(__ldg(&e.t.emis[ne.seg])) * ne.k;
-            shadow = true;
+        if constexpr (kD) {
+          float3 X, Y;
+          hit_frame(e.s, tri, v.ns, X, Y);
+          float m[kDisneyMat];
+          load_disney(e.dis, v.seg, m);
+          if (light_on) {
+            ne = nee_prepare_with(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis,
+                                  [&](float3 wl) { return disney_pdf(e.dis, v.seg, v.ns, X, Y, v.wi, wl); });
+            if (ne.valid) {
+              shc = beta * disney_eval(m, v.ns, X, Y, v.wi, ne.wl) * xyz(__ldg(&e.t.emis[ne.seg])) * ne.k;
+              shadow = true;
+            }
           }
-        }
-        if (dot(v.wi, v.ns) > 0.0f) {
-          wo = bsdf_sample(__ldg(&e.t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
-          pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
-          const float co = dot(wo, v.ns);
-          if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
-            const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
-            beta = beta * bv.f * (co / pdf);
-            org = v.x + v.ng * e.s.eps;
-            cont = true;
+          if (dot(v.wi, v.ns) > 0.0f) {
+            wo = disney_sample(e.dis, v.seg, v.ns, X, Y, v.wi, ua.x, ua.y, ua.z);
+            pdf = disney_pdf(e.dis, v.seg, v.ns, X, Y, v.wi, wo);
+            const float co = dot(wo, v.ns);
+            if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
+              beta = beta * disney_eval(m, v.ns, X, Y, v.wi, wo) * (co / pdf);
+              org = v.x + v.ng * e.s.eps;
+              cont = true;
+            }
+          }
+        } else {
+          const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
+          const float4 sa = __ldg(&e.t.samp[v.seg]);
+          if (light_on && (!lp.cache_record || k >= lp.cache_k)) {
+            ne = nee_prepare(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis, sa.y, sa.x);
+            if (ne.valid) {
+              const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
+              shc = beta * bv.f * xyz(__ldg(&e.t.emis[ne.seg])) * ne.k;
+              shadow = true;
+            }
+          }
+          if (dot(v.wi, v.ns) > 0.0f) {
+            wo = bsdf_sample(__ldg(&e.t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
+            pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
+            const float co = dot(wo, v.ns);
+            if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
+              const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
+              beta = beta * bv.f * (co / pdf);
+              org = v.x + v.ng * e.s.eps;
+              cont = true;
+            }
           }
         }
       }
@@ -629,9 +663,47 @@ __device__ __forceinline__ float3 pixel_grad(const WfScene& e, uint32_t entry, f
   return f3(e.g_img[3 * entry], e.g_img[3 * entry + 1], e.g_img[3 * entry + 2]) * inv_spp;
 }
 
-// Continuation terms of a finished path: (dw_l / dtheta) . (g * U_l).
+// The same for the Disney model's 16 values per segment.
+__device__ __forceinline__ int acc_ix16(const WfScene& e, const WfParams& lp, int seg, int j) {
+  return kDisneyStride * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
+}
+
+__device__ __forceinline__ void scatter_disney(float* sacc, int base, const float (&g)[kDisneyMat]) {
+#pragma unroll
+  for (int j = 0; j < kDisneyMat; ++j)
+    if (g[j] != 0.0f) atomicAdd(&sacc[base + j], g[j]);
+}
+
+// Continuation terms of a finished path: (dw_l / dtheta) . (g * U_l).  The
+// Disney model rebuilds vertex l (shading normal, tangent frame) from its
+// stored triangle, barycentrics and directions and contracts the BRDF
+// Jacobian there with g * U_l * cos/pdf.
+template <bool kD>
 __device__ __forceinline__ void finish_path(const WfDev& w, const WfScene& e, const WfParams& lp, uint32_t slot,
                                             float3 gp, float* sacc) {
+  if constexpr (kD) {
+    const uint32_t nv = w.nv[slot];
+    for (uint32_t l = 0; l < nv; ++l) {
+      const size_t ix = (size_t)l * w.cap + slot;
+      const float4 T = w.aT[ix], U = w.aU[ix], Wi = w.aWi[ix], Wo = w.aWo[ix];
+      const float2 R = w.aR[ix];
+      const float3 q = gp * xyz(U) * T.w;
+      if (q.x == 0.0f && q.y == 0.0f && q.z == 0.0f) continue;
+      Hit h;
+      h.tri = __float_as_int(Wi.w);
+      h.t = 0.0f;
+      h.u = R.x;
+      h.v = Wo.w;
+      const Vtx v = make_vertex(e.s, h, -xyz(Wi), lp.profile);
+      float3 X, Y;
+      hit_frame(e.s, h.tri, v.ns, X, Y);
+      const int sg = __float_as_int(R.y);
+      float m[kDisneyMat], g[kDisneyMat];
+      load_disney(e.dis, sg, m);
+      if (disney_vjp(m, v.ns, X, Y, xyz(Wi), xyz(Wo), q, g)) scatter_disney(sacc, acc_ix16(e, lp, sg, 0), g);
+    }
+    return;
+  }
   const uint32_t nv = w.nv[slot];
   for (uint32_t l = 0; l < nv; ++l) {
     const size_t ix = (size_t)l * w.cap + slot;
@@ -660,12 +732,14 @@ __device__ __forceinline__ void add_to_carry(const WfDev& w, uint32_t slot, floa
 }
 
 // Stage A: emission at the vertex, its contribution to the carry, and the
-// next-event candidate.
+// next-event candidate (with, for the Disney model, the material derivative
+// of its term, added if the shadow ray finds the light).
+template <bool kD>
 __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
                                                        int cur) {
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
-  const uint32_t np = 10u * lp.seg_n;
+  const uint32_t np = (kD ? 16u : 10u) * lp.seg_n;
   if (!lp.gacc) acc_zero(sacc, np);
   const uint32_t n = w.cnt[cur];
   const uint32_t si = set_iter(lp);
@@ -686,11 +760,12 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
     NeeResult ne;
     float3 ge = f3(0.f, 0.f, 0.f), gm = f3(0.f, 0.f, 0.f), cn = f3(0.f, 0.f, 0.f);
     float spec = 0.0f, dsdr = 0.0f;
+    float gd[kDisneyMat];
     int vseg = 0;
     float4 cq = make_float4(0.f, 0.f, 0.f, 0.f);
     Vtx cv;
     if (tri < 0) {
-      finish_path(w, e, lp, slot, gp, sacc);
+      finish_path<kD>(w, e, lp, slot, gp, sacc);
       w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
     } else {
       const double W = *e.t.W;
@@ -709,11 +784,11 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
         if (wb > 0.0f) {
           const float f = wb * v.prof;
           add_to_carry(w, slot, xyz(__ldg(&e.t.emis[v.seg])) * f);
-          scatter3(sacc, acc_ix(e, lp, v.seg, 7), gp * beta * (f * e.es));
+          scatter3(sacc, kD ? acc_ix16(e, lp, v.seg, kDisneyMat) : acc_ix(e, lp, v.seg, 7), gp * beta * (f * e.es));
         }
       }
       if (k == lp.max_depth) {
-        finish_path(w, e, lp, slot, gp, sacc);
+        finish_path<kD>(w, e, lp, slot, gp, sacc);
         w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       } else if (k == lp.cache_k) {
         // the cache's prediction and its parameter derivative close the path
@@ -724,18 +799,36 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
       } else if (light_on) {
         const PathRng rng = path_rng(e, pid, smp, si);
         const float4 ua = rng.draw(k, 0), ub = rng.draw(k, 1);
-        const float4 sa = __ldg(&e.t.samp[v.seg]);
-        ne = nee_prepare(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis, sa.y, sa.x);
-        if (ne.valid) {
-          const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
-          const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
-          const float3 Le = xyz(__ldg(&e.t.emis[ne.seg]));
-          ge = gp * beta * bv.f * (ne.k * e.es);
-          gm = gp * beta * Le * ne.k;
-          cn = bv.f * Le * ne.k;
-          spec = bv.sp.s;
-          dsdr = bv.sp.ds_dr;
-          shadow = true;
+        if constexpr (kD) {
+          float3 X, Y;
+          hit_frame(e.s, tri, v.ns, X, Y);
+          ne = nee_prepare_with(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis,
+                                [&](float3 wl) { return disney_pdf(e.dis, v.seg, v.ns, X, Y, v.wi, wl); });
+          if (ne.valid) {
+            float m[kDisneyMat];
+            load_disney(e.dis, v.seg, m);
+            const float3 fv = disney_eval(m, v.ns, X, Y, v.wi, ne.wl);
+            const float3 Le = xyz(__ldg(&e.t.emis[ne.seg]));
+            ge = gp * beta * fv * (ne.k * e.es);
+            cn = fv * Le * ne.k;
+            if (!disney_vjp(m, v.ns, X, Y, v.wi, ne.wl, gp * beta * Le * ne.k, gd))
+              for (int j = 0; j < kDisneyMat; ++j) gd[j] = 0.0f;
+            shadow = true;
+          }
+        } else {
+          const float4 sa = __ldg(&e.t.samp[v.seg]);
+          ne = nee_prepare(e.s, e.t, v, ua, ub, W, lp.profile, lp.mis, sa.y, sa.x);
+          if (ne.valid) {
+            const float4 ma = __ldg(&e.t.mat_a[v.seg]), mb = __ldg(&e.t.mat_b[v.seg]);
+            const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, ne.wl);
+            const float3 Le = xyz(__ldg(&e.t.emis[ne.seg]));
+            ge = gp * beta * bv.f * (ne.k * e.es);
+            gm = gp * beta * Le * ne.k;
+            cn = bv.f * Le * ne.k;
+            spec = bv.sp.s;
+            dsdr = bv.sp.ds_dr;
+            shadow = true;
+          }
         }
       }
     }
@@ -756,6 +849,13 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
       w.sh_ge[sq] = make_float4(ge.x, ge.y, ge.z, 0.0f);
       w.sh_gm[sq] = make_float4(gm.x, gm.y, gm.z, spec);
       w.sh_n[sq] = make_float4(cn.x, cn.y, cn.z, dsdr);
+      if constexpr (kD) {
+        float4* dv = w.sh_dv + 4 * (size_t)sq;
+        dv[0] = make_float4(gd[0], gd[1], gd[2], gd[3]);
+        dv[1] = make_float4(gd[4], gd[5], gd[6], gd[7]);
+        dv[2] = make_float4(gd[8], gd[9], gd[10], gd[11]);
+        dv[3] = make_float4(gd[12], 0.0f, 0.0f, 0.0f);
+      }
     }
   }
   if (!lp.gacc) acc_flush(sacc, np, w.blk);
@@ -763,16 +863,27 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
 
 // Unoccluded next-event terms: light emission (Eq. 5), the vertex material
 // (Eq. 6 at this vertex) and the carry of the earlier vertices.
+template <bool kD>
 __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab, WfParams lp, WfDev w) {
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
-  const uint32_t np = 10u * lp.seg_n;
+  const uint32_t np = (kD ? 16u : 10u) * lp.seg_n;
   if (!lp.gacc) acc_zero(sacc, np);
   const uint32_t n = w.cnt[2];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (!w.sh_vis[i]) continue;
     const uint4 m = w.sh_meta[i];
     const WfScene& e = tab[state_scene(__float_as_uint(w.beta[m.x].w))];
+    if constexpr (kD) {
+      const float4 ge = w.sh_ge[i], cn = w.sh_n[i];
+      scatter3(sacc, acc_ix16(e, lp, (int)m.w, kDisneyMat), xyz(ge));
+      const float4* dv = w.sh_dv + 4 * (size_t)i;
+      const float4 d0 = dv[0], d1 = dv[1], d2 = dv[2], d3 = dv[3];
+      const float g[kDisneyMat] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w, d2.x, d2.y, d2.z, d2.w, d3.x};
+      scatter_disney(sacc, acc_ix16(e, lp, (int)m.z, 0), g);
+      add_to_carry(w, m.x, xyz(cn));
+      continue;
+    }
     const float4 ge = w.sh_ge[i], gm = w.sh_gm[i], cn = w.sh_n[i];
     scatter3(sacc, acc_ix(e, lp, (int)m.w, 7), xyz(ge));
     const float3 q = xyz(gm);
@@ -786,11 +897,12 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
 }
 
 // Stage B: BRDF sampling; the new vertex joins the carry.
+template <bool kD>
 __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, WfParams lp, uint32_t p0, WfDev w,
                                                        int cur) {
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
-  const uint32_t np = 10u * lp.seg_n;
+  const uint32_t np = (kD ? 16u : 10u) * lp.seg_n;
   if (!lp.gacc) acc_zero(sacc, np);
   if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;
   const uint32_t n = w.cnt[cur];
@@ -823,8 +935,41 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
       slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
       const PathRng rng = path_rng(e, pid, smp, si);
       const float4 ua = rng.draw(k, 0);
-      const float4 sa = __ldg(&e.t.samp[v.seg]);
-      if (dot(v.wi, v.ns) > 0.0f) {
+      if constexpr (kD) {
+        if (dot(v.wi, v.ns) > 0.0f) {
+          float3 X, Y;
+          hit_frame(e.s, tri, v.ns, X, Y);
+          wo = disney_sample(e.dis, v.seg, v.ns, X, Y, v.wi, ua.x, ua.y, ua.z);
+          pdf = disney_pdf(e.dis, v.seg, v.ns, X, Y, v.wi, wo);
+          const float co = dot(wo, v.ns);
+          if (dot(wo, v.ng) > 0.0f && co > 0.0f && pdf > 0.0f) {
+            float m[kDisneyMat];
+            load_disney(e.dis, v.seg, m);
+            const float kk = co / pdf;
+            const float3 wgt = disney_eval(m, v.ns, X, Y, v.wi, wo) * kk;
+            const uint32_t nv = w.nv[slot];
+            for (uint32_t l = 0; l < nv; ++l) {
+              const size_t ix = (size_t)l * w.cap + slot;
+              float4 T = w.aT[ix];
+              T.x *= wgt.x;
+              T.y *= wgt.y;
+              T.z *= wgt.z;
+              w.aT[ix] = T;
+            }
+            const size_t ix = (size_t)nv * w.cap + slot;
+            w.aT[ix] = make_float4(beta.x, beta.y, beta.z, kk);
+            w.aU[ix] = make_float4(0.f, 0.f, 0.f, 0.f);
+            w.aR[ix] = make_float2(h.u, __int_as_float(v.seg));
+            w.aWi[ix] = make_float4(v.wi.x, v.wi.y, v.wi.z, __int_as_float(tri));
+            w.aWo[ix] = make_float4(wo.x, wo.y, wo.z, h.v);
+            w.nv[slot] = nv + 1;
+            beta = beta * wgt;
+            org = v.x + v.ng * e.s.eps;
+            cont = true;
+          }
+        }
+      } else if (dot(v.wi, v.ns) > 0.0f) {
+        const float4 sa = __ldg(&e.t.samp[v.seg]);
         wo = bsdf_sample(__ldg(&e.t.pspec[v.seg]), sa.x, v.ns, v.wi, ua.x, ua.y, ua.z);
         pdf = bsdf_pdf(sa.y, sa.x, v.ns, v.wi, wo);
         const float co = dot(wo, v.ns);
@@ -853,7 +998,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
         }
       }
       if (!cont) {
-        finish_path(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
+        finish_path<kD>(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
         w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       }
     }
@@ -890,7 +1035,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
     for (int j = 0; j < 7; ++j) atomicAdd(&sacc[base + j], dp[j]);
     uint32_t pid, smp, ent;
     slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
-    finish_path(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
+    finish_path<false>(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
     w.beta[slot].w = __uint_as_float(st | kDead);
   }
   if (!lp.gacc) acc_flush(sacc, np, w.blk);
@@ -969,6 +1114,9 @@ static WfDev wf_dev(const WfBuffers& b) {
   w.sh_ge = b.sh_ge;
   w.sh_gm = b.sh_gm;
   w.sh_n = b.sh_n;
+  w.aWi = b.aWi;
+  w.aWo = b.aWo;
+  w.sh_dv = b.sh_dv;
   w.blk = b.blk;
   w.cap = b.cap;
   return w;
@@ -1074,8 +1222,9 @@ std::vector<WfChunk> wf_plan(const std::vector<WfScene>& tab, uint32_t cap, uint
 cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, int loss_kind, const uint32_t* iter_dev, const WfBuffers& wb,
                        double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook,
-                       const CachePass* cache) {
+                       const CachePass* cache, bool disney) {
   const uint32_t ns = (uint32_t)tab.size();
+  if (disney && cache) return cudaErrorInvalidValue;
   WfParams lp = wf_params(tp, loss_kind, ns, iter_dev);
   wf_cache_params(lp, cache, tp.max_depth);
   const bool query = lp.cache_k != kNoCache && !lp.cache_record;
@@ -1086,7 +1235,8 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
   if (lp.cache_k != kNoCache && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
   const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
-  const int grid_cam = one_wave(L, wf_camera, 0), grid_sh = one_wave(L, wf_shade_fwd, 0);
+  const int grid_cam = one_wave(L, wf_camera, 0);
+  const int grid_sh = disney ? one_wave(L, wf_shade_fwd<true>, 0) : one_wave(L, wf_shade_fwd<false>, 0);
   const int red_grid = loss_partials_capacity(L);
   const size_t red_smem = sizeof(double) * ns;
   const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, 0xffffffffu);
@@ -1108,7 +1258,10 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
       }
       {
         IPT_STAGE(10);
-        wf_shade_fwd<<<grid_sh, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, w, cur);
+        if (disney)
+          wf_shade_fwd<true><<<grid_sh, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, w, cur);
+        else
+          wf_shade_fwd<false><<<grid_sh, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       if (k < last_k && k < tp.max_depth && tp.nee && !(record && k < lp.cache_k)) {
         IPT_STAGE(9);
@@ -1142,12 +1295,33 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
 
 uint32_t wf_max_segments() { return (200u * 1024u) / (10u * sizeof(float)); }
 
+template <bool kD>
+static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
+                                    const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb,
+                                    double* grad_acc, uint32_t* err, cudaStream_t st, const WfHook* hook,
+                                    const CachePass* cache);
+
 cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb, double* grad_acc,
-                       uint32_t* err, cudaStream_t st, const WfHook* hook, const CachePass* cache) {
+                       uint32_t* err, cudaStream_t st, const WfHook* hook, const CachePass* cache,
+                       bool disney) {
+  if (disney) return wf_adjoint_model<true>(L, tab_dev, tab, tp, iter_dev, wb, grad_acc, err, st, hook, nullptr);
+  return wf_adjoint_model<false>(L, tab_dev, tab, tp, iter_dev, wb, grad_acc, err, st, hook, cache);
+}
+
+// kD: the Disney model (16 values per segment, chunks of at most 10/16 of
+// the Lambert + GGX segment limit so the shared accumulators keep their size).
+template <bool kD>
+static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
+                                    const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb,
+                                    double* grad_acc, uint32_t* err, cudaStream_t st, const WfHook* hook,
+                                    const CachePass* cache) {
+  constexpr uint32_t P = kD ? 16u : 10u;
+  const uint32_t max_seg = kD ? wf_max_segments() * 10u / 16u : wf_max_segments();
   const uint32_t ns = (uint32_t)tab.size();
   WfParams lp = wf_params(tp, 0, ns, iter_dev);
   if (cache && cache->record) return cudaErrorInvalidValue;
+  if (kD && (!wb.aWi || !wb.aWo || !wb.sh_dv)) return cudaErrorInvalidValue;
   wf_cache_params(lp, cache, tp.max_depth);
   const bool query = lp.cache_k != kNoCache;
   const uint32_t last_k = query ? lp.cache_k : tp.max_depth;
@@ -1157,34 +1331,34 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
   const bool wide = all_wide(tab);
   const int grid = wf_grid(L);
   const int grid_cam = one_wave(L, wf_camera, 0);
-  const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, wf_max_segments());
-  // chunks of more than wf_max_segments() segments (one scene with that many)
+  const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, max_seg);
+  // chunks of more than max_seg segments (one scene with that many)
   // accumulate with atomics in global memory instead of shared memory
   uint32_t max_np = 0, max_np_shared = 0;
   for (const WfChunk& c : chunks) {
-    max_np = std::max(max_np, 10u * c.seg_n);
-    if (c.seg_n <= wf_max_segments()) max_np_shared = std::max(max_np_shared, 10u * c.seg_n);
+    max_np = std::max(max_np, P * c.seg_n);
+    if (c.seg_n <= max_seg) max_np_shared = std::max(max_np_shared, P * c.seg_n);
   }
   if (max_np > wb.blk_params) return cudaErrorInvalidValue;
   const size_t shmem = max_np_shared * sizeof(float);
   if (shmem > 48 * 1024) {
-    cudaFuncSetAttribute(wf_adj_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-    cudaFuncSetAttribute(wf_adj_connect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-    cudaFuncSetAttribute(wf_adj_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    cudaFuncSetAttribute(wf_adj_a<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    cudaFuncSetAttribute(wf_adj_connect<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    cudaFuncSetAttribute(wf_adj_b<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     cudaFuncSetAttribute(wf_adj_cache, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   }
   for (const WfChunk& c : chunks) {
     lp.seg_lo = c.seg_lo;
     lp.seg_n = c.seg_n;
-    const uint32_t np = 10u * c.seg_n;
-    const bool global = c.seg_n > wf_max_segments();
+    const uint32_t np = P * c.seg_n;
+    const bool global = c.seg_n > max_seg;
     lp.gacc = global ? wb.blk : nullptr;
     const size_t sm = global ? 0 : np * sizeof(float);
     // each adjoint stage runs one wave at its own occupancy for this
     // accumulator size; block b of every stage adds into gradient row b
     // (all blocks into row 0 in global mode)
-    const int g_a = one_wave(L, wf_adj_a, sm), g_c = one_wave(L, wf_adj_connect, sm);
-    const int g_b = one_wave(L, wf_adj_b, sm), g_q = one_wave(L, wf_adj_cache, sm);
+    const int g_a = one_wave(L, wf_adj_a<kD>, sm), g_c = one_wave(L, wf_adj_connect<kD>, sm);
+    const int g_b = one_wave(L, wf_adj_b<kD>, sm), g_q = one_wave(L, wf_adj_cache, sm);
     const int rows = global ? 1 : std::max(std::max(g_a, g_c), std::max(g_b, g_q));
     if (rows > wf_max_blocks(L)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(wb.blk, 0, (size_t)rows * np * sizeof(float), st);
@@ -1205,7 +1379,7 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
       }
       {
         IPT_STAGE(11);
-        wf_adj_a<<<g_a, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
+        wf_adj_a<kD><<<g_a, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       if (k < last_k) {
         if (tp.nee) {
@@ -1217,10 +1391,10 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
               wf_trace<2, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
           }
           IPT_STAGE(12);
-          wf_adj_connect<<<g_c, kWfThreads, sm, st>>>(tab_dev, lp, w);
+          wf_adj_connect<kD><<<g_c, kWfThreads, sm, st>>>(tab_dev, lp, w);
         }
         IPT_STAGE(13);
-        wf_adj_b<<<g_b, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
+        wf_adj_b<kD><<<g_b, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w, cur);
       }
       cur ^= 1;
     }
@@ -1238,7 +1412,7 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
       wf_adj_cache<<<g_q, kWfThreads, sm, st>>>(tab_dev, lp, c.p0, w);
     }
     IPT_STAGE(14);
-    wf_blk_reduce<<<(np + 31) / 32, 32 * kReduceWarps, 0, st>>>(wb.blk, rows, np, grad_acc + 10u * c.seg_lo);
+    wf_blk_reduce<<<(np + 31) / 32, 32 * kReduceWarps, 0, st>>>(wb.blk, rows, np, grad_acc + P * c.seg_lo);
   }
   return cudaGetLastError();
 }
@@ -1262,9 +1436,12 @@ cudaError_t wf_init(Launcher* L) {
   // gradient rows: the widest one-wave grid of an adjoint stage (accumulators
   // in dynamic shared memory only lower the occupancy)
   int rows = 0;
-  rows = std::max(rows, one_wave(*L, wf_adj_a, 0));
-  rows = std::max(rows, one_wave(*L, wf_adj_connect, 0));
-  rows = std::max(rows, one_wave(*L, wf_adj_b, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_a<false>, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_connect<false>, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_b<false>, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_a<true>, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_connect<true>, 0));
+  rows = std::max(rows, one_wave(*L, wf_adj_b<true>, 0));
   rows = std::max(rows, one_wave(*L, wf_adj_cache, 0));
   L->wf_max_rows = rows;
   return cudaSuccess;

@@ -15,7 +15,8 @@ namespace ipt {
 
 struct WfScene {
   SceneDev s;                // geometry
-  SegDev t;                  // parameter tables
+  SegDev t;                  // parameter tables (emission and light selection for either model)
+  DisneyDev dis;             // Disney material tables, or null pointers (Lambert + GGX)
   const ViewDev* views;
   uint32_t n_views;
   uint32_t pix_begin;        // first launch pixel of this scene
@@ -56,10 +57,12 @@ struct WfChunk {
 std::vector<WfChunk> wf_plan(const std::vector<WfScene>& tab, uint32_t cap, uint32_t spp, uint32_t max_seg);
 uint32_t wf_max_segments();
 
+// disney: the table's scenes trace with the Disney material model (their
+// `dis` tables; gradients of 16 values per segment).
 cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, int loss_kind, const uint32_t* iter_dev, const WfBuffers& wb,
                        double* loss_rows, uint32_t* err, cudaStream_t st, const WfHook* hook,
-                       const CachePass* cache = nullptr);
+                       const CachePass* cache = nullptr, bool disney = false);
 
 // Draws the pixel batch of every table entry that has one, for the iteration
 // *iter_dev (or iter when iter_dev is null).
@@ -68,6 +71,7 @@ cudaError_t wf_pick(const WfScene* tab_dev, const std::vector<WfScene>& tab, con
 
 cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vector<WfScene>& tab,
                        const TraceParams& tp, const uint32_t* iter_dev, const WfBuffers& wb, double* grad_acc,
-                       uint32_t* err, cudaStream_t st, const WfHook* hook, const CachePass* cache = nullptr);
+                       uint32_t* err, cudaStream_t st, const WfHook* hook, const CachePass* cache = nullptr,
+                       bool disney = false);
 
 }  // namespace ipt

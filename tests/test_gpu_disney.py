@@ -1,7 +1,8 @@
-"""Disney material model (Sec. 4.1) on the CUDA path, through the C ABI:
-images, loss and gradient match the FP64 oracle on the same sample sets
-(whole images and stochastic pixel batches, several depths), and Adam on the
-Disney parameters recovers the base colour and emission of a Cornell box."""
+"""Disney material model (Sec. 4.1) on the CUDA path, through the C ABI, on
+both integrators: images, loss and gradient match the FP64 oracle on the
+same sample sets (whole images and stochastic pixel batches, several depths),
+and Adam on the Disney parameters recovers the base colour and emission of a
+Cornell box."""
 import numpy as np
 import pytest
 
@@ -29,11 +30,16 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+INTEGRATORS = ["megakernel", "wavefront"]
+
+
+@pytest.mark.parametrize("integrator", INTEGRATORS)
 @pytest.mark.parametrize("depth", [1, 3, 5])
-def test_image_matches_oracle(built, depth):
+def test_image_matches_oracle(built, depth, integrator):
     sc = scenes.cornell_box(1000, 24, 20)
     p = scenes.disney_materials(sc, 3)
     tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator)
     tr.disney_set_params(p)
     opts = TraceOptions(max_depth=depth)
     img = tr.disney_render(opts, view=0, set_id=0, spp=16, iteration=5).cpu().numpy()
@@ -44,8 +50,9 @@ def test_image_matches_oracle(built, depth):
     tr.close()
 
 
+@pytest.mark.parametrize("integrator", INTEGRATORS)
 @pytest.mark.parametrize("batch,loss", [(0, "l2"), (0, "l1"), (300, "l2")])
-def test_loss_and_gradient_match_oracle(built, batch, loss):
+def test_loss_and_gradient_match_oracle(built, batch, loss, integrator):
     sc = scenes.cornell_box(1000, 24, 20)
     rng = np.random.default_rng(8)
     p = scenes.disney_materials(sc, 4).astype(np.float64)
@@ -58,6 +65,7 @@ def test_loss_and_gradient_match_oracle(built, batch, loss):
         lo, go = O.loss_grad(osc, p, targets, spp_r, spp_d, D, iteration=it, seed=SEED, loss=loss,
                              model=O.MODEL_DISNEY)
     tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator)
     tr.disney_set_params(p.astype(np.float32))
     tr.set_targets(torch.from_numpy(targets[0].astype(np.float32)).cuda())
     lg, gg = tr.disney_loss_grad(TraceOptions(spp_r=spp_r, spp_d=spp_d, max_depth=D, loss=loss,
@@ -86,7 +94,8 @@ def _oracle_batch(osc, p, targets, batch, spp_r, spp_d, D, it, loss):
     return lo, go, ids
 
 
-def test_optimisation_recovers_base_colour_and_emission(built):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_optimisation_recovers_base_colour_and_emission(built, integrator):
     """From grey walls and no light, Adam on base colour and emission (other
     material values held at the truth) brings the parameters within a few
     per cent of the truth on the segments the camera sees."""
@@ -94,6 +103,7 @@ def test_optimisation_recovers_base_colour_and_emission(built):
     truth = scenes.disney_materials(sc, 9)
     truth[:, 4] = 0.0  # dielectric walls, so that the base colour shows
     tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator)
     tr.disney_set_params(truth)
     tr.set_targets(tr.disney_render(TraceOptions(max_depth=3), set_id=L.IPT_SET_TARGET, spp=1024))
     free = np.zeros((sc.n_segments, 16), np.uint8)
