@@ -516,7 +516,10 @@ ipt_status ipt_cache_bias(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opt
  * Sec. 3 later or elsewhere): its parameters, free mask, Adam moments and
  * step count, its iteration counter and, when it has a radiance cache, the
  * cache's weights, hash table, their Adam moments and step count and its
- * on/off state.  Host memory, the library's own layout: a 64-byte header
+ * on/off state, and, when Disney parameters are set (ipt_disney_params_set),
+ * their blocks, free mask, Adam moments, step count and iteration (restored
+ * into the target scene's Disney state, which a load creates if needed).
+ * Host memory, the library's own layout: a 64-byte header
  * ("IPTCKPT1", version, segment count, counters, flags) followed by the
  * arrays.  Save: with buf == NULL, *n receives the size in bytes; with a
  * buffer, *n must hold at least that size and receives the bytes written.

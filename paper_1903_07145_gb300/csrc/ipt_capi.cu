@@ -87,6 +87,10 @@ void free_disney(DisneyState* d) {
   delete d;
 }
 
+struct DeviceScene;
+// The scene's Disney state, allocated on first use.
+ipt_status disney_state(ipt_ctx* ctx, DeviceScene* s, DisneyState** out);
+
 struct DeviceScene {
   uint32_t n_tri = 0, n_seg = 0, n_nodes = 0, depth = 0;
   float eps = 0.f, emission_scale = 1.f;
@@ -1985,7 +1989,9 @@ struct CkptHeader {           // 64 bytes
   uint64_t cache_steps;
   uint32_t cache_active;
   uint32_t cache_fell_back;
-  uint8_t pad[16];
+  uint32_t has_disney;        // Disney-model parameters and optimiser state follow
+  int32_t disney_step;
+  uint64_t disney_iteration;
 };
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header layout");
 
@@ -1994,11 +2000,13 @@ constexpr uint32_t kCkptVersion = 1;
 // Byte layout after the header: params, adam_m, adam_v (10 S floats each),
 // free mask (10 S bytes, padded to 8); with a cache: weights, their Adam m
 // and v (kCacheWeights floats each), table, its Adam m and v
-// (kCacheTableFloats floats each).
-size_t ckpt_bytes(uint32_t n_seg, bool cache) {
-  const size_t np = 10 * (size_t)n_seg;
+// (kCacheTableFloats floats each); with Disney-model state: its params,
+// adam_m, adam_v (16 S floats each) and free mask (16 S bytes, padded to 8).
+size_t ckpt_bytes(uint32_t n_seg, bool cache, bool disney) {
+  const size_t np = 10 * (size_t)n_seg, nd = 16 * (size_t)n_seg;
   size_t n = sizeof(CkptHeader) + 3 * np * sizeof(float) + ((np + 7) & ~(size_t)7);
   if (cache) n += 3 * (size_t)ipt::kCacheWeights * sizeof(float) + 3 * (size_t)ipt::kCacheTableFloats * sizeof(float);
+  if (disney) n += 3 * nd * sizeof(float) + ((nd + 7) & ~(size_t)7);
   return n;
 }
 
@@ -2012,7 +2020,8 @@ ipt_status ipt_checkpoint_save(ipt_ctx* ctx, int32_t scene, void* buf, size_t* n
   if (st != IPT_OK) return st;
   if (!n) return fail(ctx, IPT_ERR_INVALID_ARG, "null size");
   const bool cache = s->cache != nullptr;
-  const size_t need = ckpt_bytes(s->n_seg, cache);
+  const bool disney = s->disney != nullptr;
+  const size_t need = ckpt_bytes(s->n_seg, cache, disney);
   if (!buf) {
     *n = need;
     return IPT_OK;
@@ -2031,6 +2040,12 @@ ipt_status ipt_checkpoint_save(ipt_ctx* ctx, int32_t scene, void* buf, size_t* n
     h.cache_steps = s->cache->steps_done;
     h.cache_active = s->cache->active ? 1u : 0u;
     h.cache_fell_back = s->cache->fell_back ? 1u : 0u;
+  }
+  h.has_disney = disney ? 1u : 0u;
+  if (disney) {
+    IPT_CK(cudaMemcpyAsync(&h.disney_step, s->disney->step_dev, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    h.disney_iteration = s->disney->iteration;
   }
   const size_t np = 10 * (size_t)s->n_seg;
   char* p = static_cast<char*>(buf) + sizeof(CkptHeader);
@@ -2054,6 +2069,14 @@ ipt_status ipt_checkpoint_save(ipt_ctx* ctx, int32_t scene, void* buf, size_t* n
     IPT_CK(D2H(c->mt, nt));
     IPT_CK(D2H(c->vt, nt));
   }
+  if (disney) {
+    const DisneyState* d = s->disney;
+    const size_t nd = 16 * (size_t)s->n_seg;
+    IPT_CK(D2H(d->params, nd * sizeof(float)));
+    IPT_CK(D2H(d->adam_m, nd * sizeof(float)));
+    IPT_CK(D2H(d->adam_v, nd * sizeof(float)));
+    IPT_CK(D2H(d->free_mask, nd));
+  }
   IPT_CK(cudaStreamSynchronize(ctx->stream));
   std::memcpy(buf, &h, sizeof(h));
   *n = need;
@@ -2075,9 +2098,11 @@ ipt_status ipt_checkpoint_load(ipt_ctx* ctx, int32_t scene, const void* buf, siz
                                               std::to_string(s->n_seg));
   if (h.has_cache > 1 || (h.has_cache && !s->cache))
     return fail(ctx, IPT_ERR_INVALID_ARG, "checkpoint carries cache state: configure the scene's cache first");
-  if (n != ckpt_bytes(h.n_seg, h.has_cache != 0))
+  if (h.has_disney > 1) return fail(ctx, IPT_ERR_INVALID_ARG, "bad Disney flag");
+  const size_t expect = ckpt_bytes(h.n_seg, h.has_cache != 0, h.has_disney != 0);
+  if (n != expect)
     return fail(ctx, IPT_ERR_INVALID_ARG, "checkpoint of " + std::to_string(n) + " bytes, expected " +
-                                              std::to_string(ckpt_bytes(h.n_seg, h.has_cache != 0)));
+                                              std::to_string(expect));
   const size_t np = 10 * (size_t)s->n_seg;
   const float* pf = reinterpret_cast<const float*>(static_cast<const char*>(buf) + sizeof(CkptHeader));
   for (size_t i = 0; i < np; ++i)
@@ -2108,6 +2133,18 @@ ipt_status ipt_checkpoint_load(ipt_ctx* ctx, int32_t scene, const void* buf, siz
     c->steps_done = h.cache_steps;
     c->active = h.cache_active != 0;
     c->fell_back = h.cache_fell_back != 0;
+  }
+  if (h.has_disney) {
+    DisneyState* d;
+    if ((st = disney_state(ctx, s, &d)) != IPT_OK) return st;
+    const size_t nd = 16 * (size_t)s->n_seg;
+    IPT_CK(H2D(d->params, nd * sizeof(float)));
+    IPT_CK(H2D(d->adam_m, nd * sizeof(float)));
+    IPT_CK(H2D(d->adam_v, nd * sizeof(float)));
+    IPT_CK(H2D(d->free_mask, nd));
+    IPT_CK(cudaMemcpyAsync(d->step_dev, &h.disney_step, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    d->iteration = h.disney_iteration;
+    d->tab_is_ctx = false;
   }
   IPT_CK(cudaStreamSynchronize(ctx->stream));  // the caller may release buf on return
   s->iteration = h.iteration;

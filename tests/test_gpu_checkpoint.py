@@ -98,3 +98,30 @@ def test_bad_checkpoints_are_rejected(built):
     assert np.array_equal(a.get_params(), p)    # nothing changed
     for t in (a, b, c):
         t.close()
+
+
+def test_disney_state_round_trips(built):
+    """A checkpoint carries the Disney parameters and optimiser state: a fresh
+    context restored from it steps exactly as the original."""
+    sc = scenes.cornell_box(1000, 24, 24)
+    truth = scenes.disney_materials(sc, 2)
+    a = Tracer(sc, seed=3)
+    a.disney_set_params(truth)
+    target = a.disney_render(TraceOptions(max_depth=3), set_id=L.IPT_SET_TARGET, spp=64)
+    a.set_targets(target)
+    p0 = truth.copy()
+    p0[:, 0:3] = 0.5
+    a.disney_set_params(p0)
+    opts = TraceOptions(spp_r=8, spp_d=4, max_depth=3)
+    for _ in range(5):
+        a.disney_step(opts, ADAM)
+    ck = a.checkpoint()
+    b = Tracer(sc, seed=3)
+    b.set_targets(target)
+    b.restore(ck)
+    assert np.array_equal(b.disney_params(), a.disney_params())
+    assert b.checkpoint() == ck
+    la, lb = a.disney_step(opts, ADAM), b.disney_step(opts, ADAM)
+    assert abs(la - lb) <= 1e-6 * abs(la), (la, lb)
+    a.close()
+    b.close()
