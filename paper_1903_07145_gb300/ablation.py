@@ -1,12 +1,12 @@
 """Optimiser ablations as convergence curves (Sec. 5, optimiser ablation, and
-App. C): paths per pixel for the colour estimate, the split of a fixed path
+App. A): paths per pixel for the colour estimate, the split of a fixed path
 budget between colour and derivative samples, the pixel-batch size at equal
 time, multiple importance sampling, and the number of bounces fitted to a
 10-bounce target.
 
 Each setting optimises the same scene from the same start for the same
 GPU time budget on the batch-graph step (one scene, stochastic pixel
-batches, L1 loss as in Sec. 4.4).  At checkpoints it records the iteration,
+batches, the L1 loss of Sec. 3.2).  At checkpoints it records the iteration,
 the elapsed optimisation time (CUDA-synchronised, reads excluded), the
 parameter error (relative L2 over the scored parameters) and the full-image
 L1 loss of the current parameters against the target, estimated with a fixed

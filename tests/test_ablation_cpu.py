@@ -1,4 +1,4 @@
-"""The optimiser-ablation settings (Sec. 5 and App. C) are the experiments
+"""The optimiser-ablation settings (Sec. 5 and App. A) are the experiments
 they name: the paths sweep varies only the colour paths, the split keeps the
 128-path budget, the batch sweep varies only the batch size, the MIS sweep
 switches light sampling and MIS, and the bounces sweep fits depths 1-3 to a
