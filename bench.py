@@ -515,13 +515,29 @@ def run_time_to_error(args):
                             max_depth=args.batch_depth, pixel_batch=args.pixel_batch)
         tgt = TraceOptions(max_depth=args.batch_depth)
         ss, masks = convergence.prepare(rooms, tgt, target_spp=target_spp, init=0.0, seed=7)
-        ss.configure(integrator="wavefront", wavefront_slots=1 << 21, bvh_width=4)
+        # the batch's integrator: as given, or the faster of the two on 20
+        # batch steps from the start (outside the timing; make_batch restarts
+        # from the scenes' own parameters, which the steps do not touch)
+        batch_ms = {}
+        for integ in (["wavefront", "megakernel"] if args.batch_integrator == "auto" else [args.batch_integrator]):
+            ss.configure(integrator=integ, wavefront_slots=1 << 21, bvh_width=4)
+            ss.make_batch()
+            ss.batch_step(opts, adam, want_losses=False)
+            torch.cuda.synchronize(ss.device)
+            t0 = time.perf_counter()
+            for _ in range(20):
+                ss.batch_step(opts, adam, want_losses=False)
+            torch.cuda.synchronize(ss.device)
+            batch_ms[integ] = (time.perf_counter() - t0) / 20 * 1e3
+        batch_integ = min(batch_ms, key=batch_ms.get)
+        ss.configure(integrator=batch_integ, wavefront_slots=1 << 21, bvh_width=4)
         # a scene leaves the batch when it reaches the threshold, as one optimised
         # alone stops at its own crossing
         first, hist = convergence.time_to_error(ss, masks, opts, adam, threshold=0.01,
                                                 max_iters=args.max_iters, check_every=args.check_every,
                                                 halve_every=args.halve_every, retire=not args.no_retire)
-        res["batched"] = {"first": first, "history_last": hist[-1][:2]}
+        res["batched"] = {"first": first, "history_last": hist[-1][:2], "integrator": batch_integ,
+                          "ms_per_step_probe": batch_ms}
         ss.close()
         # the plain arm: each scene alone with its fastest integrator
         # configuration (autotuned on its own workload, outside the timing)
@@ -703,6 +719,8 @@ def main():
     ap.add_argument("--seq-rooms", type=int, default=64,
                     help="time-to-error: rooms optimised one after another for the plain arm")
     ap.add_argument("--check-every", type=int, default=50, help="time-to-error: iterations between error reads")
+    ap.add_argument("--batch-integrator", default="auto", choices=["auto", "wavefront", "megakernel"],
+                    help="time-to-error: the batch graph's integrator (auto: the faster on 20 steps)")
     ap.add_argument("--no-retire", action="store_true",
                     help="time-to-error: keep stepping batch members that reached the threshold")
     ap.add_argument("--halve-every", type=int, default=0,

@@ -152,6 +152,7 @@ struct Batch {
   float* adam_v = nullptr;
   uint8_t* free_mask = nullptr;
   double* grad_acc = nullptr;
+  float* gacc = nullptr;  // megakernel: global FP32 accumulators when shared memory is too small
   uint32_t* iter_dev = nullptr;
   double* loss_rows = nullptr;
   double* losses_dev = nullptr;
@@ -1285,6 +1286,7 @@ ipt_status ipt_batch_create(ipt_ctx* ctx, const int32_t* scenes, uint32_t n, int
   A(&b->adam_v, np);
   A(&b->free_mask, np);
   A(&b->grad_acc, np);
+  if (np > ipt::batch_shared_params()) A(&b->gacc, np);
   A(&b->iter_dev, 1);
   A(&b->loss_rows, (size_t)rows * n);
   A(&b->losses_dev, n);
@@ -1350,14 +1352,28 @@ static ipt_status batch_enqueue(ipt_ctx* ctx, Batch* b, const ipt_trace_opts* op
   tp.mis = opts->mis;
   tp.profile = opts->emission_profile;
   if (opts->pixel_batch) IPT_CK(ipt::wf_pick(b->tab_dev, b->tab_host, b->iter_dev, 0u, st));
-  IPT_CK(ipt::wf_forward(ctx->L, b->tab_dev, b->tab_host, tp, opts->loss, b->iter_dev, ctx->wf, b->loss_rows,
-                         ctx->err_dev, st, nullptr));
+  // the megakernel runs each pass as one launch over the whole table
+  const bool mk = ctx->cfg.integrator == 0;
+  const uint32_t ns = (uint32_t)b->tab_host.size();
+  const uint32_t total = ns ? b->tab_host.back().pix_begin + b->tab_host.back().n_pix : 0u;
+  uint32_t n_seg_active = 0;
+  for (const ipt::WfScene& e : b->tab_host) n_seg_active = std::max(n_seg_active, e.seg_offset + e.n_seg);
+  if (mk)
+    IPT_CK(ipt::launch_forward_batch(ctx->L, b->tab_dev, ns, total, tp, b->iter_dev, opts->loss, b->loss_rows,
+                                     ctx->err_dev, st));
+  else
+    IPT_CK(ipt::wf_forward(ctx->L, b->tab_dev, b->tab_host, tp, opts->loss, b->iter_dev, ctx->wf, b->loss_rows,
+                           ctx->err_dev, st, nullptr));
   IPT_CK(cudaMemsetAsync(b->grad_acc, 0, np * sizeof(double), st));
   tp.set = opts->gradcheck_same_set ? IPT_SET_RESIDUAL : IPT_SET_DERIVATIVE;
   tp.spp = opts->spp_d;
   if (opts->gradcheck_same_set) tp.sample_stride = opts->spp_r;
-  IPT_CK(ipt::wf_adjoint(ctx->L, b->tab_dev, b->tab_host, tp, b->iter_dev, ctx->wf, b->grad_acc, ctx->err_dev, st,
-                         nullptr));
+  if (mk)
+    IPT_CK(ipt::launch_adjoint_batch(ctx->L, b->tab_dev, ns, total, n_seg_active, tp, b->iter_dev, b->grad_acc,
+                                     b->gacc, ctx->err_dev, st));
+  else
+    IPT_CK(ipt::wf_adjoint(ctx->L, b->tab_dev, b->tab_host, tp, b->iter_dev, ctx->wf, b->grad_acc, ctx->err_dev,
+                           st, nullptr));
   IPT_CK(ipt::launch_batch_losses(b->loss_rows, ipt::loss_partials_capacity(ctx->L), b->mem_dev, n,
                                   (uint32_t)b->tab_host.size(), b->losses_dev, st));
   IPT_CK(ipt::launch_adam_batch(b->mem_dev, n, b->params, b->adam_m, b->adam_v, b->free_mask, b->grad_acc,

@@ -19,6 +19,7 @@
 #include "ipt_device.cuh"
 #include "ipt_internal.h"
 #include "ipt_path.cuh"
+#include "ipt_wavefront.h"
 
 namespace ipt {
 
@@ -316,6 +317,145 @@ __global__ void __launch_bounds__(kBlockThreads) k_adjoint(SceneDev s, SegDev t,
   if (!gacc)
     for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) {
       const float v = sgrad[i];
+      if (v != 0.0f) atomicAdd(&grad_acc[i], (double)v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched megakernel: the paths of every scene of a batch's launch table in
+// one forward and one adjoint launch (the small pixel batches of Sec. 4.5
+// are latency-bound, and a stage-by-stage wavefront pays ~45 launches per
+// iteration).  Launch pixel p belongs to the table entry whose pixel range
+// holds it; each scene keeps its own Philox key, emission scale, pixel draw,
+// target and segment range, so its paths are the ones it traces alone.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t table_scene(const WfScene* tab, uint32_t n, uint32_t p) {
+  uint32_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (tab[mid].pix_begin <= p)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ PathParams scene_params(const PathParams& base, const WfScene& e, uint32_t set_iter) {
+  PathParams p = base;
+  p.key = e.key;
+  p.emission_scale = e.es;
+  p.set_iter = set_iter;
+  p.pick = e.pick;
+  return p;
+}
+
+// Residual pass: the upstream gradient of every entry and, per block, each
+// scene's loss sum (rows[block * n_scenes + scene], the layout of the
+// wavefront's reduction).
+__global__ void __launch_bounds__(kBlockThreads)
+    k_forward_batch(const WfScene* tab, uint32_t n_scenes, uint32_t total, PathParams pp, uint32_t set,
+                    const uint32_t* iter_dev, int loss_kind, double* loss_rows, uint32_t* err) {
+  extern __shared__ double sloss[];
+  for (uint32_t i = threadIdx.x; i < n_scenes; i += blockDim.x) sloss[i] = 0.0;
+  __syncthreads();
+  const uint32_t set_iter = (set << 24) | (*iter_dev & 0xFFFFFFu);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t G = pp.group;
+  const uint32_t ppw = 32u / G;
+  const uint32_t sub = lane & (G - 1u);
+  const uint32_t warps_per_block = blockDim.x >> 5;
+  const uint32_t n_tasks = (total + ppw - 1) / ppw;
+  const uint32_t stride = gridDim.x * warps_per_block;
+  const float inv_spp = 1.0f / (float)pp.spp;
+  for (uint32_t task = blockIdx.x * warps_per_block + (threadIdx.x >> 5); task < n_tasks; task += stride) {
+    const uint32_t p = task * ppw + lane / G;
+    const bool active = p < total;
+    float3 a = f3(0.f, 0.f, 0.f);
+    uint32_t b = 0, entry = 0, pid = 0;
+    if (active) {
+      b = table_scene(tab, n_scenes, p);
+      const WfScene& e = tab[b];
+      entry = p - e.pix_begin + e.pix_base;
+      pid = e.pick ? e.pick[entry] : entry;
+      const uint32_t s0 = e.pick ? entry * pp.stride : 0u;
+      const PathParams q = scene_params(pp, e, set_iter);
+      const double W = *e.t.W;
+      const ViewDev& vw = find_view(e.views, e.n_views, pid);
+      const uint32_t lp = pid - vw.offset;
+      const uint32_t px = lp % vw.w, py = lp / vw.w;
+      for (uint32_t smp = sub; smp < pp.spp; smp += G) a = a + forward_path(e.s, e.t, vw, px, py, pid, s0 + smp, q, W, err);
+    }
+    for (uint32_t off = G >> 1; off >= 1; off >>= 1) {
+      a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
+      a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+      a.z += __shfl_xor_sync(0xffffffffu, a.z, off);
+    }
+    if (active && sub == 0) {
+      const WfScene& e = tab[b];
+      const float3 mean = a * inv_spp;
+      const uint32_t ti = e.pick ? pid : entry;
+      const float r[3] = {mean.x - e.target[3 * ti + 0], mean.y - e.target[3 * ti + 1], mean.z - e.target[3 * ti + 2]};
+      double l = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (loss_kind == 0) {
+          e.g_img[3 * entry + c] = 2.0f * r[c] * e.g_scale;
+          l += (double)r[c] * (double)r[c];
+        } else {
+          e.g_img[3 * entry + c] = (r[c] > 0.0f ? 1.0f : (r[c] < 0.0f ? -1.0f : 0.0f)) * e.g_scale;
+          l += fabs((double)r[c]);
+        }
+      }
+      atomicAdd(&sloss[b], l);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n_scenes; i += blockDim.x) loss_rows[(size_t)blockIdx.x * n_scenes + i] = sloss[i];
+}
+
+// Derivative pass: every entry's paths into the batch's packed segment
+// accumulators (shared per block, or global when they do not fit).
+template <int MAXD>
+__global__ void __launch_bounds__(kBlockThreads)
+    k_adjoint_batch(const WfScene* tab, uint32_t n_scenes, uint32_t total, uint32_t n_par, PathParams pp,
+                    uint32_t set, const uint32_t* iter_dev, double* grad_acc, float* gacc, uint32_t* err) {
+  extern __shared__ float bgrad_sh[];
+  float* acc = gacc ? gacc : bgrad_sh;
+  if (!gacc)
+    for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) acc[i] = 0.0f;
+  __syncthreads();
+  const uint32_t set_iter = (set << 24) | (*iter_dev & 0xFFFFFFu);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t G = pp.group;
+  const uint32_t ppw = 32u / G;
+  const uint32_t sub = lane & (G - 1u);
+  const uint32_t warps_per_block = blockDim.x >> 5;
+  const uint32_t n_tasks = (total + ppw - 1) / ppw;
+  const uint32_t stride = gridDim.x * warps_per_block;
+  const float inv_spp = 1.0f / (float)pp.spp;
+  for (uint32_t task = blockIdx.x * warps_per_block + (threadIdx.x >> 5); task < n_tasks; task += stride) {
+    const uint32_t p = task * ppw + lane / G;
+    if (p >= total) continue;
+    const WfScene& e = tab[table_scene(tab, n_scenes, p)];
+    const uint32_t entry = p - e.pix_begin + e.pix_base;
+    const uint32_t pid = e.pick ? e.pick[entry] : entry;
+    const uint32_t s0 = e.pick ? entry * pp.stride : 0u;
+    const float3 gp = f3(e.g_img[3 * entry], e.g_img[3 * entry + 1], e.g_img[3 * entry + 2]) * inv_spp;
+    if (gp.x == 0.0f && gp.y == 0.0f && gp.z == 0.0f) continue;
+    const PathParams q = scene_params(pp, e, set_iter);
+    const double W = *e.t.W;
+    const ViewDev& vw = find_view(e.views, e.n_views, pid);
+    const uint32_t lp = pid - vw.offset;
+    const uint32_t px = lp % vw.w, py = lp / vw.w;
+    float* sacc = acc + 10u * e.seg_offset;
+    for (uint32_t smp = sub; smp < pp.spp; smp += G)
+      adjoint_path<MAXD>(e.s, e.t, vw, px, py, pid, s0 + smp, q, W, gp, sacc, err);
+  }
+  __syncthreads();
+  if (!gacc)
+    for (uint32_t i = threadIdx.x; i < n_par; i += blockDim.x) {
+      const float v = acc[i];
       if (v != 0.0f) atomicAdd(&grad_acc[i], (double)v);
     }
 }
@@ -643,6 +783,65 @@ cudaError_t launch_adjoint(const Launcher& L, const SceneBuffers& s, const SegBu
     IPT_LAUNCH_ADJ(8, 3)
 #undef IPT_LAUNCH_ADJ
   if (global) k_add_to_double<<<(10u * s.n_seg + 255) / 256, 256, 0, st>>>(gacc, 10u * s.n_seg, grad_acc);
+  return cudaGetLastError();
+}
+
+static PathParams batch_path_params(const TraceParams& tp) {
+  PathParams p{};
+  p.spp = tp.spp;
+  p.group = lanes_per_pixel(tp.spp);
+  p.max_depth = tp.max_depth;
+  p.nee = tp.nee;
+  p.mis = tp.mis;
+  p.profile = tp.profile;
+  p.stride = tp.sample_stride ? tp.sample_stride : tp.spp;
+  return p;
+}
+
+cudaError_t launch_forward_batch(const Launcher& L, const WfScene* tab_dev, uint32_t n_scenes, uint32_t total,
+                                 const TraceParams& tp, const uint32_t* iter_dev, int loss_kind, double* loss_rows,
+                                 uint32_t* err, cudaStream_t st) {
+  // one block per loss row: every row of the batch's loss reduction is written
+  k_forward_batch<<<loss_partials_capacity(L), kBlockThreads, sizeof(double) * n_scenes, st>>>(
+      tab_dev, n_scenes, total, batch_path_params(tp), tp.set, iter_dev, loss_kind, loss_rows, err);
+  return cudaGetLastError();
+}
+
+uint32_t batch_shared_params() { return (96u * 1024u) / (uint32_t)sizeof(float); }
+
+cudaError_t launch_adjoint_batch(const Launcher& L, const WfScene* tab_dev, uint32_t n_scenes, uint32_t total,
+                                 uint32_t n_seg, const TraceParams& tp, const uint32_t* iter_dev, double* grad_acc,
+                                 float* gacc_scratch, uint32_t* err, cudaStream_t st) {
+  const PathParams pp = batch_path_params(tp);
+  const uint32_t n_par = 10u * n_seg;
+  const bool global = n_par > batch_shared_params();
+  if (global && !gacc_scratch) return cudaErrorInvalidValue;
+  float* gacc = global ? gacc_scratch : nullptr;
+  const size_t shmem = global ? 0 : sizeof(float) * n_par;
+  if (global) {
+    cudaError_t e = cudaMemsetAsync(gacc, 0, sizeof(float) * n_par, st);
+    if (e != cudaSuccess) return e;
+  }
+  const uint64_t tasks = ((uint64_t)total + (32 / pp.group) - 1) / (32 / pp.group);
+  const int md = tp.max_depth < 1 ? 1 : (int)tp.max_depth;
+#define IPT_LAUNCH_ADJB(D, I)                                                                              \
+  {                                                                                                        \
+    if (shmem > 48 * 1024)                                                                                 \
+      cudaFuncSetAttribute(k_adjoint_batch<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);  \
+    const int grid = grid_for(tasks, L.num_sms * L.adj_blocks_per_sm[I]);                                  \
+    k_adjoint_batch<D><<<grid, kBlockThreads, shmem, st>>>(tab_dev, n_scenes, total, n_par, pp, tp.set,    \
+                                                           iter_dev, grad_acc, gacc, err);                 \
+  }
+  if (md <= 2)
+    IPT_LAUNCH_ADJB(2, 0)
+  else if (md <= 4)
+    IPT_LAUNCH_ADJB(4, 1)
+  else if (md <= 6)
+    IPT_LAUNCH_ADJB(6, 2)
+  else
+    IPT_LAUNCH_ADJB(8, 3)
+#undef IPT_LAUNCH_ADJB
+  if (global) k_add_to_double<<<(n_par + 255) / 256, 256, 0, st>>>(gacc, n_par, grad_acc);
   return cudaGetLastError();
 }
 

@@ -74,4 +74,18 @@ cudaError_t wf_adjoint(const Launcher& L, const WfScene* tab_dev, const std::vec
                        uint32_t* err, cudaStream_t st, const WfHook* hook, const CachePass* cache = nullptr,
                        bool disney = false);
 
+// Batched megakernel over a launch table (Lambert + GGX): the residual pass
+// writes each entry's upstream gradient and per-block loss rows
+// (loss_partials_capacity(L) rows of n_scenes); the derivative pass adds
+// g . dI/dtheta into grad_acc over the table's packed segments (10 n_seg),
+// through gacc_scratch (10 n_seg floats) when they exceed a block's shared
+// memory (batch_shared_params()).
+cudaError_t launch_forward_batch(const Launcher& L, const WfScene* tab_dev, uint32_t n_scenes, uint32_t total,
+                                 const TraceParams& tp, const uint32_t* iter_dev, int loss_kind, double* loss_rows,
+                                 uint32_t* err, cudaStream_t st);
+cudaError_t launch_adjoint_batch(const Launcher& L, const WfScene* tab_dev, uint32_t n_scenes, uint32_t total,
+                                 uint32_t n_seg, const TraceParams& tp, const uint32_t* iter_dev, double* grad_acc,
+                                 float* gacc_scratch, uint32_t* err, cudaStream_t st);
+uint32_t batch_shared_params();
+
 }  // namespace ipt

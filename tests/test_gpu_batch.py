@@ -31,9 +31,9 @@ def uneven_scenes():
     ]
 
 
-def prepared(seed=5, slots=0, bvh_width=0):
+def prepared(seed=5, slots=0, bvh_width=0, integrator="wavefront"):
     ss = SceneSet(uneven_scenes(), seed=seed)
-    ss.configure("wavefront", wavefront_slots=slots, bvh_width=bvh_width)
+    ss.configure(integrator, wavefront_slots=slots, bvh_width=bvh_width)
     for i, sc in enumerate(ss.scenes):
         ss.set_params(i, sc.gt_params)
         ss.set_targets(i, ss.render(i, TraceOptions(max_depth=4), spp=32))
@@ -41,11 +41,14 @@ def prepared(seed=5, slots=0, bvh_width=0):
     return ss
 
 
-@pytest.mark.parametrize("slots,bvh_width", [(0, 4), (4096, 4), (2048, 2)])
-def test_batch_equals_single_scene_steps(built, slots, bvh_width):
+@pytest.mark.parametrize("slots,bvh_width,integrator", [(0, 4, "wavefront"), (4096, 4, "wavefront"),
+                                                        (2048, 2, "wavefront"), (0, 4, "megakernel")])
+def test_batch_equals_single_scene_steps(built, slots, bvh_width, integrator):
+    """On the megakernel the batch runs each pass as one launch over the
+    whole table (and the members alone on the single-scene megakernel)."""
     opts = TraceOptions(spp_r=8, spp_d=8, max_depth=4)
     adam = AdamOptions()
-    ss = prepared(slots=slots, bvh_width=bvh_width)
+    ss = prepared(slots=slots, bvh_width=bvh_width, integrator=integrator)
     init = [ss.params(i) for i in range(3)]
     ref_loss = [[], [], []]
     for i in range(3):
@@ -137,4 +140,24 @@ def test_inactive_member_is_frozen(built):
     ss.set_active([1, 1, 1])
     assert np.all(np.isfinite(ss.batch_step(opts, adam)))
     ss.synchronize()
+    ss.close()
+
+
+def test_megakernel_batch_with_pixel_batches_and_an_inactive_member(built):
+    """The batched megakernel with stochastic pixel batches: every active
+    member gets the loss it gets alone (same draw, same paths); an inactive
+    member keeps its parameters."""
+    opts = TraceOptions(spp_r=16, spp_d=2, max_depth=3, pixel_batch=48)
+    adam = AdamOptions()
+    ss = prepared(integrator="megakernel")
+    init = [ss.params(i) for i in range(3)]
+    ref = [ss.step(i, opts, adam) for i in range(3)]
+    for i in range(3):
+        ss.set_params(i, init[i])
+    ss.make_batch()
+    ss.set_active([1, 0, 1])
+    losses = ss.batch_step(opts, adam)
+    for i in (0, 2):
+        assert abs(losses[i] - ref[i]) <= 1e-6 * abs(ref[i]), (i, losses[i], ref[i])
+    assert losses[1] == 0.0 and np.array_equal(ss.batch_params(1), init[1])
     ss.close()
