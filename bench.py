@@ -422,7 +422,9 @@ def run_ours(args, rank, world, local):
 def run_batch64(args):
     """Aggregate fwd+adjoint Mpaths/s of one batch iteration over the 64
     uneven rooms (one launch per stage over all rooms, replayed as a CUDA
-    graph)."""
+    graph), or, with --workload cornell64, over the 64 Cornell variants in
+    the paper's pixel-batch regime (--pixel-batch, --batch-spp, --spp-d) on
+    --batch-integrator."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -430,14 +432,19 @@ def run_batch64(args):
     from paper_1903_07145_gb300.batch import SceneSet
     from paper_1903_07145_gb300.tracer import AdamOptions, TraceOptions
     t0 = time.perf_counter()
-    rooms = [scenes.batch_room(k, args.res_div) for k in range(64)]
+    cornell = args.workload == "cornell64"
+    rooms = ([scenes.cornell_variant(k) for k in range(64)] if cornell
+             else [scenes.batch_room(k, args.res_div) for k in range(64)])
     gen_s = time.perf_counter() - t0
-    opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.batch_spp, max_depth=args.batch_depth)
+    spp_d = args.spp_d or args.batch_spp
+    opts = TraceOptions(spp_r=args.batch_spp, spp_d=spp_d, max_depth=args.batch_depth,
+                        pixel_batch=args.pixel_batch)
     ss = SceneSet(rooms, seed=1903)
-    ss.configure(integrator="wavefront", wavefront_slots=1 << 21, bvh_width=4)
+    integ = "wavefront" if args.batch_integrator == "auto" else args.batch_integrator
+    ss.configure(integrator=integ, wavefront_slots=1 << 21, bvh_width=4)
     for i, sc in enumerate(rooms):
         ss.set_params(i, sc.gt_params)
-        ss.set_targets(i, ss.render(i, opts, spp=16))
+        ss.set_targets(i, ss.render(i, TraceOptions(max_depth=args.batch_depth), spp=16))
         ss.set_params(i, scenes.initial_params(sc, 0.5))
     ss.make_batch()
     adam = AdamOptions()
@@ -457,14 +464,17 @@ def run_batch64(args):
         torch.cuda.synchronize(dev)
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     pix = sum(c.width * c.height for sc in rooms for c in sc.cameras)
-    paths = 2 * args.batch_spp * pix
+    entries = 64 * args.pixel_batch if args.pixel_batch else pix
+    paths = (args.batch_spp + spp_d) * entries
+    name = (f"cornell64_variants_pixbatch{args.pixel_batch}" if cornell else f"batch64_rooms_div{args.res_div}")
     out = {"metric": METRIC, "value": paths / (ms * 1e-3) / 1e6, "unit": "Mpaths/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"batch64_rooms_div{args.res_div}", "rooms": 64,
+           "config": {"workload": name, "rooms": 64, "integrator": integ,
                       "triangles": int(sum(sc.indices.shape[0] for sc in rooms)),
                       "segments": int(sum(sc.n_segments for sc in rooms)), "pixels": int(pix),
-                      "spp_r": args.batch_spp, "spp_d": args.batch_spp, "max_depth": args.batch_depth,
+                      "pixel_batch": args.pixel_batch, "entries_per_step": int(entries),
+                      "spp_r": args.batch_spp, "spp_d": spp_d, "max_depth": args.batch_depth,
                       "l2": "256 MiB flush between timed steps (outside the step events)",
                       "generation_s": gen_s},
            "clocks": clk.summary()}
@@ -758,8 +768,9 @@ def main():
         WORKLOAD["cache"] = dict(b_term=args.cache, train_spp=max(1, WORKLOAD["spp_r"] // 16), train_steps=4,
                                  lr=1e-2)
     rank, world, local = dist_env()
-    if args.workload == "cornell64" and not args.time_to_error:
-        ap.error("--workload cornell64 is a time-to-error workload (add --time-to-error)")
+    if args.impl == "ours" and args.workload == "cornell64" and not args.time_to_error:
+        run_batch64(args)
+        return
     if args.impl == "ours" and args.time_to_error:
         run_time_to_error(args)
         return

@@ -353,7 +353,9 @@ __device__ __forceinline__ PathParams scene_params(const PathParams& base, const
 // Residual pass: the upstream gradient of every entry and, per block, each
 // scene's loss sum (rows[block * n_scenes + scene], the layout of the
 // wavefront's reduction).
-__global__ void __launch_bounds__(kBlockThreads)
+// Four resident blocks per SM (at most 128 registers), as the single-scene
+// forward: the grid is one loss row per block of a full wave.
+__global__ void __launch_bounds__(kBlockThreads, 4)
     k_forward_batch(const WfScene* tab, uint32_t n_scenes, uint32_t total, PathParams pp, uint32_t set,
                     const uint32_t* iter_dev, int loss_kind, double* loss_rows, uint32_t* err) {
   extern __shared__ double sloss[];
