@@ -560,17 +560,12 @@ __device__ __forceinline__ bool trace_any4(const SceneDev& s, float3 o, float3 d
           atomicOr(err, kErrStack);
           return true;
         }
-        const int first = __ffs(mask) - 1;
-        int next = ref[0];
+        // nearest first: an occluder near the shading point ends the search sooner
+        sort4(tn, ref);
 #pragma unroll
-        for (int i = 3; i >= 0; --i) {
-          if (!(mask & (1u << i))) continue;
-          if (i == first)
-            next = ref[i];
-          else
-            stack[sp++] = ref[i];
-        }
-        node = next;
+        for (int i = 3; i >= 1; --i)
+          if (i < k) stack[sp++] = ref[i];
+        node = ref[0];
         continue;
       }
     } else {

