@@ -186,7 +186,6 @@ template <class T>
 __device__ __forceinline__ T zero_like() {
   return Zero<T>::get();
 }
-using Dual13 = DualN<kDisneyMat>;
 
 __device__ __forceinline__ float schlick_w(float c) {
   const float m = fminf(1.0f, fmaxf(0.0f, 1.0f - c));
