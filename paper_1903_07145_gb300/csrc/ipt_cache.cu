@@ -764,7 +764,9 @@ template <bool kVjp>
 static cudaError_t launch_infer(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,
                                 const uint32_t* count_dev, uint32_t n, const CacheOut& out, int num_sms,
                                 cudaStream_t st) {
-  constexpr int W = kInferWarps, smem = infer_smem<W>();
+  // the VJP needs more than 64 registers: 12 warps per block keep two blocks
+  // per SM without spills
+  constexpr int W = kVjp ? 12 : kInferWarps, smem = infer_smem<W>();
   cudaError_t e = cudaFuncSetAttribute(cache_infer_k<kVjp, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   static int per_sm = 0;  // resident blocks per SM at this shared-memory size (the same on every GB300)
