@@ -630,7 +630,7 @@ def run_disney(args):
     for timing in (False, True):
         tr = Tracer(sc, seed=1903, flags=L.IPT_FLAG_KERNEL_TIMING if timing else 0)
         if integ == "wavefront":  # the configuration the autotuner picks for this room
-            tr.configure("wavefront", wavefront_slots=1 << 21, trace_steps=8, bvh_width=4)
+            tr.configure("wavefront", wavefront_slots=1 << 25, trace_steps=8, bvh_width=4)
         else:
             tr.configure("megakernel")
         tr.disney_set_params(truth)

@@ -1,7 +1,9 @@
 """Picks the integrator configuration of a context by measurement.
 
-Candidates: the megakernel, and the wavefront integrator with a few chunk
-sizes and traversal refill granularities.  Each candidate runs one
+Candidates: the megakernel, and the wavefront integrator with two chunk
+sizes (2M path slots, and 32M, which holds a whole pass of most workloads in
+one chunk: no drain tail between chunks, fewer launches) and two traversal
+refill granularities.  Each candidate runs one
 loss-and-gradient evaluation of the caller's workload (after one untimed
 run that allocates its buffers); the fastest by CUDA-event time wins and is
 left configured.  Every candidate traces the same paths, so the choice
@@ -16,7 +18,7 @@ import torch
 DEFAULT_CANDIDATES = (
     [dict(integrator="megakernel")]
     + [dict(integrator="wavefront", wavefront_slots=s, trace_steps=k, bvh_width=b)
-       for b, s, k in itertools.product([2, 4], [1 << 20, 1 << 21], [8, 16])]
+       for b, s, k in itertools.product([2, 4], [1 << 21, 1 << 25], [8, 16])]
 )
 
 
