@@ -16,8 +16,16 @@
  *   - Device work is queued on the context's CUDA stream.  Calls that return
  *     host data (loss, parameters) synchronise that stream first.
  *   - Argument errors are reported as IPT_ERR_INVALID_ARG before anything is
- *     launched.  Errors found on the device (a traversal stack overflow) set a
- *     status word that the next synchronising call returns as IPT_ERR_CUDA.
+ *     launched.  Errors found on the device set a status word that the next
+ *     synchronising call returns: a traversal stack overflow as IPT_ERR_CUDA,
+ *     a non-finite loss or gradient met by an Adam step as IPT_ERR_NONFINITE.
+ *   - Non-finite guard: every Adam step (ipt_adam_step, ipt_step,
+ *     ipt_batch_step per member, ipt_disney_step) first checks, on the device,
+ *     the gradient it is given and, for the context's own gradient, the loss
+ *     that came with it.  On a NaN or infinity it skips the update: the
+ *     parameters, Adam moments and Adam step count stay those of the last good
+ *     step (the iteration counter of ipt_step still advances, so the next step
+ *     draws new samples), and IPT_ERR_NONFINITE is reported.
  *   - ipt_last_error_detail gives a one-line description of the last error.
  *   - A context is bound to one device and one stream and is not thread-safe.
  *
@@ -370,13 +378,17 @@ ipt_status ipt_batch_destroy(ipt_ctx* ctx, int32_t batch);
  * an FP64 S x 10 gradient accumulator, is a file-scope __device__ array sized
  * for at most 1024 segments (80 KiB, held by every device that loads the
  * library until the process exits); a scene with more segments is rejected
- * with IPT_ERR_INVALID_ARG.  The first call on a device looks the array's
- * address up (cudaGetSymbolAddress); make that first call before any stream
- * capture.  The array is cleared at the start of every call, and all calls
- * share it: calls whose work overlaps on the GPU (other streams, other
- * contexts on the same device) race on it.  It always runs the plain
- * estimator on the megakernel integrator (a scene's radiance cache is not
- * used). */
+ * with IPT_ERR_INVALID_ARG.  The first call with each context looks the
+ * array's address on the context's device up (cudaGetSymbolAddress) and keeps
+ * it in the context; make that first call before any stream capture.  A
+ * device reset ends every context, and with it the kept address: create a
+ * new context after one.  The array is cleared at the start of every call,
+ * and all calls share it: calls whose work overlaps on the GPU (other
+ * streams, other contexts on the same device) race on it.  It always runs the
+ * plain estimator on the megakernel integrator (a scene's radiance cache is
+ * not used), whatever ipt_config_set selected.  With IPT_FLAG_KERNEL_TIMING
+ * its launches are timed like ipt_backward's (prepare, adjoint, finalize);
+ * the CUDA events this takes are host objects, not device memory. */
 ipt_status ipt_backward_noalloc(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts, uint32_t set,
                                 uint64_t iteration, const float* params, const float* sampling_params,
                                 const float* grad_image, float* grad_out);
@@ -575,13 +587,23 @@ ipt_status ipt_disney_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* op
 
 /* Measurement support (not part of the method).  Achievable bandwidth, in
  * GB/s (1e9 bytes), of random 64-byte line gathers over a device buffer of
- * `bytes` bytes on `device`: four independent gathers in flight per thread,
- * 8 blocks of 256 threads per SM, best of three timed runs after a warm-up.
+ * `bytes` bytes on `device`: each line read with two 256-bit read-only loads
+ * (as the traversal reads a node), four independent gathers in flight per
+ * thread, 8 blocks of 256 threads per SM, about 10 ms per timed run, best of
+ * three timed runs after a warm-up.
  * This is the access pattern of BVH traversal, and with the size of a
  * scene's node and triangle arrays the denominator of its roofline.  The
  * buffer is allocated and freed inside the call.  Errors: bytes < 64 KiB or
  * above 2^32 lines, out of memory, CUDA failures. */
 ipt_status ipt_probe_gather(int32_t device, uint64_t bytes, double* gbs_out);
+
+/* Build check (not part of the method): the binary version (major * 10 +
+ * minor of the SM architecture, 103 for sm_103a) and PTX version the device
+ * runs the library's kernels from, as cudaFuncGetAttributes reports them for
+ * one of its kernels on `device`.  Either output may be NULL, not both.
+ * Errors: IPT_ERR_CUDA when the device cannot load the kernels (for example a
+ * GPU other than compute capability 10.3). */
+ipt_status ipt_build_info(int32_t device, int32_t* binary_version, int32_t* ptx_version);
 
 #ifdef __cplusplus
 }

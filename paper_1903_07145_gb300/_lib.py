@@ -30,7 +30,7 @@ EXPORTED = [
     "ipt_batch_create", "ipt_batch_step", "ipt_batch_params_get", "ipt_batch_destroy", "ipt_batch_set_active",
     "ipt_cache_configure", "ipt_cache_weights_set", "ipt_cache_weights_get", "ipt_cache_eval",
     "ipt_cache_grad", "ipt_cache_train", "ipt_cache_records", "ipt_cache_status", "ipt_cache_bias",
-    "ipt_probe_gather", "ipt_checkpoint_save", "ipt_checkpoint_load",
+    "ipt_probe_gather", "ipt_build_info", "ipt_checkpoint_save", "ipt_checkpoint_load",
     "ipt_disney_params_set", "ipt_disney_params_get", "ipt_disney_render", "ipt_disney_loss_grad",
     "ipt_disney_step",
 ]
@@ -150,6 +150,7 @@ def lib():
                 "ipt_cache_bias": [P, I32, C.POINTER(ipt_trace_opts), U32, U64, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)],
                 "ipt_probe_gather": [I32, U64, C.POINTER(C.c_double)],
+                "ipt_build_info": [I32, C.POINTER(I32), C.POINTER(I32)],
                 "ipt_disney_params_set": [P, I32, P, P],
                 "ipt_disney_params_get": [P, I32, P],
                 "ipt_disney_render": [P, I32, I32, C.POINTER(ipt_trace_opts), U32, U32, U64, P, P, P],
@@ -424,3 +425,11 @@ def ipt_probe_gather(device, nbytes):
     gbs = C.c_double()
     _check(None, lib().ipt_probe_gather(device, nbytes, C.byref(gbs)))
     return gbs.value
+
+
+def ipt_build_info(device):
+    """(binary version, PTX version) of the library's kernels on `device`."""
+    b = C.c_int32()
+    p = C.c_int32()
+    _check(None, lib().ipt_build_info(device, C.byref(b), C.byref(p)))
+    return b.value, p.value

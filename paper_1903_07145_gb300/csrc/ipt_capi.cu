@@ -5,7 +5,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <algorithm>
 #include <string>
@@ -129,6 +128,8 @@ struct DeviceScene {
   float* grad_f = nullptr;
   double* loss_partials = nullptr;
   double* loss_dev = nullptr;
+  uint32_t* guard_dev = nullptr;  // the Adam step's finiteness decision (scenes over a grid)
+  bool loss_fresh = false;        // loss_dev holds the loss of the gradient in grad_acc
   uint64_t iteration = 0;
   float bb_lo[3] = {0.f, 0.f, 0.f}, bb_hi[3] = {1.f, 1.f, 1.f};  // vertex bounding box
   CacheState* cache = nullptr;
@@ -195,6 +196,7 @@ struct ipt_ctx {
   ipt::WfScene* wf_tab = nullptr;  // one-entry scene table of single-scene launches
   std::vector<Batch*> batches;
   cudaStream_t cap_stream = nullptr;  // stream the batch graphs are captured on
+  double* noalloc_acc = nullptr;      // device address of ipt_backward_noalloc's array on this device
 };
 
 namespace {
@@ -827,6 +829,7 @@ ipt_status ipt_scene_upload(ipt_ctx* ctx, const float* pos, uint32_t n_vert, con
   A(&s->grad_f, 10 * (size_t)S);
   A(&s->loss_partials, (size_t)ipt::loss_partials_capacity(ctx->L));
   A(&s->loss_dev, 1);
+  A(&s->guard_dev, 1);
   auto H = [&](void* dst, const void* src, size_t bytes) {
     if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
   };
@@ -987,6 +990,7 @@ ipt_status ipt_backward(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* opts,
   if ((st = ensure_tables(ctx, s, p, sampling_params)) != IPT_OK) return st;
   const uint32_t np = 10u * s->n_seg;
   IPT_CK(cudaMemsetAsync(s->grad_acc, 0, np * sizeof(double), ctx->stream));
+  s->loss_fresh = false;  // grad_acc now holds a vector-Jacobian product, not a loss gradient
   ipt::CachePass cp;
   if (cache_on(s) && (st = cache_pass(ctx, s, false, &cp)) != IPT_OK) return st;
   st = run_adjoint(ctx, scene, s, 0, (uint32_t)s->n_pix,
@@ -1037,6 +1041,7 @@ static ipt_status loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScene* s, c
   Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(s->loss_partials, ipt::loss_partials_capacity(ctx->L), s->loss_dev, s->grad_acc,
                               grad_out, np, ctx->stream));
+  s->loss_fresh = true;
   return IPT_OK;
 }
 
@@ -1092,8 +1097,10 @@ ipt_status ipt_adam_step(ipt_ctx* ctx, int32_t scene, const float* grad, const i
     return fail(ctx, IPT_ERR_INVALID_ARG, "invalid adam options");
   IPT_CK(cudaSetDevice(ctx->device));
   Timed tm(ctx, IPT_KERNEL_ADAM);
+  // the loss is checked with the context's own gradient (the one it belongs to)
+  const double* loss = (grad == nullptr && s->loss_fresh) ? s->loss_dev : nullptr;
   IPT_CK(ipt::launch_adam(buffers(ctx, s), s->tab, s->params, s->adam_m, s->adam_v, s->free_mask, s->grad_acc, grad,
-                          s->step_dev, adam_host(adam), ctx->stream));
+                          s->step_dev, adam_host(adam), loss, s->guard_dev, ctx->err_dev, ctx->stream));
   s->tab_is_ctx = true;  // the Adam kernel rebuilt the tables from the new parameters
   return IPT_OK;
 }
@@ -1152,7 +1159,11 @@ ipt_status ipt_synchronize(ipt_ctx* ctx) {
   IPT_CK(cudaMemcpy(&err, ctx->err_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   if (err) {
     cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
-    return fail(ctx, IPT_ERR_CUDA, "device error word " + std::to_string(err) + " (traversal stack overflow)");
+    if (err & ipt::kErrStack)
+      return fail(ctx, IPT_ERR_CUDA, "device error word " + std::to_string(err) + " (traversal stack overflow)");
+    return fail(ctx, IPT_ERR_NONFINITE,
+                "non-finite loss or gradient: the Adam step was skipped, parameters and Adam state are those of "
+                "the last good step");
   }
   return IPT_OK;
 }
@@ -1377,7 +1388,7 @@ static ipt_status batch_enqueue(ipt_ctx* ctx, Batch* b, const ipt_trace_opts* op
   IPT_CK(ipt::launch_batch_losses(b->loss_rows, ipt::loss_partials_capacity(ctx->L), b->mem_dev, n,
                                   (uint32_t)b->tab_host.size(), b->losses_dev, st));
   IPT_CK(ipt::launch_adam_batch(b->mem_dev, n, b->params, b->adam_m, b->adam_v, b->free_mask, b->grad_acc,
-                                b->iter_dev, adam_host(adam), st));
+                                b->iter_dev, adam_host(adam), b->losses_dev, ctx->err_dev, st));
   IPT_CK(ipt::launch_tick(b->iter_dev, st));
   return IPT_OK;
 }
@@ -1530,30 +1541,26 @@ ipt_status ipt_counters_read(ipt_ctx* ctx, uint64_t* out, int32_t reset) {
 // memory.  Its only scratch, the FP64 gradient accumulator, is this file-scope
 // array: 10 * kNoAllocMaxSegments doubles (80 KiB) that every device which
 // loads the library keeps until the process exits.  Host code only sees a
-// stand-in for the array; the device address is looked up once per device,
-// with that device current, and handed to the kernels.
+// stand-in for the array; the device address is looked up by the first call
+// with each context, with the context's device current, kept in the context
+// (a device reset ends every context, so no address outlives one) and
+// handed to the kernels.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr uint32_t kNoAllocMaxSegments = 1024;
-constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_grad[10 * kNoAllocMaxSegments];
 
-std::mutex g_noalloc_lock;
-double* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
-
-// Device address of g_noalloc_grad on `device` (which must be current).
-cudaError_t noalloc_scratch(int device, double** out) {
-  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> guard(g_noalloc_lock);
-  if (!g_noalloc_addr[device]) {
+// Device address of g_noalloc_grad on the context's device (current).
+cudaError_t noalloc_scratch(ipt_ctx* ctx, double** out) {
+  if (!ctx->noalloc_acc) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_grad);
     if (e != cudaSuccess) return e;
-    g_noalloc_addr[device] = static_cast<double*>(p);
+    ctx->noalloc_acc = static_cast<double*>(p);
   }
-  *out = g_noalloc_addr[device];
+  *out = ctx->noalloc_acc;
   return cudaSuccess;
 }
 
@@ -1576,18 +1583,23 @@ extern "C" ipt_status ipt_backward_noalloc(ipt_ctx* ctx, int32_t scene, const ip
                                               std::to_string(s->n_seg));
   IPT_CK(cudaSetDevice(ctx->device));
   double* acc = nullptr;
-  IPT_CK(noalloc_scratch(ctx->device, &acc));
+  IPT_CK(noalloc_scratch(ctx, &acc));
   const float* p = params ? params : s->params;
   const bool is_ctx = (p == s->params) && (sampling_params == nullptr || sampling_params == s->params);
   if (!(is_ctx && s->tab_is_ctx)) {
+    Timed tm(ctx, IPT_KERNEL_PREPARE);
     IPT_CK(ipt::launch_prepare(buffers(ctx, s), s->tab, p, sampling_params ? sampling_params : p, ctx->stream));
     s->tab_is_ctx = is_ctx;
   }
   const uint32_t np = 10u * s->n_seg;
   IPT_CK(cudaMemsetAsync(acc, 0, np * sizeof(double), ctx->stream));
-  IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), 0,
-                             (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
-                             grad_image, acc, nullptr, ctx->err_dev, ctx->stream));
+  {
+    Timed tm(ctx, IPT_KERNEL_ADJOINT);
+    IPT_CK(ipt::launch_adjoint(ctx->L, buffers(ctx, s), s->tab, s->views_dev, (uint32_t)s->views.size(), 0,
+                               (uint32_t)s->n_pix, trace_params(ctx, scene, opts, set, opts->spp_d, iteration),
+                               grad_image, acc, nullptr, ctx->err_dev, ctx->stream));
+  }
+  Timed tm(ctx, IPT_KERNEL_FINALIZE);
   IPT_CK(ipt::launch_finalize(nullptr, 0, nullptr, acc, grad_out, np, ctx->stream));
   return IPT_OK;
 }
@@ -2411,7 +2423,8 @@ ipt_status ipt_disney_step(ipt_ctx* ctx, int32_t scene, const ipt_trace_opts* op
   {
     Timed tm(ctx, IPT_KERNEL_ADAM);
     IPT_CK(ipt::launch_disney_adam(buffers(ctx, s), d->tab, d->dt, d->params, d->adam_m, d->adam_v, d->free_mask,
-                                   d->grad_acc, nullptr, d->step_dev, adam_host(adam), ctx->stream));
+                                   d->grad_acc, nullptr, d->step_dev, adam_host(adam), s->loss_dev, ctx->err_dev,
+                                   ctx->stream));
   }
   d->tab_is_ctx = true;  // the Adam kernel rebuilt the tables from the new parameters
   d->iteration++;

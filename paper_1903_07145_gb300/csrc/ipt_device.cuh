@@ -10,7 +10,8 @@ namespace ipt {
 
 constexpr float kPi = 3.14159265358979323846f;
 constexpr int kStackSize = 64;
-constexpr uint32_t kErrStack = 1u;  // traversal stack would overflow
+constexpr uint32_t kErrStack = 1u;      // traversal stack would overflow
+constexpr uint32_t kErrNonFinite = 2u;  // a loss or gradient was NaN or infinite: the Adam step was skipped
 
 // ---------------------------------------------------------------------------
 // float3 algebra

@@ -72,13 +72,21 @@ __global__ void k_disney_tables(const float* params, const float* sparams, uint3
   disney_tables_body(params, sparams, S, es, seg_area, t, d);
 }
 
+// A non-finite loss or gradient skips the update (parameters, moments and
+// step count unchanged) and sets the error word; the tables are rebuilt
+// either way.
 __global__ void k_disney_adam(float* params, float* m, float* v, const uint8_t* free_mask, const double* grad_acc,
                               const float* grad_f, int* step_dev, AdamHost a, uint32_t S, float es,
-                              const double* seg_area, SegBuffers t, DisneyBuffers d) {
+                              const double* seg_area, SegBuffers t, DisneyBuffers d, const double* loss,
+                              uint32_t* err) {
   const int step = *step_dev + 1;
   const float bc1 = 1.0f - powf(a.beta1, (float)step);
   const float bc2 = 1.0f - powf(a.beta2, (float)step);
-  for (uint32_t i = threadIdx.x; i < kDisneyStride * S; i += blockDim.x) {
+  bool bad = loss && !isfinite(*loss);
+  for (uint32_t i = threadIdx.x; i < kDisneyStride * S && !bad; i += blockDim.x)
+    bad = grad_f ? !isfinite(grad_f[i]) : !isfinite(grad_acc[i]);
+  bad = __syncthreads_or(bad) != 0;
+  for (uint32_t i = threadIdx.x; !bad && i < kDisneyStride * S; i += blockDim.x) {
     if (free_mask && !free_mask[i]) continue;
     const uint32_t j = i % kDisneyStride;
     float g = grad_f ? grad_f[i] : (float)grad_acc[i];
@@ -96,7 +104,12 @@ __global__ void k_disney_adam(float* params, float* m, float* v, const uint8_t* 
     params[i] = nt;
   }
   __syncthreads();
-  if (threadIdx.x == 0) *step_dev = step;
+  if (threadIdx.x == 0) {
+    if (bad)
+      atomicOr(err, kErrNonFinite);
+    else
+      *step_dev = step;
+  }
   disney_tables_body(params, params, S, es, seg_area, t, d);
 }
 
@@ -486,9 +499,10 @@ cudaError_t launch_disney_adjoint(const Launcher& L, const SceneBuffers& s, cons
 
 cudaError_t launch_disney_adam(const SceneBuffers& s, const SegBuffers& t, const DisneyBuffers& d, float* params,
                                float* m, float* v, const uint8_t* free_mask, const double* grad_acc,
-                               const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st) {
+                               const float* grad_f, int* step_dev, const AdamHost& a, const double* loss,
+                               uint32_t* err, cudaStream_t st) {
   k_disney_adam<<<1, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg,
-                                   s.emission_scale, s.seg_area, t, d);
+                                   s.emission_scale, s.seg_area, t, d, loss, err);
   return cudaGetLastError();
 }
 

@@ -148,9 +148,14 @@ struct AdamHost {
   float lr, beta1, beta2, eps, l1;
 };
 
+// Adam on a scene's parameters.  loss (device, nullable) and the gradient are
+// checked first: if either is not finite the step is skipped (parameters,
+// moments and step count unchanged) and kErrNonFinite is set in *err.  guard:
+// a device word the check of scenes above kWideSegments segments writes.
 cudaError_t launch_adam(const SceneBuffers& s, const SegBuffers& t, float* params, float* m,
                         float* v, const uint8_t* free_mask, const double* grad_acc,
-                        const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st);
+                        const float* grad_f, int* step_dev, const AdamHost& a, const double* loss,
+                        uint32_t* guard, uint32_t* err, cudaStream_t st);
 
 // One member scene of a batch: where its parameters sit in the batch's
 // concatenated vector, and its parameter tables.
@@ -166,10 +171,11 @@ struct BatchMember {
 };
 
 // Adam over the whole batch (block b updates member b, then rebuilds its
-// tables); step t = *iter_dev + 1.
+// tables); step t = *iter_dev + 1.  A member whose loss (losses[b]) or
+// gradient is not finite is skipped and kErrNonFinite is set in *err.
 cudaError_t launch_adam_batch(const BatchMember* members, uint32_t n_members, float* params, float* m, float* v,
                               const uint8_t* free_mask, const double* grad_acc, const uint32_t* iter_dev,
-                              const AdamHost& a, cudaStream_t st);
+                              const AdamHost& a, const double* losses, uint32_t* err, cudaStream_t st);
 // Tables of every member from the batch parameters.
 cudaError_t launch_prepare_batch(const BatchMember* members, uint32_t n_members, const float* params,
                                  cudaStream_t st);
@@ -223,9 +229,11 @@ cudaError_t launch_disney_adjoint(const Launcher& L, const SceneBuffers& s, cons
                                   double* grad_acc, float* gacc_scratch, uint32_t* err, cudaStream_t st);
 // Adam with the Disney clamps (material values in [0, 1], roughness in
 // [0.02, 1], emission >= 0 with the L1 term), then the tables.
+// As launch_adam (the same check of loss and gradient), for the Disney blocks.
 cudaError_t launch_disney_adam(const SceneBuffers& s, const SegBuffers& t, const DisneyBuffers& d, float* params,
                                float* m, float* v, const uint8_t* free_mask, const double* grad_acc,
-                               const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st);
+                               const float* grad_f, int* step_dev, const AdamHost& a, const double* loss,
+                               uint32_t* err, cudaStream_t st);
 uint32_t disney_max_shared_segments();
 
 }  // namespace ipt

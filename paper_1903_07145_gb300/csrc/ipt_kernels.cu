@@ -513,14 +513,31 @@ __device__ __forceinline__ void adam_range(float* params, float* m, float* v, co
   }
 }
 
+// True on every thread of the block when the loss (nullable) or any of the n
+// gradient values (FP64 accumulators, or FP32 when grad_f is given) is NaN or
+// infinite.
+__device__ __forceinline__ bool block_nonfinite(const double* loss, const double* grad_acc, const float* grad_f,
+                                                uint32_t n) {
+  bool bad = loss && !isfinite(*loss);
+  for (uint32_t i = threadIdx.x; i < n && !bad; i += blockDim.x)
+    bad = grad_f ? !isfinite(grad_f[i]) : !isfinite(grad_acc[i]);
+  return __syncthreads_or(bad) != 0;
+}
+
+// A member whose loss or gradient is not finite keeps its parameters and
+// Adam moments (the step is skipped for it alone) and sets the error word.
 __global__ void k_adam_batch(const BatchMember* members, float* params, float* m, float* v,
                              const uint8_t* free_mask, const double* grad_acc, const uint32_t* iter_dev,
-                             AdamHost a) {
+                             AdamHost a, const double* losses, uint32_t* err) {
   const BatchMember mb = members[blockIdx.x];
   if (!mb.active) return;
   const int step = (int)*iter_dev + 1;
-  adam_range(params, m, v, free_mask, grad_acc, nullptr, 10u * mb.seg_offset, 10u * (mb.seg_offset + mb.n_seg),
-             10u * mb.grad_offset, a, step, threadIdx.x, blockDim.x);
+  if (block_nonfinite(losses + blockIdx.x, grad_acc + 10u * mb.grad_offset, nullptr, 10u * mb.n_seg)) {
+    if (threadIdx.x == 0) atomicOr(err, kErrNonFinite);
+  } else {
+    adam_range(params, m, v, free_mask, grad_acc, nullptr, 10u * mb.seg_offset, 10u * (mb.seg_offset + mb.n_seg),
+               10u * mb.grad_offset, a, step, threadIdx.x, blockDim.x);
+  }
   __syncthreads();
   const float* p = params + 10u * mb.seg_offset;
   build_tables(p, p, mb.n_seg, mb.es, mb.seg_area, mb.tab);
@@ -556,14 +573,35 @@ __global__ void k_batch_losses(const double* rows, int n_rows, const BatchMember
 
 __global__ void k_tick(uint32_t* counter) { *counter += 1u; }
 
+// With a non-finite loss or gradient the update is skipped: parameters, Adam
+// moments and the step count stay those of the last good step, and the
+// error word reports it.  The tables are rebuilt either way.
 __global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_mask,
                        const double* grad_acc, const float* grad_f, int* step_dev, AdamHost a, uint32_t S,
-                       float es, const double* seg_area, SegBuffers t) {
+                       float es, const double* seg_area, SegBuffers t, const double* loss, uint32_t* err) {
   const int step = *step_dev + 1;
-  adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, 0u, a, step, threadIdx.x, blockDim.x);
+  const bool bad = block_nonfinite(loss, grad_acc, grad_f, 10u * S);
+  if (!bad) adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, 0u, a, step, threadIdx.x, blockDim.x);
   __syncthreads();
-  if (threadIdx.x == 0) *step_dev = step;
+  if (threadIdx.x == 0) {
+    if (bad)
+      atomicOr(err, kErrNonFinite);
+    else
+      *step_dev = step;
+  }
   build_tables(params, params, S, es, seg_area, t);
+}
+
+// The same check for launches over a grid: one block decides, *flag = 1
+// when the step must be skipped.
+__global__ void __launch_bounds__(1024) k_finite_guard(const double* loss, const double* grad_acc,
+                                                       const float* grad_f, uint32_t n, uint32_t* flag,
+                                                       uint32_t* err) {
+  const bool bad = block_nonfinite(loss, grad_acc, grad_f, n);
+  if (threadIdx.x == 0) {
+    *flag = bad ? 1u : 0u;
+    if (bad) atomicOr(err, kErrNonFinite);
+  }
 }
 
 // Scenes with many segments (per-triangle parameters): Adam over a grid, the
@@ -575,7 +613,8 @@ __global__ void k_adam(float* params, float* m, float* v, const uint8_t* free_ma
 constexpr uint32_t kWideSegments = 4096;
 
 __global__ void k_adam_wide(float* params, float* m, float* v, const uint8_t* free_mask, const double* grad_acc,
-                            const float* grad_f, const int* step_dev, AdamHost a, uint32_t S) {
+                            const float* grad_f, const int* step_dev, AdamHost a, uint32_t S, const uint32_t* skip) {
+  if (*skip) return;
   const int step = *step_dev + 1;
   adam_range(params, m, v, free_mask, grad_acc, grad_f, 0, 10u * S, 0u, a, step,
              blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
@@ -599,9 +638,10 @@ __global__ void k_tables_seg(const float* params, const float* sparams, uint32_t
   }
 }
 
-// One block of 1024 threads; bumps *step_dev when given (after Adam).
+// One block of 1024 threads; bumps *step_dev when given (after Adam) unless
+// *skip says the Adam step was skipped.
 __global__ void __launch_bounds__(1024) k_tables_cdf(uint32_t S, const double* seg_area, SegBuffers t,
-                                                     int* step_dev) {
+                                                     int* step_dev, const uint32_t* skip) {
   __shared__ double term[1024];
   __shared__ unsigned nz[32];
   __shared__ double warp_end[32];
@@ -641,7 +681,7 @@ __global__ void __launch_bounds__(1024) k_tables_cdf(uint32_t S, const double* s
   }
   if (tid == 0) {
     *t.W = carry;
-    if (step_dev) *step_dev += 1;
+    if (step_dev && !(skip && *skip)) *step_dev += 1;
   }
 }
 
@@ -656,10 +696,10 @@ __global__ void k_tables_samp(const float* sparams, uint32_t S, SegBuffers t) {
 }
 
 static cudaError_t launch_tables_wide(const SceneBuffers& s, const SegBuffers& t, const float* params,
-                                      const float* sparams, int* step_dev, cudaStream_t st) {
+                                      const float* sparams, int* step_dev, const uint32_t* skip, cudaStream_t st) {
   const int grid = (int)std::min<uint32_t>((s.n_seg + 255u) / 256u, 1024u);
   k_tables_seg<<<grid, 256, 0, st>>>(params, sparams, s.n_seg, s.emission_scale, t);
-  k_tables_cdf<<<1, 1024, 0, st>>>(s.n_seg, s.seg_area, t, step_dev);
+  k_tables_cdf<<<1, 1024, 0, st>>>(s.n_seg, s.seg_area, t, step_dev, skip);
   k_tables_samp<<<grid, 256, 0, st>>>(sparams, s.n_seg, t);
   return cudaGetLastError();
 }
@@ -729,7 +769,7 @@ static int grid_for(uint64_t n_tasks_warps, int blocks_cap) {
 
 cudaError_t launch_prepare(const SceneBuffers& s, const SegBuffers& t, const float* params,
                            const float* sparams, cudaStream_t st) {
-  if (s.n_seg > kWideSegments) return launch_tables_wide(s, t, params, sparams ? sparams : params, nullptr, st);
+  if (s.n_seg > kWideSegments) return launch_tables_wide(s, t, params, sparams ? sparams : params, nullptr, nullptr, st);
   k_prepare<<<1, 256, 0, st>>>(params, sparams ? sparams : params, s.n_seg, s.emission_scale, s.seg_area, t);
   return cudaGetLastError();
 }
@@ -856,21 +896,23 @@ cudaError_t launch_finalize(const double* loss_partials, int n_partials, double*
 
 cudaError_t launch_adam(const SceneBuffers& s, const SegBuffers& t, float* params, float* m,
                         float* v, const uint8_t* free_mask, const double* grad_acc,
-                        const float* grad_f, int* step_dev, const AdamHost& a, cudaStream_t st) {
+                        const float* grad_f, int* step_dev, const AdamHost& a, const double* loss,
+                        uint32_t* guard, uint32_t* err, cudaStream_t st) {
   if (s.n_seg > kWideSegments) {
+    k_finite_guard<<<1, 1024, 0, st>>>(loss, grad_acc, grad_f, 10u * s.n_seg, guard, err);
     const int grid = (int)std::min<uint32_t>((10u * s.n_seg + 255u) / 256u, 2048u);
-    k_adam_wide<<<grid, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg);
-    return launch_tables_wide(s, t, params, params, step_dev, st);
+    k_adam_wide<<<grid, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg, guard);
+    return launch_tables_wide(s, t, params, params, step_dev, guard, st);
   }
   k_adam<<<1, 256, 0, st>>>(params, m, v, free_mask, grad_acc, grad_f, step_dev, a, s.n_seg,
-                            s.emission_scale, s.seg_area, t);
+                            s.emission_scale, s.seg_area, t, loss, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adam_batch(const BatchMember* members, uint32_t n_members, float* params, float* m, float* v,
                               const uint8_t* free_mask, const double* grad_acc, const uint32_t* iter_dev,
-                              const AdamHost& a, cudaStream_t st) {
-  k_adam_batch<<<n_members, 256, 0, st>>>(members, params, m, v, free_mask, grad_acc, iter_dev, a);
+                              const AdamHost& a, const double* losses, uint32_t* err, cudaStream_t st) {
+  k_adam_batch<<<n_members, 256, 0, st>>>(members, params, m, v, free_mask, grad_acc, iter_dev, a, losses, err);
   return cudaGetLastError();
 }
 

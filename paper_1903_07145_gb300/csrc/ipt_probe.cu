@@ -1,9 +1,11 @@
 // Measurement support, not part of the method: the achievable bandwidth of
 // random 64-byte line gathers over a device buffer of a given size, the
 // access pattern of BVH traversal (a 64-byte node or a 48-byte triangle per
-// fetch, incoherent across lanes).  It is the denominator of the traversal
-// kernels' roofline: with the scene's node and triangle arrays (a few MB)
-// the gathers stay in L2.
+// fetch, incoherent across lanes), each line fetched with the two 256-bit
+// read-only loads the traversal issues for a node.  It is the denominator of
+// the traversal kernels' roofline: with the scene's node and triangle arrays
+// (a few MB) the gathers stay in L2.  Also the build check: which binary
+// version the device runs the library's kernels from.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,7 +41,13 @@ __global__ void __launch_bounds__(kThreads) probe_gather_k(const uint4* buf, uin
       s[k] ^= s[k] << 5;
       const uint32_t line = __umulhi(s[k], n_lines);
       const uint4* p = buf + 4 * (size_t)line;
-      const uint4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+      uint4 a, b, c, d;
+      asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                   : "l"(p));
+      asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w), "=r"(d.x), "=r"(d.y), "=r"(d.z), "=r"(d.w)
+                   : "l"(p + 2));
       acc.x ^= a.x ^ b.y ^ c.z ^ d.w;
       acc.y ^= a.y ^ b.z ^ c.w ^ d.x;
       acc.z ^= a.z ^ b.w ^ c.x ^ d.y;
@@ -75,7 +83,8 @@ extern "C" ipt_status ipt_probe_gather(int32_t device, uint64_t bytes, double* g
   } else {
     probe_fill_k<<<sms * 8, kThreads, 0, st>>>(reinterpret_cast<uint32_t*>(buf), (size_t)n_lines * 16);
     const int grid = sms * 8;
-    const uint32_t iters = 64;
+    // about 12 ms of gathers per timed run at 6 TB/s
+    const uint32_t iters = 896;
     const double bytes_moved = (double)grid * kThreads * iters * kStreams * 64.0;
     float best = 1e30f;
     for (int rep = 0; rep < 4; ++rep) {
@@ -97,4 +106,14 @@ extern "C" ipt_status ipt_probe_gather(int32_t device, uint64_t bytes, double* g
   if (buf) cudaFree(buf);
   if (sink) cudaFree(sink);
   return status;
+}
+
+extern "C" ipt_status ipt_build_info(int32_t device, int32_t* binary_version, int32_t* ptx_version) {
+  if (!binary_version && !ptx_version) return IPT_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return IPT_ERR_CUDA;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, probe_gather_k) != cudaSuccess) return IPT_ERR_CUDA;
+  if (binary_version) *binary_version = fa.binaryVersion;
+  if (ptx_version) *ptx_version = fa.ptxVersion;
+  return IPT_OK;
 }

@@ -191,6 +191,7 @@ struct Trav {
   float tmax;
   int skip_a, skip_b;
   int node, sp;
+  int tri, tri_end;  // 4-wide traversal: triangles of the current leaf still to test
   uint2 deep[kStackSize - kShortStack];
   int best, best_orig;
   float bt, bu, bv;
@@ -220,6 +221,7 @@ __device__ __forceinline__ void trav_init(Trav& T, float3 o, float3 d, float tma
   T.skip_b = skip_b;
   T.node = 0;
   T.sp = 0;
+  T.tri = T.tri_end = 0;
   T.best = -1;
   T.best_orig = 0x7fffffff;
   T.bt = tmax;
@@ -302,12 +304,61 @@ __device__ __forceinline__ bool trav_run2(const SceneDev& s, Trav& T, uint2* sh,
   return false;
 }
 
+// Makes link `ref` the lane's next unit of work: an inner node to test, or
+// the triangle range of a leaf.
+__device__ __forceinline__ void trav_enter(Trav& T, int ref) {
+  if (ref >= 0) {
+    T.node = ref;
+  } else {
+    int first, count;
+    decode_leaf(ref, first, count);
+    T.node = -1;
+    T.tri = first;
+    T.tri_end = first + count;
+    T.n_tests += count;
+  }
+}
+
+// One triangle of the current leaf; true when a shadow ray is blocked.
+template <bool kAny>
+__device__ __forceinline__ bool tri_unit(const SceneDev& s, Trav& T) {
+  const int i = T.tri++;
+  if (i == T.skip_a || i == T.skip_b) return false;
+  const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+  const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+  const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+  float t, u, v;
+  if (kAny) {
+    if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.tmax, t, u, v)) {
+      T.occluded = true;
+      return true;
+    }
+  } else if (tri_test(T.r, xyz(q0), xyz(q1), xyz(q2), T.bt * 1.0000002f, t, u, v)) {
+    const int orig = __float_as_int(q0.w);
+    if (t < T.bt || (t == T.bt && orig < T.best_orig)) {
+      T.best = i;
+      T.bt = t;
+      T.bu = u;
+      T.bv = v;
+      T.best_orig = orig;
+    }
+  }
+  return false;
+}
+
 // 4-wide quantized nodes: hit children nearest first; popped entries
-// farther than the current hit are skipped (closest hit).
+// farther than the current hit are skipped (closest hit).  Each step of a
+// lane is one unit of work, a node test or a single triangle test, so lanes
+// inside leaves of different sizes and lanes testing nodes stay in step (a
+// whole leaf per step made most steps of a warp run both a node test and a
+// loop of up to eight triangle tests).
 template <bool kAny>
 __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh, int steps, uint32_t* err) {
   for (int it = 0; it < steps; ++it) {
-    if (T.node >= 0) {
+    if (T.tri < T.tri_end) {
+      if (tri_unit<kAny>(s, T)) return true;
+      if (T.tri < T.tri_end) continue;
+    } else if (T.node >= 0) {
       ++T.n_nodes;
       float tn[4];
       int ref[4];
@@ -327,11 +378,9 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh,
 #pragma unroll
         for (int i = 3; i >= 1; --i)
           if (i < k) st_push(sh, T, ref[i], tn[i]);
-        T.node = ref[0];
+        trav_enter(T, ref[0]);
         continue;
       }
-    } else if (leaf_tests<kAny>(s, T, T.node)) {
-      return true;
     }
     uint2 e;
     for (;;) {
@@ -339,7 +388,7 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh,
       e = st_pop(sh, T);
       if (kAny || __uint_as_float(e.y) <= T.bt * 1.0000005f) break;
     }
-    T.node = (int)e.x;
+    trav_enter(T, (int)e.x);
   }
   return false;
 }

@@ -30,6 +30,8 @@ def test_backward_noalloc_matches_backward_twice():
 
     sc = scenes.cornell_box(1000, 32, 32)
     tr = Tracer(sc, seed=11)
+    # the reference runs on the integrator the no-allocation call always uses
+    tr.configure("megakernel")
     p = sc.gt_params.copy()
     p[:, 7:10] += 0.1
     tr.set_params(p)
