@@ -154,8 +154,12 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def recorded_traffic(kernel, workload, cfg):
-    """DRAM bytes (read + write) per launch, or None."""
+def recorded_traffic(kernel, cfg, rays_per_launch):
+    """DRAM bytes (read + write) per launch, or None: the committed record's
+    bytes per ray, from an ncu capture of the same kernel on a small case of
+    the workload, times this run's rays per launch.  The per-ray traffic is
+    the queue and path state each ray reads and writes (the nodes and
+    triangles stay in L2), so it scales with the rays a launch processes."""
     try:
         with open(TRAFFIC_FILE) as fh:
             lines = fh.read().splitlines()
@@ -166,12 +170,12 @@ def recorded_traffic(kernel, workload, cfg):
         if ":" in line and not line.lstrip().startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    want = {"kernel": kernel, "workload": workload, "wavefront_slots": str(cfg.get("wavefront_slots")),
-            "bvh_width": str(cfg.get("bvh_width")), "kernel_sources_sha256": kernel_sources_sha256()}
+    want = {"kernel": kernel, "bvh_width": str(cfg.get("bvh_width")),
+            "kernel_sources_sha256": kernel_sources_sha256()}
     if any(kv.get(k) != v for k, v in want.items()):
         return None
     try:
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_ray"]) * rays_per_launch
     except (KeyError, ValueError):
         return None
 
@@ -268,7 +272,7 @@ def run_ours(args, rank, world, local):
                                     wavefront_only=bool(args.cache))
         tr.set_params(scenes.initial_params(sc, w["init"]))
     else:
-        tr.configure(args.integrator)
+        tr.configure(args.integrator, wavefront_slots=args.slots)
     chosen = tr.config()
     for _ in range(args.warmup):
         tr.step(opts, adam, want_loss=False)
@@ -399,7 +403,8 @@ def run_ours(args, rank, world, local):
         # against the gather probe measured in this run with the traversal's
         # own 256-bit node loads
         "roofline": {"bound": "l2", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(dom, w["workload"], chosen),
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic(dom, chosen, rays / max(launches_per_step, 1)),
                      "peak_source": f"{src} (HBM copy)",
                      "l2_gather_peak": l2_gather_gbs,
                      "l2_frac": achieved / l2_gather_gbs if l2_gather_gbs else None,
@@ -757,6 +762,8 @@ def main():
                     help="profiling only: use the first V views (not a benchmark line)")
     ap.add_argument("--spp", type=int, default=None,
                     help="profiling only: spp_r = spp_d = S (not a benchmark line)")
+    ap.add_argument("--slots", type=int, default=0,
+                    help="profiling only: wavefront path slots per chunk with --integrator wavefront")
     args = ap.parse_args()
     if args.workload in WORKLOADS:
         WORKLOAD.clear()

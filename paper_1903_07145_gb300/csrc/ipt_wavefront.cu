@@ -686,10 +686,39 @@ __device__ __forceinline__ void acc_flush(const float* sacc, uint32_t n, float* 
   }
 }
 
-__device__ __forceinline__ void scatter3(float* acc, int i, float3 v) {
-  atomicAdd(&acc[i], v.x);
-  atomicAdd(&acc[i + 1], v.y);
-  atomicAdd(&acc[i + 2], v.z);
+// Warp-aggregated scatter: adds v[0..N) to acc[base + j] for every lane whose
+// base is >= 0.  All 32 lanes of the warp call it together.  When every
+// contributing lane targets the same parameters (the same segment of the
+// same scene: a warp holds samples of one pixel, which mostly see the same
+// surface), the values are summed by a shuffle butterfly and one lane adds
+// the N sums; otherwise each lane adds its own values.  (Grouping lanes by
+// target with __match_any_sync and reducing every group was measured slower:
+// its shuffles cost more than the atomics they save in these latency-bound
+// stages.)
+template <int N>
+__device__ __forceinline__ void warp_scatter(float* acc, int base, const float (&v)[N]) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned want = __ballot_sync(0xffffffffu, base >= 0);
+  if (!want) return;
+  const int b0 = __shfl_sync(0xffffffffu, base, __ffs(want) - 1);
+  if (__popc(want) > 1 && __all_sync(0xffffffffu, base < 0 || base == b0)) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float x = base >= 0 ? v[j] : 0.0f;
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if (lane == 0 && x != 0.0f) atomicAdd(&acc[b0 + j], x);
+    }
+  } else if (base >= 0) {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (v[j] != 0.0f) atomicAdd(&acc[base + j], v[j]);
+  }
+}
+
+__device__ __forceinline__ void warp_scatter3(float* acc, int base, float3 a) {
+  const float v[3] = {a.x, a.y, a.z};
+  warp_scatter<3>(acc, base, v);
 }
 
 // Accumulator index of parameter j of segment `seg` of scene entry e.
@@ -706,53 +735,66 @@ __device__ __forceinline__ int acc_ix16(const WfScene& e, const WfParams& lp, in
   return kDisneyStride * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
 }
 
-__device__ __forceinline__ void scatter_disney(float* sacc, int base, const float (&g)[kDisneyMat]) {
-#pragma unroll
-  for (int j = 0; j < kDisneyMat; ++j)
-    if (g[j] != 0.0f) atomicAdd(&sacc[base + j], g[j]);
-}
 
-// Continuation terms of a finished path: (dw_l / dtheta) . (g * U_l).  The
+// Continuation terms of the paths that finish: (dw_l / dtheta) . (g * U_l)
+// for every vertex l.  All 32 lanes call it; lanes with act = false (or with
+// fewer vertices) add nothing, and the sums go through warp_scatter.  The
 // Disney model rebuilds vertex l (shading normal, tangent frame) from its
 // stored triangle, barycentrics and directions and contracts the BRDF
 // Jacobian there with g * U_l * cos/pdf.
 template <bool kD>
-__device__ __forceinline__ void finish_path(const WfDev& w, const WfScene& e, const WfParams& lp, uint32_t slot,
-                                            float3 gp, float* sacc) {
-  if constexpr (kD) {
-    const uint32_t nv = w.nv[slot];
-    for (uint32_t l = 0; l < nv; ++l) {
-      const size_t ix = (size_t)l * w.cap + slot;
-      const float4 T = w.aT[ix], U = w.aU[ix], Wi = w.aWi[ix], Wo = w.aWo[ix];
-      const float2 R = w.aR[ix];
-      const float3 q = gp * xyz(U) * T.w;
-      if (q.x == 0.0f && q.y == 0.0f && q.z == 0.0f) continue;
-      Hit h;
-      h.tri = __float_as_int(Wi.w);
-      h.t = 0.0f;
-      h.u = R.x;
-      h.v = Wo.w;
-      const Vtx v = make_vertex(e.s, h, -xyz(Wi), lp.profile);
-      float3 X, Y;
-      hit_frame(e.s, h.tri, v.ns, X, Y);
-      const int sg = __float_as_int(R.y);
-      float m[kDisneyMat], g[kDisneyMat];
-      load_disney(e.dis, sg, m);
-      if (disney_vjp(m, v.ns, X, Y, xyz(Wi), xyz(Wo), q, g)) scatter_disney(sacc, acc_ix16(e, lp, sg, 0), g);
+__device__ __forceinline__ void finish_path(const WfDev& w, const WfScene* e, const WfParams& lp, uint32_t slot,
+                                            float3 gp, float* sacc, bool act) {
+  const uint32_t nv = act ? w.nv[slot] : 0u;
+  const uint32_t nmax = __reduce_max_sync(0xffffffffu, nv);
+  for (uint32_t l = 0; l < nmax; ++l) {
+    if constexpr (kD) {
+      float g[kDisneyMat];
+      int base = -1;
+      if (l < nv) {
+        const size_t ix = (size_t)l * w.cap + slot;
+        const float4 T = w.aT[ix], U = w.aU[ix], Wi = w.aWi[ix], Wo = w.aWo[ix];
+        const float2 R = w.aR[ix];
+        const float3 q = gp * xyz(U) * T.w;
+        if (q.x != 0.0f || q.y != 0.0f || q.z != 0.0f) {
+          Hit h;
+          h.tri = __float_as_int(Wi.w);
+          h.t = 0.0f;
+          h.u = R.x;
+          h.v = Wo.w;
+          const Vtx v = make_vertex(e->s, h, -xyz(Wi), lp.profile);
+          float3 X, Y;
+          hit_frame(e->s, h.tri, v.ns, X, Y);
+          const int sg = __float_as_int(R.y);
+          float m[kDisneyMat];
+          load_disney(e->dis, sg, m);
+          if (disney_vjp(m, v.ns, X, Y, xyz(Wi), xyz(Wo), q, g)) base = acc_ix16(*e, lp, sg, 0);
+        }
+      }
+      if (base < 0)
+        for (int j = 0; j < kDisneyMat; ++j) g[j] = 0.0f;
+      warp_scatter<kDisneyMat>(sacc, base, g);
+    } else {
+      float g[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      int base = -1;
+      if (l < nv) {
+        const size_t ix = (size_t)l * w.cap + slot;
+        const float4 T = w.aT[ix], U = w.aU[ix];
+        const float2 R = w.aR[ix];
+        const int sg = __float_as_int(R.y);
+        const float3 q = gp * xyz(U);
+        const float4 mb = __ldg(&e->t.mat_b[sg]);
+        g[0] = q.x * T.w;
+        g[1] = q.y * T.w;
+        g[2] = q.z * T.w;
+        g[3] = q.x * U.w;
+        g[4] = q.y * U.w;
+        g[5] = q.z * U.w;
+        g[6] = dot(q, f3(mb.x, mb.y, mb.z)) * R.x;
+        base = acc_ix(*e, lp, sg, 0);
+      }
+      warp_scatter<7>(sacc, base, g);
     }
-    return;
-  }
-  const uint32_t nv = w.nv[slot];
-  for (uint32_t l = 0; l < nv; ++l) {
-    const size_t ix = (size_t)l * w.cap + slot;
-    const float4 T = w.aT[ix], U = w.aU[ix];
-    const float2 R = w.aR[ix];
-    const int sg = __float_as_int(R.y);
-    const float3 q = gp * xyz(U);
-    scatter3(sacc, acc_ix(e, lp, sg, 0), q * T.w);
-    scatter3(sacc, acc_ix(e, lp, sg, 3), q * U.w);
-    const float4 mb = __ldg(&e.t.mat_b[sg]);
-    atomicAdd(&sacc[acc_ix(e, lp, sg, 6)], dot(q, f3(mb.x, mb.y, mb.z)) * R.x);
   }
 }
 
@@ -783,27 +825,40 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
   const uint32_t si = set_iter(lp);
   const float inv_spp = 1.0f / (float)lp.spp;
   uint32_t* qin = queue(w, cur);
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const uint32_t slot = qin[q];
-    const float4 hh = w.hit[slot];
+  // warp-uniform trip count: every lane reaches the warp-collective scatters
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t q0 = blockIdx.x * blockDim.x + threadIdx.x - lane; q0 < n; q0 += gridDim.x * blockDim.x) {
+    const uint32_t q = q0 + lane;
+    const bool act = q < n;
+    const uint32_t slot = act ? qin[q] : 0u;
+    float4 hh = make_float4(__int_as_float(-1), 0.f, 0.f, 0.f), bt = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      hh = w.hit[slot];
+      bt = w.beta[slot];
+    }
     const int tri = __float_as_int(hh.x);
-    const float4 bt = w.beta[slot];
     const uint32_t st = __float_as_uint(bt.w);
     const uint32_t k = state_k(st), b = state_scene(st);
     const WfScene& e = tab[b];
-    uint32_t pid, smp, ent;
-    slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
-    const float3 gp = pixel_grad(e, ent, inv_spp);
-    bool shadow = false, query = false;
+    uint32_t pid = 0, smp = 0, ent = 0;
+    float3 gp = f3(0.f, 0.f, 0.f);
+    if (act) {
+      slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
+      gp = pixel_grad(e, ent, inv_spp);
+    }
+    bool shadow = false, query = false, finish = false;
     NeeResult ne;
     float3 ge = f3(0.f, 0.f, 0.f), gm = f3(0.f, 0.f, 0.f), cn = f3(0.f, 0.f, 0.f);
     float spec = 0.0f, dsdr = 0.0f;
     float gd[kDisneyMat];
     int vseg = 0;
+    int ebase = -1;  // accumulator of the emission found here
+    float3 ev = f3(0.f, 0.f, 0.f);
     float4 cq = make_float4(0.f, 0.f, 0.f, 0.f);
     Vtx cv;
-    if (tri < 0) {
-      finish_path<kD>(w, e, lp, slot, gp, sacc);
+    if (!act) {
+    } else if (tri < 0) {
+      finish = true;
       w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
     } else {
       const double W = *e.t.W;
@@ -822,11 +877,12 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
         if (wb > 0.0f) {
           const float f = wb * v.prof;
           add_to_carry(w, slot, xyz(__ldg(&e.t.emis[v.seg])) * f);
-          scatter3(sacc, kD ? acc_ix16(e, lp, v.seg, kDisneyMat) : acc_ix(e, lp, v.seg, 7), gp * beta * (f * e.es));
+          ebase = kD ? acc_ix16(e, lp, v.seg, kDisneyMat) : acc_ix(e, lp, v.seg, 7);
+          ev = gp * beta * (f * e.es);
         }
       }
       if (k == lp.max_depth) {
-        finish_path<kD>(w, e, lp, slot, gp, sacc);
+        finish = true;
         w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       } else if (k == lp.cache_k) {
         // the cache's prediction and its parameter derivative close the path
@@ -870,6 +926,8 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
         }
       }
     }
+    warp_scatter3(sacc, ebase, ev);
+    finish_path<kD>(w, &e, lp, slot, gp, sacc, finish);
     if (lp.cache_k != kNoCache) {
       const uint32_t qi = enqueue(&lp.cb.counts[0], query);
       if (query) {
@@ -908,28 +966,53 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
   const uint32_t np = (kD ? 16u : 10u) * lp.seg_n;
   if (!lp.gacc) acc_zero(sacc, np);
   const uint32_t n = w.cnt[2];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (!w.sh_vis[i]) continue;
-    const uint4 m = w.sh_meta[i];
-    const WfScene& e = tab[state_scene(__float_as_uint(w.beta[m.x].w))];
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < n; i0 += gridDim.x * blockDim.x) {
+    const uint32_t i = i0 + lane;
+    const bool vis = i < n && w.sh_vis[i];
+    int lbase = -1, mbase = -1;  // accumulators of the light's emission and the vertex material
+    float3 ge3 = f3(0.f, 0.f, 0.f);
     if constexpr (kD) {
-      const float4 ge = w.sh_ge[i], cn = w.sh_n[i];
-      scatter3(sacc, acc_ix16(e, lp, (int)m.w, kDisneyMat), xyz(ge));
-      const float4* dv = w.sh_dv + 4 * (size_t)i;
-      const float4 d0 = dv[0], d1 = dv[1], d2 = dv[2], d3 = dv[3];
-      const float g[kDisneyMat] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w, d2.x, d2.y, d2.z, d2.w, d3.x};
-      scatter_disney(sacc, acc_ix16(e, lp, (int)m.z, 0), g);
-      add_to_carry(w, m.x, xyz(cn));
+      float g[kDisneyMat];
+      for (int j = 0; j < kDisneyMat; ++j) g[j] = 0.0f;
+      if (vis) {
+        const uint4 m = w.sh_meta[i];
+        const WfScene& e = tab[state_scene(__float_as_uint(w.beta[m.x].w))];
+        const float4 ge = w.sh_ge[i], cn = w.sh_n[i];
+        lbase = acc_ix16(e, lp, (int)m.w, kDisneyMat);
+        ge3 = xyz(ge);
+        const float4* dv = w.sh_dv + 4 * (size_t)i;
+        const float4 d0 = dv[0], d1 = dv[1], d2 = dv[2], d3 = dv[3];
+        const float gg[kDisneyMat] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w, d2.x, d2.y, d2.z, d2.w, d3.x};
+        for (int j = 0; j < kDisneyMat; ++j) g[j] = gg[j];
+        mbase = acc_ix16(e, lp, (int)m.z, 0);
+        add_to_carry(w, m.x, xyz(cn));
+      }
+      warp_scatter3(sacc, lbase, ge3);
+      warp_scatter<kDisneyMat>(sacc, mbase, g);
       continue;
     }
-    const float4 ge = w.sh_ge[i], gm = w.sh_gm[i], cn = w.sh_n[i];
-    scatter3(sacc, acc_ix(e, lp, (int)m.w, 7), xyz(ge));
-    const float3 q = xyz(gm);
-    scatter3(sacc, acc_ix(e, lp, (int)m.z, 0), q * (1.0f / kPi));
-    scatter3(sacc, acc_ix(e, lp, (int)m.z, 3), q * gm.w);
-    const float4 mb = __ldg(&e.t.mat_b[m.z]);
-    atomicAdd(&sacc[acc_ix(e, lp, (int)m.z, 6)], dot(q, f3(mb.x, mb.y, mb.z)) * cn.w);
-    add_to_carry(w, m.x, xyz(cn));
+    float g[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (vis) {
+      const uint4 m = w.sh_meta[i];
+      const WfScene& e = tab[state_scene(__float_as_uint(w.beta[m.x].w))];
+      const float4 ge = w.sh_ge[i], gm = w.sh_gm[i], cn = w.sh_n[i];
+      lbase = acc_ix(e, lp, (int)m.w, 7);
+      ge3 = xyz(ge);
+      const float3 q = xyz(gm);
+      const float4 mb = __ldg(&e.t.mat_b[m.z]);
+      g[0] = q.x * (1.0f / kPi);
+      g[1] = q.y * (1.0f / kPi);
+      g[2] = q.z * (1.0f / kPi);
+      g[3] = q.x * gm.w;
+      g[4] = q.y * gm.w;
+      g[5] = q.z * gm.w;
+      g[6] = dot(q, f3(mb.x, mb.y, mb.z)) * cn.w;
+      mbase = acc_ix(e, lp, (int)m.z, 0);
+      add_to_carry(w, m.x, xyz(cn));
+    }
+    warp_scatter3(sacc, lbase, ge3);
+    warp_scatter<7>(sacc, mbase, g);
   }
   if (!lp.gacc) acc_flush(sacc, np, w.blk);
 }
@@ -949,17 +1032,22 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
   uint32_t* qin = queue(w, cur);
   uint32_t* qout = queue(w, cur ^ 1);
   uint32_t* nout = &w.cnt[cur ^ 1];
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const uint32_t slot = qin[q];
-    const float4 bt = w.beta[slot];
+  // warp-uniform trip count: every lane reaches the warp-collective scatters
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t q0 = blockIdx.x * blockDim.x + threadIdx.x - lane; q0 < n; q0 += gridDim.x * blockDim.x) {
+    const uint32_t q = q0 + lane;
+    const bool act = q < n;
+    const uint32_t slot = act ? qin[q] : 0u;
+    const float4 bt = act ? w.beta[slot] : make_float4(0.f, 0.f, 0.f, __uint_as_float(kDead));
     const uint32_t st = __float_as_uint(bt.w);
-    bool cont = false;
+    bool cont = false, finish = false;
     float3 org = f3(0.f, 0.f, 0.f), wo = f3(0.f, 0.f, 0.f), beta = xyz(bt);
     float pdf = 0.0f;
     int tri = -1;
     const uint32_t k = state_k(st), b = state_scene(st);
+    const WfScene& e = tab[b];
+    float3 gfin = f3(0.f, 0.f, 0.f);
     if (!(st & kDead)) {
-      const WfScene& e = tab[b];
       const float4 hh = w.hit[slot];
       tri = __float_as_int(hh.x);
       const float4 rd = w.ray_d[slot];
@@ -1036,10 +1124,12 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
         }
       }
       if (!cont) {
-        finish_path<kD>(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
+        finish = true;
+        gfin = pixel_grad(e, ent, inv_spp);
         w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       }
     }
+    finish_path<kD>(w, &e, lp, slot, gfin, sacc, finish);
     const uint32_t ci = enqueue(nout, cont);
     if (cont) {
       qout[ci] = slot;
@@ -1061,20 +1151,30 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
   if (!lp.gacc) acc_zero(sacc, np);
   const uint32_t n = lp.cb.counts[0];
   const float inv_spp = 1.0f / (float)lp.spp;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const uint32_t slot = __float_as_uint(lp.cb.q.d[q].w);
-    const int seg = __float_as_int(lp.cb.q.x[q].w);
-    const uint32_t st = __float_as_uint(w.beta[slot].w);
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t q0 = blockIdx.x * blockDim.x + threadIdx.x - lane; q0 < n; q0 += gridDim.x * blockDim.x) {
+    const uint32_t q = q0 + lane;
+    const bool act = q < n;
+    const uint32_t slot = act ? __float_as_uint(lp.cb.q.d[q].w) : 0u;
+    const uint32_t st = act ? __float_as_uint(w.beta[slot].w) : 0u;
     const WfScene& e = tab[state_scene(st)];
-    add_to_carry(w, slot, xyz(lp.cb.qc[q]));
-    const float* dp = lp.cb.qdp + 8 * (size_t)q;
-    const int base = acc_ix(e, lp, seg, 0);
+    float g[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int base = -1;
+    float3 gp = f3(0.f, 0.f, 0.f);
+    if (act) {
+      const int seg = __float_as_int(lp.cb.q.x[q].w);
+      add_to_carry(w, slot, xyz(lp.cb.qc[q]));
+      const float* dp = lp.cb.qdp + 8 * (size_t)q;
 #pragma unroll
-    for (int j = 0; j < 7; ++j) atomicAdd(&sacc[base + j], dp[j]);
-    uint32_t pid, smp, ent;
-    slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
-    finish_path<false>(w, e, lp, slot, pixel_grad(e, ent, inv_spp), sacc);
-    w.beta[slot].w = __uint_as_float(st | kDead);
+      for (int j = 0; j < 7; ++j) g[j] = dp[j];
+      base = acc_ix(e, lp, seg, 0);
+      uint32_t pid, smp, ent;
+      slot_pixel(e, p0, slot, lp.spp, lp.stride, pid, smp, ent);
+      gp = pixel_grad(e, ent, inv_spp);
+    }
+    warp_scatter<7>(sacc, base, g);
+    finish_path<false>(w, &e, lp, slot, gp, sacc, act);
+    if (act) w.beta[slot].w = __uint_as_float(st | kDead);
   }
   if (!lp.gacc) acc_flush(sacc, np, w.blk);
 }
