@@ -154,12 +154,13 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def recorded_traffic(kernel, cfg, rays_per_launch):
+def recorded_traffic(kernel, cfg, slots_per_launch):
     """DRAM bytes (read + write) per launch, or None: the committed record's
-    bytes per ray, from an ncu capture of the same kernel on a small case of
-    the workload, times this run's rays per launch.  The per-ray traffic is
-    the queue and path state each ray reads and writes (the nodes and
-    triangles stay in L2), so it scales with the rays a launch processes."""
+    bytes per path slot, from an ncu capture of the same kernel on a small
+    case of the workload, times the slots of this run's chunks.  The traffic
+    is the per-slot ray state read in 32-byte sectors across a chunk's slot
+    range (the nodes and triangles stay in L2), so it scales with the chunk,
+    not with the rays still alive in it."""
     try:
         with open(TRAFFIC_FILE) as fh:
             lines = fh.read().splitlines()
@@ -175,7 +176,7 @@ def recorded_traffic(kernel, cfg, rays_per_launch):
     if any(kv.get(k) != v for k, v in want.items()):
         return None
     try:
-        return float(kv["dram_bytes_per_ray"]) * rays_per_launch
+        return float(kv["dram_bytes_per_slot"]) * slots_per_launch
     except (KeyError, ValueError):
         return None
 
@@ -378,6 +379,10 @@ def run_ours(args, rank, world, local):
         nodes = tris = rays = 0
     # counters cover one step's passes; the timed region ran args.steps steps
     launches_per_step = dom_launches / args.steps
+    # slots of one wavefront chunk: a pass of P paths in ceil(P / cap) chunks
+    pass_paths = w["spp_r"] * w["views"] * w["width"] * w["height"]
+    cap = chosen.get("wavefront_slots") or (1 << 20)
+    chunk_slots = pass_paths / math.ceil(pass_paths / cap)
     alg_bytes_step = nodes * NODE_BYTES + tris * TRI_BYTES
     alg_bytes_launch = alg_bytes_step / max(launches_per_step, 1)
     dom_ms = dom_total_ms / max(1, dom_launches)
@@ -404,7 +409,7 @@ def run_ours(args, rank, world, local):
         # own 256-bit node loads
         "roofline": {"bound": "l2", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": recorded_traffic(dom, chosen, rays / max(launches_per_step, 1)),
+                     "traffic": recorded_traffic(dom, chosen, chunk_slots),
                      "peak_source": f"{src} (HBM copy)",
                      "l2_gather_peak": l2_gather_gbs,
                      "l2_frac": achieved / l2_gather_gbs if l2_gather_gbs else None,
