@@ -18,7 +18,9 @@
  *   - Argument errors are reported as IPT_ERR_INVALID_ARG before anything is
  *     launched.  Errors found on the device set a status word that the next
  *     synchronising call returns: a traversal stack overflow as IPT_ERR_CUDA,
- *     a non-finite loss or gradient met by an Adam step as IPT_ERR_NONFINITE.
+ *     a non-finite loss or gradient met by an Adam step as IPT_ERR_NONFINITE,
+ *     a bounded wait for the tensor cores that gave up (radiance-cache
+ *     training) as IPT_ERR_TIMEOUT.
  *   - Non-finite guard: every Adam step (ipt_adam_step, ipt_step,
  *     ipt_batch_step per member, ipt_disney_step) first checks, on the device,
  *     the gradient it is given and, for the context's own gradient, the loss

@@ -17,10 +17,13 @@
 // and the inference VJP needs only their ReLU masks (one register per layer).
 // Inference blocks of 16 warps share one weight image (two blocks per SM).
 // The backward pass loads the transposed weights with ldmatrix.trans from the
-// same out-major image.  Training keeps the block's 64 rows of activations
-// and pre-activation gradients in shared memory, so each warp then forms
-// whole weight-gradient tiles over all 64 rows (K = rows) and accumulates
-// them in a block-private FP32 copy, flushed once per launch.
+// same out-major image.  Training keeps the block's 64 rows of inputs,
+// activations and pre-activation gradients in shared memory in the
+// core-matrix-blocked layout that the fifth-generation tensor cores read;
+// the weight gradients dW = A^T dZ over those rows (K = rows) are one
+// tcgen05.mma batch per tile, issued by one thread and accumulated in tensor
+// memory (TMEM) across every tile the block processes, then read back with
+// tcgen05.ld and added to the global gradient once per launch.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,20 +48,55 @@ constexpr int kWt1 = 0, kWt2 = 64 * kXs, kWt3 = kWt2 + 64 * kHs, kWt4 = kWt3 + 6
 // FP32 master weight offsets: W1 80 x 64, W2..W4 64 x 64, W5 64 x 16, in-major.
 constexpr int kW1 = 0, kW2 = 80 * 64, kW3 = kW2 + 4096, kW4 = kW3 + 4096, kW5 = kW4 + 4096;
 
-// Shared-memory layout (bytes, 16-byte aligned regions).
+// Shared-memory layout (bytes, 16-byte aligned regions).  Inference: the
+// BF16 weight image, then each warp's input tile (row stride kXs) and row
+// metadata (infer_smem).  Training: the weight image, then the block's
+// 64-row tiles in the core-matrix-blocked layout of BlockTile -- X (80
+// features), H1..H4 and dZ1..dZ4 (64 each), dY (16) -- the rows' metadata,
+// and the weight-gradient MMAs' mbarrier and TMEM address.
 constexpr int kSmWt = 0;
 constexpr int kSmX = kSmWt + (int)kCacheWtElems * 2;
-constexpr int kSmMeta = kSmX + kTileRows * kXs * 2;
-constexpr int kSmH = kSmMeta + kTileRows * 16;
-constexpr int kSmDz = kSmH + 4 * kTileRows * kHs * 2;
-constexpr int kSmDy = kSmDz + 4 * kTileRows * kHs * 2;
-constexpr int kSmDw = kSmDy + kTileRows * kYs * 2;
-constexpr int kSmEnd = kSmDw + (int)kCacheWeights * 4;
-constexpr int kSmemTrain = kSmEnd;  // weights, tiles, activations, pre-activation gradients, dY, dW
-static_assert(kSmX % 16 == 0 && kSmMeta % 16 == 0 && kSmH % 16 == 0 && kSmDz % 16 == 0 && kSmDy % 16 == 0 &&
-                  kSmDw % 16 == 0,
+// bytes between consecutive 8-row groups of a blocked tile (features / 8 chunks of 128 B)
+constexpr int kLboX = 10 * 128, kLboH = 8 * 128, kLboY = 2 * 128;
+constexpr int kTX = kSmX;
+constexpr int kTH = kTX + 8 * kLboX;       // H1..H4: 8 row groups of kLboH each
+constexpr int kTDz = kTH + 4 * 8 * kLboH;  // dZ1..dZ4
+constexpr int kTDy = kTDz + 4 * 8 * kLboH;
+constexpr int kTMeta = kTDy + 8 * kLboY;
+constexpr int kTBar = kTMeta + kTileRows * 16;  // mbarrier (8 B), TMEM address (4 B)
+constexpr int kSmemTrain = kTBar + 16;
+static_assert(kSmX % 16 == 0 && kTH % 16 == 0 && kTDz % 16 == 0 && kTDy % 16 == 0 && kTMeta % 16 == 0 &&
+                  kTBar % 16 == 0,
               "shared regions must be 16-byte aligned");
 static_assert(kSmemTrain <= 227 * 1024, "training tile exceeds shared memory");
+// An M = 128 operand reads 16 feature chunks of every row group; the X and
+// H tiles have fewer, so the reads of the last group run past the tile into
+// the next region (never past dZ1).  The rows of D they feed are not used.
+static_assert(kTX + 7 * kLboX + 16 * 128 <= kTDz && kTH + 3 * 8 * kLboH + 7 * kLboH + 16 * 128 <= kTDy,
+              "M = 128 operand reads must stay inside the tiles");
+
+// A tile of 16-bit pairs addressed by (row, word); word w of a row holds
+// features 2w and 2w + 1.
+struct RowTile {  // row-major, `stride` words per row
+  uint32_t* p;
+  int stride;
+  __device__ __forceinline__ uint32_t& operator()(int r, int w) const { return p[r * stride + w]; }
+};
+
+// Core-matrix-blocked tile: 8-row groups `lbo` words apart; inside a group,
+// chunks of 8 features (4 words) 32 words apart, each chunk holding its 8
+// rows at 4-word steps (16 bytes).  Stored this way a [rows x features] tile
+// is the no-swizzle MN-major operand of tcgen05.mma (features along M or N,
+// rows along K), and the mma.sync fragment accesses (8 rows x 4 words per
+// instruction) touch 32 consecutive words.
+struct BlockTile {
+  uint32_t* p;
+  int lbo;
+  __device__ __forceinline__ uint32_t& operator()(int r, int w) const {
+    return p[(r >> 3) * lbo + (w >> 2) * 32 + (r & 7) * 4 + (w & 3)];
+  }
+  __device__ __forceinline__ BlockTile rows_from(int r0) const { return BlockTile{p + (r0 >> 3) * lbo, lbo}; }
+};
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -139,13 +177,14 @@ __device__ __forceinline__ float3 unit_pos(const CacheNet& net, float4 x) {
 }
 
 // Encodes rows [r0, r0 + 16) (valid below `end`) into the warp's input tile
-// X (16 x kXs BF16) and its row metadata (unit position, valid flag).
+// X (16 rows of 80 BF16 features) and its row metadata (unit position, valid
+// flag).
+template <class Tile>
 __device__ __forceinline__ void encode_rows(const CacheNet& net, const int* res, const CacheRows& rows, const float4* mat_a,
-                            const float4* mat_b, uint32_t r0, uint32_t end, uint32_t* X, float4* meta, int lane) {
+                            const float4* mat_b, uint32_t r0, uint32_t end, Tile X, float4* meta, int lane) {
   const int row = lane & 15;
   const uint32_t r = r0 + (uint32_t)row;
   const bool valid = r < end;
-  uint32_t* xr = X + row * kXw;
   if (lane < 16) {
     const float4 xq = valid ? rows.x[r] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float3 p = unit_pos(net, xq);
@@ -156,12 +195,12 @@ __device__ __forceinline__ void encode_rows(const CacheNet& net, const int* res,
       ma = __ldg(&mat_a[seg]);
       mb = __ldg(&mat_b[seg]);
     }
-    xr[32] = pack2(ma.x, ma.y);  // kd r, g
-    xr[33] = pack2(ma.z, mb.x);  // kd b, ks r
-    xr[34] = pack2(mb.y, mb.z);  // ks g, b
-    xr[35] = pack2(ma.w, 0.0f);  // roughness
+    X(row, 32) = pack2(ma.x, ma.y);  // kd r, g
+    X(row, 33) = pack2(ma.z, mb.x);  // kd b, ks r
+    X(row, 34) = pack2(mb.y, mb.z);  // ks g, b
+    X(row, 35) = pack2(ma.w, 0.0f);  // roughness
 #pragma unroll
-    for (int i = 36; i < 40; ++i) xr[i] = 0u;
+    for (int i = 36; i < 40; ++i) X(row, i) = 0u;
   }
   {
     float3 dir = make_float3(0.f, 0.f, 1.f);
@@ -173,7 +212,7 @@ __device__ __forceinline__ void encode_rows(const CacheNet& net, const int* res,
     sh16(dir, sh);
     const int w0 = lane < 16 ? 16 : 24;  // columns 32.. and 48..
 #pragma unroll
-    for (int i = 0; i < 8; ++i) xr[w0 + i] = valid ? pack2(sh[2 * i], sh[2 * i + 1]) : 0u;
+    for (int i = 0; i < 8; ++i) X(row, w0 + i) = valid ? pack2(sh[2 * i], sh[2 * i + 1]) : 0u;
   }
   __syncwarp();
 #pragma unroll 1
@@ -195,7 +234,7 @@ __device__ __forceinline__ void encode_rows(const CacheNet& net, const int* res,
       }
       word = pack2(f0, f1);
     }
-    X[rr * kXw + l] = word;
+    X(rr, l) = word;
   }
   __syncwarp();
 }
@@ -216,9 +255,9 @@ __device__ __forceinline__ void layer_fwd(const uint32_t* Wt, const uint32_t (&a
 }
 
 // ReLU, BF16 A fragments of the next layer, and (optionally) the activation
-// tile H (warp rows, row stride kHw words).
+// tile H (the warp's 16 rows).
 template <bool kStore>
-__device__ __forceinline__ void relu_pack(const float (&c)[8][4], uint32_t (&a)[4][4], uint32_t* H, int g, int t) {
+__device__ __forceinline__ void relu_pack(const float (&c)[8][4], uint32_t (&a)[4][4], BlockTile H, int g, int t) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint32_t lo = pack2(fmaxf(c[j][0], 0.0f), fmaxf(c[j][1], 0.0f));
@@ -226,38 +265,44 @@ __device__ __forceinline__ void relu_pack(const float (&c)[8][4], uint32_t (&a)[
     a[j >> 1][(j & 1) * 2 + 0] = lo;
     a[j >> 1][(j & 1) * 2 + 1] = hi;
     if (kStore) {
-      H[g * kHw + 4 * j + t] = lo;
-      H[(g + 8) * kHw + 4 * j + t] = hi;
+      H(g, 4 * j + t) = lo;
+      H(g + 8, 4 * j + t) = hi;
     }
   }
 }
 
+// First-layer A fragments of the warp's 16 rows from its input tile.
+template <class Tile>
+__device__ __forceinline__ void input_frags(Tile X, uint32_t (&a)[5][4], int g, int t) {
+#pragma unroll
+  for (int kk = 0; kk < 5; ++kk) {
+    a[kk][0] = X(g, 8 * kk + t);
+    a[kk][1] = X(g + 8, 8 * kk + t);
+    a[kk][2] = X(g, 8 * kk + 4 + t);
+    a[kk][3] = X(g + 8, 8 * kk + 4 + t);
+  }
+}
+
 // Forward pass of the warp's 16 rows from its input tile; hidden
-// activations of layer i go to H + i * hstride when kStore.
+// activations of layer i go to H advanced by i * hstride words when kStore.
 template <bool kStore>
-__device__ __forceinline__ void net_forward(const uint32_t* Wt, const uint32_t* X, uint32_t* H, int hstride,
+__device__ __forceinline__ void net_forward(const uint32_t* Wt, BlockTile X, BlockTile H, int hstride,
                                             float (&y)[2][4], int lane) {
   const int g = lane >> 2, t = lane & 3;
   float c[8][4];
   uint32_t h[4][4];
   {
     uint32_t a[5][4];
-#pragma unroll
-    for (int kk = 0; kk < 5; ++kk) {
-      a[kk][0] = X[g * kXw + 8 * kk + t];
-      a[kk][1] = X[(g + 8) * kXw + 8 * kk + t];
-      a[kk][2] = X[g * kXw + 8 * kk + 4 + t];
-      a[kk][3] = X[(g + 8) * kXw + 8 * kk + 4 + t];
-    }
+    input_frags(X, a, g, t);
     layer_fwd<5, 8, kXw>(Wt + kWt1 / 2, a, c, g, t);
   }
   relu_pack<kStore>(c, h, H, g, t);
   layer_fwd<4, 8, kHw>(Wt + kWt2 / 2, h, c, g, t);
-  relu_pack<kStore>(c, h, H + hstride, g, t);
+  relu_pack<kStore>(c, h, BlockTile{H.p + hstride, H.lbo}, g, t);
   layer_fwd<4, 8, kHw>(Wt + kWt3 / 2, h, c, g, t);
-  relu_pack<kStore>(c, h, H + 2 * hstride, g, t);
+  relu_pack<kStore>(c, h, BlockTile{H.p + 2 * hstride, H.lbo}, g, t);
   layer_fwd<4, 8, kHw>(Wt + kWt4 / 2, h, c, g, t);
-  relu_pack<kStore>(c, h, H + 3 * hstride, g, t);
+  relu_pack<kStore>(c, h, BlockTile{H.p + 3 * hstride, H.lbo}, g, t);
   layer_fwd<4, 2, kHw>(Wt + kWt5 / 2, h, y, g, t);
 }
 
@@ -287,19 +332,19 @@ __device__ __forceinline__ void layer_bwd(const __nv_bfloat16* Wt, const uint32_
 // dZ = dH * (H > 0) at the fragment positions, packed to A fragments and
 // (optionally) stored as a BF16 tile.
 template <bool kStore>
-__device__ __forceinline__ void relu_grad(const float (&dh)[8][4], const uint32_t* H, uint32_t (&a)[4][4],
-                                          uint32_t* Dz, int g, int t) {
+__device__ __forceinline__ void relu_grad(const float (&dh)[8][4], BlockTile H, uint32_t (&a)[4][4],
+                                          BlockTile Dz, int g, int t) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const float2 h0 = unpack2(H[g * kHw + 4 * j + t]);
-    const float2 h1 = unpack2(H[(g + 8) * kHw + 4 * j + t]);
+    const float2 h0 = unpack2(H(g, 4 * j + t));
+    const float2 h1 = unpack2(H(g + 8, 4 * j + t));
     const uint32_t lo = pack2(h0.x > 0.0f ? dh[j][0] : 0.0f, h0.y > 0.0f ? dh[j][1] : 0.0f);
     const uint32_t hi = pack2(h1.x > 0.0f ? dh[j][2] : 0.0f, h1.y > 0.0f ? dh[j][3] : 0.0f);
     a[j >> 1][(j & 1) * 2 + 0] = lo;
     a[j >> 1][(j & 1) * 2 + 1] = hi;
     if (kStore) {
-      Dz[g * kHw + 4 * j + t] = lo;
-      Dz[(g + 8) * kHw + 4 * j + t] = hi;
+      Dz(g, 4 * j + t) = lo;
+      Dz(g + 8, 4 * j + t) = hi;
     }
   }
 }
@@ -334,20 +379,14 @@ __device__ __forceinline__ void relu_grad_mask(const float (&dh)[8][4], uint32_t
 }
 
 // Forward pass keeping the hidden layers' ReLU masks (mask[i]: layer i + 1).
-__device__ __forceinline__ void net_forward_mask(const uint32_t* Wt, const uint32_t* X, float (&y)[2][4],
+__device__ __forceinline__ void net_forward_mask(const uint32_t* Wt, RowTile X, float (&y)[2][4],
                                                  uint32_t (&mask)[4], int lane) {
   const int g = lane >> 2, t = lane & 3;
   float c[8][4];
   uint32_t h[4][4];
   {
     uint32_t a[5][4];
-#pragma unroll
-    for (int kk = 0; kk < 5; ++kk) {
-      a[kk][0] = X[g * kXw + 8 * kk + t];
-      a[kk][1] = X[(g + 8) * kXw + 8 * kk + t];
-      a[kk][2] = X[g * kXw + 8 * kk + 4 + t];
-      a[kk][3] = X[(g + 8) * kXw + 8 * kk + 4 + t];
-    }
+    input_frags(X, a, g, t);
     layer_fwd<5, 8, kXw>(Wt + kWt1 / 2, a, c, g, t);
   }
   mask[0] = relu_pack_mask(c, h);
@@ -386,10 +425,11 @@ __device__ __forceinline__ void net_backward_mask(const __nv_bfloat16* Wtb, cons
 
 // Backward pass of the warp's rows from dL/dy down to the inputs: returns the
 // input-gradient fragments of n-tile pairs [JP0, JP1) of the 80 inputs.
-// Pre-activation gradients (and dY) are stored when kStore.
+// Pre-activation gradients (and dY) are stored when kStore; layer i of H and
+// Dz is hstride words after layer i - 1.
 template <bool kStore, int JP0, int JP1>
-__device__ __forceinline__ void net_backward(const __nv_bfloat16* Wtb, const uint32_t* H, int hstride,
-                                             uint32_t* Dz, uint32_t* Dy, const float (&dy)[2][4],
+__device__ __forceinline__ void net_backward(const __nv_bfloat16* Wtb, BlockTile H, int hstride, BlockTile Dz,
+                                             BlockTile Dy, const float (&dy)[2][4],
                                              float (&dx)[2 * (JP1 - JP0)][4], int lane) {
   const int g = lane >> 2, t = lane & 3;
   uint32_t ay[1][4];
@@ -398,19 +438,20 @@ __device__ __forceinline__ void net_backward(const __nv_bfloat16* Wtb, const uin
   ay[0][2] = pack2(dy[1][0], dy[1][1]);
   ay[0][3] = pack2(dy[1][2], dy[1][3]);
   if (kStore) {
-    Dy[g * kYw + t] = ay[0][0];
-    Dy[(g + 8) * kYw + t] = ay[0][1];
-    Dy[g * kYw + 4 + t] = ay[0][2];
-    Dy[(g + 8) * kYw + 4 + t] = ay[0][3];
+    Dy(g, t) = ay[0][0];
+    Dy(g + 8, t) = ay[0][1];
+    Dy(g, 4 + t) = ay[0][2];
+    Dy(g + 8, 4 + t) = ay[0][3];
   }
   float dh[8][4];
   uint32_t a[4][4];
   layer_bwd<1, 0, 4, kHs>(Wtb + kWt5, ay, dh, lane);
-  relu_grad<kStore>(dh, H + 3 * hstride, a, Dz + 3 * hstride, g, t);
+  auto at = [](BlockTile b, int i, int stride) { return BlockTile{b.p + i * stride, b.lbo}; };
+  relu_grad<kStore>(dh, at(H, 3, hstride), a, at(Dz, 3, hstride), g, t);
   layer_bwd<4, 0, 4, kHs>(Wtb + kWt4, a, dh, lane);
-  relu_grad<kStore>(dh, H + 2 * hstride, a, Dz + 2 * hstride, g, t);
+  relu_grad<kStore>(dh, at(H, 2, hstride), a, at(Dz, 2, hstride), g, t);
   layer_bwd<4, 0, 4, kHs>(Wtb + kWt3, a, dh, lane);
-  relu_grad<kStore>(dh, H + hstride, a, Dz + hstride, g, t);
+  relu_grad<kStore>(dh, at(H, 1, hstride), a, at(Dz, 1, hstride), g, t);
   layer_bwd<4, 0, 4, kHs>(Wtb + kWt2, a, dh, lane);
   relu_grad<kStore>(dh, H, a, Dz, g, t);
   layer_bwd<4, JP0, JP1, kXs>(Wtb + kWt1, a, dx, lane);
@@ -448,7 +489,7 @@ __global__ void __launch_bounds__(W * 32, 2) cache_infer_k(CacheNet net, CacheRo
   const int g = lane >> 2, t = lane & 3;
   const uint32_t* Wt = reinterpret_cast<const uint32_t*>(sm + kSmWt);
   const __nv_bfloat16* Wtb = reinterpret_cast<const __nv_bfloat16*>(sm + kSmWt);
-  uint32_t* X = reinterpret_cast<uint32_t*>(sm + kSmX) + warp * 16 * kXw;
+  const RowTile X{reinterpret_cast<uint32_t*>(sm + kSmX) + warp * 16 * kXw, kXw};
   float4* meta = reinterpret_cast<float4*>(sm + kSmX + W * 16 * kXs * 2) + warp * 16;
   const uint32_t n_tiles = (n + 15u) / 16u;
   for (uint32_t tile = blockIdx.x * (uint32_t)W + (uint32_t)warp; tile < n_tiles; tile += gridDim.x * (uint32_t)W) {
@@ -510,7 +551,110 @@ __global__ void __launch_bounds__(W * 32, 2) cache_infer_k(CacheNet net, CacheRo
   }
 }
 
-// Training gradients over block tiles of 64 rows of one minibatch.
+// ---------------------------------------------------------------------------
+// Fifth-generation tensor cores (tcgen05): the training pass's weight
+// gradients.  Operands come from shared memory through matrix descriptors,
+// the FP32 accumulators live in tensor memory (TMEM), one thread issues the
+// MMAs, and an mbarrier tracks their completion.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kDwCols = 512;       // TMEM columns held by a training block (272 used)
+constexpr uint32_t kWaitLimit = 1u << 24;  // mbarrier polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Descriptor of a no-swizzle operand in shared memory: start address, the
+// byte offset between 8-row groups along K (lbo) and between 8-element
+// chunks along M or N (sbo), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of a dense kind::f16 MMA: BF16 A and B, FP32 D,
+// both operands MN-major, shape M x N.
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Polls the mbarrier's phase with the given parity at most `limit` times.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// One tile's weight gradients added to the TMEM accumulators (sums over the
+// tile's 64 rows, K, in four steps of 16): dW1 = X^T dZ1, dW2..dW4 =
+// H1..H3^T dZ2..dZ4, dW5 = H4^T dY.  D rows (TMEM lanes) are the layer's
+// inputs (M = 128; rows past 80 or 64 inputs take values that are never
+// read), columns its outputs: dW1 at columns 0-63, dW2..dW4 at 64-255, dW5
+// at 256-271.  accumulate = 0 overwrites (the block's first tile).
+__device__ __forceinline__ void issue_weight_grads(const unsigned char* sm, uint32_t tmem, bool accumulate) {
+  const uint32_t base = smem_addr(sm);
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const uint32_t a = base + (uint32_t)(l == 0 ? kTX : kTH + (l - 1) * 8 * kLboH);
+    const uint32_t alb = l == 0 ? kLboX : kLboH;
+    const uint32_t b = base + (uint32_t)(l < 4 ? kTDz + l * 8 * kLboH : kTDy);
+    const uint32_t blb = l < 4 ? kLboH : kLboY;
+    const uint32_t idesc = umma_idesc(128, l < 4 ? 64 : 16);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      umma_bf16(tmem + 64u * (uint32_t)l, umma_sdesc(a + 2u * k * alb, alb, 128), umma_sdesc(b + 2u * k * blb, blb, 128),
+                idesc, (accumulate || k > 0) ? 1u : 0u);
+  }
+}
+
+// Adds the block's accumulated weight gradients to gw (FP32 master layout,
+// input index first).  Warp w reads TMEM lanes 32w..32w + 31, i.e. input m =
+// 32w + lane of every layer.
+__device__ __forceinline__ void flush_weight_grads(uint32_t tmem, float* gw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = 32 * warp + lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < 272; c0 += 16) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int l = c0 >> 6, n0 = c0 & 63;
+    if (m < (l == 0 ? 80 : 64)) {
+      float* dst = gw + (l == 0 ? kW1 + m * 64 : (l < 4 ? kW2 + (l - 1) * 4096 + m * 64 : kW5 + m * 16)) + n0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float v = __uint_as_float(r[j]);
+        if (v != 0.0f) atomicAdd(dst + j, v);
+      }
+    }
+  }
+}
+
+// Training gradients over block tiles of 64 rows of one minibatch.  The
+// forward and backward passes run on mma.sync per warp (16 rows each); the
+// weight gradients of each tile go to the tensor cores as one batch of 20
+// tcgen05.mma (issued after the tile's tiles are written, waited for before
+// the next tile overwrites them), accumulated in TMEM for the whole launch.
 __global__ void __launch_bounds__(kThreads) cache_grad_k(CacheNet net, CacheRows rows, const float4* mat_a,
                                                          const float4* mat_b, const uint32_t* count_dev,
                                                          uint32_t n_max, uint32_t batch, uint32_t n_batches,
@@ -518,27 +662,51 @@ __global__ void __launch_bounds__(kThreads) cache_grad_k(CacheNet net, CacheRows
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int res[kCacheLevels];
   load_weights(net, sm, res);
-  float* dW = reinterpret_cast<float*>(sm + kSmDw);
-  for (uint32_t i = threadIdx.x; i < kCacheWeights; i += blockDim.x) dW[i] = 0.0f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kTBar + 8);
+  const uint32_t mbar = smem_addr(sm + kTBar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(kDwCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
   const uint32_t n = count_dev ? min(*count_dev, n_max) : n_max;
   const uint32_t per = (n + n_batches - 1u) / n_batches;
   const uint32_t begin = min(batch * per, n), end = min(begin + per, n);
   const uint32_t rows_n = end - begin;
   const float scale = rows_n ? 1.0f / (3.0f * (float)rows_n) : 0.0f;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const uint32_t* Wt = reinterpret_cast<const uint32_t*>(sm + kSmWt);
   const __nv_bfloat16* Wtb = reinterpret_cast<const __nv_bfloat16*>(sm + kSmWt);
-  uint32_t* X = reinterpret_cast<uint32_t*>(sm + kSmX) + warp * 16 * kXw;
-  float4* meta = reinterpret_cast<float4*>(sm + kSmMeta) + warp * 16;
-  uint32_t* H = reinterpret_cast<uint32_t*>(sm + kSmH) + warp * 16 * kHw;
-  uint32_t* Dz = reinterpret_cast<uint32_t*>(sm + kSmDz) + warp * 16 * kHw;
-  uint32_t* Dy = reinterpret_cast<uint32_t*>(sm + kSmDy) + warp * 16 * kYw;
-  const int hstride = kTileRows * kHw;
+  // the warp's 16 rows of each block tile
+  const BlockTile X = BlockTile{reinterpret_cast<uint32_t*>(sm + kTX), kLboX / 4}.rows_from(16 * warp);
+  const BlockTile H = BlockTile{reinterpret_cast<uint32_t*>(sm + kTH), kLboH / 4}.rows_from(16 * warp);
+  const BlockTile Dz = BlockTile{reinterpret_cast<uint32_t*>(sm + kTDz), kLboH / 4}.rows_from(16 * warp);
+  const BlockTile Dy = BlockTile{reinterpret_cast<uint32_t*>(sm + kTDy), kLboY / 4}.rows_from(16 * warp);
+  const int hstride = 8 * kLboH / 4;  // words between layers
+  float4* meta = reinterpret_cast<float4*>(sm + kTMeta) + warp * 16;
   double loss = 0.0;
+  uint32_t issued = 0;  // MMA batches committed to the mbarrier
+  bool failed = false;
   const uint32_t n_tiles = (rows_n + kTileRows - 1u) / kTileRows;
   for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (issued) {
+      // the previous tile's MMAs read these tiles: wait before overwriting
+      const bool ok = mbar_wait(mbar, (issued - 1u) & 1u, kWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+    }
     const uint32_t r0 = begin + tile * kTileRows + 16u * (uint32_t)warp;
     encode_rows(net, res, rows, mat_a, mat_b, r0, end, X, meta, lane);
     float y[2][4];
@@ -602,66 +770,28 @@ __global__ void __launch_bounds__(kThreads) cache_grad_k(CacheNet net, CacheRows
         }
       }
     }
+    // the tiles' generic-proxy writes become visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    // weight gradients over the block's 64 rows: 72 units of (layer, 16 inputs, 16 outputs)
-    for (int u = warp; u < 72; u += 4) {
-      const __nv_bfloat16 *A, *B;
-      int sa, sb, mt, np, ostride, off;
-      if (u < 20) {
-        A = reinterpret_cast<const __nv_bfloat16*>(sm + kSmX);
-        sa = kXs;
-        B = reinterpret_cast<const __nv_bfloat16*>(sm + kSmDz);
-        sb = kHs;
-        mt = u >> 2;
-        np = u & 3;
-        ostride = 64;
-        off = kW1;
-      } else if (u < 68) {
-        const int L = (u - 20) >> 4;  // 0..2: dW2..dW4
-        A = reinterpret_cast<const __nv_bfloat16*>(sm + kSmH) + L * kTileRows * kHs;
-        sa = kHs;
-        B = reinterpret_cast<const __nv_bfloat16*>(sm + kSmDz) + (L + 1) * kTileRows * kHs;
-        sb = kHs;
-        mt = ((u - 20) & 15) >> 2;
-        np = (u - 20) & 3;
-        ostride = 64;
-        off = kW2 + L * 4096;
-      } else {
-        A = reinterpret_cast<const __nv_bfloat16*>(sm + kSmH) + 3 * kTileRows * kHs;
-        sa = kHs;
-        B = reinterpret_cast<const __nv_bfloat16*>(sm + kSmDy);
-        sb = kYs;
-        mt = u - 68;
-        np = 0;
-        ostride = 16;
-        off = kW5;
-      }
-      const int m = lane >> 3, r = lane & 7;
-      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        uint32_t a[4], b[4];
-        ldsm4t(a, A + (16 * ks + r + 8 * (m >> 1)) * sa + 16 * mt + 8 * (m & 1));
-        ldsm4t(b, B + (16 * ks + r + 8 * (m & 1)) * sb + 16 * np + 8 * (m >> 1));
-        mma16816(acc[0], a, b[0], b[1]);
-        mma16816(acc[1], a, b[2], b[3]);
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int col = 16 * np + 8 * h + 2 * t;
-        float2* p0 = reinterpret_cast<float2*>(&dW[off + (16 * mt + g) * ostride + col]);
-        float2* p1 = reinterpret_cast<float2*>(&dW[off + (16 * mt + g + 8) * ostride + col]);
-        const float2 v0 = *p0, v1 = *p1;
-        *p0 = make_float2(v0.x + acc[h][0], v0.y + acc[h][1]);
-        *p1 = make_float2(v1.x + acc[h][2], v1.y + acc[h][3]);
-      }
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      issue_weight_grads(sm, tmem, issued > 0);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                   : "memory");
     }
-    __syncthreads();
+    ++issued;
   }
-  for (uint32_t i = threadIdx.x; i < kCacheWeights; i += blockDim.x) {
-    const float v = dW[i];
-    if (v != 0.0f) atomicAdd(&o.gw[i], v);
-  }
+  // wait for the last batch (also after a failed wait: its MMAs may still run)
+  bool drained = true;
+  if (issued) drained = __syncthreads_or(!mbar_wait(mbar, (issued - 1u) & 1u, kWaitLimit)) == 0;
+  if ((failed || !drained) && threadIdx.x == 0 && o.err) atomicOr(o.err, kErrTimeout);
+  tc_fence_after();
+  if (issued && drained && !failed) flush_weight_grads(tmem, o.gw);
+  tc_fence_before();
+  __syncthreads();
+  // the TMEM is freed unless MMAs may still write it
+  if (warp == 0 && drained)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kDwCols) : "memory");
   if (o.loss) {
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, s);

@@ -42,6 +42,10 @@ struct CacheRows {
   float4* u;
 };
 
+// Device error word bit: a bounded wait for the tensor cores gave up (the
+// pass's results are incomplete).
+constexpr uint32_t kErrTimeout = 4u;
+
 // What a kernel writes for its rows.
 struct CacheOut {
   float4* c;      // prediction per row (nullable)
@@ -50,6 +54,7 @@ struct CacheOut {
   float* gw;      // training: weight gradients (accumulated)
   float2* gt;     // training: hash-table gradients (accumulated)
   double* loss;   // training: sum over rows and channels of the relative L2 terms
+  uint32_t* err;  // training: error word (kErrTimeout), nullable
 };
 
 // Query and record buffers of the wavefront integrator.

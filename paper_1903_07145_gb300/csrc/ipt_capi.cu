@@ -676,6 +676,7 @@ ipt_status cache_train_pass(ipt_ctx* ctx, int32_t scene, DeviceScene* s, const i
       o.gw = c->gw;
       o.gt = reinterpret_cast<float2*>(c->gt);
       o.loss = c->loss_dev + i;
+      o.err = ctx->err_dev;
       IPT_CK(ipt::cache_grad(net, c->buf.r, s->tab.mat_a, s->tab.mat_b, c->buf.counts + 1, c->buf.r_cap, i, steps, o,
                              ctx->L.num_sms, ctx->stream));
     }
@@ -1161,6 +1162,10 @@ ipt_status ipt_synchronize(ipt_ctx* ctx) {
     cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
     if (err & ipt::kErrStack)
       return fail(ctx, IPT_ERR_CUDA, "device error word " + std::to_string(err) + " (traversal stack overflow)");
+    if (err & ipt::kErrTimeout)
+      return fail(ctx, IPT_ERR_TIMEOUT,
+                  "a bounded wait for the tensor cores gave up in the radiance cache's training pass; its "
+                  "gradients are incomplete");
     return fail(ctx, IPT_ERR_NONFINITE,
                 "non-finite loss or gradient: the Adam step was skipped, parameters and Adam state are those of "
                 "the last good step");
@@ -1848,6 +1853,7 @@ ipt_status ipt_cache_grad(ipt_ctx* ctx, int32_t scene, uint32_t n, const float* 
   o.gw = c->gw;
   o.gt = reinterpret_cast<float2*>(c->gt);
   o.loss = c->loss_dev;
+  o.err = ctx->err_dev;
   {
     Timed tm(ctx, IPT_KERNEL_CACHE_GRAD);
     IPT_CK(ipt::cache_grad(cache_net(s, true), c->api, c->api_ma, c->api_mb, nullptr, n, 0, 1, o, ctx->L.num_sms,
