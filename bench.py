@@ -17,6 +17,11 @@ at vertex B (1 or 2) in the cache, which is trained online on 1 in 16
 full-length paths (a training pass per step, counted in the step's time;
 the metric still counts residual plus derivative paths).
 
+``--shard`` instead shards one room by pixels over the ranks: each rank
+traces both sample sets of a contiguous range of the views' pixels with the
+room's Philox key, one all-reduce of the S x 10 gradient and the loss joins
+them, and every rank takes the same Adam step (strong scaling).
+
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the reference arm of this comparison).
 """
@@ -249,13 +254,16 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = WORKLOAD
-    sc = make_scene(rank)
+    # --shard: every rank holds the same room and traces a contiguous range
+    # of its pixels with the same Philox key; otherwise each rank its own room
+    sc = make_scene(0 if args.shard else rank)
     if args.per_triangle:
         sc = scenes.per_triangle(sc)
     sc.cameras = sc.cameras[:w["views"]]
     opts = TraceOptions(spp_r=w["spp_r"], spp_d=w["spp_d"], max_depth=w["max_depth"], nee=True, mis=True)
     adam = AdamOptions()
-    tr = Tracer(sc, device=local, seed=1903 + rank, flags=L.IPT_FLAG_KERNEL_TIMING)
+    seed = 1903 if args.shard else 1903 + rank
+    tr = Tracer(sc, device=local, seed=seed, flags=L.IPT_FLAG_KERNEL_TIMING)
     # targets: the ground truth rendered with an independent sample set
     tr.set_params(sc.gt_params)
     target = tr.render(opts, view=-1, set_id=L.IPT_SET_TARGET, spp=w["target_spp"])
@@ -275,8 +283,21 @@ def run_ours(args, rank, world, local):
     else:
         tr.configure(args.integrator, wavefront_slots=args.slots)
     chosen = tr.config()
+    shard_iter = [0]
+
+    def step(want_loss=False):
+        """One nested-SGD iteration: the whole room on this GPU, or (--shard)
+        this rank's pixel shard, one all-reduce of the S x 10 gradient and the
+        loss over the ranks, and the same Adam step on every rank."""
+        if args.shard:
+            from paper_1903_07145_gb300 import parallel
+            loss = parallel.sharded_step(tr, opts, adam, shard_iter[0])
+            shard_iter[0] += 1
+            return loss
+        return tr.step(opts, adam, want_loss=want_loss)
+
     for _ in range(args.warmup):
-        tr.step(opts, adam, want_loss=False)
+        step()
     torch.cuda.synchronize(dev)
     tr.kernel_times(reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -292,7 +313,7 @@ def run_ours(args, rank, world, local):
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            tr.step(opts, adam, want_loss=False)
+            step()
             ev[i][1].record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
@@ -315,7 +336,7 @@ def run_ours(args, rank, world, local):
 
     # algorithmic traffic of the dominant kernel: node and triangle fetches per
     # launch, counted by a separate context with counters (same seeds, same paths)
-    ct = Tracer(sc, device=local, seed=1903 + rank, flags=L.IPT_FLAG_COUNTERS)
+    ct = Tracer(sc, device=local, seed=seed, flags=L.IPT_FLAG_COUNTERS)
     ct.configure(**chosen)
     ct.set_targets(target)
     ct.set_params(scenes.initial_params(sc, w["init"]))
@@ -341,7 +362,7 @@ def run_ours(args, rank, world, local):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         L.ipt_targets_set(tr.ctx, tr.sid, host_target.data_ptr(), 0)
-        tr.step(opts, adam, want_loss=True)
+        step(want_loss=True)
         L.ipt_params_get(tr.ctx, tr.sid, host_params.ctypes.data)
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
@@ -360,12 +381,16 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return
-    n_paths = paths_per_step() * world
+    # --shard: the ranks share one room's paths (strong scaling); otherwise
+    # each rank steps its own room (weak scaling)
+    n_paths = paths_per_step() * (1 if args.shard else world)
     value = n_paths / (ms * 1e-3) / 1e6
     # dominant kernel by total device time in the timed region
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     dom_total_ms, dom_launches = ktimes[dom]
-    both = {k: fwd_cnt[k] + adj_cnt[k] for k in fwd_cnt}
+    # counters cover the whole room; a shard traces its share of the rays
+    share = world if args.shard else 1
+    both = {k: (fwd_cnt[k] + adj_cnt[k]) / share for k in fwd_cnt}
     if dom in ("wf_closest", "wf_shadow"):
         kind = "closest" if dom == "wf_closest" else "shadow"
         nodes, tris = both[f"{kind}_node_visits"], both[f"{kind}_tri_tests"]
@@ -380,7 +405,7 @@ def run_ours(args, rank, world, local):
     # counters cover one step's passes; the timed region ran args.steps steps
     launches_per_step = dom_launches / args.steps
     # slots of one wavefront chunk: a pass of P paths in ceil(P / cap) chunks
-    pass_paths = w["spp_r"] * w["views"] * w["width"] * w["height"]
+    pass_paths = w["spp_r"] * w["views"] * w["width"] * w["height"] / share
     cap = chosen.get("wavefront_slots") or (1 << 20)
     chunk_slots = pass_paths / math.ceil(pass_paths / cap)
     alg_bytes_step = nodes * NODE_BYTES + tris * TRI_BYTES
@@ -392,11 +417,14 @@ def run_ours(args, rank, world, local):
     rays_step = both["closest_rays"] + both["shadow_rays"]
     out = {
         "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if args.shard else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD["workload"], **{k: v for k, v in WORKLOAD.items() if k != "workload"},
                    "l2": "256 MiB flush between timed steps (outside the step events)",
-                   "parallelism": f"{world} independent rooms, one per GPU",
+                   "parallelism": (f"one room in {world} pixel shards, one NCCL all-reduce of the S x 10 "
+                                   f"gradient and the loss per step" if args.shard
+                                   else f"{world} independent rooms, one per GPU"),
                    "integrator": {**chosen, "integrator": ["megakernel", "wavefront"][chosen["integrator"]]},
                    "autotune_ms": tuned},
         "mrays_per_s": rays_step / (ms * 1e-3) / 1e6,
@@ -537,12 +565,13 @@ def run_time_to_error(args):
             rooms = [scenes.cornell_variant(k) for k in range(64)]
             target_spp = 1024
         else:
-            rooms = [scenes.batch_room(k, args.res_div) for k in range(64)]
+            rooms = [scenes.batch_room(k, args.res_div) for k in range(args.rooms)]
             target_spp = 256
         opts = TraceOptions(spp_r=args.batch_spp, spp_d=args.spp_d or args.batch_spp,
                             max_depth=args.batch_depth, pixel_batch=args.pixel_batch)
         tgt = TraceOptions(max_depth=args.batch_depth)
-        ss, masks = convergence.prepare(rooms, tgt, target_spp=target_spp, init=0.0, seed=7)
+        ss, masks = convergence.prepare(rooms, tgt, target_spp=target_spp, init=args.init, seed=7,
+                                        unknowns=args.unknowns, score=args.score)
         # the batch's integrator: as given, or the faster of the two on 20
         # batch steps from the start (outside the timing; make_batch restarts
         # from the scenes' own parameters, which the steps do not touch)
@@ -561,7 +590,7 @@ def run_time_to_error(args):
         ss.configure(integrator=batch_integ, wavefront_slots=1 << 21, bvh_width=4)
         # a scene leaves the batch when it reaches the threshold, as one optimised
         # alone stops at its own crossing
-        first, hist = convergence.time_to_error(ss, masks, opts, adam, threshold=0.01,
+        first, hist = convergence.time_to_error(ss, masks, opts, adam, threshold=args.threshold,
                                                 max_iters=args.max_iters, check_every=args.check_every,
                                                 halve_every=args.halve_every, retire=not args.no_retire)
         res["batched"] = {"first": first, "history_last": hist[-1][:2], "integrator": batch_integ,
@@ -570,18 +599,30 @@ def run_time_to_error(args):
         # the plain arm: each scene alone with its fastest integrator
         # configuration (autotuned on its own workload, outside the timing)
         from paper_1903_07145_gb300 import autotune
-        seq, seq_cfg = [], []
+        seq, seq_cfg, seq_hist = [], [], []
         for i, sc in enumerate(rooms[:args.seq_rooms]):
-            tr, m = convergence.prepare_single(sc, tgt, target_spp=target_spp, seed=7)
+            tr, m = convergence.prepare_single(sc, tgt, target_spp=target_spp, seed=7, init=args.init,
+                                               unknowns=args.unknowns, score=args.score)
             p0 = tr.get_params()
             best, _ = autotune.tune(tr, lambda: tr.loss_grad(opts, iteration=0), repeats=3)
-            tr.set_params(p0, free_mask=convergence.diffuse_and_emission_mask(sc).astype(np.uint8))
+            tr.set_params(p0, free_mask=convergence.unknowns_mask(sc, args.unknowns).astype(np.uint8))
             seq_cfg.append(best.get("integrator"))
-            f, _ = convergence.time_to_error_single(tr, m, opts, adam, threshold=0.01, max_iters=args.max_iters,
+            f, h = convergence.time_to_error_single(tr, m, opts, adam, threshold=args.threshold,
+                                                    max_iters=args.max_iters,
                                                     check_every=args.check_every, halve_every=args.halve_every)
             seq.append(f)
+            seq_hist.append(h)
             tr.close()
-        res["sequential_plain"] = {"first": seq, "integrators": seq_cfg}
+        res["sequential_plain"] = {"first": seq, "integrators": seq_cfg,
+                                   "final_error": [h[-1][2] for h in seq_hist]}
+        res["batched"]["final_error"] = hist[-1][2]
+
+        # first crossings of looser thresholds, from the error histories (the
+        # runs stop at --threshold or --max-iters)
+        def crossings(thr):
+            b = [next(((it, t) for it, t, errs in hist if errs[i] <= thr), None) for i in range(len(rooms))]
+            q = [next(((h_[0], h_[1]) for h_ in hh if h_[2] <= thr), None) for hh in seq_hist]
+            return b, q
 
         def summary(fs):
             t = np.array([f[1] for f in fs if f is not None])
@@ -616,9 +657,18 @@ def run_time_to_error(args):
                 "scenes": len(reached), "batched_wall_s": max(f[1] for f in reached),
                 "sequential_s_estimate": sum(f[0] for f in reached) * it_alone,
                 "speedup": sum(f[0] for f in reached) * it_alone / max(f[1] for f in reached)}}
+        res["thresholds"] = {}
+        for thr in sorted({args.threshold, 0.02, 0.05, 0.1}):
+            b, q = crossings(thr)
+            both = [i for i in range(len(q)) if b[i] is not None and q[i] is not None]
+            res["thresholds"][f"{thr:g}"] = {
+                "batched": summary(b), "sequential_plain": summary(q), "scenes_compared": len(both),
+                "batched_wall_s_compared": max((b[i][1] for i in both), default=None),
+                "sequential_sum_s_compared": sum(q[i][1] for i in both) if both else None}
         workload = ("cornell64_variants" if args.workload == "cornell64" else f"batch64_rooms_div{args.res_div}")
         workload += f"_pixbatch{args.pixel_batch}" if args.pixel_batch else ""
-    print(json.dumps({"metric": "time to 1% parameter error", "unit": "s", "workload": workload,
+    print(json.dumps({"metric": f"time to {100 * args.threshold:g}% parameter error", "unit": "s",
+                      "workload": workload, "unknowns": args.unknowns, "score": args.score, "init": args.init,
                       "lr": args.lr, "halve_every": args.halve_every, "retire": not args.no_retire,
                       "spp": args.batch_spp,
                       "spp_d": args.spp_d or args.batch_spp, "pixel_batch": args.pixel_batch,
@@ -754,6 +804,15 @@ def main():
     ap.add_argument("--halve-every", type=int, default=0,
                     help="time-to-error: halve the learning rate every N iterations (0 = constant)")
     ap.add_argument("--max-iters", type=int, default=6000)
+    ap.add_argument("--threshold", type=float, default=0.01, help="time-to-error: relative parameter error")
+    ap.add_argument("--unknowns", default="kd_e", choices=["kd_e", "kd", "material"],
+                    help="time-to-error: free parameters (kd_e: diffuse albedo + emission; kd: diffuse albedo; "
+                         "material: diffuse, specular albedo, roughness); the rest held at the truth")
+    ap.add_argument("--score", default="legacy", choices=["legacy", "survey"],
+                    help="time-to-error: legacy (free parameters of seen segments, not the lights' albedo) or "
+                         "survey (albedos, emission of seen segments, roughness where lum(ks) >= 0.05)")
+    ap.add_argument("--init", type=float, default=0.0, help="time-to-error: start value of the unknowns")
+    ap.add_argument("--rooms", type=int, default=64, help="time-to-error: the first N of the 64 procedural rooms")
     ap.add_argument("--sweep", default=None, choices=["paths", "split", "batch", "mis", "bounces", "all"],
                     help="optimiser ablation curves (paths per pixel, sample split, batch size, MIS, bounces)")
     ap.add_argument("--sweep-seconds", type=float, default=8.0, help="optimisation time per sweep setting")
@@ -767,6 +826,8 @@ def main():
                     help="profiling only: use the first V views (not a benchmark line)")
     ap.add_argument("--spp", type=int, default=None,
                     help="profiling only: spp_r = spp_d = S (not a benchmark line)")
+    ap.add_argument("--shard", action="store_true",
+                    help="one room sharded by pixels over the GPUs (strong scaling), NCCL all-reduce per step")
     ap.add_argument("--slots", type=int, default=0,
                     help="profiling only: wavefront path slots per chunk with --integrator wavefront")
     args = ap.parse_args()
@@ -806,15 +867,25 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if world > 1:
+    if args.shard and args.cache:
+        raise SystemExit("--shard runs the plain estimator (no --cache)")
+    dist_on = world > 1 or args.shard
+    if dist_on:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if world > 1:
+            dist.init_process_group("nccl")
+        else:  # one shard: a single-rank group, so the step runs the same all-reduce
+            import socket
+            with socket.socket() as so:
+                so.bind(("127.0.0.1", 0))
+                port = so.getsockname()[1]
+            dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
     try:
         run_ours(args, rank, world, local)
     finally:
-        if world > 1:
+        if dist_on:
             import torch.distributed as dist
             dist.destroy_process_group()
 

@@ -1,12 +1,12 @@
 """Time to a parameter-error threshold for one scene or a batch.
 
 The measured quantity is the wall time (and the number of iterations) until
-a member's parameter error first falls to the threshold.  The unknowns are
-the diffuse albedo and emission of every segment (the quantities the paper
-evaluates, Table 1); specular albedo and roughness are held at their true
-values through the free mask, because without a Fresnel term a rough GGX
-lobe can stand in for a Lambertian one and a few views cannot tell them
-apart.  The error covers segments that a pixel centre sees, except the
+a member's parameter error first falls to the threshold.  By default the
+unknowns are the diffuse albedo and emission of every segment (the
+quantities the paper evaluates, Table 1); specular albedo and roughness are
+held at their true values through the free mask, because without a Fresnel
+term a rough GGX lobe can stand in for a Lambertian one and a few views
+cannot tell them apart (unknowns_mask and scored_mask select other sets).  The error covers segments that a pixel centre sees, except the
 diffuse albedo of emitting segments: an emitter's appearance is almost all
 emission (Sec. 4 notes the same emission/albedo trade-off for objects in
 few pixels), so its albedo is left free but not scored.  Iterations run as batch-graph replays; the error is read every
@@ -26,15 +26,32 @@ from .tracer import AdamOptions, TraceOptions, Tracer
 
 
 def diffuse_and_emission_mask(scene) -> np.ndarray:
+    return unknowns_mask(scene, "kd_e")
+
+
+def unknowns_mask(scene, kind: str = "kd_e") -> np.ndarray:
+    """The free parameters of an optimisation: "kd_e" diffuse albedo and
+    emission (the rest at the truth), "kd" diffuse albedo only, "material"
+    diffuse and specular albedo and roughness (emission at the truth)."""
     m = np.zeros((scene.n_segments, 10), bool)
     m[:, 0:3] = True
-    m[:, 7:10] = True
+    if kind == "kd_e":
+        m[:, 7:10] = True
+    elif kind == "material":
+        m[:, 3:7] = True
+    elif kind != "kd":
+        raise ValueError(kind)
     return m
 
 
-def scored_mask(scene, free, visible) -> np.ndarray:
-    """Parameters the error scores: free ones of visible segments, without
-    the diffuse albedo of emitting segments."""
+def scored_mask(scene, free, visible, score: str = "legacy") -> np.ndarray:
+    """Parameters the error scores.  "legacy": free ones of visible segments,
+    without the diffuse albedo of emitting segments.  "survey": the
+    identifiable set of metrics.identifiable_mask (diffuse and specular
+    albedo and emission of visible segments, roughness where the true
+    specular albedo has luminance >= 0.05) among the free parameters."""
+    if score == "survey":
+        return metrics.identifiable_mask(scene.gt_params, visible) & free
     m = free.copy()
     m[~visible] = False
     m[np.asarray(scene.light_segments, int), 0:3] = False
@@ -42,7 +59,7 @@ def scored_mask(scene, free, visible) -> np.ndarray:
 
 
 def prepare(scenes, opts: TraceOptions, target_spp: int = 1024, init: float = 0.0, seed: int = 0,
-            configure=None):
+            configure=None, unknowns: str = "kd_e", score: str = "legacy"):
     """Context with every scene uploaded, targets rendered from the ground
     truth (sample set 2), and the unknowns reset to `init`."""
     ss = SceneSet(scenes, seed=seed)
@@ -52,14 +69,14 @@ def prepare(scenes, opts: TraceOptions, target_spp: int = 1024, init: float = 0.
     for i, sc in enumerate(scenes):
         ss.set_params(i, sc.gt_params)
         ss.set_targets(i, ss.render(i, opts, spp=target_spp))
-        free = diffuse_and_emission_mask(sc)
+        free = unknowns_mask(sc, unknowns)
         p0 = sc.gt_params.copy()
         p0[free] = init
         ss.set_params(i, p0, free_mask=free.astype(np.uint8))
         tr = Tracer(sc)
         vis = metrics.visible_segments(tr, sc)
         tr.close()
-        masks.append(scored_mask(sc, free, vis))
+        masks.append(scored_mask(sc, free, vis, score))
     return ss, masks
 
 
@@ -102,17 +119,17 @@ def time_to_error(ss: SceneSet, masks, opts: TraceOptions, adam: AdamOptions, th
 
 
 def prepare_single(scene, opts: TraceOptions, target_spp: int = 1024, init: float = 0.0, seed: int = 0,
-                   device: int = 0):
+                   device: int = 0, unknowns: str = "kd_e", score: str = "legacy"):
     """One-scene counterpart of prepare(): a Tracer with targets rendered from
     the ground truth (sample set 2) and the unknowns reset to `init`."""
     tr = Tracer(scene, device=device, seed=seed)
     tr.set_params(scene.gt_params)
     tr.set_targets(tr.render(opts, view=-1, set_id=2, spp=target_spp))
-    free = diffuse_and_emission_mask(scene)
+    free = unknowns_mask(scene, unknowns)
     p0 = scene.gt_params.copy()
     p0[free] = init
     tr.set_params(p0, free_mask=free.astype(np.uint8))
-    return tr, scored_mask(scene, free, metrics.visible_segments(tr, scene))
+    return tr, scored_mask(scene, free, metrics.visible_segments(tr, scene), score)
 
 
 def time_to_error_single(tr: Tracer, mask, opts: TraceOptions, adam: AdamOptions, threshold: float = 0.01,

@@ -40,8 +40,7 @@ constexpr int kThreads = 128;   // 4 warps
 constexpr int kTileRows = 64;   // rows of one block tile (16 per warp)
 constexpr int kXs = 88;         // BF16 row stride of the input tile and W1t
 constexpr int kHs = 72;         // hidden tiles, W2t..W5t
-constexpr int kYs = 24;         // output-gradient tile
-constexpr int kXw = kXs / 2, kHw = kHs / 2, kYw = kYs / 2;  // strides in 32-bit words
+constexpr int kXw = kXs / 2, kHw = kHs / 2;  // strides in 32-bit words
 
 // BF16 weight image offsets (elements).
 constexpr int kWt1 = 0, kWt2 = 64 * kXs, kWt3 = kWt2 + 64 * kHs, kWt4 = kWt3 + 64 * kHs, kWt5 = kWt4 + 64 * kHs;

@@ -105,3 +105,79 @@ def test_sharded_equals_unsharded(world):
     assert abs(ref_loss - l2) <= 1e-12 * abs(l2) and np.allclose(ref_grad, g2, rtol=1e-12, atol=1e-14)
     assert abs(loss - ref_loss) <= 1e-12 * abs(ref_loss)
     assert np.allclose(grad, ref_grad, rtol=1e-10, atol=1e-12)
+
+
+class _OracleTracer:
+    """The attributes and calls parallel.sharded_step uses (device, n_pix,
+    n_seg, loss_grad_shard, adam_step), computed by the oracle on the CPU:
+    a GPU rank's Tracer stands in for it on a GPU machine."""
+
+    def __init__(self, osc, params, targets):
+        self.osc, self.targets = osc, targets
+        self.device = torch.device("cpu")
+        self.n_pix = int(osc.offsets[-1])
+        self.n_seg = osc.n_seg
+        self.params = np.array(params, np.float64)
+        self.m = np.zeros_like(self.params)
+        self.v = np.zeros_like(self.params)
+        self.t = 0
+
+    def loss_grad_shard(self, opts, iteration, begin, count, n_total):
+        return _oracle_shard(self.osc, self.params, self.targets, begin, count, n_total, iteration)
+
+    def adam_step(self, adam, grad):
+        from oracle import oracle as O
+        self.t += 1
+        self.params, self.m, self.v = O.adam_update(self.params, grad.numpy().astype(np.float64), self.m, self.v,
+                                                    self.t, lr=adam["lr"])
+
+
+def _step_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import oracle as O
+        from paper_1903_07145_gb300.parallel import sharded_step
+        sc = _scene()
+        osc = O.OracleScene(sc)
+        rng = np.random.default_rng(0)
+        targets = [rng.uniform(0, 1, (c.width * c.height, 3)) for c in sc.cameras]
+        tr = _OracleTracer(osc, sc.gt_params.astype(np.float64) * 0.9, targets)
+        losses = [sharded_step(tr, None, {"lr": 1e-2}, it) for it in range(3)]
+        q.put((rank, losses, tr.params))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_step_equals_unsharded_optimisation():
+    """Three iterations of parallel.sharded_step on two gloo ranks: every rank
+    ends with the same parameters, and they equal three unsharded oracle
+    iterations (loss, gradient cast to FP32 as a GPU rank hands it to Adam,
+    Adam)."""
+    from oracle import oracle as O
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_step_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = dict((r, (l, p)) for r, l, p in (q.get(timeout=300) for _ in range(world)))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    assert np.array_equal(got[0][1], got[1][1])
+    sc = _scene()
+    osc = O.OracleScene(sc)
+    rng = np.random.default_rng(0)
+    targets = [rng.uniform(0, 1, (c.width * c.height, 3)) for c in sc.cameras]
+    p = sc.gt_params.astype(np.float64) * 0.9
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    n = int(osc.offsets[-1])
+    for it in range(3):
+        loss, grad = _oracle_shard(osc, p, targets, 0, n, n, it)
+        assert abs(got[0][0][it] - loss) <= 1e-12 * abs(loss)
+        p, m, v = O.adam_update(p, grad.astype(np.float32).astype(np.float64), m, v, it + 1, lr=1e-2)
+    assert np.allclose(got[0][1], p, rtol=0, atol=1e-7), np.abs(got[0][1] - p).max()
