@@ -281,7 +281,7 @@ def run_ours(args, rank, world, local):
                                     wavefront_only=bool(args.cache))
         tr.set_params(scenes.initial_params(sc, w["init"]))
     else:
-        tr.configure(args.integrator, wavefront_slots=args.slots)
+        tr.configure(args.integrator, wavefront_slots=args.slots, bvh_width=args.bvh_width)
     chosen = tr.config()
     shard_iter = [0]
 
@@ -828,6 +828,8 @@ def main():
                     help="profiling only: spp_r = spp_d = S (not a benchmark line)")
     ap.add_argument("--shard", action="store_true",
                     help="one room sharded by pixels over the GPUs (strong scaling), NCCL all-reduce per step")
+    ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4, 8],
+                    help="profiling only: BVH width with --integrator wavefront or megakernel")
     ap.add_argument("--slots", type=int, default=0,
                     help="profiling only: wavefront path slots per chunk with --integrator wavefront")
     args = ap.parse_args()

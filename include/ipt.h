@@ -115,8 +115,12 @@ typedef struct {
  *     (0 = 16).
  *   blocks_per_sm: persistent blocks per SM for the wavefront kernels (0 =
  *     as many as fit).
- *   bvh_width: BVH used by the wavefront traversal: 2 = binary nodes with
- *     float boxes, 4 = 4-wide nodes with 8-bit child boxes (0 = 4). */
+ *   bvh_width: BVH the traversal walks (every integrator, and
+ *     ipt_trace_rays): 2 = binary nodes with float boxes, 4 = 4-wide nodes
+ *     with 8-bit child boxes visited nearest first, 8 = 8-wide nodes with
+ *     8-bit child boxes whose children sit in slots by octant and are
+ *     visited in the ray's octant order (0 = 4).  All three give the same
+ *     closest hits up to exact ties. */
 typedef struct {
   int32_t integrator;
   uint32_t wavefront_slots;

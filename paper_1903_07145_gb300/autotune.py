@@ -1,6 +1,7 @@
 """Picks the integrator configuration of a context by measurement.
 
-Candidates: the megakernel, and the wavefront integrator with two chunk
+Candidates: the megakernel, and the wavefront integrator with the three BVH
+widths (binary, 4-wide sorted by distance, 8-wide in octant order), two chunk
 sizes (2M path slots, and 32M, which holds a whole pass of most workloads in
 one chunk: no drain tail between chunks, fewer launches) and two traversal
 refill granularities.  Each candidate runs one
@@ -18,7 +19,7 @@ import torch
 DEFAULT_CANDIDATES = (
     [dict(integrator="megakernel")]
     + [dict(integrator="wavefront", wavefront_slots=s, trace_steps=k, bvh_width=b)
-       for b, s, k in itertools.product([2, 4], [1 << 21, 1 << 25], [8, 16])]
+       for b, s, k in itertools.product([2, 4, 8], [1 << 21, 1 << 25], [8, 16])]
 )
 
 

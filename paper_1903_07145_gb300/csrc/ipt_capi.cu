@@ -77,9 +77,10 @@ void stage_end(void* user) {
 ipt::SceneBuffers buffers(const ipt_ctx* ctx, const DeviceScene* s) {
   ipt::SceneBuffers b;
   b.counters = ctx->counters_dev;
-  b.wide = ctx->cfg.bvh_width != 2 ? 1 : 0;
+  b.wide = ctx->cfg.bvh_width == 2 ? 0 : (ctx->cfg.bvh_width == 8 ? 2 : 1);
   b.nodes = s->nodes;
   b.nodes4 = s->nodes4;
+  b.nodes8 = s->nodes8;
   b.tris = s->tris;
   b.vnrm = s->vnrm;
   b.seg_tris = s->seg_tris;
@@ -630,6 +631,7 @@ ipt_status ipt_scene_upload(ipt_ctx* ctx, const float* pos, uint32_t n_vert, con
   };
   A(&s->nodes, 4 * (size_t)hs.n_nodes);
   A(&s->nodes4, 4 * (size_t)hs.n_nodes4);
+  A(&s->nodes8, 6 * (size_t)hs.n_nodes8);
   A(&s->tris, 3 * (size_t)n_tri);
   if (!hs.vnrm.empty()) A(&s->vnrm, 3 * (size_t)n_tri);
   A(&s->seg_tris, n_tri);
@@ -660,6 +662,7 @@ ipt_status ipt_scene_upload(ipt_ctx* ctx, const float* pos, uint32_t n_vert, con
   };
   H(s->nodes, hs.nodes.data(), hs.nodes.size() * sizeof(float));
   H(s->nodes4, hs.nodes4.data(), hs.nodes4.size() * sizeof(uint32_t));
+  H(s->nodes8, hs.nodes8.data(), hs.nodes8.size() * sizeof(uint32_t));
   H(s->tris, hs.tris.data(), hs.tris.size() * sizeof(float));
   if (s->vnrm) H(s->vnrm, hs.vnrm.data(), hs.vnrm.size() * sizeof(float));
   H(s->seg_tris, hs.seg_tris.data(), hs.seg_tris.size() * sizeof(uint32_t));
@@ -960,8 +963,8 @@ ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg) {
   if (cfg->wavefront_slots && cfg->wavefront_slots < 1024)
     return fail(ctx, IPT_ERR_INVALID_ARG, "wavefront_slots must be 0 or at least 1024");
   if (cfg->trace_steps > 4096) return fail(ctx, IPT_ERR_INVALID_ARG, "trace_steps above 4096");
-  if (cfg->bvh_width != 0 && cfg->bvh_width != 2 && cfg->bvh_width != 4)
-    return fail(ctx, IPT_ERR_INVALID_ARG, "bvh_width must be 0, 2 or 4");
+  if (cfg->bvh_width != 0 && cfg->bvh_width != 2 && cfg->bvh_width != 4 && cfg->bvh_width != 8)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "bvh_width must be 0, 2, 4 or 8");
   IPT_CK(cudaSetDevice(ctx->device));
   const uint32_t old_cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
   const uint32_t new_cap = cfg->wavefront_slots ? cfg->wavefront_slots : (1u << 20);

@@ -103,6 +103,7 @@ struct DeviceScene {
   // geometry
   float4* nodes = nullptr;
   uint4* nodes4 = nullptr;
+  uint4* nodes8 = nullptr;
   float4* tris = nullptr;
   float4* vnrm = nullptr;
   uint32_t* seg_tris = nullptr;

@@ -79,6 +79,7 @@ struct PathRng {
 struct SceneDev {
   const float4* nodes;
   const uint4* nodes4;  // 4-wide quantized nodes (4 x uint4 each), or nullptr
+  const uint4* nodes8;  // 8-wide quantized nodes (6 x uint4 each), or nullptr
   const float4* tris;
   const float4* vnrm;
   const uint32_t* seg_tris;
@@ -89,7 +90,7 @@ struct SceneDev {
   uint32_t n_tri;
   float eps;  // spawn offset along the oriented geometric normal
   unsigned long long* counters;  // optional: closest rays, shadow rays, node visits, triangle tests
-  int wide;   // traverse the 4-wide quantized BVH
+  int wide;   // 0: binary BVH, 1: 4-wide, 2: 8-wide quantized BVH
 };
 
 // kind 0: closest-hit ray, 1: shadow ray
@@ -312,6 +313,63 @@ __device__ __forceinline__ uint32_t node4_children(const SceneDev& s, int node, 
     mask |= hit ? (1u << i) : 0u;
   }
   return mask;
+}
+
+// ---------------------------------------------------------------------------
+// 8-wide node with 8-bit child boxes (96 bytes; the node test reads the first
+// 64 with two 256-bit loads, the slots' links are read one at a time as the
+// slots are entered).  Children sit in slots by octant (see the scene
+// builder), so a ray visits the slots in the order of (slot ^ sgn), sgn the
+// sign bits of its direction: no sort, and one stack entry per node (its
+// remaining hit slots) instead of one per child.  Returns the mask of hit
+// slots in visiting order (bit k: slot k ^ sgn); the plane arithmetic and
+// its conservative margins are those of node4_children.
+__device__ __forceinline__ uint32_t node8_hits(const SceneDev& s, int node, const RayPre& r, float tmax,
+                                               uint32_t sgn) {
+  uint4 a, b, c, d;
+  load_node4(&s.nodes8[6 * node], a, b, c, d);  // words 0-7 (a, b) and 8-15 (c, d)
+  const float sx = __uint_as_float(((a.w & 0xffu) + 15u) << 23);
+  const float sy = __uint_as_float((((a.w >> 8) & 0xffu) + 15u) << 23);
+  const float sz = __uint_as_float((((a.w >> 16) & 0xffu) + 15u) << 23);
+  const uint32_t valid = a.w >> 24;
+  const float Ax = sx * r.inv.x, Bx = fmaf(__uint_as_float(a.x) - r.o.x, r.inv.x, -Ax);
+  const float Ay = sy * r.inv.y, By = fmaf(__uint_as_float(a.y) - r.o.y, r.inv.y, -Ay);
+  const float Az = sz * r.inv.z, Bz = fmaf(__uint_as_float(a.z) - r.o.z, r.inv.z, -Az);
+  const float Bnx = fmaf(fabsf(Ax), -0x1p-22f, Bx), Bfx = fmaf(fabsf(Ax), 0x1p-22f, Bx);
+  const float Bny = fmaf(fabsf(Ay), -0x1p-22f, By), Bfy = fmaf(fabsf(Ay), 0x1p-22f, By);
+  const float Bnz = fmaf(fabsf(Az), -0x1p-22f, Bz), Bfz = fmaf(fabsf(Az), 0x1p-22f, Bz);
+  const bool nx = sgn & 1u, ny = sgn & 2u, nz = sgn & 4u;
+  // near / far plane words of slots 0-3 (index 0) and 4-7 (index 1)
+  const uint32_t nwx[2] = {nx ? b.z : b.x, nx ? b.w : b.y}, fwx[2] = {nx ? b.x : b.z, nx ? b.y : b.w};
+  const uint32_t nwy[2] = {ny ? c.z : c.x, ny ? c.w : c.y}, fwy[2] = {ny ? c.x : c.z, ny ? c.y : c.w};
+  const uint32_t nwz[2] = {nz ? d.z : d.x, nz ? d.w : d.y}, fwz[2] = {nz ? d.x : d.z, nz ? d.y : d.w};
+  uint32_t mask = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int h = i >> 2, q = i & 3;
+    const float tnx = fmaf(q_unit(nwx[h], q), Ax, Bnx), tfx = fmaf(q_unit(fwx[h], q), Ax, Bfx);
+    const float tny = fmaf(q_unit(nwy[h], q), Ay, Bny), tfy = fmaf(q_unit(fwy[h], q), Ay, Bfy);
+    const float tnz = fmaf(q_unit(nwz[h], q), Az, Bnz), tfz = fmaf(q_unit(fwz[h], q), Az, Bfz);
+    const float tnear = max3f(tnx, tny, fmaxf(tnz, 0.0f));
+    const float tfar = min3f(tfx, tfy, fminf(tfz, tmax)) * 1.0000005f;
+    mask |= (tnear <= tfar ? 1u : 0u) << (i ^ (int)sgn);
+  }
+  // empty slots: their bit moves with the same permutation
+  uint32_t vp = valid;
+  if (sgn & 1u) vp = ((vp & 0x55u) << 1) | ((vp >> 1) & 0x55u);
+  if (sgn & 2u) vp = ((vp & 0x33u) << 2) | ((vp >> 2) & 0x33u);
+  if (sgn & 4u) vp = ((vp & 0x0fu) << 4) | ((vp >> 4) & 0x0fu);
+  return mask & vp;
+}
+
+// Link of slot `slot` of 8-wide node `node`.
+__device__ __forceinline__ int node8_link(const SceneDev& s, int node, int slot) {
+  return (int)__ldg(reinterpret_cast<const uint32_t*>(&s.nodes8[6 * node]) + 16 + slot);
+}
+
+// Direction sign bits of a ray (bit k set: component k negative).
+__device__ __forceinline__ uint32_t ray_sgn(const RayPre& r) {
+  return (r.inv.x < 0.0f ? 1u : 0u) | (r.inv.y < 0.0f ? 2u : 0u) | (r.inv.z < 0.0f ? 4u : 0u);
 }
 
 // Sorts four (distance, link) pairs by distance (misses carry +inf).
@@ -592,13 +650,111 @@ __device__ __forceinline__ bool trace_any4(const SceneDev& s, float3 o, float3 d
   return false;
 }
 
+// The same two queries over the 8-wide quantized BVH: a stack entry is a
+// node and the mask of its hit slots not yet entered (visiting order).
+template <bool kAny>
+__device__ __forceinline__ void trace8(const SceneDev& s, const RayPre& r, float tmax, int skip_a, int skip_b,
+                                       Hit& h, bool& occluded, uint32_t* err) {
+  const uint32_t sgn = ray_sgn(r);
+  uint2 stack[kStackSize];
+  int sp = 0;
+  int best_orig = 0x7fffffff;
+  int gnode = 0;
+  uint32_t gmask = node8_hits(s, 0, r, tmax, sgn);
+  uint32_t n_nodes = 1, n_tests = 0;
+  for (;;) {
+    while (gmask == 0) {
+      if (sp == 0) {
+        count_ray(s, kAny ? 1 : 0, n_nodes, n_tests);
+        return;
+      }
+      --sp;
+      gnode = (int)stack[sp].x;
+      gmask = stack[sp].y;
+    }
+    const int k = __ffs(gmask) - 1;
+    gmask &= gmask - 1u;
+    const int ref = node8_link(s, gnode, k ^ (int)sgn);
+    if (ref >= 0) {
+      ++n_nodes;
+      const uint32_t m = node8_hits(s, ref, r, kAny ? tmax : h.t, sgn);
+      if (m) {
+        if (gmask) {
+          if (sp >= kStackSize) {
+            atomicOr(err, kErrStack);
+            h.tri = -1;
+            occluded = true;
+            return;
+          }
+          stack[sp++] = make_uint2((uint32_t)gnode, gmask);
+        }
+        gnode = ref;
+        gmask = m;
+      }
+      continue;
+    }
+    int first, count;
+    decode_leaf(ref, first, count);
+    n_tests += count;
+    for (int i = first; i < first + count; ++i) {
+      if (i == skip_a || i == skip_b) continue;
+      const float4 q0 = __ldg(&s.tris[3 * i + 0]);
+      const float4 q1 = __ldg(&s.tris[3 * i + 1]);
+      const float4 q2 = __ldg(&s.tris[3 * i + 2]);
+      float t, u, v;
+      if (kAny) {
+        if (tri_test(r, xyz(q0), xyz(q1), xyz(q2), tmax, t, u, v)) {
+          occluded = true;
+          count_ray(s, 1, n_nodes, n_tests);
+          return;
+        }
+      } else if (tri_test(r, xyz(q0), xyz(q1), xyz(q2), h.t * 1.0000002f, t, u, v)) {
+        const int orig = __float_as_int(q0.w);
+        if (t < h.t || (t == h.t && orig < best_orig)) {
+          h.tri = i;
+          h.t = t;
+          h.u = u;
+          h.v = v;
+          best_orig = orig;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ Hit trace_closest8(const SceneDev& s, float3 o, float3 d, float tmax, int skip,
+                                              uint32_t* err) {
+  const RayPre r = ray_pre(o, d);
+  Hit h;
+  h.tri = -1;
+  h.t = tmax;
+  h.u = h.v = 0.0f;
+  bool occ = false;
+  trace8<false>(s, r, tmax, skip, -1, h, occ, err);
+  return h;
+}
+
+__device__ __forceinline__ bool trace_any8(const SceneDev& s, float3 o, float3 d, float tmax, int skip_a,
+                                           int skip_b, uint32_t* err) {
+  const RayPre r = ray_pre(o, d);
+  Hit h;
+  h.tri = -1;
+  h.t = tmax;
+  h.u = h.v = 0.0f;
+  bool occ = false;
+  trace8<true>(s, r, tmax, skip_a, skip_b, h, occ, err);
+  return occ;
+}
+
 __device__ __forceinline__ Hit trace_closest(const SceneDev& s, float3 o, float3 d, float tmax, int skip,
                                              uint32_t* err) {
+  if (s.wide == 2) return trace_closest8(s, o, d, tmax, skip, err);
   return s.wide ? trace_closest4(s, o, d, tmax, skip, err) : trace_closest2(s, o, d, tmax, skip, err);
 }
 
 __device__ __forceinline__ bool trace_any(const SceneDev& s, float3 o, float3 d, float tmax, int skip_a,
                                           int skip_b, uint32_t* err) {
+  if (s.wide == 2) return trace_any8(s, o, d, tmax, skip_a, skip_b, err);
   return s.wide ? trace_any4(s, o, d, tmax, skip_a, skip_b, err) : trace_any2(s, o, d, tmax, skip_a, skip_b, err);
 }
 

@@ -15,6 +15,8 @@ struct HostScene {
   std::vector<float> nodes;      // 16 floats per inner node
   std::vector<uint32_t> nodes4;  // 16 words per 4-wide quantized node
   uint32_t n_nodes4 = 0;
+  std::vector<uint32_t> nodes8;  // 24 words per 8-wide quantized node
+  uint32_t n_nodes8 = 0;
   std::vector<float> tris;       // 12 floats per triangle (leaf order)
   std::vector<float> vnrm;       // 12 floats per triangle, empty if no normals
   std::vector<uint32_t> orig_to_internal;
@@ -34,6 +36,7 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
 struct SceneBuffers {
   const float4* nodes;
   const uint4* nodes4;
+  const uint4* nodes8;
   const float4* tris;
   const float4* vnrm;
   const uint32_t* seg_tris;
@@ -45,7 +48,7 @@ struct SceneBuffers {
   float eps;
   float emission_scale;
   unsigned long long* counters;  // nullptr unless counting
-  int wide;                      // traverse the 4-wide quantized BVH
+  int wide;                      // 0: binary BVH, 1: 4-wide, 2: 8-wide quantized BVH
 };
 
 // Per-segment parameter tables (device).

@@ -55,6 +55,7 @@ inline SceneDev scene_dev(const SceneBuffers& s) {
   SceneDev d;
   d.nodes = s.nodes;
   d.nodes4 = s.nodes4;
+  d.nodes8 = s.nodes8;
   d.tris = s.tris;
   d.vnrm = s.vnrm;
   d.seg_tris = s.seg_tris;

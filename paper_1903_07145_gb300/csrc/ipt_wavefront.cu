@@ -191,7 +191,10 @@ struct Trav {
   float tmax;
   int skip_a, skip_b;
   int node, sp;
-  int tri, tri_end;  // 4-wide traversal: triangles of the current leaf still to test
+  int tri, tri_end;  // wide traversals: triangles of the current leaf still to test
+  int gnode;         // 8-wide: node whose hit slots are being entered
+  uint32_t gmask;    // 8-wide: its hit slots not yet entered (visiting order)
+  uint32_t sgn;      // 8-wide: direction sign bits of the ray
   uint2 deep[kStackSize - kShortStack];
   int best, best_orig;
   float bt, bu, bv;
@@ -222,6 +225,9 @@ __device__ __forceinline__ void trav_init(Trav& T, float3 o, float3 d, float tma
   T.node = 0;
   T.sp = 0;
   T.tri = T.tri_end = 0;
+  T.gnode = 0;
+  T.gmask = 0u;
+  T.sgn = ray_sgn(T.r);
   T.best = -1;
   T.best_orig = 0x7fffffff;
   T.bt = tmax;
@@ -393,10 +399,54 @@ __device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh,
   return false;
 }
 
+// 8-wide quantized nodes: each step tests one node or one triangle, then
+// enters the next hit slot (visiting order by the ray's octant; see
+// node8_hits).  A tested node with hits becomes the current group; the
+// group it replaces, if it still has slots, goes on the stack as (node,
+// remaining slots).  Entered leaves are not re-tested against a closer hit
+// (their triangle tests are).
+template <bool kAny>
+__device__ __forceinline__ bool trav_run8(const SceneDev& s, Trav& T, uint2* sh, int steps, uint32_t* err) {
+  for (int it = 0; it < steps; ++it) {
+    if (T.tri < T.tri_end) {
+      if (tri_unit<kAny>(s, T)) return true;
+      if (T.tri < T.tri_end) continue;
+    } else if (T.node >= 0) {
+      ++T.n_nodes;
+      const uint32_t m = node8_hits(s, T.node, T.r, kAny ? T.tmax : T.bt, T.sgn);
+      if (m) {
+        if (T.gmask) {
+          if (T.sp >= kStackSize) {
+            atomicOr(err, kErrStack);
+            T.best = -1;
+            T.occluded = true;
+            return true;
+          }
+          st_push(sh, T, T.gnode, __uint_as_float(T.gmask));
+        }
+        T.gnode = T.node;
+        T.gmask = m;
+      }
+      T.node = -1;
+    }
+    while (T.gmask == 0u) {
+      if (T.sp == 0) return true;
+      const uint2 e = st_pop(sh, T);
+      T.gnode = (int)e.x;
+      T.gmask = e.y;
+    }
+    const int k = __ffs(T.gmask) - 1;
+    T.gmask &= T.gmask - 1u;
+    trav_enter(T, node8_link(s, T.gnode, k ^ (int)T.sgn));
+  }
+  return false;
+}
+
 // Lanes run rounds of `steps` node visits; between rounds the warp fetches
 // new rays for the lanes whose ray has finished (one atomic per warp).
-template <int kMode, bool kWide>
-__global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev w, int cur, int steps,
+// kWidth: 2, 4 or 8 (the BVH the traversal walks).
+template <int kMode, int kWidth>
+__global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, WfDev w, int cur, int steps,
                                                        uint32_t* err) {
   constexpr bool kAny = kMode != 0;
   if (!kAny && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -442,7 +492,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_trace(const WfScene* tab, WfDev
     }
     if (__all_sync(0xffffffffu, item < 0)) break;
     const bool done =
-        item >= 0 && (kWide ? trav_run4<kAny>(sd, T, sh, steps, err) : trav_run2<kAny>(sd, T, sh, steps, err));
+        item >= 0 && (kWidth == 8   ? trav_run8<kAny>(sd, T, sh, steps, err)
+                      : kWidth == 4 ? trav_run4<kAny>(sd, T, sh, steps, err)
+                                    : trav_run2<kAny>(sd, T, sh, steps, err));
     if (done) {
       const uint32_t i = (uint32_t)item;
       count_ray(sd, kAny ? 1 : 0, T.n_nodes, T.n_tests);
@@ -484,11 +536,13 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_shade_fwd(const WfScene* tab
   uint32_t* qin = queue(w, cur);
   uint32_t* qout = queue(w, cur ^ 1);
   uint32_t* nout = &w.cnt[cur ^ 1];
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const uint32_t slot = qin[q];
-    const float4 hh = w.hit[slot];
+  for (uint32_t q0 = blockIdx.x * blockDim.x; q0 < n; q0 += gridDim.x * blockDim.x) {
+    const uint32_t q = q0 + threadIdx.x;
+    const bool act = q < n;
+    const uint32_t slot = act ? qin[q] : 0u;
+    const float4 hh = act ? w.hit[slot] : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
     const int tri = __float_as_int(hh.x);
-    const float4 bt = w.beta[slot];
+    const float4 bt = act ? w.beta[slot] : make_float4(0.f, 0.f, 0.f, __uint_as_float(kDead));
     const uint32_t st = __float_as_uint(bt.w);
     const uint32_t k = state_k(st), b = state_scene(st);
     bool cont = false, shadow = false, query = false, record = false;
@@ -1033,9 +1087,8 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
   uint32_t* qout = queue(w, cur ^ 1);
   uint32_t* nout = &w.cnt[cur ^ 1];
   // warp-uniform trip count: every lane reaches the warp-collective scatters
-  const uint32_t lane = threadIdx.x & 31u;
-  for (uint32_t q0 = blockIdx.x * blockDim.x + threadIdx.x - lane; q0 < n; q0 += gridDim.x * blockDim.x) {
-    const uint32_t q = q0 + lane;
+  for (uint32_t q0 = blockIdx.x * blockDim.x; q0 < n; q0 += gridDim.x * blockDim.x) {
+    const uint32_t q = q0 + threadIdx.x;
     const bool act = q < n;
     const uint32_t slot = act ? qin[q] : 0u;
     const float4 bt = act ? w.beta[slot] : make_float4(0.f, 0.f, 0.f, __uint_as_float(kDead));
@@ -1320,10 +1373,27 @@ static uint32_t total_pixels(const std::vector<WfScene>& tab) {
   return tab.empty() ? 0u : tab.back().pix_begin + tab.back().n_pix;
 }
 
-static bool all_wide(const std::vector<WfScene>& tab) {
-  for (const WfScene& e : tab)
-    if (!e.s.wide || !e.s.nodes4) return false;
-  return true;
+// BVH width every scene of the table can be traversed with: 8 when all of
+// them select the 8-wide BVH, 4 when all have a wide one, else 2.
+static int table_width(const std::vector<WfScene>& tab) {
+  bool w8 = true, w4 = true;
+  for (const WfScene& e : tab) {
+    w8 = w8 && e.s.wide == 2 && e.s.nodes8;
+    w4 = w4 && e.s.wide >= 1 && e.s.nodes4;
+  }
+  return w8 ? 8 : (w4 ? 4 : 2);
+}
+
+// One launch of traversal mode kMode over the table's BVH width.
+template <int kMode>
+static void launch_trace(int width, int grid, const WfScene* tab_dev, const WfDev& w, int cur, int steps,
+                         uint32_t* err, cudaStream_t st) {
+  if (width == 8)
+    wf_trace<kMode, 8><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, err);
+  else if (width == 4)
+    wf_trace<kMode, 4><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, err);
+  else
+    wf_trace<kMode, 2><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, err);
 }
 
 // Chunks of at most cap / spp pixels; an adjoint chunk also ends before a
@@ -1371,7 +1441,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
   const WfDev w = wf_dev(wb);
   if (wb.cap < tp.spp || ns == 0) return cudaErrorInvalidValue;
   if (lp.cache_k != kNoCache && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
-  const bool wide = all_wide(tab);
+  const int width = table_width(tab);
   const int grid = wf_grid(L);
   const int grid_cam = one_wave(L, wf_camera, 0);
   const int grid_sh = disney ? one_wave(L, wf_shade_fwd<true>, 0) : one_wave(L, wf_shade_fwd<false>, 0);
@@ -1389,10 +1459,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
     for (uint32_t k = 0; k <= last_k; ++k) {
       {
         IPT_STAGE(8);
-        if (wide)
-          wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
-        else
-          wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+        launch_trace<0>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
       }
       {
         IPT_STAGE(10);
@@ -1403,10 +1470,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
       }
       if (k < last_k && k < tp.max_depth && tp.nee && !(record && k < lp.cache_k)) {
         IPT_STAGE(9);
-        if (wide)
-          wf_trace<1, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
-        else
-          wf_trace<1, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+        launch_trace<1>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
       }
       cur ^= 1;
     }
@@ -1466,7 +1530,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
   const WfDev w = wf_dev(wb);
   if (wb.cap < tp.spp || !wb.aT || ns == 0) return cudaErrorInvalidValue;
   if (query && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
-  const bool wide = all_wide(tab);
+  const int width = table_width(tab);
   const int grid = wf_grid(L);
   const int grid_cam = one_wave(L, wf_camera, 0);
   const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, max_seg);
@@ -1510,10 +1574,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
     for (uint32_t k = 0; k <= last_k; ++k) {
       {
         IPT_STAGE(8);
-        if (wide)
-          wf_trace<0, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
-        else
-          wf_trace<0, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+        launch_trace<0>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
       }
       {
         IPT_STAGE(11);
@@ -1523,10 +1584,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
         if (tp.nee) {
           {
             IPT_STAGE(9);
-            if (wide)
-              wf_trace<2, true><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
-            else
-              wf_trace<2, false><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, L.wf_steps, err);
+            launch_trace<2>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
           }
           IPT_STAGE(12);
           wf_adj_connect<kD><<<g_c, kWfThreads, sm, st>>>(tab_dev, lp, w);
@@ -1566,9 +1624,18 @@ cudaError_t wf_pick(const WfScene* tab_dev, const std::vector<WfScene>& tab, con
 }
 
 cudaError_t wf_init(Launcher* L) {
-  int b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wf_trace<0, true>, kWfThreads, 0);
-  if (e != cudaSuccess) return e;
+  // the fewest resident blocks of any traversal variant, so that every
+  // width's persistent grid fits in one wave
+  int b = 1 << 30;
+  const void* variants[] = {(const void*)wf_trace<0, 2>, (const void*)wf_trace<0, 4>, (const void*)wf_trace<0, 8>,
+                            (const void*)wf_trace<1, 2>, (const void*)wf_trace<1, 4>, (const void*)wf_trace<1, 8>,
+                            (const void*)wf_trace<2, 2>, (const void*)wf_trace<2, 4>, (const void*)wf_trace<2, 8>};
+  for (const void* k : variants) {
+    int bk = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bk, k, kWfThreads, 0);
+    if (e != cudaSuccess) return e;
+    b = std::min(b, bk);
+  }
   L->wf_blocks_per_sm = b < 1 ? 1 : b;
   if (L->wf_fixed_blocks > 0) L->wf_blocks_per_sm = L->wf_fixed_blocks;
   // gradient rows: the widest one-wave grid of an adjoint stage (accumulators

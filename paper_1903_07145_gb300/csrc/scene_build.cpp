@@ -181,6 +181,10 @@ struct Builder {
 //   child count << 24; w4..w7: child links (inner node index, or a leaf code
 //   as in the binary layout); w8: lo.x of children 0..3 (one byte each),
 //   w9: hi.x, w10: lo.y, w11: hi.y, w12: lo.z, w13: hi.z; w14, w15 unused.
+// 8-wide node (96 bytes, 24 words): w0..w2 origin, w3 exponents | mask of
+//   occupied slots << 24; per axis k, w4+4k..w5+4k the lower bytes and
+//   w6+4k..w7+4k the upper bytes of slots 0..3 and 4..7; w16..w23 the
+//   slots' links (the first 64 bytes are all a node test reads).
 // A child box is p + q * 2^(e - 127) per axis, rounded outward so that it
 // contains the child's (padded) box in float arithmetic.
 struct Quantizer {
@@ -481,6 +485,152 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
       std::memcpy(&out[16 * (size_t)it.slot], w, sizeof(w));
     }
     s.n_nodes4 = (uint32_t)(out.size() / 16);
+  }
+  // 8-wide quantized nodes: the same dynamic programming over at most eight
+  // child slots, then the children assigned to slots by octant
+  {
+    const size_t NB = B.nodes.size();
+    const double kCn = 1.0, kCt = 0.4;
+    std::vector<double> f(NB * 9, 0.0);
+    std::vector<int8_t> sp(NB * 9, 0);
+    std::vector<int8_t> gi(NB, 1);
+    for (size_t t = NB; t-- > 0;) {
+      const BNode& n = B.nodes[t];
+      const double A = n.box.area();
+      if (n.left < 0) {
+        for (int k = 1; k <= 8; ++k) f[t * 9 + k] = kCt * A * n.count;
+        continue;
+      }
+      const size_t L = (size_t)n.left, R = (size_t)n.right;
+      double best = 1e300;
+      for (int i = 1; i <= 7; ++i) {
+        const double c = f[L * 9 + i] + f[R * 9 + 8 - i];
+        if (c < best) {
+          best = c;
+          gi[t] = (int8_t)i;
+        }
+      }
+      f[t * 9 + 1] = kCn * A + best;  // n as one 8-wide node
+      for (int k = 2; k <= 8; ++k) {
+        double b2 = f[t * 9 + k - 1];
+        int8_t choice = 0;
+        for (int i = 1; i <= k - 1; ++i) {
+          const double c = f[L * 9 + i] + f[R * 9 + k - i];
+          if (c < b2) {
+            b2 = c;
+            choice = (int8_t)i;
+          }
+        }
+        f[t * 9 + k] = b2;
+        sp[t * 9 + k] = choice;
+      }
+    }
+    std::function<void(int, int, std::vector<int>&)> collect = [&](int n, int k, std::vector<int>& out) {
+      while (k > 1 && B.nodes[n].left >= 0 && sp[(size_t)n * 9 + k] == 0) --k;
+      if (k == 1 || B.nodes[n].left < 0) {
+        out.push_back(n);
+        return;
+      }
+      const int i = sp[(size_t)n * 9 + k];
+      collect(B.nodes[n].left, i, out);
+      collect(B.nodes[n].right, k - i, out);
+    };
+    std::vector<uint32_t>& out = s.nodes8;
+    out.clear();
+    struct Item {
+      int bnode;
+      uint32_t slot;
+    };
+    std::vector<Item> work;
+    auto alloc = [&]() {
+      out.resize(out.size() + 24, 0u);
+      return (uint32_t)(out.size() / 24 - 1);
+    };
+    work.push_back({0, alloc()});
+    while (!work.empty()) {
+      const Item it = work.back();
+      work.pop_back();
+      std::vector<int> ch;
+      const BNode& root = B.nodes[it.bnode];
+      if (root.left < 0) {
+        ch.push_back(it.bnode);
+      } else {
+        const int i = gi[(size_t)it.bnode];
+        collect(root.left, i, ch);
+        collect(root.right, 8 - i, ch);
+      }
+      Box u;
+      u.reset();
+      std::vector<Box> cb(ch.size());
+      for (size_t i = 0; i < ch.size(); ++i) {
+        cb[i] = B.nodes[ch[i]].box;
+        for (int k = 0; k < 3; ++k) {
+          cb[i].lo[k] -= pad;
+          cb[i].hi[k] += pad;
+        }
+        u.grow(cb[i]);
+      }
+      // Slot j takes the child whose centre lies most towards the octant
+      // that is positive on the axes of j's set bits and negative on the
+      // others: a ray with direction sign bits sgn (bit set = negative)
+      // then meets the children roughly front to back in the order of
+      // (slot ^ sgn).  Greedy assignment of the highest remaining
+      // (child, slot) score.
+      int slot_of[8];
+      {
+        double score[8][8];
+        for (size_t i = 0; i < ch.size(); ++i)
+          for (int j = 0; j < 8; ++j) {
+            double sc = 0.0;
+            for (int k = 0; k < 3; ++k) {
+              const double off = 0.5 * (cb[i].lo[k] + cb[i].hi[k]) - 0.5 * (u.lo[k] + u.hi[k]);
+              sc += ((j >> k) & 1) ? off : -off;
+            }
+            score[i][j] = sc;
+          }
+        bool child_done[8] = {false}, slot_used[8] = {false};
+        for (size_t round = 0; round < ch.size(); ++round) {
+          double best = -1e300;
+          int bi = -1, bj = -1;
+          for (size_t i = 0; i < ch.size(); ++i)
+            for (int j = 0; j < 8; ++j)
+              if (!child_done[i] && !slot_used[j] && score[i][j] > best) {
+                best = score[i][j];
+                bi = (int)i;
+                bj = j;
+              }
+          child_done[bi] = true;
+          slot_used[bj] = true;
+          slot_of[bi] = bj;
+        }
+      }
+      Quantizer qa[3];
+      for (int k = 0; k < 3; ++k) qa[k] = make_axis(u.lo[k], u.hi[k]);
+      uint32_t w[24] = {0};
+      for (int k = 0; k < 3; ++k) std::memcpy(&w[k], &qa[k].p, 4);
+      uint32_t valid = 0;
+      for (size_t i = 0; i < ch.size(); ++i) valid |= 1u << slot_of[i];
+      w[3] = (uint32_t)qa[0].e | ((uint32_t)qa[1].e << 8) | ((uint32_t)qa[2].e << 16) | (valid << 24);
+      for (size_t i = 0; i < ch.size(); ++i) {
+        const BNode& c = B.nodes[ch[i]];
+        const int j = slot_of[i];
+        int ref;
+        if (c.left < 0) {
+          ref = leaf_code(c);
+        } else {
+          const uint32_t slot = alloc();
+          ref = (int)slot;
+          work.push_back({ch[i], slot});
+        }
+        std::memcpy(&w[16 + j], &ref, 4);
+        for (int k = 0; k < 3; ++k) {
+          w[4 + 4 * k + j / 4] |= q_lo(qa[k], cb[i].lo[k]) << (8 * (j % 4));
+          w[6 + 4 * k + j / 4] |= q_hi(qa[k], cb[i].hi[k]) << (8 * (j % 4));
+        }
+      }
+      std::memcpy(&out[24 * (size_t)it.slot], w, sizeof(w));
+    }
+    s.n_nodes8 = (uint32_t)(out.size() / 24);
   }
   // triangles in leaf order
   s.tris.assign(12 * (size_t)n_tri, 0.0f);

@@ -42,7 +42,8 @@ def prepared(seed=5, slots=0, bvh_width=0, integrator="wavefront"):
 
 
 @pytest.mark.parametrize("slots,bvh_width,integrator", [(0, 4, "wavefront"), (4096, 4, "wavefront"),
-                                                        (2048, 2, "wavefront"), (0, 4, "megakernel")])
+                                                        (2048, 2, "wavefront"), (4096, 8, "wavefront"),
+                                                        (0, 4, "megakernel")])
 def test_batch_equals_single_scene_steps(built, slots, bvh_width, integrator):
     """On the megakernel the batch runs each pass as one launch over the
     whole table (and the members alone on the single-scene megakernel)."""

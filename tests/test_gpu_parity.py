@@ -82,7 +82,7 @@ def test_philox_bit_exact(built):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("bvh_width", [2, 4])
+@pytest.mark.parametrize("bvh_width", [2, 4, 8])
 @pytest.mark.parametrize("which", ["cornell", "room_small", "room_61k", "room_516k"])
 def test_ray_hits_match_oracle(built, which, bvh_width):
     if which == "cornell":
@@ -466,7 +466,8 @@ def test_loss_grad_shards_add_up(built, integrator):
         tr.loss_grad_shard(opts, 3, n - 1, 2, n)
 
 
-@pytest.mark.parametrize("spp,slots,bvh_width", [(32, 1 << 20, 4), (12, 4096, 4), (1, 1024, 4), (8, 4096, 2)])
+@pytest.mark.parametrize("spp,slots,bvh_width", [(32, 1 << 20, 4), (12, 4096, 4), (1, 1024, 4), (8, 4096, 2),
+                                                  (16, 4096, 8)])
 def test_wavefront_equals_megakernel(built, spp, slots, bvh_width):
     """Both integrators draw the same numbers at the same slots: images agree
     to float rounding, gradients to the order of the float sums."""
@@ -489,19 +490,20 @@ def test_wavefront_equals_megakernel(built, spp, slots, bvh_width):
 
 
 def test_bvh_widths_give_the_same_images(built):
-    """The binary and the 4-wide BVH find the same closest hits (up to exact
-    ties), so images agree to float rounding."""
+    """The binary, 4-wide and 8-wide BVHs find the same closest hits (up to
+    exact ties), so images agree to float rounding."""
     sc = scenes.room_60k()
     sc.cameras = sc.cameras[:2]
     p = perturbed(sc, emission=0.02)
     imgs = []
-    for width in (2, 4):
+    for width in (2, 4, 8):
         tr = Tracer(sc, seed=SEED)
         tr.configure("wavefront", bvh_width=width)
         tr.set_params(p)
         imgs.append(tr.render(TraceOptions(max_depth=5), set_id=0, spp=8).cpu().numpy())
         tr.close()
     assert rel(imgs[1], imgs[0]) <= 1e-4
+    assert rel(imgs[2], imgs[0]) <= 1e-4
 
 
 def test_kernels_run_from_an_sm103a_binary(built):
