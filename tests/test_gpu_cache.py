@@ -8,8 +8,10 @@ ReLU decisions on the same values; what remains is FP32 vs FP64
 accumulation and the BF16 rounding of the backward signals (relative 2^-9
 each, over 5 layers):
   * predictions: relative L2 <= 1e-2;
-  * input vector-Jacobian products and training gradients: relative L2
-    <= 3e-2 and cosine >= 0.999;
+  * input vector-Jacobian products and training gradients (every weight
+    layer on its own and the table): relative L2 <= 1e-2 and cosine >=
+    0.999 (measured: 0.4-0.6% for the VJP, under 0.2% per weight layer,
+    0.4% for the table);
   * cached images and gradients (same Philox streams, FP32 vs FP64 paths):
     relative L2 <= 1e-2 and gradient cosine >= 0.999;
   * training records: the same paths reach the cache vertex, and their
@@ -157,7 +159,7 @@ def test_input_vjp_matches_oracle(built, n):
     ref = np.einsum("nc,ncj->nj", u, J)
     got = dp.cpu().numpy().astype(np.float64)
     assert rel(rgb.cpu().numpy(), ref_y) <= 1e-2
-    assert rel(got, ref) <= 3e-2, rel(got, ref)
+    assert rel(got, ref) <= 1e-2, rel(got, ref)
     assert cosine(got, ref) >= 0.999
 
 
@@ -180,16 +182,16 @@ def test_training_gradients_match_oracle(built, n):
     assert abs(loss - ref_loss) <= 1e-2 * ref_loss
     got_w = gw.cpu().numpy().astype(np.float64)
     ref_w = np.concatenate([g.reshape(-1) for g in ref_gw])
-    assert rel(got_w, ref_w) <= 3e-2 and cosine(got_w, ref_w) >= 0.999, (rel(got_w, ref_w), cosine(got_w, ref_w))
+    assert rel(got_w, ref_w) <= 1e-2 and cosine(got_w, ref_w) >= 0.999, (rel(got_w, ref_w), cosine(got_w, ref_w))
     # every layer on its own (W1 80 x 64, W2..W4 64 x 64, W5 64 x 16)
     off = 0
     for g in ref_gw:
         a, b = got_w[off:off + g.size], g.reshape(-1)
-        assert rel(a, b) <= 3e-2 and cosine(a, b) >= 0.999, (off, rel(a, b), cosine(a, b))
+        assert rel(a, b) <= 1e-2 and cosine(a, b) >= 0.999, (off, rel(a, b), cosine(a, b))
         off += g.size
     got_t = gt.cpu().numpy().astype(np.float64)
     ref_t = ref_gt.reshape(-1)
-    assert rel(got_t, ref_t) <= 3e-2 and cosine(got_t, ref_t) >= 0.999, (rel(got_t, ref_t), cosine(got_t, ref_t))
+    assert rel(got_t, ref_t) <= 1e-2 and cosine(got_t, ref_t) >= 0.999, (rel(got_t, ref_t), cosine(got_t, ref_t))
     # entries no row touches stay exactly zero
     assert np.all(got_t[ref_t == 0] == 0)
 
