@@ -281,7 +281,8 @@ def run_ours(args, rank, world, local):
                                     wavefront_only=bool(args.cache))
         tr.set_params(scenes.initial_params(sc, w["init"]))
     else:
-        tr.configure(args.integrator, wavefront_slots=args.slots, bvh_width=args.bvh_width)
+        tr.configure(args.integrator, wavefront_slots=args.slots, trace_steps=args.trace_steps,
+                     bvh_width=args.bvh_width)
     chosen = tr.config()
     shard_iter = [0]
 
@@ -698,7 +699,7 @@ def run_disney(args):
     for timing in (False, True):
         tr = Tracer(sc, seed=1903, flags=L.IPT_FLAG_KERNEL_TIMING if timing else 0)
         if integ == "wavefront":  # the configuration the autotuner picks for this room
-            tr.configure("wavefront", wavefront_slots=1 << 25, trace_steps=8, bvh_width=4)
+            tr.configure("wavefront", wavefront_slots=1 << 25, trace_steps=16, bvh_width=4)
         else:
             tr.configure("megakernel")
         tr.disney_set_params(truth)
@@ -832,6 +833,8 @@ def main():
                     help="profiling only: BVH width with --integrator wavefront or megakernel")
     ap.add_argument("--slots", type=int, default=0,
                     help="profiling only: wavefront path slots per chunk with --integrator wavefront")
+    ap.add_argument("--trace-steps", type=int, default=0,
+                    help="profiling only: traversal refill point with --integrator wavefront")
     args = ap.parse_args()
     if args.workload in WORKLOADS:
         WORKLOAD.clear()

@@ -111,8 +111,10 @@ typedef struct {
  *     compacted ray queues).
  *   wavefront_slots: path slots per wavefront chunk (0 = 1 << 20); rounded
  *     down to whole pixels.
- *   trace_steps: node visits per refill round of the persistent traversal
- *     (0 = 16).
+ *   trace_steps: refill point of the persistent traversal kernels (0 = 16).
+ *     4- and 8-wide BVHs: a warp fetches new rays once this many of its 32
+ *     lanes are idle (values above 32 act as 32).  Binary BVH: node visits
+ *     per refill round.
  *   blocks_per_sm: persistent blocks per SM for the wavefront kernels (0 =
  *     as many as fit).
  *   bvh_width: BVH the traversal walks (every integrator, and

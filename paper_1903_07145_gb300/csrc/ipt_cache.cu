@@ -570,9 +570,9 @@ __device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr, uint32_t lbo, uint
 }
 
 // Instruction descriptor of a dense kind::f16 MMA: BF16 A and B, FP32 D,
-// both operands MN-major, shape M x N.
-__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+// shape M x N, both operands MN-major (mn = true) or both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n, bool mn = true) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (mn ? (1u << 15) | (1u << 16) : 0u) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(m >> 4) << 24);
 }
 
@@ -798,6 +798,202 @@ __global__ void __launch_bounds__(kThreads) cache_grad_k(CacheNet net, CacheRows
   }
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the fifth-generation tensor cores: 128-row tiles per block of
+// four warps, one row per thread.  Each warp encodes its 32 rows into the
+// block's input tile; per layer one thread issues the MMAs (A = the tile,
+// K-major: the rows' features in 128-byte chunks; B = the layer's weights in
+// the same blocked layout, K-major: each output's inputs in chunks) into a
+// 128 x 64 FP32 accumulator in TMEM; every thread then reads its row back
+// with tcgen05.ld, applies the ReLU and writes the next layer's BF16 tile
+// (over the layer's own input tile, whose MMAs have completed).  Two blocks
+// per SM: one block's gathers overlap the other's MMA round trips, and the
+// 74 KB of shared memory a block takes leave most of the SM's L1 to the
+// hash-table gathers (three blocks per SM, with 28 KB of L1 left, were 36%
+// slower).
+// ---------------------------------------------------------------------------
+constexpr int kQRows = 128;
+constexpr int kQLboX = 10 * 128, kQLboH = 8 * 128;  // bytes between 8-row groups (activation tiles, weights)
+constexpr int kQW1 = 0;                               // 64 outputs x 80 inputs
+constexpr int kQW2 = kQW1 + 8 * kQLboX;               // W2..W4: 64 x 64 each
+constexpr int kQW5 = kQW2 + 3 * 8 * kQLboH;           // 16 outputs x 64 inputs
+constexpr int kQX = kQW5 + 2 * kQLboH;
+constexpr int kQH = kQX + (kQRows / 8) * kQLboX;      // one 128 x 64 tile
+constexpr int kQMeta = kQH + (kQRows / 8) * kQLboH;
+constexpr int kQBar = kQMeta + kQRows * 16;
+constexpr int kSmemInferTc = kQBar + 16;
+constexpr uint32_t kQCols = 128;                      // TMEM columns of a block
+static_assert(kQX % 128 == 0 && kQH % 128 == 0 && kQMeta % 16 == 0 && kQBar % 16 == 0, "tile alignment");
+static_assert(2 * kSmemInferTc <= 227 * 1024, "two inference blocks per SM");
+static_assert(2 * kQCols <= 512, "two inference blocks' TMEM per SM");
+
+// The out-major BF16 weight image (mma.sync layout, padded rows) re-laid in
+// the blocked K-major layout: output n, input chunk c (8 inputs, 16 bytes)
+// at (n / 8) * lbo + c * 128 + (n % 8) * 16.
+__device__ __forceinline__ void load_weights_blocked(const CacheNet& net, unsigned char* sm, int* res) {
+  const uint4* img = net.wt;  // BF16 elements, 8 per uint4
+  constexpr int chunks1 = 64 * 10, chunks24 = 64 * 8, chunks5 = 16 * 8;
+  constexpr int total = chunks1 + 3 * chunks24 + chunks5;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int n, c, src, dst;
+    if (t < chunks1) {
+      n = t / 10;
+      c = t % 10;
+      src = (kWt1 + n * kXs + 8 * c) / 8;
+      dst = kQW1 + (n >> 3) * kQLboX + c * 128 + (n & 7) * 16;
+    } else if (t < chunks1 + 3 * chunks24) {
+      const int u = t - chunks1, L = u / chunks24, v = u % chunks24;
+      n = v / 8;
+      c = v % 8;
+      src = (kWt2 + L * 64 * kHs + n * kHs + 8 * c) / 8;
+      dst = kQW2 + L * 8 * kQLboH + (n >> 3) * kQLboH + c * 128 + (n & 7) * 16;
+    } else {
+      const int v = t - chunks1 - 3 * chunks24;
+      n = v / 8;
+      c = v % 8;
+      src = (kWt5 + n * kHs + 8 * c) / 8;
+      dst = kQW5 + (n >> 3) * kQLboH + c * 128 + (n & 7) * 16;
+    }
+    *reinterpret_cast<uint4*>(sm + dst) = __ldg(&img[src]);
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int l = 0; l < kCacheLevels; ++l) res[l] = net.res[l];
+  }
+}
+
+// Reads 16 FP32 accumulator columns of this thread's row (TMEM lane) into r.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) r[j] = __uint_as_float(u[j]);
+}
+
+// One layer's MMAs: D[128 x n_out] = A[128 x k_in] x W^T, both K-major
+// blocked (A rows grouped at a_lbo bytes, W outputs at w_lbo), K in steps of 16.
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a, uint32_t a_lbo, uint32_t w, uint32_t w_lbo,
+                                            int k_in, int n_out) {
+  const uint32_t idesc = umma_idesc(128, n_out, false);
+  for (int k = 0; k < k_in / 16; ++k)
+    umma_bf16(tmem, umma_sdesc(a + 256u * k, 128, a_lbo), umma_sdesc(w + 256u * k, 128, w_lbo), idesc, k > 0 ? 1u : 0u);
+}
+
+__global__ void __launch_bounds__(128, 2) cache_infer_tc_k(CacheNet net, CacheRows rows, const float4* mat_a,
+                                                           const float4* mat_b, const uint32_t* count_dev,
+                                                           uint32_t n_max, CacheOut o) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int res[kCacheLevels];
+  load_weights_blocked(net, sm, res);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kQBar + 8);
+  const uint32_t mbar = smem_addr(sm + kQBar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(kQCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 TMEM lanes
+  const uint32_t n = count_dev ? min(*count_dev, n_max) : n_max;
+  const uint32_t base = smem_addr(sm);
+  const BlockTile X{reinterpret_cast<uint32_t*>(sm + kQX), kQLboX / 4};
+  float4* meta = reinterpret_cast<float4*>(sm + kQMeta);
+  const int row = 32 * warp + lane;  // this thread's row of the tile
+  uint32_t phase = 0;
+  bool ok = true;
+  const uint32_t n_tiles = (n + kQRows - 1u) / kQRows;
+  for (uint32_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const uint32_t r0 = tile * kQRows;
+    encode_rows(net, res, rows, mat_a, mat_b, r0 + 32u * warp, n, X.rows_from(32 * warp), meta + 32 * warp, lane);
+    encode_rows(net, res, rows, mat_a, mat_b, r0 + 32u * warp + 16u, n, X.rows_from(32 * warp + 16),
+                meta + 32 * warp + 16, lane);
+    float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int l = 0; l < 5 && ok; ++l) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        const uint32_t a = base + (uint32_t)(l == 0 ? kQX : kQH);
+        const uint32_t a_lbo = l == 0 ? kQLboX : kQLboH;
+        const uint32_t w = base + (uint32_t)(l == 0 ? kQW1 : (l < 4 ? kQW2 + (l - 1) * 8 * kQLboH : kQW5));
+        const uint32_t w_lbo = l == 0 ? kQLboX : kQLboH;
+        issue_layer(tmem, a, a_lbo, w, w_lbo, l == 0 ? 80 : 64, l < 4 ? 64 : 16);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                     : "memory");
+      }
+      ok = __syncthreads_and(mbar_wait(mbar, phase, kWaitLimit)) != 0;
+      phase ^= 1u;
+      tc_fence_after();
+      if (!ok) break;
+      if (l < 4) {
+        // ReLU, BF16, this row of the next tile
+        const BlockTile H{reinterpret_cast<uint32_t*>(sm + kQH), kQLboH / 4};
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          float v[16];
+          tmem_ld16(tlane + (uint32_t)c0, v);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            uint4 pk;
+            pk.x = pack2(fmaxf(v[8 * q + 0], 0.f), fmaxf(v[8 * q + 1], 0.f));
+            pk.y = pack2(fmaxf(v[8 * q + 2], 0.f), fmaxf(v[8 * q + 3], 0.f));
+            pk.z = pack2(fmaxf(v[8 * q + 4], 0.f), fmaxf(v[8 * q + 5], 0.f));
+            pk.w = pack2(fmaxf(v[8 * q + 6], 0.f), fmaxf(v[8 * q + 7], 0.f));
+            *reinterpret_cast<uint4*>(&H(row, (c0 + 8 * q) / 2)) = pk;
+          }
+        }
+      } else {
+        float v[16];
+        tmem_ld16(tlane, v);
+        y[0] = v[0];
+        y[1] = v[1];
+        y[2] = v[2];
+      }
+    }
+    if (!ok) break;
+    const uint32_t r = r0 + (uint32_t)row;
+    if (r < n) {
+      if (o.c) o.c[r] = make_float4(y[0], y[1], y[2], 0.0f);
+      if (o.rad) {
+        const float4 b = rows.u[r];
+        float4* dst = &o.rad[__float_as_uint(rows.d[r].w)];
+        const float4 v = *dst;
+        *dst = make_float4(v.x + b.x * y[0], v.y + b.y * y[1], v.z + b.z * y[2], v.w);
+      }
+    }
+    // the next tile's encoding overwrites X (read by layer 1, done) and meta
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  // MMAs in flight after a failed wait must finish before the TMEM goes back
+  bool drained = ok;
+  if (!ok) {
+    drained = __syncthreads_and(mbar_wait(mbar, phase ^ 1u, kWaitLimit)) != 0;
+    if (threadIdx.x == 0 && o.err) atomicOr(o.err, kErrTimeout);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0 && drained)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kQCols) : "memory");
+}
+
 // Position of FP32 master weight i in the BF16 image (out-major rows).
 __device__ __forceinline__ int image_index(int i) {
   if (i < kW2) return kWt1 + (i % 64) * kXs + i / 64;
@@ -911,12 +1107,28 @@ static cudaError_t launch_infer(const CacheNet& net, const CacheRows& rows, cons
   return cudaGetLastError();
 }
 
+static cudaError_t launch_infer_tc(const CacheNet& net, const CacheRows& rows, const float4* mat_a,
+                                   const float4* mat_b, const uint32_t* count_dev, uint32_t n, const CacheOut& out,
+                                   int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(cache_infer_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemInferTc);
+  if (e != cudaSuccess) return e;
+  // the smallest shared-memory carveout that holds two blocks (with the 1 KB
+  // the system reserves per block): the rest of the 256 KB stays L1
+  const int carveout = (2 * (kSmemInferTc + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024);
+  e = cudaFuncSetAttribute(cache_infer_tc_k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+  if (e != cudaSuccess) return e;
+  const uint32_t tiles = (n + kQRows - 1u) / kQRows;
+  const int grid = (int)std::max<uint32_t>(1u, std::min<uint32_t>(tiles, (uint32_t)(2 * num_sms)));
+  cache_infer_tc_k<<<grid, 128, kSmemInferTc, st>>>(net, rows, mat_a, mat_b, count_dev, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t cache_infer(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,
                         const uint32_t* count_dev, uint32_t n, const CacheOut& out, bool vjp, int num_sms,
                         cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  return vjp ? launch_infer<true>(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st)
-             : launch_infer<false>(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st);
+  if (vjp) return launch_infer<true>(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st);
+  return launch_infer_tc(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st);
 }
 
 cudaError_t cache_grad(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,

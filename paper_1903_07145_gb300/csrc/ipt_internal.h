@@ -94,7 +94,7 @@ struct Launcher {
   int wf_blocks_per_sm = 0;  // traversal kernels
   int wf_fixed_blocks = 0;   // configured blocks per SM for every wavefront kernel (0: by occupancy)
   int wf_max_rows = 0;       // gradient rows any adjoint stage may use (blocks of its widest grid)
-  int wf_steps = 16;  // node visits per refill round of the persistent traversal
+  int wf_steps = 16;  // refill point of the persistent traversal (idle lanes; binary BVH: steps)
 };
 
 // Wavefront state (device), sized for `cap` path slots per chunk.

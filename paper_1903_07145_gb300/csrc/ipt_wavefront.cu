@@ -352,99 +352,138 @@ __device__ __forceinline__ bool tri_unit(const SceneDev& s, Trav& T) {
   return false;
 }
 
-// 4-wide quantized nodes: hit children nearest first; popped entries
-// farther than the current hit are skipped (closest hit).  Each step of a
-// lane is one unit of work, a node test or a single triangle test, so lanes
-// inside leaves of different sizes and lanes testing nodes stay in step (a
-// whole leaf per step made most steps of a warp run both a node test and a
-// loop of up to eight triangle tests).
+// Pops to the next stack entry still in range (closest hit: entry distance
+// not beyond the current hit) and makes it the lane's unit of work; true
+// when the stack is empty (the traversal is over).  4-wide nodes.
 template <bool kAny>
-__device__ __forceinline__ bool trav_run4(const SceneDev& s, Trav& T, uint2* sh, int steps, uint32_t* err) {
-  for (int it = 0; it < steps; ++it) {
-    if (T.tri < T.tri_end) {
-      if (tri_unit<kAny>(s, T)) return true;
-      if (T.tri < T.tri_end) continue;
-    } else if (T.node >= 0) {
-      ++T.n_nodes;
-      float tn[4];
-      int ref[4];
-      const uint32_t mask = node4_children(s, T.node, T.r, kAny ? T.tmax : T.bt, tn, ref);
-      const int k = __popc(mask);
-      if (k > 0) {
-        if (T.sp + k - 1 > kStackSize) {
+__device__ __forceinline__ bool advance4(Trav& T, uint2* sh) {
+  uint2 e;
+  for (;;) {
+    if (T.sp == 0) return true;
+    e = st_pop(sh, T);
+    if (kAny || __uint_as_float(e.y) <= T.bt * 1.0000005f) break;
+  }
+  trav_enter(T, (int)e.x);
+  return false;
+}
+
+// 8-wide nodes: enters the next hit slot of the current group, popping
+// groups (node, remaining slots) as they run out; true when none is left.
+__device__ __forceinline__ bool advance8(const SceneDev& s, Trav& T, uint2* sh) {
+  while (T.gmask == 0u) {
+    if (T.sp == 0) return true;
+    const uint2 e = st_pop(sh, T);
+    T.gnode = (int)e.x;
+    T.gmask = e.y;
+  }
+  const int k = __ffs(T.gmask) - 1;
+  T.gmask &= T.gmask - 1u;
+  trav_enter(T, node8_link(s, T.gnode, k ^ (int)T.sgn));
+  return false;
+}
+
+// One triangle of the lane's current leaf, then (leaf done) the next unit;
+// true when the traversal is over (a shadow ray blocked, or nothing left).
+template <bool kAny, int kWidth>
+__device__ __forceinline__ bool tri_step(const SceneDev& s, Trav& T, uint2* sh) {
+  if (tri_unit<kAny>(s, T)) return true;
+  if (T.tri < T.tri_end) return false;
+  return kWidth == 8 ? advance8(s, T, sh) : advance4<kAny>(T, sh);
+}
+
+// One 4-wide node test: hit children nearest first (for shadow rays too: an
+// occluder near the shading point is found after fewer visits, -5% shadow
+// traversal time on the 61k room against slot order), the nearest entered;
+// a missed node pops the next entry.
+template <bool kAny>
+__device__ __forceinline__ bool node_step4(const SceneDev& s, Trav& T, uint2* sh, uint32_t* err) {
+  if (T.node >= 0) {
+    ++T.n_nodes;
+    float tn[4];
+    int ref[4];
+    const uint32_t mask = node4_children(s, T.node, T.r, kAny ? T.tmax : T.bt, tn, ref);
+    const int k = __popc(mask);
+    if (k > 0) {
+      if (T.sp + k - 1 > kStackSize) {
+        atomicOr(err, kErrStack);
+        T.best = -1;
+        T.occluded = true;
+        return true;
+      }
+      sort4(tn, ref);
+#pragma unroll
+      for (int i = 3; i >= 1; --i)
+        if (i < k) st_push(sh, T, ref[i], tn[i]);
+      trav_enter(T, ref[0]);
+      return false;
+    }
+  }
+  return advance4<kAny>(T, sh);
+}
+
+// One 8-wide node test: a node with hits becomes the current group (the
+// group it replaces, if it still has slots, goes on the stack as (node,
+// remaining slots)); then the next hit slot is entered.  Entered leaves are
+// not re-tested against a closer hit (their triangle tests are).
+template <bool kAny>
+__device__ __forceinline__ bool node_step8(const SceneDev& s, Trav& T, uint2* sh, uint32_t* err) {
+  if (T.node >= 0) {
+    ++T.n_nodes;
+    const uint32_t m = node8_hits(s, T.node, T.r, kAny ? T.tmax : T.bt, T.sgn);
+    if (m) {
+      if (T.gmask) {
+        if (T.sp >= kStackSize) {
           atomicOr(err, kErrStack);
           T.best = -1;
           T.occluded = true;
           return true;
         }
-        // nearest first, for shadow rays too: an occluder near the shading
-        // point is found after fewer visits (-5% shadow traversal time on
-        // the 61k room against slot order)
-        sort4(tn, ref);
-#pragma unroll
-        for (int i = 3; i >= 1; --i)
-          if (i < k) st_push(sh, T, ref[i], tn[i]);
-        trav_enter(T, ref[0]);
-        continue;
+        st_push(sh, T, T.gnode, __uint_as_float(T.gmask));
       }
+      T.gnode = T.node;
+      T.gmask = m;
     }
-    uint2 e;
-    for (;;) {
-      if (T.sp == 0) return true;
-      e = st_pop(sh, T);
-      if (kAny || __uint_as_float(e.y) <= T.bt * 1.0000005f) break;
-    }
-    trav_enter(T, (int)e.x);
+    T.node = -1;
   }
-  return false;
+  return advance8(s, T, sh);
 }
 
-// 8-wide quantized nodes: each step tests one node or one triangle, then
-// enters the next hit slot (visiting order by the ray's octant; see
-// node8_hits).  A tested node with hits becomes the current group; the
-// group it replaces, if it still has slots, goes on the stack as (node,
-// remaining slots).  Entered leaves are not re-tested against a closer hit
-// (their triangle tests are).
-template <bool kAny>
-__device__ __forceinline__ bool trav_run8(const SceneDev& s, Trav& T, uint2* sh, int steps, uint32_t* err) {
-  for (int it = 0; it < steps; ++it) {
-    if (T.tri < T.tri_end) {
-      if (tri_unit<kAny>(s, T)) return true;
-      if (T.tri < T.tri_end) continue;
-    } else if (T.node >= 0) {
-      ++T.n_nodes;
-      const uint32_t m = node8_hits(s, T.node, T.r, kAny ? T.tmax : T.bt, T.sgn);
-      if (m) {
-        if (T.gmask) {
-          if (T.sp >= kStackSize) {
-            atomicOr(err, kErrStack);
-            T.best = -1;
-            T.occluded = true;
-            return true;
-          }
-          st_push(sh, T, T.gnode, __uint_as_float(T.gmask));
-        }
-        T.gnode = T.node;
-        T.gmask = m;
-      }
-      T.node = -1;
+// Stores a finished ray's result: the hit record (closest), the unoccluded
+// light contribution (forward shadow rays) or the visibility flag (adjoint
+// shadow rays).
+template <int kMode>
+__device__ __forceinline__ void trace_finish(const WfDev& w, int cur, uint32_t i, const Trav& T,
+                                             const SceneDev& sd) {
+  count_ray(sd, kMode != 0 ? 1 : 0, T.n_nodes, T.n_tests);
+  if (kMode == 0) {
+    const uint32_t slot = queue(w, cur)[i];
+    w.hit[slot] = make_float4(__int_as_float(T.best), T.bt, T.bu, T.bv);
+  } else if (kMode == 1) {
+    if (!T.occluded) {
+      const uint32_t slot = w.sh_meta[i].x;
+      const float4 c = w.sh_c[i];
+      float4 r = w.rad[slot];
+      r.x += c.x;
+      r.y += c.y;
+      r.z += c.z;
+      w.rad[slot] = r;
     }
-    while (T.gmask == 0u) {
-      if (T.sp == 0) return true;
-      const uint2 e = st_pop(sh, T);
-      T.gnode = (int)e.x;
-      T.gmask = e.y;
-    }
-    const int k = __ffs(T.gmask) - 1;
-    T.gmask &= T.gmask - 1u;
-    trav_enter(T, node8_link(s, T.gnode, k ^ (int)T.sgn));
+  } else {
+    w.sh_vis[i] = T.occluded ? 0u : 1u;
   }
-  return false;
 }
 
-// Lanes run rounds of `steps` node visits; between rounds the warp fetches
-// new rays for the lanes whose ray has finished (one atomic per warp).
-// kWidth: 2, 4 or 8 (the BVH the traversal walks).
+// Persistent traversal: each warp fetches rays for its idle lanes with one
+// atomic, then steps its lanes' traversals.
+//  * 4- and 8-wide BVHs: every step is one unit of work per lane, a node
+//    test or a single triangle test, and the warp runs one kind per step:
+//    triangle tests when at least as many lanes wait at a triangle as at a
+//    node, node tests otherwise (the other lanes sit the step out).  Letting
+//    both kinds run in one step serialises the two code paths with most
+//    lanes masked off in each.  The warp refetches once `steps` of its lanes
+//    are idle (or all are).
+//  * Binary BVH: rounds of `steps` node visits, whole leaves at a time, and a
+//    refetch after each round.
 template <int kMode, int kWidth>
 __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, WfDev w, int cur, int steps,
                                                        uint32_t* err) {
@@ -458,6 +497,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
   uint32_t* fetch = kAny ? &w.cnt[4] : &w.cnt[3];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  const int refill = min(max(steps, 1), 32);
   __shared__ uint2 s_stack[kShortStack * kWfThreads];
   uint2* sh = s_stack + threadIdx.x;
   Trav T;
@@ -491,30 +531,30 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
       }
     }
     if (__all_sync(0xffffffffu, item < 0)) break;
-    const bool done =
-        item >= 0 && (kWidth == 8   ? trav_run8<kAny>(sd, T, sh, steps, err)
-                      : kWidth == 4 ? trav_run4<kAny>(sd, T, sh, steps, err)
-                                    : trav_run2<kAny>(sd, T, sh, steps, err));
-    if (done) {
-      const uint32_t i = (uint32_t)item;
-      count_ray(sd, kAny ? 1 : 0, T.n_nodes, T.n_tests);
-      if (kMode == 0) {
-        const uint32_t slot = queue(w, cur)[i];
-        w.hit[slot] = make_float4(__int_as_float(T.best), T.bt, T.bu, T.bv);
-      } else if (kMode == 1) {
-        if (!T.occluded) {
-          const uint32_t slot = w.sh_meta[i].x;
-          const float4 c = w.sh_c[i];
-          float4 r = w.rad[slot];
-          r.x += c.x;
-          r.y += c.y;
-          r.z += c.z;
-          w.rad[slot] = r;
-        }
-      } else {
-        w.sh_vis[i] = T.occluded ? 0u : 1u;
+    if (kWidth == 2) {
+      if (item >= 0 && trav_run2<kAny>(sd, T, sh, steps, err)) {
+        trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
+        item = -1;
       }
-      item = -1;
+      continue;
+    }
+    for (;;) {
+      const bool live = item >= 0;
+      const bool at_tri = live && T.tri < T.tri_end;
+      const unsigned ml = __ballot_sync(0xffffffffu, live);
+      const unsigned mt = __ballot_sync(0xffffffffu, at_tri);
+      const unsigned mi = __ballot_sync(0xffffffffu, !live && !exhausted);
+      if (ml == 0u || __popc(mi) >= refill) break;
+      const bool tri_phase = __popc(mt) >= __popc(ml & ~mt);
+      if (live && at_tri == tri_phase) {
+        const bool done = at_tri        ? tri_step<kAny, kWidth>(sd, T, sh)
+                          : kWidth == 8 ? node_step8<kAny>(sd, T, sh, err)
+                                        : node_step4<kAny>(sd, T, sh, err);
+        if (done) {
+          trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
+          item = -1;
+        }
+      }
     }
   }
 }

@@ -506,6 +506,31 @@ def test_bvh_widths_give_the_same_images(built):
     assert rel(imgs[2], imgs[0]) <= 1e-4
 
 
+@pytest.mark.parametrize("bvh_width", [2, 4, 8])
+def test_refill_points_give_the_same_results(built, bvh_width):
+    """The traversal's refill point (trace_steps) only changes which lanes
+    run which ray when: every ray's closest hit and occlusion stay the same,
+    so images agree to float rounding and gradients to the order of the
+    float sums, with a refill after every lane (1), at 8 and 16 idle lanes
+    (16: the default), only when the whole warp is idle (32) and beyond it
+    (100)."""
+    sc = scenes.indoor_room(17, n_cuboids=10, cuboid_sub=3, room_sub=4, n_lights=3, n_views=2,
+                            width=40, height=30)
+    p = perturbed(sc, emission=0.05)
+    opts = TraceOptions(spp_r=8, spp_d=8, max_depth=5)
+    w = torch.from_numpy(np.random.default_rng(2).normal(size=(2 * 40 * 30, 3)).astype(np.float32)).cuda()
+    out = []
+    for steps in (1, 8, 16, 32, 100):
+        tr = Tracer(sc, seed=SEED)
+        tr.configure("wavefront", wavefront_slots=4096, trace_steps=steps, bvh_width=bvh_width)
+        tr.set_params(p)
+        out.append((tr.render(opts, set_id=0, spp=8).cpu().numpy(), tr.backward(w, opts, set_id=1).cpu().numpy()))
+        tr.close()
+    for img, g in out[1:]:
+        assert rel(img, out[0][0]) <= 1e-6
+        assert rel(g, out[0][1]) <= 1e-5
+
+
 def test_kernels_run_from_an_sm103a_binary(built):
     """The device loads the library's kernels from the sm_103a cubin, not a
     JIT-compiled PTX fallback."""
