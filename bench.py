@@ -144,7 +144,7 @@ def measured_peaks():
 # section of the wavefront source.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wf_closest_room61k_traffic.txt")
 CSRC = os.path.join(ROOT, "paper_1903_07145_gb300", "csrc")
-TRAVERSAL_SECTION = ("// Persistent traversal with per-lane refill", "// Forward shading of queue")
+TRAVERSAL_SECTION = ("// Persistent traversal with warp refills", "// Forward shading of queue")
 
 
 def kernel_sources_sha256():
@@ -154,7 +154,9 @@ def kernel_sources_sha256():
             h.update(fh.read())
     with open(os.path.join(CSRC, "ipt_wavefront.cu")) as fh:
         text = fh.read()
-    a, b = text.index(TRAVERSAL_SECTION[0]), text.index(TRAVERSAL_SECTION[1])
+    a, b = text.find(TRAVERSAL_SECTION[0]), text.find(TRAVERSAL_SECTION[1])
+    if a < 0 or b < a:
+        return None  # section markers moved: no record can match
     h.update(text[a:b].encode())
     return h.hexdigest()
 
@@ -178,7 +180,7 @@ def recorded_traffic(kernel, cfg, slots_per_launch):
             kv[k.strip()] = v.strip()
     want = {"kernel": kernel, "bvh_width": str(cfg.get("bvh_width")),
             "kernel_sources_sha256": kernel_sources_sha256()}
-    if any(kv.get(k) != v for k, v in want.items()):
+    if want["kernel_sources_sha256"] is None or any(kv.get(k) != v for k, v in want.items()):
         return None
     try:
         return float(kv["dram_bytes_per_slot"]) * slots_per_launch

@@ -10,20 +10,24 @@
 // 64 -> 64 -> 16, ReLU on hidden layers, no biases; the first 3 outputs are
 // the predicted reflected radiance.
 //
-// Each warp runs 16 rows through the network with mma.sync m16n8k16 (BF16
-// operands, FP32 accumulation).  The encoded input tile is staged in shared
-// memory; a layer's FP32 accumulator fragments are exactly the next layer's
-// A fragments once packed to BF16, so hidden activations stay in registers,
-// and the inference VJP needs only their ReLU masks (one register per layer).
-// Inference blocks of 16 warps share one weight image (two blocks per SM).
-// The backward pass loads the transposed weights with ldmatrix.trans from the
-// same out-major image.  Training keeps the block's 64 rows of inputs,
-// activations and pre-activation gradients in shared memory in the
-// core-matrix-blocked layout that the fifth-generation tensor cores read;
-// the weight gradients dW = A^T dZ over those rows (K = rows) are one
-// tcgen05.mma batch per tile, issued by one thread and accumulated in tensor
-// memory (TMEM) across every tile the block processes, then read back with
-// tcgen05.ld and added to the global gradient once per launch.
+// Queries run on the fifth-generation tensor cores: a block of 128 threads
+// encodes 128 rows (one per thread) into a BF16 tile in shared memory, one
+// thread issues each layer as tcgen05.mma (M = 128 rows) into FP32
+// accumulators in tensor memory (TMEM), and every thread reads its row back
+// with tcgen05.ld, applies the ReLU and writes the next layer's tile.  The
+// input VJP and training run each warp's 16 rows forward and backward with
+// mma.sync m16n8k16: a layer's FP32 accumulator fragments are the next
+// layer's A fragments once packed to BF16, so the VJP needs only the hidden
+// layers' ReLU masks (one register per layer), and the backward pass loads
+// the transposed weights with ldmatrix.trans from the out-major image.  (A
+// tcgen05 VJP, ten dependent MMA round trips per 128-row tile, measured 28%
+// slower than these independent per-warp chains.)  Training keeps the
+// block's 64 rows of inputs, activations and pre-activation gradients in
+// shared memory in the core-matrix-blocked layout that the tensor cores
+// read: the weight gradients dW = A^T dZ over those rows (K = rows) are one
+// tcgen05.mma batch per tile, accumulated in TMEM across every tile the
+// block processes, then read back and added to the global gradient once per
+// launch.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,9 +51,9 @@ constexpr int kWt1 = 0, kWt2 = 64 * kXs, kWt3 = kWt2 + 64 * kHs, kWt4 = kWt3 + 6
 // FP32 master weight offsets: W1 80 x 64, W2..W4 64 x 64, W5 64 x 16, in-major.
 constexpr int kW1 = 0, kW2 = 80 * 64, kW3 = kW2 + 4096, kW4 = kW3 + 4096, kW5 = kW4 + 4096;
 
-// Shared-memory layout (bytes, 16-byte aligned regions).  Inference: the
+// Shared-memory layout (bytes, 16-byte aligned regions).  Input VJP: the
 // BF16 weight image, then each warp's input tile (row stride kXs) and row
-// metadata (infer_smem).  Training: the weight image, then the block's
+// metadata (kSmemVjp).  Training: the weight image, then the block's
 // 64-row tiles in the core-matrix-blocked layout of BlockTile -- X (80
 // features), H1..H4 and dZ1..dZ4 (64 each), dY (16) -- the rows' metadata,
 // and the weight-gradient MMAs' mbarrier and TMEM address.
@@ -465,20 +469,18 @@ __device__ __forceinline__ void load_weights(const CacheNet& net, unsigned char*
   }
 }
 
-// Inference (and input VJP) over warp tiles of 16 rows; W warps share one
-// shared-memory weight image.  The VJP keeps the hidden layers' ReLU masks in
-// registers, so a block holds only the weights and its warps' input tiles.
-constexpr int kInferWarps = 16;
-template <int W>
-constexpr int infer_smem() {
-  return kSmX + W * 16 * kXs * 2 + W * 16 * 16;
-}
-static_assert(kSmX % 16 == 0 && (kSmX + kInferWarps * 16 * kXs * 2) % 16 == 0, "infer tiles must be aligned");
+// Input VJP (with the query's outputs) over warp tiles of 16 rows; the warps
+// share one shared-memory weight image.  The hidden layers' ReLU masks stay
+// in registers, so a block holds only the weights and its warps' input
+// tiles.  The VJP needs more than 64 registers: 12 warps per block keep two
+// blocks per SM without spills.
+constexpr int kVjpWarps = 12;
+constexpr int kSmemVjp = kSmX + kVjpWarps * 16 * kXs * 2 + kVjpWarps * 16 * 16;
+static_assert(kSmX % 16 == 0 && (kSmX + kVjpWarps * 16 * kXs * 2) % 16 == 0, "VJP tiles must be aligned");
 
-template <bool kVjp, int W>
-__global__ void __launch_bounds__(W * 32, 2) cache_infer_k(CacheNet net, CacheRows rows, const float4* mat_a,
-                                                           const float4* mat_b, const uint32_t* count_dev,
-                                                           uint32_t n_max, CacheOut o) {
+__global__ void __launch_bounds__(kVjpWarps * 32, 2) cache_vjp_k(CacheNet net, CacheRows rows, const float4* mat_a,
+                                                         const float4* mat_b, const uint32_t* count_dev,
+                                                         uint32_t n_max, CacheOut o) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int res[kCacheLevels];
   load_weights(net, sm, res);
@@ -489,9 +491,10 @@ __global__ void __launch_bounds__(W * 32, 2) cache_infer_k(CacheNet net, CacheRo
   const uint32_t* Wt = reinterpret_cast<const uint32_t*>(sm + kSmWt);
   const __nv_bfloat16* Wtb = reinterpret_cast<const __nv_bfloat16*>(sm + kSmWt);
   const RowTile X{reinterpret_cast<uint32_t*>(sm + kSmX) + warp * 16 * kXw, kXw};
-  float4* meta = reinterpret_cast<float4*>(sm + kSmX + W * 16 * kXs * 2) + warp * 16;
+  float4* meta = reinterpret_cast<float4*>(sm + kSmX + kVjpWarps * 16 * kXs * 2) + warp * 16;
   const uint32_t n_tiles = (n + 15u) / 16u;
-  for (uint32_t tile = blockIdx.x * (uint32_t)W + (uint32_t)warp; tile < n_tiles; tile += gridDim.x * (uint32_t)W) {
+  for (uint32_t tile = blockIdx.x * (uint32_t)kVjpWarps + (uint32_t)warp; tile < n_tiles;
+       tile += gridDim.x * (uint32_t)kVjpWarps) {
     const uint32_t r0 = tile * 16u;
     __syncwarp();
     encode_rows(net, res, rows, mat_a, mat_b, r0, n, X, meta, lane);
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(W * 32, 2) cache_infer_k(CacheNet net, CacheRo
         }
       }
     }
-    if (kVjp) {
+    {
       // upstream u on outputs 0..2: lane t = 0 takes (u.x, u.y), t = 1 (u.z, 0)
       float dy[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
       if (t < 2) {
@@ -1085,25 +1088,21 @@ void cache_grid(int res[kCacheLevels], uint32_t* dense) {
   }
 }
 
-template <bool kVjp>
-static cudaError_t launch_infer(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,
-                                const uint32_t* count_dev, uint32_t n, const CacheOut& out, int num_sms,
-                                cudaStream_t st) {
-  // the VJP needs more than 64 registers: 12 warps per block keep two blocks
-  // per SM without spills
-  constexpr int W = kVjp ? 12 : kInferWarps, smem = infer_smem<W>();
-  cudaError_t e = cudaFuncSetAttribute(cache_infer_k<kVjp, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+static cudaError_t launch_vjp(const CacheNet& net, const CacheRows& rows, const float4* mat_a, const float4* mat_b,
+                              const uint32_t* count_dev, uint32_t n, const CacheOut& out, int num_sms,
+                              cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(cache_vjp_k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemVjp);
   if (e != cudaSuccess) return e;
   static int per_sm = 0;  // resident blocks per SM at this shared-memory size (the same on every GB300)
   if (per_sm == 0) {
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cache_infer_k<kVjp, W>, W * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cache_vjp_k, kVjpWarps * 32, kSmemVjp);
     if (e != cudaSuccess) return e;
     per_sm = b < 1 ? 1 : b;
   }
-  const uint32_t tiles = (n + 16u * W - 1u) / (16u * W);
+  const uint32_t tiles = (n + 16u * kVjpWarps - 1u) / (16u * kVjpWarps);
   const int grid = (int)std::max<uint32_t>(1u, std::min<uint32_t>(tiles, (uint32_t)(num_sms * per_sm)));
-  cache_infer_k<kVjp, W><<<grid, W * 32, smem, st>>>(net, rows, mat_a, mat_b, count_dev, n, out);
+  cache_vjp_k<<<grid, kVjpWarps * 32, kSmemVjp, st>>>(net, rows, mat_a, mat_b, count_dev, n, out);
   return cudaGetLastError();
 }
 
@@ -1127,7 +1126,7 @@ cudaError_t cache_infer(const CacheNet& net, const CacheRows& rows, const float4
                         const uint32_t* count_dev, uint32_t n, const CacheOut& out, bool vjp, int num_sms,
                         cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  if (vjp) return launch_infer<true>(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st);
+  if (vjp) return launch_vjp(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st);
   return launch_infer_tc(net, rows, mat_a, mat_b, count_dev, n, out, num_sms, st);
 }
 

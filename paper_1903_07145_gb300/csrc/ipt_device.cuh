@@ -285,7 +285,6 @@ __device__ __forceinline__ uint32_t node4_children(const SceneDev& s, int node, 
   const float sx = __uint_as_float(((a.w & 0xffu) + 15u) << 23);
   const float sy = __uint_as_float((((a.w >> 8) & 0xffu) + 15u) << 23);
   const float sz = __uint_as_float((((a.w >> 16) & 0xffu) + 15u) << 23);
-  const int n = (int)(a.w >> 24);
   const float Ax = sx * r.inv.x, Bx = fmaf(__uint_as_float(a.x) - r.o.x, r.inv.x, -Ax);
   const float Ay = sy * r.inv.y, By = fmaf(__uint_as_float(a.y) - r.o.y, r.inv.y, -Ay);
   const float Az = sz * r.inv.z, Bz = fmaf(__uint_as_float(a.z) - r.o.z, r.inv.z, -Az);
@@ -308,7 +307,7 @@ __device__ __forceinline__ uint32_t node4_children(const SceneDev& s, int node, 
     const float tnz = fmaf(q_unit(nwz, i), Az, Bnz), tfz = fmaf(q_unit(fwz, i), Az, Bfz);
     const float tnear = max3f(tnx, tny, fmaxf(tnz, 0.0f));
     const float tfar = min3f(tfx, tfy, fminf(tfz, tmax)) * 1.0000005f;
-    const bool hit = i < n && tnear <= tfar;
+    const bool hit = tnear <= tfar;  // empty slots hold inverted boxes
     tn[i] = hit ? tnear : __int_as_float(0x7f800000);
     mask |= hit ? (1u << i) : 0u;
   }

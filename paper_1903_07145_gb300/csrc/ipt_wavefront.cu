@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfPa
 }
 
 // ---------------------------------------------------------------------------
-// Persistent traversal with per-lane refill.  kMode 0: closest hit of queue
+// Persistent traversal with warp refills.  kMode 0: closest hit of queue
 // `cur` into w.hit; 1: shadow rays, adding the forward contribution of the
 // unoccluded ones; 2: shadow rays, visibility flag only (adjoint).
 // ---------------------------------------------------------------------------
@@ -486,7 +486,7 @@ __device__ __forceinline__ void trace_finish(const WfDev& w, int cur, uint32_t i
 //    refetch after each round.
 template <int kMode, int kWidth>
 __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, WfDev w, int cur, int steps,
-                                                       uint32_t* err) {
+                                                       int one_scene, uint32_t* err) {
   constexpr bool kAny = kMode != 0;
   if (!kAny && blockIdx.x == 0 && threadIdx.x == 0) {
     w.cnt[cur ? 0 : 1] = 0;  // next queue, filled by the shading stage
@@ -503,56 +503,53 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
   Trav T;
   SceneDev sd = tab[0].s;
   int64_t item = -1;
-  bool exhausted = false;
+  bool drained = false;  // warp-uniform: the queue has no rays left
   for (;;) {
-    const bool need = item < 0 && !exhausted;
+    const bool need = item < 0 && !drained;
     const unsigned m = __ballot_sync(0xffffffffu, need);
     if (m) {
       const int leader = __ffs(m) - 1;
       uint32_t base = 0;
       if ((int)lane == leader) base = atomicAdd(fetch, (uint32_t)__popc(m));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (need) {
-        const uint32_t i = base + (uint32_t)__popc(m & lt_mask);
-        if (i < n) {
-          item = i;
-          const uint32_t slot = kAny ? w.sh_meta[i].x : queue(w, cur)[i];
-          sd = tab[state_scene(__float_as_uint(w.beta[slot].w))].s;
-          if (kAny) {
-            const float4 o = w.sh_o[i], d = w.sh_d[i];
-            trav_init(T, xyz(o), xyz(d), d.w, __float_as_int(o.w), (int)w.sh_meta[i].y);
-          } else {
-            const float4 o = w.ray_o[slot], d = w.ray_d[slot];
-            trav_init(T, xyz(o), xyz(d), __int_as_float(0x7f800000), __float_as_int(o.w), -1);
-          }
+      drained = base + (uint32_t)__popc(m) >= n;
+      const uint32_t i = base + (uint32_t)__popc(m & lt_mask);
+      if (need && i < n) {
+        item = i;
+        // a launch over one scene skips the lookup of the ray's scene
+        const uint32_t slot = kAny ? w.sh_meta[i].x : queue(w, cur)[i];
+        if (!one_scene) sd = tab[state_scene(__float_as_uint(w.beta[slot].w))].s;
+        if (kAny) {
+          const float4 o = w.sh_o[i], d = w.sh_d[i];
+          trav_init(T, xyz(o), xyz(d), d.w, __float_as_int(o.w), (int)w.sh_meta[i].y);
         } else {
-          exhausted = true;
+          const float4 o = w.ray_o[slot], d = w.ray_d[slot];
+          trav_init(T, xyz(o), xyz(d), __int_as_float(0x7f800000), __float_as_int(o.w), -1);
         }
       }
     }
     if (__all_sync(0xffffffffu, item < 0)) break;
-    if (kWidth == 2) {
+    if constexpr (kWidth == 2) {
       if (item >= 0 && trav_run2<kAny>(sd, T, sh, steps, err)) {
         trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
         item = -1;
       }
-      continue;
-    }
-    for (;;) {
-      const bool live = item >= 0;
-      const bool at_tri = live && T.tri < T.tri_end;
-      const unsigned ml = __ballot_sync(0xffffffffu, live);
-      const unsigned mt = __ballot_sync(0xffffffffu, at_tri);
-      const unsigned mi = __ballot_sync(0xffffffffu, !live && !exhausted);
-      if (ml == 0u || __popc(mi) >= refill) break;
-      const bool tri_phase = __popc(mt) >= __popc(ml & ~mt);
-      if (live && at_tri == tri_phase) {
-        const bool done = at_tri        ? tri_step<kAny, kWidth>(sd, T, sh)
-                          : kWidth == 8 ? node_step8<kAny>(sd, T, sh, err)
-                                        : node_step4<kAny>(sd, T, sh, err);
-        if (done) {
-          trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
-          item = -1;
+    } else {
+      for (;;) {
+        const bool live = item >= 0;
+        const bool at_tri = live && T.tri < T.tri_end;
+        const unsigned ml = __ballot_sync(0xffffffffu, live);
+        const unsigned mt = __ballot_sync(0xffffffffu, at_tri);
+        if (ml == 0u || (!drained && 32 - __popc(ml) >= refill)) break;
+        const bool tri_phase = __popc(mt) >= __popc(ml & ~mt);
+        if (live && at_tri == tri_phase) {
+          const bool done = at_tri        ? tri_step<kAny, kWidth>(sd, T, sh)
+                            : kWidth == 8 ? node_step8<kAny>(sd, T, sh, err)
+                                          : node_step4<kAny>(sd, T, sh, err);
+          if (done) {
+            trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
+            item = -1;
+          }
         }
       }
     }
@@ -838,8 +835,8 @@ __device__ __forceinline__ int acc_ix16(const WfScene& e, const WfParams& lp, in
 // Jacobian there with g * U_l * cos/pdf.
 template <bool kD>
 __device__ __forceinline__ void finish_path(const WfDev& w, const WfScene* e, const WfParams& lp, uint32_t slot,
-                                            float3 gp, float* sacc, bool act) {
-  const uint32_t nv = act ? w.nv[slot] : 0u;
+                                            uint32_t nv_slot, float3 gp, float* sacc, bool act) {
+  const uint32_t nv = act ? nv_slot : 0u;
   const uint32_t nmax = __reduce_max_sync(0xffffffffu, nv);
   for (uint32_t l = 0; l < nmax; ++l) {
     if constexpr (kD) {
@@ -892,16 +889,52 @@ __device__ __forceinline__ void finish_path(const WfDev& w, const WfScene* e, co
   }
 }
 
-__device__ __forceinline__ void add_to_carry(const WfDev& w, uint32_t slot, float3 C) {
-  const uint32_t nv = w.nv[slot];
-  for (uint32_t l = 0; l < nv; ++l) {
-    const size_t ix = (size_t)l * w.cap + slot;
-    const float4 T = w.aT[ix];
-    float4 U = w.aU[ix];
-    U.x += T.x * C.x;
-    U.y += T.y * C.y;
-    U.z += T.z * C.z;
-    w.aU[ix] = U;
+// U_l += T_l * C for the path's nv earlier vertices.  The carry is read in
+// groups of kG vertices whose loads are all issued before the first use
+// (the stages are latency-bound; nv <= kMaxAdjointDepth).  Stages short of
+// registers take smaller groups.
+template <uint32_t kG>
+__device__ __forceinline__ void add_to_carry(const WfDev& w, uint32_t slot, uint32_t nv, float3 C) {
+#pragma unroll
+  for (uint32_t l0 = 0; l0 < (uint32_t)kMaxAdjointDepth; l0 += kG) {
+    if (l0 >= nv) break;
+    float4 T[kG], U[kG];
+#pragma unroll
+    for (uint32_t j = 0; j < kG; ++j)
+      if (l0 + j < nv) {
+        const size_t ix = (size_t)(l0 + j) * w.cap + slot;
+        T[j] = w.aT[ix];
+        U[j] = w.aU[ix];
+      }
+#pragma unroll
+    for (uint32_t j = 0; j < kG; ++j)
+      if (l0 + j < nv) {
+        U[j].x += T[j].x * C.x;
+        U[j].y += T[j].y * C.y;
+        U[j].z += T[j].z * C.z;
+        w.aU[(size_t)(l0 + j) * w.cap + slot] = U[j];
+      }
+  }
+}
+
+// T_l *= wgt for the path's nv earlier vertices (the new vertex's BSDF
+// weight joins their throughputs), loads grouped as in add_to_carry.
+__device__ __forceinline__ void scale_carry(const WfDev& w, uint32_t slot, uint32_t nv, float3 wgt) {
+#pragma unroll
+  for (uint32_t l0 = 0; l0 < (uint32_t)kMaxAdjointDepth; l0 += 4) {
+    if (l0 >= nv) break;
+    float4 T[4];
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j)
+      if (l0 + j < nv) T[j] = w.aT[(size_t)(l0 + j) * w.cap + slot];
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j)
+      if (l0 + j < nv) {
+        T[j].x *= wgt.x;
+        T[j].y *= wgt.y;
+        T[j].z *= wgt.z;
+        w.aT[(size_t)(l0 + j) * w.cap + slot] = T[j];
+      }
   }
 }
 
@@ -926,9 +959,13 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
     const bool act = q < n;
     const uint32_t slot = act ? qin[q] : 0u;
     float4 hh = make_float4(__int_as_float(-1), 0.f, 0.f, 0.f), bt = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (act) {
+    float4 rd = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t nv = 0;
+    if (act) {  // the slot's state, all loads issued together
       hh = w.hit[slot];
       bt = w.beta[slot];
+      rd = w.ray_d[slot];
+      nv = w.nv[slot];
     }
     const int tri = __float_as_int(hh.x);
     const uint32_t st = __float_as_uint(bt.w);
@@ -958,7 +995,6 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
       const double W = *e.t.W;
       const bool light_on = lp.nee && W > 0.0;
       const float3 beta = xyz(bt);
-      const float4 rd = w.ray_d[slot];
       Hit h;
       h.tri = tri;
       h.t = hh.y;
@@ -970,7 +1006,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
         const float wb = emission_weight(e.t, v, h.t, k > 0, light_on, rd.w, lp.mis);
         if (wb > 0.0f) {
           const float f = wb * v.prof;
-          add_to_carry(w, slot, xyz(__ldg(&e.t.emis[v.seg])) * f);
+          add_to_carry<2>(w, slot, nv, xyz(__ldg(&e.t.emis[v.seg])) * f);
           ebase = kD ? acc_ix16(e, lp, v.seg, kDisneyMat) : acc_ix(e, lp, v.seg, 7);
           ev = gp * beta * (f * e.es);
         }
@@ -1021,7 +1057,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
       }
     }
     warp_scatter3(sacc, ebase, ev);
-    finish_path<kD>(w, &e, lp, slot, gp, sacc, finish);
+    finish_path<kD>(w, &e, lp, slot, nv, gp, sacc, finish);
     if (lp.cache_k != kNoCache) {
       const uint32_t qi = enqueue(&lp.cb.counts[0], query);
       if (query) {
@@ -1080,7 +1116,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
         const float gg[kDisneyMat] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w, d2.x, d2.y, d2.z, d2.w, d3.x};
         for (int j = 0; j < kDisneyMat; ++j) g[j] = gg[j];
         mbase = acc_ix16(e, lp, (int)m.z, 0);
-        add_to_carry(w, m.x, xyz(cn));
+        add_to_carry<4>(w, m.x, w.nv[m.x], xyz(cn));
       }
       warp_scatter3(sacc, lbase, ge3);
       warp_scatter<kDisneyMat>(sacc, mbase, g);
@@ -1103,7 +1139,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
       g[5] = q.z * gm.w;
       g[6] = dot(q, f3(mb.x, mb.y, mb.z)) * cn.w;
       mbase = acc_ix(e, lp, (int)m.z, 0);
-      add_to_carry(w, m.x, xyz(cn));
+      add_to_carry<4>(w, m.x, w.nv[m.x], xyz(cn));
     }
     warp_scatter3(sacc, lbase, ge3);
     warp_scatter<7>(sacc, mbase, g);
@@ -1131,7 +1167,15 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
     const uint32_t q = q0 + threadIdx.x;
     const bool act = q < n;
     const uint32_t slot = act ? qin[q] : 0u;
-    const float4 bt = act ? w.beta[slot] : make_float4(0.f, 0.f, 0.f, __uint_as_float(kDead));
+    // the slot's state, all loads issued together
+    float4 bt = make_float4(0.f, 0.f, 0.f, __uint_as_float(kDead)), hh = bt, rd = bt;
+    uint32_t nv = 0;
+    if (act) {
+      bt = w.beta[slot];
+      hh = w.hit[slot];
+      rd = w.ray_d[slot];
+      nv = w.nv[slot];
+    }
     const uint32_t st = __float_as_uint(bt.w);
     bool cont = false, finish = false;
     float3 org = f3(0.f, 0.f, 0.f), wo = f3(0.f, 0.f, 0.f), beta = xyz(bt);
@@ -1141,9 +1185,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
     const WfScene& e = tab[b];
     float3 gfin = f3(0.f, 0.f, 0.f);
     if (!(st & kDead)) {
-      const float4 hh = w.hit[slot];
       tri = __float_as_int(hh.x);
-      const float4 rd = w.ray_d[slot];
       Hit h;
       h.tri = tri;
       h.t = hh.y;
@@ -1166,15 +1208,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
             load_disney(e.dis, v.seg, m);
             const float kk = co / pdf;
             const float3 wgt = disney_eval(m, v.ns, X, Y, v.wi, wo) * kk;
-            const uint32_t nv = w.nv[slot];
-            for (uint32_t l = 0; l < nv; ++l) {
-              const size_t ix = (size_t)l * w.cap + slot;
-              float4 T = w.aT[ix];
-              T.x *= wgt.x;
-              T.y *= wgt.y;
-              T.z *= wgt.z;
-              w.aT[ix] = T;
-            }
+            scale_carry(w, slot, nv, wgt);
             const size_t ix = (size_t)nv * w.cap + slot;
             w.aT[ix] = make_float4(beta.x, beta.y, beta.z, kk);
             w.aU[ix] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1197,15 +1231,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
           const BrdfVal bv = brdf_eval(ma, mb, v.ns, v.wi, wo);
           const float kk = co / pdf;
           const float3 wgt = bv.f * kk;
-          const uint32_t nv = w.nv[slot];
-          for (uint32_t l = 0; l < nv; ++l) {
-            const size_t ix = (size_t)l * w.cap + slot;
-            float4 T = w.aT[ix];
-            T.x *= wgt.x;
-            T.y *= wgt.y;
-            T.z *= wgt.z;
-            w.aT[ix] = T;
-          }
+          scale_carry(w, slot, nv, wgt);
           const size_t ix = (size_t)nv * w.cap + slot;
           w.aT[ix] = make_float4(beta.x, beta.y, beta.z, kk * (1.0f / kPi));
           w.aU[ix] = make_float4(0.f, 0.f, 0.f, kk * bv.sp.s);
@@ -1222,7 +1248,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
         w.beta[slot] = make_float4(bt.x, bt.y, bt.z, __uint_as_float(st | kDead));
       }
     }
-    finish_path<kD>(w, &e, lp, slot, gfin, sacc, finish);
+    finish_path<kD>(w, &e, lp, slot, nv, gfin, sacc, finish);
     const uint32_t ci = enqueue(nout, cont);
     if (cont) {
       qout[ci] = slot;
@@ -1250,13 +1276,14 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
     const bool act = q < n;
     const uint32_t slot = act ? __float_as_uint(lp.cb.q.d[q].w) : 0u;
     const uint32_t st = act ? __float_as_uint(w.beta[slot].w) : 0u;
+    const uint32_t nv = act ? w.nv[slot] : 0u;
     const WfScene& e = tab[state_scene(st)];
     float g[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int base = -1;
     float3 gp = f3(0.f, 0.f, 0.f);
     if (act) {
       const int seg = __float_as_int(lp.cb.q.x[q].w);
-      add_to_carry(w, slot, xyz(lp.cb.qc[q]));
+      add_to_carry<2>(w, slot, nv, xyz(lp.cb.qc[q]));
       const float* dp = lp.cb.qdp + 8 * (size_t)q;
 #pragma unroll
       for (int j = 0; j < 7; ++j) g[j] = dp[j];
@@ -1266,7 +1293,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
       gp = pixel_grad(e, ent, inv_spp);
     }
     warp_scatter<7>(sacc, base, g);
-    finish_path<false>(w, &e, lp, slot, gp, sacc, act);
+    finish_path<false>(w, &e, lp, slot, nv, gp, sacc, act);
     if (act) w.beta[slot].w = __uint_as_float(st | kDead);
   }
   if (!lp.gacc) acc_flush(sacc, np, w.blk);
@@ -1426,14 +1453,15 @@ static int table_width(const std::vector<WfScene>& tab) {
 
 // One launch of traversal mode kMode over the table's BVH width.
 template <int kMode>
-static void launch_trace(int width, int grid, const WfScene* tab_dev, const WfDev& w, int cur, int steps,
-                         uint32_t* err, cudaStream_t st) {
+static void launch_trace(int width, int grid, const WfScene* tab_dev, int n_scenes, const WfDev& w, int cur,
+                         int steps, uint32_t* err, cudaStream_t st) {
+  const int one = n_scenes == 1 ? 1 : 0;
   if (width == 8)
-    wf_trace<kMode, 8><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, err);
+    wf_trace<kMode, 8><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, err);
   else if (width == 4)
-    wf_trace<kMode, 4><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, err);
+    wf_trace<kMode, 4><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, err);
   else
-    wf_trace<kMode, 2><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, err);
+    wf_trace<kMode, 2><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, err);
 }
 
 // Chunks of at most cap / spp pixels; an adjoint chunk also ends before a
@@ -1499,7 +1527,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
     for (uint32_t k = 0; k <= last_k; ++k) {
       {
         IPT_STAGE(8);
-        launch_trace<0>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
+        launch_trace<0>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st);
       }
       {
         IPT_STAGE(10);
@@ -1510,7 +1538,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
       }
       if (k < last_k && k < tp.max_depth && tp.nee && !(record && k < lp.cache_k)) {
         IPT_STAGE(9);
-        launch_trace<1>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
+        launch_trace<1>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st);
       }
       cur ^= 1;
     }
@@ -1614,7 +1642,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
     for (uint32_t k = 0; k <= last_k; ++k) {
       {
         IPT_STAGE(8);
-        launch_trace<0>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
+        launch_trace<0>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st);
       }
       {
         IPT_STAGE(11);
@@ -1624,7 +1652,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
         if (tp.nee) {
           {
             IPT_STAGE(9);
-            launch_trace<2>(width, grid, tab_dev, w, cur, L.wf_steps, err, st);
+            launch_trace<2>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st);
           }
           IPT_STAGE(12);
           wf_adj_connect<kD><<<g_c, kWfThreads, sm, st>>>(tab_dev, lp, w);

@@ -482,6 +482,14 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
           w[9 + 2 * k] |= q_hi(qa[k], cb[i].hi[k]) << (8 * i);
         }
       }
+      // Empty slots: an inverted box (lower code 255, upper code 0 on every
+      // axis; its near plane lies 255 codes past its far plane whatever the
+      // ray's direction), so the node test needs no child count; its link
+      // repeats child 0, so even a hit would only revisit a real child.
+      for (size_t i = ch.size(); i < 4; ++i) {
+        w[4 + i] = w[4];
+        for (int k = 0; k < 3; ++k) w[8 + 2 * k] |= 255u << (8 * i);
+      }
       std::memcpy(&out[16 * (size_t)it.slot], w, sizeof(w));
     }
     s.n_nodes4 = (uint32_t)(out.size() / 16);

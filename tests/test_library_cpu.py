@@ -66,3 +66,14 @@ def test_oracle_and_product_share_no_code():
                 assert not re.search(r"#include\s+[\"<][^\">]*oracle", text), f
     src = open(os.path.join(ROOT, "oracle", "ipt_oracle.cpp")).read()
     assert "#include \"" not in src
+
+
+def test_bench_finds_the_traversal_section():
+    """bench.py matches its recorded DRAM traffic to the traversal kernel's
+    sources by hashing a section of the wavefront source between two marker
+    comments; both markers must be present, in order."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert bench.kernel_sources_sha256() is not None
