@@ -19,7 +19,7 @@ import torch
 DEFAULT_CANDIDATES = (
     [dict(integrator="megakernel")]
     + [dict(integrator="wavefront", wavefront_slots=s, trace_steps=k, bvh_width=b)
-       for b, s, k in itertools.product([2, 4, 8], [1 << 21, 1 << 25], [8, 16])]
+       for b, s, k in itertools.product([2, 4, 8], [1 << 21, 1 << 25], [16, 24])]
 )
 
 

@@ -481,7 +481,9 @@ __device__ __forceinline__ void trace_finish(const WfDev& w, int cur, uint32_t i
 //    node, node tests otherwise (the other lanes sit the step out).  Letting
 //    both kinds run in one step serialises the two code paths with most
 //    lanes masked off in each.  The warp refetches once `steps` of its lanes
-//    are idle (or all are).
+//    are idle (or all are); the lanes whose rays have ended store their
+//    results then, together, rather than each in the step its ray ends
+//    (with one or two lanes active).
 //  * Binary BVH: rounds of `steps` node visits, whole leaves at a time, and a
 //    refetch after each round.
 template <int kMode, int kWidth>
@@ -503,8 +505,14 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
   Trav T;
   SceneDev sd = tab[0].s;
   int64_t item = -1;
+  bool fin = false;      // wide BVHs: the lane's ray has ended, its result not yet stored
   bool drained = false;  // warp-uniform: the queue has no rays left
   for (;;) {
+    if (fin) {  // results are stored at the refill, by all ended lanes together
+      trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
+      item = -1;
+      fin = false;
+    }
     const bool need = item < 0 && !drained;
     const unsigned m = __ballot_sync(0xffffffffu, need);
     if (m) {
@@ -536,21 +544,16 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
       }
     } else {
       for (;;) {
-        const bool live = item >= 0;
+        const bool live = item >= 0 && !fin;
         const bool at_tri = live && T.tri < T.tri_end;
         const unsigned ml = __ballot_sync(0xffffffffu, live);
         const unsigned mt = __ballot_sync(0xffffffffu, at_tri);
         if (ml == 0u || (!drained && 32 - __popc(ml) >= refill)) break;
         const bool tri_phase = __popc(mt) >= __popc(ml & ~mt);
-        if (live && at_tri == tri_phase) {
-          const bool done = at_tri        ? tri_step<kAny, kWidth>(sd, T, sh)
-                            : kWidth == 8 ? node_step8<kAny>(sd, T, sh, err)
-                                          : node_step4<kAny>(sd, T, sh, err);
-          if (done) {
-            trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
-            item = -1;
-          }
-        }
+        if (live && at_tri == tri_phase)
+          fin = at_tri        ? tri_step<kAny, kWidth>(sd, T, sh)
+                : kWidth == 8 ? node_step8<kAny>(sd, T, sh, err)
+                              : node_step4<kAny>(sd, T, sh, err);
       }
     }
   }
