@@ -764,18 +764,28 @@ __global__ void __launch_bounds__(kWfThreads) wf_reduce(const WfScene* tab, WfPa
 
 // ---------------------------------------------------------------------------
 // Adjoint stages.  Shared accumulators cover segments [seg_lo, seg_lo + seg_n)
-// of the launch's concatenated segment space.
+// of the launch's concatenated segment space: P values per segment (10, or
+// 16 for the Disney model) at a stride of P + 1 floats, an odd stride, so
+// that lanes adding parameter j of different segments fall in different
+// banks (at stride 10 only 16 of the 32 banks are reachable for a given j;
+// at 16, two).  Global accumulators and the per-block gradient rows keep
+// stride P.
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr uint32_t acc_shared_floats(uint32_t P, uint32_t seg_n) { return (P + 1u) * seg_n; }
+
 __device__ __forceinline__ void acc_zero(float* sacc, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sacc[i] = 0.0f;
   __syncthreads();
 }
 
-__device__ __forceinline__ void acc_flush(const float* sacc, uint32_t n, float* blk) {
+// Adds the block's shared accumulators (stride P + 1) to its gradient row
+// (np = P * seg_n values, stride P).
+template <uint32_t P>
+__device__ __forceinline__ void acc_flush(const float* sacc, uint32_t np, float* blk) {
   __syncthreads();
-  float* row = blk + (size_t)blockIdx.x * n;
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const float v = sacc[i];
+  float* row = blk + (size_t)blockIdx.x * np;
+  for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
+    const float v = sacc[(i / P) * (P + 1u) + i % P];
     if (v != 0.0f) row[i] += v;
   }
 }
@@ -817,7 +827,7 @@ __device__ __forceinline__ void warp_scatter3(float* acc, int base, float3 a) {
 
 // Accumulator index of parameter j of segment `seg` of scene entry e.
 __device__ __forceinline__ int acc_ix(const WfScene& e, const WfParams& lp, int seg, int j) {
-  return 10 * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
+  return (lp.gacc ? 10 : 11) * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
 }
 
 __device__ __forceinline__ float3 pixel_grad(const WfScene& e, uint32_t entry, float inv_spp) {
@@ -826,7 +836,7 @@ __device__ __forceinline__ float3 pixel_grad(const WfScene& e, uint32_t entry, f
 
 // The same for the Disney model's 16 values per segment.
 __device__ __forceinline__ int acc_ix16(const WfScene& e, const WfParams& lp, int seg, int j) {
-  return kDisneyStride * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
+  return (lp.gacc ? kDisneyStride : kDisneyStride + 1) * ((int)e.seg_offset + seg - (int)lp.seg_lo) + j;
 }
 
 
@@ -950,7 +960,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = (kD ? 16u : 10u) * lp.seg_n;
-  if (!lp.gacc) acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, acc_shared_floats(kD ? 16u : 10u, lp.seg_n));
   const uint32_t n = w.cnt[cur];
   const uint32_t si = set_iter(lp);
   const float inv_spp = 1.0f / (float)lp.spp;
@@ -1087,7 +1097,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
       }
     }
   }
-  if (!lp.gacc) acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush<kD ? 16u : 10u>(sacc, np, w.blk);
 }
 
 // Unoccluded next-event terms: light emission (Eq. 5), the vertex material
@@ -1097,7 +1107,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = (kD ? 16u : 10u) * lp.seg_n;
-  if (!lp.gacc) acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, acc_shared_floats(kD ? 16u : 10u, lp.seg_n));
   const uint32_t n = w.cnt[2];
   const uint32_t lane = threadIdx.x & 31u;
   for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < n; i0 += gridDim.x * blockDim.x) {
@@ -1147,7 +1157,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
     warp_scatter3(sacc, lbase, ge3);
     warp_scatter<7>(sacc, mbase, g);
   }
-  if (!lp.gacc) acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush<kD ? 16u : 10u>(sacc, np, w.blk);
 }
 
 // Stage B: BRDF sampling; the new vertex joins the carry.
@@ -1157,7 +1167,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = (kD ? 16u : 10u) * lp.seg_n;
-  if (!lp.gacc) acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, acc_shared_floats(kD ? 16u : 10u, lp.seg_n));
   if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[3] = 0;
   const uint32_t n = w.cnt[cur];
   const uint32_t si = set_iter(lp);
@@ -1260,7 +1270,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
       w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
     }
   }
-  if (!lp.gacc) acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush<kD ? 16u : 10u>(sacc, np, w.blk);
 }
 
 // Paths closed by the cache: its prediction joins the earlier vertices'
@@ -1270,7 +1280,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
   extern __shared__ float sacc_sh[];
   float* sacc = lp.gacc ? lp.gacc : sacc_sh;
   const uint32_t np = 10u * lp.seg_n;
-  if (!lp.gacc) acc_zero(sacc, np);
+  if (!lp.gacc) acc_zero(sacc, acc_shared_floats(10u, lp.seg_n));
   const uint32_t n = lp.cb.counts[0];
   const float inv_spp = 1.0f / (float)lp.spp;
   const uint32_t lane = threadIdx.x & 31u;
@@ -1299,7 +1309,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
     finish_path<false>(w, &e, lp, slot, nv, gp, sacc, act);
     if (act) w.beta[slot].w = __uint_as_float(st | kDead);
   }
-  if (!lp.gacc) acc_flush(sacc, np, w.blk);
+  if (!lp.gacc) acc_flush<10u>(sacc, np, w.blk);
 }
 
 // grad_acc[i] += sum over block rows (FP64), for the chunk's parameters.
@@ -1607,13 +1617,13 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
   const std::vector<WfChunk> chunks = wf_plan(tab, wb.cap, tp.spp, max_seg);
   // chunks of more than max_seg segments (one scene with that many)
   // accumulate with atomics in global memory instead of shared memory
-  uint32_t max_np = 0, max_np_shared = 0;
+  uint32_t max_np = 0, max_shared = 0;
   for (const WfChunk& c : chunks) {
     max_np = std::max(max_np, P * c.seg_n);
-    if (c.seg_n <= max_seg) max_np_shared = std::max(max_np_shared, P * c.seg_n);
+    if (c.seg_n <= max_seg) max_shared = std::max(max_shared, acc_shared_floats(P, c.seg_n));
   }
   if (max_np > wb.blk_params) return cudaErrorInvalidValue;
-  const size_t shmem = max_np_shared * sizeof(float);
+  const size_t shmem = max_shared * sizeof(float);
   if (shmem > 48 * 1024) {
     cudaFuncSetAttribute(wf_adj_a<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     cudaFuncSetAttribute(wf_adj_connect<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
@@ -1626,7 +1636,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
     const uint32_t np = P * c.seg_n;
     const bool global = c.seg_n > max_seg;
     lp.gacc = global ? wb.blk : nullptr;
-    const size_t sm = global ? 0 : np * sizeof(float);
+    const size_t sm = global ? 0 : acc_shared_floats(P, c.seg_n) * sizeof(float);
     // each adjoint stage runs one wave at its own occupancy for this
     // accumulator size; block b of every stage adds into gradient row b
     // (all blocks into row 0 in global mode)
