@@ -798,7 +798,8 @@ __device__ __forceinline__ void acc_flush(const float* sacc, uint32_t np, float*
 // the N sums; otherwise each lane adds its own values.  (Grouping lanes by
 // target with __match_any_sync and reducing every group was measured slower:
 // its shuffles cost more than the atomics they save in these latency-bound
-// stages.)
+// stages; so was reducing only the lanes that share the first lane's
+// target.)
 template <int N>
 __device__ __forceinline__ void warp_scatter(float* acc, int base, const float (&v)[N]) {
   const uint32_t lane = threadIdx.x & 31u;

@@ -303,6 +303,43 @@ def test_gradient_central_differences(built, integrator):
         assert abs(fd - g[k]) <= 1e-2 * max(abs(g[k]), 1e-2 * scale), (k, fd, g[k])
 
 
+def test_gradient_central_differences_large_room(built):
+    """The ~516k-triangle, 150-segment room at 640x480: central differences
+    (h = 1e-3, same sample set on both sides, sampling frozen at p) of
+    <w, I> against J^T w on 20 random parameters among those the weights
+    reach, w nonzero on a 64x48 crop."""
+    sc = scenes.room_500k()
+    sc.cameras = sc.cameras[:1]
+    p = perturbed(sc, emission=0.05)
+    tr = tracer(sc, SEED, "wavefront")
+    tr.set_params(p)
+    opts = TraceOptions(spp_r=8, spp_d=8, max_depth=4, gradcheck_same_set=True)
+    W = sc.cameras[0].width
+    rng = np.random.default_rng(6)
+    w_np = np.zeros((tr.n_pix, 3), np.float32)
+    for y in range(200, 248):
+        w_np[y * W + 300: y * W + 364] = rng.normal(size=(64, 3))
+    w = torch.from_numpy(w_np).cuda()
+    pt = torch.from_numpy(p).cuda()
+    g = tr.backward(w, opts, set_id=0, params=pt, sampling_params=pt).cpu().numpy().reshape(-1)
+    scale = np.abs(g).max()
+    reached = np.flatnonzero(np.abs(g) > 1e-3 * scale)
+    assert len(reached) >= 20
+    h = 1e-3
+    for k in rng.choice(reached, 20, replace=False):
+        pp = p.copy().reshape(-1)
+        pm = p.copy().reshape(-1)
+        pp[k] += h
+        pm[k] -= h
+        ip = tr.render(opts, set_id=0, spp=8, params=torch.from_numpy(pp.reshape(p.shape)).cuda(),
+                       sampling_params=pt)
+        im = tr.render(opts, set_id=0, spp=8, params=torch.from_numpy(pm.reshape(p.shape)).cuda(),
+                       sampling_params=pt)
+        fd = float((w.double() * (ip.double() - im.double())).sum() / (2 * h))
+        assert abs(fd - g[k]) <= 1e-2 * max(abs(g[k]), 1e-2 * scale), (k, fd, g[k])
+    tr.close()
+
+
 def test_autograd_function(built):
     sc = scenes.cornell_box(1000, 16, 16)
     tr = Tracer(sc, seed=SEED)
