@@ -29,6 +29,7 @@
 // block processes, then read back and added to the global gradient once per
 // launch.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -182,7 +183,11 @@ __device__ __forceinline__ float3 unit_pos(const CacheNet& net, float4 x) {
 // Encodes rows [r0, r0 + 16) (valid below `end`) into the warp's input tile
 // X (16 rows of 80 BF16 features) and its row metadata (unit position, valid
 // flag).
-template <class Tile>
+// Encodes 16 rows into X.  kHalf: the hash-grid features come from the
+// table's FP16 copy (queries) instead of the FP32 master (training and the
+// input VJP, whose result depends on the table only through the ReLU
+// decisions, which the FP16 rounding would move near their kinks).
+template <bool kHalf, class Tile>
 __device__ __forceinline__ void encode_rows(const CacheNet& net, const int* res, const CacheRows& rows, const float4* mat_a,
                             const float4* mat_b, uint32_t r0, uint32_t end, Tile X, float4* meta, int lane) {
   const int row = lane & 15;
@@ -231,7 +236,13 @@ __device__ __forceinline__ void encode_rows(const CacheNet& net, const int* res,
       float f0 = 0.0f, f1 = 0.0f;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        const float2 v = __ldg(&net.table[idx[c]]);
+        float2 v;
+        if (kHalf) {
+          const uint32_t hv = __ldg(&net.table_h[idx[c]]);
+          v = __half22float2(*reinterpret_cast<const __half2*>(&hv));
+        } else {
+          v = __ldg(&net.table[idx[c]]);
+        }
         f0 += w[c] * v.x;
         f1 += w[c] * v.y;
       }
@@ -497,7 +508,7 @@ __global__ void __launch_bounds__(kVjpWarps * 32, 2) cache_vjp_k(CacheNet net, C
        tile += gridDim.x * (uint32_t)kVjpWarps) {
     const uint32_t r0 = tile * 16u;
     __syncwarp();
-    encode_rows(net, res, rows, mat_a, mat_b, r0, n, X, meta, lane);
+    encode_rows<false>(net, res, rows, mat_a, mat_b, r0, n, X, meta, lane);
     float y[2][4];
     uint32_t mask[4];
     net_forward_mask(Wt, X, y, mask, lane);
@@ -710,7 +721,7 @@ __global__ void __launch_bounds__(kThreads) cache_grad_k(CacheNet net, CacheRows
       }
     }
     const uint32_t r0 = begin + tile * kTileRows + 16u * (uint32_t)warp;
-    encode_rows(net, res, rows, mat_a, mat_b, r0, end, X, meta, lane);
+    encode_rows<false>(net, res, rows, mat_a, mat_b, r0, end, X, meta, lane);
     float y[2][4];
     net_forward<true>(Wt, X, H, hstride, y, lane);
     // relative L2: d/dy_c of (y_c - t_c)^2 / (sg(y_c)^2 + 0.01), mean over rows and channels
@@ -921,8 +932,8 @@ __global__ void __launch_bounds__(128, 2) cache_infer_tc_k(CacheNet net, CacheRo
   const uint32_t n_tiles = (n + kQRows - 1u) / kQRows;
   for (uint32_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const uint32_t r0 = tile * kQRows;
-    encode_rows(net, res, rows, mat_a, mat_b, r0 + 32u * warp, n, X.rows_from(32 * warp), meta + 32 * warp, lane);
-    encode_rows(net, res, rows, mat_a, mat_b, r0 + 32u * warp + 16u, n, X.rows_from(32 * warp + 16),
+    encode_rows<true>(net, res, rows, mat_a, mat_b, r0 + 32u * warp, n, X.rows_from(32 * warp), meta + 32 * warp, lane);
+    encode_rows<true>(net, res, rows, mat_a, mat_b, r0 + 32u * warp + 16u, n, X.rows_from(32 * warp + 16),
                 meta + 32 * warp + 16, lane);
     float y[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
@@ -1009,8 +1020,8 @@ __device__ __forceinline__ int image_index(int i) {
 }
 
 __global__ void cache_adam_k(float* w, float* mw, float* vw, float* gw, float* table, float* mt, float* vt,
-                             float* gt, __nv_bfloat16* wt, float lr, float b1, float b2, float eps, float bc1,
-                             float bc2) {
+                             float* gt, __nv_bfloat16* wt, __half* table_h, float lr, float b1, float b2, float eps,
+                             float bc1, float bc2) {
   const size_t nw = kCacheWeights, n = nw + kCacheTableFloats;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     float *p, *m, *v, *gp;
@@ -1028,8 +1039,17 @@ __global__ void cache_adam_k(float* w, float* mw, float* vw, float* gw, float* t
     gp[k] = 0.0f;
     const float np = p[k] - lr * (m1 / bc1) / (sqrtf(v1 / bc2) + eps);
     p[k] = np;
-    if (i < nw) wt[image_index((int)i)] = __float2bfloat16_rn(np);
+    if (i < nw)
+      wt[image_index((int)i)] = __float2bfloat16_rn(np);
+    else
+      table_h[k] = __float2half_rn(np);
   }
+}
+
+__global__ void cache_pack_table_k(const float* table, __half* table_h) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < kCacheTableFloats;
+       i += (size_t)gridDim.x * blockDim.x)
+    table_h[i] = __float2half_rn(table[i]);
 }
 
 __global__ void cache_pack_k(const float* w, __nv_bfloat16* wt) {
@@ -1142,10 +1162,16 @@ cudaError_t cache_grad(const CacheNet& net, const CacheRows& rows, const float4*
 }
 
 cudaError_t cache_adam(float* w, float* mw, float* vw, float* gw, float* table, float* mt, float* vt, float* gt,
-                       uint4* wt, float lr, float beta1, float beta2, float eps, float bc1, float bc2,
-                       int num_sms, cudaStream_t st) {
-  cache_adam_k<<<num_sms * 8, 256, 0, st>>>(w, mw, vw, gw, table, mt, vt, gt,
-                                            reinterpret_cast<__nv_bfloat16*>(wt), lr, beta1, beta2, eps, bc1, bc2);
+                       uint4* wt, uint32_t* table_h, float lr, float beta1, float beta2, float eps, float bc1,
+                       float bc2, int num_sms, cudaStream_t st) {
+  cache_adam_k<<<num_sms * 8, 256, 0, st>>>(w, mw, vw, gw, table, mt, vt, gt, reinterpret_cast<__nv_bfloat16*>(wt),
+                                            reinterpret_cast<__half*>(table_h), lr, beta1, beta2, eps, bc1, bc2);
+  return cudaGetLastError();
+}
+
+cudaError_t cache_pack_table(const float* table, uint32_t* table_h, cudaStream_t st) {
+  cache_pack_table_k<<<grid_of((uint32_t)(kCacheTableFloats / 4), 256), 256, 0, st>>>(
+      table, reinterpret_cast<__half*>(table_h));
   return cudaGetLastError();
 }
 

@@ -24,7 +24,8 @@ constexpr uint32_t kCacheWtElems = 64 * 88 + 3 * 64 * 72 + 16 * 72;
 // Device view of the network used by a pass.
 struct CacheNet {
   const uint4* wt;        // BF16 weight image (kCacheWtElems / 8 uint4)
-  const float2* table;    // [level][kCacheT] features
+  const float2* table;    // [level][kCacheT] features (FP32 master, read by training and the VJP)
+  const uint32_t* table_h;  // the same as FP16 pairs, read by queries
   float3 lo, inv_ext;     // world -> unit cube (the scene's bounding box)
   int res[kCacheLevels];  // grid resolution of each level
   uint32_t dense;         // bit l: level l indexes its (res+1)^3 vertices directly
@@ -85,13 +86,16 @@ cudaError_t cache_grad(const CacheNet& net, const CacheRows& rows, const float4*
                        const CacheOut& out, int num_sms, cudaStream_t st);
 
 // Adam on weights and table with the accumulated gradients (which it
-// clears); rewrites the BF16 weight image.  bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
+// clears); rewrites the BF16 weight image and the table's FP16 copy.
+// bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
 cudaError_t cache_adam(float* w, float* mw, float* vw, float* gw, float* table, float* mt, float* vt, float* gt,
-                       uint4* wt, float lr, float beta1, float beta2, float eps, float bc1, float bc2,
-                       int num_sms, cudaStream_t st);
+                       uint4* wt, uint32_t* table_h, float lr, float beta1, float beta2, float eps, float bc1,
+                       float bc2, int num_sms, cudaStream_t st);
 
 // BF16 weight image from the FP32 master weights.
 cudaError_t cache_pack_weights(const float* w, uint4* wt, cudaStream_t st);
+// FP16 copy of the hash table (kCacheTableFloats halves), from the FP32 master.
+cudaError_t cache_pack_table(const float* table, uint32_t* table_h, cudaStream_t st);
 
 // Rows of the evaluation entry points: row i gets x = x01[i], segment i,
 // and per-row parameter tables (kd, r) / (ks, 0) from params7[i].

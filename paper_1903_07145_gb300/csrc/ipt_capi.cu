@@ -360,6 +360,7 @@ ipt::CacheNet cache_net(const DeviceScene* s, bool unit_inputs) {
   ipt::CacheNet n{};
   n.wt = c->wt;
   n.table = reinterpret_cast<const float2*>(c->table);
+  n.table_h = c->table_h;
   for (int l = 0; l < ipt::kCacheLevels; ++l) n.res[l] = c->res[l];
   n.dense = c->dense;
   if (unit_inputs) {
@@ -448,8 +449,9 @@ ipt_status cache_train_pass(ipt_ctx* ctx, int32_t scene, DeviceScene* s, const i
     const double t = (double)(++c->steps_done);
     const float bc1 = (float)(1.0 - std::pow((double)c->opts.beta1, t));
     const float bc2 = (float)(1.0 - std::pow((double)c->opts.beta2, t));
-    IPT_CK(ipt::cache_adam(c->w, c->mw, c->vw, c->gw, c->table, c->mt, c->vt, c->gt, c->wt, c->opts.lr,
-                           c->opts.beta1, c->opts.beta2, c->opts.eps, bc1, bc2, ctx->L.num_sms, ctx->stream));
+    IPT_CK(ipt::cache_adam(c->w, c->mw, c->vw, c->gw, c->table, c->mt, c->vt, c->gt, c->wt, c->table_h,
+                           c->opts.lr, c->opts.beta1, c->opts.beta2, c->opts.eps, bc1, bc2, ctx->L.num_sms,
+                           ctx->stream));
   }
   c->last_pass_steps = steps;
   return IPT_OK;

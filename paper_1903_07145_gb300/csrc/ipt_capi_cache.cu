@@ -86,6 +86,7 @@ ipt_status cache_create(ipt_ctx* ctx, DeviceScene* s, const ipt_cache_opts* o) {
   A(&c->gw, nw);
   A(&c->wt, ipt::kCacheWtElems / 8);
   A(&c->table, nt);
+  A(&c->table_h, nt / 2);
   A(&c->mt, nt);
   A(&c->vt, nt);
   A(&c->gt, nt);
@@ -112,6 +113,7 @@ ipt_status cache_create(ipt_ctx* ctx, DeviceScene* s, const ipt_cache_opts* o) {
   if (e == cudaSuccess) e = cudaMemset(c->wt, 0, ipt::kCacheWtElems * 2);
   if (e == cudaSuccess) e = cudaMemset(c->buf.counts, 0, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = ipt::cache_pack_weights(c->w, c->wt, ctx->stream);
+  if (e == cudaSuccess) e = ipt::cache_pack_table(c->table, c->table_h, ctx->stream);
   if (e != cudaSuccess) {
     free_cache(c);
     return cuda_fail(ctx, e, "cache allocation");
@@ -180,7 +182,10 @@ ipt_status ipt_cache_weights_set(ipt_ctx* ctx, int32_t scene, const float* weigh
     IPT_CK(cudaMemcpyAsync(c->w, weights, nw * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     IPT_CK(ipt::cache_pack_weights(c->w, c->wt, ctx->stream));
   }
-  if (table) IPT_CK(cudaMemcpyAsync(c->table, table, nt * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  if (table) {
+    IPT_CK(cudaMemcpyAsync(c->table, table, nt * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    IPT_CK(ipt::cache_pack_table(c->table, c->table_h, ctx->stream));
+  }
   IPT_CK(cudaMemsetAsync(c->mw, 0, nw * sizeof(float), ctx->stream));
   IPT_CK(cudaMemsetAsync(c->vw, 0, nw * sizeof(float), ctx->stream));
   IPT_CK(cudaMemsetAsync(c->mt, 0, nt * sizeof(float), ctx->stream));

@@ -159,6 +159,7 @@ ipt_status ipt_checkpoint_load(ipt_ctx* ctx, int32_t scene, const void* buf, siz
     IPT_CK(H2D(c->mt, nt));
     IPT_CK(H2D(c->vt, nt));
     IPT_CK(ipt::cache_pack_weights(c->w, c->wt, ctx->stream));
+    IPT_CK(ipt::cache_pack_table(c->table, c->table_h, ctx->stream));
     c->steps_done = h.cache_steps;
     c->active = h.cache_active != 0;
     c->fell_back = h.cache_fell_back != 0;

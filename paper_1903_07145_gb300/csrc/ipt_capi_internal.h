@@ -40,7 +40,8 @@ struct CacheState {
   float* vw = nullptr;
   float* gw = nullptr;
   uint4* wt = nullptr;     // BF16 image
-  float* table = nullptr;
+  float* table = nullptr;       // FP32 master
+  uint32_t* table_h = nullptr;  // FP16 pairs read by queries
   float* mt = nullptr;
   float* vt = nullptr;
   float* gt = nullptr;
