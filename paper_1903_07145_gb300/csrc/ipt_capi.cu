@@ -137,6 +137,7 @@ ipt::TraceParams trace_params(const ipt_ctx* ctx, int32_t scene, const ipt_trace
 ipt_status ensure_pick(ipt_ctx* ctx, DeviceScene* s, uint32_t batch) {
   if (s->pick_cap >= batch) return IPT_OK;
   IPT_CK(cudaStreamSynchronize(ctx->stream));
+  ++ctx->alloc_gen;
   cudaFree(s->pick);
   cudaFree(s->g_pick);
   s->pick = nullptr;
@@ -154,6 +155,7 @@ ipt_status ensure_tables(ipt_ctx* ctx, DeviceScene* s, const float* params, cons
   Timed tm(ctx, IPT_KERNEL_PREPARE);
   IPT_CK(ipt::launch_prepare(buffers(ctx, s), s->tab, params, sparams ? sparams : params, ctx->stream));
   s->tab_is_ctx = is_ctx;
+  s->tab_batch = -1;
   return IPT_OK;
 }
 
@@ -167,13 +169,17 @@ void wf_release(ipt_ctx* c) {
 
 // Wavefront buffers for `cap` slots (plus the adjoint's carry when asked),
 // allocated on first use and kept by the context.
-ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney) {
+ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney, uint32_t depth) {
   const uint32_t cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
-  const bool fits = ctx->wf.cap == cap && (!adjoint || (ctx->wf_adjoint && ctx->wf.blk_params >= n_params)) &&
+  if (adjoint && (depth == 0 || depth > (uint32_t)ipt::kMaxAdjointDepth)) depth = ipt::kMaxAdjointDepth;
+  const bool fits = ctx->wf.cap == cap &&
+                    (!adjoint || (ctx->wf_adjoint && ctx->wf.blk_params >= n_params && ctx->wf.depth_cap >= depth)) &&
                     (!disney || ctx->wf_disney);
   if (fits) return IPT_OK;
   IPT_CK(cudaStreamSynchronize(ctx->stream));
+  ++ctx->alloc_gen;
   const uint32_t keep_params = std::max(n_params, ctx->wf.blk_params);
+  const uint32_t keep_depth = std::max(adjoint ? depth : 0u, ctx->wf_adjoint ? ctx->wf.depth_cap : 0u);
   const bool want_adj = adjoint || ctx->wf_adjoint;
   const bool want_disney = want_adj && (disney || ctx->wf_disney);
   wf_release(ctx);
@@ -202,16 +208,16 @@ ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney)
   A(&w.sh_c, cap);
   A(&w.sh_vis, cap);
   if (want_adj) {
-    A(&w.aT, (size_t)ipt::kMaxAdjointDepth * cap);
-    A(&w.aU, (size_t)ipt::kMaxAdjointDepth * cap);
-    A(&w.aR, (size_t)ipt::kMaxAdjointDepth * cap);
+    A(&w.aT, (size_t)keep_depth * cap);
+    A(&w.aU, (size_t)keep_depth * cap);
+    A(&w.aR, (size_t)keep_depth * cap);
     A(&w.nv, cap);
     A(&w.sh_ge, cap);
     A(&w.sh_gm, cap);
     A(&w.sh_n, cap);
     if (want_disney) {
-      A(&w.aWi, (size_t)ipt::kMaxAdjointDepth * cap);
-      A(&w.aWo, (size_t)ipt::kMaxAdjointDepth * cap);
+      A(&w.aWi, (size_t)keep_depth * cap);
+      A(&w.aWo, (size_t)keep_depth * cap);
       A(&w.sh_dv, 4 * (size_t)cap);
     }
     // block-private rows for chunks whose accumulators fit in shared memory;
@@ -225,6 +231,7 @@ ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney)
   }
   w.cap = cap;
   w.blk_params = want_adj ? keep_params : 0;
+  w.depth_cap = want_adj ? keep_depth : 0;
   ctx->wf_adjoint = want_adj;
   ctx->wf_disney = want_disney;
   return IPT_OK;
@@ -328,7 +335,7 @@ ipt_status run_adjoint(ipt_ctx* ctx, int32_t scene_id, DeviceScene* s, uint32_t 
   if (cache && !use_wavefront_cap(ctx, tp.spp))
     return fail(ctx, IPT_ERR_INVALID_ARG, "cached passes need spp <= wavefront_slots");
   if (cache || use_wavefront(ctx, tp.spp)) {
-    ipt_status st = ensure_wf(ctx, true, 10u * s->n_seg);
+    ipt_status st = ensure_wf(ctx, true, 10u * s->n_seg, false, tp.max_depth);
     if (st != IPT_OK) return st;
     ipt::WfScene e = wf_entry(ctx, scene_id, s, begin, n);
     e.pick = pick;
@@ -874,6 +881,7 @@ ipt_status ipt_adam_step(ipt_ctx* ctx, int32_t scene, const float* grad, const i
   IPT_CK(ipt::launch_adam(buffers(ctx, s), s->tab, s->params, s->adam_m, s->adam_v, s->free_mask, s->grad_acc, grad,
                           s->step_dev, adam_host(adam), loss, s->guard_dev, ctx->err_dev, ctx->stream));
   s->tab_is_ctx = true;  // the Adam kernel rebuilt the tables from the new parameters
+  s->tab_batch = -1;
   return IPT_OK;
 }
 

@@ -136,6 +136,7 @@ ipt_status ipt_batch_create(ipt_ctx* ctx, const int32_t* scenes, uint32_t n, int
   }
   ctx->batches.push_back(b);
   *batch_id = (int32_t)ctx->batches.size() - 1;
+  for (int32_t id : b->members) ctx->scenes[id]->tab_batch = *batch_id;
   return IPT_OK;
 }
 
@@ -205,7 +206,8 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
     if (losses_out) std::fill(losses_out, losses_out + b->members.size(), 0.0);
     return IPT_OK;
   }
-  if (!b->exec || !same_opts(*opts, b->g_opts) || !same_adam(*adam, b->g_adam) || !same_cfg(ctx->cfg, b->g_cfg)) {
+  if (!b->exec || !same_opts(*opts, b->g_opts) || !same_adam(*adam, b->g_adam) || !same_cfg(ctx->cfg, b->g_cfg) ||
+      b->g_alloc_gen != ctx->alloc_gen) {
     // everything the graph touches is allocated before the capture
     if (opts->pixel_batch)
       for (int32_t id : b->members)
@@ -216,7 +218,7 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
     uint32_t max_seg = 0;
     for (const ipt::WfChunk& c : ipt::wf_plan(b->tab_host, cap, opts->spp_d, ipt::wf_max_segments()))
       max_seg = std::max(max_seg, c.seg_n);
-    if ((st = ensure_wf(ctx, true, 10u * max_seg)) != IPT_OK) return st;
+    if ((st = ensure_wf(ctx, true, 10u * max_seg, false, opts->max_depth)) != IPT_OK) return st;
     IPT_CK(cudaMemcpyAsync(b->tab_dev, b->tab_host.data(), b->tab_host.size() * sizeof(ipt::WfScene),
                            cudaMemcpyHostToDevice, ctx->stream));
     IPT_CK(cudaStreamSynchronize(ctx->stream));
@@ -237,6 +239,15 @@ ipt_status ipt_batch_step(ipt_ctx* ctx, int32_t batch, const ipt_trace_opts* opt
     b->g_opts = *opts;
     b->g_adam = *adam;
     b->g_cfg = ctx->cfg;
+    b->g_alloc_gen = ctx->alloc_gen;
+  }
+  // the members' parameter tables (shared with the single-scene calls) hold
+  // the batch's parameters unless a single-scene call rebuilt them since
+  bool stale = false;
+  for (int32_t id : b->members) stale = stale || ctx->scenes[id]->tab_batch != batch;
+  if (stale) {
+    IPT_CK(ipt::launch_prepare_batch(b->mem_dev, (uint32_t)b->members.size(), b->params, ctx->stream));
+    for (int32_t id : b->members) ctx->scenes[id]->tab_batch = batch;
   }
   {
     Timed tm(ctx, IPT_KERNEL_BATCH_STEP);
@@ -294,7 +305,10 @@ ipt_status ipt_batch_destroy(ipt_ctx* ctx, int32_t batch) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (void* p : b->owned) cudaFree(p);
   if (b->losses_host) cudaFreeHost(b->losses_host);
-  for (int32_t id : b->members) ctx->scenes[id]->tab_is_ctx = false;
+  for (int32_t id : b->members) {
+    ctx->scenes[id]->tab_is_ctx = false;
+    ctx->scenes[id]->tab_batch = -1;
+  }
   delete b;
   ctx->batches[batch] = nullptr;
   return IPT_OK;

@@ -189,7 +189,7 @@ static ipt_status disney_loss_grad_async(ipt_ctx* ctx, int32_t scene, DeviceScen
     StageTimer timer{ctx};
     const ipt::WfHook hook{stage_begin, stage_end, &timer};
     const ipt::WfHook* hp = (ctx->flags & IPT_FLAG_KERNEL_TIMING) ? &hook : nullptr;
-    if ((st = ensure_wf(ctx, true, np, true)) != IPT_OK) return st;
+    if ((st = ensure_wf(ctx, true, np, true, opts->max_depth)) != IPT_OK) return st;
     ipt::WfScene e = disney_entry(ctx, scene, s, d, 0u, n);
     e.pick = const_cast<uint32_t*>(pick);
     e.g_scale = g_scale;

@@ -115,6 +115,7 @@ struct DeviceScene {
   // parameter tables
   ipt::SegBuffers tab{};
   bool tab_is_ctx = false;  // tables were built from the context's own parameters
+  int32_t tab_batch = -1;   // batch whose parameters built the tables (-1: a single-scene call did)
   // parameters and optimiser state
   float* params = nullptr;
   float* adam_m = nullptr;
@@ -171,6 +172,7 @@ struct Batch {
   ipt_trace_opts g_opts{};
   ipt_adam_opts g_adam{};
   ipt_config g_cfg{};
+  uint64_t g_alloc_gen = 0;  // the context's alloc_gen when the graph was captured
 };
 
 struct PendingTiming {
@@ -201,6 +203,10 @@ struct ipt_ctx {
   ipt::WfBuffers wf;
   std::vector<void*> wf_owned;
   bool wf_adjoint = false;
+  // bumped whenever device buffers that a captured batch graph may use are
+  // reallocated (wavefront state, pixel-batch buffers): a batch whose graph
+  // was captured at an older value recaptures before its next replay
+  uint64_t alloc_gen = 0;
   bool wf_disney = false;          // the adjoint buffers include the Disney model's records
   ipt::WfScene* wf_tab = nullptr;  // one-entry scene table of single-scene launches
   std::vector<ipt_capi::Batch*> batches;
@@ -225,7 +231,11 @@ ipt::TraceParams trace_params(const ipt_ctx* ctx, int32_t scene, const ipt_trace
 ipt_status ensure_pick(ipt_ctx* ctx, DeviceScene* s, uint32_t batch);
 ipt_status ensure_tables(ipt_ctx* ctx, DeviceScene* s, const float* params, const float* sparams);
 void wf_release(ipt_ctx* c);
-ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney = false);
+// Wavefront state for the context's chunk size; an adjoint caller passes
+// the trace's max_depth (the per-vertex carry holds that many vertices) and
+// the S x 10 (or S x 16) parameters of its widest chunk.  Capacities only
+// grow.
+ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney = false, uint32_t depth = 0);
 bool use_wavefront_cap(const ipt_ctx* ctx, uint32_t spp);
 bool use_wavefront(const ipt_ctx* ctx, uint32_t spp);
 ipt::WfScene wf_entry(const ipt_ctx* ctx, int32_t scene_id, const DeviceScene* s, uint32_t pix_base, uint32_t n);

@@ -58,6 +58,7 @@ extern "C" ipt_status ipt_backward_noalloc(ipt_ctx* ctx, int32_t scene, const ip
     Timed tm(ctx, IPT_KERNEL_PREPARE);
     IPT_CK(ipt::launch_prepare(buffers(ctx, s), s->tab, p, sampling_params ? sampling_params : p, ctx->stream));
     s->tab_is_ctx = is_ctx;
+    s->tab_batch = -1;
   }
   const uint32_t np = 10u * s->n_seg;
   IPT_CK(cudaMemsetAsync(acc, 0, np * sizeof(double), ctx->stream));

@@ -115,6 +115,7 @@ struct WfBuffers {
   float* blk = nullptr;
   uint32_t cap = 0;
   uint32_t blk_params = 0;  // S x 10 capacity of each block row
+  uint32_t depth_cap = 0;   // vertices the per-vertex carry holds (adjoint max_depth)
 };
 
 constexpr int kMaxAdjointDepth = 8;

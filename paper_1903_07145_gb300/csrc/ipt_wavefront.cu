@@ -1610,7 +1610,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
   const bool query = lp.cache_k != kNoCache;
   const uint32_t last_k = query ? lp.cache_k : tp.max_depth;
   const WfDev w = wf_dev(wb);
-  if (wb.cap < tp.spp || !wb.aT || ns == 0) return cudaErrorInvalidValue;
+  if (wb.cap < tp.spp || !wb.aT || ns == 0 || tp.max_depth > wb.depth_cap) return cudaErrorInvalidValue;
   if (query && (ns != 1 || cache->buf.q_cap < wb.cap)) return cudaErrorInvalidValue;
   const int width = table_width(tab);
   const int grid = wf_grid(L);

@@ -84,6 +84,32 @@ def test_batch_graph_recaptures_on_new_options(built):
     ss.close()
 
 
+def test_batch_recaptures_after_the_context_reallocates(built):
+    """A captured batch graph uses the context's wavefront buffers and the
+    members' parameter tables.  A member stepped alone between two batch
+    steps, with a deeper adjoint, makes the context reallocate the wavefront
+    state (the per-vertex carry grows) and rebuilds the member's tables from
+    its own parameters (the batch keeps its own copy of them).  The next
+    batch step recaptures and rebuilds the tables from the batch's
+    parameters: the batch then steps as a twin batch in another context."""
+    opts = TraceOptions(spp_r=4, spp_d=4, max_depth=3)
+    deep = TraceOptions(spp_r=4, spp_d=4, max_depth=6)
+    adam = AdamOptions()
+    ss, twin = prepared(), prepared()
+    for s_ in (ss, twin):
+        s_.make_batch()
+    for it in range(2):  # later losses follow the float sums' rounding through Adam
+        a, b = ss.batch_step(opts, adam), twin.batch_step(opts, adam)
+        assert np.allclose(a, b, rtol=1e-6 if it == 0 else 1e-3, atol=0), (it, a, b)
+    ss.step(0, deep, adam)
+    a, b = ss.batch_step(opts, adam), twin.batch_step(opts, adam)
+    assert np.all(np.isfinite(a)) and np.allclose(a, b, rtol=1e-3, atol=0), (a, b)
+    for i in range(3):
+        assert np.abs(ss.batch_params(i) - twin.batch_params(i)).max() <= 6 * adam.lr, i
+    ss.close()
+    twin.close()
+
+
 def test_batch_loss_decreases(built):
     ss = prepared()
     ss.make_batch()
