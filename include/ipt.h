@@ -110,7 +110,11 @@ typedef struct {
  *     1 = wavefront (chunks of path slots; persistent traversal kernels over
  *     compacted ray queues).
  *   wavefront_slots: path slots per wavefront chunk (0 = 1 << 20); rounded
- *     down to whole pixels.
+ *     down to whole pixels.  The context keeps 156 bytes of device memory
+ *     per slot, and once it has run an adjoint 52 + 40 D more (D: the
+ *     largest max_depth its adjoints have used; the Disney model's adjoint
+ *     adds 32 D + 64); the buffers are allocated on first use and grow, never
+ *     shrink, while the context lives.
  *   trace_steps: refill point of the persistent traversal kernels (0 = 16).
  *     4- and 8-wide BVHs: a warp fetches new rays once this many of its 32
  *     lanes are idle (values above 32 act as 32).  Binary BVH: node visits
