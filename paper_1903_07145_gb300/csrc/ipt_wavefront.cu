@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_shade_fwd(const WfScene* tab
     float pdf = 0.0f;
     Vtx v;
     if (tri >= 0) {
-      const WfScene& e = tab[b];
+      const WfScene& e = tab[lp.n_scenes == 1 ? 0u : b];
       const double W = *e.t.W;
       const bool light_on = lp.nee && W > 0.0;
       const float4 rd = w.ray_d[slot];
@@ -984,7 +984,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
     const int tri = __float_as_int(hh.x);
     const uint32_t st = __float_as_uint(bt.w);
     const uint32_t k = state_k(st), b = state_scene(st);
-    const WfScene& e = tab[b];
+    const WfScene& e = tab[lp.n_scenes == 1 ? 0u : b];
     uint32_t pid = 0, smp = 0, ent = 0;
     float3 gp = f3(0.f, 0.f, 0.f);
     if (act) {
@@ -1102,7 +1102,8 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_a(const WfScene* tab, Wf
 }
 
 // Unoccluded next-event terms: light emission (Eq. 5), the vertex material
-// (Eq. 6 at this vertex) and the carry of the earlier vertices.
+// (Eq. 6 at this vertex) and the carry of the earlier vertices.  A launch
+// over one scene skips reading the slot's state word for its scene.
 template <bool kD>
 __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab, WfParams lp, WfDev w) {
   extern __shared__ float sacc_sh[];
@@ -1121,7 +1122,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
       for (int j = 0; j < kDisneyMat; ++j) g[j] = 0.0f;
       if (vis) {
         const uint4 m = w.sh_meta[i];
-        const WfScene& e = tab[state_scene(__float_as_uint(w.beta[m.x].w))];
+        const WfScene& e = tab[lp.n_scenes == 1 ? 0u : state_scene(__float_as_uint(w.beta[m.x].w))];
         const float4 ge = w.sh_ge[i], cn = w.sh_n[i];
         lbase = acc_ix16(e, lp, (int)m.w, kDisneyMat);
         ge3 = xyz(ge);
@@ -1139,7 +1140,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_connect(const WfScene* tab,
     float g[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (vis) {
       const uint4 m = w.sh_meta[i];
-      const WfScene& e = tab[state_scene(__float_as_uint(w.beta[m.x].w))];
+      const WfScene& e = tab[lp.n_scenes == 1 ? 0u : state_scene(__float_as_uint(w.beta[m.x].w))];
       const float4 ge = w.sh_ge[i], gm = w.sh_gm[i], cn = w.sh_n[i];
       lbase = acc_ix(e, lp, (int)m.w, 7);
       ge3 = xyz(ge);
@@ -1196,7 +1197,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
     float pdf = 0.0f;
     int tri = -1;
     const uint32_t k = state_k(st), b = state_scene(st);
-    const WfScene& e = tab[b];
+    const WfScene& e = tab[lp.n_scenes == 1 ? 0u : b];
     float3 gfin = f3(0.f, 0.f, 0.f);
     if (!(st & kDead)) {
       tri = __float_as_int(hh.x);
@@ -1291,7 +1292,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_adj_cache(const WfScene* tab, W
     const uint32_t slot = act ? __float_as_uint(lp.cb.q.d[q].w) : 0u;
     const uint32_t st = act ? __float_as_uint(w.beta[slot].w) : 0u;
     const uint32_t nv = act ? w.nv[slot] : 0u;
-    const WfScene& e = tab[state_scene(st)];
+    const WfScene& e = tab[lp.n_scenes == 1 ? 0u : state_scene(st)];
     float g[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int base = -1;
     float3 gp = f3(0.f, 0.f, 0.f);
