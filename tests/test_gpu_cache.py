@@ -247,6 +247,42 @@ def test_cached_image_matches_oracle(built, b_term, D):
     assert rel(img, ref) <= 1e-2, rel(img, ref)
 
 
+def test_cached_image_full_size_room_sampled_pixels(built):
+    """The 61k-triangle room at its benchmark size (8 views of 320x240, 32
+    spp, depth 5) with the cache at vertex 1 and a random network: 24 pixels
+    sampled across the views, recomputed one by one by the cut-path oracle
+    composed with the oracle network (the queries read the table's FP16
+    copy, the oracle the FP32 table)."""
+    sc = scenes.room_60k()
+    rng = np.random.default_rng(5)
+    p = sc.gt_params.astype(np.float32).copy()
+    p[:, 7:10] += rng.uniform(0.0, 0.05, (sc.n_segments, 3)).astype(np.float32)
+    tr = cache_tracer(sc, CacheOptions(enabled=True, b_term=1))
+    tr.set_params(p)
+    W, table = network(14, out_scale=30.0)
+    tr.set_cache_weights(flat(W), table)
+    st = tr.cache_status()
+    lo, hi = np.array(st["lo"], np.float64), np.array(st["hi"], np.float64)
+    spp = 32
+    img = tr.render(TraceOptions(spp_r=spp, max_depth=5), view=-1, set_id=0, spp=spp,
+                    iteration=1).cpu().numpy().astype(np.float64)
+    osc = O.OracleScene(sc)
+    p64 = p.astype(np.float64)
+    got, ref, part = [], [], []
+    for v in range(len(sc.cameras)):
+        px = rng.choice(320 * 240, 3, replace=False).astype(np.uint32)
+        term = osc.cache_terminals(p64, 1, view=v, pixels=px, spp=spp, max_depth=5, set_id=0, iteration=1,
+                                   seed=SEED)
+        cval, _ = K.cached_values(term, p64, W, table, lo, hi, BF)
+        ref.append(K.cached_image(term, spp, cval))
+        part.append((term["beta"] * cval).reshape(-1, spp, 3).mean(1))
+        got.append(img[tr.offsets[v] + px.astype(np.int64)])
+    got, ref, part = np.concatenate(got), np.concatenate(ref), np.concatenate(part)
+    assert np.linalg.norm(part) > 0.1 * np.linalg.norm(ref)  # the cache term matters here
+    assert rel(got, ref) <= 1e-2, rel(got, ref)
+    tr.close()
+
+
 @pytest.mark.parametrize("b_term", [1, 2])
 def test_cached_gradient_matches_oracle(built, b_term):
     sc, p, tr, W, table, lo, hi = cached_setup(b_term)
