@@ -57,6 +57,31 @@ def test_image_matches_oracle(built, depth, integrator):
     tr.close()
 
 
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_full_size_room_sampled_pixels(built, integrator):
+    """The 61k-triangle room at its benchmark size (8 views of 320x240, 32
+    spp, depth 5) with random Disney materials: 16 pixels sampled across the
+    views, recomputed one by one by the oracle's Disney model with the same
+    key."""
+    sc = scenes.room_60k()
+    p = scenes.disney_materials(sc, 7)
+    tr = Tracer(sc, seed=SEED)
+    tr.configure(integrator)
+    tr.disney_set_params(p)
+    img = tr.disney_render(TraceOptions(max_depth=5), view=-1, set_id=0, spp=32, iteration=3).cpu().numpy()
+    osc = O.OracleScene(sc)
+    rng = np.random.default_rng(9)
+    got, ref = [], []
+    for v in range(len(sc.cameras)):
+        px = rng.choice(320 * 240, 2, replace=False).astype(np.uint32)
+        m, _ = osc.render(p.astype(np.float64), view=v, pixels=px, spp=32, max_depth=5, set_id=0, iteration=3,
+                          seed=SEED, model=O.MODEL_DISNEY)
+        ref.append(m)
+        got.append(img[tr.offsets[v] + px.astype(np.int64)])
+    assert rel(np.concatenate(got), np.concatenate(ref)) <= 1e-3, rel(np.concatenate(got), np.concatenate(ref))
+    tr.close()
+
+
 def test_image_independent_keys_4096spp(built):
     """Independent Philox keys on the two sides: the difference is Monte Carlo
     noise, so at most 0.5% of pixel-channels lie beyond 3 combined standard
