@@ -179,6 +179,7 @@ def recorded_traffic(kernel, cfg, slots_per_launch):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     want = {"kernel": kernel, "bvh_width": str(cfg.get("bvh_width")),
+            "sort_cells": str(cfg.get("sort_cells", 0)), "sort_dirs": str(cfg.get("sort_dirs", 0)),
             "kernel_sources_sha256": kernel_sources_sha256()}
     if want["kernel_sources_sha256"] is None or any(kv.get(k) != v for k, v in want.items()):
         return None
@@ -284,7 +285,7 @@ def run_ours(args, rank, world, local):
         tr.set_params(scenes.initial_params(sc, w["init"]))
     else:
         tr.configure(args.integrator, wavefront_slots=args.slots, trace_steps=args.trace_steps,
-                     bvh_width=args.bvh_width)
+                     bvh_width=args.bvh_width, sort_cells=args.sort_cells, sort_dirs=args.sort_dirs)
     chosen = tr.config()
     shard_iter = [0]
 
@@ -837,6 +838,11 @@ def main():
                     help="profiling only: wavefront path slots per chunk with --integrator wavefront")
     ap.add_argument("--trace-steps", type=int, default=0,
                     help="profiling only: traversal refill point with --integrator wavefront")
+    ap.add_argument("--sort-cells", type=int, default=0,
+                    help="with --integrator wavefront: reorder secondary closest-hit rays by origin cell "
+                         "(cells per axis; 0: queue order)")
+    ap.add_argument("--sort-dirs", type=int, default=0,
+                    help="direction cells per cube-map face side of the reordering (0: origin cells only)")
     args = ap.parse_args()
     if args.workload in WORKLOADS:
         WORKLOAD.clear()

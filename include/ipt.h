@@ -90,7 +90,8 @@ typedef enum {
   IPT_KERNEL_CACHE_RECORDS = 18, /* training-record targets */
   IPT_KERNEL_CACHE_GRAD = 19,    /* training forward + backward */
   IPT_KERNEL_CACHE_ADAM = 20,    /* optimizer step on weights and hash table */
-  IPT_KERNEL_COUNT = 21
+  IPT_KERNEL_WF_SORT = 21,       /* reordering of secondary closest-hit rays */
+  IPT_KERNEL_COUNT = 22
 } ipt_kernel_id;
 
 /* device: CUDA device ordinal.  stream: the cudaStream_t every call queues
@@ -110,7 +111,7 @@ typedef struct {
  *     1 = wavefront (chunks of path slots; persistent traversal kernels over
  *     compacted ray queues).
  *   wavefront_slots: path slots per wavefront chunk (0 = 1 << 20); rounded
- *     down to whole pixels.  The context keeps 156 bytes of device memory
+ *     down to whole pixels.  The context keeps 162 bytes of device memory
  *     per slot, and once it has run an adjoint 52 + 40 D more (D: the
  *     largest max_depth its adjoints have used; the Disney model's adjoint
  *     adds 32 D + 64); the buffers are allocated on first use and grow, never
@@ -126,13 +127,24 @@ typedef struct {
  *     with 8-bit child boxes visited nearest first, 8 = 8-wide nodes with
  *     8-bit child boxes whose children sit in slots by octant and are
  *     visited in the ray's octant order (0 = 4).  All three give the same
- *     closest hits up to exact ties. */
+ *     closest hits up to exact ties.
+ *   sort_cells, sort_dirs: wavefront launches over one scene reorder each
+ *     secondary closest-hit queue (after the first vertex) by bin before
+ *     tracing it: origin cell (sort_cells^3 boxes of the scene's bounding
+ *     box) and direction cell (the cube-map face of the direction's
+ *     dominant axis, split into sort_dirs x sort_dirs squares; 0: the
+ *     origin cell alone).  sort_cells = 0 traces in queue order.  The bins,
+ *     6 sort_dirs^2 sort_cells^3 (sort_cells^3 without directions), must not
+ *     exceed 8192.  The order changes no result.  The context keeps 6
+ *     more bytes of device memory per slot for it. */
 typedef struct {
   int32_t integrator;
   uint32_t wavefront_slots;
   uint32_t trace_steps;
   uint32_t blocks_per_sm;
   uint32_t bvh_width;
+  uint32_t sort_cells;
+  uint32_t sort_dirs;
 } ipt_config;
 
 /* Pinhole camera.  cam_to_world is row-major 3x4; its columns are the

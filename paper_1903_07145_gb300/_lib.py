@@ -39,7 +39,7 @@ IPT_FLAG_KERNEL_TIMING, IPT_FLAG_COUNTERS, IPT_FLAG_OWN_STREAM = 1, 2, 4
 KERNEL_NAMES = ["prepare", "forward", "adjoint", "finalize", "adam", "trace_rays", "philox",
                 "wf_camera", "wf_closest", "wf_shadow", "wf_shade", "wf_adj_a", "wf_adj_connect",
                 "wf_adj_b", "wf_reduce", "batch_step", "cache_infer", "cache_vjp", "cache_records",
-                "cache_grad", "cache_adam"]
+                "cache_grad", "cache_adam", "wf_sort"]
 
 
 class IptError(RuntimeError):
@@ -61,7 +61,7 @@ class ipt_camera(C.Structure):
 class ipt_config(C.Structure):
     _fields_ = [("integrator", C.c_int32), ("wavefront_slots", C.c_uint32),
                 ("trace_steps", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("bvh_width", C.c_uint32)]
+                ("bvh_width", C.c_uint32), ("sort_cells", C.c_uint32), ("sort_dirs", C.c_uint32)]
 
 
 class ipt_trace_opts(C.Structure):
@@ -334,8 +334,9 @@ def ipt_loss_grad_shard(ctx, scene, opts, iteration, pix_begin, pix_count, n_tot
     return loss.value
 
 
-def ipt_config_set(ctx, integrator=1, wavefront_slots=0, trace_steps=0, blocks_per_sm=0, bvh_width=0):
-    c = ipt_config(integrator, wavefront_slots, trace_steps, blocks_per_sm, bvh_width)
+def ipt_config_set(ctx, integrator=1, wavefront_slots=0, trace_steps=0, blocks_per_sm=0, bvh_width=0,
+                   sort_cells=0, sort_dirs=0):
+    c = ipt_config(integrator, wavefront_slots, trace_steps, blocks_per_sm, bvh_width, sort_cells, sort_dirs)
     _check(ctx, lib().ipt_config_set(ctx, C.byref(c)))
 
 
@@ -343,7 +344,8 @@ def ipt_config_get(ctx):
     c = ipt_config()
     _check(ctx, lib().ipt_config_get(ctx, C.byref(c)))
     return dict(integrator=c.integrator, wavefront_slots=c.wavefront_slots,
-                trace_steps=c.trace_steps, blocks_per_sm=c.blocks_per_sm, bvh_width=c.bvh_width)
+                trace_steps=c.trace_steps, blocks_per_sm=c.blocks_per_sm, bvh_width=c.bvh_width,
+                sort_cells=c.sort_cells, sort_dirs=c.sort_dirs)
 
 
 def ipt_batch_create(ctx, scene_ids):

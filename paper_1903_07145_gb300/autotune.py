@@ -4,7 +4,8 @@ Candidates: the megakernel, and the wavefront integrator with the three BVH
 widths (binary, 4-wide sorted by distance, 8-wide in octant order), two chunk
 sizes (2M path slots, and 32M, which holds a whole pass of most workloads in
 one chunk: no drain tail between chunks, fewer launches) and two traversal
-refill granularities.  Each candidate runs one
+refill granularities; with 32M slots and the wide BVHs also the reordering
+of secondary rays by origin and direction cell (6^3 cells x 24 directions).  Each candidate runs one
 loss-and-gradient evaluation of the caller's workload (after one untimed
 run that allocates its buffers); the fastest by CUDA-event time wins and is
 left configured.  Every candidate traces the same paths, so the choice
@@ -20,6 +21,8 @@ DEFAULT_CANDIDATES = (
     [dict(integrator="megakernel")]
     + [dict(integrator="wavefront", wavefront_slots=s, trace_steps=k, bvh_width=b)
        for b, s, k in itertools.product([2, 4, 8], [1 << 21, 1 << 25], [16, 24])]
+    + [dict(integrator="wavefront", wavefront_slots=1 << 25, trace_steps=k, bvh_width=b, sort_cells=6, sort_dirs=2)
+       for b, k in itertools.product([4, 8], [16, 24])]
 )
 
 

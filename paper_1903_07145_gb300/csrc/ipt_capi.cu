@@ -207,6 +207,9 @@ ipt_status ensure_wf(ipt_ctx* ctx, bool adjoint, uint32_t n_params, bool disney,
   A(&w.sh_meta, cap);
   A(&w.sh_c, cap);
   A(&w.sh_vis, cap);
+  A(&w.qs, cap);
+  A(&w.keys, (size_t)cap + 16);  // padded: the sort reads whole groups of 8
+  A(&w.bins, ipt::kSortMaxBins);
   if (want_adj) {
     A(&w.aT, (size_t)keep_depth * cap);
     A(&w.aU, (size_t)keep_depth * cap);
@@ -262,6 +265,8 @@ ipt::WfScene wf_entry(const ipt_ctx* ctx, int32_t scene_id, const DeviceScene* s
   e.n_seg = s->n_seg;
   e.key = make_uint2((uint32_t)(ctx->seed & 0xFFFFFFFFu), (uint32_t)(ctx->seed >> 32) ^ (uint32_t)scene_id);
   e.es = s->emission_scale;
+  e.bb_lo = make_float3(s->bb_lo[0], s->bb_lo[1], s->bb_lo[2]);
+  e.bb_hi = make_float3(s->bb_hi[0], s->bb_hi[1], s->bb_hi[2]);
   return e;
 }
 
@@ -975,6 +980,13 @@ ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg) {
   if (cfg->trace_steps > 4096) return fail(ctx, IPT_ERR_INVALID_ARG, "trace_steps above 4096");
   if (cfg->bvh_width != 0 && cfg->bvh_width != 2 && cfg->bvh_width != 4 && cfg->bvh_width != 8)
     return fail(ctx, IPT_ERR_INVALID_ARG, "bvh_width must be 0, 2, 4 or 8");
+  if (cfg->sort_cells > 16 || cfg->sort_dirs > 16)
+    return fail(ctx, IPT_ERR_INVALID_ARG, "sort_cells and sort_dirs must be at most 16");
+  {
+    const uint64_t d = cfg->sort_dirs, c = cfg->sort_cells;
+    if ((d ? 6u * d * d : 1u) * c * c * c > ipt::kSortMaxBins)
+      return fail(ctx, IPT_ERR_INVALID_ARG, "6 sort_dirs^2 sort_cells^3 above 8192");
+  }
   IPT_CK(cudaSetDevice(ctx->device));
   const uint32_t old_cap = ctx->cfg.wavefront_slots ? ctx->cfg.wavefront_slots : (1u << 20);
   const uint32_t new_cap = cfg->wavefront_slots ? cfg->wavefront_slots : (1u << 20);
@@ -985,6 +997,8 @@ ipt_status ipt_config_set(ipt_ctx* ctx, const ipt_config* cfg) {
   ctx->cfg = *cfg;
   ctx->L.wf_steps = cfg->trace_steps ? (int)cfg->trace_steps : 16;
   ctx->L.wf_fixed_blocks = (int)cfg->blocks_per_sm;
+  ctx->L.sort_cells = (int)cfg->sort_cells;
+  ctx->L.sort_dirs = (int)cfg->sort_dirs;
   IPT_CK(ipt::wf_init(&ctx->L));
   return IPT_OK;
 }

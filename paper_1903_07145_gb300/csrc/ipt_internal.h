@@ -95,6 +95,8 @@ struct Launcher {
   int wf_fixed_blocks = 0;   // configured blocks per SM for every wavefront kernel (0: by occupancy)
   int wf_max_rows = 0;       // gradient rows any adjoint stage may use (blocks of its widest grid)
   int wf_steps = 16;  // refill point of the persistent traversal (idle lanes; binary BVH: steps)
+  int sort_cells = 0; // secondary closest-hit rays reordered by origin cell (cells per axis; 0: off)
+  int sort_dirs = 0;  //   and direction (divisions of each cube-map face side; 0: none)
 };
 
 // Wavefront state (device), sized for `cap` path slots per chunk.
@@ -113,12 +115,18 @@ struct WfBuffers {
   // records' material derivatives (4 float4 = 13 values per record)
   float4 *aWi = nullptr, *aWo = nullptr, *sh_dv = nullptr;
   float* blk = nullptr;
+  // reordering of secondary closest-hit rays: the queue's slots by bin, the
+  // bin of each queue entry, and per-bin counts / offsets
+  uint32_t* qs = nullptr;
+  uint16_t* keys = nullptr;
+  uint32_t* bins = nullptr;
   uint32_t cap = 0;
   uint32_t blk_params = 0;  // S x 10 capacity of each block row
   uint32_t depth_cap = 0;   // vertices the per-vertex carry holds (adjoint max_depth)
 };
 
 constexpr int kMaxAdjointDepth = 8;
+constexpr uint32_t kSortMaxBins = 8192;  // bins of the ray reordering (6 dirs^2 cells^3 at most)
 constexpr int kMaxForwardDepth = 64;
 constexpr int kBlockThreads = 128;
 

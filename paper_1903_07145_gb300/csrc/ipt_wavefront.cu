@@ -74,6 +74,13 @@ struct WfDev {
   uint32_t cap;
 };
 
+// Bin grid of the reordering of secondary closest-hit rays (see ray_bin).
+struct BinGrid {
+  float3 lo, scale;  // origin cell along an axis: (o - lo) * scale
+  int cells, dirs;
+  uint32_t n_bins;   // 6 dirs^2 cells^3 (cells^3 for dirs = 0)
+};
+
 // Per-launch constants.
 struct WfParams {
   uint32_t set;
@@ -86,6 +93,8 @@ struct WfParams {
   uint32_t n_scenes;
   uint32_t seg_lo, seg_n;    // segment range of the chunk's gradient accumulators
   float* gacc;               // accumulators in global memory (chunks too wide for shared memory), or nullptr
+  BinGrid bin;               // reordering: bin grid of the rays appended to the next closest-hit queue
+  uint16_t* keys;            //   and their bins, by queue position (nullptr: no reordering)
   uint32_t cache_k;          // vertex where the radiance cache ends paths (kNoCache: off)
   int cache_record;          // training pass: record at cache_k, gather only from there on
   CacheBuffers cb;
@@ -171,6 +180,186 @@ __global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfPa
     w.rad[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     w.q0[slot] = slot;
     if (w.nv) w.nv[slot] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reordering of a closest-hit queue (secondary rays): a counting sort of its
+// entries by bin, bin = (direction cell, origin cell).  The direction cell is
+// the cube-map face of the dominant axis and sign, split into dirs x dirs
+// squares (dirs = 0: one cell for all directions); the origin cell one of
+// cells^3 boxes of the scene's bounding box.  Only the order in which the
+// traversal takes the rays changes: each ray's result is the same.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 1024;
+
+
+__device__ __forceinline__ uint32_t ray_bin(const BinGrid& g, float3 o, float3 d) {
+  const int c = g.cells;
+  const int cx = min(max((int)((o.x - g.lo.x) * g.scale.x), 0), c - 1);
+  const int cy = min(max((int)((o.y - g.lo.y) * g.scale.y), 0), c - 1);
+  const int cz = min(max((int)((o.z - g.lo.z) * g.scale.z), 0), c - 1);
+  const uint32_t cell = (uint32_t)((cz * c + cy) * c + cx);
+  if (g.dirs == 0) return cell;
+  const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  int face;
+  float u, v, m;
+  if (ax >= ay && ax >= az) {
+    face = d.x < 0.0f ? 1 : 0;
+    u = d.y;
+    v = d.z;
+    m = ax;
+  } else if (ay >= az) {
+    face = d.y < 0.0f ? 3 : 2;
+    u = d.x;
+    v = d.z;
+    m = ay;
+  } else {
+    face = d.z < 0.0f ? 5 : 4;
+    u = d.x;
+    v = d.y;
+    m = az;
+  }
+  // (u / m + 1) / 2 in [0, 1] on the face, in dirs squares
+  const float k = 0.5f * (float)g.dirs / fmaxf(m, 1e-30f);
+  const int iu = min(max((int)((u + m) * k), 0), g.dirs - 1);
+  const int iv = min(max((int)((v + m) * k), 0), g.dirs - 1);
+  const uint32_t dir = (uint32_t)((face * g.dirs + iu) * g.dirs + iv);
+  return dir * (uint32_t)(c * c * c) + cell;
+}
+
+// The sort kernels take the queue in groups of 8 entries per thread (one
+// 16-byte load of their bins; the key array is padded to whole groups).
+// Neighbouring entries mostly share a bin, so each thread adds a run of equal
+// bins with one shared atomic.
+__device__ __forceinline__ void load_bins8(const uint16_t* keys, uint32_t g, uint32_t k[8]) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(keys) + g);
+  k[0] = v.x & 0xffffu, k[1] = v.x >> 16, k[2] = v.y & 0xffffu, k[3] = v.y >> 16;
+  k[4] = v.z & 0xffffu, k[5] = v.z >> 16, k[6] = v.w & 0xffffu, k[7] = v.w >> 16;
+}
+
+// Adds the first m (1..8) of the group's 8 bins to h, one atomic per run.
+__device__ __forceinline__ void count_bins8(uint32_t* h, const uint32_t k[8], uint32_t m) {
+  uint32_t run = 1u, last = k[0];
+#pragma unroll
+  for (uint32_t j = 1; j < 8; ++j) {
+    if (j >= m) break;
+    if (k[j] == last) {
+      ++run;
+    } else {
+      atomicAdd(&h[last], run);
+      last = k[j];
+      run = 1u;
+    }
+  }
+  atomicAdd(&h[last], run);
+}
+
+// Counts of the bins of queue `cur`'s entries (their bins written by the
+// stage that appended them), added to `bins` (cleared before).
+__global__ void __launch_bounds__(kSortThreads) wf_bin_count(uint32_t n_bins, WfDev w, int cur,
+                                                            const uint16_t* keys, uint32_t* bins) {
+  extern __shared__ uint32_t h[];
+  for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const uint32_t n = w.cnt[cur];
+  const uint32_t ng = (n + 7u) / 8u;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    uint32_t k[8];
+    load_bins8(keys, g, k);
+    count_bins8(h, k, min(8u, n - 8u * g));
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x)
+    if (h[i]) atomicAdd(&bins[i], h[i]);
+}
+
+// Counts -> exclusive offsets, in place (one block of kSortThreads threads,
+// at most 8 bins each).
+__global__ void __launch_bounds__(kSortThreads) wf_bin_scan(uint32_t* bins, uint32_t n_bins) {
+  __shared__ uint32_t ws[kSortThreads / 32];
+  const uint32_t per = (n_bins + kSortThreads - 1) / kSortThreads;
+  const uint32_t b0 = threadIdx.x * per;
+  uint32_t v[8];
+  uint32_t sum = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < 8; ++k) {
+    v[k] = (k < per && b0 + k < n_bins) ? bins[b0 + k] : 0u;
+    sum += v[k];
+  }
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t x = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= (uint32_t)off) x += y;
+  }
+  if (lane == 31u) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = ws[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, off);
+      if (lane >= (uint32_t)off) t += y;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  uint32_t run = x - sum + (warp ? ws[warp - 1] : 0u);
+#pragma unroll
+  for (uint32_t k = 0; k < 8; ++k) {
+    if (k < per && b0 + k < n_bins) bins[b0 + k] = run;
+    run += v[k];
+  }
+}
+
+// Each block takes a contiguous part of the queue (rays of neighbouring
+// pixels stay together within a bin), reserves its share of every bin with
+// one atomic and writes its slots there, a run of equal bins at a time.
+__global__ void __launch_bounds__(kSortThreads) wf_bin_scatter(uint32_t n_bins, WfDev w, int cur,
+                                                              const uint16_t* keys, uint32_t* bins,
+                                                              uint32_t* order) {
+  extern __shared__ uint32_t h[];
+  for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const uint32_t n = w.cnt[cur];
+  const uint32_t ng = (n + 7u) / 8u;
+  const uint32_t per = (ng + gridDim.x - 1u) / gridDim.x;
+  const uint32_t lo = min(ng, blockIdx.x * per), hi = min(ng, lo + per);
+  for (uint32_t g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+    uint32_t k[8];
+    load_bins8(keys, g, k);
+    count_bins8(h, k, min(8u, n - 8u * g));
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x) {
+    const uint32_t c = h[i];
+    if (c) h[i] = atomicAdd(&bins[i], c);
+  }
+  __syncthreads();
+  const uint32_t* qin = queue(w, cur);
+  for (uint32_t g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+    uint32_t k[8], slot[8];
+    load_bins8(keys, g, k);
+    const uint32_t m = min(8u, n - 8u * g);
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) slot[j] = j < m ? qin[8u * g + j] : 0u;
+    uint32_t pos = 0u;
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+      if (j >= m) break;
+      if (j == 0 || k[j] != k[j - 1]) {  // a run starts: reserve its places
+        uint32_t len = 1u;
+#pragma unroll
+        for (uint32_t t = j + 1; t < 8; ++t) {
+          if (t >= m || k[t] != k[j]) break;
+          ++len;
+        }
+        pos = atomicAdd(&h[k[j]], len);
+      }
+      order[pos++] = slot[j];
+    }
   }
 }
 
@@ -452,11 +641,11 @@ __device__ __forceinline__ bool node_step8(const SceneDev& s, Trav& T, uint2* sh
 // light contribution (forward shadow rays) or the visibility flag (adjoint
 // shadow rays).
 template <int kMode>
-__device__ __forceinline__ void trace_finish(const WfDev& w, int cur, uint32_t i, const Trav& T,
+__device__ __forceinline__ void trace_finish(const WfDev& w, const uint32_t* qsrc, uint32_t i, const Trav& T,
                                              const SceneDev& sd) {
   count_ray(sd, kMode != 0 ? 1 : 0, T.n_nodes, T.n_tests);
   if (kMode == 0) {
-    const uint32_t slot = queue(w, cur)[i];
+    const uint32_t slot = qsrc[i];
     w.hit[slot] = make_float4(__int_as_float(T.best), T.bt, T.bu, T.bv);
   } else if (kMode == 1) {
     if (!T.occluded) {
@@ -486,9 +675,11 @@ __device__ __forceinline__ void trace_finish(const WfDev& w, int cur, uint32_t i
 //    (with one or two lanes active).
 //  * Binary BVH: rounds of `steps` node visits, whole leaves at a time, and a
 //    refetch after each round.
+// Closest hit takes queue `cur`'s slots in the order of `order` when given
+// (the same slots reordered by bin), else in queue order.
 template <int kMode, int kWidth>
 __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, WfDev w, int cur, int steps,
-                                                       int one_scene, uint32_t* err) {
+                                                       int one_scene, const uint32_t* order, uint32_t* err) {
   constexpr bool kAny = kMode != 0;
   if (!kAny && blockIdx.x == 0 && threadIdx.x == 0) {
     w.cnt[cur ? 0 : 1] = 0;  // next queue, filled by the shading stage
@@ -496,6 +687,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
     w.cnt[4] = 0;            // shadow fetch counter
   }
   const uint32_t n = kAny ? w.cnt[2] : w.cnt[cur];
+  const uint32_t* qsrc = order ? order : queue(w, cur);
   uint32_t* fetch = kAny ? &w.cnt[4] : &w.cnt[3];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -509,7 +701,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
   bool drained = false;  // warp-uniform: the queue has no rays left
   for (;;) {
     if (fin) {  // results are stored at the refill, by all ended lanes together
-      trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
+      trace_finish<kMode>(w, qsrc, (uint32_t)item, T, sd);
       item = -1;
       fin = false;
     }
@@ -525,7 +717,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
       if (need && i < n) {
         item = i;
         // a launch over one scene skips the lookup of the ray's scene
-        const uint32_t slot = kAny ? w.sh_meta[i].x : queue(w, cur)[i];
+        const uint32_t slot = kAny ? w.sh_meta[i].x : qsrc[i];
         if (!one_scene) sd = tab[state_scene(__float_as_uint(w.beta[slot].w))].s;
         if (kAny) {
           const float4 o = w.sh_o[i], d = w.sh_d[i];
@@ -539,7 +731,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_trace(const WfScene* tab, Wf
     if (__all_sync(0xffffffffu, item < 0)) break;
     if constexpr (kWidth == 2) {
       if (item >= 0 && trav_run2<kAny>(sd, T, sh, steps, err)) {
-        trace_finish<kMode>(w, cur, (uint32_t)item, T, sd);
+        trace_finish<kMode>(w, qsrc, (uint32_t)item, T, sd);
         item = -1;
       }
     } else {
@@ -698,6 +890,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_shade_fwd(const WfScene* tab
     const uint32_t ci = enqueue(nout, cont);
     if (cont) {
       qout[ci] = slot;
+      if (lp.keys) lp.keys[ci] = (uint16_t)ray_bin(lp.bin, org, wo);
       w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
       w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
       w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
@@ -1267,6 +1460,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
     const uint32_t ci = enqueue(nout, cont);
     if (cont) {
       qout[ci] = slot;
+      if (lp.keys) lp.keys[ci] = (uint16_t)ray_bin(lp.bin, org, wo);
       w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
       w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
       w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
@@ -1441,6 +1635,8 @@ static WfParams wf_params(const TraceParams& tp, int loss_kind, uint32_t n_scene
   p.cache_k = kNoCache;
   p.cache_record = 0;
   p.cb = CacheBuffers{};
+  p.bin = BinGrid{};
+  p.keys = nullptr;
   return p;
 }
 
@@ -1469,14 +1665,47 @@ static int table_width(const std::vector<WfScene>& tab) {
 // One launch of traversal mode kMode over the table's BVH width.
 template <int kMode>
 static void launch_trace(int width, int grid, const WfScene* tab_dev, int n_scenes, const WfDev& w, int cur,
-                         int steps, uint32_t* err, cudaStream_t st) {
+                         int steps, uint32_t* err, cudaStream_t st, const uint32_t* order = nullptr) {
   const int one = n_scenes == 1 ? 1 : 0;
   if (width == 8)
-    wf_trace<kMode, 8><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, err);
+    wf_trace<kMode, 8><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, order, err);
   else if (width == 4)
-    wf_trace<kMode, 4><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, err);
+    wf_trace<kMode, 4><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, order, err);
   else
-    wf_trace<kMode, 2><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, err);
+    wf_trace<kMode, 2><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, order, err);
+}
+
+// Secondary closest-hit rays are reordered in launches over one scene when
+// the launcher asks for it: sets the launch's bin grid and key array (the
+// shading and adjoint stages then write each appended ray's bin).
+static void sort_setup(const Launcher& L, const std::vector<WfScene>& tab, const WfBuffers& wb, WfParams& lp) {
+  lp.keys = nullptr;
+  lp.bin = BinGrid{};
+  if (L.sort_cells <= 0 || tab.size() != 1 || !wb.qs || !wb.keys || !wb.bins) return;
+  BinGrid g;
+  g.cells = L.sort_cells;
+  g.dirs = L.sort_dirs;
+  g.n_bins = (g.dirs ? 6u * (uint32_t)(g.dirs * g.dirs) : 1u) * (uint32_t)(g.cells * g.cells * g.cells);
+  if (g.n_bins > kSortMaxBins) return;
+  const WfScene& e = tab[0];
+  const float ex = e.bb_hi.x - e.bb_lo.x, ey = e.bb_hi.y - e.bb_lo.y, ez = e.bb_hi.z - e.bb_lo.z;
+  g.lo = e.bb_lo;
+  g.scale = make_float3(ex > 0.f ? g.cells / ex : 0.f, ey > 0.f ? g.cells / ey : 0.f, ez > 0.f ? g.cells / ez : 0.f);
+  lp.bin = g;
+  lp.keys = wb.keys;
+}
+
+// Reorders queue `cur` by the bins its entries were given; returns the order
+// the closest-hit traversal takes.
+static const uint32_t* sort_queue(const Launcher& L, const WfParams& lp, const WfBuffers& wb, const WfDev& w,
+                                  int cur, cudaStream_t st) {
+  const uint32_t nb = lp.bin.n_bins;
+  const size_t sm = nb * sizeof(uint32_t);
+  if (cudaMemsetAsync(wb.bins, 0, sm, st) != cudaSuccess) return nullptr;
+  wf_bin_count<<<2 * L.num_sms, kSortThreads, sm, st>>>(nb, w, cur, wb.keys, wb.bins);
+  wf_bin_scan<<<1, kSortThreads, 0, st>>>(wb.bins, nb);
+  wf_bin_scatter<<<2 * L.num_sms, kSortThreads, sm, st>>>(nb, w, cur, wb.keys, wb.bins, wb.qs);
+  return wb.qs;
 }
 
 // Chunks of at most cap / spp pixels; an adjoint chunk also ends before a
@@ -1517,6 +1746,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
   const uint32_t ns = (uint32_t)tab.size();
   if (disney && cache) return cudaErrorInvalidValue;
   WfParams lp = wf_params(tp, loss_kind, ns, iter_dev);
+  sort_setup(L, tab, wb, lp);
   wf_cache_params(lp, cache, tp.max_depth);
   const bool query = lp.cache_k != kNoCache && !lp.cache_record;
   const bool record = lp.cache_k != kNoCache && lp.cache_record;
@@ -1540,9 +1770,14 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
     }
     int cur = 0;
     for (uint32_t k = 0; k <= last_k; ++k) {
+      const uint32_t* order = nullptr;
+      if (k > 0 && lp.keys) {  // the camera rays (k = 0) are coherent already
+        IPT_STAGE(21);
+        order = sort_queue(L, lp, wb, w, cur, st);
+      }
       {
         IPT_STAGE(8);
-        launch_trace<0>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st);
+        launch_trace<0>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st, order);
       }
       {
         IPT_STAGE(10);
@@ -1605,6 +1840,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
   const uint32_t max_seg = kD ? wf_max_segments() * 10u / 16u : wf_max_segments();
   const uint32_t ns = (uint32_t)tab.size();
   WfParams lp = wf_params(tp, 0, ns, iter_dev);
+  sort_setup(L, tab, wb, lp);
   if (cache && cache->record) return cudaErrorInvalidValue;
   if (kD && (!wb.aWi || !wb.aWo || !wb.sh_dv)) return cudaErrorInvalidValue;
   wf_cache_params(lp, cache, tp.max_depth);
@@ -1655,9 +1891,14 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
     }
     int cur = 0;
     for (uint32_t k = 0; k <= last_k; ++k) {
+      const uint32_t* order = nullptr;
+      if (k > 0 && lp.keys) {  // the camera rays (k = 0) are coherent already
+        IPT_STAGE(21);
+        order = sort_queue(L, lp, wb, w, cur, st);
+      }
       {
         IPT_STAGE(8);
-        launch_trace<0>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st);
+        launch_trace<0>(width, grid, tab_dev, (int)tab.size(), w, cur, L.wf_steps, err, st, order);
       }
       {
         IPT_STAGE(11);

@@ -260,11 +260,11 @@ class Tracer:
         return L.ipt_scene_info(self.ctx, self.sid)
 
     def configure(self, integrator="wavefront", wavefront_slots=0, trace_steps=0, blocks_per_sm=0,
-                  bvh_width=0):
+                  bvh_width=0, sort_cells=0, sort_dirs=0):
         if isinstance(integrator, int):
             integrator = "wavefront" if integrator == 1 else "megakernel"
         L.ipt_config_set(self.ctx, 1 if integrator == "wavefront" else 0, wavefront_slots,
-                         trace_steps, blocks_per_sm, bvh_width)
+                         trace_steps, blocks_per_sm, bvh_width, sort_cells, sort_dirs)
 
     def config(self):
         return L.ipt_config_get(self.ctx)

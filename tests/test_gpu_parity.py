@@ -568,6 +568,41 @@ def test_refill_points_give_the_same_results(built, bvh_width):
         assert rel(g, out[0][1]) <= 1e-5
 
 
+@pytest.mark.parametrize("bvh_width", [4, 8])
+def test_ray_reordering_gives_the_same_results(built, bvh_width):
+    """Reordering the secondary closest-hit queues by origin and direction
+    cell only changes the order in which the traversal takes the rays: images
+    and gradients equal those traced in queue order (gradients up to the
+    order of the float sums), for coarse and fine bin grids, with chunks that
+    end inside a view."""
+    sc = scenes.indoor_room(17, n_cuboids=10, cuboid_sub=3, room_sub=4, n_lights=3, n_views=2,
+                            width=40, height=30)
+    p = perturbed(sc, emission=0.05)
+    opts = TraceOptions(spp_r=8, spp_d=8, max_depth=5)
+    w = torch.from_numpy(np.random.default_rng(2).normal(size=(2 * 40 * 30, 3)).astype(np.float32)).cuda()
+    out = []
+    for cells, dirs in ((0, 0), (1, 1), (4, 2), (4, 4), (2, 8), (16, 0)):
+        tr = Tracer(sc, seed=SEED)
+        tr.configure("wavefront", wavefront_slots=4096, bvh_width=bvh_width, sort_cells=cells, sort_dirs=dirs)
+        assert tr.config()["sort_cells"] == cells
+        tr.set_params(p)
+        out.append((tr.render(opts, set_id=0, spp=8).cpu().numpy(), tr.backward(w, opts, set_id=1).cpu().numpy()))
+        tr.close()
+    for img, g in out[1:]:
+        assert np.array_equal(img, out[0][0])
+        assert rel(g, out[0][1]) <= 1e-5
+
+
+def test_ray_reordering_rejects_too_many_bins(built):
+    sc = scenes.cornell_box(1000, 16, 16)
+    tr = Tracer(sc, seed=SEED)
+    for cells, dirs in ((8, 2), (17, 0), (1, 17)):
+        with pytest.raises(_lib.IptError):
+            tr.configure("wavefront", sort_cells=cells, sort_dirs=dirs)
+    tr.configure("wavefront", sort_cells=8, sort_dirs=1)
+    tr.close()
+
+
 def test_kernels_run_from_an_sm103a_binary(built):
     """The device loads the library's kernels from the sm_103a cubin, not a
     JIT-compiled PTX fallback."""
