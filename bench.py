@@ -178,7 +178,7 @@ def recorded_traffic(kernel, cfg, slots_per_launch):
         if ":" in line and not line.lstrip().startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    want = {"kernel": kernel, "bvh_width": str(cfg.get("bvh_width")),
+    want = {"kernel": kernel, "workload": WORKLOAD["workload"], "bvh_width": str(cfg.get("bvh_width")),
             "sort_cells": str(cfg.get("sort_cells", 0)), "sort_dirs": str(cfg.get("sort_dirs", 0)),
             "kernel_sources_sha256": kernel_sources_sha256()}
     if want["kernel_sources_sha256"] is None or any(kv.get(k) != v for k, v in want.items()):
