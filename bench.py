@@ -702,7 +702,8 @@ def run_disney(args):
     for timing in (False, True):
         tr = Tracer(sc, seed=1903, flags=L.IPT_FLAG_KERNEL_TIMING if timing else 0)
         if integ == "wavefront":  # the configuration the autotuner picks for this room
-            tr.configure("wavefront", wavefront_slots=1 << 25, trace_steps=16, bvh_width=4)
+            tr.configure("wavefront", wavefront_slots=1 << 25, trace_steps=24, bvh_width=4, sort_cells=6,
+                         sort_dirs=2)
         else:
             tr.configure("megakernel")
         tr.disney_set_params(truth)
