@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfPa
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 1024;
 
-
+// Bin of the ray from o in direction d (any length): direction cell major,
+// origin cell minor; always below g.n_bins.
 __device__ __forceinline__ uint32_t ray_bin(const BinGrid& g, float3 o, float3 d) {
   const int c = g.cells;
   const int cx = min(max((int)((o.x - g.lo.x) * g.scale.x), 0), c - 1);
@@ -230,8 +231,8 @@ __device__ __forceinline__ uint32_t ray_bin(const BinGrid& g, float3 o, float3 d
 
 // The sort kernels take the queue in groups of 8 entries per thread (one
 // 16-byte load of their bins; the key array is padded to whole groups).
-// Neighbouring entries mostly share a bin, so each thread adds a run of equal
-// bins with one shared atomic.
+// Neighbouring entries (samples of one pixel) often share a bin, so each
+// thread adds a run of equal bins with one shared atomic.
 __device__ __forceinline__ void load_bins8(const uint16_t* keys, uint32_t g, uint32_t k[8]) {
   const uint4 v = __ldg(reinterpret_cast<const uint4*>(keys) + g);
   k[0] = v.x & 0xffffu, k[1] = v.x >> 16, k[2] = v.y & 0xffffu, k[3] = v.y >> 16;
