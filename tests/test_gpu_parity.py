@@ -593,6 +593,51 @@ def test_ray_reordering_gives_the_same_results(built, bvh_width):
         assert rel(g, out[0][1]) <= 1e-5
 
 
+@pytest.mark.parametrize("path", ["disney", "pixel_batch", "cache"])
+def test_ray_reordering_other_paths(built, path):
+    """The reordering under the Disney model's loss and gradient, under
+    stochastic pixel batches and with the radiance cache ending paths: the
+    same results as queue order (gradients up to the order of the float
+    sums)."""
+    from paper_1903_07145_gb300.tracer import CacheOptions
+    sc = scenes.indoor_room(23, n_cuboids=8, cuboid_sub=3, room_sub=4, n_lights=2, n_views=2,
+                            width=40, height=30)
+    p = perturbed(sc, emission=0.05)
+    out = []
+    for cells in (0, 6):
+        tr = Tracer(sc, seed=SEED)
+        tr.configure("wavefront", wavefront_slots=8192, sort_cells=cells, sort_dirs=2 if cells else 0)
+        if path == "disney":
+            dp = scenes.disney_materials(sc, 5)
+            tr.disney_set_params(dp)
+            tr.set_targets(tr.disney_render(TraceOptions(max_depth=4), set_id=_lib.IPT_SET_TARGET, spp=16))
+            dp[:, 0:3] = 0.5
+            tr.disney_set_params(dp)
+            loss, g = tr.disney_loss_grad(TraceOptions(spp_r=8, spp_d=8, max_depth=4), iteration=2)
+            out.append((loss, g.cpu().numpy(), None))
+        elif path == "pixel_batch":
+            tr.set_params(sc.gt_params)
+            tr.set_targets(tr.render(TraceOptions(max_depth=4), set_id=_lib.IPT_SET_TARGET, spp=16))
+            tr.set_params(p)
+            loss, g = tr.loss_grad(TraceOptions(spp_r=16, spp_d=2, max_depth=4, pixel_batch=256), iteration=3)
+            out.append((loss, g.cpu().numpy(), None))
+        else:
+            tr.configure_cache(CacheOptions(enabled=True, b_term=1))
+            rng = np.random.default_rng(8)  # a random network, so the cache's term is not zero
+            tr.set_cache_weights(rng.normal(0.0, 0.2, _lib.IPT_CACHE_WEIGHTS).astype(np.float32),
+                                 rng.normal(0.0, 0.5, _lib.IPT_CACHE_TABLE_FLOATS).astype(np.float32))
+            tr.set_params(p)
+            img = tr.render(TraceOptions(spp_r=8, max_depth=4), view=-1, set_id=0, spp=8).cpu().numpy()
+            out.append((0.0, None, img))
+        tr.close()
+    (l0, g0, i0), (l1, g1, i1) = out
+    if i0 is not None:
+        assert np.array_equal(i0, i1)
+    else:
+        assert abs(l1 - l0) <= 1e-6 * abs(l0), (l0, l1)
+        assert rel(g1, g0) <= 1e-5, rel(g1, g0)
+
+
 def test_ray_reordering_rejects_too_many_bins(built):
     sc = scenes.cornell_box(1000, 16, 16)
     tr = Tracer(sc, seed=SEED)
