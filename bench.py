@@ -491,7 +491,8 @@ def run_batch64(args):
                         pixel_batch=args.pixel_batch)
     ss = SceneSet(rooms, seed=1903)
     integ = "wavefront" if args.batch_integrator == "auto" else args.batch_integrator
-    ss.configure(integrator=integ, wavefront_slots=1 << 25, bvh_width=4)
+    ss.configure(integrator=integ, wavefront_slots=1 << 25, bvh_width=4, sort_cells=args.sort_cells,
+                 sort_dirs=args.sort_dirs)
     for i, sc in enumerate(rooms):
         ss.set_params(i, sc.gt_params)
         ss.set_targets(i, ss.render(i, TraceOptions(max_depth=args.batch_depth), spp=16))

@@ -128,14 +128,16 @@ typedef struct {
  *     8-bit child boxes whose children sit in slots by octant and are
  *     visited in the ray's octant order (0 = 4).  All three give the same
  *     closest hits up to exact ties.
- *   sort_cells, sort_dirs: wavefront launches over one scene reorder each
- *     secondary closest-hit queue (after the first vertex) by bin before
- *     tracing it: origin cell (sort_cells^3 boxes of the scene's bounding
- *     box) and direction cell (the cube-map face of the direction's
- *     dominant axis, split into sort_dirs x sort_dirs squares; 0: the
- *     origin cell alone).  sort_cells = 0 traces in queue order.  The bins,
+ *   sort_cells, sort_dirs: wavefront launches reorder each secondary
+ *     closest-hit queue (after the first vertex) by bin before tracing it:
+ *     origin cell (sort_cells^3 boxes of the ray's scene's bounding box)
+ *     and direction cell (the cube-map face of the direction's dominant
+ *     axis, split into sort_dirs x sort_dirs squares; 0: the origin cell
+ *     alone).  sort_cells = 0 traces in queue order.  The bins of one scene,
  *     6 sort_dirs^2 sort_cells^3 (sort_cells^3 without directions), must not
- *     exceed 8192.  The order changes no result.  The context keeps 6
+ *     exceed 8192; a chunk of a batch keeps its scenes' bins apart and
+ *     coarsens the grid (fewer cells, then fewer directions) until they fit
+ *     8192 together.  The order changes no result.  The context keeps 6
  *     more bytes of device memory per slot for it. */
 typedef struct {
   int32_t integrator;

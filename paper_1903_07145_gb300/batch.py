@@ -53,9 +53,9 @@ class SceneSet:
             pass
 
     def configure(self, integrator="wavefront", wavefront_slots=0, trace_steps=0, blocks_per_sm=0,
-                  bvh_width=0):
+                  bvh_width=0, sort_cells=0, sort_dirs=0):
         L.ipt_config_set(self.ctx, 1 if integrator == "wavefront" else 0, wavefront_slots, trace_steps,
-                         blocks_per_sm, bvh_width)
+                         blocks_per_sm, bvh_width, sort_cells, sort_dirs)
 
     def set_params(self, i, params, free_mask=None):
         p = np.ascontiguousarray(np.asarray(params, np.float32).reshape(-1, 10))

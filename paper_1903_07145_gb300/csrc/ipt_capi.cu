@@ -266,7 +266,8 @@ ipt::WfScene wf_entry(const ipt_ctx* ctx, int32_t scene_id, const DeviceScene* s
   e.key = make_uint2((uint32_t)(ctx->seed & 0xFFFFFFFFu), (uint32_t)(ctx->seed >> 32) ^ (uint32_t)scene_id);
   e.es = s->emission_scale;
   e.bb_lo = make_float3(s->bb_lo[0], s->bb_lo[1], s->bb_lo[2]);
-  e.bb_hi = make_float3(s->bb_hi[0], s->bb_hi[1], s->bb_hi[2]);
+  const float ex = s->bb_hi[0] - s->bb_lo[0], ey = s->bb_hi[1] - s->bb_lo[1], ez = s->bb_hi[2] - s->bb_lo[2];
+  e.bb_inv = make_float3(ex > 0.f ? 1.f / ex : 0.f, ey > 0.f ? 1.f / ey : 0.f, ez > 0.f ? 1.f / ez : 0.f);
   return e;
 }
 

@@ -76,9 +76,10 @@ struct WfDev {
 
 // Bin grid of the reordering of secondary closest-hit rays (see ray_bin).
 struct BinGrid {
-  float3 lo, scale;  // origin cell along an axis: (o - lo) * scale
-  int cells, dirs;
-  uint32_t n_bins;   // 6 dirs^2 cells^3 (cells^3 for dirs = 0)
+  int cells, dirs;     // origin cells per axis of a scene's box; direction cells per cube-map face side
+  uint32_t per_scene;  // bins per scene: 6 dirs^2 cells^3 (cells^3 for dirs = 0)
+  uint32_t scene0;     // first scene of the chunk (its scenes' bins follow one another)
+  uint32_t n_bins;     // per_scene x the chunk's scenes
 };
 
 // Per-launch constants.
@@ -193,15 +194,18 @@ __global__ void __launch_bounds__(kWfThreads) wf_camera(const WfScene* tab, WfPa
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 1024;
 
-// Bin of the ray from o in direction d (any length): direction cell major,
-// origin cell minor; always below g.n_bins.
-__device__ __forceinline__ uint32_t ray_bin(const BinGrid& g, float3 o, float3 d) {
+// Bin of the ray from o in direction d (any length) of scene b (table entry
+// e): scene major, then direction cell, then origin cell in the scene's
+// bounding box; always below g.n_bins for the chunk's scenes.
+__device__ __forceinline__ uint32_t ray_bin(const BinGrid& g, const WfScene& e, uint32_t b, float3 o, float3 d) {
   const int c = g.cells;
-  const int cx = min(max((int)((o.x - g.lo.x) * g.scale.x), 0), c - 1);
-  const int cy = min(max((int)((o.y - g.lo.y) * g.scale.y), 0), c - 1);
-  const int cz = min(max((int)((o.z - g.lo.z) * g.scale.z), 0), c - 1);
+  const float fc = (float)c;
+  const int cx = min(max((int)((o.x - e.bb_lo.x) * (e.bb_inv.x * fc)), 0), c - 1);
+  const int cy = min(max((int)((o.y - e.bb_lo.y) * (e.bb_inv.y * fc)), 0), c - 1);
+  const int cz = min(max((int)((o.z - e.bb_lo.z) * (e.bb_inv.z * fc)), 0), c - 1);
   const uint32_t cell = (uint32_t)((cz * c + cy) * c + cx);
-  if (g.dirs == 0) return cell;
+  const uint32_t base = (b - g.scene0) * g.per_scene;
+  if (g.dirs == 0) return base + cell;
   const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
   int face;
   float u, v, m;
@@ -226,7 +230,7 @@ __device__ __forceinline__ uint32_t ray_bin(const BinGrid& g, float3 o, float3 d
   const int iu = min(max((int)((u + m) * k), 0), g.dirs - 1);
   const int iv = min(max((int)((v + m) * k), 0), g.dirs - 1);
   const uint32_t dir = (uint32_t)((face * g.dirs + iu) * g.dirs + iv);
-  return dir * (uint32_t)(c * c * c) + cell;
+  return base + dir * (uint32_t)(c * c * c) + cell;
 }
 
 // The sort kernels take the queue in groups of 8 entries per thread (one
@@ -891,7 +895,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_shade_fwd(const WfScene* tab
     const uint32_t ci = enqueue(nout, cont);
     if (cont) {
       qout[ci] = slot;
-      if (lp.keys) lp.keys[ci] = (uint16_t)ray_bin(lp.bin, org, wo);
+      if (lp.keys) lp.keys[ci] = (uint16_t)ray_bin(lp.bin, tab[lp.n_scenes == 1 ? 0u : b], b, org, wo);
       w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
       w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
       w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
@@ -1461,7 +1465,7 @@ __global__ void __launch_bounds__(kWfThreads, 8) wf_adj_b(const WfScene* tab, Wf
     const uint32_t ci = enqueue(nout, cont);
     if (cont) {
       qout[ci] = slot;
-      if (lp.keys) lp.keys[ci] = (uint16_t)ray_bin(lp.bin, org, wo);
+      if (lp.keys) lp.keys[ci] = (uint16_t)ray_bin(lp.bin, tab[lp.n_scenes == 1 ? 0u : b], b, org, wo);
       w.ray_o[slot] = make_float4(org.x, org.y, org.z, __int_as_float(tri));
       w.ray_d[slot] = make_float4(wo.x, wo.y, wo.z, pdf);
       w.beta[slot] = make_float4(beta.x, beta.y, beta.z, __uint_as_float(pack_state(k + 1, b)));
@@ -1676,22 +1680,37 @@ static void launch_trace(int width, int grid, const WfScene* tab_dev, int n_scen
     wf_trace<kMode, 2><<<grid, kWfThreads, 0, st>>>(tab_dev, w, cur, steps, one, order, err);
 }
 
-// Secondary closest-hit rays are reordered in launches over one scene when
-// the launcher asks for it: sets the launch's bin grid and key array (the
-// shading and adjoint stages then write each appended ray's bin).
-static void sort_setup(const Launcher& L, const std::vector<WfScene>& tab, const WfBuffers& wb, WfParams& lp) {
+// Secondary closest-hit rays are reordered when the launcher asks for it:
+// sets the chunk's bin grid and key array (the shading and adjoint stages
+// then write each appended ray's bin).  A chunk over several scenes keeps
+// their bins apart (scene major) and coarsens the grid until all its scenes'
+// bins fit the kSortMaxBins the shared histograms hold.
+static void sort_setup(const Launcher& L, const std::vector<WfScene>& tab, const WfBuffers& wb, const WfChunk& c,
+                       WfParams& lp) {
   lp.keys = nullptr;
   lp.bin = BinGrid{};
-  if (L.sort_cells <= 0 || tab.size() != 1 || !wb.qs || !wb.keys || !wb.bins) return;
+  if (L.sort_cells <= 0 || !wb.qs || !wb.keys || !wb.bins) return;
+  uint32_t b0 = 0;
+  while (b0 + 1 < tab.size() && tab[b0].pix_begin + tab[b0].n_pix <= c.p0) ++b0;
+  uint32_t b1 = b0 + 1;
+  while (b1 < tab.size() && tab[b1].pix_begin < c.p0 + c.n_pix) ++b1;
+  const uint32_t nsc = b1 - b0;
   BinGrid g;
   g.cells = L.sort_cells;
   g.dirs = L.sort_dirs;
-  g.n_bins = (g.dirs ? 6u * (uint32_t)(g.dirs * g.dirs) : 1u) * (uint32_t)(g.cells * g.cells * g.cells);
-  if (g.n_bins > kSortMaxBins) return;
-  const WfScene& e = tab[0];
-  const float ex = e.bb_hi.x - e.bb_lo.x, ey = e.bb_hi.y - e.bb_lo.y, ez = e.bb_hi.z - e.bb_lo.z;
-  g.lo = e.bb_lo;
-  g.scale = make_float3(ex > 0.f ? g.cells / ex : 0.f, ey > 0.f ? g.cells / ey : 0.f, ez > 0.f ? g.cells / ez : 0.f);
+  for (;;) {
+    g.per_scene = (g.dirs ? 6u * (uint32_t)(g.dirs * g.dirs) : 1u) * (uint32_t)(g.cells * g.cells * g.cells);
+    if ((uint64_t)g.per_scene * nsc <= kSortMaxBins) break;
+    if (g.cells > 1) {
+      --g.cells;
+    } else if (g.dirs > 0) {
+      --g.dirs;
+    } else {
+      return;  // more scenes in the chunk than bins: queue order
+    }
+  }
+  g.scene0 = b0;
+  g.n_bins = g.per_scene * nsc;
   lp.bin = g;
   lp.keys = wb.keys;
 }
@@ -1747,7 +1766,6 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
   const uint32_t ns = (uint32_t)tab.size();
   if (disney && cache) return cudaErrorInvalidValue;
   WfParams lp = wf_params(tp, loss_kind, ns, iter_dev);
-  sort_setup(L, tab, wb, lp);
   wf_cache_params(lp, cache, tp.max_depth);
   const bool query = lp.cache_k != kNoCache && !lp.cache_record;
   const bool record = lp.cache_k != kNoCache && lp.cache_record;
@@ -1765,6 +1783,7 @@ cudaError_t wf_forward(const Launcher& L, const WfScene* tab_dev, const std::vec
   int first = 1;
   for (const WfChunk& c : chunks) {
     const uint32_t slots = c.n_pix * tp.spp;
+    sort_setup(L, tab, wb, c, lp);
     {
       IPT_STAGE(7);
       wf_camera<<<grid_cam, kWfThreads, 0, st>>>(tab_dev, lp, c.p0, slots, w);
@@ -1841,7 +1860,6 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
   const uint32_t max_seg = kD ? wf_max_segments() * 10u / 16u : wf_max_segments();
   const uint32_t ns = (uint32_t)tab.size();
   WfParams lp = wf_params(tp, 0, ns, iter_dev);
-  sort_setup(L, tab, wb, lp);
   if (cache && cache->record) return cudaErrorInvalidValue;
   if (kD && (!wb.aWi || !wb.aWo || !wb.sh_dv)) return cudaErrorInvalidValue;
   wf_cache_params(lp, cache, tp.max_depth);
@@ -1872,6 +1890,7 @@ static cudaError_t wf_adjoint_model(const Launcher& L, const WfScene* tab_dev, c
   for (const WfChunk& c : chunks) {
     lp.seg_lo = c.seg_lo;
     lp.seg_n = c.seg_n;
+    sort_setup(L, tab, wb, c, lp);
     const uint32_t np = P * c.seg_n;
     const bool global = c.seg_n > max_seg;
     lp.gacc = global ? wb.blk : nullptr;

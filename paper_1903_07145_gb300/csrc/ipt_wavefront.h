@@ -37,7 +37,7 @@ struct WfScene {
   // the entry of a launch pixel is its scene pixel id.
   uint32_t* pick;
   uint32_t n_all;            // pixels of the scene the batch draws from
-  float3 bb_lo, bb_hi;       // vertex bounding box (ray reordering's origin grid)
+  float3 bb_lo, bb_inv;      // vertex bounding box: lower corner, 1 / extent per axis (0 if flat)
 };
 
 // Radiance cache in a pass: query mode ends paths at vertex b_term and adds

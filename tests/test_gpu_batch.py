@@ -31,9 +31,10 @@ def uneven_scenes():
     ]
 
 
-def prepared(seed=5, slots=0, bvh_width=0, integrator="wavefront"):
+def prepared(seed=5, slots=0, bvh_width=0, integrator="wavefront", sort_cells=0, sort_dirs=0):
     ss = SceneSet(uneven_scenes(), seed=seed)
-    ss.configure(integrator, wavefront_slots=slots, bvh_width=bvh_width)
+    ss.configure(integrator, wavefront_slots=slots, bvh_width=bvh_width, sort_cells=sort_cells,
+                 sort_dirs=sort_dirs)
     for i, sc in enumerate(ss.scenes):
         ss.set_params(i, sc.gt_params)
         ss.set_targets(i, ss.render(i, TraceOptions(max_depth=4), spp=32))
@@ -72,6 +73,31 @@ def test_batch_equals_single_scene_steps(built, slots, bvh_width, integrator):
         d = np.abs(ss.batch_params(i) - ref_params[i])
         assert np.mean(d < 1e-5) >= 0.95 and d.max() <= 6 * adam.lr, (i, d.max())
     ss.close()
+
+
+@pytest.mark.parametrize("slots", [0, 4096])
+def test_batch_ray_reordering_gives_the_same_steps(built, slots):
+    """A batch whose bounces are reordered by (scene, direction cell, origin
+    cell) takes the same steps as one in queue order: the grid is coarsened
+    per chunk until its scenes' bins fit (three scenes: 6^3 cells x 24
+    directions becomes 4^3 x 24), and chunks that end inside scenes keep
+    each scene's rays in its own bins."""
+    opts = TraceOptions(spp_r=8, spp_d=8, max_depth=4)
+    adam = AdamOptions()
+    out = []
+    for cells, dirs in ((0, 0), (6, 2), (16, 0)):
+        ss = prepared(slots=slots, bvh_width=4, sort_cells=cells, sort_dirs=dirs)
+        ss.make_batch()
+        losses = [ss.batch_step(opts, adam) for _ in range(2)]
+        out.append((losses, [ss.batch_params(i) for i in range(3)]))
+        ss.close()
+    (l0, p0) = out[0]
+    for losses, params in out[1:]:
+        for i in range(3):
+            assert abs(losses[0][i] - l0[0][i]) <= 1e-6 * abs(l0[0][i]), i
+            assert abs(losses[1][i] - l0[1][i]) <= 1e-3 * abs(l0[1][i]), i
+            d = np.abs(params[i] - p0[i])
+            assert np.mean(d < 1e-5) >= 0.95 and d.max() <= 6 * adam.lr, (i, d.max())
 
 
 def test_batch_graph_recaptures_on_new_options(built):
