@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <functional>
 #include <cmath>
+#include <queue>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -176,6 +177,135 @@ struct Builder {
   }
 };
 
+// Insertion-based optimisation of the binary tree (after Bittner, Hapala
+// and Havran, "Fast insertion-based optimization of bounding volume
+// hierarchies", 2013): each subtree in turn is taken out and put back as the
+// sibling of the node where the tree's surface-area cost grows least (a
+// best-first search over the induced cost of the ancestors).  Leaves keep
+// their triangle ranges; the root stays node 0.
+struct Reinserter {
+  std::vector<BNode>& nd;
+  std::vector<int> parent;
+
+  explicit Reinserter(std::vector<BNode>& n) : nd(n), parent(n.size(), -1) {
+    for (size_t i = 0; i < nd.size(); ++i)
+      if (nd[i].left >= 0) {
+        parent[nd[i].left] = (int)i;
+        parent[nd[i].right] = (int)i;
+      }
+  }
+  static double merged_area(const Box& a, const Box& b) {
+    Box r = a;
+    r.grow(b);
+    return r.area();
+  }
+  void refit(int i) {
+    for (; i >= 0; i = parent[i]) {
+      nd[i].box = nd[nd[i].left].box;
+      nd[i].box.grow(nd[nd[i].right].box);
+    }
+  }
+  // takes subtree x out (its parent is bypassed); returns the freed parent
+  int take_out(int x) {
+    const int p = parent[x], g = parent[p];
+    const int sib = nd[p].left == x ? nd[p].right : nd[p].left;
+    (nd[g].left == p ? nd[g].left : nd[g].right) = sib;
+    parent[sib] = g;
+    refit(g);
+    return p;
+  }
+  // the node whose new parent (shared with a subtree of box b) adds least cost
+  int best_sibling(const Box& b) const {
+    struct Cand {
+      double induced;
+      int n;
+      bool operator<(const Cand& o) const { return induced > o.induced; }
+    };
+    const double ab = b.area();
+    int best = 0;
+    double best_cost = merged_area(nd[0].box, b);
+    std::priority_queue<Cand> q;
+    q.push({0.0, 0});
+    while (!q.empty()) {
+      const Cand c = q.top();
+      q.pop();
+      if (c.induced + ab >= best_cost) break;
+      const double total = c.induced + merged_area(nd[c.n].box, b);
+      if (total < best_cost) {
+        best_cost = total;
+        best = c.n;
+      }
+      if (nd[c.n].left >= 0) {
+        const double induced = total - nd[c.n].box.area();
+        if (induced + ab < best_cost) {
+          q.push({induced, nd[c.n].left});
+          q.push({induced, nd[c.n].right});
+        }
+      }
+    }
+    return best;
+  }
+  // puts subtree x back as the sibling of node `at`, under the freed node p
+  void put_back(int x, int p, int at) {
+    const int g = parent[at];
+    nd[p].left = at;
+    nd[p].right = x;
+    parent[at] = p;
+    parent[x] = p;
+    parent[p] = g;
+    if (g >= 0) {
+      (nd[g].left == at ? nd[g].left : nd[g].right) = p;
+      refit(p);
+      return;
+    }
+    // `at` is the root: the new parent takes index 0, the old root index p
+    std::swap(nd[0], nd[p]);
+    nd[0].left = p;
+    for (int c : {nd[p].left, nd[p].right})
+      if (c >= 0) parent[c] = p;
+    parent[p] = 0;
+    parent[x] = 0;
+    parent[0] = -1;
+    refit(0);
+  }
+  void run(int passes) {
+    for (int it = 0; it < passes; ++it)
+      for (int x = 1; x < (int)nd.size(); ++x) {
+        const int p = parent[x];
+        if (p <= 0) continue;  // the root's children stay
+        const int freed = take_out(x);
+        put_back(x, freed, best_sibling(nd[x].box));
+      }
+  }
+};
+
+// Renumbers the tree in pre-order from the root (parents before children,
+// as the collapse to wide nodes expects) and sets every node's depth.
+void preorder(std::vector<BNode>& nd) {
+  std::vector<BNode> out;
+  out.reserve(nd.size());
+  std::vector<std::pair<int, int>> st = {{0, -1}};  // (old index, new parent index)
+  while (!st.empty()) {
+    const auto [o, np] = st.back();
+    st.pop_back();
+    BNode n = nd[o];
+    n.depth = np < 0 ? 0 : out[np].depth + 1;
+    const int me = (int)out.size();
+    if (np >= 0) (out[np].left == -2 ? out[np].left : out[np].right) = me;
+    const int l = n.left, r = n.right;
+    if (l >= 0) {
+      n.left = -2;  // filled in when the children are emitted
+      n.right = -2;
+    }
+    out.push_back(n);
+    if (l >= 0) {
+      st.push_back({r, me});
+      st.push_back({l, me});
+    }
+  }
+  nd.swap(out);
+}
+
 // 4-wide node with 8-bit child boxes (64 bytes, 16 words):
 //   w0..w2: origin p (float bits); w3: exponents ex | ey << 8 | ez << 16 |
 //   child count << 24; w4..w7: child links (inner node index, or a leaf code
@@ -321,6 +451,16 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
     for (int k = 0; k < 3; ++k) B.cen[3 * t + k] = 0.5 * (B.pbox[t].lo[k] + B.pbox[t].hi[k]);
   }
   B.build(n_tri);
+  {
+    // three passes of subtree reinsertion (one above a million triangles);
+    // kept unless it deepens the tree beyond what the traversal stack holds
+    std::vector<BNode> keep = B.nodes;
+    Reinserter(B.nodes).run(n_tri > (1u << 20) ? 1 : 3);
+    preorder(B.nodes);
+    int deepest = 0;
+    for (const BNode& n : B.nodes) deepest = std::max(deepest, n.depth);
+    if (deepest > 48) B.nodes.swap(keep);
+  }
 
   // inner nodes in depth-first order; children boxes stored in the parent
   const double pad = maxabs * 1e-6 + 1e-30;
