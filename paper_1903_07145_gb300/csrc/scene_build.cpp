@@ -1,6 +1,7 @@
-// Host-side scene build: input validation, a binned-SAH binary BVH laid out
-// for the GPU traversal, triangles in leaf order, and the per-segment area
-// tables used for light selection.  Compiled without floating-point
+// Host-side scene build: input validation, a binned-SAH binary BVH refined by
+// subtree reinsertion and laid out for the GPU traversal (binary, 4-wide and
+// 8-wide nodes), triangles in leaf order, and the per-segment area tables
+// used for light selection.  Compiled without floating-point
 // contraction so the FP64 area sums are reproducible across hosts.
 #include <algorithm>
 #include <functional>
