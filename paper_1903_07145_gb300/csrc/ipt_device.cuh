@@ -272,7 +272,9 @@ __device__ __forceinline__ float q_unit(uint32_t w, int i) {
 //    B = (origin - o) / d - A, evaluated as one fma.  Rounding B, and the
 //    margins below, add absolute errors of at most 2^-24 |A| each to a plane
 //    distance of that axis (beyond the relative rounding the far-plane factor
-//    1.0000005 covers).  Each axis's near planes therefore use B - 2^-22 |A|
+//    1.0000005 covers).  A itself is a rounded product (the node stores
+//    2^15 * scale as a float), but B carries the same A, so its rounding
+//    enters t only through (u - 1) * A, u - 1 < 2^-7: below 2^-31 |A|.  Each axis's near planes therefore use B - 2^-22 |A|
 //    and its far planes B + 2^-22 |A| (a widening of 2^-7 of a code on each
 //    side, a few times the error bound): a child box is never missed because
 //    of it.
@@ -280,11 +282,8 @@ __device__ __forceinline__ uint32_t node4_children(const SceneDev& s, int node, 
                                                    float tn[4], int ref[4]) {
   uint4 a, c, qa, qb;
   load_node4(&s.nodes4[4 * node], a, c, qa, qb);
-  // 2^15 * scale: the stored biased exponent plus 15 (the builder keeps the
-  // exponent at most 239)
-  const float sx = __uint_as_float(((a.w & 0xffu) + 15u) << 23);
-  const float sy = __uint_as_float((((a.w >> 8) & 0xffu) + 15u) << 23);
-  const float sz = __uint_as_float((((a.w >> 16) & 0xffu) + 15u) << 23);
+  // 2^15 * scale of each axis, stored in words 3, 14 and 15
+  const float sx = __uint_as_float(a.w), sy = __uint_as_float(qb.z), sz = __uint_as_float(qb.w);
   const float Ax = sx * r.inv.x, Bx = fmaf(__uint_as_float(a.x) - r.o.x, r.inv.x, -Ax);
   const float Ay = sy * r.inv.y, By = fmaf(__uint_as_float(a.y) - r.o.y, r.inv.y, -Ay);
   const float Az = sz * r.inv.z, Bz = fmaf(__uint_as_float(a.z) - r.o.z, r.inv.z, -Az);

@@ -308,16 +308,18 @@ void preorder(std::vector<BNode>& nd) {
 }
 
 // 4-wide node with 8-bit child boxes (64 bytes, 16 words):
-//   w0..w2: origin p (float bits); w3: exponents ex | ey << 8 | ez << 16 |
-//   child count << 24; w4..w7: child links (inner node index, or a leaf code
-//   as in the binary layout); w8: lo.x of children 0..3 (one byte each),
-//   w9: hi.x, w10: lo.y, w11: hi.y, w12: lo.z, w13: hi.z; w14, w15 unused.
+//   w0..w2: origin p (float bits); w3, w14, w15: 2^15 * scale of the x, y
+//   and z axes (float bits); w4..w7: child links (inner node index, or a
+//   leaf code as in the binary layout); w8: lo.x of children 0..3 (one byte
+//   each), w9: hi.x, w10: lo.y, w11: hi.y, w12: lo.z, w13: hi.z.  A child
+//   box is p + q * scale per axis, the scale the smallest float for which 255
+//   codes span the node's box (at most one code of slack per side).
 // 8-wide node (96 bytes, 24 words): w0..w2 origin, w3 exponents | mask of
 //   occupied slots << 24; per axis k, w4+4k..w5+4k the lower bytes and
 //   w6+4k..w7+4k the upper bytes of slots 0..3 and 4..7; w16..w23 the
 //   slots' links (the first 64 bytes are all a node test reads).
-// A child box is p + q * 2^(e - 127) per axis, rounded outward so that it
-// contains the child's (padded) box in float arithmetic.
+// An 8-wide child box is p + q * 2^(e - 127) per axis, rounded outward so
+// that it contains the child's (padded) box in float arithmetic.
 struct Quantizer {
   float p;
   int e;  // biased exponent of the scale
@@ -359,6 +361,33 @@ uint32_t q_hi(const Quantizer& a, double hi) {
   int q = (int)std::ceil((hi - (double)a.p) / (double)s);
   q = std::min(std::max(q, 0), 255);
   while (q < 255 && (double)(a.p + (float)q * s) < hi) ++q;
+  return (uint32_t)q;
+}
+
+// 4-wide nodes: any float scale (the traversal reads it from the node).
+struct ScaleQuantizer {
+  float p, s;  // plane q of the axis at p + q * s (exact in double)
+};
+
+ScaleQuantizer make_scale_axis(double lo, double hi) {
+  ScaleQuantizer q;
+  q.p = std::nextafter((float)lo, -INFINITY);
+  q.s = (float)std::max((hi - (double)q.p) / 255.0, 1e-30);
+  while ((double)q.p + 255.0 * (double)q.s < hi) q.s = std::nextafter(q.s, INFINITY);
+  return q;
+}
+
+uint32_t q_lo(const ScaleQuantizer& a, double lo) {
+  int q = (int)std::floor((lo - (double)a.p) / (double)a.s);
+  q = std::min(std::max(q, 0), 255);
+  while (q > 0 && (double)a.p + q * (double)a.s > lo) --q;
+  return (uint32_t)q;
+}
+
+uint32_t q_hi(const ScaleQuantizer& a, double hi) {
+  int q = (int)std::ceil((hi - (double)a.p) / (double)a.s);
+  q = std::min(std::max(q, 0), 255);
+  while (q < 255 && (double)a.p + q * (double)a.s < hi) ++q;
   return (uint32_t)q;
 }
 
@@ -603,12 +632,14 @@ bool build_scene(const float* pos, uint32_t n_vert, const float* nrm, const uint
         }
         u.grow(cb[i]);
       }
-      Quantizer qa[3];
-      for (int k = 0; k < 3; ++k) qa[k] = make_axis(u.lo[k], u.hi[k]);
+      ScaleQuantizer qa[3];
+      for (int k = 0; k < 3; ++k) qa[k] = make_scale_axis(u.lo[k], u.hi[k]);
       uint32_t w[16] = {0};
-      for (int k = 0; k < 3; ++k) std::memcpy(&w[k], &qa[k].p, 4);
-      w[3] = (uint32_t)qa[0].e | ((uint32_t)qa[1].e << 8) | ((uint32_t)qa[2].e << 16) |
-             ((uint32_t)ch.size() << 24);
+      for (int k = 0; k < 3; ++k) {
+        std::memcpy(&w[k], &qa[k].p, 4);
+        const float s15 = qa[k].s * 32768.0f;  // exact: a power-of-two factor
+        std::memcpy(&w[k == 0 ? 3 : 13 + k], &s15, 4);
+      }
       for (size_t i = 0; i < ch.size(); ++i) {
         const BNode& c = B.nodes[ch[i]];
         int ref;
