@@ -1,12 +1,15 @@
-// Structural check of the scene builder's 4-wide BVH, compiled and run on
-// the host by tests/test_bvh_cpu.py: decodes the 64-byte nodes on its own
-// (origin, per-axis float scales, 8-bit child codes, links) and checks that
+// Structural check of the scene builder's wide BVHs, compiled and run on the
+// host by tests/test_bvh_cpu.py.  It decodes the nodes on its own and checks
+// that, in the 4-wide tree (64-byte nodes: origin, per-axis float scales,
+// 8-bit child codes, links) and in the 8-wide tree (96-byte nodes: origin,
+// per-axis power-of-two scales, occupied-slot mask, codes, links),
 //  * every triangle lies in exactly one leaf,
 //  * every child box, p + q * scale per axis evaluated in double, contains
 //    the exact bounds of all triangles below that child,
-//  * empty slots hold inverted boxes and repeat child 0's link.
+//  * 4-wide empty slots hold inverted boxes and repeat child 0's link.
 // Input (binary files): float32 positions (n_vert x 3), uint32 indices
-// (n_tri x 3).  Prints "tris_once violations nodes4 depth".
+// (n_tri x 3).  Prints "tris_once4 violations4 tris_once8 violations8
+// nodes4 depth".
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -85,6 +88,30 @@ Bounds visit(int ref) {
   return b;
 }
 
+// the same for the 8-wide tree
+Bounds visit8(int ref) {
+  Bounds b;
+  if (ref < 0) return visit(ref);
+  const uint32_t* w = &S->nodes8[24 * (size_t)ref];
+  const double p[3] = {word_f(w[0]), word_f(w[1]), word_f(w[2])};
+  double s[3];
+  for (int k = 0; k < 3; ++k) s[k] = std::ldexp(1.0, (int)((w[3] >> (8 * k)) & 0xffu) - 127);
+  const uint32_t valid = w[3] >> 24;
+  for (int j = 0; j < 8; ++j) {
+    if (!(valid >> j & 1u)) continue;
+    int link;
+    std::memcpy(&link, &w[16 + j], 4);
+    const Bounds c = visit8(link);
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t qlo = (w[4 + 4 * k + j / 4] >> (8 * (j % 4))) & 0xffu;
+      const uint32_t qhi = (w[6 + 4 * k + j / 4] >> (8 * (j % 4))) & 0xffu;
+      if (p[k] + qlo * s[k] > c.lo[k] || p[k] + qhi * s[k] < c.hi[k]) ++violations;
+    }
+    b.grow(c);
+  }
+  return b;
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
@@ -101,10 +128,15 @@ int main(int argc, char** argv) {
     return 1;
   }
   S = &hs;
-  seen.assign(nt, 0);
-  visit(0);
-  long once = 0;
-  for (int v : seen) once += v == 1;
-  std::printf("%ld %ld %u %u\n", once, violations, hs.n_nodes4, hs.depth);
+  long once[2] = {0, 0}, viol[2] = {0, 0};
+  for (int wide = 0; wide < 2; ++wide) {
+    seen.assign(nt, 0);
+    violations = 0;
+    if (wide == 0) visit(0);
+    else if (hs.n_nodes8 > 0) visit8(0);
+    for (int v : seen) once[wide] += v == 1;
+    viol[wide] = violations;
+  }
+  std::printf("%ld %ld %ld %ld %u %u\n", once[0], viol[0], once[1], viol[1], hs.n_nodes4, hs.depth);
   return 0;
 }

@@ -1,8 +1,9 @@
-"""The scene builder's 4-wide BVH checked on the host: tests/bvh_check.cpp is
-compiled with the builder (g++, no GPU) and decodes the nodes on its own.
-Every triangle must lie in exactly one leaf, every quantized child box
-(origin + code * scale per axis, in double) must contain the exact bounds of
-the triangles below it, and empty slots must hold inverted boxes.  Meshes:
+"""The scene builder's wide BVHs checked on the host: tests/bvh_check.cpp is
+compiled with the builder (g++, no GPU) and decodes the 4- and 8-wide nodes
+on its own.  Every triangle must lie in exactly one leaf of each tree, every
+quantized child box (origin + code * scale per axis, in double) must contain
+the exact bounds of the triangles below it, and 4-wide empty slots must hold
+inverted boxes.  Meshes:
 a small procedural room, the 61k-triangle benchmark room, a flat grid (zero
 extent on one axis), the same grid at coordinates near 1e26, a random
 triangle soup, and one and two triangles."""
@@ -74,7 +75,7 @@ def test_bvh_covers_every_triangle_with_conservative_boxes(checker, tmp_path, na
     np.ascontiguousarray(idx, np.uint32).tofile(xf)
     out = subprocess.run([checker, str(pf), str(xf), str(len(pos)), str(len(idx))], capture_output=True,
                          text=True, check=True).stdout.split()
-    once, violations, nodes4, depth = (int(v) for v in out)
-    assert once == len(idx), (once, len(idx))
-    assert violations == 0
+    once4, violations4, once8, violations8, nodes4, depth = (int(v) for v in out)
+    assert once4 == len(idx) and once8 == len(idx), (once4, once8, len(idx))
+    assert violations4 == 0 and violations8 == 0
     assert nodes4 >= 1 and depth <= 48
